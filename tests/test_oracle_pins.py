@@ -1,0 +1,338 @@
+"""Pins of the FP64 oracle against things other than itself: closed forms,
+brute-force state-vector simulation of the uncut circuit, invariants, the
+paper's worked-example counts, and hand counts.  A planted mistake in the
+oracle must fail at least one of them (see the planted-mistake tests)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import attribution, dd, fd, metrics, statevector
+from oracle import mlp as omlp
+from workloads import circuits as C
+from workloads.cutting import build_cut, search_cut, eq2_cost, Dag
+from workloads.simulate import simulate_variants
+
+
+def _attr(subs, variants):
+    return [attribution.attribute(v, s.w, s.in_local, s.out_local, s.in_edge, s.out_edge)
+            for s, v in zip(subs, variants)]
+
+
+def _reconstruct(cut, order="original"):
+    subs = cut.subcircuits
+    A = _attr(subs, [simulate_variants(s) for s in subs])
+    pk = fd.reconstruct_kron(A, [s.edges for s in subs], cut.K)
+    if order == "kron":
+        return pk, A
+    return fd.kron_to_original(pk, [s.out_qubit for s in subs]), A
+
+
+# ---------------------------------------------------------------- closed forms
+
+def _rand_rho(rng):
+    g = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+    r = g @ g.conj().T
+    return r / np.trace(r)
+
+
+def _rand_unitary(rng):
+    q, r = np.linalg.qr(rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2)))
+    return q * (np.diag(r) / abs(np.diag(r)))
+
+
+H = np.array([[1, 1], [1, -1]]) / math.sqrt(2)
+SDG = np.diag([1, -1j])
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_single_cut_pauli_identity(seed):
+    """One cut between a (mixed) one-qubit state rho and a unitary V: the
+    reconstruction must give <b| V rho V^+ |b>.  Variants written from the
+    closed forms, not from any simulator."""
+    rng = np.random.default_rng(seed)
+    rho, V = _rand_rho(rng), _rand_unitary(rng)
+    up = np.zeros((1, 3, 2))       # upstream: w=1, the qubit is the measured cut
+    for m, R in enumerate([np.eye(2), H, H @ SDG]):
+        r = R @ rho @ R.conj().T
+        up[0, m] = np.real(np.diag(r))
+    states = [np.array([1, 0]), np.array([0, 1]),
+              np.array([1, 1]) / math.sqrt(2), np.array([1, 1j]) / math.sqrt(2)]
+    down = np.zeros((4, 1, 2))     # downstream: w=1, init cut, output
+    for s, st in enumerate(states):
+        down[s, 0] = np.abs(V @ st) ** 2
+    A_up = attribution.attribute(up, 1, [], [0], [], [0])
+    A_dn = attribution.attribute(down, 1, [0], [], [0], [])
+    assert A_up.shape == (1, 4) and A_dn.shape == (2, 4)
+    p = fd.reconstruct_kron([A_up, A_dn], [[0], [0]], 1)
+    exact = np.real(np.diag(V @ rho @ V.conj().T))
+    np.testing.assert_allclose(p, exact, atol=1e-14)
+
+
+def test_attribution_bases_match_pauli_traces():
+    """Upstream attributed entries are Tr(rho M) for M = I, X, Y, Z."""
+    rng = np.random.default_rng(7)
+    rho = _rand_rho(rng)
+    up = np.zeros((1, 3, 2))
+    for m, R in enumerate([np.eye(2), H, H @ SDG]):
+        up[0, m] = np.real(np.diag(R @ rho @ R.conj().T))
+    A = attribution.attribute(up, 1, [], [0], [], [0])[0]
+    paulis = [np.eye(2), np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.diag([1, -1])]
+    np.testing.assert_allclose(A, [np.real(np.trace(rho @ P)) for P in paulis], atol=1e-14)
+
+
+def test_qft_of_zero_is_uniform():
+    """AQFT on |0...0> (input angles 0) outputs |+>^n: uniform 2^-n."""
+    c = C.aqft(9, 0, max_dist=3, input_scale=0.0)
+    cut = search_cut(c, 6, 2, restarts=4)
+    assert cut is not None and cut.K > 0
+    p, _ = _reconstruct(cut)
+    np.testing.assert_allclose(p, np.full(2 ** 9, 2.0 ** -9), atol=1e-14)
+
+
+@pytest.mark.parametrize("n,seed", [(9, 1), (12, 4)])
+def test_bv_single_bitstring(n, seed):
+    c = C.bv(n, seed, hidden=[1, 0, 1, 1, 0, 1, 1, 0, 1, 1, 0][: n - 1])
+    cut = search_cut(c, 4, 4, restarts=4)
+    assert cut is not None and cut.K >= 1
+    p, _ = _reconstruct(cut)
+    hidden = c.meta["hidden"]
+    x = sum(b << q for q, b in enumerate(hidden)) | (1 << (n - 1))
+    assert np.argmax(p) == x
+    assert abs(p[x] - 1) < 1e-12
+    assert metrics.norm_error(p) < 1e-12
+
+
+# ------------------------------------------------------------ worked example
+
+def _worked_example_circuit():
+    c = C.Circuit(5)
+    for q in range(5):
+        c.add("h", (q,))
+    c.add("cz", (0, 1))
+    c.add("rx", (2,), (0.3,))
+    c.add("cz", (1, 2))       # first CZ on q2
+    c.add("ry", (2,), (1.1,))
+    c.add("cz", (2, 3))       # second CZ on q2
+    c.add("cz", (3, 4))
+    c.add("rz", (4,), (0.7,))
+    return c
+
+
+def test_worked_example_counts(repo_root):
+    g = json.load(open(os.path.join(repo_root, "tests", "golden", "worked_example.json")))
+    c = _worked_example_circuit()
+    # cluster: gates on q0..q2 up to the first CZ on q2 -> 0, the rest -> 1
+    cut = build_cut(c, [0, 0, 1, 1])
+    assert cut.K == g["cuts"]
+    assert [s.w for s in cut.subcircuits] == g["subcircuit_widths"]
+    var = [simulate_variants(s) for s in cut.subcircuits]
+    assert [v.shape[0] * v.shape[1] for v in var] == g["variants"]
+    assert 4 ** cut.K == g["kronecker_terms"]
+    p, _ = _reconstruct(cut)
+    np.testing.assert_allclose(p, statevector.probabilities(c), atol=1e-14)
+
+
+# ------------------------------------------------------------ brute force
+
+def _cases():
+    yield "brickwall8", C.brickwall(8, 6, 0), 7, 2
+    yield "brickwall9_3sub", C.brickwall(9, 4, 3), 5, 3
+    yield "supremacy3x3", C.supremacy(3, 3, 6, 2), 6, 2
+    yield "aqft10_3sub", C.aqft(10, 5, max_dist=2), 6, 3
+    yield "aqft10_4sub", C.aqft(10, 6, max_dist=2), 5, 4
+
+
+@pytest.mark.parametrize("name,c,w,nsub", list(_cases()))
+def test_fd_matches_bruteforce(name, c, w, nsub):
+    cut = search_cut(c, w, nsub, restarts=4)
+    assert cut is not None and cut.K > 0
+    assert sum(s.w for s in cut.subcircuits) == c.n + cut.K
+    assert sum(s.o for s in cut.subcircuits) == c.n
+    p, A = _reconstruct(cut)
+    exact = statevector.probabilities(c)
+    assert metrics.max_abs(p, exact) < 1e-12
+    assert metrics.tv(p, exact) < 1e-12
+    # analytic total and sampled entries agree with the full vector
+    edges = [s.edges for s in cut.subcircuits]
+    assert abs(fd.total_probability(A, edges, cut.K) - 1) < 1e-12
+    idx = np.random.default_rng(0).integers(0, 2 ** c.n, size=64)
+    parts = fd.split_original_index(idx, [s.out_qubit for s in cut.subcircuits])
+    np.testing.assert_allclose(fd.entries(A, edges, cut.K, parts), exact[idx], atol=1e-13)
+
+
+def test_kron_order_is_numpy_kron():
+    """'kron' order = np.kron of the per-subcircuit vectors for one term."""
+    a0 = np.array([1.0, 2.0])[:, None]
+    a1 = np.array([3.0, 5.0, 7.0, 11.0])[:, None]
+    np.testing.assert_allclose(fd.reconstruct_kron([a0, a1], [[], []], 0), np.kron(a0[:, 0], a1[:, 0]))
+    # original order: subcircuit 0 owns qubit 2, subcircuit 1 owns qubits 0, 1
+    p = fd.kron_to_original(np.kron(a0[:, 0], a1[:, 0]), [[2], [0, 1]])
+    for x in range(8):
+        b0, b12 = (x >> 2) & 1, x & 3
+        assert p[x] == a0[b0, 0] * a1[b12, 0]
+
+
+# ------------------------------------------------------------ DD invariants
+
+def _dd_setup(c, w, nsub):
+    cut = search_cut(c, w, nsub, restarts=4)
+    subs = cut.subcircuits
+    A = _attr(subs, [simulate_variants(s) for s in subs])
+    return cut, A, [s.out_qubit for s in subs], [s.edges for s in subs]
+
+
+def _marginal(p, n, active, zoom):
+    x = np.arange(2 ** n)
+    keep = np.ones(2 ** n, bool)
+    for q, b in zoom.items():
+        keep &= ((x >> q) & 1) == b
+    a = np.zeros(2 ** n, np.int64)
+    for j, q in enumerate(active):
+        a |= ((x >> q) & 1) << j
+    out = np.zeros(2 ** len(active))
+    np.add.at(out, a[keep], p[keep])
+    return out
+
+
+@pytest.mark.parametrize("strategy", ["dfs", "bfs"])
+def test_dd_bins_are_marginals_and_children_sum_to_parent(strategy):
+    c = C.brickwall(10, 4, 11)
+    cut, A, oq, edges = _dd_setup(c, 7, 2)
+    exact = statevector.probabilities(c)
+    jobs = dd.run(A, oq, edges, cut.K, c.n, M=3, R=5, T=2, strategy=strategy)
+    assert len(jobs) >= 3
+    assert abs(jobs[0]["bins"].sum() - 1) < 1e-12
+    for j in jobs:
+        np.testing.assert_allclose(j["bins"], _marginal(exact, c.n, j["active"], j["zoom"]), atol=1e-13)
+    # each child job's bins sum to the parent bin it zooms into
+    for j in jobs[1:]:
+        parent = [p for p in jobs if set(p["zoom"]) < set(j["zoom"])
+                  and all(j["zoom"][q] == v for q, v in p["zoom"].items())
+                  and set(j["zoom"]) == set(p["zoom"]) | set(p["active"])]
+        assert parent
+        par = parent[-1]
+        b = sum(j["zoom"][q] << k for k, q in enumerate(par["active"]))
+        assert abs(j["bins"].sum() - par["bins"][b]) < 1e-13
+
+
+def test_dd_dfs_finds_bv_string():
+    n = 14
+    c = C.bv(n, 9)
+    cut, A, oq, edges = _dd_setup(c, 5, 5)
+    M = 4
+    jobs = dd.run(A, oq, edges, cut.K, n, M=M, R=math.ceil(n / M), T=2, strategy="dfs")
+    last = jobs[-1]
+    assert len(last["zoom"]) + len(last["active"]) == n
+    b = int(np.argmax(last["bins"]))
+    bits = dict(last["zoom"])
+    for j, q in enumerate(last["active"]):
+        bits[q] = (b >> j) & 1
+    hidden = c.meta["hidden"]
+    assert [bits[q] for q in range(n - 1)] == hidden and bits[n - 1] == 1
+    assert abs(last["bins"][b] - 1) < 1e-12
+    assert len(jobs) == math.ceil(n / M)
+
+
+# ------------------------------------------------------------ metrics, costs
+
+def test_metrics_hand_values():
+    a = np.array([0.5, 0.5, 0.0])
+    b = np.array([0.25, 0.5, 0.25])
+    assert metrics.tv(a, b) == pytest.approx(0.25)
+    # Eq. 3: (0.25^2 / 0.75) + 0 + (0.25^2 / 0.25)
+    assert metrics.chi2(a, b) == pytest.approx(0.0625 / 0.75 + 0.25)
+    assert metrics.norm_error(b) == 0.0
+
+
+def test_eq2_hand_counts():
+    c = _worked_example_circuit()
+    cut = build_cut(c, [0, 0, 1, 1])
+    # two subcircuits with 2 and 3 outputs, one cut: 4 * 2^2 * 2^3
+    assert eq2_cost(cut) == 4 * 2 ** 5
+    # three clusters: CZ(0,1) | CZ(1,2), CZ(2,3) | CZ(3,4): cuts on q1 and q3,
+    # outputs 1 (q0), 2 (q1, q2), 2 (q3, q4): 4^2 * (2^(1+2) + 2^(1+2+2)) = 640
+    cut3 = build_cut(c, [0, 1, 1, 2])
+    assert cut3.K == 2 and [s.o for s in cut3.subcircuits] == [1, 2, 2]
+    assert eq2_cost(cut3) == 640
+
+
+def test_dag_counts():
+    c = _worked_example_circuit()
+    d = Dag(c)
+    assert d.nv == 4
+    assert [len(w) for w in d.wire] == [1, 2, 2, 2, 1]
+
+
+# ------------------------------------------------------------ MLP reference
+
+def test_mlp_gradients_finite_difference():
+    rng = np.random.default_rng(3)
+    sizes = (6, 5, 4, 1)
+    params = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        params += [rng.normal(size=(a, b)) * 0.5, rng.normal(size=b) * 0.1]
+    x = rng.normal(size=(7, 6))
+    t = rng.normal(size=7)
+    g = omlp.backward(params, x, t)
+    eps = 1e-6
+    for pi, p in enumerate(params):
+        flat = p.reshape(-1)
+        for k in range(0, flat.size, max(1, flat.size // 5)):
+            old = flat[k]
+            flat[k] = old + eps
+            lp = omlp.loss(params, x, t)
+            flat[k] = old - eps
+            lm = omlp.loss(params, x, t)
+            flat[k] = old
+            assert abs((lp - lm) / (2 * eps) - g[pi].reshape(-1)[k]) < 1e-6
+
+
+def test_adam_first_step_is_signed_lr():
+    p = [np.array([1.0, -2.0])]
+    g = [np.array([0.3, -4.0])]
+    z = [np.zeros(2)]
+    p2, _, _ = omlp.adam_step(p, g, z, z, 1, lr=0.1)
+    np.testing.assert_allclose(p2[0], [0.9, -1.9], atol=1e-7)
+
+
+# ------------------------------------------------------------ planted mistakes
+
+def test_planted_sign_error_is_caught(monkeypatch):
+    """Flip the sign of the Y basis on the init side only: brute force fails."""
+    bad = attribution.INIT_MAP.copy()
+    bad[2] *= -1
+    monkeypatch.setattr(attribution, "INIT_MAP", bad)
+    c = C.brickwall(8, 6, 0)
+    cut = search_cut(c, 7, 2, restarts=4)
+    p, _ = _reconstruct(cut)
+    assert metrics.max_abs(p, statevector.probabilities(c)) > 1e-4
+
+
+def test_planted_swapped_meas_bases_is_caught(monkeypatch):
+    """Use the Y-basis run for X and vice versa on the measured side."""
+    bad = list(attribution.MEAS_MAP)
+    bad[1], bad[2] = (2, 1.0, -1.0), (1, 1.0, -1.0)
+    monkeypatch.setattr(attribution, "MEAS_MAP", tuple(bad))
+    c = C.brickwall(8, 6, 0)
+    cut = search_cut(c, 7, 2, restarts=4)
+    p, _ = _reconstruct(cut)
+    assert metrics.max_abs(p, statevector.probabilities(c)) > 1e-4
+
+
+def test_planted_missing_scale_is_caught():
+    c = C.brickwall(8, 6, 0)
+    cut = search_cut(c, 7, 2, restarts=4)
+    p, _ = _reconstruct(cut)
+    assert metrics.norm_error(p * 2) > 0.5   # a dropped 1/2 per cut breaks sum p = 1
+
+
+def test_planted_order_swap_is_caught():
+    c = C.brickwall(8, 6, 0)
+    cut = search_cut(c, 7, 2, restarts=4)
+    pk, _ = _reconstruct(cut, order="kron")
+    subs = cut.subcircuits
+    wrong = fd.kron_to_original(pk, [s.out_qubit for s in reversed(subs)])
+    assert metrics.max_abs(wrong, statevector.probabilities(c)) > 1e-4

@@ -1,0 +1,74 @@
+"""Input generators: gate matrices, variant tensors, cut structure, and the
+shapes of the benchmark workloads."""
+import math
+
+import numpy as np
+import pytest
+
+from workloads import circuits as C
+from workloads import configs
+from workloads.cutting import build_cut, contraction_plan, search_cut
+from workloads.simulate import simulate_variants
+
+
+@pytest.mark.parametrize("name", ["h", "x", "s", "sdg", "sx", "sy", "sw"])
+def test_gates_unitary(name):
+    U = C.gate_matrix(name)
+    np.testing.assert_allclose(U @ U.conj().T, np.eye(2), atol=1e-14)
+
+
+def test_square_roots():
+    X = C.gate_matrix("x")
+    Y = np.array([[0, -1j], [1j, 0]])
+    W = (X + Y) / math.sqrt(2)
+    for name, P in (("sx", X), ("sy", Y), ("sw", W)):
+        U = C.gate_matrix(name)
+        np.testing.assert_allclose(U @ U, P, atol=1e-14)
+
+
+@pytest.mark.parametrize("name", ["cz", "cx", "cp"])
+def test_two_qubit_unitary(name):
+    U = C.gate_matrix(name, (0.4,))
+    np.testing.assert_allclose(U @ U.conj().T, np.eye(4), atol=1e-14)
+
+
+def test_variants_are_distributions():
+    c = C.brickwall(8, 6, 0)
+    cut = search_cut(c, 7, 2, restarts=4)
+    for s in cut.subcircuits:
+        v = simulate_variants(s)
+        assert v.shape == (4 ** s.k_in, 3 ** s.k_out, 2 ** s.w)
+        np.testing.assert_allclose(v.sum(axis=2), 1.0, atol=1e-12)
+        assert v.min() >= 0
+
+
+def test_cut_structure_invariants():
+    c = C.aqft(12, 2, max_dist=3)
+    cut = search_cut(c, 7, 3, restarts=4)
+    assert sum(s.w for s in cut.subcircuits) == c.n + cut.K
+    ins = sorted(e for s in cut.subcircuits for e in s.in_edge)
+    outs = sorted(e for s in cut.subcircuits for e in s.out_edge)
+    assert ins == outs == list(range(cut.K))
+    qs = sorted(q for s in cut.subcircuits for q in s.out_qubit)
+    assert qs == list(range(c.n))
+
+
+def test_contraction_plan_meets_in_the_middle():
+    # chain 0-1-2-3 with 4 edges per boundary
+    e = [{0, 1, 2, 3}, {0, 1, 2, 3, 4, 5, 6, 7}, {4, 5, 6, 7, 8, 9, 10, 11}, {8, 9, 10, 11}]
+    steps, _ = contraction_plan([7, 7, 7, 11], e)
+    assert steps == [(0, 1), (2, 3), (4, 5)]
+
+
+def test_benchmark_shapes():
+    w1 = configs.fd_plain()
+    assert w1.n == 8 and len(w1.subcircuits) == 2 and max(s.w for s in w1.subcircuits) <= 7
+    w2 = configs.fd_two_sub()
+    assert w2.n == 30 and w2.K == 4
+    assert [(s.w, s.k_in, s.k_out, s.o) for s in w2.subcircuits] == [(17, 0, 4, 13), (17, 4, 0, 17)]
+    w3 = configs.fd_chain()
+    assert w3.n == 32 and len(w3.subcircuits) == 4 and all(s.w <= 11 for s in w3.subcircuits)
+    assert sum(s.o for s in w3.subcircuits) == 32
+    for w in configs.dd_batched():
+        assert all(s.w <= 15 for s in w.subcircuits) and len(w.subcircuits) in (4, 5)
+        assert all(1 <= s.k_in + s.k_out <= 3 for s in w.subcircuits)
