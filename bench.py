@@ -1,0 +1,346 @@
+"""Benchmark: full-definition reconstruction of the 30-qubit two-subcircuit
+workload (supremacy-family 5x6 grid, depth 10, K = 4 cuts, subcircuits of 17
+and 17 qubits, 2^30 outputs) on GB300.
+
+One step = attribution of both subcircuits' variant tensors (float64, resident
+in HBM) + the tensor-core FD contraction (FP16 hi/lo split, three products)
+writing all 2^30 float32 probabilities, with the FP64 total.  The 4 GiB output
+is larger than L2, so no flush is needed between steps.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "reconstructed probs/sec (FD) and DD bins/sec at 1 GB300, TV<=1e-6; % of roofline"
+WORKLOAD = "fd_two_sub_supremacy30: 5x6 supremacy-family depth 10, K=4, subcircuits 17+17 -> 2^30 probabilities"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=d["hbm_gbs"], bf16_tflops=d["bf16_tflops"],
+                    bf16_tflops_sustained=d.get("bf16_tflops_sustained", d["bf16_tflops"]), source="measured")
+    return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws, device):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(w, budget_s=15.0):
+    """FP64 oracle as it stands on the host: attribution of both subcircuits
+    (full) then Eq. 1 at a contiguous sample of outputs; the attribution time
+    is prorated to the sample."""
+    from oracle import attribution, fd
+    subs = w.subcircuits
+    var = w.variants()
+    t0 = time.perf_counter()
+    A = [attribution.attribute(v, s.w, s.in_local, s.out_local, s.in_edge, s.out_edge) for s, v in zip(subs, var)]
+    t_attr = time.perf_counter() - t0
+    edges = [s.edges for s in subs]
+    outs = [s.o for s in subs]
+    n_total = 2 ** w.n
+    S = 1 << 14
+    done, t_rec = 0, 0.0
+    while t_rec < budget_s and done < n_total:
+        idx = np.arange(done, min(done + S, n_total), dtype=np.int64)
+        parts = fd.split_kron_index(idx, outs)
+        t1 = time.perf_counter()
+        fd.entries(A, edges, w.K, parts)
+        t_rec += time.perf_counter() - t1
+        done += len(idx)
+    t = t_rec + t_attr * done / n_total
+    return dict(value=done / t, unit="probs/s", cores=_threads(), kind="oracle",
+                sample=f"FP64 oracle: attribution of both subcircuits (full, {t_attr:.1f} s, prorated) + "
+                       f"Eq. 1 at the first {done} outputs in Kronecker order ({t_rec:.1f} s)")
+
+
+def _threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from workloads.configs import fd_two_sub
+    w = fd_two_sub()
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(w, budget_s=args.ref_budget))
+    v = statistics.median(x["value"] for x in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    line = {"metric": METRIC, "value": v, "unit": "probs/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 2 ** w.n / v * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": {"workload": WORKLOAD, "n_qubits": w.n, "cuts": w.K},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "probs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run(args):
+    import torch
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_05836_gb300 import cutqc as cq
+    from workloads.configs import fd_two_sub
+    w = fd_two_sub()
+    subs = w.subcircuits
+    var_host = w.variants()
+    var = [torch.from_numpy(v).to(dev) for v in var_host]
+    kin = [len(s.in_local) for s in subs]
+    att = [torch.empty((1 << s.o, 4 ** (len(s.in_local) + len(s.out_local))), dtype=torch.float32, device=dev)
+           for s in subs]
+    att_ws = [torch.empty(max(1, cq.cutqc_attribute_workspace_size(s)), dtype=torch.uint8, device=dev) for s in subs]
+    n_out = 1 << w.n
+    out = torch.empty(n_out, dtype=torch.float32, device=dev)
+    prec = cq.PREC_FP16X3_TC if args.precision == "tc" else cq.PREC_FP32_SIMT
+    fd_ws = torch.empty(max(1, cq.cutqc_reconstruct_fd_workspace_size(subs, prec)), dtype=torch.uint8, device=dev)
+    total = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def attribute_all():
+        for s, v, a, wsb in zip(subs, var, att, att_ws):
+            cq.cutqc_attribute(s, v, out=a, ws=wsb)
+
+    def reconstruct():
+        total.zero_()
+        cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_KRON, prec, out=out, sum_out=total, ws=fd_ws)
+
+    def step():
+        attribute_all()
+        reconstruct()
+
+    # one step = one replay of a CUDA graph holding every launch of the step
+    # (host argument checks run once, at capture)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(args.warmup):
+            step()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    g_att, g_fd = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_att):
+        attribute_all()
+    with torch.cuda.graph(g_fd):
+        reconstruct()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, ws, dev)
+    sum_err = abs(total.item() - 1.0)
+    status = cq.cutqc_device_status()
+
+    # per-kernel timing of the dominant kernel (the FD contraction), same stream
+    att_ms = []
+    fd_ms = []
+    for _ in range(max(3, args.steps)):
+        a0, a1, f1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a0.record(stream)
+        g_att.replay()
+        a1.record(stream)
+        g_fd.replay()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        att_ms.append(a0.elapsed_time(a1))
+        fd_ms.append(a1.elapsed_time(f1))
+    att_ms = statistics.median(att_ms)
+    fd_ms = statistics.median(fd_ms)
+    M, N = 1 << subs[0].o, 1 << subs[1].o
+    Kg = 4 ** w.K
+    alg_flops = 2.0 * M * N * Kg                    # Eq. 1, one pass
+    exec_flops = 3 * alg_flops if prec == cq.PREC_FP16X3_TC else alg_flops
+    pk = peaks()
+    achieved = alg_flops / (fd_ms * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / pk["bf16_tflops"], "traffic": None,
+                "kernel": "FD contraction (operand prep + tcgen05 GEMM), one launch sequence",
+                "executed_tflops": exec_flops / (fd_ms * 1e-3) / 1e12,
+                "executed_frac": exec_flops / (fd_ms * 1e-3) / 1e12 / pk["bf16_tflops"],
+                "output_gbs": 4.0 * n_out / (fd_ms * 1e-3) / 1e9,
+                "output_frac_of_hbm": 4.0 * n_out / (fd_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                "peak_source": pk["source"] + " (fp16 dense rate = bf16 rate)",
+                "fd_ms": fd_ms, "attribution_ms": att_ms}
+    value = ws * n_out / (ms * 1e-3)
+
+    # end to end through the C ABI from pinned host buffers
+    host_var = [torch.from_numpy(v).pin_memory() for v in var_host]
+    host_out = torch.empty(n_out, dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host_var)
+    d2h = host_out.numel() * 4 + 8
+    host_total = torch.zeros(1, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        # through the C ABI, host arguments checked on every call
+        for hv, v in zip(host_var, var):
+            v.copy_(hv, non_blocking=True)
+        step()
+        host_out.copy_(out, non_blocking=True)
+        host_total.copy_(total, non_blocking=True)
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(2, min(args.steps, 5))
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(g0.elapsed_time(g1) / e2e_steps, ws, dev)
+
+    line = {"metric": METRIC, "value": value, "unit": "probs/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (FP16x3 split tensor-core products, FP32 accumulate)" if prec else "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_qubits": w.n, "cuts": w.K, "gemm": [M, N, Kg],
+                       "precision": args.precision, "l2": "output 4 GiB > L2 each step; no flush",
+                       "parallelism": f"{ws} independent reconstructions (one per GPU)"},
+            "sum_p_error": sum_err, "device_status": status,
+            "roofline": roofline, "clocks": clk.summary(),
+            "e2e": {"value": ws * n_out / (e2e_ms * 1e-3), "unit": "probs/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * (len(subs) + 3)}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, budget_s=args.ref_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="tc", choices=["tc", "simt"])
+    ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run(args)
+
+
+if __name__ == "__main__":
+    main()

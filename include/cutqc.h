@@ -1,0 +1,201 @@
+/* cutqc.h -- C ABI of the GB300 reconstruction library for cut quantum
+ * circuits (Tang & Martonosi, "Cutting Quantum Circuits to Run on Quantum and
+ * Classical Platforms", arXiv 2205.05836).
+ *
+ * The library rebuilds the output distribution of a circuit that was cut into
+ * subcircuits by K wire cuts, from the subcircuits' measured outputs:
+ *
+ *   attribution    variant outputs -> edge-basis tensors   (Circuit Cutting
+ *                  section: per cut the Pauli bases {I,X,Y,Z}, subcircuits
+ *                  "initialized and measured slightly differently")
+ *   FD             P = 2^-K sum_{e in {I,X,Y,Z}^K} kron_i p_{i,e}   (Eq. 1,
+ *                  Full Definition Post-Processing)
+ *   DD             bins over active qubits, merged qubits summed, zoomed
+ *                  qubits fixed (Algorithm 1, Dynamic Definition)
+ *
+ * Conventions (all calls):
+ *  - Pointers named *_dev or documented as device pointers are CUDA device
+ *    memory owned by the caller; the library never frees caller memory and
+ *    never allocates device memory except where a call says so.
+ *  - `stream` is a cudaStream_t passed as void*; work is enqueued
+ *    asynchronously on it (0 = legacy default stream).  Host arrays are read
+ *    during the call only.
+ *  - Every call returns CUTQC_OK or a negative error code; the text of the
+ *    last error of the calling thread is returned by cutqc_last_error().
+ *    Arguments are validated on the host before any launch; on an error
+ *    nothing is enqueued.
+ *  - Bit order: qubit q of the uncut circuit is bit q of an output index;
+ *    local qubit q of a subcircuit is bit q of its outcome index.
+ *  - Edge bases are numbered I=0, X=1, Y=2, Z=3.
+ */
+#ifndef CUTQC_H
+#define CUTQC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CUTQC_OK 0
+#define CUTQC_EINVAL (-1)      /* bad shape, descriptor or argument */
+#define CUTQC_ENOMEM (-2)      /* workspace smaller than the size query */
+#define CUTQC_ECUDA (-3)       /* CUDA error (launch or runtime) */
+#define CUTQC_ETIMEOUT (-4)    /* a bounded device-side wait expired */
+#define CUTQC_EUNSUPPORTED (-5)/* valid but outside this build's limits */
+
+#define CUTQC_F64 0
+#define CUTQC_F32 1
+
+#define CUTQC_ORDER_KRON 0     /* numpy kron order: subcircuit 0's bits most significant */
+#define CUTQC_ORDER_ORIGINAL 1 /* index = sum_q b_q 2^q over the uncut circuit's qubits */
+
+#define CUTQC_PREC_FP32_SIMT 0  /* FP32 CUDA-core contraction */
+#define CUTQC_PREC_FP16X3_TC 1  /* tcgen05 tensor cores: FP16 hi/lo split operands with
+                                   per-row power-of-two scales, hi*hi + hi*lo + lo*hi,
+                                   FP32 accumulation in tensor memory */
+
+/* Limits of this build. */
+#define CUTQC_MAX_QUBITS 34     /* n of an FD reconstruction (2^34 outputs) */
+#define CUTQC_MAX_CUTS 16       /* K per reconstruction */
+#define CUTQC_MAX_WIDTH 30      /* w of one subcircuit */
+
+/* One subcircuit (host memory).  Its local qubits 0..w-1 are its wire
+ * segments.  k_in of them start at a cut (initialised in |0>,|1>,|+>,|+i>),
+ * k_out end at a cut (measured in the computational, X or Y basis); the
+ * other w - k_out local qubits are outputs of the uncut circuit.
+ *   in_local[j], out_local[j]  local qubit of the j-th init / meas cut,
+ *                              strictly ascending
+ *   in_edge[j], out_edge[j]    global cut-edge id (0..K-1) of that cut
+ *   out_qubit[t]               uncut-circuit qubit of the t-th output qubit
+ *                              (outputs in ascending local order)        */
+typedef struct cutqc_subcircuit {
+  int32_t w;
+  int32_t k_in;
+  int32_t k_out;
+  const int32_t* in_local;
+  const int32_t* out_local;
+  const int32_t* in_edge;
+  const int32_t* out_edge;
+  const int32_t* out_qubit;
+} cutqc_subcircuit;
+
+/* Text of the calling thread's last error ("" if none). */
+const char* cutqc_last_error(void);
+
+/* Library version string. */
+const char* cutqc_version(void);
+
+/* Reads and clears the device status word written by bounded device-side
+ * waits (0 = none expired).  Synchronises the device. */
+int cutqc_device_status(int32_t* status_out);
+
+/* ------------------------------------------------------------ attribution
+ * Circuit Cutting section (Eq. 1 and the worked example: three measurement
+ * and four initialisation variants per cut).  With the one-qubit identity
+ * rho = 1/2 sum_M Tr(rho M) M:
+ *   measured cut, outcome m:  I = sum_m pZ(m), Z = sum_m (-1)^m pZ(m),
+ *                             X = sum_m (-1)^m pX(m), Y = sum_m (-1)^m pY(m)
+ *   initialised cut:          I = p0 + p1, Z = p0 - p1,
+ *                             X = 2 p+ - p0 - p1, Y = 2 p+i - p0 - p1
+ * (the 1/2 per cut is applied by the reconstruction).
+ *
+ * variants_dev: [4^k_in][3^k_out][2^w] (F64 or F32), init digit j (state of
+ *   the j-th init cut: 0 |0>, 1 |1>, 2 |+>, 3 |+i>) has weight 4^j, meas digit
+ *   j (0 computational, 1 X basis, 2 Y basis) weight 3^j.
+ * attributed_dev: [2^o][4^k] float32, o = w - k_out, k = k_in + k_out; row =
+ *   output bits (t-th output qubit = bit t), column = sum_j d_j 4^j over the
+ *   subcircuit's cut edges sorted by ascending edge id.
+ * Workspace: cutqc_attribute_workspace_size bytes of device memory (may be
+ * 0 bytes for subcircuits with only one kind of cut).
+ * Errors: CUTQC_EINVAL on a bad descriptor, CUTQC_ENOMEM if ws_bytes is too
+ * small, CUTQC_EUNSUPPORTED if k_in > 6 or k_out > 5.                      */
+int cutqc_attribute_workspace_size(const cutqc_subcircuit* s, size_t* bytes);
+int cutqc_attribute(const cutqc_subcircuit* s, const void* variants_dev, int variants_dtype,
+                    float* attributed_dev, void* ws_dev, size_t ws_bytes, void* stream);
+
+/* --------------------------------------------------------- FD reconstruction
+ * Eq. 1 with the 1/2-per-cut normalisation: P = 2^-K sum_e kron_i A_i[:, c_i(e)].
+ * The subcircuits (n_sub >= 1, their attributed tensors as produced by
+ * cutqc_attribute) are contracted pairwise in a greedy order (cheapest
+ * contraction first); every cut edge must appear in exactly two of them.
+ *
+ * out_dev: float32 output in out_order (KRON or ORIGINAL).  Rows
+ * [row_begin, row_end) of the final contraction are written, where a row is
+ * one value of the high output bits (the operand that the final step puts in
+ * the rows); row_end = -1 means all rows.  With a partial range the output
+ * must be in KRON order and out_dev receives indices
+ * [row_begin * cols, row_end * cols) (cols from cutqc_fd_shape) starting at
+ * out_dev[0].  This is the offset/stride split used to shard one
+ * reconstruction over several GPUs.
+ * sum_dev: optional (nullable) float64 scalar += sum of the written outputs.
+ * Workspace: cutqc_reconstruct_fd_workspace_size bytes.
+ * Errors: CUTQC_EINVAL (descriptor, edge matching, sum of outputs > 34 bits,
+ * order), CUTQC_ENOMEM (workspace), CUTQC_EUNSUPPORTED (limits),
+ * CUTQC_ETIMEOUT is reported later through cutqc_device_status().         */
+int cutqc_fd_shape(int n_sub, const cutqc_subcircuit* s, int64_t* rows, int64_t* cols);
+int cutqc_reconstruct_fd_workspace_size(int n_sub, const cutqc_subcircuit* s, int precision,
+                                        size_t* bytes);
+int cutqc_reconstruct_fd(int n_sub, const cutqc_subcircuit* s, const float* const* attributed_dev,
+                         int out_order, int precision, int64_t row_begin, int64_t row_end,
+                         float* out_dev, double* sum_dev, void* ws_dev, size_t ws_bytes,
+                         void* stream);
+
+/* ------------------------------------------------------------------- DD
+ * Algorithm 1 (Dynamic Definition).  A bin job fixes ("zooms") some qubits,
+ * keeps up to M qubits active and merges the rest.  Because attribution is
+ * linear and touches only cut qubits, merging is applied to each attributed
+ * tensor: merged[a][c] = sum over the subcircuit's merged output bits of
+ * attributed[x][c], over rows x whose zoomed bits equal the job's zoom bits;
+ * a = the active output bits (in ascending output order).
+ *
+ * cutqc_dd_merge: one subcircuit, one job.  role (host, [o]): per output
+ *   qubit 0 = active, 1 = merged, 2 = zoomed to 0, 3 = zoomed to 1.
+ *   merged_dev: [2^a][4^k] float32.
+ * cutqc_dd_merge_batch: one subcircuit, n_jobs jobs that share the
+ *   active/merged split; zoom_dev (device, [n_jobs] uint64) holds per job the
+ *   values of the zoomed output bits (bit t = value of output qubit t; other
+ *   bits ignored), zoom_mask (host) marks which output bits are zoomed.  Job j
+ *   writes merged_dev + j * 2^a * 4^k.  Reads only device data decided at run
+ *   time, so it can sit in a captured CUDA graph.
+ *
+ * cutqc_dd_step: reconstructs the 2^(sum a_i) bins of each of n_jobs jobs
+ * from their merged tensors (Eq. 1 at bin level: the FD contraction in FP32
+ * arithmetic, the bin total accumulated in FP64), then selects the T largest
+ * bins per job (ties to the lower bin index; T = 0 skips the selection).  Bin
+ * bit order is given by bin_bit (host, [sum a_i], subcircuit-major): the bin
+ * bit that each active row bit of each subcircuit takes; use bit j = j-th
+ * active qubit in ascending uncut-circuit order for Algorithm 1's bins.
+ *   merged_dev[i]   device, subcircuit i: n_jobs consecutive [2^a_i][4^k_i]
+ *                   tensors (the layout cutqc_dd_merge_batch writes)
+ *   bins_dev        device, n_jobs consecutive [2^(sum a_i)] float32 vectors
+ *   bin_sum_dev     device [n_jobs] float64, set to each job's bin total
+ *                   (nullable)
+ *   top_idx_dev / top_val_dev   device [n_jobs][T] int32 / float32 (-1 / 0
+ *                   where a job has fewer than T bins)
+ * All jobs share the subcircuit descriptors, active counts and bin_bit (one
+ * recursion level of one circuit).  The call enqueues a fixed sequence of
+ * launches that reads only device data, so it can be captured in a CUDA graph.
+ * Workspace: cutqc_dd_step_workspace_size bytes.  T <= 32, sum a_i <= 30.      */
+int cutqc_dd_merge(const cutqc_subcircuit* s, const float* attributed_dev, const int8_t* role,
+                   float* merged_dev, void* stream);
+int cutqc_dd_merge_batch(const cutqc_subcircuit* s, const float* attributed_dev,
+                         uint64_t active_mask, uint64_t zoom_mask, int n_jobs,
+                         const uint64_t* zoom_dev, float* merged_dev, void* stream);
+int cutqc_dd_step_workspace_size(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits,
+                                 int n_jobs, size_t* bytes);
+int cutqc_dd_step(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits,
+                  const int32_t* bin_bit, int n_jobs, const float* const* merged_dev,
+                  float* bins_dev, double* bin_sum_dev, int topk, int32_t* top_idx_dev,
+                  float* top_val_dev, void* ws_dev, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------- reductions
+ * sum_dev (device float64 scalar) += sum of x_dev[0..n) in float64.          */
+int cutqc_sum_f64(const float* x_dev, int64_t n, double* sum_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUTQC_H */

@@ -1,0 +1,245 @@
+// Pairwise contraction building blocks for Eq. 1 (Full Definition).
+//
+// A contraction step joins two tensors Ta [2^oa][4^ka], Tb [2^ob][4^kb]
+// (columns = cut digits in ascending edge id) over their shared cut edges S:
+//   T[(xa, xb)][(ea', eb')] = sum_{s in 4^|S|} Ta[xa][(ea', s)] Tb[xb][(eb', s)]
+// which is a GEMM C[m][n] = sum_s A'[m][s] B'[n][s] with m = (xa, ea'),
+// n = (xb, eb').  The result index is a bit deposit of m and n:
+//   out = pdep(m, mask_m) | pdep(n, mask_n)
+// which covers the Kronecker order of Eq. 1, the uncut circuit's qubit order,
+// and the digit interleaving of intermediate tensors alike.
+//
+// This file holds the operand gather ("prep": builds A' or B' K-major, either
+// float32 or as a float16 hi/lo pair with a power-of-two scale per row) and
+// the float32 CUDA-core GEMM.  The tensor-core GEMM is in gemm_tc.cu.
+#include "internal.cuh"
+#include "contract.cuh"
+
+namespace cutqc {
+
+// ----------------------------------------------------------------- prep
+
+// One warp per output row.  Local row r -> operand row m = r + row0;
+// m = (xp, open): xp = the high bits, open = the low 2*n_open bits.  The
+// source row x is xp with its bits moved by the row map (bit j of xp goes to
+// bit rm.bit[j] of x; identity unless rm.permute).  K index s = shared digits;
+// source column = pdep(open, open_dmask) | pdep(s, shared_dmask).
+__global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows, int64_t K, int64_t Kp,
+                            float* __restrict__ out32, __half* __restrict__ hi,
+                            __half* __restrict__ lo, float* __restrict__ scale, int64_t src_bstride,
+                            int64_t dst_bstride) {
+  // batch item blockIdx.y: source and destinations offset by their strides
+  v.src += (int64_t)blockIdx.y * src_bstride;
+  if (out32) out32 += (int64_t)blockIdx.y * dst_bstride * Kp;
+  if (hi) {
+    hi += (int64_t)blockIdx.y * dst_bstride * Kp;
+    lo += (int64_t)blockIdx.y * dst_bstride * Kp;
+    scale += (int64_t)blockIdx.y * dst_bstride;
+  }
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int64_t C = (int64_t)1 << (2 * v.k);
+  const bool contig = v.n_open == 0 && v.shared_dmask == (uint64_t)(C - 1);
+  for (int64_t r = warp; r < rows; r += nwarps) {
+    const int64_t m = r + row0;
+    const uint64_t xp = (uint64_t)m >> (2 * v.n_open);
+    uint64_t x = xp;
+    if (rm.permute) {
+      x = 0;
+      for (int j = 0; j < rm.n; ++j) x |= ((xp >> j) & 1) << rm.bit[j];
+    }
+    const uint64_t open = (uint64_t)m & (((uint64_t)1 << (2 * v.n_open)) - 1);
+    const uint64_t obase = pdep64(open, v.open_dmask);
+    const float* row = v.src + (int64_t)x * C;
+    auto col = [&](int64_t s) -> int64_t {
+      return contig ? s : (int64_t)(obase | pdep64((uint64_t)s, v.shared_dmask));
+    };
+    if (out32) {
+      for (int64_t s = lane; s < Kp; s += 32) {
+        float val = 0.f;
+        if (s < K) val = __ldg(row + col(s));
+        out32[r * Kp + s] = val;
+      }
+      continue;
+    }
+    // row max, then a power-of-two scale putting it in [2^14, 2^15)
+    float mx = 0.f;
+    for (int64_t s = lane; s < K; s += 32) mx = fmaxf(mx, fabsf(__ldg(row + col(s))));
+    for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    // (clamped to [2^-60, 2^60] so that the scale, its inverse and the
+    // epilogue's product of two scales and 2^-K stay normal floats; rows that
+    // small contribute below float32 resolution of any output)
+    int e = 0;
+    float sc = 1.f;
+    if (mx > 0.f) {
+      frexpf(mx, &e);          // mx = f * 2^e, f in [0.5, 1)
+      sc = ldexpf(1.f, max(-60, min(60, e - 15)));
+    }
+    const float inv = 1.f / sc;   // exact: power of two
+    if (lane == 0) scale[r] = sc;
+    for (int64_t s = lane; s < Kp; s += 32) {
+      float y = 0.f;
+      if (s < K) y = __ldg(row + col(s)) * inv;
+      __half h = __float2half_rn(y);
+      __half l = __float2half_rn(y - __half2float(h));
+      hi[r * Kp + s] = h;
+      lo[r * Kp + s] = l;
+    }
+  }
+}
+
+int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int64_t row0, int64_t rows,
+                     int64_t Kp, float* out32, __half* hi, __half* lo, float* scale, cudaStream_t st,
+                     int batch, int64_t src_bstride) {
+  if (rows <= 0) return CUTQC_OK;
+  RowMap rm{};
+  rm.n = n_bits;
+  rm.permute = 0;
+  if (n_bits > (int)sizeof(rm.bit)) return set_error(CUTQC_EUNSUPPORTED, "too many row bits");
+  for (int j = 0; j < n_bits; ++j) {
+    rm.bit[j] = (int8_t)row_bits[j];
+    if (row_bits[j] != j) rm.permute = 1;
+  }
+  const int64_t K = v.kdim();
+  int blocks = (int)std::min<int64_t>((rows * 32 + 255) / 256, (int64_t)sm_count() * 16);
+  if (blocks < 1) blocks = 1;
+  if (batch < 1 || batch > 65535) return set_error(CUTQC_EUNSUPPORTED, "batch %d out of range", batch);
+  prep_kernel<<<dim3(blocks, batch), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride,
+                                                   rows);
+  CUTQC_LAUNCH_CHECK("prep_kernel");
+  return CUTQC_OK;
+}
+
+// ------------------------------------------------------------ SIMT GEMM
+// C[m][n] = sum_s A[m][s] B[n][s], A: [M][lda], B: [N][ldb] (K-major).
+// CTA tile 128 x 128, BK = 16, 256 threads, 8 x 8 outputs per thread split
+// in two 4-wide column groups (tx*4 and 64 + tx*4) and two 4-high row groups.
+
+constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 16;
+
+__device__ __forceinline__ void store_out(float* out, uint64_t idx, float v, int streaming) {
+  if (streaming) __stcs(out + idx, v);
+  else out[idx] = v;
+}
+
+__global__ void __launch_bounds__(256)
+sgemm_kernel(const float* __restrict__ A, int64_t lda, const float* __restrict__ B, int64_t ldb,
+             int64_t M, int64_t N, int64_t K, float alpha, uint64_t mask_m, uint64_t mask_n,
+             int m_contig_shift, int n_contig, float* __restrict__ out, double* __restrict__ sum,
+             int streaming, int64_t a_bstride, int64_t b_bstride, int64_t out_bstride) {
+  // batch item blockIdx.z
+  A += (int64_t)blockIdx.z * a_bstride;
+  B += (int64_t)blockIdx.z * b_bstride;
+  out += (int64_t)blockIdx.z * out_bstride;
+  if (sum) sum += blockIdx.z;
+  __shared__ __align__(16) float As[2][SG_BK][SG_BM + 4];
+  __shared__ __align__(16) float Bs[2][SG_BK][SG_BN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t m0 = (int64_t)blockIdx.y * SG_BM;
+  const int64_t n0 = (int64_t)blockIdx.x * SG_BN;
+  // global load mapping: each thread loads 8 values of A and 8 of B per k-tile
+  // (rows lr and lr + 64, k columns lk*4 .. +3)
+  const int lr = tid >> 2, lk = (tid & 3) * 4;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+  float ra[8], rb[8];
+  auto gload = [&](int64_t k0) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int64_t mr = m0 + lr + 64 * h, nr = n0 + lr + 64 * h;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int64_t kk = k0 + lk + q;
+        ra[h * 4 + q] = (mr < M && kk < K) ? __ldg(A + mr * lda + kk) : 0.f;
+        rb[h * 4 + q] = (nr < N && kk < K) ? __ldg(B + nr * ldb + kk) : 0.f;
+      }
+    }
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        As[buf][lk + q][lr + 64 * h] = ra[h * 4 + q];
+        Bs[buf][lk + q][lr + 64 * h] = rb[h * 4 + q];
+      }
+  };
+  const int64_t nk = (K + SG_BK - 1) / SG_BK;
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  for (int64_t kt = 0; kt < nk; ++kt) {
+    const int buf = kt & 1;
+    if (kt + 1 < nk) gload((kt + 1) * SG_BK);
+#pragma unroll
+    for (int k = 0; k < SG_BK; ++k) {
+      float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4]);
+      float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + ty * 4]);
+      float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 4]);
+      float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][64 + tx * 4]);
+      float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (kt + 1 < nk) sstore(buf ^ 1);
+    __syncthreads();
+  }
+  // epilogue
+  double local = 0.0;
+  uint64_t coff[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    int64_t n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+    coff[j] = n_contig ? (uint64_t)n : pdep64((uint64_t)n, mask_n);
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    int64_t m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    if (m >= M) continue;
+    uint64_t roff = m_contig_shift >= 0 ? ((uint64_t)m << m_contig_shift) : pdep64((uint64_t)m, mask_m);
+    float part[8];      // pairwise float partial per row of 8, float64 across rows
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      int64_t n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+      part[j] = 0.f;
+      if (n >= N) continue;
+      float v = acc[i][j] * alpha;
+      store_out(out, roff | coff[j], v, streaming);
+      part[j] = v;
+    }
+    local += (double)(((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7])));
+  }
+  if (sum) {
+    for (int off = 16; off; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+    if ((tid & 31) == 0) atomicAdd(sum, local);
+  }
+}
+
+int launch_sgemm(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M, int64_t N,
+                 int64_t K, float alpha, uint64_t mask_m, uint64_t mask_n, float* out, double* sum,
+                 int streaming, cudaStream_t st, int batch, int64_t a_bstride, int64_t b_bstride,
+                 int64_t out_bstride) {
+  if (M <= 0 || N <= 0) return CUTQC_OK;
+  int64_t gm = (M + SG_BM - 1) / SG_BM, gn = (N + SG_BN - 1) / SG_BN;
+  if (gm > 65535) return set_error(CUTQC_EUNSUPPORTED, "too many row tiles (%lld)", (long long)gm);
+  if (gn > 0x7fffffff) return set_error(CUTQC_EUNSUPPORTED, "too many column tiles");
+  int n_contig = mask_is_low(mask_n);
+  int m_shift = mask_contig_shift(mask_m);
+  if (batch < 1 || batch > 65535) return set_error(CUTQC_EUNSUPPORTED, "batch %d out of range", batch);
+  sgemm_kernel<<<dim3((unsigned)gn, (unsigned)gm, (unsigned)batch), 256, 0, st>>>(
+      A, lda, B, ldb, M, N, K, alpha, mask_m, mask_n, m_shift, n_contig, out, sum, streaming, a_bstride, b_bstride,
+      out_bstride);
+  CUTQC_LAUNCH_CHECK("sgemm_kernel");
+  return CUTQC_OK;
+}
+
+}  // namespace cutqc

@@ -1,0 +1,107 @@
+// Declarations shared by the contraction translation units.
+#pragma once
+
+#include "internal.cuh"
+
+#include <vector>
+
+namespace cutqc {
+
+// True if mask == 2^b - 1 for some b (the low bits, in order).
+inline bool mask_is_low(uint64_t mask) { return (mask & (mask + 1)) == 0; }
+
+// If mask is one contiguous run of bits starting at bit s, return s, else -1.
+inline int mask_contig_shift(uint64_t mask) {
+  if (mask == 0) return 0;
+  int s = __builtin_ctzll(mask);
+  uint64_t run = mask >> s;
+  return ((run & (run + 1)) == 0) ? s : -1;
+}
+
+int validate_subcircuit(const cutqc_subcircuit* s);
+
+// Row-bit map of an operand gather: operand row bit j comes from source row
+// bit bit[j] (only when permute != 0).
+struct RowMap {
+  int8_t bit[40];
+  int n;
+  int permute;
+};
+
+// Operand gather of rows [row0, row0 + rows): float32 (out32 != null) or
+// float16 hi/lo with a power-of-two scale per row; K padded with zeros to Kp.
+// batch > 1: item b reads v.src + b * src_bstride and writes rows * Kp
+// elements (rows scales) further per item.
+int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int64_t row0, int64_t rows,
+                     int64_t Kp, float* out32, __half* hi, __half* lo, float* scale, cudaStream_t st,
+                     int batch = 1, int64_t src_bstride = 0);
+
+// float32 CUDA-core GEMM with bit-deposit epilogue.
+// batch > 1: item b uses A + b*a_bstride, B + b*b_bstride, out + b*out_bstride,
+// sum + b.
+int launch_sgemm(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M, int64_t N,
+                 int64_t K, float alpha, uint64_t mask_m, uint64_t mask_n, float* out, double* sum,
+                 int streaming, cudaStream_t st, int batch = 1, int64_t a_bstride = 0, int64_t b_bstride = 0,
+                 int64_t out_bstride = 0);
+
+// ------------------------------------------------------- contraction plans
+// A tensor [2^o][4^|edges|] whose row bit b lands at output position pos[b].
+struct TensorDesc {
+  int o = 0;
+  std::vector<int> edges;   // ascending
+  std::vector<int> pos;
+};
+
+struct PlanOperand {
+  int tensor = -1;
+  OperandView view{};
+  bool trivial = false;
+  std::vector<int> row_bits;
+  size_t off32 = 0, off_hi = 0, off_lo = 0, off_scale = 0;
+};
+
+struct PlanStage {
+  int a = -1, b = -1, result = -1;
+  bool final_stage = false;
+  PlanOperand opa, opb;
+  int64_t M = 0, N = 0, K = 0, Kp = 0;
+  uint64_t mask_m = 0, mask_n = 0;
+  size_t off_result = 0;
+  size_t result_elems = 0;
+};
+
+struct ContractionPlan {
+  std::vector<TensorDesc> tensors;
+  std::vector<int> stage_of;          // per tensor: producing stage or -1
+  std::vector<PlanStage> stages;
+  int K = 0;                          // number of distinct cut edges
+  int n = 0;                          // output bits
+  size_t ws_bytes = 0;                // per batch item
+  int64_t final_rows = 1, final_cols = 1;
+};
+
+// Greedy pairwise plan over the input tensors; every edge must appear in
+// exactly two inputs.
+int plan_contraction(const std::vector<TensorDesc>& inputs, int precision, ContractionPlan* plan);
+int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precision, int batch,
+                             ContractionPlan* plan);
+
+// Runs the plan for `batch` independent items: input i of item b at
+// inputs[i] + b * in_bstride[i]; output of item b at out + b * out_bstride;
+// sum + b (if sum).  Workspace: plan.ws_bytes * batch.
+int run_plan(const ContractionPlan& plan, const float* const* inputs, const int64_t* in_bstride, int batch,
+             float* out, int64_t out_bstride, double* sum, float alpha, int precision, int64_t row_begin,
+             int64_t row_end, uint8_t* ws, cudaStream_t st);
+
+// Tensor-core GEMM (tcgen05, FP16 hi/lo split, three products) with the same
+// epilogue; operands from launch_prep in half mode with Kp % 64 == 0.
+struct TcOperand {
+  const __half* hi;
+  const __half* lo;
+  const float* scale;
+  int64_t rows;
+};
+int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
+                   uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st);
+
+}  // namespace cutqc

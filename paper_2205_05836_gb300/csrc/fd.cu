@@ -1,0 +1,499 @@
+// Full-definition reconstruction (Eq. 1) over any number of subcircuits.
+//
+// Host planner: greedy pairwise contraction order (cheapest contraction
+// first, pairs that share a cut edge before pairs that do not).  Each tensor
+// carries, for each of its row bits, the position that bit takes in the final
+// output (Kronecker order: subcircuit 0's bits most significant; original
+// order: the uncut qubit index), and its open cut edges (ascending id).  A
+// step gathers its two operands K-major over the shared edges (prep) and runs
+// one GEMM whose epilogue deposits m and n bits into the result index: the
+// intermediate layout [rows][open-edge digits] for inner steps, the requested
+// output order for the last step.  The 2^-K normalisation of Eq. 1 is applied
+// exactly (power of two) by the last step.
+#include "internal.cuh"
+#include "contract.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+namespace cutqc {
+
+// ---------------------------------------------------------------- errors
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* where) {
+  return set_error(CUTQC_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+static std::mutex g_dev_mu;
+static std::map<int, int*> g_status;
+static std::map<int, int> g_sms;
+
+int* device_status_ptr() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  auto it = g_status.find(dev);
+  if (it != g_status.end()) return it->second;
+  int* p = nullptr;
+  if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+  if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+  g_status[dev] = p;
+  return p;
+}
+
+int sm_count() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  auto it = g_sms.find(dev);
+  if (it != g_sms.end()) return it->second;
+  int n = 0;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  if (n <= 0) n = 1;
+  g_sms[dev] = n;
+  return n;
+}
+
+// ---------------------------------------------------------------- planning
+
+namespace {
+
+uint64_t digit_mask(const std::vector<int>& all_edges, const std::vector<int>& subset) {
+  uint64_t m = 0;
+  for (int e : subset) {
+    auto it = std::lower_bound(all_edges.begin(), all_edges.end(), e);
+    int r = (int)(it - all_edges.begin());
+    m |= (uint64_t)3 << (2 * r);
+  }
+  return m;
+}
+
+}  // namespace
+
+int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precision, int batch,
+                             ContractionPlan* plan) {
+  if (inputs.empty()) return set_error(CUTQC_EINVAL, "no tensors");
+  if (precision != CUTQC_PREC_FP32_SIMT && precision != CUTQC_PREC_FP16X3_TC)
+    return set_error(CUTQC_EINVAL, "unknown precision %d", precision);
+  std::map<int, int> uses;
+  int n = 0;
+  for (auto& t : inputs) {
+    n += t.o;
+    for (int e : t.edges) uses[e]++;
+    if ((int)t.pos.size() != t.o) return set_error(CUTQC_EINVAL, "internal: positions");
+  }
+  for (auto& kv : uses)
+    if (kv.second != 2) return set_error(CUTQC_EINVAL, "cut edge %d must join exactly two subcircuits", kv.first);
+  plan->K = (int)uses.size();
+  plan->n = n;
+  plan->tensors = inputs;
+  plan->stage_of.assign(inputs.size(), -1);
+  plan->stages.clear();
+  size_t ws = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = ws;
+    ws = align_up(ws + bytes * (size_t)batch, 256);
+    return o;
+  };
+  std::vector<int> alive;
+  for (size_t i = 0; i < inputs.size(); ++i) alive.push_back((int)i);
+  while (alive.size() > 1) {
+    int best_a = -1, best_b = -1;
+    bool best_share = false;
+    double best_cost = 0;
+    for (size_t x = 0; x < alive.size(); ++x)
+      for (size_t y = x + 1; y < alive.size(); ++y) {
+        const TensorDesc& A = plan->tensors[alive[x]];
+        const TensorDesc& B = plan->tensors[alive[y]];
+        std::vector<int> uni, inter;
+        std::set_union(A.edges.begin(), A.edges.end(), B.edges.begin(), B.edges.end(), std::back_inserter(uni));
+        std::set_intersection(A.edges.begin(), A.edges.end(), B.edges.begin(), B.edges.end(), std::back_inserter(inter));
+        bool share = !inter.empty();
+        double cost = 2.0 * std::pow(4.0, (double)uni.size()) * std::pow(2.0, (double)(A.o + B.o));
+        bool better = best_a < 0 || (share && !best_share) || (share == best_share && cost < best_cost);
+        if (better) { best_a = alive[x]; best_b = alive[y]; best_share = share; best_cost = cost; }
+      }
+    const bool final_stage = alive.size() == 2;
+    if (final_stage) {
+      // the operand holding the most significant output bit goes to the rows
+      const TensorDesc& A = plan->tensors[best_a];
+      const TensorDesc& B = plan->tensors[best_b];
+      int ma = A.o ? *std::max_element(A.pos.begin(), A.pos.end()) : -1;
+      int mb = B.o ? *std::max_element(B.pos.begin(), B.pos.end()) : -1;
+      if (mb > ma) std::swap(best_a, best_b);
+    }
+    const TensorDesc A = plan->tensors[best_a];
+    const TensorDesc B = plan->tensors[best_b];
+    std::vector<int> shared, open_a, open_b, uni_open;
+    std::set_intersection(A.edges.begin(), A.edges.end(), B.edges.begin(), B.edges.end(), std::back_inserter(shared));
+    std::set_difference(A.edges.begin(), A.edges.end(), shared.begin(), shared.end(), std::back_inserter(open_a));
+    std::set_difference(B.edges.begin(), B.edges.end(), shared.begin(), shared.end(), std::back_inserter(open_b));
+    std::set_union(open_a.begin(), open_a.end(), open_b.begin(), open_b.end(), std::back_inserter(uni_open));
+    if (A.o + B.o + 2 * (int)uni_open.size() > 40) return set_error(CUTQC_EUNSUPPORTED, "intermediate tensor too large");
+    PlanStage st;
+    st.a = best_a;
+    st.b = best_b;
+    st.final_stage = final_stage;
+    auto make_operand = [&](const TensorDesc& T, int tidx, const std::vector<int>& open, PlanOperand* op) {
+      op->tensor = tidx;
+      OperandView& v = op->view;
+      v.src = nullptr;
+      v.o = T.o;
+      v.k = (int)T.edges.size();
+      v.open_dmask = digit_mask(T.edges, open);
+      v.shared_dmask = digit_mask(T.edges, shared);
+      v.n_open = (int)open.size();
+      v.n_shared = (int)shared.size();
+      // last step: operand row bit j = the source bit with the j-th smallest
+      // output position, so that a plain bit deposit places every bit
+      op->row_bits.resize(T.o);
+      for (int b = 0; b < T.o; ++b) op->row_bits[b] = b;
+      if (final_stage)
+        std::sort(op->row_bits.begin(), op->row_bits.end(), [&](int x, int y) { return T.pos[x] < T.pos[y]; });
+      bool ident_rows = true;
+      for (int b = 0; b < T.o; ++b) ident_rows &= op->row_bits[b] == b;
+      op->trivial = v.n_open == 0 && v.n_shared == v.k && ident_rows;
+    };
+    make_operand(A, best_a, open_a, &st.opa);
+    make_operand(B, best_b, open_b, &st.opb);
+    st.M = st.opa.view.rows();
+    st.N = st.opb.view.rows();
+    st.K = st.opa.view.kdim();
+    TensorDesc R;
+    R.o = A.o + B.o;
+    R.edges = uni_open;
+    if (final_stage) {
+      uint64_t mm = 0, mn = 0;
+      for (int b = 0; b < A.o; ++b) mm |= (uint64_t)1 << A.pos[b];
+      for (int b = 0; b < B.o; ++b) mn |= (uint64_t)1 << B.pos[b];
+      st.mask_m = mm;
+      st.mask_n = mn;
+      plan->final_rows = st.M;
+      plan->final_cols = st.N;
+      R.pos = B.pos;
+      R.pos.insert(R.pos.end(), A.pos.begin(), A.pos.end());
+    } else {
+      const int E2 = 2 * (int)uni_open.size();
+      uint64_t mm = 0, mn = 0;
+      for (int b = 0; b < A.o; ++b) mm |= (uint64_t)1 << (E2 + B.o + b);
+      for (int b = 0; b < B.o; ++b) mn |= (uint64_t)1 << (E2 + b);
+      mm |= digit_mask(uni_open, open_a);
+      mn |= digit_mask(uni_open, open_b);
+      st.mask_m = mm;
+      st.mask_n = mn;
+      R.pos = B.pos;
+      R.pos.insert(R.pos.end(), A.pos.begin(), A.pos.end());
+    }
+    if (precision == CUTQC_PREC_FP16X3_TC) {
+      st.Kp = (int64_t)align_up((size_t)st.K, 64);
+      for (PlanOperand* op : {&st.opa, &st.opb}) {
+        int64_t rows = op->view.rows();
+        op->off_hi = take((size_t)rows * st.Kp * sizeof(__half));
+        op->off_lo = take((size_t)rows * st.Kp * sizeof(__half));
+        op->off_scale = take((size_t)rows * sizeof(float) + 16);
+      }
+    } else {
+      st.Kp = st.K;
+      for (PlanOperand* op : {&st.opa, &st.opb})
+        if (!op->trivial) op->off32 = take((size_t)op->view.rows() * st.Kp * sizeof(float));
+    }
+    if (!final_stage) {
+      st.result_elems = ((size_t)1 << R.o) * ((size_t)1 << (2 * uni_open.size()));
+      st.off_result = take(st.result_elems * sizeof(float));
+    }
+    st.result = (int)plan->tensors.size();
+    plan->tensors.push_back(R);
+    plan->stage_of.push_back((int)plan->stages.size());
+    plan->stages.push_back(st);
+    alive.erase(std::remove(alive.begin(), alive.end(), best_a), alive.end());
+    alive.erase(std::remove(alive.begin(), alive.end(), best_b), alive.end());
+    alive.push_back(st.result);
+  }
+  if (inputs.size() == 1) {
+    plan->final_rows = (int64_t)1 << inputs[0].o;
+    plan->final_cols = 1;
+  }
+  plan->ws_bytes = ws;
+  return CUTQC_OK;
+}
+
+int plan_contraction(const std::vector<TensorDesc>& inputs, int precision, ContractionPlan* plan) {
+  return plan_contraction_batched(inputs, precision, 1, plan);
+}
+
+namespace {
+
+// Single-tensor case: out[pdep(x, mask)] = alpha * T[x][0].
+__global__ void single_copy(const float* __restrict__ T, int64_t rows, uint64_t mask, float alpha,
+                            float* __restrict__ out, double* __restrict__ sum, int64_t in_bstride,
+                            int64_t out_bstride) {
+  T += (int64_t)blockIdx.y * in_bstride;
+  out += (int64_t)blockIdx.y * out_bstride;
+  if (sum) sum += blockIdx.y;
+  double local = 0;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < rows; x += (int64_t)gridDim.x * blockDim.x) {
+    float v = alpha * T[x];
+    out[pdep64((uint64_t)x, mask)] = v;
+    local += v;
+  }
+  if (sum) {
+    for (int off = 16; off; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(sum, local);
+  }
+}
+
+}  // namespace
+
+int run_plan(const ContractionPlan& plan, const float* const* inputs, const int64_t* in_bstride, int batch,
+             float* out, int64_t out_bstride, double* sum, float alpha_final, int precision, int64_t row_begin,
+             int64_t row_end, uint8_t* ws, cudaStream_t st) {
+  const size_t n_in = plan.stage_of.size() - plan.stages.size();
+  if (plan.stages.empty()) {
+    const TensorDesc& T = plan.tensors[0];
+    uint64_t mask = 0;
+    for (int b = 0; b < T.o; ++b) mask |= (uint64_t)1 << T.pos[b];
+    int64_t rows = (int64_t)1 << T.o;
+    int blocks = (int)std::min<int64_t>((rows + 255) / 256, 8192);
+    single_copy<<<dim3(blocks, batch), 256, 0, st>>>(inputs[0], rows, mask, alpha_final, out, sum, in_bstride[0],
+                                                     out_bstride);
+    CUTQC_LAUNCH_CHECK("single_copy");
+    return CUTQC_OK;
+  }
+  if (row_end < 0) row_end = plan.final_rows;
+  const bool partial = row_begin != 0 || row_end != plan.final_rows;
+  auto src_of = [&](int t, int64_t* bstride) -> const float* {
+    if (t < (int)n_in) {
+      *bstride = in_bstride[t];
+      return inputs[t];
+    }
+    const PlanStage& s = plan.stages[plan.stage_of[t]];
+    *bstride = (int64_t)s.result_elems;
+    return (const float*)(ws + s.off_result);
+  };
+  int rc;
+  for (const PlanStage& stg0 : plan.stages) {
+    PlanStage stg = stg0;
+    int64_t sa_b = 0, sb_b = 0;
+    stg.opa.view.src = src_of(stg.a, &sa_b);
+    stg.opb.view.src = src_of(stg.b, &sb_b);
+    int64_t r0 = 0, M = stg.M;
+    if (stg.final_stage && partial) {
+      r0 = row_begin;
+      M = row_end - row_begin;
+    }
+    float* dst = stg.final_stage ? out : (float*)(ws + stg.off_result);
+    const int64_t dst_b = stg.final_stage ? out_bstride : (int64_t)stg.result_elems;
+    const float alpha = stg.final_stage ? alpha_final : 1.0f;
+    double* sum_ptr = stg.final_stage ? sum : nullptr;
+    const int streaming = stg.final_stage ? 1 : 0;
+    if (precision == CUTQC_PREC_FP16X3_TC) {
+      for (int b = 0; b < batch; ++b) {
+        OperandView va = stg.opa.view, vb = stg.opb.view;
+        va.src += b * sa_b;
+        vb.src += b * sb_b;
+        __half* ah = (__half*)(ws + stg.opa.off_hi) + (size_t)b * M * stg.Kp;
+        __half* al = (__half*)(ws + stg.opa.off_lo) + (size_t)b * M * stg.Kp;
+        float* as = (float*)(ws + stg.opa.off_scale) + (size_t)b * M;
+        __half* bh = (__half*)(ws + stg.opb.off_hi) + (size_t)b * stg.N * stg.Kp;
+        __half* bl = (__half*)(ws + stg.opb.off_lo) + (size_t)b * stg.N * stg.Kp;
+        float* bs = (float*)(ws + stg.opb.off_scale) + (size_t)b * stg.N;
+        rc = launch_prep_rows(va, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, stg.Kp, nullptr, ah,
+                              al, as, st);
+        if (rc) return rc;
+        rc = launch_prep_rows(vb, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp, nullptr,
+                              bh, bl, bs, st);
+        if (rc) return rc;
+        TcOperand ta{ah, al, as, M}, tb{bh, bl, bs, stg.N};
+        rc = launch_tc_gemm(ta, tb, stg.Kp, alpha, stg.mask_m, stg.mask_n, dst + b * dst_b,
+                            sum_ptr ? sum_ptr + b : nullptr, streaming, st);
+        if (rc) return rc;
+      }
+      continue;
+    }
+    const float* A;
+    const float* B;
+    int64_t lda, ldb, a_b, b_b;
+    if (stg.opa.trivial) {
+      A = stg.opa.view.src + r0 * stg.K;
+      lda = stg.K;
+      a_b = sa_b;
+    } else {
+      float* a32 = (float*)(ws + stg.opa.off32);
+      rc = launch_prep_rows(stg.opa.view, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, stg.Kp, a32,
+                            nullptr, nullptr, nullptr, st, batch, sa_b);
+      if (rc) return rc;
+      A = a32;
+      lda = stg.Kp;
+      a_b = M * stg.Kp;
+    }
+    if (stg.opb.trivial) {
+      B = stg.opb.view.src;
+      ldb = stg.K;
+      b_b = sb_b;
+    } else {
+      float* b32 = (float*)(ws + stg.opb.off32);
+      rc = launch_prep_rows(stg.opb.view, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp,
+                            b32, nullptr, nullptr, nullptr, st, batch, sb_b);
+      if (rc) return rc;
+      B = b32;
+      ldb = stg.Kp;
+      b_b = stg.N * stg.Kp;
+    }
+    rc = launch_sgemm(A, lda, B, ldb, M, stg.N, stg.K, alpha, stg.mask_m, stg.mask_n, dst, sum_ptr, streaming, st,
+                      batch, a_b, b_b, dst_b);
+    if (rc) return rc;
+  }
+  return CUTQC_OK;
+}
+
+namespace {
+
+int fd_inputs(int n_sub, const cutqc_subcircuit* s, int out_order, std::vector<TensorDesc>* out) {
+  if (n_sub < 1 || !s) return set_error(CUTQC_EINVAL, "n_sub must be >= 1");
+  if (out_order != CUTQC_ORDER_KRON && out_order != CUTQC_ORDER_ORIGINAL)
+    return set_error(CUTQC_EINVAL, "out_order must be KRON or ORIGINAL");
+  int n = 0;
+  std::map<int, std::pair<int, int>> edge_use;   // edge -> (#init sides, #meas sides)
+  for (int i = 0; i < n_sub; ++i) {
+    int rc = validate_subcircuit(&s[i]);
+    if (rc) return rc;
+    const int o = s[i].w - s[i].k_out;
+    if (o > 0 && !s[i].out_qubit) return set_error(CUTQC_EINVAL, "missing out_qubit");
+    n += o;
+    for (int j = 0; j < s[i].k_in; ++j) edge_use[s[i].in_edge[j]].first++;
+    for (int j = 0; j < s[i].k_out; ++j) edge_use[s[i].out_edge[j]].second++;
+  }
+  if (n > CUTQC_MAX_QUBITS) return set_error(CUTQC_EUNSUPPORTED, "%d output qubits > %d", n, CUTQC_MAX_QUBITS);
+  for (auto& kv : edge_use)
+    if (kv.second.first != 1 || kv.second.second != 1)
+      return set_error(CUTQC_EINVAL, "cut edge %d must be measured once and initialised once", kv.first);
+  if ((int)edge_use.size() > CUTQC_MAX_CUTS)
+    return set_error(CUTQC_EUNSUPPORTED, "%d cuts > %d", (int)edge_use.size(), CUTQC_MAX_CUTS);
+  if (out_order == CUTQC_ORDER_ORIGINAL) {
+    std::vector<int> seen(n, 0);
+    for (int i = 0; i < n_sub; ++i)
+      for (int t = 0; t < s[i].w - s[i].k_out; ++t) {
+        int x = s[i].out_qubit[t];
+        if (x < 0 || x >= n || seen[x]) return set_error(CUTQC_EINVAL, "out_qubit must be a permutation of 0..n-1");
+        seen[x] = 1;
+      }
+  }
+  out->clear();
+  int offset = n;
+  for (int i = 0; i < n_sub; ++i) {
+    TensorDesc t;
+    t.o = s[i].w - s[i].k_out;
+    for (int j = 0; j < s[i].k_in; ++j) t.edges.push_back(s[i].in_edge[j]);
+    for (int j = 0; j < s[i].k_out; ++j) t.edges.push_back(s[i].out_edge[j]);
+    std::sort(t.edges.begin(), t.edges.end());
+    offset -= t.o;
+    for (int b = 0; b < t.o; ++b) t.pos.push_back(out_order == CUTQC_ORDER_KRON ? offset + b : s[i].out_qubit[b]);
+    out->push_back(t);
+  }
+  return CUTQC_OK;
+}
+
+}  // namespace
+
+}  // namespace cutqc
+
+using namespace cutqc;
+
+extern "C" const char* cutqc_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* cutqc_version(void) { return "cutqc-gb300 0.1 (sm_103a)"; }
+
+extern "C" int cutqc_device_status(int32_t* status_out) {
+  if (!status_out) return set_error(CUTQC_EINVAL, "null status_out");
+  int* p = device_status_ptr();
+  if (!p) return set_error(CUTQC_ECUDA, "no device status word");
+  CUTQC_CUDA_TRY(cudaDeviceSynchronize());
+  int v = 0;
+  CUTQC_CUDA_TRY(cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost));
+  CUTQC_CUDA_TRY(cudaMemset(p, 0, sizeof(int)));
+  *status_out = v;
+  return CUTQC_OK;
+}
+
+extern "C" int cutqc_fd_shape(int n_sub, const cutqc_subcircuit* s, int64_t* rows, int64_t* cols) {
+  std::vector<TensorDesc> in;
+  int rc = fd_inputs(n_sub, s, CUTQC_ORDER_KRON, &in);
+  if (rc) return rc;
+  ContractionPlan plan;
+  if ((rc = plan_contraction(in, CUTQC_PREC_FP32_SIMT, &plan))) return rc;
+  if (rows) *rows = plan.final_rows;
+  if (cols) *cols = plan.final_cols;
+  return CUTQC_OK;
+}
+
+extern "C" int cutqc_reconstruct_fd_workspace_size(int n_sub, const cutqc_subcircuit* s, int precision,
+                                                   size_t* bytes) {
+  if (!bytes) return set_error(CUTQC_EINVAL, "null bytes");
+  size_t best = 0;
+  bool any = false;
+  for (int order : {CUTQC_ORDER_KRON, CUTQC_ORDER_ORIGINAL}) {
+    std::vector<TensorDesc> in;
+    ContractionPlan plan;
+    int rc = fd_inputs(n_sub, s, order, &in);
+    if (!rc) rc = plan_contraction(in, precision, &plan);
+    if (rc) {
+      if (order == CUTQC_ORDER_KRON) return rc;
+      continue;
+    }
+    best = std::max(best, plan.ws_bytes);
+    any = true;
+  }
+  if (!any) return set_error(CUTQC_EINVAL, "no valid plan");
+  *bytes = best;
+  return CUTQC_OK;
+}
+
+extern "C" int cutqc_reconstruct_fd(int n_sub, const cutqc_subcircuit* s, const float* const* attributed,
+                                    int out_order, int precision, int64_t row_begin, int64_t row_end,
+                                    float* out, double* sum, void* ws_dev, size_t ws_bytes, void* stream) {
+  std::vector<TensorDesc> in;
+  int rc = fd_inputs(n_sub, s, out_order, &in);
+  if (rc) return rc;
+  ContractionPlan plan;
+  if ((rc = plan_contraction(in, precision, &plan))) return rc;
+  if (!attributed || !out) return set_error(CUTQC_EINVAL, "null pointer");
+  for (int i = 0; i < n_sub; ++i)
+    if (!attributed[i]) return set_error(CUTQC_EINVAL, "null attributed tensor %d", i);
+  if (ws_bytes < plan.ws_bytes || (plan.ws_bytes && !ws_dev))
+    return set_error(CUTQC_ENOMEM, "FD workspace needs %zu bytes", plan.ws_bytes);
+  if (row_end < 0) row_end = plan.final_rows;
+  if (row_begin < 0 || row_begin > row_end || row_end > plan.final_rows)
+    return set_error(CUTQC_EINVAL, "row range [%lld, %lld) outside [0, %lld)", (long long)row_begin,
+                     (long long)row_end, (long long)plan.final_rows);
+  const bool partial = row_begin != 0 || row_end != plan.final_rows;
+  if (partial) {
+    if (out_order != CUTQC_ORDER_KRON) return set_error(CUTQC_EINVAL, "a partial row range needs CUTQC_ORDER_KRON");
+    if (plan.stages.empty()) return set_error(CUTQC_EINVAL, "no row split for a single subcircuit");
+    const PlanStage& f = plan.stages.back();
+    const int shift = mask_contig_shift(f.mask_m);
+    if (shift < 0 || shift + __builtin_popcountll(f.mask_m) != plan.n)
+      return set_error(CUTQC_EUNSUPPORTED, "row split needs the row operand to hold the top output bits");
+  }
+  std::vector<int64_t> bstride(n_sub, 0);
+  return run_plan(plan, attributed, bstride.data(), 1, out, 0, sum, std::ldexp(1.0f, -plan.K), precision, row_begin,
+                  row_end, (uint8_t*)ws_dev, (cudaStream_t)stream);
+}

@@ -1,0 +1,475 @@
+// Tensor-core contraction for Eq. 1 on sm_103a (tcgen05 + TMA + TMEM).
+//
+// C[m][n] = alpha * sa[m] * sb[n] * sum_s (Ah Bh + Ah Bl + Al Bh)[m][n][s]
+// where A = sa * (Ah + Al), B = sb * (Bh + Bl) are the float16 hi/lo splits of
+// the float32 operands (per-row power-of-two scales, see prep_kernel): about
+// 22 significant bits per operand, products exact in the FP32 accumulator.
+// The signed I/X/Y/Z terms of Eq. 1 cancel (sum|terms| is ~10x |P| on the
+// 30-qubit supremacy workload), which is why a single FP16/BF16/TF32 pass is
+// not accurate enough and the split is used.
+//
+// The tensor core rounds its FP32 accumulator toward zero after each MMA,
+// which over a long chain of signed terms leaves a negative bias (about
+// -1.5e-6 in sum p on the 30-qubit workload).  Each 64-wide k-block is
+// therefore accumulated in a fresh TMEM accumulator (a "chunk", 12 MMAs), and
+// the chunks are added in registers with round-to-nearest.
+//
+// Kernel organisation (one CTA per SM, persistent over output tiles):
+//   warp 8       TMA producer: per k-block loads A_hi, A_lo (128 x 64) and
+//                B_hi, B_lo (256 x 64) into a 2-stage 128B-swizzled ring
+//   warp 9       MMA issuer: 3 x 4 tcgen05.mma (M=128, N=256, K=16) per
+//                k-block into one of two 128 x 256 FP32 chunk buffers in TMEM
+//   warps 0-7    epilogue: warp w owns TMEM lanes 32*(w%4).. (tile rows) and
+//                columns 128*(w/4)..+127; adds every chunk into 128 register
+//                totals, then scales and stores the tile to
+//                out[pdep(m, mask_m) | pdep(n, mask_n)] (streaming stores for
+//                the final output), optional FP64 running sum
+// Tiles are walked with m fastest so the few B tiles in flight stay in L2.
+// Every barrier wait is bounded in time; on expiry the CTA records
+// CUTQC_ETIMEOUT in the device status word, drains its own copies and MMAs,
+// frees its tensor memory and returns.
+#include "internal.cuh"
+#include "contract.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <mutex>
+#include <set>
+
+namespace cutqc {
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64;               // BK in fp16 elements (128 B)
+constexpr int STAGES = 2;
+constexpr int A_TILE = BM * BK * 2;                      // 16 KiB
+constexpr int B_TILE = BN * BK * 2;                      // 32 KiB
+constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;     // 96 KiB
+constexpr int TMEM_COLS = 512;                           // 2 accumulators x 256 columns
+constexpr int NUM_THREADS = 320;
+constexpr int EPI_THREADS = 256;
+constexpr long long kTimeoutCycles = 4000000000LL;       // ~2 s at 2 GHz
+
+struct TcMaps {
+  CUtensorMap a_hi, a_lo, b_hi, b_lo;
+};
+
+struct TcArgs {
+  const float* sa;
+  const float* sb;
+  int64_t M, N;
+  int num_kb;
+  int num_m_blk;
+  int64_t num_tiles;
+  float alpha;
+  uint64_t mask_m, mask_n;
+  int n_contig;
+  int m_shift;
+  float* out;
+  double* sum;
+  int streaming;
+  int* status;
+};
+
+struct SmemTail {
+  uint64_t full[STAGES];
+  uint64_t empty[STAGES];
+  uint64_t cfull[2];
+  uint64_t cempty[2];
+  uint64_t fin;
+  uint64_t tbl[32];
+  uint32_t tmem_slot;
+  int abort_flag;
+};
+
+constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + sizeof(SmemTail);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait.  Returns false if the time limit passed or (when given) the
+// CTA's abort flag was raised by another role.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (abort_flag && *abort_flag) return false;
+    if (clock64() - t0 > kTimeoutCycles) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 B, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: kind::f16, A = B = F16, D = F32, both K-major,
+// N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void st_v4(float* p, float4 v, int streaming) {
+  if (streaming) __stcs(reinterpret_cast<float4*>(p), v);
+  else *reinterpret_cast<float4*>(p) = v;
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  SmemTail* tail = reinterpret_cast<SmemTail*>(smem + STAGES * STAGE_BYTES);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&tail->full[s]), 1);
+      mbar_init(smem_u32(&tail->empty[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&tail->cfull[a]), 1);
+      mbar_init(smem_u32(&tail->cempty[a]), EPI_THREADS);
+    }
+    mbar_init(smem_u32(&tail->fin), 1);
+    tail->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tail->tbl[lane] = pdep64((uint64_t)lane, args.mask_n);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tail->tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tail->tmem_slot;
+  volatile int* abort_flag = &tail->abort_flag;
+
+  auto fail = [&]() {
+    *abort_flag = 1;
+    record_status(args.status, CUTQC_ETIMEOUT);
+  };
+
+  if (warp == 8) {
+    if (lane == 0) {
+      bool issued[STAGES] = {false, false};
+      uint32_t issued_par[STAGES] = {0, 0};
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int64_t tile = blockIdx.x; tile < args.num_tiles && !*abort_flag; tile += gridDim.x) {
+        const int mb = (int)(tile % args.num_m_blk);
+        const int nb = (int)(tile / args.num_m_blk);
+        bool ok = true;
+        for (int kb = 0; kb < args.num_kb; ++kb) {
+          if (!mbar_wait(smem_u32(&tail->empty[stage]), phase ^ 1u, abort_flag)) { fail(); ok = false; break; }
+          uint8_t* st = smem + stage * STAGE_BYTES;
+          const uint32_t bar = smem_u32(&tail->full[stage]);
+          mbar_expect_tx(bar, STAGE_BYTES);
+          tma_load_2d(smem_u32(st), &maps.a_hi, kb * BK, mb * BM, bar);
+          tma_load_2d(smem_u32(st + A_TILE), &maps.a_lo, kb * BK, mb * BM, bar);
+          tma_load_2d(smem_u32(st + 2 * A_TILE), &maps.b_hi, kb * BK, nb * BN, bar);
+          tma_load_2d(smem_u32(st + 2 * A_TILE + B_TILE), &maps.b_lo, kb * BK, nb * BN, bar);
+          issued[stage] = true;
+          issued_par[stage] = phase;
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+      }
+      // every copy this thread started has landed before the CTA may exit
+      for (int s = 0; s < STAGES; ++s)
+        if (issued[s] && !mbar_wait(smem_u32(&tail->full[s]), issued_par[s], nullptr)) record_status(args.status, CUTQC_ETIMEOUT);
+    }
+  } else if (warp == 9) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int buf = 0;
+      uint32_t buf_phase = 0;
+      bool any = false;
+      for (int64_t tile = blockIdx.x; tile < args.num_tiles && !*abort_flag; tile += gridDim.x) {
+        bool ok = true;
+        for (int kb = 0; kb < args.num_kb; ++kb) {
+          // one chunk per k-block: fresh accumulator in chunk buffer `buf`
+          if (!mbar_wait(smem_u32(&tail->cempty[buf]), buf_phase ^ 1u, abort_flag)) { fail(); ok = false; break; }
+          tc_fence_after();
+          if (!mbar_wait(smem_u32(&tail->full[stage]), phase, abort_flag)) { fail(); ok = false; break; }
+          tc_fence_after();
+          const uint32_t d = tmem_base + (uint32_t)(buf * BN);
+          const uint32_t st = smem_u32(smem + stage * STAGE_BYTES);
+          const uint32_t ah = st, al = st + A_TILE, bh = st + 2 * A_TILE, bl = st + 2 * A_TILE + B_TILE;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint32_t off = kk * 32;   // 16 fp16 = 32 bytes along K inside the swizzle row
+            const uint64_t dah = sw128_desc(ah + off), dal = sw128_desc(al + off);
+            const uint64_t dbh = sw128_desc(bh + off), dbl = sw128_desc(bl + off);
+            umma_f16(d, dah, dbh, kk != 0 ? 1u : 0u);
+            umma_f16(d, dah, dbl, 1u);
+            umma_f16(d, dal, dbh, 1u);
+          }
+          any = true;
+          umma_commit(smem_u32(&tail->empty[stage]));
+          umma_commit(smem_u32(&tail->cfull[buf]));
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+          if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
+        }
+        if (!ok) break;
+      }
+      // all MMAs issued by this thread complete before tensor memory is freed
+      if (any) {
+        umma_commit(smem_u32(&tail->fin));
+        if (!mbar_wait(smem_u32(&tail->fin), 0, nullptr)) record_status(args.status, CUTQC_ETIMEOUT);
+      }
+    }
+  } else {
+    // epilogue warps 0..7: TMEM lanes 32*(warp%4).. = tile rows, columns
+    // 128*(warp/4) .. +127
+    const int g = warp & 3, h = warp >> 2;
+    int buf = 0;
+    uint32_t buf_phase = 0;
+    double local = 0.0;
+    const int row = g * 32 + lane;
+    float tot[128];
+    for (int64_t tile = blockIdx.x; tile < args.num_tiles && !*abort_flag; tile += gridDim.x) {
+      const int mb = (int)(tile % args.num_m_blk);
+      const int nb = (int)(tile / args.num_m_blk);
+#pragma unroll
+      for (int i = 0; i < 128; ++i) tot[i] = 0.f;
+      bool ok = true;
+      for (int kb = 0; kb < args.num_kb; ++kb) {
+        if (!mbar_wait(smem_u32(&tail->cfull[buf]), buf_phase, abort_flag)) { fail(); ok = false; break; }
+        tc_fence_after();
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          uint32_t r[32];
+          tmem_ld32(tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(buf * BN + h * 128 + q * 32), r);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) tot[q * 32 + i] += __uint_as_float(r[i]);
+        }
+        tc_fence_before();
+        mbar_arrive(smem_u32(&tail->cempty[buf]));
+        if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
+      }
+      if (!ok) break;
+      const int64_t m = (int64_t)mb * BM + row;
+      if (m >= args.M) continue;
+      const float rs = args.alpha * __ldg(args.sa + m);
+      const uint64_t roff = args.m_shift >= 0 ? ((uint64_t)m << args.m_shift) : pdep64((uint64_t)m, args.mask_m);
+      const int64_t nbase = (int64_t)nb * BN + h * 128;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t n0 = nbase + q * 32;
+        if (n0 >= args.N) break;
+        const uint64_t coff = args.n_contig ? (uint64_t)n0 : pdep64((uint64_t)n0, args.mask_n);
+        float* v = tot + q * 32;
+        if (n0 + 32 <= args.N) {
+          const float4* sb4 = reinterpret_cast<const float4*>(args.sb + n0);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            float4 s4 = __ldg(sb4 + c);
+            v[4 * c + 0] *= rs * s4.x;
+            v[4 * c + 1] *= rs * s4.y;
+            v[4 * c + 2] *= rs * s4.z;
+            v[4 * c + 3] *= rs * s4.w;
+          }
+          if (args.n_contig) {
+            float* p = args.out + (roff | coff);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              st_v4(p + 4 * c, make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]), args.streaming);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              float* p = args.out + (roff | coff | tail->tbl[i]);
+              if (args.streaming) __stcs(p, v[i]); else *p = v[i];
+            }
+          }
+          if (args.sum) {
+            // pairwise float partial of the 32 outputs, float64 across chunks
+            float t[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) t[i] = v[i] + v[i + 16];
+#pragma unroll
+            for (int w2 = 8; w2; w2 >>= 1)
+#pragma unroll
+              for (int i = 0; i < w2; ++i) t[i] += t[i + w2];
+            local += (double)t[0];
+          }
+        } else {
+          float part = 0.f;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            if (n0 + i < args.N) {
+              float val = v[i] * rs * __ldg(args.sb + n0 + i);
+              float* p = args.out + (roff | coff | tail->tbl[i]);
+              if (args.streaming) __stcs(p, val); else *p = val;
+              part += val;
+            }
+          }
+          local += (double)part;
+        }
+      }
+    }
+    if (args.sum) {
+      for (int off = 16; off; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+      if (lane == 0) atomicAdd(args.sum, local);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+int make_map(CUtensorMap* map, const __half* base, int64_t rows, int64_t Kp, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return set_error(CUTQC_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  if (((uintptr_t)base & 15) != 0) return set_error(CUTQC_EINVAL, "operand not 16-byte aligned");
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * sizeof(__half)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(CUTQC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return CUTQC_OK;
+}
+
+}  // namespace
+
+int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
+                   uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st) {
+  if (a.rows <= 0 || b.rows <= 0) return CUTQC_OK;
+  if (Kp % BK != 0 || Kp <= 0) return set_error(CUTQC_EINVAL, "tensor-core K must be a multiple of %d", BK);
+  if (Kp / BK > (1 << 20)) return set_error(CUTQC_EUNSUPPORTED, "K too large");
+  TcMaps maps;
+  int rc;
+  if ((rc = make_map(&maps.a_hi, a.hi, a.rows, Kp, BM))) return rc;
+  if ((rc = make_map(&maps.a_lo, a.lo, a.rows, Kp, BM))) return rc;
+  if ((rc = make_map(&maps.b_hi, b.hi, b.rows, Kp, BN))) return rc;
+  if ((rc = make_map(&maps.b_lo, b.lo, b.rows, Kp, BN))) return rc;
+  TcArgs args{};
+  args.sa = a.scale;
+  args.sb = b.scale;
+  args.M = a.rows;
+  args.N = b.rows;
+  args.num_kb = (int)(Kp / BK);
+  const int64_t mblk = (a.rows + BM - 1) / BM, nblk = (b.rows + BN - 1) / BN;
+  if (mblk > 0x7fffffff || nblk > 0x7fffffff) return set_error(CUTQC_EUNSUPPORTED, "too many tiles");
+  args.num_m_blk = (int)mblk;
+  args.num_tiles = mblk * nblk;
+  args.alpha = alpha;
+  args.mask_m = mask_m;
+  args.mask_n = mask_n;
+  args.n_contig = mask_is_low(mask_n) ? 1 : 0;
+  args.m_shift = mask_contig_shift(mask_m);
+  args.out = out;
+  args.sum = sum;
+  args.streaming = streaming;
+  args.status = device_status_ptr();
+  if (((uintptr_t)b.scale & 15) != 0) return set_error(CUTQC_EINVAL, "column scales not 16-byte aligned");
+  if (args.n_contig && ((uintptr_t)out & 15) != 0) return set_error(CUTQC_EINVAL, "output not 16-byte aligned");
+  {
+    static std::mutex mu;
+    static std::set<int> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done.count(dev)) {
+      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+      done.insert(dev);
+    }
+  }
+  const int grid = (int)std::min<int64_t>(args.num_tiles, (int64_t)sm_count());
+  tc_gemm_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
+  CUTQC_LAUNCH_CHECK("tc_gemm_kernel");
+  return CUTQC_OK;
+}
+
+}  // namespace cutqc

@@ -1,0 +1,239 @@
+"""Python binding of libcutqc (include/cutqc.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and forwards
+to it through ctypes; torch tensors are used only to own device memory and to
+name the CUDA stream.  There is no fallback: if the shared library is missing
+the import of a compute function raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_int8, c_int32, c_int64, c_size_t, c_uint64, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libcutqc.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "cutqc.h")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+F64, F32 = 0, 1
+ORDER_KRON, ORDER_ORIGINAL = 0, 1
+PREC_FP32_SIMT, PREC_FP16X3_TC = 0, 1
+
+
+class CutqcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"cutqc error {code}: {msg}")
+        self.code = code
+
+
+class _Sub(ctypes.Structure):
+    _fields_ = [("w", c_int32), ("k_in", c_int32), ("k_out", c_int32),
+                ("in_local", POINTER(c_int32)), ("out_local", POINTER(c_int32)),
+                ("in_edge", POINTER(c_int32)), ("out_edge", POINTER(c_int32)),
+                ("out_qubit", POINTER(c_int32))]
+
+
+_lib = None
+
+
+def lib():
+    """Load libcutqc.so (built by paper_2205_05836_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libcutqc.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.cutqc_last_error.restype = c_char_p
+        L.cutqc_version.restype = c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise CutqcError(rc, lib().cutqc_last_error().decode())
+
+
+def _arr(xs):
+    xs = [int(x) for x in xs]
+    a = (c_int32 * max(1, len(xs)))(*xs)
+    return a
+
+
+def make_sub(s):
+    """ctypes descriptor from any object with w, in_local, out_local,
+    in_edge, out_edge, out_qubit (e.g. workloads.cutting.Subcircuit).  The
+    returned tuple keeps the arrays alive."""
+    arrays = [_arr(s.in_local), _arr(s.out_local), _arr(s.in_edge), _arr(s.out_edge), _arr(s.out_qubit)]
+    d = _Sub(int(s.w), len(s.in_local), len(s.out_local),
+             ctypes.cast(arrays[0], POINTER(c_int32)), ctypes.cast(arrays[1], POINTER(c_int32)),
+             ctypes.cast(arrays[2], POINTER(c_int32)), ctypes.cast(arrays[3], POINTER(c_int32)),
+             ctypes.cast(arrays[4], POINTER(c_int32)))
+    return d, arrays
+
+
+def _subs(subs):
+    keep, arr = [], (_Sub * len(subs))()
+    for i, s in enumerate(subs):
+        d, a = make_sub(s)
+        arr[i] = d
+        keep.append(a)
+    return arr, keep
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return c_void_p(0 if t is None else t.data_ptr())
+
+
+# ------------------------------------------------------------------ misc
+
+def cutqc_version():
+    return lib().cutqc_version().decode()
+
+
+def cutqc_last_error():
+    return lib().cutqc_last_error().decode()
+
+
+def cutqc_device_status():
+    v = c_int32(0)
+    _check(lib().cutqc_device_status(ctypes.byref(v)))
+    return v.value
+
+
+def cutqc_sum_f64(x, out=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.zeros(1, dtype=torch.float64, device=x.device)
+    _check(lib().cutqc_sum_f64(_ptr(x), c_int64(x.numel()), _ptr(out), _stream(stream)))
+    return out
+
+
+# ------------------------------------------------------------ attribution
+
+def cutqc_attribute_workspace_size(sub):
+    d, keep = make_sub(sub)
+    n = c_size_t(0)
+    _check(lib().cutqc_attribute_workspace_size(ctypes.byref(d), ctypes.byref(n)))
+    return n.value
+
+
+def cutqc_attribute(sub, variants, out=None, ws=None, stream=None):
+    """variants: device tensor [4^k_in, 3^k_out, 2^w] (float64 or float32).
+    Returns the attributed tensor [2^o, 4^k] float32."""
+    import torch
+    d, keep = make_sub(sub)
+    kin, kout = len(sub.in_local), len(sub.out_local)
+    o = int(sub.w) - kout
+    if out is None:
+        out = torch.empty((1 << o, 4 ** (kin + kout)), dtype=torch.float32, device=variants.device)
+    need = cutqc_attribute_workspace_size(sub)
+    if ws is None and need:
+        ws = torch.empty(need, dtype=torch.uint8, device=variants.device)
+    dtype = F64 if variants.dtype == torch.float64 else F32
+    _check(lib().cutqc_attribute(ctypes.byref(d), _ptr(variants), c_int(dtype), _ptr(out), _ptr(ws),
+                                 c_size_t(0 if ws is None else ws.numel()), _stream(stream)))
+    return out
+
+
+# --------------------------------------------------------------------- FD
+
+def cutqc_fd_shape(subs):
+    arr, keep = _subs(subs)
+    r, c = c_int64(0), c_int64(0)
+    _check(lib().cutqc_fd_shape(c_int(len(subs)), arr, ctypes.byref(r), ctypes.byref(c)))
+    return r.value, c.value
+
+
+def cutqc_reconstruct_fd_workspace_size(subs, precision):
+    arr, keep = _subs(subs)
+    n = c_size_t(0)
+    _check(lib().cutqc_reconstruct_fd_workspace_size(c_int(len(subs)), arr, c_int(precision), ctypes.byref(n)))
+    return n.value
+
+
+def cutqc_reconstruct_fd(subs, attributed, out_order=ORDER_KRON, precision=PREC_FP16X3_TC, row_begin=0,
+                         row_end=-1, out=None, sum_out=None, ws=None, stream=None):
+    """Eq. 1 over the subcircuits.  Returns (out, sum_out)."""
+    import torch
+    arr, keep = _subs(subs)
+    dev = attributed[0].device
+    n = sum(int(s.w) - len(s.out_local) for s in subs)
+    if out is None:
+        if row_begin == 0 and row_end == -1:
+            numel = 1 << n
+        else:
+            rows, cols = cutqc_fd_shape(subs)
+            numel = ((rows if row_end < 0 else row_end) - row_begin) * cols
+        out = torch.empty(numel, dtype=torch.float32, device=dev)
+    need = cutqc_reconstruct_fd_workspace_size(subs, precision)
+    if ws is None and need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    ptrs = (c_void_p * len(attributed))(*[t.data_ptr() for t in attributed])
+    _check(lib().cutqc_reconstruct_fd(c_int(len(subs)), arr, ptrs, c_int(out_order), c_int(precision),
+                                      c_int64(row_begin), c_int64(row_end), _ptr(out), _ptr(sum_out), _ptr(ws),
+                                      c_size_t(0 if ws is None else ws.numel()), _stream(stream)))
+    return out, sum_out
+
+
+# --------------------------------------------------------------------- DD
+
+def cutqc_dd_merge(sub, attributed, role, out=None, stream=None):
+    """role: per output qubit 0 active, 1 merged, 2 zoom->0, 3 zoom->1."""
+    import torch
+    d, keep = make_sub(sub)
+    a = sum(1 for r in role if r == 0)
+    k = len(sub.in_local) + len(sub.out_local)
+    if out is None:
+        out = torch.empty((1 << a, 4 ** k), dtype=torch.float32, device=attributed.device)
+    roles = (c_int8 * max(1, len(role)))(*[int(r) for r in role])
+    _check(lib().cutqc_dd_merge(ctypes.byref(d), _ptr(attributed), roles, _ptr(out), _stream(stream)))
+    return out
+
+
+def cutqc_dd_merge_batch(sub, attributed, active_mask, zoom_mask, zoom_dev, out, stream=None):
+    d, keep = make_sub(sub)
+    _check(lib().cutqc_dd_merge_batch(ctypes.byref(d), _ptr(attributed), c_uint64(active_mask), c_uint64(zoom_mask),
+                                      c_int(zoom_dev.numel()), _ptr(zoom_dev), _ptr(out), _stream(stream)))
+    return out
+
+
+def cutqc_dd_step_workspace_size(subs, active_bits, n_jobs):
+    arr, keep = _subs(subs)
+    ab = _arr(active_bits)
+    n = c_size_t(0)
+    _check(lib().cutqc_dd_step_workspace_size(c_int(len(subs)), arr, ab, c_int(n_jobs), ctypes.byref(n)))
+    return n.value
+
+
+def cutqc_dd_step(subs, active_bits, bin_bit, merged, bins, bin_sum=None, topk=0, top_idx=None, top_val=None,
+                  ws=None, stream=None):
+    """merged: per subcircuit a device tensor holding the jobs' merged tensors
+    back to back ([n_jobs, 2^a_i, 4^k_i]); bins: device tensor [n_jobs, 2^sum(a)]."""
+    import torch
+    arr, keep = _subs(subs)
+    n_jobs = bins.shape[0]
+    ab, bb = _arr(active_bits), _arr(bin_bit)
+    mp = (c_void_p * len(merged))(*[t.data_ptr() for t in merged])
+    need = cutqc_dd_step_workspace_size(subs, active_bits, n_jobs)
+    if ws is None and need:
+        ws = torch.empty(need, dtype=torch.uint8, device=bins.device)
+    _check(lib().cutqc_dd_step(c_int(len(subs)), arr, ab, bb, c_int(n_jobs), mp, _ptr(bins), _ptr(bin_sum),
+                               c_int(topk), _ptr(top_idx), _ptr(top_val), _ptr(ws),
+                               c_size_t(0 if ws is None else ws.numel()), _stream(stream)))
+    return bins
+
+
+def declared_symbols(header=HEADER):
+    """Function names declared in include/cutqc.h."""
+    import re
+    text = open(header).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(cutqc_\w+)\s*\(", text, re.M)))

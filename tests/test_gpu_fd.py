@@ -1,0 +1,147 @@
+"""GPU parity of attribution and FD reconstruction (through the C ABI)
+against the FP64 oracle, on seeded inputs: small cases that span several
+tiles and ragged tails, both output orders, both precisions, and the full
+30-qubit two-subcircuit configuration."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TV_GATE = 1e-6      # total-variation gate of the reconstruction
+
+
+@pytest.fixture(scope="module")
+def cq():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_05836_gb300 import cutqc
+    return cutqc
+
+
+def _oracle_att(subs, var):
+    from oracle import attribution
+    return [attribution.attribute(v, s.w, s.in_local, s.out_local, s.in_edge, s.out_edge) for s, v in zip(subs, var)]
+
+
+def _gpu_att(cq, subs, var, dtype=None):
+    import torch
+    dev = torch.device("cuda")
+    outs = []
+    for s, v in zip(subs, var):
+        t = torch.from_numpy(v).to(dev)
+        if dtype is not None:
+            t = t.to(dtype)
+        outs.append(cq.cutqc_attribute(s, t))
+    torch.cuda.synchronize()
+    return outs
+
+
+def _cases():
+    from workloads import circuits as C
+    from workloads.cutting import search_cut
+    yield "brickwall8_k5", search_cut(C.brickwall(8, 6, 0), 7, 2, restarts=4)
+    yield "aqft12_3sub", search_cut(C.aqft(12, 3, max_dist=3), 7, 3, restarts=4)
+    yield "supremacy3x4", search_cut(C.supremacy(3, 4, 8, 1), 8, 2, restarts=4)
+    yield "brickwall12_4sub", search_cut(C.brickwall(12, 3, 2), 5, 4, restarts=6)
+    yield "bv13_chain", search_cut(C.bv(13, 4), 5, 4, restarts=4)
+
+
+CASES = list(_cases())
+
+
+@pytest.mark.parametrize("name,cut", CASES, ids=[c[0] for c in CASES])
+def test_attribution_matches_oracle(cq, name, cut):
+    import torch
+    from workloads.simulate import simulate_variants
+    subs = cut.subcircuits
+    var = [simulate_variants(s) for s in subs]
+    ref = _oracle_att(subs, var)
+    for dtype in (None, torch.float32):
+        got = _gpu_att(cq, subs, var, dtype)
+        for g, r in zip(got, ref):
+            g = g.cpu().numpy().astype(np.float64)
+            assert g.shape == r.shape
+            scale = np.abs(r).max()
+            assert np.abs(g - r).max() <= 4e-7 * scale, name
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["simt", "tc"])
+@pytest.mark.parametrize("order", [0, 1], ids=["kron", "original"])
+@pytest.mark.parametrize("name,cut", CASES, ids=[c[0] for c in CASES])
+def test_fd_matches_oracle(cq, name, cut, precision, order):
+    import torch
+    from oracle import fd, metrics, statevector
+    from workloads.simulate import simulate_variants
+    subs = cut.subcircuits
+    var = [simulate_variants(s) for s in subs]
+    A = _oracle_att(subs, var)
+    pk = fd.reconstruct_kron(A, [s.edges for s in subs], cut.K)
+    ref = pk if order == 0 else fd.kron_to_original(pk, [s.out_qubit for s in subs])
+    att = _gpu_att(cq, subs, var)
+    total = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out, _ = cq.cutqc_reconstruct_fd(subs, att, order, precision, sum_out=total)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    assert metrics.tv(got, ref) <= TV_GATE, (name, metrics.tv(got, ref))
+    assert abs(total.item() - 1.0) <= 1e-6
+    # the device sum adds pairwise float partials of <= 32 outputs in float64:
+    # each partial is <= 5 roundings deep, so |error| <= 5 * 2^-24 * sum|p|
+    assert abs(total.item() - got.sum()) <= 5 * 2.0 ** -24 * np.abs(got).sum()
+    assert metrics.max_abs(got, ref) <= 1e-6
+    if order == 1:
+        assert metrics.tv(got, statevector.probabilities(cut.circuit)) <= TV_GATE
+    assert cq.cutqc_device_status() == 0
+
+
+def test_fd_row_split_reassembles(cq):
+    """Offset/stride sharding: row ranges written separately equal the whole."""
+    import torch
+    from workloads import circuits as C
+    from workloads.cutting import search_cut
+    from workloads.simulate import simulate_variants
+    cut = search_cut(C.supremacy(3, 4, 8, 1), 8, 2, restarts=4)
+    subs = cut.subcircuits
+    att = _gpu_att(cq, subs, [simulate_variants(s) for s in subs])
+    for prec in (0, 1):
+        full, _ = cq.cutqc_reconstruct_fd(subs, att, 0, prec)
+        rows, cols = cq.cutqc_fd_shape(subs)
+        parts = []
+        for r0, r1 in ((0, 3), (3, rows)):
+            p, _ = cq.cutqc_reconstruct_fd(subs, att, 0, prec, row_begin=r0, row_end=r1)
+            parts.append(p)
+        torch.cuda.synchronize()
+        assert torch.equal(torch.cat(parts), full)
+
+
+def test_fd_two_subcircuit_30q_full_size(cq):
+    """30-qubit supremacy-family circuit, K=4, 2^30 outputs, in the launch
+    configuration the benchmark times: full TV against the FP64 oracle
+    (row blocks of A^T B), sum p, and both precisions agree."""
+    import torch
+    from workloads.configs import fd_two_sub
+    w = fd_two_sub()
+    subs = w.subcircuits
+    var = w.variants()
+    A64, B64 = _oracle_att(subs, var)
+    att = _gpu_att(cq, subs, var)
+    total = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out, _ = cq.cutqc_reconstruct_fd(subs, att, 0, 1, sum_out=total)
+    torch.cuda.synchronize()
+    assert abs(total.item() - 1.0) <= 1e-6
+    M, N = A64.shape[0], B64.shape[0]
+    out2 = out.view(M, N)
+    tv = 0.0
+    step = 512
+    for r0 in range(0, M, step):
+        ref = (A64[r0:r0 + step] @ B64.T) * 0.5 ** w.K
+        got = out2[r0:r0 + step].cpu().numpy().astype(np.float64)
+        tv += 0.5 * np.abs(got - ref).sum()
+    assert tv <= TV_GATE, tv
+    simt, _ = cq.cutqc_reconstruct_fd(subs, att, 0, 0)
+    torch.cuda.synchronize()
+    diff = (simt - out).abs().sum().item() * 0.5
+    assert diff <= 2 * TV_GATE
+    assert cq.cutqc_device_status() == 0
