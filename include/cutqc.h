@@ -190,6 +190,44 @@ int cutqc_dd_step(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bi
                   float* bins_dev, double* bin_sum_dev, int topk, int32_t* top_idx_dev,
                   float* top_val_dev, void* ws_dev, size_t ws_bytes, void* stream);
 
+/* Algorithm 1 end to end.  Active qubits at depth d are the M lowest
+ * unresolved ones, i.e. qubits [d*M, min(n, d*M + M)); the qubits below d*M
+ * are zoomed to the bin being expanded; the rest are merged.
+ *   strategy 0 (DFS, Algorithm 1 as written): each recursion reconstructs one
+ *     bin job, appends its T largest bins that still have merged qubits to L,
+ *     keeps the T largest of L (stable: earlier entries first among equal
+ *     values) and pops the largest as the next job; stops after R recursions
+ *     or when L is empty.
+ *   strategy 1 (BFS): level by level; the next level expands the T largest
+ *     bins (with merged qubits) over all jobs of the current level; at most R
+ *     levels.  The jobs of one level run as one batch.
+ * jobs (host, [max_jobs]) receives one record per job in execution order;
+ * bins_dev receives each job's 2^n_active bins at jobs[j].bins_offset
+ * (floats), bins_capacity floats in all.  Synchronises `stream` once per
+ * level (the selection is read on the host).  Limits: n <= 128, M <= 30,
+ * T <= 32.  Workspace: cutqc_dd_run_workspace_size bytes.                   */
+typedef struct cutqc_dd_job_result {
+  int32_t level;            /* recursion (DFS) or level (BFS) index */
+  int32_t depth;            /* qubits below depth * M are zoomed */
+  int32_t parent;           /* job this one zooms into, -1 for the first */
+  int32_t parent_bin;       /* bin of the parent it expands */
+  int32_t n_active;
+  int32_t active[32];       /* active qubits, ascending: bin bit j = active[j] */
+  uint64_t zoom_mask[2];    /* qubit q fixed <=> bit q (q < 128) */
+  uint64_t zoom_val[2];     /* its value */
+  double bin_sum;           /* float64 total of the job's bins */
+  int32_t top_idx[32];      /* T largest bins, -1 past the end */
+  float top_val[32];
+  int64_t bins_offset;      /* offset of the bins in bins_dev (floats) */
+} cutqc_dd_job_result;
+
+int cutqc_dd_run_workspace_size(int n_sub, const cutqc_subcircuit* s, int n_qubits, int M, int T,
+                                size_t* bytes);
+int cutqc_dd_run(int n_sub, const cutqc_subcircuit* s, const float* const* attributed_dev,
+                 int n_qubits, int M, int R, int T, int strategy, int max_jobs,
+                 cutqc_dd_job_result* jobs, int* n_jobs_out, float* bins_dev, int64_t bins_capacity,
+                 void* ws_dev, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------- reductions
  * sum_dev (device float64 scalar) += sum of x_dev[0..n) in float64.          */
 int cutqc_sum_f64(const float* x_dev, int64_t n, double* sum_dev, void* stream);

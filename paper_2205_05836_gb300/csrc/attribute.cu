@@ -46,151 +46,211 @@ struct AttrParams {
 __device__ __forceinline__ float load_val(const double* p) { return (float)__ldg(p); }
 __device__ __forceinline__ float load_val(const float* p) { return __ldg(p); }
 
-// 4x4 map of the initialised side: rows I, X, Y, Z; columns |0>,|1>,|+>,|+i>.
-__device__ __forceinline__ float init_map(int d, const float* in, int stride) {
-  float p0 = in[0], p1 = in[stride], pp = in[2 * stride], ppi = in[3 * stride];
-  switch (d) {
-    case 0: return p0 + p1;
-    case 1: return 2.f * pp - p0 - p1;
-    case 2: return 2.f * ppi - p0 - p1;
-    default: return p0 - p1;
-  }
+// 4x4 map of the initialised side: bases I, X, Y, Z from the runs
+// |0>, |1>, |+>, |+i> (in registers).
+__device__ __forceinline__ void init_map4(const float (&p)[4], float (&o)[4]) {
+  const float s01 = p[0] + p[1];
+  o[0] = s01;
+  o[1] = 2.f * p[2] - s01;
+  o[2] = 2.f * p[3] - s01;
+  o[3] = p[0] - p[1];
 }
 
-// Initialised-side pass.  Fiber over the 4^k_in init digits, R consecutive
-// outcome rows x (full w-bit index), fixed measurement run index `mrun`
-// (blockIdx.y).  final_layout: write attributed[x][col] (only valid when
-// k_out == 0); else write the [4^k_in][3^k_out][2^w] layout with states
-// replaced by bases.
-template <typename T>
+// Rows per CTA for a fiber of F values (compile time): as many as fit a
+// 48 KiB padded [F][R + 1] block, at most 32.
+__host__ __device__ constexpr int rows_for(int F) {
+  return F * 33 * 4 <= 48 * 1024 ? 32 : F * 17 * 4 <= 48 * 1024 ? 16 : F * 9 * 4 <= 48 * 1024 ? 8
+       : F * 5 * 4 <= 48 * 1024 ? 4 : F * 3 * 4 <= 48 * 1024 ? 2 : 1;
+}
+__host__ __device__ constexpr int pow3(int k) { return k == 0 ? 1 : 3 * pow3(k - 1); }
+
+// Initialised-side pass (KIN init cuts, compile time).  Fiber over the 4^KIN
+// init digits, R consecutive outcome rows x (full w-bit index), fixed
+// measurement run index `mrun` (blockIdx.y).  Shared memory holds the fiber
+// as [f][R + 1] (padded: row-major and column-major walks are conflict
+// free).  Each step takes two digits: a thread loads the 16 values of one
+// (digit j, digit j+1) block of one row, applies the 4x4 map along both in
+// registers and writes them back.  final_layout: write attributed[x][col]
+// (only when k_out == 0); otherwise the [4^k_in][3^k_out][2^w] layout with
+// states replaced by bases.
+template <typename T, int KIN>
 __global__ void __launch_bounds__(kThreads)
 attr_init_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, int final_layout) {
+  constexpr int F = 1 << (2 * KIN);
+  constexpr int R = rows_for(F);
+  constexpr int RS = R + 1;
   extern __shared__ float sm[];
-  const int F = 1 << (2 * p.k_in);
-  const int R = p.R;
-  float* buf0 = sm;
-  float* buf1 = sm + F * R;
+  float* buf = sm;                                             // [F][RS]
+  unsigned short* cperm = reinterpret_cast<unsigned short*>(buf + F * RS);   // column -> fiber index
   const int64_t x0 = (int64_t)blockIdx.x * R;
   const int mrun = blockIdx.y;
-  const int nm = [&] { int v = 1; for (int j = 0; j < p.k_out; ++j) v *= 3; return v; }();
-  const int64_t W = (int64_t)1 << p.w;
-  const int rows = (int)(p.n_rows - x0 < R ? p.n_rows - x0 : R);
-  // load: element (f, r) at src[(f * nm + mrun) * W + x0 + r]
-  for (int i = threadIdx.x; i < F * R; i += blockDim.x) {
-    int f = i / R, r = i - f * R;
-    float v = 0.f;
-    if (r < rows) v = load_val(src + ((int64_t)f * nm + mrun) * W + x0 + r);
-    buf0[i] = v;
-  }
-  __syncthreads();
-  float* in = buf0;
-  float* out = buf1;
-  for (int j = 0; j < p.k_in; ++j) {
-    const int stride = (1 << (2 * j)) * R;   // digit j of f has weight 4^j
-    for (int i = threadIdx.x; i < F * R; i += blockDim.x) {
-      int f = i / R, r = i - f * R;
-      int d = (f >> (2 * j)) & 3;
-      int base = ((f & ~(3 << (2 * j))) * R) + r;
-      out[i] = init_map(d, in + base, stride);
-    }
-    __syncthreads();
-    float* t = in; in = out; out = t;
-  }
-  if (final_layout) {
-    // attributed[x][col]: col = sum_j d_j << col_shift_in[j]
-    const int C = F;   // k_out == 0 so 4^k == F
-    for (int i = threadIdx.x; i < rows * C; i += blockDim.x) {
-      int r = i / C, c = i - r * C;
-      int f = 0;
-      for (int j = 0; j < p.k_in; ++j) f |= ((c >> p.col_shift_in[j]) & 3) << (2 * j);
-      dst[(x0 + r) * C + c] = in[f * R + r];
-    }
-  } else {
-    for (int i = threadIdx.x; i < F * R; i += blockDim.x) {
-      int f = i / R, r = i - f * R;
-      if (r < rows) dst[((int64_t)f * nm + mrun) * W + x0 + r] = in[i];
-    }
-  }
-}
-
-// Measured-side pass.  Fiber over (run digit m_j in {0,1,2}, outcome bit b_j)
-// per measured cut, combined as u_j = 2 m_j + b_j (radix 6); R consecutive
-// output rows x_out; fixed init digits `dinit` (blockIdx.y).  Writes
-// attributed[x_out][col(dinit, dmeas)].
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-attr_meas_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p) {
-  extern __shared__ float sm[];
-  int F = 1;
-  for (int j = 0; j < p.k_out; ++j) F *= 6;
-  const int R = p.R;
-  float* buf0 = sm;
-  float* buf1 = sm + F * R;
-  int64_t* rowbase = reinterpret_cast<int64_t*>(buf1 + F * R);   // [R]
-  int64_t* bpart = rowbase + R;                                  // [2^k_out]
-  const int64_t x0 = (int64_t)blockIdx.x * R;
-  const int dinit = blockIdx.y;
   int nm = 1;
   for (int j = 0; j < p.k_out; ++j) nm *= 3;
   const int64_t W = (int64_t)1 << p.w;
   const int rows = (int)(p.n_rows - x0 < R ? p.n_rows - x0 : R);
-  for (int r = threadIdx.x; r < R; r += blockDim.x) rowbase[r] = (int64_t)pdep64((uint64_t)(x0 + r), p.out_mask);
-  for (int b = threadIdx.x; b < (1 << p.k_out); b += blockDim.x) {
+  if (final_layout) {
+    for (int c = threadIdx.x; c < F; c += kThreads) {
+      int f = 0;
+#pragma unroll
+      for (int j = 0; j < KIN; ++j) f |= ((c >> p.col_shift_in[j]) & 3) << (2 * j);
+      cperm[c] = (unsigned short)f;
+    }
+  }
+  const T* base = src + (int64_t)mrun * W + x0;
+  const int64_t fstride = (int64_t)nm * W;
+#pragma unroll 4
+  for (int i = threadIdx.x; i < F * R; i += kThreads) {
+    const int f = i / R, r = i % R;
+    float v = 0.f;
+    if (r < rows) v = load_val(base + f * fstride + r);
+    buf[f * RS + r] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < KIN; j += 2) {
+    if (j + 1 < KIN) {
+      const int groups = F >> 4;
+      for (int it = threadIdx.x; it < groups * R; it += kThreads) {
+        const int r = it % R, grp = it / R;
+        const int lowmask = (1 << (2 * j)) - 1;
+        const int base_f = (grp & lowmask) | ((grp >> (2 * j)) << (2 * j + 4));
+        float v[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) v[a][b] = buf[(base_f | (a << (2 * j)) | (b << (2 * j + 2))) * RS + r];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          float col[4] = {v[0][b], v[1][b], v[2][b], v[3][b]}, o[4];
+          init_map4(col, o);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) v[a][b] = o[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          float o[4];
+          init_map4(v[a], o);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) buf[(base_f | (a << (2 * j)) | (b << (2 * j + 2))) * RS + r] = o[b];
+        }
+      }
+    } else {
+      const int groups = F >> 2;
+      for (int it = threadIdx.x; it < groups * R; it += kThreads) {
+        const int r = it % R, grp = it / R;
+        const int lowmask = (1 << (2 * j)) - 1;
+        const int base_f = (grp & lowmask) | ((grp >> (2 * j)) << (2 * j + 2));
+        float v[4], o[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) v[a] = buf[(base_f | (a << (2 * j))) * RS + r];
+        init_map4(v, o);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) buf[(base_f | (a << (2 * j))) * RS + r] = o[a];
+      }
+    }
+    __syncthreads();
+  }
+  if (final_layout) {
+    // attributed[x][col], c fastest: coalesced along the row
+    float* out = dst + x0 * F;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < rows * F; i += kThreads) {
+      const int r = i / F, c = i % F;
+      out[i] = buf[cperm[c] * RS + r];
+    }
+  } else {
+    float* out = dst + (int64_t)mrun * W + x0;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < F * R; i += kThreads) {
+      const int f = i / R, r = i % R;
+      if (r < rows) out[f * fstride + r] = buf[f * RS + r];
+    }
+  }
+}
+
+// Measured-side pass (KOUT measured cuts, compile time).  For each measured
+// cut the basis digit d selects the measurement run (I, Z: computational;
+// X: X basis; Y: Y basis) and the sign of outcome 1 (+ for I, - otherwise):
+//   out[d] = sum_{b in {0,1}^KOUT} (-1)^{popcount(b & nonI(d))} V[run(d)][b]
+// with V[m][b] the run-m probability of outcome bits b of the measured cuts.
+// Shared memory: V as [(m << KOUT) | b][R + 1] for R consecutive output rows
+// x_out and fixed init digits `dinit` (blockIdx.y).
+template <typename T, int KOUT>
+__global__ void __launch_bounds__(kThreads)
+attr_meas_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p) {
+  constexpr int NM = pow3(KOUT);
+  constexpr int F = NM << KOUT;
+  constexpr int R = rows_for(F);
+  constexpr int RS = R + 1;
+  constexpr int G = 1 << (2 * KOUT);
+  extern __shared__ float sm[];
+  float* buf = sm;                                                     // [F][RS]
+  int64_t* rowbase = reinterpret_cast<int64_t*>(buf + ((F * RS + 1) & ~1));   // [R]
+  int64_t* bpart = rowbase + R;                                       // [2^KOUT]
+  int* runoff = reinterpret_cast<int*>(bpart + (1 << KOUT));          // [G]: (run << KOUT) * RS
+  int* nonI = runoff + G;                                             // [G]
+  int* colm = nonI + G;                                               // [G]: column of the measured digits
+  const int64_t x0 = (int64_t)blockIdx.x * R;
+  const int dinit = blockIdx.y;
+  const int64_t W = (int64_t)1 << p.w;
+  const int rows = (int)(p.n_rows - x0 < R ? p.n_rows - x0 : R);
+  for (int r = threadIdx.x; r < R; r += kThreads) rowbase[r] = (int64_t)pdep64((uint64_t)(x0 + r), p.out_mask);
+  for (int b = threadIdx.x; b < (1 << KOUT); b += kThreads) {
     uint64_t v = 0;
-    for (int j = 0; j < p.k_out; ++j)
+#pragma unroll
+    for (int j = 0; j < KOUT; ++j)
       if ((b >> j) & 1) v |= p.meas_mask[j];
     bpart[b] = (int64_t)v;
   }
-  __syncthreads();
-  // load: fiber index f = sum_j u_j 6^j, u_j = 2 m_j + b_j
-  for (int i = threadIdx.x; i < F * R; i += blockDim.x) {
-    int f = i / R, r = i - f * R;
-    int t = f, m = 0, b = 0, w3 = 1;
-    for (int j = 0; j < p.k_out; ++j) {
-      int u = t % 6; t /= 6;
-      m += (u >> 1) * w3; w3 *= 3;
-      b |= (u & 1) << j;
+  for (int d = threadIdx.x; d < G; d += kThreads) {
+    int run = 0, w3 = 1, mask = 0, c = 0;
+#pragma unroll
+    for (int j = 0; j < KOUT; ++j) {
+      const int dj = (d >> (2 * j)) & 3;          // I, X, Y, Z
+      run += (dj == 3 ? 0 : dj) * w3;             // Z shares the computational run
+      w3 *= 3;
+      if (dj) mask |= 1 << j;
+      c |= dj << p.col_shift_out[j];
     }
+    runoff[d] = (run << KOUT) * RS;
+    nonI[d] = mask;
+    colm[d] = c;
+  }
+  __syncthreads();
+  const T* base = src + (int64_t)dinit * NM * W;
+#pragma unroll 4
+  for (int i = threadIdx.x; i < F * R; i += kThreads) {
+    const int e = i / R, r = i % R;
+    const int m = e >> KOUT, b = e & ((1 << KOUT) - 1);
     float v = 0.f;
-    if (r < rows) v = load_val(src + ((int64_t)dinit * nm + m) * W + (rowbase[r] | bpart[b]));
-    buf0[i] = v;
+    if (r < rows) v = load_val(base + (int64_t)m * W + (rowbase[r] | bpart[b]));
+    buf[e * RS + r] = v;
   }
   __syncthreads();
-  // axis j: radix 6 -> radix 4; digits < j already radix 4
-  float* in = buf0;
-  float* out = buf1;
-  int Fin = F;
-  for (int j = 0; j < p.k_out; ++j) {
-    int low = 1 << (2 * j);          // size of processed (radix-4) digits below j
-    int hi_in = Fin / (low * 6);     // size of the digits above j
-    int Fout = low * 4 * hi_in;
-    for (int i = threadIdx.x; i < Fout * R; i += blockDim.x) {
-      int g = i / R, r = i - g * R;
-      int lo_part = g % low;
-      int d = (g / low) & 3;
-      int hi_part = g / (low * 4);
-      // (run, w0, w1): I (0,+,+) X (1,+,-) Y (2,+,-) Z (0,+,-)
-      int run = (d == 3) ? 0 : d;
-      float w1 = (d == 0) ? 1.f : -1.f;
-      int f0 = lo_part + low * (2 * run + 0) + low * 6 * hi_part;
-      int f1 = lo_part + low * (2 * run + 1) + low * 6 * hi_part;
-      out[i] = in[f0 * R + r] + w1 * in[f1 * R + r];
-    }
-    Fin = Fout;
-    __syncthreads();
-    float* t = in; in = out; out = t;
-  }
-  // write: dmeas index g = sum_j d_j 4^j
-  const int G = Fin;                         // 4^k_out
   const int64_t C = (int64_t)1 << (2 * p.k);
   int cin = 0;
   for (int j = 0; j < p.k_in; ++j) cin |= ((dinit >> (2 * j)) & 3) << p.col_shift_in[j];
-  for (int i = threadIdx.x; i < rows * G; i += blockDim.x) {
-    int r = i / G, g = i - r * G;
-    int c = cin;
-    for (int j = 0; j < p.k_out; ++j) c |= ((g >> (2 * j)) & 3) << p.col_shift_out[j];
-    dst[(x0 + r) * C + c] = in[g * R + r];
+  for (int i = threadIdx.x; i < rows * G; i += kThreads) {
+    const int r = i / G, g = i % G;
+    const float* vb = buf + runoff[g] + r;
+    const int mask = nonI[g];
+    float acc = 0.f;
+#pragma unroll
+    for (int b = 0; b < (1 << KOUT); ++b) {
+      const float v = vb[b * RS];
+      acc += (__popc(b & mask) & 1) ? -v : v;
+    }
+    dst[(x0 + r) * C + (cin | colm[g])] = acc;
   }
+}
+
+template <typename T, int KIN>
+size_t init_smem() { return (size_t)(1 << (2 * KIN)) * (rows_for(1 << (2 * KIN)) + 1) * 4 + (2u << (2 * KIN)); }
+template <typename T, int KOUT>
+size_t meas_smem() {
+  constexpr int F = pow3(KOUT) << KOUT;
+  constexpr int R = rows_for(F);
+  return (((size_t)F * (R + 1) + 1) & ~(size_t)1) * 4 + (size_t)(R + (1 << KOUT)) * 8 + 3 * ((size_t)1 << (2 * KOUT)) * 4;
 }
 
 // k == 0: plain conversion to float32.
@@ -261,11 +321,56 @@ cudaError_t set_max_smem(const void* fn) {
   return e;
 }
 
-int pick_rows(int fiber, int64_t max_rows) {
-  int R = 32;
-  while (R > 1 && (size_t)fiber * R * 2 * sizeof(float) > 96 * 1024) R >>= 1;
-  while (R > 1 && R > max_rows) R >>= 1;
-  return R;
+
+template <typename T, int KIN>
+int run_init(const T* src, float* out, const AttrParams& p, int final_layout, cudaStream_t st) {
+  constexpr int F = 1 << (2 * KIN);
+  constexpr int R = rows_for(F);
+  const size_t smem = init_smem<T, KIN>();
+  int nm = 1;
+  for (int j = 0; j < p.k_out; ++j) nm *= 3;
+  dim3 grid((unsigned)((p.n_rows + R - 1) / R), nm);
+  CUTQC_CUDA_TRY(set_max_smem((const void*)attr_init_pass<T, KIN>));
+  attr_init_pass<T, KIN><<<grid, kThreads, smem, st>>>(src, out, p, final_layout);
+  CUTQC_LAUNCH_CHECK("attr_init_pass");
+  return CUTQC_OK;
+}
+
+template <typename T, int KOUT>
+int run_meas(const T* src, float* out, const AttrParams& p, cudaStream_t st) {
+  constexpr int F = pow3(KOUT) << KOUT;
+  constexpr int R = rows_for(F);
+  const size_t smem = meas_smem<T, KOUT>();
+  dim3 grid((unsigned)((p.n_rows + R - 1) / R), 1u << (2 * p.k_in));
+  CUTQC_CUDA_TRY(set_max_smem((const void*)attr_meas_pass<T, KOUT>));
+  attr_meas_pass<T, KOUT><<<grid, kThreads, smem, st>>>(src, out, p);
+  CUTQC_LAUNCH_CHECK("attr_meas_pass");
+  return CUTQC_OK;
+}
+
+template <typename T>
+int dispatch_init(const T* src, float* out, const AttrParams& p, int final_layout, cudaStream_t st) {
+  switch (p.k_in) {
+    case 1: return run_init<T, 1>(src, out, p, final_layout, st);
+    case 2: return run_init<T, 2>(src, out, p, final_layout, st);
+    case 3: return run_init<T, 3>(src, out, p, final_layout, st);
+    case 4: return run_init<T, 4>(src, out, p, final_layout, st);
+    case 5: return run_init<T, 5>(src, out, p, final_layout, st);
+    case 6: return run_init<T, 6>(src, out, p, final_layout, st);
+  }
+  return set_error(CUTQC_EUNSUPPORTED, "k_in = %d", p.k_in);
+}
+
+template <typename T>
+int dispatch_meas(const T* src, float* out, const AttrParams& p, cudaStream_t st) {
+  switch (p.k_out) {
+    case 1: return run_meas<T, 1>(src, out, p, st);
+    case 2: return run_meas<T, 2>(src, out, p, st);
+    case 3: return run_meas<T, 3>(src, out, p, st);
+    case 4: return run_meas<T, 4>(src, out, p, st);
+    case 5: return run_meas<T, 5>(src, out, p, st);
+  }
+  return set_error(CUTQC_EUNSUPPORTED, "k_out = %d", p.k_out);
 }
 
 template <typename T>
@@ -280,43 +385,16 @@ int launch_attr(const cutqc_subcircuit* s, const T* src, float* dst, float* tmp,
     CUTQC_LAUNCH_CHECK("attr_copy");
     return CUTQC_OK;
   }
-  const T* meas_src = src;
-  bool meas_from_tmp = false;
   if (s->k_in > 0) {
-    const int F = 1 << (2 * s->k_in);
     p.n_rows = (int64_t)1 << s->w;
-    p.R = pick_rows(F, p.n_rows);
-    size_t smem = (size_t)F * p.R * 2 * sizeof(float);
-    if (smem > (size_t)kAttrMaxSmem) return set_error(CUTQC_EUNSUPPORTED, "attribution fiber too large");
-    int nm = 1;
-    for (int j = 0; j < s->k_out; ++j) nm *= 3;
-    dim3 grid((unsigned)((p.n_rows + p.R - 1) / p.R), nm);
-    int final_layout = s->k_out == 0;
-    float* out = final_layout ? dst : tmp;
-    CUTQC_CUDA_TRY(set_max_smem((const void*)attr_init_pass<T>));
-    attr_init_pass<T><<<grid, kThreads, smem, st>>>(src, out, p, final_layout);
-    CUTQC_LAUNCH_CHECK("attr_init_pass");
-    if (final_layout) return CUTQC_OK;
-    meas_from_tmp = true;
-  }
-  {
-    int F = 1;
-    for (int j = 0; j < s->k_out; ++j) F *= 6;
+    const int final_layout = s->k_out == 0;
+    int rc = dispatch_init<T>(src, final_layout ? dst : tmp, p, final_layout, st);
+    if (rc || final_layout) return rc;
     p.n_rows = (int64_t)1 << o;
-    p.R = pick_rows(F, p.n_rows);
-    size_t smem = (size_t)F * p.R * 2 * sizeof(float) + (size_t)(p.R + (1 << s->k_out)) * sizeof(int64_t);
-    if (smem > (size_t)kAttrMaxSmem) return set_error(CUTQC_EUNSUPPORTED, "attribution fiber too large");
-    dim3 grid((unsigned)((p.n_rows + p.R - 1) / p.R), 1u << (2 * s->k_in));
-    if (meas_from_tmp) {
-      CUTQC_CUDA_TRY(set_max_smem((const void*)attr_meas_pass<float>));
-      attr_meas_pass<float><<<grid, kThreads, smem, st>>>(tmp, dst, p);
-    } else {
-      CUTQC_CUDA_TRY(set_max_smem((const void*)attr_meas_pass<T>));
-      attr_meas_pass<T><<<grid, kThreads, smem, st>>>(meas_src, dst, p);
-    }
-    CUTQC_LAUNCH_CHECK("attr_meas_pass");
+    return dispatch_meas<float>(tmp, dst, p, st);
   }
-  return CUTQC_OK;
+  p.n_rows = (int64_t)1 << o;
+  return dispatch_meas<T>(src, dst, p, st);
 }
 
 }  // namespace

@@ -24,10 +24,13 @@ namespace cutqc {
 // source row x is xp with its bits moved by the row map (bit j of xp goes to
 // bit rm.bit[j] of x; identity unless rm.permute).  K index s = shared digits;
 // source column = pdep(open, open_dmask) | pdep(s, shared_dmask).
+// mode: 0 = per-row scale, 1 = one scale from *gmax for every row (written
+// to scale[0]), 2 = only accumulate max|x| into *gmax (as float bits; the
+// values are non-negative so integer max orders them).
 __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows, int64_t K, int64_t Kp,
                             float* __restrict__ out32, __half* __restrict__ hi,
                             __half* __restrict__ lo, float* __restrict__ scale, int64_t src_bstride,
-                            int64_t dst_bstride) {
+                            int64_t dst_bstride, int mode, unsigned int* __restrict__ gmax) {
   // batch item blockIdx.y: source and destinations offset by their strides
   v.src += (int64_t)blockIdx.y * src_bstride;
   if (out32) out32 += (int64_t)blockIdx.y * dst_bstride * Kp;
@@ -63,13 +66,21 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
       }
       continue;
     }
-    // row max, then a power-of-two scale putting it in [2^14, 2^15)
+    // row max (or the operand's max), then a power-of-two scale putting it in
+    // [2^14, 2^15) (clamped to [2^-60, 2^60] so that the scale, its inverse
+    // and the epilogue's product of two scales and 2^-K stay normal floats;
+    // values that small contribute below float32 resolution of any output)
     float mx = 0.f;
-    for (int64_t s = lane; s < K; s += 32) mx = fmaxf(mx, fabsf(__ldg(row + col(s))));
-    for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    // (clamped to [2^-60, 2^60] so that the scale, its inverse and the
-    // epilogue's product of two scales and 2^-K stay normal floats; rows that
-    // small contribute below float32 resolution of any output)
+    if (mode == 1) {
+      mx = __uint_as_float(*gmax);
+    } else {
+      for (int64_t s = lane; s < K; s += 32) mx = fmaxf(mx, fabsf(__ldg(row + col(s))));
+      for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      if (mode == 2) {
+        if (lane == 0) atomicMax(gmax, __float_as_uint(mx));
+        continue;
+      }
+    }
     int e = 0;
     float sc = 1.f;
     if (mx > 0.f) {
@@ -77,7 +88,7 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
       sc = ldexpf(1.f, max(-60, min(60, e - 15)));
     }
     const float inv = 1.f / sc;   // exact: power of two
-    if (lane == 0) scale[r] = sc;
+    if (lane == 0 && (mode == 0 || r == 0)) scale[mode == 0 ? r : 0] = sc;
     for (int64_t s = lane; s < Kp; s += 32) {
       float y = 0.f;
       if (s < K) y = __ldg(row + col(s)) * inv;
@@ -91,7 +102,7 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
 
 int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int64_t row0, int64_t rows,
                      int64_t Kp, float* out32, __half* hi, __half* lo, float* scale, cudaStream_t st,
-                     int batch, int64_t src_bstride) {
+                     int batch, int64_t src_bstride, unsigned int* gmax) {
   if (rows <= 0) return CUTQC_OK;
   RowMap rm{};
   rm.n = n_bits;
@@ -105,8 +116,19 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
   int blocks = (int)std::min<int64_t>((rows * 32 + 255) / 256, (int64_t)sm_count() * 16);
   if (blocks < 1) blocks = 1;
   if (batch < 1 || batch > 65535) return set_error(CUTQC_EUNSUPPORTED, "batch %d out of range", batch);
-  prep_kernel<<<dim3(blocks, batch), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride,
-                                                   rows);
+  if (gmax) {
+    // one scale for the whole operand: max pass, then the split
+    if (batch != 1) return set_error(CUTQC_EINVAL, "internal: operand-wide scale needs batch 1");
+    CUTQC_CUDA_TRY(cudaMemsetAsync(gmax, 0, sizeof(unsigned int), st));
+    prep_kernel<<<dim3(blocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride, rows, 2,
+                                                 gmax);
+    CUTQC_LAUNCH_CHECK("prep_kernel (max)");
+    prep_kernel<<<dim3(blocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride, rows, 1,
+                                                 gmax);
+  } else {
+    prep_kernel<<<dim3(blocks, batch), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride,
+                                                     rows, 0, nullptr);
+  }
   CUTQC_LAUNCH_CHECK("prep_kernel");
   return CUTQC_OK;
 }

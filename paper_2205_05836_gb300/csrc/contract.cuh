@@ -31,10 +31,12 @@ struct RowMap {
 // Operand gather of rows [row0, row0 + rows): float32 (out32 != null) or
 // float16 hi/lo with a power-of-two scale per row; K padded with zeros to Kp.
 // batch > 1: item b reads v.src + b * src_bstride and writes rows * Kp
-// elements (rows scales) further per item.
+// elements (rows scales) further per item.  gmax != null (half mode, batch
+// 1): one scale for the whole operand, written to scale[0]; gmax is a device
+// word of scratch.
 int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int64_t row0, int64_t rows,
                      int64_t Kp, float* out32, __half* hi, __half* lo, float* scale, cudaStream_t st,
-                     int batch = 1, int64_t src_bstride = 0);
+                     int batch = 1, int64_t src_bstride = 0, unsigned int* gmax = nullptr);
 
 // float32 CUDA-core GEMM with bit-deposit epilogue.
 // batch > 1: item b uses A + b*a_bstride, B + b*b_bstride, out + b*out_bstride,
@@ -94,7 +96,9 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
              int64_t row_end, uint8_t* ws, cudaStream_t st);
 
 // Tensor-core GEMM (tcgen05, FP16 hi/lo split, three products) with the same
-// epilogue; operands from launch_prep in half mode with Kp % 64 == 0.
+// epilogue; operands from launch_prep_rows in half mode with Kp % 64 == 0:
+// the row operand with per-row scales, the column operand with one scale
+// (scale[0]).
 struct TcOperand {
   const __half* hi;
   const __half* lo;

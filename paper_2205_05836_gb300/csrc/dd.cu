@@ -13,6 +13,7 @@
 #include "contract.cuh"
 
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <map>
 #include <vector>
@@ -291,5 +292,248 @@ extern "C" int cutqc_sum_f64(const float* x, int64_t n, double* sum, void* strea
   int blocks = (int)std::min<int64_t>((n / 16 + 255) / 256 + 1, (int64_t)sm_count() * 8);
   sum_f64_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(x, n, sum);
   CUTQC_LAUNCH_CHECK("sum_f64_kernel");
+  return CUTQC_OK;
+}
+
+// ---------------------------------------------------------------- Algorithm 1
+
+namespace cutqc {
+namespace {
+
+struct LevelShape {
+  int depth = 0;
+  std::vector<int> active;                 // qubits, ascending
+  std::vector<int32_t> active_bits;        // per subcircuit
+  std::vector<int32_t> bin_bit;            // subcircuit-major
+  std::vector<uint64_t> act_mask, zoom_mask;   // per subcircuit, over output bits
+};
+
+int level_shape(int n_sub, const cutqc_subcircuit* s, int n, int M, int depth, LevelShape* L) {
+  L->depth = depth;
+  L->active.clear();
+  for (int q = depth * M; q < std::min(n, depth * M + M); ++q) L->active.push_back(q);
+  const int lo = depth * M, hi = depth * M + (int)L->active.size();
+  L->active_bits.assign(n_sub, 0);
+  L->bin_bit.clear();
+  L->act_mask.assign(n_sub, 0);
+  L->zoom_mask.assign(n_sub, 0);
+  for (int i = 0; i < n_sub; ++i) {
+    const int o = s[i].w - s[i].k_out;
+    for (int t = 0; t < o; ++t) {
+      const int q = s[i].out_qubit[t];
+      if (q < 0 || q >= n) return set_error(CUTQC_EINVAL, "out_qubit %d outside 0..%d", q, n - 1);
+      if (q >= lo && q < hi) {
+        L->act_mask[i] |= (uint64_t)1 << t;
+        L->active_bits[i]++;
+        L->bin_bit.push_back(q - lo);
+      } else if (q < lo) {
+        L->zoom_mask[i] |= (uint64_t)1 << t;
+      }
+    }
+  }
+  return CUTQC_OK;
+}
+
+struct RunLayout {
+  size_t merged_off[64];
+  size_t zoom_off[64];
+  size_t step_off = 0, top_idx_off = 0, top_val_off = 0, sum_off = 0;
+  size_t total = 0;
+};
+
+// Workspace for one level of n_jobs jobs.
+int level_layout(int n_sub, const cutqc_subcircuit* s, const LevelShape& L, int n_jobs, RunLayout* R) {
+  size_t ws = 0;
+  auto take = [&](size_t b) { size_t o = ws; ws = align_up(ws + b, 256); return o; };
+  for (int i = 0; i < n_sub; ++i) {
+    const int k = s[i].k_in + s[i].k_out;
+    R->merged_off[i] = take((size_t)n_jobs * ((size_t)1 << L.active_bits[i]) * ((size_t)1 << (2 * k)) * sizeof(float));
+    R->zoom_off[i] = take((size_t)n_jobs * sizeof(uint64_t));
+  }
+  size_t step = 0;
+  int rc = cutqc_dd_step_workspace_size(n_sub, s, L.active_bits.data(), n_jobs, &step);
+  if (rc) return rc;
+  R->step_off = take(step);
+  R->top_idx_off = take((size_t)n_jobs * 32 * sizeof(int32_t));
+  R->top_val_off = take((size_t)n_jobs * 32 * sizeof(float));
+  R->sum_off = take((size_t)n_jobs * sizeof(double));
+  R->total = ws;
+  return CUTQC_OK;
+}
+
+int validate_run(int n_sub, const cutqc_subcircuit* s, int n, int M, int T) {
+  if (n_sub < 1 || n_sub > 64) return set_error(CUTQC_EINVAL, "n_sub must be in 1..64");
+  if (n < 1 || n > 128) return set_error(CUTQC_EUNSUPPORTED, "n_qubits must be in 1..128");
+  if (M < 1 || M > 30) return set_error(CUTQC_EUNSUPPORTED, "M must be in 1..30");
+  if (T < 0 || T > 32) return set_error(CUTQC_EUNSUPPORTED, "T must be in 0..32");
+  int tot = 0;
+  for (int i = 0; i < n_sub; ++i) {
+    int rc = validate_subcircuit(&s[i]);
+    if (rc) return rc;
+    tot += s[i].w - s[i].k_out;
+  }
+  if (tot != n) return set_error(CUTQC_EINVAL, "outputs (%d) != n_qubits (%d)", tot, n);
+  return CUTQC_OK;
+}
+
+}  // namespace
+}  // namespace cutqc
+
+extern "C" int cutqc_dd_run_workspace_size(int n_sub, const cutqc_subcircuit* s, int n, int M, int T,
+                                           size_t* bytes) {
+  int rc = validate_run(n_sub, s, n, M, T);
+  if (rc) return rc;
+  if (!bytes) return set_error(CUTQC_EINVAL, "null bytes");
+  size_t best = 0;
+  const int depths = (n + M - 1) / M;
+  for (int d = 0; d < depths; ++d) {
+    LevelShape L;
+    if ((rc = level_shape(n_sub, s, n, M, d, &L))) return rc;
+    RunLayout R;
+    if ((rc = level_layout(n_sub, s, L, std::max(1, T), &R))) return rc;
+    best = std::max(best, R.total);
+  }
+  *bytes = best;
+  return CUTQC_OK;
+}
+
+extern "C" int cutqc_dd_run(int n_sub, const cutqc_subcircuit* s, const float* const* att, int n, int M, int Rmax,
+                            int T, int strategy, int max_jobs, cutqc_dd_job_result* jobs, int* n_jobs_out,
+                            float* bins, int64_t bins_cap, void* ws_dev, size_t ws_bytes, void* stream) {
+  int rc = validate_run(n_sub, s, n, M, T);
+  if (rc) return rc;
+  if (!att || !jobs || !n_jobs_out || !bins || max_jobs < 1 || Rmax < 1)
+    return set_error(CUTQC_EINVAL, "bad arguments");
+  if (strategy != 0 && strategy != 1) return set_error(CUTQC_EINVAL, "strategy must be 0 (DFS) or 1 (BFS)");
+  size_t need = 0;
+  if ((rc = cutqc_dd_run_workspace_size(n_sub, s, n, M, T, &need))) return rc;
+  if (ws_bytes < need || !ws_dev) return set_error(CUTQC_ENOMEM, "DD workspace needs %zu bytes", need);
+  cudaStream_t st = (cudaStream_t)stream;
+  uint8_t* ws = (uint8_t*)ws_dev;
+  int n_jobs = 0;
+  int64_t bins_used = 0;
+  struct Pending { double value; int parent; int bin; int depth; uint64_t zm[2], zv[2]; };
+  auto qbit = [](const uint64_t* m, int q) { return (m[q >> 6] >> (q & 63)) & 1; };
+  // run one level: all `todo` entries share `depth`
+  auto run_level = [&](int level, std::vector<Pending>& todo, std::vector<int>* new_jobs) -> int {
+    const int depth = todo[0].depth;
+    const int nj = (int)todo.size();
+    LevelShape L;
+    int r = level_shape(n_sub, s, n, M, depth, &L);
+    if (r) return r;
+    RunLayout lay;
+    if ((r = level_layout(n_sub, s, L, nj, &lay))) return r;
+    if (lay.total > ws_bytes) return set_error(CUTQC_ENOMEM, "DD workspace too small for a level");
+    if (n_jobs + nj > max_jobs) return set_error(CUTQC_ENOMEM, "more than max_jobs jobs");
+    const int64_t nb = (int64_t)1 << L.active.size();
+    if (bins_used + nb * nj > bins_cap) return set_error(CUTQC_ENOMEM, "bins_capacity too small");
+    // per subcircuit zoom values of each job (over its output bits)
+    std::vector<const float*> merged(n_sub);
+    for (int i = 0; i < n_sub; ++i) {
+      const int o = s[i].w - s[i].k_out;
+      std::vector<uint64_t> zv(nj, 0);
+      for (int j = 0; j < nj; ++j)
+        for (int t = 0; t < o; ++t) {
+          const int q = s[i].out_qubit[t];
+          if (((L.zoom_mask[i] >> t) & 1) && qbit(todo[j].zv, q)) zv[j] |= (uint64_t)1 << t;
+        }
+      uint64_t* zdev = (uint64_t*)(ws + lay.zoom_off[i]);
+      CUTQC_CUDA_TRY(cudaMemcpyAsync(zdev, zv.data(), nj * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+      float* mdev = (float*)(ws + lay.merged_off[i]);
+      r = cutqc_dd_merge_batch(&s[i], att[i], L.act_mask[i], L.zoom_mask[i], nj, zdev, mdev, st);
+      if (r) return r;
+      merged[i] = mdev;
+      // the pageable source of the copy above must outlive it
+      CUTQC_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    float* bdev = bins + bins_used;
+    int32_t* tidx = (int32_t*)(ws + lay.top_idx_off);
+    float* tval = (float*)(ws + lay.top_val_off);
+    double* bsum = (double*)(ws + lay.sum_off);
+    r = cutqc_dd_step(n_sub, s, L.active_bits.data(), L.bin_bit.data(), nj, merged.data(), bdev, bsum, T, tidx, tval,
+                      ws + lay.step_off, lay.total - lay.step_off, st);
+    if (r) return r;
+    std::vector<int32_t> hidx((size_t)nj * std::max(1, T));
+    std::vector<float> hval((size_t)nj * std::max(1, T));
+    std::vector<double> hsum(nj);
+    if (T > 0) {
+      CUTQC_CUDA_TRY(cudaMemcpyAsync(hidx.data(), tidx, (size_t)nj * T * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      CUTQC_CUDA_TRY(cudaMemcpyAsync(hval.data(), tval, (size_t)nj * T * sizeof(float), cudaMemcpyDeviceToHost, st));
+    }
+    CUTQC_CUDA_TRY(cudaMemcpyAsync(hsum.data(), bsum, nj * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUTQC_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int j = 0; j < nj; ++j) {
+      cutqc_dd_job_result& J = jobs[n_jobs];
+      memset(&J, 0, sizeof(J));
+      J.level = level;
+      J.depth = depth;
+      J.parent = todo[j].parent;
+      J.parent_bin = todo[j].bin;
+      J.n_active = (int)L.active.size();
+      for (int a = 0; a < J.n_active; ++a) J.active[a] = L.active[a];
+      for (int w = 0; w < 2; ++w) { J.zoom_mask[w] = todo[j].zm[w]; J.zoom_val[w] = todo[j].zv[w]; }
+      J.bin_sum = hsum[j];
+      for (int t = 0; t < 32; ++t) { J.top_idx[t] = -1; J.top_val[t] = 0.f; }
+      for (int t = 0; t < T; ++t) { J.top_idx[t] = hidx[(size_t)j * T + t]; J.top_val[t] = hval[(size_t)j * T + t]; }
+      J.bins_offset = bins_used + (int64_t)j * nb;
+      new_jobs->push_back(n_jobs);
+      ++n_jobs;
+    }
+    bins_used += nb * nj;
+    return CUTQC_OK;
+  };
+  // children of a job: its top bins, if merged qubits remain
+  auto children = [&](int jid, std::vector<Pending>* out) {
+    const cutqc_dd_job_result& J = jobs[jid];
+    if ((J.depth + 1) * M >= n) return;          // nothing left to merge
+    for (int t = 0; t < T; ++t) {
+      const int b = J.top_idx[t];
+      if (b < 0) continue;
+      Pending p{};
+      p.value = J.top_val[t];
+      p.parent = jid;
+      p.bin = b;
+      p.depth = J.depth + 1;
+      for (int w = 0; w < 2; ++w) { p.zm[w] = J.zoom_mask[w]; p.zv[w] = J.zoom_val[w]; }
+      for (int a = 0; a < J.n_active; ++a) {
+        const int q = J.active[a];
+        p.zm[q >> 6] |= (uint64_t)1 << (q & 63);
+        if ((b >> a) & 1) p.zv[q >> 6] |= (uint64_t)1 << (q & 63);
+      }
+      out->push_back(p);
+    }
+  };
+  auto by_value = [](const Pending& a, const Pending& b) { return a.value > b.value; };
+  std::vector<Pending> first(1);
+  first[0].parent = -1;
+  first[0].bin = -1;
+  first[0].depth = 0;
+  if (strategy == 1) {
+    std::vector<Pending> todo = first;
+    for (int level = 0; level < Rmax && !todo.empty(); ++level) {
+      std::vector<int> made;
+      if ((rc = run_level(level, todo, &made))) return rc;
+      std::vector<Pending> cand;
+      for (int jid : made) children(jid, &cand);
+      std::stable_sort(cand.begin(), cand.end(), by_value);
+      if ((int)cand.size() > T) cand.resize(T);
+      todo = cand;
+    }
+  } else {
+    std::vector<Pending> Lst;
+    Pending cur = first[0];
+    for (int r = 0; r < Rmax; ++r) {
+      std::vector<Pending> one{cur};
+      std::vector<int> made;
+      if ((rc = run_level(r, one, &made))) return rc;
+      children(made[0], &Lst);
+      std::stable_sort(Lst.begin(), Lst.end(), by_value);
+      if ((int)Lst.size() > T) Lst.resize(T);
+      if (Lst.empty()) break;
+      cur = Lst.front();
+      Lst.erase(Lst.begin());
+    }
+  }
+  *n_jobs_out = n_jobs;
   return CUTQC_OK;
 }

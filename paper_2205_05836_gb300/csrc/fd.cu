@@ -320,7 +320,7 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
                               al, as, st);
         if (rc) return rc;
         rc = launch_prep_rows(vb, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp, nullptr,
-                              bh, bl, bs, st);
+                              bh, bl, bs, st, 1, 0, reinterpret_cast<unsigned int*>(bs + 1));
         if (rc) return rc;
         TcOperand ta{ah, al, as, M}, tb{bh, bl, bs, stg.N};
         rc = launch_tc_gemm(ta, tb, stg.Kp, alpha, stg.mask_m, stg.mask_n, dst + b * dst_b,

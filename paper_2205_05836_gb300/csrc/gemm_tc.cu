@@ -1,9 +1,10 @@
 // Tensor-core contraction for Eq. 1 on sm_103a (tcgen05 + TMA + TMEM).
 //
-// C[m][n] = alpha * sa[m] * sb[n] * sum_s (Ah Bh + Ah Bl + Al Bh)[m][n][s]
+// C[m][n] = alpha * sa[m] * sb * sum_s (Ah Bh + Ah Bl + Al Bh)[m][n][s]
 // where A = sa * (Ah + Al), B = sb * (Bh + Bl) are the float16 hi/lo splits of
-// the float32 operands (per-row power-of-two scales, see prep_kernel): about
-// 22 significant bits per operand, products exact in the FP32 accumulator.
+// the float32 operands (power-of-two scales: one per row of A, one for all of
+// B, see prep_kernel): about 22 significant bits per operand, products exact
+// in the FP32 accumulator.
 // The signed I/X/Y/Z terms of Eq. 1 cancel (sum|terms| is ~10x |P| on the
 // 30-qubit supremacy workload), which is why a single FP16/BF16/TF32 pass is
 // not accurate enough and the split is used.
@@ -52,6 +53,7 @@ constexpr long long kTimeoutCycles = 4000000000LL;       // ~2 s at 2 GHz
 
 struct TcMaps {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
+  CUtensorMap out;   // used when TcArgs::tma_store: 2-D [M][N] float32, 32 x 32 box, 128B swizzle
 };
 
 struct TcArgs {
@@ -68,6 +70,7 @@ struct TcArgs {
   float* out;
   double* sum;
   int streaming;
+  int tma_store;
   int* status;
 };
 
@@ -82,7 +85,13 @@ struct SmemTail {
   int abort_flag;
 };
 
-constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + sizeof(SmemTail);
+// one 32 x 32 float32 staging block per epilogue warp (4 KiB, 1024-aligned):
+// XOR-swizzled by row for the transposing store path, 128B-swizzled for the
+// bulk-tensor store path
+constexpr int STG_WARP_FLOATS = 32 * 32;
+constexpr int STG_BYTES = 8 * STG_WARP_FLOATS * 4;
+constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + STG_BYTES + sizeof(SmemTail);
+static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -173,16 +182,45 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int c0, int c1) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];"
+               ::"l"((uint64_t)map), "r"(src), "r"(c0), "r"(c1)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void st_v4(float* p, float4 v, int streaming) {
   if (streaming) __stcs(reinterpret_cast<float4*>(p), v);
   else *reinterpret_cast<float4*>(p) = v;
 }
 
+template <bool kTmaStore>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  SmemTail* tail = reinterpret_cast<SmemTail*>(smem + STAGES * STAGE_BYTES);
+  float* stg_all = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);
+  SmemTail* tail = reinterpret_cast<SmemTail*>(smem + STAGES * STAGE_BYTES + STG_BYTES);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 
@@ -309,52 +347,51 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
         tc_fence_after();
         __syncwarp();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          uint32_t r[32];
-          tmem_ld32(tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(buf * BN + h * 128 + q * 32), r);
+        for (int q = 0; q < 16; ++q) {
+          uint32_t r[8];
+          tmem_ld8(tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(buf * BN + h * 128 + q * 8), r);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) tot[q * 32 + i] += __uint_as_float(r[i]);
+          for (int i = 0; i < 8; ++i) tot[q * 8 + i] += __uint_as_float(r[i]);
         }
         tc_fence_before();
         mbar_arrive(smem_u32(&tail->cempty[buf]));
         if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
       }
       if (!ok) break;
+      // store: each 32 x 32 block goes through the warp's padded staging
+      // buffer so that one warp instruction writes one row segment of 32
+      // consecutive outputs (a full 128-byte line in Kronecker order)
       const int64_t m = (int64_t)mb * BM + row;
-      if (m >= args.M) continue;
-      const float rs = args.alpha * __ldg(args.sa + m);
-      const uint64_t roff = args.m_shift >= 0 ? ((uint64_t)m << args.m_shift) : pdep64((uint64_t)m, args.mask_m);
+      const bool mvalid = m < args.M;
+      const float rs = mvalid ? args.alpha * __ldg(args.sa + m) * __ldg(args.sb) : 0.f;
+      const uint64_t roff = mvalid ? (args.m_shift >= 0 ? ((uint64_t)m << args.m_shift) : pdep64((uint64_t)m, args.mask_m)) : 0;
       const int64_t nbase = (int64_t)nb * BN + h * 128;
+      float* stg = stg_all + warp * STG_WARP_FLOATS;
+      if (kTmaStore) {
+        // rows m..: one 32 x 32 box per block, written by the TMA engine from
+        // a 128B-swizzled staging block (16-byte chunk j of row r sits at
+        // chunk j ^ (r & 7)); rows or columns beyond the output are clipped
+        const int64_t mrow0 = (int64_t)mb * BM + g * 32;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t n0 = nbase + q * 32;
-        if (n0 >= args.N) break;
-        const uint64_t coff = args.n_contig ? (uint64_t)n0 : pdep64((uint64_t)n0, args.mask_n);
-        float* v = tot + q * 32;
-        if (n0 + 32 <= args.N) {
-          const float4* sb4 = reinterpret_cast<const float4*>(args.sb + n0);
+        for (int q = 0; q < 4; ++q) {
+          const int64_t n0 = nbase + q * 32;
+          if (n0 >= args.N) break;
+          float* v = tot + q * 32;
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            float4 s4 = __ldg(sb4 + c);
-            v[4 * c + 0] *= rs * s4.x;
-            v[4 * c + 1] *= rs * s4.y;
-            v[4 * c + 2] *= rs * s4.z;
-            v[4 * c + 3] *= rs * s4.w;
+          for (int c = 0; c < 32; ++c) v[c] *= rs;
+          if (lane == 0) bulk_wait_read0();     // staging block free again
+          __syncwarp();
+          float4* row4 = reinterpret_cast<float4*>(stg + lane * 32);
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            row4[c ^ (lane & 7)] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d(&maps.out, smem_u32(stg), (int)n0, (int)mrow0);
+            bulk_commit();
           }
-          if (args.n_contig) {
-            float* p = args.out + (roff | coff);
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-              st_v4(p + 4 * c, make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]), args.streaming);
-          } else {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              float* p = args.out + (roff | coff | tail->tbl[i]);
-              if (args.streaming) __stcs(p, v[i]); else *p = v[i];
-            }
-          }
-          if (args.sum) {
-            // pairwise float partial of the 32 outputs, float64 across chunks
+          if (args.sum && mvalid) {
             float t[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) t[i] = v[i] + v[i + 16];
@@ -364,21 +401,43 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
               for (int i = 0; i < w2; ++i) t[i] += t[i + w2];
             local += (double)t[0];
           }
-        } else {
-          float part = 0.f;
+        }
+        continue;
+      }
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            if (n0 + i < args.N) {
-              float val = v[i] * rs * __ldg(args.sb + n0 + i);
-              float* p = args.out + (roff | coff | tail->tbl[i]);
-              if (args.streaming) __stcs(p, val); else *p = val;
-              part += val;
+      for (int q = 0; q < 4; ++q) {
+        const int64_t n0 = nbase + q * 32;
+        if (n0 >= args.N) break;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) stg[lane * 32 + (c ^ lane)] = tot[q * 32 + c] * rs;
+        __syncwarp();
+        const int64_t n = n0 + lane;
+        const bool nvalid = n < args.N;
+        const float sbl = nvalid ? 1.f : 0.f;
+        const uint64_t coff = args.n_contig ? (uint64_t)n : pdep64((uint64_t)n, args.mask_n);
+#pragma unroll
+        for (int r0 = 0; r0 < 32; r0 += 4) {
+          float a[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = r0 + u;
+            const uint64_t roff_r = __shfl_sync(0xffffffffu, roff, r);
+            const bool mv_r = __shfl_sync(0xffffffffu, mvalid ? 1 : 0, r) != 0;
+            const float val = stg[r * 32 + (lane ^ r)] * sbl;
+            a[u] = 0.f;
+            if (mv_r && nvalid) {
+              float* ptr = args.out + (roff_r | coff);
+              if (args.streaming) __stcs(ptr, val); else *ptr = val;
+              a[u] = val;
             }
           }
-          local += (double)part;
+          if (args.sum) local += (double)((a[0] + a[1]) + (a[2] + a[3]));
         }
+        __syncwarp();
       }
     }
+    if (kTmaStore && lane == 0) bulk_wait0();   // every bulk store has completed
+    __syncwarp();
     if (args.sum) {
       for (int off = 16; off; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
       if (lane == 0) atomicAdd(args.sum, local);
@@ -404,6 +463,19 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
       fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
   });
   return fn;
+}
+
+int make_out_map(CUtensorMap* map, float* base, int64_t rows, int64_t cols) {
+  auto enc = get_encode();
+  if (!enc) return set_error(CUTQC_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(CUTQC_ECUDA, "cuTensorMapEncodeTiled (output) failed (%d)", (int)r);
+  return CUTQC_OK;
 }
 
 int make_map(CUtensorMap* map, const __half* base, int64_t rows, int64_t Kp, int box_rows) {
@@ -453,7 +525,15 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alp
   args.sum = sum;
   args.streaming = streaming;
   args.status = device_status_ptr();
-  if (((uintptr_t)b.scale & 15) != 0) return set_error(CUTQC_EINVAL, "column scales not 16-byte aligned");
+  // bulk-tensor stores when the output is out[m * N + n] with a 16-byte
+  // aligned base and row pitch
+  args.tma_store = 0;
+  if (args.n_contig && args.m_shift >= 0 && mask_n == (((uint64_t)1 << args.m_shift) - 1) &&
+      ((uint64_t)1 << args.m_shift) == (uint64_t)b.rows && (b.rows * 4) % 16 == 0 && ((uintptr_t)out & 15) == 0 &&
+      b.rows <= ((int64_t)1 << 31) && a.rows <= ((int64_t)1 << 31)) {
+    if ((rc = make_out_map(&maps.out, out, a.rows, b.rows))) return rc;
+    args.tma_store = 1;
+  }
   if (args.n_contig && ((uintptr_t)out & 15) != 0) return set_error(CUTQC_EINVAL, "output not 16-byte aligned");
   {
     static std::mutex mu;
@@ -462,12 +542,14 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alp
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(mu);
     if (!done.count(dev)) {
-      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
       done.insert(dev);
     }
   }
   const int grid = (int)std::min<int64_t>(args.num_tiles, (int64_t)sm_count());
-  tc_gemm_kernel<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
+  if (args.tma_store) tc_gemm_kernel<true><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
+  else tc_gemm_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
   CUTQC_LAUNCH_CHECK("tc_gemm_kernel");
   return CUTQC_OK;
 }

@@ -232,6 +232,48 @@ def cutqc_dd_step(subs, active_bits, bin_bit, merged, bins, bin_sum=None, topk=0
     return bins
 
 
+class DDJob(ctypes.Structure):
+    _fields_ = [("level", c_int32), ("depth", c_int32), ("parent", c_int32), ("parent_bin", c_int32),
+                ("n_active", c_int32), ("active", c_int32 * 32), ("zoom_mask", c_uint64 * 2),
+                ("zoom_val", c_uint64 * 2), ("bin_sum", c_double), ("top_idx", c_int32 * 32),
+                ("top_val", c_float * 32), ("bins_offset", c_int64)]
+
+    def zoom(self):
+        z = {}
+        for q in range(128):
+            if (self.zoom_mask[q >> 6] >> (q & 63)) & 1:
+                z[q] = int((self.zoom_val[q >> 6] >> (q & 63)) & 1)
+        return z
+
+
+def cutqc_dd_run_workspace_size(subs, n_qubits, M, T):
+    arr, keep = _subs(subs)
+    n = c_size_t(0)
+    _check(lib().cutqc_dd_run_workspace_size(c_int(len(subs)), arr, c_int(n_qubits), c_int(M), c_int(T), ctypes.byref(n)))
+    return n.value
+
+
+def cutqc_dd_run(subs, attributed, n_qubits, M, R, T, strategy, max_jobs=256, bins=None, ws=None, stream=None):
+    """Algorithm 1 on the device.  strategy 0 = DFS, 1 = BFS.  Returns
+    (list of DDJob, bins tensor); job j's bins are
+    bins[job.bins_offset : job.bins_offset + 2**job.n_active]."""
+    import torch
+    arr, keep = _subs(subs)
+    dev = attributed[0].device
+    if bins is None:
+        bins = torch.empty(max_jobs << min(M, n_qubits), dtype=torch.float32, device=dev)
+    need = cutqc_dd_run_workspace_size(subs, n_qubits, M, T)
+    if ws is None:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    jobs = (DDJob * max_jobs)()
+    nj = c_int(0)
+    ptrs = (c_void_p * len(attributed))(*[t.data_ptr() for t in attributed])
+    _check(lib().cutqc_dd_run(c_int(len(subs)), arr, ptrs, c_int(n_qubits), c_int(M), c_int(R), c_int(T),
+                              c_int(strategy), c_int(max_jobs), jobs, ctypes.byref(nj), _ptr(bins),
+                              c_int64(bins.numel()), _ptr(ws), c_size_t(ws.numel()), _stream(stream)))
+    return [jobs[i] for i in range(nj.value)], bins
+
+
 def declared_symbols(header=HEADER):
     """Function names declared in include/cutqc.h."""
     import re

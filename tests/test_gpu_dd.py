@@ -1,0 +1,110 @@
+"""GPU parity of the dynamic-definition path (merge, bin reconstruction,
+top-T selection, Algorithm 1 end to end) against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cq():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_05836_gb300 import cutqc
+    return cutqc
+
+
+def _setup(cut):
+    import torch
+    from oracle import attribution
+    from workloads.simulate import simulate_variants
+    subs = cut.subcircuits
+    var = [simulate_variants(s) for s in subs]
+    A = [attribution.attribute(v, s.w, s.in_local, s.out_local, s.in_edge, s.out_edge) for s, v in zip(subs, var)]
+    return subs, A, [torch.from_numpy(a.astype(np.float32)).cuda() for a in A]
+
+
+def _cut(kind):
+    from workloads import circuits as C
+    from workloads.cutting import search_cut
+    if kind == "brickwall":
+        return search_cut(C.brickwall(10, 4, 11), 7, 2, restarts=4)
+    if kind == "aqft":
+        return search_cut(C.aqft(12, 2, max_dist=2), 5, 4, restarts=4)
+    return search_cut(C.bv(14, 9), 5, 5, restarts=4)
+
+
+@pytest.mark.parametrize("kind", ["brickwall", "aqft", "bv"])
+def test_merge_matches_oracle(cq, kind):
+    import torch
+    from oracle import dd
+    cut = _cut(kind)
+    subs, A, At = _setup(cut)
+    rng = np.random.default_rng(0)
+    for s, a64, at in zip(subs, A, At):
+        o = s.o
+        for _ in range(3):
+            role = rng.integers(0, 4, size=o)
+            got = cq.cutqc_dd_merge(s, at, role)
+            active = {q for q, r in zip(s.out_qubit, role) if r == 0}
+            zoom = {q: int(r - 2) for q, r in zip(s.out_qubit, role) if r >= 2}
+            ref = dd.merge(a64, s.out_qubit, active, zoom)
+            torch.cuda.synchronize()
+            g = got.cpu().numpy().astype(np.float64)
+            assert g.shape == ref.shape
+            assert np.abs(g - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("strategy", [0, 1], ids=["dfs", "bfs"])
+@pytest.mark.parametrize("kind", ["brickwall", "aqft", "bv"])
+def test_dd_run_matches_oracle(cq, kind, strategy):
+    import torch
+    from oracle import dd
+    cut = _cut(kind)
+    subs, A, At = _setup(cut)
+    n = cut.circuit.n
+    # a BV output is one basis state: its other bins are all zero and their
+    # order is decided by rounding noise, so only the top bin is expanded
+    M, R, T = 4, 6, (1 if kind == "bv" else 3)
+    jobs, bins = cq.cutqc_dd_run(subs, At, n, M, R, T, strategy)
+    torch.cuda.synchronize()
+    ref = dd.run(A, [s.out_qubit for s in subs], [s.edges for s in subs], cut.K, n, M, R, T,
+                 strategy="dfs" if strategy == 0 else "bfs")
+    assert len(jobs) == len(ref)
+    for J, rj in zip(jobs, ref):
+        assert list(J.active[:J.n_active]) == rj["active"]
+        assert J.zoom() == rj["zoom"]
+        b = bins[J.bins_offset:J.bins_offset + (1 << J.n_active)].cpu().numpy().astype(np.float64)
+        assert np.abs(b - rj["bins"]).max() <= 1e-6
+        assert abs(J.bin_sum - rj["bins"].sum()) <= 1e-6
+        # selection: same bins (values may tie within float32 rounding)
+        top = [i for i in J.top_idx[:T] if i >= 0]
+        if rj["top"]:
+            assert len(top) == len(rj["top"])
+            np.testing.assert_allclose(sorted(rj["bins"][top]), sorted(rj["bins"][rj["top"]]), atol=1e-6)
+
+
+def test_dd_bv_finds_hidden_string(cq):
+    """DFS on a Bernstein-Vazirani circuit reaches the single solution state."""
+    from workloads import circuits as C
+    from workloads.cutting import search_cut
+    n = 24
+    c = C.bv(n, 3)
+    cut = search_cut(c, 8, 4, restarts=4)
+    subs, A, At = _setup(cut)
+    M = 6
+    jobs, bins = cq.cutqc_dd_run(subs, At, n, M, math.ceil(n / M), 2, 0)
+    last = jobs[-1]
+    assert last.depth * M + last.n_active == n
+    b = bins[last.bins_offset:last.bins_offset + (1 << last.n_active)].cpu().numpy()
+    top = int(np.argmax(b))
+    bits = last.zoom()
+    for j in range(last.n_active):
+        bits[last.active[j]] = (top >> j) & 1
+    assert [bits[q] for q in range(n - 1)] == c.meta["hidden"] and bits[n - 1] == 1
+    assert abs(b[top] - 1) < 1e-5
