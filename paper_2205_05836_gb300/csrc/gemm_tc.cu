@@ -4,27 +4,32 @@
 // where A = sa * (Ah + Al), B = sb * (Bh + Bl) are the float16 hi/lo splits of
 // the float32 operands (power-of-two scales: one per row of A, one for all of
 // B, see prep_kernel): about 22 significant bits per operand, products exact
-// in the FP32 accumulator.
-// The signed I/X/Y/Z terms of Eq. 1 cancel (sum|terms| is ~10x |P| on the
-// 30-qubit supremacy workload), which is why a single FP16/BF16/TF32 pass is
-// not accurate enough and the split is used.
+// in the FP32 accumulator.  The signed I/X/Y/Z terms of Eq. 1 cancel (sum
+// |terms| is ~10x |P| on the 30-qubit supremacy workload), which is why a
+// single FP16/BF16/TF32 pass is not accurate enough and the split is used.
 //
 // The tensor core rounds its FP32 accumulator toward zero after each MMA,
 // which over a long chain of signed terms leaves a negative bias (about
-// -1.5e-6 in sum p on the 30-qubit workload).  Each 64-wide k-block is
-// therefore accumulated in a fresh TMEM accumulator (a "chunk", 12 MMAs), and
-// the chunks are added in registers with round-to-nearest.
+// -1.5e-6 in sum p on the 30-qubit workload).  Every 64 values of k are
+// therefore accumulated in a fresh TMEM accumulator (a "chunk", 12 MMAs),
+// and the chunks are added in registers with round-to-nearest.
 //
-// Kernel organisation (one CTA per SM, persistent over output tiles):
-//   warp 8       TMA producer: per k-block loads A_hi, A_lo (128 x 64) and
-//                B_hi, B_lo (256 x 64) into a 2-stage 128B-swizzled ring
-//   warp 9       MMA issuer: 3 x 4 tcgen05.mma (M=128, N=256, K=16) per
-//                k-block into one of two 128 x 256 FP32 chunk buffers in TMEM
+// Kernel organisation (one CTA per SM, persistent over 128 x 128 tiles):
+//   warp 8       TMA producer: per 64-wide k-block loads A_hi, A_lo, B_hi,
+//                B_lo (128 x 64 each) into a 2-stage 128B-swizzled ring
+//   warp 9       MMA issuer: 4 x 3 tcgen05.mma (M=128, N=128, K=16) per
+//                k-block (one chunk) into one of four 128 x 128 FP32 chunk
+//                buffers in TMEM (so the MMAs run up to three chunks ahead
+//                of the epilogue)
 //   warps 0-7    epilogue: warp w owns TMEM lanes 32*(w%4).. (tile rows) and
-//                columns 128*(w/4)..+127; adds every chunk into 128 register
-//                totals, then scales and stores the tile to
-//                out[pdep(m, mask_m) | pdep(n, mask_n)] (streaming stores for
-//                the final output), optional FP64 running sum
+//                columns 64*(w/4)..+63; adds every chunk into 64 register
+//                totals, then scales and stores the tile.  Row-major outputs
+//                (out[m * N + n]) go out as 32 x 32 TMA bulk-tensor stores
+//                from a 128B-swizzled staging block per 32 x 32 block (one
+//                block per store, so a warp never waits for its own stores
+//                within a tile); other bit-deposit layouts
+//                (out[pdep(m, mask_m) | pdep(n, mask_n)]) through a staged
+//                transpose and per-element stores.  Optional FP64 sum.
 // Tiles are walked with m fastest so the few B tiles in flight stay in L2.
 // Every barrier wait is bounded in time; on expiry the CTA records
 // CUTQC_ETIMEOUT in the device status word, drains its own copies and MMAs,
@@ -41,19 +46,24 @@ namespace cutqc {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64;               // BK in fp16 elements (128 B)
+constexpr int BM = 128, BN = 128, BK = 64;               // BK in fp16 elements (128-byte rows)
 constexpr int STAGES = 2;
+constexpr int KB_PER_CHUNK = 1;                          // chunk = 64 values of k = 12 MMAs
+constexpr int NBUF = 4;                                  // chunk buffers in TMEM
 constexpr int A_TILE = BM * BK * 2;                      // 16 KiB
-constexpr int B_TILE = BN * BK * 2;                      // 32 KiB
-constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;     // 96 KiB
-constexpr int TMEM_COLS = 512;                           // 2 accumulators x 256 columns
+constexpr int B_TILE = BN * BK * 2;                      // 16 KiB
+constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;     // 64 KiB
+constexpr int TMEM_COLS = NBUF * BN;                     // 512
 constexpr int NUM_THREADS = 320;
 constexpr int EPI_THREADS = 256;
+constexpr int EPI_COLS = 64;                             // columns per epilogue warp
+constexpr int BLK_FLOATS = 32 * 32;                      // one 32 x 32 staging block
+constexpr int STG_BYTES = 8 * (EPI_COLS / 32) * BLK_FLOATS * 4;   // 64 KiB
 constexpr long long kTimeoutCycles = 4000000000LL;       // ~2 s at 2 GHz
 
 struct TcMaps {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
-  CUtensorMap out;   // used when TcArgs::tma_store: 2-D [M][N] float32, 32 x 32 box, 128B swizzle
+  CUtensorMap out;   // row-major output [M][N] float32, 32 x 32 box, 128B swizzle
 };
 
 struct TcArgs {
@@ -70,26 +80,20 @@ struct TcArgs {
   float* out;
   double* sum;
   int streaming;
-  int tma_store;
+  int row_major;      // out[m * N + n]: bulk-tensor stores through maps.out
   int* status;
 };
 
 struct SmemTail {
   uint64_t full[STAGES];
   uint64_t empty[STAGES];
-  uint64_t cfull[2];
-  uint64_t cempty[2];
+  uint64_t cfull[NBUF];
+  uint64_t cempty[NBUF];
   uint64_t fin;
-  uint64_t tbl[32];
   uint32_t tmem_slot;
   int abort_flag;
 };
 
-// one 32 x 32 float32 staging block per epilogue warp (4 KiB, 1024-aligned):
-// XOR-swizzled by row for the transposing store path, 128B-swizzled for the
-// bulk-tensor store path
-constexpr int STG_WARP_FLOATS = 32 * 32;
-constexpr int STG_BYTES = 8 * STG_WARP_FLOATS * 4;
 constexpr size_t SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + STG_BYTES + sizeof(SmemTail);
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
@@ -136,8 +140,9 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 B, 8-row groups 1024 B apart.
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows
+// of 128 B (64 fp16 of k), 8-row groups 1024 B apart.  (TMA moves 128-byte
+// rows at about twice the rate of 64-byte rows, so BK = 64.)
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
@@ -149,7 +154,7 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 }
 
 // Instruction descriptor: kind::f16, A = B = F16, D = F32, both K-major,
-// N = 256, M = 128.
+// N = 128, M = 128.
 constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
                             ((uint32_t)(BM >> 4) << 24);
 
@@ -188,33 +193,11 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t sr
                : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_le1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void st_v4(float* p, float4 v, int streaming) {
-  if (streaming) __stcs(reinterpret_cast<float4*>(p), v);
-  else *reinterpret_cast<float4*>(p) = v;
-}
-
-template <bool kTmaStore>
+template <bool kRowMajor>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
   extern __shared__ uint8_t smem_raw[];
@@ -229,16 +212,13 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
       mbar_init(smem_u32(&tail->full[s]), 1);
       mbar_init(smem_u32(&tail->empty[s]), 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < NBUF; ++a) {
       mbar_init(smem_u32(&tail->cfull[a]), 1);
       mbar_init(smem_u32(&tail->cempty[a]), EPI_THREADS);
     }
     mbar_init(smem_u32(&tail->fin), 1);
     tail->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 1) {
-    tail->tbl[lane] = pdep64((uint64_t)lane, args.mask_n);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tail->tmem_slot)),
@@ -258,9 +238,10 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
   };
 
   if (warp == 8) {
+    // ------------------------------------------------------------ producer
     if (lane == 0) {
-      bool issued[STAGES] = {false, false};
-      uint32_t issued_par[STAGES] = {0, 0};
+      bool issued[STAGES] = {};
+      uint32_t issued_par[STAGES] = {};
       int stage = 0;
       uint32_t phase = 0;
       for (int64_t tile = blockIdx.x; tile < args.num_tiles && !*abort_flag; tile += gridDim.x) {
@@ -284,9 +265,11 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
       }
       // every copy this thread started has landed before the CTA may exit
       for (int s = 0; s < STAGES; ++s)
-        if (issued[s] && !mbar_wait(smem_u32(&tail->full[s]), issued_par[s], nullptr)) record_status(args.status, CUTQC_ETIMEOUT);
+        if (issued[s] && !mbar_wait(smem_u32(&tail->full[s]), issued_par[s], nullptr))
+          record_status(args.status, CUTQC_ETIMEOUT);
     }
   } else if (warp == 9) {
+    // ----------------------------------------------------------- MMA issue
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
@@ -296,9 +279,11 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
       for (int64_t tile = blockIdx.x; tile < args.num_tiles && !*abort_flag; tile += gridDim.x) {
         bool ok = true;
         for (int kb = 0; kb < args.num_kb; ++kb) {
-          // one chunk per k-block: fresh accumulator in chunk buffer `buf`
-          if (!mbar_wait(smem_u32(&tail->cempty[buf]), buf_phase ^ 1u, abort_flag)) { fail(); ok = false; break; }
-          tc_fence_after();
+          const int ks = kb % KB_PER_CHUNK;
+          if (ks == 0) {
+            if (!mbar_wait(smem_u32(&tail->cempty[buf]), buf_phase ^ 1u, abort_flag)) { fail(); ok = false; break; }
+            tc_fence_after();
+          }
           if (!mbar_wait(smem_u32(&tail->full[stage]), phase, abort_flag)) { fail(); ok = false; break; }
           tc_fence_after();
           const uint32_t d = tmem_base + (uint32_t)(buf * BN);
@@ -306,18 +291,20 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
           const uint32_t ah = st, al = st + A_TILE, bh = st + 2 * A_TILE, bl = st + 2 * A_TILE + B_TILE;
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint32_t off = kk * 32;   // 16 fp16 = 32 bytes along K inside the swizzle row
+            const uint32_t off = kk * 32;   // 16 fp16 = 32 bytes along k inside the swizzle row
             const uint64_t dah = sw128_desc(ah + off), dal = sw128_desc(al + off);
             const uint64_t dbh = sw128_desc(bh + off), dbl = sw128_desc(bl + off);
-            umma_f16(d, dah, dbh, kk != 0 ? 1u : 0u);
+            umma_f16(d, dah, dbh, (ks | kk) != 0 ? 1u : 0u);
             umma_f16(d, dah, dbl, 1u);
             umma_f16(d, dal, dbh, 1u);
           }
           any = true;
           umma_commit(smem_u32(&tail->empty[stage]));
-          umma_commit(smem_u32(&tail->cfull[buf]));
+          if (ks == KB_PER_CHUNK - 1 || kb == args.num_kb - 1) {
+            umma_commit(smem_u32(&tail->cfull[buf]));
+            if (++buf == NBUF) { buf = 0; buf_phase ^= 1u; }
+          }
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-          if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
         }
         if (!ok) break;
       }
@@ -328,58 +315,60 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
       }
     }
   } else {
-    // epilogue warps 0..7: TMEM lanes 32*(warp%4).. = tile rows, columns
-    // 128*(warp/4) .. +127
+    // ------------------------------------------------------------ epilogue
+    // warp w: TMEM lanes 32*(w%4).. = tile rows, columns 64*(w/4) .. +63
     const int g = warp & 3, h = warp >> 2;
     int buf = 0;
     uint32_t buf_phase = 0;
     double local = 0.0;
     const int row = g * 32 + lane;
-    float tot[128];
+    const int num_chunks = (args.num_kb + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
+    const float sbg = __ldg(args.sb);
+    float* stg0 = stg_all + warp * (EPI_COLS / 32) * BLK_FLOATS;
+    float tot[EPI_COLS];
     for (int64_t tile = blockIdx.x; tile < args.num_tiles && !*abort_flag; tile += gridDim.x) {
       const int mb = (int)(tile % args.num_m_blk);
       const int nb = (int)(tile / args.num_m_blk);
 #pragma unroll
-      for (int i = 0; i < 128; ++i) tot[i] = 0.f;
+      for (int i = 0; i < EPI_COLS; ++i) tot[i] = 0.f;
       bool ok = true;
-      for (int kb = 0; kb < args.num_kb; ++kb) {
+      for (int ch = 0; ch < num_chunks; ++ch) {
         if (!mbar_wait(smem_u32(&tail->cfull[buf]), buf_phase, abort_flag)) { fail(); ok = false; break; }
         tc_fence_after();
         __syncwarp();
+        uint32_t r0[32], r1[32];
+        const uint32_t taddr = tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(buf * BN + h * EPI_COLS);
+        tmem_ld32(taddr, r0);
+        tmem_ld32(taddr + 32, r1);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          uint32_t r[8];
-          tmem_ld8(tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(buf * BN + h * 128 + q * 8), r);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) tot[q * 8 + i] += __uint_as_float(r[i]);
+        for (int i = 0; i < 32; ++i) {
+          tot[i] += __uint_as_float(r0[i]);
+          tot[32 + i] += __uint_as_float(r1[i]);
         }
         tc_fence_before();
         mbar_arrive(smem_u32(&tail->cempty[buf]));
-        if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
+        if (++buf == NBUF) { buf = 0; buf_phase ^= 1u; }
       }
       if (!ok) break;
-      // store: each 32 x 32 block goes through the warp's padded staging
-      // buffer so that one warp instruction writes one row segment of 32
-      // consecutive outputs (a full 128-byte line in Kronecker order)
       const int64_t m = (int64_t)mb * BM + row;
       const bool mvalid = m < args.M;
-      const float rs = mvalid ? args.alpha * __ldg(args.sa + m) * __ldg(args.sb) : 0.f;
-      const uint64_t roff = mvalid ? (args.m_shift >= 0 ? ((uint64_t)m << args.m_shift) : pdep64((uint64_t)m, args.mask_m)) : 0;
-      const int64_t nbase = (int64_t)nb * BN + h * 128;
-      float* stg = stg_all + warp * STG_WARP_FLOATS;
-      if (kTmaStore) {
-        // rows m..: one 32 x 32 box per block, written by the TMA engine from
-        // a 128B-swizzled staging block (16-byte chunk j of row r sits at
-        // chunk j ^ (r & 7)); rows or columns beyond the output are clipped
+      const float rs = mvalid ? args.alpha * __ldg(args.sa + m) * sbg : 0.f;
+      const int64_t nbase = (int64_t)nb * BN + h * EPI_COLS;
+      if (kRowMajor) {
+        // one 32 x 32 TMA box per block, from its own 128B-swizzled staging
+        // block (16-byte chunk j of row r sits at chunk j ^ (r & 7)); rows or
+        // columns beyond the output are clipped by the tensor map
         const int64_t mrow0 = (int64_t)mb * BM + g * 32;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < EPI_COLS / 32; ++q) {
           const int64_t n0 = nbase + q * 32;
           if (n0 >= args.N) break;
           float* v = tot + q * 32;
 #pragma unroll
           for (int c = 0; c < 32; ++c) v[c] *= rs;
-          if (lane == 0) bulk_wait_read0();     // staging block free again
+          float* stg = stg0 + q * BLK_FLOATS;
+          // this block's previous store (one tile ago) has read the staging
+          if (lane == 0) bulk_wait_read_le1();
           __syncwarp();
           float4* row4 = reinterpret_cast<float4*>(stg + lane * 32);
 #pragma unroll
@@ -402,41 +391,38 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
             local += (double)t[0];
           }
         }
-        continue;
-      }
+      } else {
+        // general bit deposit: each 32 x 32 block goes through the staging
+        // block (XOR-swizzled by row) so that lanes walk the columns of one
+        // row at a time
+        const uint64_t roff = mvalid ? (args.m_shift >= 0 ? ((uint64_t)m << args.m_shift) : pdep64((uint64_t)m, args.mask_m)) : 0;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t n0 = nbase + q * 32;
-        if (n0 >= args.N) break;
+        for (int q = 0; q < EPI_COLS / 32; ++q) {
+          const int64_t n0 = nbase + q * 32;
+          if (n0 >= args.N) break;
+          float* stg = stg0 + q * BLK_FLOATS;
+          __syncwarp();
 #pragma unroll
-        for (int c = 0; c < 32; ++c) stg[lane * 32 + (c ^ lane)] = tot[q * 32 + c] * rs;
-        __syncwarp();
-        const int64_t n = n0 + lane;
-        const bool nvalid = n < args.N;
-        const float sbl = nvalid ? 1.f : 0.f;
-        const uint64_t coff = args.n_contig ? (uint64_t)n : pdep64((uint64_t)n, args.mask_n);
-#pragma unroll
-        for (int r0 = 0; r0 < 32; r0 += 4) {
-          float a[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int r = r0 + u;
+          for (int c = 0; c < 32; ++c) stg[lane * 32 + (c ^ lane)] = tot[q * 32 + c] * rs;
+          __syncwarp();
+          const int64_t n = n0 + lane;
+          const bool nvalid = n < args.N;
+          const uint64_t coff = args.n_contig ? (uint64_t)n : pdep64((uint64_t)n, args.mask_n);
+#pragma unroll 4
+          for (int r = 0; r < 32; ++r) {
             const uint64_t roff_r = __shfl_sync(0xffffffffu, roff, r);
             const bool mv_r = __shfl_sync(0xffffffffu, mvalid ? 1 : 0, r) != 0;
-            const float val = stg[r * 32 + (lane ^ r)] * sbl;
-            a[u] = 0.f;
+            const float val = stg[r * 32 + (lane ^ r)];
             if (mv_r && nvalid) {
               float* ptr = args.out + (roff_r | coff);
               if (args.streaming) __stcs(ptr, val); else *ptr = val;
-              a[u] = val;
+              if (args.sum) local += (double)val;
             }
           }
-          if (args.sum) local += (double)((a[0] + a[1]) + (a[2] + a[3]));
         }
-        __syncwarp();
       }
     }
-    if (kTmaStore && lane == 0) bulk_wait0();   // every bulk store has completed
+    if (kRowMajor && lane == 0) bulk_wait0();   // every bulk store has completed
     __syncwarp();
     if (args.sum) {
       for (int off = 16; off; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
@@ -527,12 +513,12 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alp
   args.status = device_status_ptr();
   // bulk-tensor stores when the output is out[m * N + n] with a 16-byte
   // aligned base and row pitch
-  args.tma_store = 0;
+  args.row_major = 0;
   if (args.n_contig && args.m_shift >= 0 && mask_n == (((uint64_t)1 << args.m_shift) - 1) &&
       ((uint64_t)1 << args.m_shift) == (uint64_t)b.rows && (b.rows * 4) % 16 == 0 && ((uintptr_t)out & 15) == 0 &&
       b.rows <= ((int64_t)1 << 31) && a.rows <= ((int64_t)1 << 31)) {
     if ((rc = make_out_map(&maps.out, out, a.rows, b.rows))) return rc;
-    args.tma_store = 1;
+    args.row_major = 1;
   }
   if (args.n_contig && ((uintptr_t)out & 15) != 0) return set_error(CUTQC_EINVAL, "output not 16-byte aligned");
   {
@@ -548,7 +534,7 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alp
     }
   }
   const int grid = (int)std::min<int64_t>(args.num_tiles, (int64_t)sm_count());
-  if (args.tma_store) tc_gemm_kernel<true><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
+  if (args.row_major) tc_gemm_kernel<true><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
   else tc_gemm_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
   CUTQC_LAUNCH_CHECK("tc_gemm_kernel");
   return CUTQC_OK;
