@@ -115,6 +115,21 @@ int cutqc_attribute_workspace_size(const cutqc_subcircuit* s, size_t* bytes);
 int cutqc_attribute(const cutqc_subcircuit* s, const void* variants_dev, int variants_dtype,
                     float* attributed_dev, void* ws_dev, size_t ws_bytes, void* stream);
 
+/* Attribution that allocates nothing (the paper has no counterpart).  For
+ * callers that cannot allocate device memory during the call (a memory pool
+ * owns the device, the host forbids cudaMalloc after set-up, or an
+ * allocation's implicit synchronisation is not allowed): same inputs, outputs
+ * and results as cutqc_attribute, but the scratch of the two-pass case comes
+ * from a static 32 MiB device array of the library (held on every GPU that
+ * loads it until the process exits).  The first call on a device looks up
+ * that array's address with that device current; make it before any stream
+ * capture.  Calls share the array and it keeps the last call's contents:
+ * calls that can overlap on the GPU race and must be ordered by the caller.
+ * Errors as cutqc_attribute, plus CUTQC_EUNSUPPORTED when the subcircuit
+ * needs more than 32 MiB of scratch (cutqc_attribute_workspace_size).       */
+int cutqc_attribute_noalloc(const cutqc_subcircuit* s, const void* variants_dev, int variants_dtype,
+                            float* attributed_dev, void* stream);
+
 /* --------------------------------------------------------- FD reconstruction
  * Eq. 1 with the 1/2-per-cut normalisation: P = 2^-K sum_e kron_i A_i[:, c_i(e)].
  * The subcircuits (n_sub >= 1, their attributed tensors as produced by

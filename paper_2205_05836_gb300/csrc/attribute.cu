@@ -434,3 +434,70 @@ extern "C" int cutqc_attribute(const cutqc_subcircuit* s, const void* variants_d
     return launch_attr<double>(s, (const double*)variants_dev, attributed_dev, (float*)ws_dev, st);
   return launch_attr<float>(s, (const float*)variants_dev, attributed_dev, (float*)ws_dev, st);
 }
+
+// ------------------------------------------------- attribution, no allocation
+//
+// Some callers cannot allocate device memory at all: code that runs while a
+// memory pool owns the whole device, plugins whose host forbids cudaMalloc
+// between set-up and tear-down, or callers that must not synchronise (a
+// cudaMalloc or cudaFree can synchronise the device).  For them this variant
+// takes its scratch from a fixed array that the library declares at file
+// scope, so the call itself allocates nothing; the caller still owns the
+// variant and attributed tensors.
+//
+// The array is kNoAllocScratchBytes (32 MiB) of device memory on every GPU
+// that loads this library, held until the process exits.  Its device
+// address is looked up once per device (cudaGetSymbolAddress) on the first
+// call made with that device current, so that first call should come before
+// any stream capture.  All calls share the one array and it keeps whatever
+// the last call left there: calls that may overlap on the GPU (different
+// streams, no ordering between them) race on it and must not be issued that
+// way.  Nothing in it needs to start at zero: the pass that writes it covers
+// every element the next pass reads.
+
+namespace cutqc {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+int noalloc_scratch(void** ptr) {
+  static std::mutex mu;
+  static std::vector<void*> addr;       // per device id
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)addr.size() <= dev) addr.resize(dev + 1, nullptr);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-allocation scratch)");
+    addr[dev] = p;
+  }
+  *ptr = addr[dev];
+  return CUTQC_OK;
+}
+
+}  // namespace
+}  // namespace cutqc
+
+extern "C" int cutqc_attribute_noalloc(const cutqc_subcircuit* s, const void* variants_dev, int dtype,
+                                       float* attributed_dev, void* stream) {
+  size_t need = 0;
+  int rc = cutqc_attribute_workspace_size(s, &need);
+  if (rc) return rc;
+  if (!variants_dev || !attributed_dev) return set_error(CUTQC_EINVAL, "null tensor pointer");
+  if (dtype != CUTQC_F64 && dtype != CUTQC_F32) return set_error(CUTQC_EINVAL, "dtype must be CUTQC_F64 or CUTQC_F32");
+  if (need > kNoAllocScratchBytes)
+    return set_error(CUTQC_EUNSUPPORTED,
+                     "this subcircuit needs %zu bytes of scratch; the no-allocation variant has %zu "
+                     "(use cutqc_attribute with a workspace)",
+                     need, kNoAllocScratchBytes);
+  void* scratch = nullptr;
+  if ((rc = noalloc_scratch(&scratch))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == CUTQC_F64)
+    return launch_attr<double>(s, (const double*)variants_dev, attributed_dev, (float*)scratch, st);
+  return launch_attr<float>(s, (const float*)variants_dev, attributed_dev, (float*)scratch, st);
+}

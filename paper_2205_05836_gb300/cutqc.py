@@ -144,6 +144,16 @@ def cutqc_attribute(sub, variants, out=None, ws=None, stream=None):
     return out
 
 
+def cutqc_attribute_noalloc(sub, variants, out, stream=None):
+    """cutqc_attribute without any device allocation: the caller passes the
+    output tensor; the library's static scratch array is used."""
+    import torch
+    d, keep = make_sub(sub)
+    dtype = F64 if variants.dtype == torch.float64 else F32
+    _check(lib().cutqc_attribute_noalloc(ctypes.byref(d), _ptr(variants), c_int(dtype), _ptr(out), _stream(stream)))
+    return out
+
+
 # --------------------------------------------------------------------- FD
 
 def cutqc_fd_shape(subs):
