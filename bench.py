@@ -28,6 +28,16 @@ METRIC = "reconstructed probs/sec (FD) and DD bins/sec at 1 GB300, TV<=1e-6; % o
 WORKLOAD = "fd_two_sub_supremacy30: 5x6 supremacy-family depth 10, K=4, subcircuits 17+17 -> 2^30 probabilities"
 
 
+_T0 = time.perf_counter()
+
+
+def _log(msg):
+    """Progress line on stderr (elapsed seconds, peak host RSS)."""
+    import resource
+    rss = resource.getrusage(resource.RUSAGE_SELF).ru_maxrss / 1024
+    print(f"[bench {time.perf_counter() - _T0:7.1f}s rss {rss:7.0f} MB] {msg}", file=sys.stderr, flush=True)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -202,9 +212,11 @@ def run(args):
     __graft_entry__.build()
     from paper_2205_05836_gb300 import cutqc as cq
     from workloads.configs import fd_two_sub
+    _log("library built")
     w = fd_two_sub()
     subs = w.subcircuits
     var_host = w.variants()
+    _log("variants simulated")
     var = [torch.from_numpy(v).to(dev) for v in var_host]
     kin = [len(s.in_local) for s in subs]
     att = [torch.empty((1 << s.o, 4 ** (len(s.in_local) + len(s.out_local))), dtype=torch.float32, device=dev)
@@ -297,6 +309,11 @@ def run(args):
                 "peak_source": pk["source"] + " (fp16 dense rate = bf16 rate)",
                 "fd_ms": fd_ms, "attribution_ms": att_ms}
     value = ws * n_out / (ms * 1e-3)
+    # library kernels per step: one attribution pass per subcircuit side that
+    # carries cuts (init and/or meas), three operand-prep passes and the
+    # tcgen05 GEMM (the FP64 total's zeroing is a torch fill, not counted)
+    launches_per_step = sum((len(s.in_local) > 0) + (len(s.out_local) > 0) for s in subs) + \
+        (4 if prec == cq.PREC_FP16X3_TC else 3)
 
     # end to end through the C ABI from pinned host buffers
     host_var = [torch.from_numpy(v).pin_memory() for v in var_host]
@@ -334,11 +351,127 @@ def run(args):
             "roofline": roofline, "clocks": clk.summary(),
             "e2e": {"value": ws * n_out / (e2e_ms * 1e-3), "unit": "probs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * (len(subs) + 3)}
+            "gpu_launches": args.steps * launches_per_step}
+    _log("FD step, per-kernel and end-to-end timing done")
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, budget_s=args.ref_budget)
+        _log("cpu baseline done")
+    if rank == 0 and not args.no_extras:
+        del out, fd_ws, graph, g_att, g_fd, host_out, host_var
+        torch.cuda.empty_cache()
+        line["dd_batched"] = dd_extras(dev, cq)
+        _log("DD extras done")
+        line["learned"] = learned_extras(dev, cq)
+        _log("cut-scorer extras done")
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def learned_extras(dev, cq, n_circuits=10000, train_steps=4000, batch=1024):
+    """Cut scorer at scale: training set from seeded random circuits of 20-60
+    qubits (labels: exact contraction cost of candidate cuts), GPU training
+    by the library's kernels, then cut proposal for a 100-qubit BV circuit
+    (subcircuits <= 20 qubits) against the local cut search, and dynamic
+    definition on the proposed cut down to the hidden string."""
+    import math
+    import torch
+    from paper_2205_05836_gb300.scorer import propose_cut
+    from workloads import circuits as C
+    from workloads.cutting import contraction_cost, search_cut
+    from workloads.features import training_set, training_set_parallel
+    from workloads.simulate import simulate_variants
+    t0 = time.perf_counter()
+    x, t, _ = training_set_parallel(n_circuits, 4, seed=0, workers=min(8, os.cpu_count() or 1))
+    gen_s = time.perf_counter() - t0
+    _log(f"training set: {len(t)} samples from {n_circuits} circuits in {gen_s:.1f} s")
+    xv, tv, _ = training_set(200, 8, seed=99)
+    net = cq.MLP(seed=0)
+    X, T = torch.from_numpy(x).to(dev), torch.from_numpy(t).to(dev)
+    net.fit(X, T, steps=20, batch=batch, lr=1e-3, seed=1)       # warm-up
+    net = cq.MLP(seed=0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    net.fit(X, T, steps=train_steps, batch=batch, lr=1e-3, seed=0)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    loss = net.loss.item()
+    pv = net.forward(torch.from_numpy(xv).to(dev)).cpu().numpy()
+    val_mse = float(((pv - tv) ** 2).mean())
+    # inference latency: 4096 candidates in one forward
+    xq = torch.from_numpy(np.ascontiguousarray(np.resize(xv, (4096, xv.shape[1])))).to(dev)
+    for _ in range(3):
+        net.forward(xq)
+    torch.cuda.synchronize()
+    i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    i0.record()
+    for _ in range(20):
+        net.forward(xq)
+    i1.record()
+    torch.cuda.synchronize()
+    infer_ms = i0.elapsed_time(i1) / 20
+
+    _log("scorer trained")
+    n, w_max = 100, 20
+    c = C.bv(n, 5)
+    t0 = time.perf_counter()
+    searched = search_cut(c, w_max, -(-(n + 8) // w_max), restarts=4, seed=5)
+    search_s = time.perf_counter() - t0
+    cut, info = propose_cut(c, w_max, net, n_candidates=4096, n_exact=8, seed=0)
+    subs = cut.subcircuits
+    att = [cq.cutqc_attribute(s, torch.from_numpy(simulate_variants(s)).to(dev)) for s in subs]
+    M = 16
+    R = math.ceil(n / M)
+    cq.cutqc_dd_run(subs, att, n, M, R, 1, 0)        # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    jobs, bins = cq.cutqc_dd_run(subs, att, n, M, R, 1, 0)
+    torch.cuda.synchronize()
+    dd_s = time.perf_counter() - t0
+    last = jobs[-1]
+    b = bins[last.bins_offset:last.bins_offset + (1 << last.n_active)].cpu().numpy()
+    top = int(np.argmax(b))
+    bits = last.zoom()
+    for j in range(last.n_active):
+        bits[last.active[j]] = (top >> j) & 1
+    exact = [bits.get(q, -1) for q in range(n - 1)] == c.meta["hidden"] and bits.get(n - 1) == 1
+    return {"train_circuits": n_circuits, "train_samples": int(len(t)), "train_set_seconds": gen_s,
+            "train_steps": train_steps, "batch": batch, "train_ms": train_ms,
+            "train_samples_per_s": train_steps * batch / (train_ms * 1e-3), "final_loss": loss,
+            "val_mse": val_mse, "val_label_var": float(tv.var()), "infer_4096_ms": infer_ms,
+            "bv100": {"mlp_cut_log2_cost": math.log2(contraction_cost(cut)), "mlp_cut_K": cut.K,
+                      "mlp_seconds": info["seconds"], "feasible_candidates": info["feasible"],
+                      "searched_cut_log2_cost": math.log2(contraction_cost(searched)), "searched_cut_K": searched.K,
+                      "search_seconds": search_s, "dd_recursions": len(jobs), "dd_seconds": dd_s,
+                      "bitstring_exact": bool(exact), "p_top": float(b[top])}}
+
+
+def dd_extras(dev, cq, M=16, R=6, T=4):
+    """Dynamic definition on the three blocked brick-wall circuits (40, 50
+    and 60 qubits, subcircuits <= 15 qubits): Algorithm 1, depth first,
+    16 active qubits per recursion, top-4 bins expanded per level."""
+    import torch
+    from workloads.configs import dd_batched
+    out = []
+    tot_bins, tot_s = 0, 0.0
+    for w in dd_batched():
+        _log(f"DD {w.name}")
+        subs = w.subcircuits
+        att = [cq.cutqc_attribute(s, torch.from_numpy(v).to(dev)) for s, v in zip(subs, w.variants())]
+        cq.cutqc_dd_run(subs, att, w.n, M, R, T, 0, max_jobs=512)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        jobs, bins = cq.cutqc_dd_run(subs, att, w.n, M, R, T, 0, max_jobs=512)
+        torch.cuda.synchronize()
+        s = time.perf_counter() - t0
+        nb = sum(1 << j.n_active for j in jobs)
+        tot_bins += nb
+        tot_s += s
+        out.append({"circuit": w.name, "n": w.n, "subcircuits": len(subs), "K": w.K, "jobs": len(jobs),
+                    "bins": nb, "seconds": s, "root_sum_error": abs(jobs[0].bin_sum - 1.0)})
+    return {"M": M, "R": R, "T": T, "strategy": "dfs", "circuits": out, "bins_per_s": tot_bins / tot_s,
+            "note": "one host-driven launch sequence per recursion; selection read on the host"}
 
 
 def run_profile_case(args):
@@ -370,6 +503,7 @@ def main():
     ap.add_argument("--precision", default="tc", choices=["tc", "simt"])
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the DD and cut-scorer measurements")
     ap.add_argument("--profile-case", action="store_true",
                     help="run the kernels once on a row slice (for ncu) and exit")
     ap.add_argument("--profile-rows", type=int, default=2048)

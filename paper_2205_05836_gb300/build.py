@@ -40,7 +40,7 @@ def build(force=False, verbose=False):
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(HERE, "..", "include", "cutqc.h"))
+    headers += [os.path.join(HERE, "..", "include", h) for h in ("cutqc.h", "cutqc_mlp.h")]
     jobs = []
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")

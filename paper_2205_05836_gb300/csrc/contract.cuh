@@ -85,8 +85,10 @@ struct ContractionPlan {
 // Greedy pairwise plan over the input tensors; every edge must appear in
 // exactly two inputs.
 int plan_contraction(const std::vector<TensorDesc>& inputs, int precision, ContractionPlan* plan);
+// ws_upper_bound: size the workspace as if every operand needed its gather
+// copy, so that the size holds for any output-bit order of the inputs.
 int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precision, int batch,
-                             ContractionPlan* plan);
+                             ContractionPlan* plan, bool ws_upper_bound = false);
 
 // Runs the plan for `batch` independent items: input i of item b at
 // inputs[i] + b * in_bstride[i]; output of item b at out + b * out_bstride;

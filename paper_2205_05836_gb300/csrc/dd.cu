@@ -240,7 +240,8 @@ extern "C" int cutqc_dd_step_workspace_size(int n_sub, const cutqc_subcircuit* s
   if (!bytes) return set_error(CUTQC_EINVAL, "null bytes");
   std::vector<TensorDesc> in;
   int tot = 0;
-  // bin_bit does not change the workspace: use the identity order
+  // the bin order decides which operands need a gather copy: plan with the
+  // identity order and size for the worst case
   std::vector<int32_t> ident;
   for (int i = 0; i < n_sub && active_bits; ++i)
     for (int b = 0; b < active_bits[i]; ++b) ident.push_back((int32_t)ident.size());
@@ -248,7 +249,7 @@ extern "C" int cutqc_dd_step_workspace_size(int n_sub, const cutqc_subcircuit* s
   if (rc) return rc;
   if (n_jobs < 1) return set_error(CUTQC_EINVAL, "n_jobs must be >= 1");
   ContractionPlan plan;
-  if ((rc = plan_contraction_batched(in, CUTQC_PREC_FP32_SIMT, n_jobs, &plan))) return rc;
+  if ((rc = plan_contraction_batched(in, CUTQC_PREC_FP32_SIMT, n_jobs, &plan, true))) return rc;
   *bytes = plan.ws_bytes;
   return CUTQC_OK;
 }

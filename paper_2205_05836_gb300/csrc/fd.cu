@@ -90,7 +90,7 @@ uint64_t digit_mask(const std::vector<int>& all_edges, const std::vector<int>& s
 }  // namespace
 
 int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precision, int batch,
-                             ContractionPlan* plan) {
+                             ContractionPlan* plan, bool ws_upper_bound) {
   if (inputs.empty()) return set_error(CUTQC_EINVAL, "no tensors");
   if (precision != CUTQC_PREC_FP32_SIMT && precision != CUTQC_PREC_FP16X3_TC)
     return set_error(CUTQC_EINVAL, "unknown precision %d", precision);
@@ -214,7 +214,7 @@ int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precisio
     } else {
       st.Kp = st.K;
       for (PlanOperand* op : {&st.opa, &st.opb})
-        if (!op->trivial) op->off32 = take((size_t)op->view.rows() * st.Kp * sizeof(float));
+        if (!op->trivial || ws_upper_bound) op->off32 = take((size_t)op->view.rows() * st.Kp * sizeof(float));
     }
     if (!final_stage) {
       st.result_elems = ((size_t)1 << R.o) * ((size_t)1 << (2 * uni_open.size()));

@@ -14,6 +14,7 @@ from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_int8, c_int32,
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libcutqc.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "cutqc.h")
+HEADERS = [HEADER, os.path.join(os.path.dirname(HERE), "include", "cutqc_mlp.h")]
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 F64, F32 = 0, 1
@@ -284,8 +285,135 @@ def cutqc_dd_run(subs, attributed, n_qubits, M, R, T, strategy, max_jobs=256, bi
     return [jobs[i] for i in range(nj.value)], bins
 
 
-def declared_symbols(header=HEADER):
-    """Function names declared in include/cutqc.h."""
+def declared_symbols(headers=None):
+    """Function names declared in include/*.h."""
     import re
-    text = open(header).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(cutqc_\w+)\s*\(", text, re.M)))
+    names = set()
+    for h in headers or HEADERS:
+        text = open(h).read()
+        names.update(re.findall(r"^\s*(?:int|const char\*)\s+(cutqc_\w+)\s*\(", text, re.M))
+    return sorted(names)
+
+
+# -------------------------------------------------------------------- MLP
+
+class MLP:
+    """Device-resident cut-scoring network: FP32 master parameters, BF16
+    copy, Adam moments; every step runs in the library's kernels."""
+
+    def __init__(self, params=None, device="cuda", seed=0):
+        import torch
+        n = c_int64(0)
+        _check(lib().cutqc_mlp_param_count(ctypes.byref(n)))
+        self.n = n.value
+        self.device = torch.device(device)
+        if params is None:
+            params = init_params(seed)
+        self.p = torch.as_tensor(params, dtype=torch.float32).to(self.device).contiguous()
+        assert self.p.numel() == self.n
+        self.pb = torch.empty(self.n, dtype=torch.bfloat16, device=self.device)
+        self.grad = torch.zeros(self.n, dtype=torch.float32, device=self.device)
+        self.m = torch.zeros_like(self.grad)
+        self.v = torch.zeros_like(self.grad)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self.step = 0
+        self._ws = None
+        _check(lib().cutqc_mlp_sync_bf16(_ptr(self.p), _ptr(self.pb), _stream(None)))
+
+    def _work(self, batch):
+        import torch
+        b = c_size_t(0)
+        _check(lib().cutqc_mlp_workspace_size(c_int(batch), ctypes.byref(b)))
+        if self._ws is None or self._ws.numel() < b.value:
+            self._ws = torch.empty(b.value, dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def _rows(self, x, t=None):
+        import torch
+        if x.dim() != 2 or x.shape[1] != SIZES[0] or x.dtype != torch.float32 or not x.is_contiguous():
+            raise ValueError("x must be a contiguous float32 [batch, 64] device tensor")
+        if t is not None and (t.shape != (x.shape[0],) or t.dtype != torch.float32 or not t.is_contiguous()):
+            raise ValueError("t must be a contiguous float32 [batch] device tensor")
+        return x.shape[0]
+
+    def forward(self, x):
+        import torch
+        B = self._rows(x)
+        y = torch.empty(B, dtype=torch.float32, device=self.device)
+        ws = self._work(B)
+        _check(lib().cutqc_mlp_forward(_ptr(self.p), _ptr(self.pb), _ptr(x), c_int(B), _ptr(y), _ptr(ws),
+                                       c_size_t(ws.numel()), _stream(None)))
+        return y
+
+    def gradients(self, x, t):
+        B = self._rows(x, t)
+        ws = self._work(B)
+        _check(lib().cutqc_mlp_gradients(_ptr(self.p), _ptr(self.pb), _ptr(x), _ptr(t), c_int(B), _ptr(self.grad),
+                                         _ptr(self.loss), _ptr(ws), c_size_t(ws.numel()), _stream(None)))
+        return self.grad, self.loss
+
+    def adam(self, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        """Adam update of the parameters from ``self.grad`` (step >= 1)."""
+        _check(lib().cutqc_mlp_adam(_ptr(self.p), _ptr(self.pb), _ptr(self.grad), _ptr(self.m), _ptr(self.v),
+                                    c_int(step), c_float(lr), c_float(beta1), c_float(beta2), c_float(eps),
+                                    _stream(None)))
+
+    def train_step(self, x, t, lr=1e-3):
+        B = self._rows(x, t)
+        ws = self._work(B)
+        self.step += 1
+        _check(lib().cutqc_mlp_train_step(_ptr(self.p), _ptr(self.pb), _ptr(self.grad), _ptr(self.m), _ptr(self.v),
+                                          c_int(self.step), c_float(lr), _ptr(x), _ptr(t), c_int(B),
+                                          _ptr(self.loss), _ptr(ws), c_size_t(ws.numel()), _stream(None)))
+        return self.loss
+
+
+    def fit(self, x, t, steps, batch=512, lr=1e-3, seed=0):
+        """``steps`` Adam steps over contiguous minibatches of (x, t), both
+        device tensors; the rows are put in a seeded random order once per
+        pass over the data.  Returns the device loss tensor of the last step."""
+        import numpy as np
+        import torch
+        N = x.shape[0]
+        batch = min(batch, N)
+        rng = np.random.default_rng(seed)
+        done = 0
+        while done < steps:
+            perm = torch.from_numpy(rng.permutation(N)).to(x.device)
+            xp, tp = x[perm].contiguous(), t[perm].contiguous()
+            for b0 in range(0, N - batch + 1, batch):
+                if done == steps:
+                    break
+                self.train_step(xp[b0:b0 + batch], tp[b0:b0 + batch], lr)
+                done += 1
+        return self.loss
+
+    def params_numpy(self):
+        """FP32 master parameters split into (W1, b1, W2, b2, W3, b3)."""
+        return split_params(self.p.cpu().numpy())
+
+
+SIZES = (64, 256, 256, 1)
+
+
+def split_params(flat):
+    """Flat parameter vector -> [W1, b1, W2, b2, W3, b3] ([in][out] weights)."""
+    out, o = [], 0
+    for a, b in zip(SIZES[:-1], SIZES[1:]):
+        out.append(flat[o:o + a * b].reshape(a, b))
+        o += a * b
+        out.append(flat[o:o + b])
+        o += b
+    assert o == flat.size
+    return out
+
+
+def init_params(seed=0):
+    """He-style initial weights (numpy, float32), layout of cutqc_mlp.h."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    parts = []
+    for a, b in ((64, 256), (256, 256), (256, 1)):
+        parts.append((rng.standard_normal((a, b)) * np.sqrt(2.0 / a)).astype(np.float32).reshape(-1))
+        parts.append(np.zeros(b, dtype=np.float32))
+    return np.concatenate(parts)

@@ -108,3 +108,32 @@ def test_dd_bv_finds_hidden_string(cq):
         bits[last.active[j]] = (top >> j) & 1
     assert [bits[q] for q in range(n - 1)] == c.meta["hidden"] and bits[n - 1] == 1
     assert abs(b[top] - 1) < 1e-5
+
+
+@pytest.mark.parametrize("kind", ["aqft", "bv"])
+def test_dd_step_any_bin_order(cq, kind):
+    """One reconstruction with every output qubit active and the bin bits in
+    a random order: bins[sum_q b_q 2^perm[q]] = p(b), with the workspace the
+    size query reports."""
+    import torch
+    from oracle import fd
+    cut = _cut(kind)
+    subs, A, At = _setup(cut)
+    n = cut.circuit.n
+    p = fd.kron_to_original(fd.reconstruct_kron(A, [s.edges for s in subs], cut.K), [s.out_qubit for s in subs])
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        perm = rng.permutation(n)
+        merged = [cq.cutqc_dd_merge(s, at, np.zeros(s.o, dtype=np.int8)) for s, at in zip(subs, At)]
+        active_bits = [s.o for s in subs]
+        bin_bit = [int(perm[q]) for s in subs for q in s.out_qubit]
+        bins = torch.empty((1, 1 << n), dtype=torch.float32, device="cuda")
+        total = torch.zeros(1, dtype=torch.float64, device="cuda")
+        cq.cutqc_dd_step(subs, active_bits, bin_bit, merged, bins, bin_sum=total)
+        torch.cuda.synchronize()
+        idx = np.zeros(1 << n, dtype=np.int64)
+        for q in range(n):
+            idx |= ((np.arange(1 << n) >> q) & 1) << perm[q]
+        got = bins[0].cpu().numpy().astype(np.float64)[idx]
+        assert np.abs(got - p).max() <= 1e-6
+        assert abs(total.item() - 1.0) <= 1e-6

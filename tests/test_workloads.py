@@ -72,3 +72,46 @@ def test_benchmark_shapes():
     for w in configs.dd_batched():
         assert all(s.w <= 15 for s in w.subcircuits) and len(w.subcircuits) in (4, 5)
         assert all(1 <= s.k_in + s.k_out <= 3 for s in w.subcircuits)
+
+
+def test_candidate_structure_matches_built_cut():
+    """The array-derived widths, output counts, cut count and exact cost of
+    candidate clusterings equal those of the subcircuits build_cut makes."""
+    from workloads.cutting import Dag, build_cut, contraction_cost
+    from workloads.features import CandidateSet, candidates
+    rng = np.random.default_rng(1)
+    checked = 0
+    for _ in range(30):
+        n = int(rng.integers(12, 40))
+        c = C.random_family_circuit(rng, n)
+        dag = Dag(c)
+        w_max = int(rng.integers(max(4, n // 6), max(5, n // 2) + 1))
+        A = candidates(dag, w_max, 12, rng)
+        cs = CandidateSet(dag, A, w_max)
+        for i in range(len(A)):
+            cut = build_cut(c, A[i], w_max=w_max)
+            feasible = all(s.w <= w_max for s in cut.subcircuits)
+            assert feasible == bool(cs.feasible[i])
+            if not feasible:
+                continue
+            checked += 1
+            assert sorted(s.w for s in cut.subcircuits) == sorted(cs.w[i][cs.used[i]].tolist())
+            assert sorted(s.o for s in cut.subcircuits) == sorted(cs.o[i][cs.used[i]].tolist())
+            assert cut.K == cs.K[i]
+            assert contraction_cost(cut) == cs.exact_cost(i)
+    assert checked >= 50
+
+
+def test_features_shape_and_permutation_invariance():
+    """64 finite features; relabelling the clusters changes none of them."""
+    from workloads.cutting import Dag
+    from workloads.features import N_FEATURES, CandidateSet, candidates
+    rng = np.random.default_rng(2)
+    c = C.brickwall(30, 6, 4)
+    dag = Dag(c)
+    A = candidates(dag, 12, 64, rng)
+    f = CandidateSet(dag, A, 12).features()
+    assert f.shape == (64, N_FEATURES) and np.isfinite(f).all()
+    perm = rng.permutation(7)
+    f2 = CandidateSet(dag, perm[A], 12).features()
+    np.testing.assert_array_equal(f, f2)
