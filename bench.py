@@ -297,16 +297,23 @@ def run(args):
     alg_flops = 2.0 * M * N * Kg                    # Eq. 1, one pass
     exec_flops = 3 * alg_flops if prec == cq.PREC_FP16X3_TC else alg_flops
     pk = peaks()
-    achieved = alg_flops / (fd_ms * 1e-3) / 1e12
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                "frac": achieved / pk["bf16_tflops"],
+    # algorithmic bytes of one FD launch sequence: read both attributed
+    # tensors once, write 4 B per probability.  At the peaks these bytes take
+    # longer than the algorithmic flops, so the bound is HBM.
+    alg_bytes = 4.0 * n_out + sum(a.numel() * 4 for a in att)
+    achieved = alg_bytes / (fd_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"],
                 "traffic": profiled_traffic("paper_2205_05836_gb300/csrc/gemm_tc.cu", "profiles/tc_gemm_fd_two_sub.md"),
                 "kernel": "FD contraction (operand prep + tcgen05 GEMM), one launch sequence",
+                "algorithmic_bytes": alg_bytes, "algorithmic_flops": alg_flops,
+                "hbm_bound_ms": alg_bytes / (pk["hbm_gbs"] * 1e9) * 1e3,
+                "tensor_bound_ms_1pass": alg_flops / (pk["bf16_tflops"] * 1e12) * 1e3,
+                "tensor_bound_ms_executed": exec_flops / (pk["bf16_tflops"] * 1e12) * 1e3,
+                "algorithmic_tflops": alg_flops / (fd_ms * 1e-3) / 1e12,
                 "executed_tflops": exec_flops / (fd_ms * 1e-3) / 1e12,
-                "executed_frac": exec_flops / (fd_ms * 1e-3) / 1e12 / pk["bf16_tflops"],
-                "output_gbs": 4.0 * n_out / (fd_ms * 1e-3) / 1e9,
-                "output_frac_of_hbm": 4.0 * n_out / (fd_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
-                "peak_source": pk["source"] + " (fp16 dense rate = bf16 rate)",
+                "executed_frac_of_bf16_peak": exec_flops / (fd_ms * 1e-3) / 1e12 / pk["bf16_tflops"],
+                "peak_source": pk["source"] + " (copy bandwidth; fp16 dense rate = bf16 rate)",
                 "fd_ms": fd_ms, "attribution_ms": att_ms}
     value = ws * n_out / (ms * 1e-3)
     # library kernels per step: one attribution pass per subcircuit side that
@@ -359,6 +366,9 @@ def run(args):
     if rank == 0 and not args.no_extras:
         del out, fd_ws, graph, g_att, g_fd, host_out, host_var
         torch.cuda.empty_cache()
+        line["fd_chain"] = fd_chain_extras(dev, cq)
+        torch.cuda.empty_cache()
+        _log("FD chain extras done")
         line["dd_batched"] = dd_extras(dev, cq)
         _log("DD extras done")
         line["learned"] = learned_extras(dev, cq)
@@ -447,10 +457,72 @@ def learned_extras(dev, cq, n_circuits=10000, train_steps=4000, batch=1024):
                       "bitstring_exact": bool(exact), "p_top": float(b[top])}}
 
 
+def fd_chain_extras(dev, cq, steps=10, warmup=3):
+    """The 32-qubit AQFT chain (4 subcircuits of 11 qubits, K = 12, 2^32
+    float32 outputs = 16 GiB): attribution of the four subcircuits, then the
+    pairwise contraction chain, tensor-core path, timed as one CUDA graph;
+    the FP32 CUDA-core path timed the same way for the speed-up."""
+    import torch
+    from workloads.configs import fd_chain
+    w = fd_chain()
+    subs = w.subcircuits
+    var = [torch.from_numpy(v).to(dev) for v in w.variants()]
+    att = [cq.cutqc_attribute(s, v) for s, v in zip(subs, var)]
+    n_out = 1 << w.n
+    out = torch.empty(n_out, dtype=torch.float32, device=dev)
+    total = torch.zeros(1, dtype=torch.float64, device=dev)
+    res = {"workload": "fd_chain_aqft32: 32-qubit AQFT (phases to distance 4), 4 subcircuits of 11 qubits, K=12",
+           "n_qubits": w.n, "cuts": w.K}
+    stream = torch.cuda.current_stream(dev)
+    for name, prec in (("tc", cq.PREC_FP16X3_TC), ("simt", cq.PREC_FP32_SIMT)):
+        fws = torch.empty(max(1, cq.cutqc_reconstruct_fd_workspace_size(subs, prec)), dtype=torch.uint8, device=dev)
+
+        def rec():
+            total.zero_()
+            cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_KRON, prec, out=out, sum_out=total, ws=fws)
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                rec()
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            rec()
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = steps if name == "tc" else 3
+        e0.record(stream)
+        for _ in range(k):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name + "_ms"] = e0.elapsed_time(e1) / k
+        res[name + "_sum_p_error"] = abs(total.item() - 1.0)
+        del g, fws
+    pk = peaks()
+    alg_bytes = 4.0 * n_out + sum(a.numel() * 4 for a in att)
+    # final stage: rows 2^14 x cols 2^18 x 4^4 shared cut digits; the two
+    # intermediate stages add ~1% more
+    from workloads.cutting import contraction_plan
+    _, alg_flops = contraction_plan([s.o for s in subs], [set(s.edges) for s in subs])
+    ms = res["tc_ms"]
+    res.update({"probs_per_s": n_out / (ms * 1e-3), "speedup_tc_over_simt": res["simt_ms"] / ms,
+                "roofline": {"bound": "hbm", "achieved": alg_bytes / (ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
+                             "unit": "GB/s", "frac": alg_bytes / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                             "hbm_bound_ms": alg_bytes / (pk["hbm_gbs"] * 1e9) * 1e3,
+                             "tensor_bound_ms_executed": 3 * alg_flops / (pk["bf16_tflops"] * 1e12) * 1e3,
+                             "algorithmic_flops": alg_flops}})
+    return res
+
+
 def dd_extras(dev, cq, M=16, R=6, T=4):
     """Dynamic definition on the three blocked brick-wall circuits (40, 50
-    and 60 qubits, subcircuits <= 15 qubits): Algorithm 1, depth first,
-    16 active qubits per recursion, top-4 bins expanded per level."""
+    and 60 qubits, subcircuits <= 15 qubits): Algorithm 1 level by level
+    (breadth first), 16 active qubits per recursion, the top-4 bins of each
+    level expanded in the next, 6 levels (1 + 4 * 5 = 21 jobs per circuit)."""
     import torch
     from workloads.configs import dd_batched
     out = []
@@ -459,10 +531,10 @@ def dd_extras(dev, cq, M=16, R=6, T=4):
         _log(f"DD {w.name}")
         subs = w.subcircuits
         att = [cq.cutqc_attribute(s, torch.from_numpy(v).to(dev)) for s, v in zip(subs, w.variants())]
-        cq.cutqc_dd_run(subs, att, w.n, M, R, T, 0, max_jobs=512)
+        cq.cutqc_dd_run(subs, att, w.n, M, R, T, 1, max_jobs=512)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        jobs, bins = cq.cutqc_dd_run(subs, att, w.n, M, R, T, 0, max_jobs=512)
+        jobs, bins = cq.cutqc_dd_run(subs, att, w.n, M, R, T, 1, max_jobs=512)
         torch.cuda.synchronize()
         s = time.perf_counter() - t0
         nb = sum(1 << j.n_active for j in jobs)
@@ -470,7 +542,7 @@ def dd_extras(dev, cq, M=16, R=6, T=4):
         tot_s += s
         out.append({"circuit": w.name, "n": w.n, "subcircuits": len(subs), "K": w.K, "jobs": len(jobs),
                     "bins": nb, "seconds": s, "root_sum_error": abs(jobs[0].bin_sum - 1.0)})
-    return {"M": M, "R": R, "T": T, "strategy": "dfs", "circuits": out, "bins_per_s": tot_bins / tot_s,
+    return {"M": M, "R": R, "T": T, "strategy": "bfs", "circuits": out, "bins_per_s": tot_bins / tot_s,
             "note": "one host-driven launch sequence per recursion; selection read on the host"}
 
 

@@ -145,3 +145,38 @@ def test_fd_two_subcircuit_30q_full_size(cq):
     diff = (simt - out).abs().sum().item() * 0.5
     assert diff <= 2 * TV_GATE
     assert cq.cutqc_device_status() == 0
+
+
+def test_fd_chain_32q_full_size(cq):
+    """32-qubit AQFT chain (4 subcircuits, K = 12, 2^32 outputs = 16 GiB) on
+    the tensor-core path, in both output orders: sum p against 1, and 2^14
+    seeded uniformly sampled outputs against the FP64 oracle (max error, and
+    the total variation they estimate)."""
+    import torch
+    from oracle import fd
+    from workloads.configs import fd_chain
+    w = fd_chain()
+    subs = w.subcircuits
+    var = w.variants()
+    A64 = _oracle_att(subs, var)
+    att = _gpu_att(cq, subs, var)
+    edges = [s.edges for s in subs]
+    rng = np.random.default_rng(2024)
+    idx = np.unique(rng.integers(0, 1 << w.n, size=1 << 14))
+    for order in (0, 1):
+        total = torch.zeros(1, dtype=torch.float64, device="cuda")
+        out, _ = cq.cutqc_reconstruct_fd(subs, att, order, 1, sum_out=total)
+        torch.cuda.synchronize()
+        assert out.numel() == 1 << 32
+        assert abs(total.item() - 1.0) <= 1e-6
+        got = out[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+        del out
+        torch.cuda.empty_cache()
+        parts = fd.split_kron_index(idx, [s.o for s in subs]) if order == 0 else \
+            fd.split_original_index(idx, [s.out_qubit for s in subs])
+        ref = fd.entries(A64, edges, w.K, parts)
+        err = np.abs(got - ref)
+        assert err.max() <= 1e-6, err.max()
+        tv_est = 0.5 * (1 << w.n) * err.mean()
+        assert tv_est <= TV_GATE, tv_est
+    assert cq.cutqc_device_status() == 0
