@@ -107,6 +107,10 @@ struct TcOperand {
   const float* scale;
   int64_t rows;
 };
+// Pairs of SMs (tcgen05 cta_group::2) with A resident, for Kp <= 256.
+bool tc_pair_supported(int64_t Kp);
+int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
+                        uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st);
 int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
                    uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st);
 

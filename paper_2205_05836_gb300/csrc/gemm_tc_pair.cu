@@ -1,0 +1,539 @@
+// Tensor-core contraction for Eq. 1 on pairs of SMs (tcgen05 cta_group::2).
+//
+// Same arithmetic as tc_gemm_kernel (FP16 hi/lo split operands, three
+// products, one fresh TMEM accumulator per 64 values of k added in registers
+// with round-to-nearest, power-of-two row / operand scales), for K <= 256
+// (four 64-wide k-blocks), organised to move fewer operand bytes per output:
+//
+// * a cluster of two CTAs on two SMs computes 256 x 128 output tiles with
+//   one MMA stream (M = 256, N = 128, K = 16 per instruction): CTA r holds
+//   A rows r*128 .. +127 and B rows r*64 .. +63 of the tile, the tensor core
+//   reads both halves of B from both shared memories, and each CTA's tensor
+//   memory receives its own 128 rows x 128 columns;
+// * A stays resident: a pair takes a work item (one 256-row block of A and a
+//   run of consecutive 128-column tiles), loads its A rows once (hi and lo,
+//   all k, up to 128 KiB per CTA) and streams only B (16 KiB per CTA per
+//   k-block), so a CTA moves 1 byte of operands per byte of output instead of
+//   4 for a 128 x 128 tile that streams both operands.
+//
+// Roles (both CTAs): warp 8 lane 0 loads (A once per item, B per k-block);
+// warp 9 lane 0 of CTA 0 issues the MMAs; warps 0-7 drain the chunks, scale
+// and store their CTA's rows exactly as tc_gemm_kernel does.  The loads of
+// both CTAs complete on CTA 0's barriers (it waits for both halves); MMA
+// completion is multicast to the barriers of both CTAs; epilogue warps of
+// both CTAs release a chunk buffer on CTA 0's barrier.  Every wait is bounded;
+// on expiry a CTA records CUTQC_ETIMEOUT, raises its abort flag and falls
+// through to the common exit (a cluster barrier, then tensor memory is freed).
+#include "internal.cuh"
+#include "contract.cuh"
+#include "tc_ptx.cuh"
+
+#include <algorithm>
+#include <mutex>
+#include <set>
+
+namespace cutqc {
+
+namespace {
+
+using namespace tc;
+
+constexpr int BM = 128;                                  // A rows per CTA (256 per pair)
+constexpr int BN = 128;                                  // output columns per tile
+constexpr int BNH = BN / 2;                              // B rows per CTA
+constexpr int BK = 64;                                   // k per block (128-byte rows)
+constexpr int MAX_KB = 4;                                // resident A: k <= 256
+constexpr int STAGES = 4;
+constexpr int NBUF = 4;                                  // chunk buffers in TMEM
+constexpr int A_KB_BYTES = BM * BK * 2;                  // 16 KiB: one of hi / lo, one k-block
+constexpr int A_BYTES = MAX_KB * 2 * A_KB_BYTES;         // 128 KiB
+constexpr int B_HALF = BNH * BK * 2;                     // 8 KiB
+constexpr int STAGE_BYTES = 2 * B_HALF;                  // 16 KiB: B hi + lo, one k-block
+constexpr int TMEM_COLS = NBUF * BN;                     // 512
+constexpr int NUM_THREADS = 320;
+constexpr int EPI_WARPS = 8;
+constexpr int EPI_COLS = 64;                             // columns per epilogue warp
+constexpr int BLK_FLOATS = 32 * 32;                      // one 32 x 32 staging block
+constexpr int STG_BYTES = EPI_WARPS * BLK_FLOATS * 4;    // 32 KiB: one block per warp
+
+struct PairMaps {
+  CUtensorMap a_hi, a_lo;   // [rows][Kp] fp16, box 64 x 128
+  CUtensorMap b_hi, b_lo;   // [rows][Kp] fp16, box 64 x 64
+  CUtensorMap out;          // row-major float32 [M][N], box 32 x 32, 128B swizzle
+};
+
+struct PairArgs {
+  const float* sa;
+  const float* sb;
+  int64_t M, N;
+  int num_kb;
+  int num_mp;           // 256-row blocks of A
+  int64_t num_nt;       // 128-column tiles
+  int64_t tiles_per_item;
+  int64_t num_items;
+  float alpha;
+  uint64_t mask_m, mask_n;
+  int n_contig;
+  int m_shift;
+  float* out;
+  double* sum;
+  int streaming;
+  int* status;
+};
+
+struct Tail {
+  uint64_t full[STAGES];     // CTA 0: both CTAs' B halves of a stage landed
+  uint64_t empty[STAGES];    // each CTA: its stage may be refilled
+  uint64_t cfull[NBUF];      // each CTA: chunk buffer holds a finished chunk
+  uint64_t cempty[NBUF];     // CTA 0: both CTAs' epilogues read the buffer
+  uint64_t afull;            // CTA 0: both CTAs' A rows landed
+  uint64_t aempty;           // each CTA: A may be reloaded
+  uint64_t fin;              // CTA 0: every MMA finished
+  uint32_t tmem_slot;
+  int abort_flag;
+};
+
+constexpr size_t SMEM_BYTES = 1024 + A_BYTES + STAGES * STAGE_BYTES + STG_BYTES + sizeof(Tail);
+static_assert(SMEM_BYTES <= 232448, "shared memory budget");
+
+// kind::f16, A = B = F16, D = F32, both K-major, N = 128, M = 256.
+constexpr uint32_t kIdescPair = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+
+__device__ __forceinline__ uint32_t cta_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// address of the same shared variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Arrive on a barrier of another CTA of the cluster.  Default (CTA-scope
+// release) semantics: the only thing published is that this warp's tensor
+// memory reads finished, which tcgen05.wait::ld and the tcgen05 fence before
+// it already order; a cluster-scope release would add a full memory fence
+// per chunk.
+__device__ __forceinline__ void remote_arrive(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+// TMA load into this CTA's shared memory, completing on an mbarrier that may
+// sit in the peer CTA (a shared::cluster address)
+__device__ __forceinline__ void tma_load_pair(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                              uint32_t cluster_bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(cluster_bar)
+      : "memory");
+}
+__device__ __forceinline__ void umma_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(kIdescPair), "r"(accum)
+      : "memory");
+}
+// arrive (once) on the barrier at this offset in every CTA of `mask` when
+// all tcgen05 operations issued so far by this thread have completed
+__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+      ::"r"(bar), "h"(mask)
+      : "memory");
+}
+
+template <bool kRowMajor>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
+tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* a_smem = smem;
+  uint8_t* b_smem = smem + A_BYTES;
+  float* stg_all = reinterpret_cast<float*>(smem + A_BYTES + STAGES * STAGE_BYTES);
+  Tail* tail = reinterpret_cast<Tail*>(smem + A_BYTES + STAGES * STAGE_BYTES + STG_BYTES);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t rank = cta_rank();
+  const int64_t pair = blockIdx.x >> 1;
+  const int64_t num_pairs = gridDim.x >> 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&tail->full[s]), 1);
+      mbar_init(smem_u32(&tail->empty[s]), 1);
+    }
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(smem_u32(&tail->cfull[b]), 1);
+      mbar_init(smem_u32(&tail->cempty[b]), 2 * EPI_WARPS);
+    }
+    mbar_init(smem_u32(&tail->afull), 1);
+    mbar_init(smem_u32(&tail->aempty), 1);
+    mbar_init(smem_u32(&tail->fin), 1);
+    tail->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    // one warp of each CTA of the pair allocates, collectively
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tail->tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();           // both CTAs' barriers are initialised before any remote use
+  tc_fence_after();
+  const uint32_t tmem_base = tail->tmem_slot;
+  volatile int* abort_flag = &tail->abort_flag;
+  auto fail = [&]() {
+    *abort_flag = 1;
+    record_status(args.status, CUTQC_ETIMEOUT);
+  };
+
+  if (warp == 8) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      const uint32_t lead_afull = map_to_rank(smem_u32(&tail->afull), 0);
+      const uint32_t a_bytes_pair = (uint32_t)(2 * args.num_kb * 2 * A_KB_BYTES);
+      bool a_issued = false, issued[STAGES] = {};
+      uint32_t a_par = 0, issued_par[STAGES] = {};
+      uint32_t aphase = 0;
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t item = pair; item < args.num_items && ok && !*abort_flag; item += num_pairs) {
+        const int mp = (int)(item % args.num_mp);
+        const int64_t t0 = (item / args.num_mp) * args.tiles_per_item;
+        const int64_t t1 = t0 + args.tiles_per_item < args.num_nt ? t0 + args.tiles_per_item : args.num_nt;
+        // CTA 1's rows may lie wholly beyond M; it then loads rows from 0
+        // instead (every load stays a real box; those rows are never stored)
+        int arow = mp * 2 * BM + (int)rank * BM;
+        if (arow >= args.M) arow = 0;
+        // A rows of this item, once
+        if (!mbar_wait(smem_u32(&tail->aempty), aphase ^ 1u, abort_flag)) { fail(); ok = false; break; }
+        if (rank == 0) mbar_expect_tx(smem_u32(&tail->afull), a_bytes_pair);
+        for (int kb = 0; kb < args.num_kb; ++kb) {
+          uint8_t* a = a_smem + kb * 2 * A_KB_BYTES;
+          tma_load_pair(smem_u32(a), &maps.a_hi, kb * BK, arow, lead_afull);
+          tma_load_pair(smem_u32(a + A_KB_BYTES), &maps.a_lo, kb * BK, arow, lead_afull);
+        }
+        a_issued = true;
+        a_par = aphase;
+        aphase ^= 1u;
+        // B halves, k-block by k-block
+        for (int64_t nt = t0; nt < t1 && ok; ++nt) {
+          int brow = (int)(nt * BN) + (int)rank * BNH;
+          if (brow >= args.N) brow = 0;     // columns beyond N are never stored
+          for (int kb = 0; kb < args.num_kb; ++kb) {
+            if (!mbar_wait(smem_u32(&tail->empty[stage]), phase ^ 1u, abort_flag)) { fail(); ok = false; break; }
+            uint8_t* st = b_smem + stage * STAGE_BYTES;
+            const uint32_t lead_full = map_to_rank(smem_u32(&tail->full[stage]), 0);
+            if (rank == 0) mbar_expect_tx(smem_u32(&tail->full[stage]), 2 * STAGE_BYTES);
+            tma_load_pair(smem_u32(st), &maps.b_hi, kb * BK, brow, lead_full);
+            tma_load_pair(smem_u32(st + B_HALF), &maps.b_lo, kb * BK, brow, lead_full);
+            issued[stage] = true;
+            issued_par[stage] = phase;
+            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+          }
+        }
+      }
+      // Every copy this CTA started completes on CTA 0's barriers, which
+      // this thread cannot wait on; wait instead until the MMAs that read
+      // them have finished (each stage's and A's last use) before exiting.
+      for (int s = 0; s < STAGES; ++s)
+        if (issued[s] && !mbar_wait(smem_u32(&tail->empty[s]), issued_par[s], nullptr))
+          record_status(args.status, CUTQC_ETIMEOUT);
+      if (a_issued && !mbar_wait(smem_u32(&tail->aempty), a_par, nullptr)) record_status(args.status, CUTQC_ETIMEOUT);
+    }
+  } else if (warp == 9) {
+    // ----------------------------------------------------------- MMA issue
+    if (lane == 0 && rank == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int buf = 0;
+      uint32_t buf_phase = 0;
+      uint32_t aphase = 0;
+      bool any = false, ok = true;
+      for (int64_t item = pair; item < args.num_items && ok && !*abort_flag; item += num_pairs) {
+        const int64_t t0 = (item / args.num_mp) * args.tiles_per_item;
+        const int64_t t1 = t0 + args.tiles_per_item < args.num_nt ? t0 + args.tiles_per_item : args.num_nt;
+        if (!mbar_wait(smem_u32(&tail->afull), aphase, abort_flag)) { fail(); ok = false; break; }
+        aphase ^= 1u;
+        tc_fence_after();
+        for (int64_t nt = t0; nt < t1 && ok; ++nt) {
+          for (int kb = 0; kb < args.num_kb; ++kb) {
+            if (!mbar_wait(smem_u32(&tail->cempty[buf]), buf_phase ^ 1u, abort_flag)) { fail(); ok = false; break; }
+            tc_fence_after();
+            if (!mbar_wait(smem_u32(&tail->full[stage]), phase, abort_flag)) { fail(); ok = false; break; }
+            tc_fence_after();
+            const uint32_t d = tmem_base + (uint32_t)(buf * BN);
+            const uint32_t ah = smem_u32(a_smem + kb * 2 * A_KB_BYTES), al = ah + A_KB_BYTES;
+            const uint32_t bh = smem_u32(b_smem + stage * STAGE_BYTES), bl = bh + B_HALF;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint32_t off = kk * 32;   // 16 fp16 = 32 bytes along k inside the swizzle row
+              const uint64_t dah = sw128_desc(ah + off), dal = sw128_desc(al + off);
+              const uint64_t dbh = sw128_desc(bh + off), dbl = sw128_desc(bl + off);
+              umma_pair(d, dah, dbh, kk != 0 ? 1u : 0u);
+              umma_pair(d, dah, dbl, 1u);
+              umma_pair(d, dal, dbh, 1u);
+            }
+            any = true;
+            umma_commit_mc(smem_u32(&tail->empty[stage]), 0x3);
+            umma_commit_mc(smem_u32(&tail->cfull[buf]), 0x3);
+            if (++buf == NBUF) { buf = 0; buf_phase ^= 1u; }
+            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+          }
+        }
+        if (ok) umma_commit_mc(smem_u32(&tail->aempty), 0x3);   // A may be replaced
+      }
+      if (any) {
+        umma_commit_mc(smem_u32(&tail->fin), 0x1);
+        if (!mbar_wait(smem_u32(&tail->fin), 0, nullptr)) record_status(args.status, CUTQC_ETIMEOUT);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    // warp w: TMEM lanes 32*(w%4).. = tile rows, columns 64*(w/4) .. +63
+    const int g = warp & 3, h = warp >> 2;
+    int buf = 0;
+    uint32_t buf_phase = 0;
+    double local = 0.0;
+    const float sbg = __ldg(args.sb);
+    float* stg = stg_all + warp * BLK_FLOATS;
+    float tot[EPI_COLS];
+    bool ok = true;
+    for (int64_t item = pair; item < args.num_items && ok && !*abort_flag; item += num_pairs) {
+      const int mp = (int)(item % args.num_mp);
+      const int64_t t0 = (item / args.num_mp) * args.tiles_per_item;
+      const int64_t t1 = t0 + args.tiles_per_item < args.num_nt ? t0 + args.tiles_per_item : args.num_nt;
+      const int64_t mrow0 = (int64_t)mp * 2 * BM + (int64_t)rank * BM + g * 32;
+      const int64_t m = mrow0 + lane;
+      const bool mvalid = m < args.M;
+      const bool any_row = mrow0 < args.M;
+      for (int64_t nt = t0; nt < t1 && ok; ++nt) {
+#pragma unroll
+        for (int i = 0; i < EPI_COLS; ++i) tot[i] = 0.f;
+        for (int ch = 0; ch < args.num_kb; ++ch) {
+          if (!mbar_wait(smem_u32(&tail->cfull[buf]), buf_phase, abort_flag)) { fail(); ok = false; break; }
+          tc_fence_after();
+          __syncwarp();
+          uint32_t r0[32], r1[32];
+          const uint32_t taddr = tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(buf * BN + h * EPI_COLS);
+          tmem_ld32(taddr, r0);
+          tmem_ld32(taddr + 32, r1);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            tot[i] += __uint_as_float(r0[i]);
+            tot[32 + i] += __uint_as_float(r1[i]);
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) remote_arrive(map_to_rank(smem_u32(&tail->cempty[buf]), 0));
+          if (++buf == NBUF) { buf = 0; buf_phase ^= 1u; }
+        }
+        if (!ok) break;
+        const float rs = mvalid ? args.alpha * __ldg(args.sa + m) * sbg : 0.f;
+        const int64_t nbase = nt * BN + h * EPI_COLS;
+        if (kRowMajor) {
+          // 32 x 32 TMA boxes from this warp's 128B-swizzled staging block
+          // (16-byte chunk j of row r at chunk j ^ (r & 7)); rows or columns
+          // beyond the output are clipped by the tensor map
+#pragma unroll
+          for (int q = 0; q < EPI_COLS / 32; ++q) {
+            const int64_t n0 = nbase + q * 32;
+            if (n0 >= args.N) break;
+            float* v = tot + q * 32;
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v[c] *= rs;
+            // the previous store from this staging block has read it
+            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            __syncwarp();
+            float4* row4 = reinterpret_cast<float4*>(stg + lane * 32);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              row4[c ^ (lane & 7)] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0 && any_row) {
+              tma_store_2d(&maps.out, smem_u32(stg), (int)n0, (int)mrow0);
+              bulk_commit();
+            }
+            if (args.sum && mvalid) {
+              float t[16];
+#pragma unroll
+              for (int i = 0; i < 16; ++i) t[i] = v[i] + v[i + 16];
+#pragma unroll
+              for (int w2 = 8; w2; w2 >>= 1)
+#pragma unroll
+                for (int i = 0; i < w2; ++i) t[i] += t[i + w2];
+              local += (double)t[0];
+            }
+          }
+        } else {
+          // general bit deposit through the staging block (XOR-swizzled by
+          // row) so that lanes walk the columns of one row at a time
+          const uint64_t roff =
+              mvalid ? (args.m_shift >= 0 ? ((uint64_t)m << args.m_shift) : pdep64((uint64_t)m, args.mask_m)) : 0;
+#pragma unroll
+          for (int q = 0; q < EPI_COLS / 32; ++q) {
+            const int64_t n0 = nbase + q * 32;
+            if (n0 >= args.N) break;
+            __syncwarp();
+#pragma unroll
+            for (int c = 0; c < 32; ++c) stg[lane * 32 + (c ^ lane)] = tot[q * 32 + c] * rs;
+            __syncwarp();
+            const int64_t n = n0 + lane;
+            const bool nvalid = n < args.N;
+            const uint64_t coff = args.n_contig ? (uint64_t)n : pdep64((uint64_t)n, args.mask_n);
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r) {
+              const uint64_t roff_r = __shfl_sync(0xffffffffu, roff, r);
+              const bool mv_r = __shfl_sync(0xffffffffu, mvalid ? 1 : 0, r) != 0;
+              const float val = stg[r * 32 + (lane ^ r)];
+              if (mv_r && nvalid) {
+                float* ptr = args.out + (roff_r | coff);
+                if (args.streaming) __stcs(ptr, val); else *ptr = val;
+                if (args.sum) local += (double)val;
+              }
+            }
+          }
+        }
+      }
+    }
+    if (kRowMajor && lane == 0) bulk_wait0();   // every bulk store has completed
+    __syncwarp();
+    if (args.sum) {
+      for (int off = 16; off; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+      if (lane == 0) atomicAdd(args.sum, local);
+    }
+  }
+
+  // Both CTAs reach this point only after their roles ended: CTA 0's MMAs
+  // have completed, every chunk was read, every copy landed.
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+int make_map(CUtensorMap* map, const __half* base, int64_t rows, int64_t Kp, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return set_error(CUTQC_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  if (((uintptr_t)base & 15) != 0) return set_error(CUTQC_EINVAL, "operand not 16-byte aligned");
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * sizeof(__half)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(CUTQC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return CUTQC_OK;
+}
+
+int make_out_map(CUtensorMap* map, float* base, int64_t rows, int64_t cols) {
+  auto enc = get_encode();
+  if (!enc) return set_error(CUTQC_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(CUTQC_ECUDA, "cuTensorMapEncodeTiled (output) failed (%d)", (int)r);
+  return CUTQC_OK;
+}
+
+// Tiles per work item: the fewest tile slots on the busiest pair, counting
+// an A load as about one tile of time.
+int64_t pick_tiles_per_item(int64_t num_mp, int64_t num_nt, int64_t pairs) {
+  int64_t best_t = 1;
+  double best = 1e300;
+  for (int64_t t = 4; t <= 64; ++t) {
+    const int64_t items = num_mp * ((num_nt + t - 1) / t);
+    const int64_t per_pair = (items + pairs - 1) / pairs;
+    const double cost = (double)per_pair * ((double)std::min(t, num_nt) + 1.0);
+    if (cost < best) { best = cost; best_t = t; }
+  }
+  return std::min(best_t, num_nt);
+}
+
+}  // namespace
+
+bool tc_pair_supported(int64_t Kp) { return Kp > 0 && Kp % BK == 0 && Kp / BK <= MAX_KB; }
+
+int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
+                        uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st) {
+  if (a.rows <= 0 || b.rows <= 0) return CUTQC_OK;
+  if (!tc_pair_supported(Kp)) return set_error(CUTQC_EINVAL, "paired tensor-core K must be 64..256, a multiple of 64");
+  if (a.rows >= ((int64_t)1 << 30) || b.rows >= ((int64_t)1 << 30)) return set_error(CUTQC_EUNSUPPORTED, "too many rows");
+  PairMaps maps;
+  int rc;
+  if ((rc = make_map(&maps.a_hi, a.hi, a.rows, Kp, BM))) return rc;
+  if ((rc = make_map(&maps.a_lo, a.lo, a.rows, Kp, BM))) return rc;
+  if ((rc = make_map(&maps.b_hi, b.hi, b.rows, Kp, BNH))) return rc;
+  if ((rc = make_map(&maps.b_lo, b.lo, b.rows, Kp, BNH))) return rc;
+  PairArgs args{};
+  args.sa = a.scale;
+  args.sb = b.scale;
+  args.M = a.rows;
+  args.N = b.rows;
+  args.num_kb = (int)(Kp / BK);
+  const int64_t num_mp = (a.rows + 2 * BM - 1) / (2 * BM);
+  args.num_mp = (int)num_mp;
+  args.num_nt = (b.rows + BN - 1) / BN;
+  const int64_t pairs_avail = std::max(1, sm_count() / 2);
+  args.tiles_per_item = pick_tiles_per_item(num_mp, args.num_nt, pairs_avail);
+  args.num_items = num_mp * ((args.num_nt + args.tiles_per_item - 1) / args.tiles_per_item);
+  args.alpha = alpha;
+  args.mask_m = mask_m;
+  args.mask_n = mask_n;
+  args.n_contig = mask_is_low(mask_n) ? 1 : 0;
+  args.m_shift = mask_contig_shift(mask_m);
+  args.out = out;
+  args.sum = sum;
+  args.streaming = streaming;
+  args.status = device_status_ptr();
+  // bulk-tensor stores when the output is out[m * N + n] with a 16-byte
+  // aligned base and row pitch
+  bool row_major = false;
+  if (args.n_contig && args.m_shift >= 0 && mask_n == (((uint64_t)1 << args.m_shift) - 1) &&
+      ((uint64_t)1 << args.m_shift) == (uint64_t)b.rows && (b.rows * 4) % 16 == 0 && ((uintptr_t)out & 15) == 0) {
+    if ((rc = make_out_map(&maps.out, out, a.rows, b.rows))) return rc;
+    row_major = true;
+  }
+  if (args.n_contig && ((uintptr_t)out & 15) != 0) return set_error(CUTQC_EINVAL, "output not 16-byte aligned");
+  {
+    static std::mutex mu;
+    static std::set<int> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done.count(dev)) {
+      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_pair_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)SMEM_BYTES));
+      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_pair_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)SMEM_BYTES));
+      done.insert(dev);
+    }
+  }
+  const int64_t pairs = std::min<int64_t>(args.num_items, pairs_avail);
+  const int grid = (int)(2 * pairs);
+  if (row_major) tc_pair_gemm_kernel<true><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
+  else tc_pair_gemm_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
+  CUTQC_LAUNCH_CHECK("tc_pair_gemm_kernel");
+  return CUTQC_OK;
+}
+
+}  // namespace cutqc
