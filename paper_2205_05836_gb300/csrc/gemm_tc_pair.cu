@@ -11,19 +11,29 @@
 //   reads both halves of B from both shared memories, and each CTA's tensor
 //   memory receives its own 128 rows x 128 columns;
 // * A stays resident: a pair takes a work item (one 256-row block of A and a
-//   run of consecutive 128-column tiles), loads its A rows once (hi and lo,
-//   all k, up to 128 KiB per CTA) and streams only B (16 KiB per CTA per
-//   k-block), so a CTA moves 1 byte of operands per byte of output instead of
-//   4 for a 128 x 128 tile that streams both operands.
+//   run of consecutive 128-column tiles) and keeps the CTA's A rows for all
+//   k: A hi in tensor memory (written by the epilogue warps, read by two of
+//   the three products), A lo in shared memory (one TMA load per item).
+//   Only B streams (16 KiB per CTA per k-block, 5 stages), so a CTA moves 1
+//   byte of operands per byte of output (4 for a 128 x 128 tile that streams
+//   both operands).
+// * one thread cannot issue N = 128 pair MMAs as fast as the tensor core
+//   runs them, so two threads issue alternate chunks;
+// * three 128-column accumulator buffers let the MMAs run two chunks ahead
+//   of the epilogue.
 //
-// Roles (both CTAs): warp 8 lane 0 loads (A once per item, B per k-block);
-// warp 9 lane 0 of CTA 0 issues the MMAs; warps 0-7 drain the chunks, scale
-// and store their CTA's rows exactly as tc_gemm_kernel does.  The loads of
-// both CTAs complete on CTA 0's barriers (it waits for both halves); MMA
-// completion is multicast to the barriers of both CTAs; epilogue warps of
-// both CTAs release a chunk buffer on CTA 0's barrier.  Every wait is bounded;
-// on expiry a CTA records CUTQC_ETIMEOUT, raises its abort flag and falls
-// through to the common exit (a cluster barrier, then tensor memory is freed).
+// Tensor memory per CTA (512 columns): A hi [0, 128) (two fp16 values of k
+// per 32-bit column), chunk accumulators at 128, 256, 384.
+//
+// Roles (both CTAs): warp 8 lane 0 loads B per k-block; lane 0 of warps 9
+// and 10 of CTA 0 issue the MMAs (alternate chunks); warps 0-7 write A hi to
+// tensor memory and load A lo at the start of an item, then drain the
+// chunks, scale and store their CTA's rows exactly as tc_gemm_kernel does.  The loads of both CTAs complete on CTA 0's
+// barriers (it waits for both halves); MMA completion is multicast to the
+// barriers of both CTAs; epilogue warps of both CTAs report A written and
+// chunk buffers read on CTA 0's barriers.  Every wait is bounded; on expiry
+// a CTA records CUTQC_ETIMEOUT, raises its abort flag and falls through to
+// the common exit (a cluster barrier, then tensor memory is freed).
 #include "internal.cuh"
 #include "contract.cuh"
 #include "tc_ptx.cuh"
@@ -43,26 +53,31 @@ constexpr int BN = 128;                                  // output columns per t
 constexpr int BNH = BN / 2;                              // B rows per CTA
 constexpr int BK = 64;                                   // k per block (128-byte rows)
 constexpr int MAX_KB = 4;                                // resident A: k <= 256
-constexpr int STAGES = 4;
-constexpr int NBUF = 4;                                  // chunk buffers in TMEM
-constexpr int A_KB_BYTES = BM * BK * 2;                  // 16 KiB: one of hi / lo, one k-block
-constexpr int A_BYTES = MAX_KB * 2 * A_KB_BYTES;         // 128 KiB
+constexpr int STAGES = 5;
+constexpr int NBUF = 3;                                  // chunk buffers in TMEM
+constexpr int A_COLS = MAX_KB * BK / 2;                  // 128 TMEM columns of A hi
+constexpr int ACC_COL0 = A_COLS;                         // first accumulator column
+constexpr int A_KB_BYTES = BM * BK * 2;                  // 16 KiB: A lo, one k-block
+constexpr int ALO_BYTES = MAX_KB * A_KB_BYTES;           // 64 KiB
 constexpr int B_HALF = BNH * BK * 2;                     // 8 KiB
 constexpr int STAGE_BYTES = 2 * B_HALF;                  // 16 KiB: B hi + lo, one k-block
-constexpr int TMEM_COLS = NBUF * BN;                     // 512
-constexpr int NUM_THREADS = 320;
+constexpr int TMEM_COLS = 512;
+static_assert(ACC_COL0 + NBUF * BN <= TMEM_COLS, "tensor memory budget");
+constexpr int NUM_THREADS = 352;
 constexpr int EPI_WARPS = 8;
 constexpr int EPI_COLS = 64;                             // columns per epilogue warp
 constexpr int BLK_FLOATS = 32 * 32;                      // one 32 x 32 staging block
-constexpr int STG_BYTES = EPI_WARPS * BLK_FLOATS * 4;    // 32 KiB: one block per warp
+constexpr int STG_BYTES = EPI_WARPS * (EPI_COLS / 32) * BLK_FLOATS * 4;   // 64 KiB
 
 struct PairMaps {
-  CUtensorMap a_hi, a_lo;   // [rows][Kp] fp16, box 64 x 128
+  CUtensorMap a_lo;         // [rows][Kp] fp16, box 64 x 128
   CUtensorMap b_hi, b_lo;   // [rows][Kp] fp16, box 64 x 64
   CUtensorMap out;          // row-major float32 [M][N], box 32 x 32, 128B swizzle
 };
 
 struct PairArgs {
+  const __half* a_hi;   // [M][Kp]
+  int64_t Kp;
   const float* sa;
   const float* sb;
   int64_t M, N;
@@ -86,14 +101,14 @@ struct Tail {
   uint64_t empty[STAGES];    // each CTA: its stage may be refilled
   uint64_t cfull[NBUF];      // each CTA: chunk buffer holds a finished chunk
   uint64_t cempty[NBUF];     // CTA 0: both CTAs' epilogues read the buffer
-  uint64_t afull;            // CTA 0: both CTAs' A rows landed
-  uint64_t aempty;           // each CTA: A may be reloaded
-  uint64_t fin;              // CTA 0: every MMA finished
+  uint64_t afull;            // CTA 0: both CTAs wrote A hi to TMEM and their A lo landed
+  uint64_t aempty;           // each CTA: both issuers are done with A
+  uint64_t fin[2];           // CTA 0: every MMA of issuer j finished
   uint32_t tmem_slot;
   int abort_flag;
 };
 
-constexpr size_t SMEM_BYTES = 1024 + A_BYTES + STAGES * STAGE_BYTES + STG_BYTES + sizeof(Tail);
+constexpr size_t SMEM_BYTES = 1024 + ALO_BYTES + STAGES * STAGE_BYTES + STG_BYTES + sizeof(Tail);
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
 // kind::f16, A = B = F16, D = F32, both K-major, N = 128, M = 256.
@@ -132,13 +147,40 @@ __device__ __forceinline__ void tma_load_pair(uint32_t dst, const CUtensorMap* m
       ::"r"(dst), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(cluster_bar)
       : "memory");
 }
-__device__ __forceinline__ void umma_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+// D (TMEM) (+)= A (shared memory, both CTAs' rows) x B (shared memory, both CTAs' halves)
+__device__ __forceinline__ void umma_pair_ss(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
       ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(kIdescPair), "r"(accum)
       : "memory");
+}
+// D (TMEM) (+)= A (TMEM, both CTAs' rows) x B (shared memory, both CTAs' halves)
+__device__ __forceinline__ void umma_pair_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+      ::"r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(kIdescPair), "r"(accum)
+      : "memory");
+}
+// 32 lanes x 32 columns of 32 bits from registers (lane = thread)
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+      ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+        "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+        "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+// Arrive on CTA 0's barrier after writing tensor memory that CTA 0's MMAs
+// read: cluster-scope release (once per work item).
+__device__ __forceinline__ void remote_arrive_release_cluster(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
 }
 // arrive (once) on the barrier at this offset in every CTA of `mask` when
 // all tcgen05 operations issued so far by this thread have completed
@@ -154,10 +196,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t* a_smem = smem;
-  uint8_t* b_smem = smem + A_BYTES;
-  float* stg_all = reinterpret_cast<float*>(smem + A_BYTES + STAGES * STAGE_BYTES);
-  Tail* tail = reinterpret_cast<Tail*>(smem + A_BYTES + STAGES * STAGE_BYTES + STG_BYTES);
+  uint8_t* alo_smem = smem;
+  uint8_t* b_smem = smem + ALO_BYTES;
+  float* stg_all = reinterpret_cast<float*>(smem + ALO_BYTES + STAGES * STAGE_BYTES);
+  Tail* tail = reinterpret_cast<Tail*>(smem + ALO_BYTES + STAGES * STAGE_BYTES + STG_BYTES);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const uint32_t rank = cta_rank();
@@ -173,9 +215,10 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
       mbar_init(smem_u32(&tail->cfull[b]), 1);
       mbar_init(smem_u32(&tail->cempty[b]), 2 * EPI_WARPS);
     }
-    mbar_init(smem_u32(&tail->afull), 1);
-    mbar_init(smem_u32(&tail->aempty), 1);
-    mbar_init(smem_u32(&tail->fin), 1);
+    mbar_init(smem_u32(&tail->afull), 2 * EPI_WARPS);
+    mbar_init(smem_u32(&tail->aempty), 2);
+    mbar_init(smem_u32(&tail->fin[0]), 1);
+    mbar_init(smem_u32(&tail->fin[1]), 1);
     tail->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -200,34 +243,14 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
   if (warp == 8) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      const uint32_t lead_afull = map_to_rank(smem_u32(&tail->afull), 0);
-      const uint32_t a_bytes_pair = (uint32_t)(2 * args.num_kb * 2 * A_KB_BYTES);
-      bool a_issued = false, issued[STAGES] = {};
-      uint32_t a_par = 0, issued_par[STAGES] = {};
-      uint32_t aphase = 0;
+      bool issued[STAGES] = {};
+      uint32_t issued_par[STAGES] = {};
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
       for (int64_t item = pair; item < args.num_items && ok && !*abort_flag; item += num_pairs) {
-        const int mp = (int)(item % args.num_mp);
         const int64_t t0 = (item / args.num_mp) * args.tiles_per_item;
         const int64_t t1 = t0 + args.tiles_per_item < args.num_nt ? t0 + args.tiles_per_item : args.num_nt;
-        // CTA 1's rows may lie wholly beyond M; it then loads rows from 0
-        // instead (every load stays a real box; those rows are never stored)
-        int arow = mp * 2 * BM + (int)rank * BM;
-        if (arow >= args.M) arow = 0;
-        // A rows of this item, once
-        if (!mbar_wait(smem_u32(&tail->aempty), aphase ^ 1u, abort_flag)) { fail(); ok = false; break; }
-        if (rank == 0) mbar_expect_tx(smem_u32(&tail->afull), a_bytes_pair);
-        for (int kb = 0; kb < args.num_kb; ++kb) {
-          uint8_t* a = a_smem + kb * 2 * A_KB_BYTES;
-          tma_load_pair(smem_u32(a), &maps.a_hi, kb * BK, arow, lead_afull);
-          tma_load_pair(smem_u32(a + A_KB_BYTES), &maps.a_lo, kb * BK, arow, lead_afull);
-        }
-        a_issued = true;
-        a_par = aphase;
-        aphase ^= 1u;
-        // B halves, k-block by k-block
         for (int64_t nt = t0; nt < t1 && ok; ++nt) {
           int brow = (int)(nt * BN) + (int)rank * BNH;
           if (brow >= args.N) brow = 0;     // columns beyond N are never stored
@@ -246,21 +269,21 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
       }
       // Every copy this CTA started completes on CTA 0's barriers, which
       // this thread cannot wait on; wait instead until the MMAs that read
-      // them have finished (each stage's and A's last use) before exiting.
+      // them have finished (each stage's last use) before exiting.
       for (int s = 0; s < STAGES; ++s)
         if (issued[s] && !mbar_wait(smem_u32(&tail->empty[s]), issued_par[s], nullptr))
           record_status(args.status, CUTQC_ETIMEOUT);
-      if (a_issued && !mbar_wait(smem_u32(&tail->aempty), a_par, nullptr)) record_status(args.status, CUTQC_ETIMEOUT);
     }
-  } else if (warp == 9) {
+  } else if (warp == 9 || warp == 10) {
     // ----------------------------------------------------------- MMA issue
+    // Two issuing threads: chunk c (one k-block of one tile, counted over
+    // the whole kernel) is issued by thread c % 2 into accumulator buffer
+    // c % NBUF from stage c % STAGES; each thread commits what it issued.
+    const int j = warp - 9;
     if (lane == 0 && rank == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      int buf = 0;
-      uint32_t buf_phase = 0;
       uint32_t aphase = 0;
-      bool any = false, ok = true;
+      int64_t c = 0;
+      bool ok = true;
       for (int64_t item = pair; item < args.num_items && ok && !*abort_flag; item += num_pairs) {
         const int64_t t0 = (item / args.num_mp) * args.tiles_per_item;
         const int64_t t1 = t0 + args.tiles_per_item < args.num_nt ? t0 + args.tiles_per_item : args.num_nt;
@@ -268,46 +291,54 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
         aphase ^= 1u;
         tc_fence_after();
         for (int64_t nt = t0; nt < t1 && ok; ++nt) {
-          for (int kb = 0; kb < args.num_kb; ++kb) {
+          for (int kb = 0; kb < args.num_kb; ++kb, ++c) {
+            if ((int)(c & 1) != j) continue;
+            const int stage = (int)(c % STAGES);
+            const uint32_t phase = (uint32_t)((c / STAGES) & 1);
+            const int buf = (int)(c % NBUF);
+            const uint32_t buf_phase = (uint32_t)((c / NBUF) & 1);
             if (!mbar_wait(smem_u32(&tail->cempty[buf]), buf_phase ^ 1u, abort_flag)) { fail(); ok = false; break; }
             tc_fence_after();
             if (!mbar_wait(smem_u32(&tail->full[stage]), phase, abort_flag)) { fail(); ok = false; break; }
             tc_fence_after();
-            const uint32_t d = tmem_base + (uint32_t)(buf * BN);
-            const uint32_t ah = smem_u32(a_smem + kb * 2 * A_KB_BYTES), al = ah + A_KB_BYTES;
+            const uint32_t d = tmem_base + (uint32_t)(ACC_COL0 + buf * BN);
+            const uint32_t ah = tmem_base + (uint32_t)(kb * (BK / 2));
+            const uint32_t al = smem_u32(alo_smem + kb * A_KB_BYTES);
             const uint32_t bh = smem_u32(b_smem + stage * STAGE_BYTES), bl = bh + B_HALF;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-              const uint32_t off = kk * 32;   // 16 fp16 = 32 bytes along k inside the swizzle row
-              const uint64_t dah = sw128_desc(ah + off), dal = sw128_desc(al + off);
+              // 16 values of k: 8 TMEM columns of A hi, 32 bytes inside the
+              // swizzle rows of A lo and B
+              const uint32_t ta = kk * 8, off = kk * 32;
               const uint64_t dbh = sw128_desc(bh + off), dbl = sw128_desc(bl + off);
-              umma_pair(d, dah, dbh, kk != 0 ? 1u : 0u);
-              umma_pair(d, dah, dbl, 1u);
-              umma_pair(d, dal, dbh, 1u);
+              umma_pair_ts(d, ah + ta, dbh, kk != 0 ? 1u : 0u);
+              umma_pair_ts(d, ah + ta, dbl, 1u);
+              umma_pair_ss(d, sw128_desc(al + off), dbh, 1u);
             }
-            any = true;
             umma_commit_mc(smem_u32(&tail->empty[stage]), 0x3);
             umma_commit_mc(smem_u32(&tail->cfull[buf]), 0x3);
-            if (++buf == NBUF) { buf = 0; buf_phase ^= 1u; }
-            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
           }
         }
-        if (ok) umma_commit_mc(smem_u32(&tail->aempty), 0x3);   // A may be replaced
+        if (ok) umma_commit_mc(smem_u32(&tail->aempty), 0x3);   // this issuer is done with A
       }
-      if (any) {
-        umma_commit_mc(smem_u32(&tail->fin), 0x1);
-        if (!mbar_wait(smem_u32(&tail->fin), 0, nullptr)) record_status(args.status, CUTQC_ETIMEOUT);
-      }
+      // all MMAs this thread issued complete before tensor memory is freed
+      umma_commit_mc(smem_u32(&tail->fin[j]), 0x1);
+      if (!mbar_wait(smem_u32(&tail->fin[j]), 0, nullptr)) record_status(args.status, CUTQC_ETIMEOUT);
     }
   } else {
     // ------------------------------------------------------------ epilogue
     // warp w: TMEM lanes 32*(w%4).. = tile rows, columns 64*(w/4) .. +63
+    // At the start of an item, warp w also writes A hi rows 32*(w%4) .. +31
+    // of the CTA's block, k-blocks kb with kb % 2 == w / 4, to tensor memory;
+    // warp 0 lane 0 loads the CTA's A lo rows by TMA.
     const int g = warp & 3, h = warp >> 2;
     int buf = 0;
     uint32_t buf_phase = 0;
+    uint32_t aphase = 0;
     double local = 0.0;
     const float sbg = __ldg(args.sb);
-    float* stg = stg_all + warp * BLK_FLOATS;
+    float* stg0 = stg_all + warp * (EPI_COLS / 32) * BLK_FLOATS;
+    const uint32_t lead_afull = map_to_rank(smem_u32(&tail->afull), 0);
     float tot[EPI_COLS];
     bool ok = true;
     for (int64_t item = pair; item < args.num_items && ok && !*abort_flag; item += num_pairs) {
@@ -318,6 +349,45 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
       const int64_t m = mrow0 + lane;
       const bool mvalid = m < args.M;
       const bool any_row = mrow0 < args.M;
+      // ---- A rows of this item into tensor memory, once the previous
+      // item's MMAs are done with the old ones
+      if (!mbar_wait(smem_u32(&tail->aempty), aphase ^ 1u, abort_flag)) { fail(); ok = false; break; }
+      aphase ^= 1u;
+      tc_fence_after();
+      if (warp == 0 && lane == 0) {
+        // A lo rows of this CTA (CTA 1's rows may lie wholly beyond M: it then
+        // loads rows from 0, which are never stored)
+        int arow = mp * 2 * BM + (int)rank * BM;
+        if (arow >= args.M) arow = 0;
+        for (int kb = 0; kb < args.num_kb; ++kb)
+          tma_load_pair(smem_u32(alo_smem + kb * A_KB_BYTES), &maps.a_lo, kb * BK, arow, lead_afull);
+      }
+      {
+        const uint4* row = reinterpret_cast<const uint4*>(args.a_hi + (mvalid ? m : 0) * args.Kp);
+        const uint32_t tbase = tmem_base + ((uint32_t)(g * 32) << 16);
+        for (int kb = h; kb < args.num_kb; kb += 2) {
+          uint32_t r[32];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            uint4 v = mvalid ? __ldg(row + kb * 8 + q) : make_uint4(0, 0, 0, 0);
+            r[4 * q] = v.x;
+            r[4 * q + 1] = v.y;
+            r[4 * q + 2] = v.z;
+            r[4 * q + 3] = v.w;
+          }
+          tmem_st32(tbase + (uint32_t)(kb * (BK / 2)), r);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        // CTA 0's warp 0 arrives with the byte count of both CTAs' A lo loads
+        if (rank == 0 && warp == 0)
+          mbar_expect_tx(smem_u32(&tail->afull), (uint32_t)(2 * args.num_kb * A_KB_BYTES));
+        else
+          remote_arrive_release_cluster(lead_afull);
+      }
       for (int64_t nt = t0; nt < t1 && ok; ++nt) {
 #pragma unroll
         for (int i = 0; i < EPI_COLS; ++i) tot[i] = 0.f;
@@ -326,7 +396,8 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
           tc_fence_after();
           __syncwarp();
           uint32_t r0[32], r1[32];
-          const uint32_t taddr = tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(buf * BN + h * EPI_COLS);
+          const uint32_t taddr =
+              tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(ACC_COL0 + buf * BN + h * EPI_COLS);
           tmem_ld32(taddr, r0);
           tmem_ld32(taddr + 32, r1);
 #pragma unroll
@@ -353,8 +424,9 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
             float* v = tot + q * 32;
 #pragma unroll
             for (int c = 0; c < 32; ++c) v[c] *= rs;
-            // the previous store from this staging block has read it
-            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            float* stg = stg0 + q * BLK_FLOATS;
+            // this block's previous store (one tile ago) has read the staging
+            if (lane == 0) bulk_wait_read_le1();
             __syncwarp();
             float4* row4 = reinterpret_cast<float4*>(stg + lane * 32);
 #pragma unroll
@@ -386,6 +458,7 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
           for (int q = 0; q < EPI_COLS / 32; ++q) {
             const int64_t n0 = nbase + q * 32;
             if (n0 >= args.N) break;
+            float* stg = stg0 + q * BLK_FLOATS;
             __syncwarp();
 #pragma unroll
             for (int c = 0; c < 32; ++c) stg[lane * 32 + (c ^ lane)] = tot[q * 32 + c] * rs;
@@ -480,11 +553,13 @@ int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, floa
   if (a.rows >= ((int64_t)1 << 30) || b.rows >= ((int64_t)1 << 30)) return set_error(CUTQC_EUNSUPPORTED, "too many rows");
   PairMaps maps;
   int rc;
-  if ((rc = make_map(&maps.a_hi, a.hi, a.rows, Kp, BM))) return rc;
+  if (((uintptr_t)a.hi & 15) != 0) return set_error(CUTQC_EINVAL, "operand not 16-byte aligned");
   if ((rc = make_map(&maps.a_lo, a.lo, a.rows, Kp, BM))) return rc;
   if ((rc = make_map(&maps.b_hi, b.hi, b.rows, Kp, BNH))) return rc;
   if ((rc = make_map(&maps.b_lo, b.lo, b.rows, Kp, BNH))) return rc;
   PairArgs args{};
+  args.a_hi = a.hi;
+  args.Kp = Kp;
   args.sa = a.scale;
   args.sb = b.scale;
   args.M = a.rows;
