@@ -24,9 +24,27 @@ namespace cutqc {
 // source row x is xp with its bits moved by the row map (bit j of xp goes to
 // bit rm.bit[j] of x; identity unless rm.permute).  K index s = shared digits;
 // source column = pdep(open, open_dmask) | pdep(s, shared_dmask).
-// mode: 0 = per-row scale, 1 = one scale from *gmax for every row (written
-// to scale[0]), 2 = only accumulate max|x| into *gmax (as float bits; the
-// values are non-negative so integer max orders them).
+// Half mode: a power-of-two scale puts the max |x| of the row (mode 0) or of
+// the whole operand (mode 1, max read from *gmax) in [2^14, 2^15) (clamped to
+// [2^-60, 2^60] so that the scale, its inverse and the epilogue's product of
+// two scales and 2^-K stay normal floats; values that small contribute below
+// float32 resolution of any output); y = x / scale is split as hi = fp16(y),
+// lo = fp16(y - hi).  Mode 2 only accumulates max|x| into *gmax (float bits:
+// the values are non-negative, so integer max orders them).  When the source
+// columns are the row itself (no gather) and K is a multiple of 4, lanes move
+// float4 / 4 x half vectors, each lane holding its part of the row.
+__device__ __forceinline__ float pow2_scale(float mx) {
+  if (!(mx > 0.f)) return 1.f;
+  int e = 0;
+  frexpf(mx, &e);          // mx = f * 2^e, f in [0.5, 1)
+  return ldexpf(1.f, max(-60, min(60, e - 15)));
+}
+__device__ __forceinline__ uint2 pack4(__half a, __half b, __half c, __half d) {
+  __half2 p = __halves2half2(a, b), q = __halves2half2(c, d);
+  return make_uint2(*reinterpret_cast<uint32_t*>(&p), *reinterpret_cast<uint32_t*>(&q));
+}
+constexpr int PREP_VEC_MAX = 8;   // float4 per lane kept in registers (K <= 1024)
+
 __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows, int64_t K, int64_t Kp,
                             float* __restrict__ out32, __half* __restrict__ hi,
                             __half* __restrict__ lo, float* __restrict__ scale, int64_t src_bstride,
@@ -44,6 +62,7 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int64_t C = (int64_t)1 << (2 * v.k);
   const bool contig = v.n_open == 0 && v.shared_dmask == (uint64_t)(C - 1);
+  float wmax = 0.f;    // mode 2: this warp's running max
   for (int64_t r = warp; r < rows; r += nwarps) {
     const int64_t m = r + row0;
     const uint64_t xp = (uint64_t)m >> (2 * v.n_open);
@@ -66,10 +85,45 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
       }
       continue;
     }
-    // row max (or the operand's max), then a power-of-two scale putting it in
-    // [2^14, 2^15) (clamped to [2^-60, 2^60] so that the scale, its inverse
-    // and the epilogue's product of two scales and 2^-K stay normal floats;
-    // values that small contribute below float32 resolution of any output)
+    if (contig && (K & 3) == 0 && K <= 128 * PREP_VEC_MAX && ((reinterpret_cast<uintptr_t>(row) & 15) == 0)) {
+      const float4* row4 = reinterpret_cast<const float4*>(row);
+      const int64_t K4 = K >> 2, Kp4 = Kp >> 2;
+      float4 val[PREP_VEC_MAX];
+      float mx = 0.f;
+#pragma unroll
+      for (int i = 0; i < PREP_VEC_MAX; ++i) {
+        const int64_t j = lane + 32 * i;
+        val[i] = j < K4 ? __ldg(row4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(val[i].x), fabsf(val[i].y)), fmaxf(fabsf(val[i].z), fabsf(val[i].w))));
+      }
+      for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      if (mode == 2) {
+        wmax = fmaxf(wmax, mx);
+        continue;
+      }
+      const float sc = pow2_scale(mode == 1 ? __uint_as_float(*gmax) : mx);
+      const float inv = 1.f / sc;   // exact: power of two
+      if (lane == 0 && (mode == 0 || r == 0)) scale[mode == 0 ? r : 0] = sc;
+      uint2* h4 = reinterpret_cast<uint2*>(hi + r * Kp);
+      uint2* l4 = reinterpret_cast<uint2*>(lo + r * Kp);
+#pragma unroll
+      for (int i = 0; i < PREP_VEC_MAX; ++i) {
+        const int64_t j = lane + 32 * i;
+        if (j < K4) {
+          const float y0 = val[i].x * inv, y1 = val[i].y * inv, y2 = val[i].z * inv, y3 = val[i].w * inv;
+          const __half a0 = __float2half_rn(y0), a1 = __float2half_rn(y1), a2 = __float2half_rn(y2),
+                       a3 = __float2half_rn(y3);
+          h4[j] = pack4(a0, a1, a2, a3);
+          l4[j] = pack4(__float2half_rn(y0 - __half2float(a0)), __float2half_rn(y1 - __half2float(a1)),
+                        __float2half_rn(y2 - __half2float(a2)), __float2half_rn(y3 - __half2float(a3)));
+        }
+      }
+      for (int64_t j = K4 + lane; j < Kp4; j += 32) {
+        h4[j] = make_uint2(0, 0);
+        l4[j] = make_uint2(0, 0);
+      }
+      continue;
+    }
     float mx = 0.f;
     if (mode == 1) {
       mx = __uint_as_float(*gmax);
@@ -77,16 +131,11 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
       for (int64_t s = lane; s < K; s += 32) mx = fmaxf(mx, fabsf(__ldg(row + col(s))));
       for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
       if (mode == 2) {
-        if (lane == 0) atomicMax(gmax, __float_as_uint(mx));
+        wmax = fmaxf(wmax, mx);
         continue;
       }
     }
-    int e = 0;
-    float sc = 1.f;
-    if (mx > 0.f) {
-      frexpf(mx, &e);          // mx = f * 2^e, f in [0.5, 1)
-      sc = ldexpf(1.f, max(-60, min(60, e - 15)));
-    }
+    const float sc = pow2_scale(mx);
     const float inv = 1.f / sc;   // exact: power of two
     if (lane == 0 && (mode == 0 || r == 0)) scale[mode == 0 ? r : 0] = sc;
     for (int64_t s = lane; s < Kp; s += 32) {
@@ -96,6 +145,17 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
       __half l = __float2half_rn(y - __half2float(h));
       hi[r * Kp + s] = h;
       lo[r * Kp + s] = l;
+    }
+  }
+  if (mode == 2) {
+    // one atomic per block
+    __shared__ float bmax[32];
+    if (lane == 0) bmax[threadIdx.x >> 5] = wmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float m = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, bmax[w]);
+      atomicMax(gmax, __float_as_uint(m));
     }
   }
 }
