@@ -304,7 +304,7 @@ def run(args):
     achieved = alg_bytes / (fd_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"],
-                "traffic": profiled_traffic("paper_2205_05836_gb300/csrc/gemm_tc.cu", "profiles/tc_gemm_fd_two_sub.md"),
+                "traffic": profiled_traffic("paper_2205_05836_gb300/csrc/gemm_tc_pair.cu", "profiles/tc_pair_gemm_fd_two_sub.md"),
                 "kernel": "FD contraction (operand prep + tcgen05 GEMM), one launch sequence",
                 "algorithmic_bytes": alg_bytes, "algorithmic_flops": alg_flops,
                 "hbm_bound_ms": alg_bytes / (pk["hbm_gbs"] * 1e9) * 1e3,
