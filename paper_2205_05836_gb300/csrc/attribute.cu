@@ -30,7 +30,9 @@ namespace {
 
 constexpr int kMaxKin = 6;
 constexpr int kMaxKout = 5;
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
+constexpr int kMeasThreads = 512;
+constexpr int kBatch = 8;            // loads in flight per thread
 
 struct AttrParams {
   int w, k_in, k_out;
@@ -56,11 +58,17 @@ __device__ __forceinline__ void init_map4(const float (&p)[4], float (&o)[4]) {
   o[3] = p[0] - p[1];
 }
 
-// Rows per CTA for a fiber of F values (compile time): as many as fit a
-// 48 KiB padded [F][R + 1] block, at most 32.
+// Rows per CTA of the measured-side pass: as many as fit a 96 KiB padded
+// [F][R + 1] block (two CTAs per SM), at most 32.
+__host__ __device__ constexpr int meas_rows_for(int F) {
+  return F * 33 * 4 <= 96 * 1024 ? 32 : F * 17 * 4 <= 96 * 1024 ? 16 : F * 9 * 4 <= 96 * 1024 ? 8
+       : F * 5 * 4 <= 96 * 1024 ? 4 : F * 3 * 4 <= 96 * 1024 ? 2 : 1;
+}
+// Rows per CTA of the initialised-side pass: as many as fit a 72 KiB padded
+// [F][R + 1] block (three CTAs per SM), at most 64 (512-byte runs of float64).
 __host__ __device__ constexpr int rows_for(int F) {
-  return F * 33 * 4 <= 48 * 1024 ? 32 : F * 17 * 4 <= 48 * 1024 ? 16 : F * 9 * 4 <= 48 * 1024 ? 8
-       : F * 5 * 4 <= 48 * 1024 ? 4 : F * 3 * 4 <= 48 * 1024 ? 2 : 1;
+  return F * 65 * 4 <= 72 * 1024 ? 64 : F * 33 * 4 <= 72 * 1024 ? 32 : F * 17 * 4 <= 72 * 1024 ? 16
+       : F * 9 * 4 <= 72 * 1024 ? 8 : F * 5 * 4 <= 72 * 1024 ? 4 : F * 3 * 4 <= 72 * 1024 ? 2 : 1;
 }
 __host__ __device__ constexpr int pow3(int k) { return k == 0 ? 1 : 3 * pow3(k - 1); }
 
@@ -98,12 +106,20 @@ attr_init_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p,
   }
   const T* base = src + (int64_t)mrun * W + x0;
   const int64_t fstride = (int64_t)nm * W;
-#pragma unroll 4
-  for (int i = threadIdx.x; i < F * R; i += kThreads) {
-    const int f = i / R, r = i % R;
-    float v = 0.f;
-    if (r < rows) v = load_val(base + f * fstride + r);
-    buf[f * RS + r] = v;
+  // loads in batches of kBatch per thread (all issued before any store)
+  for (int i0 = 0; i0 < F * R; i0 += kThreads * kBatch) {
+    float v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + u * kThreads + threadIdx.x;
+      const int f = i / R, r = i % R;
+      v[u] = (i < F * R && r < rows) ? load_val(base + f * fstride + r) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + u * kThreads + threadIdx.x;
+      if (i < F * R) buf[(i / R) * RS + i % R] = v[u];
+    }
   }
   __syncthreads();
 #pragma unroll
@@ -176,11 +192,11 @@ attr_init_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p,
 // Shared memory: V as [(m << KOUT) | b][R + 1] for R consecutive output rows
 // x_out and fixed init digits `dinit` (blockIdx.y).
 template <typename T, int KOUT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kMeasThreads)
 attr_meas_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p) {
   constexpr int NM = pow3(KOUT);
   constexpr int F = NM << KOUT;
-  constexpr int R = rows_for(F);
+  constexpr int R = meas_rows_for(F);
   constexpr int RS = R + 1;
   constexpr int G = 1 << (2 * KOUT);
   extern __shared__ float sm[];
@@ -194,15 +210,15 @@ attr_meas_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p)
   const int dinit = blockIdx.y;
   const int64_t W = (int64_t)1 << p.w;
   const int rows = (int)(p.n_rows - x0 < R ? p.n_rows - x0 : R);
-  for (int r = threadIdx.x; r < R; r += kThreads) rowbase[r] = (int64_t)pdep64((uint64_t)(x0 + r), p.out_mask);
-  for (int b = threadIdx.x; b < (1 << KOUT); b += kThreads) {
+  for (int r = threadIdx.x; r < R; r += kMeasThreads) rowbase[r] = (int64_t)pdep64((uint64_t)(x0 + r), p.out_mask);
+  for (int b = threadIdx.x; b < (1 << KOUT); b += kMeasThreads) {
     uint64_t v = 0;
 #pragma unroll
     for (int j = 0; j < KOUT; ++j)
       if ((b >> j) & 1) v |= p.meas_mask[j];
     bpart[b] = (int64_t)v;
   }
-  for (int d = threadIdx.x; d < G; d += kThreads) {
+  for (int d = threadIdx.x; d < G; d += kMeasThreads) {
     int run = 0, w3 = 1, mask = 0, c = 0;
 #pragma unroll
     for (int j = 0; j < KOUT; ++j) {
@@ -218,19 +234,27 @@ attr_meas_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p)
   }
   __syncthreads();
   const T* base = src + (int64_t)dinit * NM * W;
-#pragma unroll 4
-  for (int i = threadIdx.x; i < F * R; i += kThreads) {
-    const int e = i / R, r = i % R;
-    const int m = e >> KOUT, b = e & ((1 << KOUT) - 1);
-    float v = 0.f;
-    if (r < rows) v = load_val(base + (int64_t)m * W + (rowbase[r] | bpart[b]));
-    buf[e * RS + r] = v;
+  // loads in batches of kBatch per thread (all issued before any store)
+  for (int i0 = 0; i0 < F * R; i0 += kMeasThreads * kBatch) {
+    float v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + u * kMeasThreads + threadIdx.x;
+      const int e = i / R, r = i % R;
+      const int m = e >> KOUT, b = e & ((1 << KOUT) - 1);
+      v[u] = (i < F * R && r < rows) ? load_val(base + (int64_t)m * W + (rowbase[r] | bpart[b])) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + u * kMeasThreads + threadIdx.x;
+      if (i < F * R) buf[(i / R) * RS + i % R] = v[u];
+    }
   }
   __syncthreads();
   const int64_t C = (int64_t)1 << (2 * p.k);
   int cin = 0;
   for (int j = 0; j < p.k_in; ++j) cin |= ((dinit >> (2 * j)) & 3) << p.col_shift_in[j];
-  for (int i = threadIdx.x; i < rows * G; i += kThreads) {
+  for (int i = threadIdx.x; i < rows * G; i += kMeasThreads) {
     const int r = i / G, g = i % G;
     const float* vb = buf + runoff[g] + r;
     const int mask = nonI[g];
@@ -249,7 +273,7 @@ size_t init_smem() { return (size_t)(1 << (2 * KIN)) * (rows_for(1 << (2 * KIN))
 template <typename T, int KOUT>
 size_t meas_smem() {
   constexpr int F = pow3(KOUT) << KOUT;
-  constexpr int R = rows_for(F);
+  constexpr int R = meas_rows_for(F);
   return (((size_t)F * (R + 1) + 1) & ~(size_t)1) * 4 + (size_t)(R + (1 << KOUT)) * 8 + 3 * ((size_t)1 << (2 * KOUT)) * 4;
 }
 
@@ -308,7 +332,7 @@ void fill_params(const cutqc_subcircuit* s, AttrParams* p) {
 
 // Opt a kernel in to the largest dynamic shared memory the passes use, once
 // per kernel and device.
-constexpr int kAttrMaxSmem = 100 * 1024;
+constexpr int kAttrMaxSmem = 110 * 1024;
 cudaError_t set_max_smem(const void* fn) {
   static std::mutex mu;
   static std::set<std::pair<const void*, int>> done;
@@ -339,11 +363,11 @@ int run_init(const T* src, float* out, const AttrParams& p, int final_layout, cu
 template <typename T, int KOUT>
 int run_meas(const T* src, float* out, const AttrParams& p, cudaStream_t st) {
   constexpr int F = pow3(KOUT) << KOUT;
-  constexpr int R = rows_for(F);
+  constexpr int R = meas_rows_for(F);
   const size_t smem = meas_smem<T, KOUT>();
   dim3 grid((unsigned)((p.n_rows + R - 1) / R), 1u << (2 * p.k_in));
   CUTQC_CUDA_TRY(set_max_smem((const void*)attr_meas_pass<T, KOUT>));
-  attr_meas_pass<T, KOUT><<<grid, kThreads, smem, st>>>(src, out, p);
+  attr_meas_pass<T, KOUT><<<grid, kMeasThreads, smem, st>>>(src, out, p);
   CUTQC_LAUNCH_CHECK("attr_meas_pass");
   return CUTQC_OK;
 }
