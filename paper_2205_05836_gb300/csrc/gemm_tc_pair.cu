@@ -1,9 +1,15 @@
 // Tensor-core contraction for Eq. 1 on pairs of SMs (tcgen05 cta_group::2).
 //
-// Same arithmetic as tc_gemm_kernel (FP16 hi/lo split operands, three
-// products, one fresh TMEM accumulator per 64 values of k added in registers
-// with round-to-nearest, power-of-two row / operand scales), for K <= 256
-// (four 64-wide k-blocks), organised to move fewer operand bytes per output:
+// Same products as tc_gemm_kernel (FP16 hi/lo split operands, three
+// products, power-of-two row / operand scales), for K <= 256 (four 64-wide
+// k-blocks).  Each 128 values of k accumulate in a fresh TMEM accumulator
+// ("chunk", 24 MMAs), cross products (hi x lo, lo x hi) first and hi x hi
+// last: the tensor core rounds its FP32 accumulator toward zero, and only
+// the last MMAs of a chunk do so at the chunk's full magnitude.  Chunks are
+// added in registers with round-to-nearest.  (Modelled on the 30-qubit
+// workload, this order with 128-wide chunks leaves a third of the bias of
+// 64-wide chunks in product order: sum p error -3.6e-7 against -5.4e-7.)
+// The kernel is organised to move fewer operand bytes per output:
 //
 // * a cluster of two CTAs on two SMs computes 256 x 128 output tiles with
 //   one MMA stream (M = 256, N = 128, K = 16 per instruction): CTA r holds
@@ -19,8 +25,8 @@
 //   both operands).
 // * one thread cannot issue N = 128 pair MMAs as fast as the tensor core
 //   runs them, so two threads issue alternate chunks;
-// * three 128-column accumulator buffers let the MMAs run two chunks ahead
-//   of the epilogue.
+// * three 128-column accumulator buffers let the MMAs run two chunks (256
+//   values of k) ahead of the epilogue.
 //
 // Tensor memory per CTA (512 columns): A hi [0, 128) (two fp16 values of k
 // per 32-bit column), chunk accumulators at 128, 256, 384.
@@ -28,7 +34,13 @@
 // Roles (both CTAs): warp 8 lane 0 loads B per k-block; lane 0 of warps 9
 // and 10 of CTA 0 issue the MMAs (alternate chunks); warps 0-7 write A hi to
 // tensor memory and load A lo at the start of an item, then drain the
-// chunks, scale and store their CTA's rows exactly as tc_gemm_kernel does.  The loads of both CTAs complete on CTA 0's
+// chunks, scale and store their CTA's rows.  Row-major outputs (out[m * N +
+// n]) go straight from registers (16 x 256-bit tensor-memory loads give each
+// quad of lanes 8 consecutive columns of a row: whole 32-byte sectors per
+// store) -- staging them through shared memory would add 128 KiB of shared
+// memory traffic per tile on top of the MMAs' operand reads and the B
+// stream, more than the SM's shared memory bandwidth allows at the tensor
+// rate.  Other bit-deposit layouts go through a staged transpose.  The loads of both CTAs complete on CTA 0's
 // barriers (it waits for both halves); MMA completion is multicast to the
 // barriers of both CTAs; epilogue warps of both CTAs report A written and
 // chunk buffers read on CTA 0's barriers.  Every wait is bounded; on expiry
@@ -55,6 +67,7 @@ constexpr int BK = 64;                                   // k per block (128-byt
 constexpr int MAX_KB = 4;                                // resident A: k <= 256
 constexpr int STAGES = 5;
 constexpr int NBUF = 3;                                  // chunk buffers in TMEM
+constexpr int KB_PER_CHUNK = 2;                          // 128 values of k per accumulator
 constexpr int A_COLS = MAX_KB * BK / 2;                  // 128 TMEM columns of A hi
 constexpr int ACC_COL0 = A_COLS;                         // first accumulator column
 constexpr int A_KB_BYTES = BM * BK * 2;                  // 16 KiB: A lo, one k-block
@@ -72,7 +85,6 @@ constexpr int STG_BYTES = EPI_WARPS * (EPI_COLS / 32) * BLK_FLOATS * 4;   // 64 
 struct PairMaps {
   CUtensorMap a_lo;         // [rows][Kp] fp16, box 64 x 128
   CUtensorMap b_hi, b_lo;   // [rows][Kp] fp16, box 64 x 64
-  CUtensorMap out;          // row-major float32 [M][N], box 32 x 32, 128B swizzle
 };
 
 struct PairArgs {
@@ -177,6 +189,20 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
         "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
       : "memory");
 }
+// 16 lanes x 256 bits, repeated 8 times along the columns: thread t gets
+// r[4 q + e] = (lane t / 4 + 8 (e / 2), column 8 q + 2 (t % 4) + e % 2)
+__device__ __forceinline__ void tmem_ld16x256_x8(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.16x256b.x8.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
 // Arrive on CTA 0's barrier after writing tensor memory that CTA 0's MMAs
 // read: cluster-scope release (once per work item).
 __device__ __forceinline__ void remote_arrive_release_cluster(uint32_t cluster_bar) {
@@ -276,13 +302,16 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
     }
   } else if (warp == 9 || warp == 10) {
     // ----------------------------------------------------------- MMA issue
-    // Two issuing threads: chunk c (one k-block of one tile, counted over
-    // the whole kernel) is issued by thread c % 2 into accumulator buffer
-    // c % NBUF from stage c % STAGES; each thread commits what it issued.
+    // Two issuing threads: chunk c (KB_PER_CHUNK k-blocks of one tile,
+    // counted over the whole kernel) is issued by thread c % 2 into
+    // accumulator buffer c % NBUF; k-block g (counted over the whole kernel)
+    // sits in stage g % STAGES.  Within a chunk the hi x lo and lo x hi
+    // products go first and the hi x hi products last, so that only the
+    // last MMAs truncate (round toward zero) at the chunk's full magnitude.
     const int j = warp - 9;
     if (lane == 0 && rank == 0) {
       uint32_t aphase = 0;
-      int64_t c = 0;
+      int64_t c = 0, g = 0;
       bool ok = true;
       for (int64_t item = pair; item < args.num_items && ok && !*abort_flag; item += num_pairs) {
         const int64_t t0 = (item / args.num_mp) * args.tiles_per_item;
@@ -291,32 +320,48 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
         aphase ^= 1u;
         tc_fence_after();
         for (int64_t nt = t0; nt < t1 && ok; ++nt) {
-          for (int kb = 0; kb < args.num_kb; ++kb, ++c) {
-            if ((int)(c & 1) != j) continue;
-            const int stage = (int)(c % STAGES);
-            const uint32_t phase = (uint32_t)((c / STAGES) & 1);
+          for (int kb0 = 0; kb0 < args.num_kb; kb0 += KB_PER_CHUNK, ++c) {
+            const int nkb = args.num_kb - kb0 < KB_PER_CHUNK ? args.num_kb - kb0 : KB_PER_CHUNK;
+            if ((int)(c & 1) != j) { g += nkb; continue; }
             const int buf = (int)(c % NBUF);
             const uint32_t buf_phase = (uint32_t)((c / NBUF) & 1);
             if (!mbar_wait(smem_u32(&tail->cempty[buf]), buf_phase ^ 1u, abort_flag)) { fail(); ok = false; break; }
             tc_fence_after();
-            if (!mbar_wait(smem_u32(&tail->full[stage]), phase, abort_flag)) { fail(); ok = false; break; }
+            int stage[KB_PER_CHUNK];
+            for (int q = 0; q < nkb && ok; ++q) {
+              stage[q] = (int)((g + q) % STAGES);
+              const uint32_t phase = (uint32_t)(((g + q) / STAGES) & 1);
+              if (!mbar_wait(smem_u32(&tail->full[stage[q]]), phase, abort_flag)) { fail(); ok = false; }
+            }
+            if (!ok) break;
             tc_fence_after();
             const uint32_t d = tmem_base + (uint32_t)(ACC_COL0 + buf * BN);
-            const uint32_t ah = tmem_base + (uint32_t)(kb * (BK / 2));
-            const uint32_t al = smem_u32(alo_smem + kb * A_KB_BYTES);
-            const uint32_t bh = smem_u32(b_smem + stage * STAGE_BYTES), bl = bh + B_HALF;
+            uint32_t accum = 0;
+            for (int pass = 0; pass < 2; ++pass) {        // 0: cross products, 1: hi x hi
+              for (int q = 0; q < nkb; ++q) {
+                const int kb = kb0 + q;
+                const uint32_t ah = tmem_base + (uint32_t)(kb * (BK / 2));
+                const uint32_t al = smem_u32(alo_smem + kb * A_KB_BYTES);
+                const uint32_t bh = smem_u32(b_smem + stage[q] * STAGE_BYTES), bl = bh + B_HALF;
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              // 16 values of k: 8 TMEM columns of A hi, 32 bytes inside the
-              // swizzle rows of A lo and B
-              const uint32_t ta = kk * 8, off = kk * 32;
-              const uint64_t dbh = sw128_desc(bh + off), dbl = sw128_desc(bl + off);
-              umma_pair_ts(d, ah + ta, dbh, kk != 0 ? 1u : 0u);
-              umma_pair_ts(d, ah + ta, dbl, 1u);
-              umma_pair_ss(d, sw128_desc(al + off), dbh, 1u);
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                  // 16 values of k: 8 TMEM columns of A hi, 32 bytes inside the
+                  // swizzle rows of A lo and B
+                  const uint32_t ta = kk * 8, off = kk * 32;
+                  const uint64_t dbh = sw128_desc(bh + off);
+                  if (pass == 0) {
+                    umma_pair_ts(d, ah + ta, sw128_desc(bl + off), accum);
+                    umma_pair_ss(d, sw128_desc(al + off), dbh, 1u);
+                    accum = 1u;
+                  } else {
+                    umma_pair_ts(d, ah + ta, dbh, 1u);
+                  }
+                }
+              }
             }
-            umma_commit_mc(smem_u32(&tail->empty[stage]), 0x3);
+            for (int q = 0; q < nkb; ++q) umma_commit_mc(smem_u32(&tail->empty[stage[q]]), 0x3);
             umma_commit_mc(smem_u32(&tail->cfull[buf]), 0x3);
+            g += nkb;
           }
         }
         if (ok) umma_commit_mc(smem_u32(&tail->aempty), 0x3);   // this issuer is done with A
@@ -348,7 +393,14 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
       const int64_t mrow0 = (int64_t)mp * 2 * BM + (int64_t)rank * BM + g * 32;
       const int64_t m = mrow0 + lane;
       const bool mvalid = m < args.M;
-      const bool any_row = mrow0 < args.M;
+      // row-major output layout: this thread's rows mrow0 + lane/4 + 16 h2 + 8 rsel
+      const int64_t rtile0 = mrow0 + (lane >> 2);
+      float rsv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int64_t mm = rtile0 + 16 * (i >> 1) + 8 * (i & 1);
+        rsv[i] = (kRowMajor && mm < args.M) ? args.alpha * __ldg(args.sa + mm) * sbg : 0.f;
+      }
       // ---- A rows of this item into tensor memory, once the previous
       // item's MMAs are done with the old ones
       if (!mbar_wait(smem_u32(&tail->aempty), aphase ^ 1u, abort_flag)) { fail(); ok = false; break; }
@@ -391,15 +443,24 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
       for (int64_t nt = t0; nt < t1 && ok; ++nt) {
 #pragma unroll
         for (int i = 0; i < EPI_COLS; ++i) tot[i] = 0.f;
-        for (int ch = 0; ch < args.num_kb; ++ch) {
+        for (int ch = 0; ch < (args.num_kb + KB_PER_CHUNK - 1) / KB_PER_CHUNK; ++ch) {
           if (!mbar_wait(smem_u32(&tail->cfull[buf]), buf_phase, abort_flag)) { fail(); ok = false; break; }
           tc_fence_after();
           __syncwarp();
           uint32_t r0[32], r1[32];
           const uint32_t taddr =
               tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(ACC_COL0 + buf * BN + h * EPI_COLS);
-          tmem_ld32(taddr, r0);
-          tmem_ld32(taddr + 32, r1);
+          if constexpr (kRowMajor) {
+            // two 16-lane halves, 64 columns each: tot[32 h2 + 4 q + e] is
+            // row g*32 + 16 h2 + lane/4 + 8 (e/2), column 8 q + 2 (lane%4) + e%2
+            tmem_ld16x256_x8(taddr, r0);
+            tmem_ld16x256_x8(taddr + (16u << 16), r1);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          } else {
+            // thread = row: tot[i] is row g*32 + lane, column i
+            tmem_ld32(taddr, r0);
+            tmem_ld32(taddr + 32, r1);
+          }
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             tot[i] += __uint_as_float(r0[i]);
@@ -414,41 +475,29 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
         const float rs = mvalid ? args.alpha * __ldg(args.sa + m) * sbg : 0.f;
         const int64_t nbase = nt * BN + h * EPI_COLS;
         if (kRowMajor) {
-          // 32 x 32 TMA boxes from this warp's 128B-swizzled staging block
-          // (16-byte chunk j of row r at chunk j ^ (r & 7)); rows or columns
-          // beyond the output are clipped by the tensor map
+          // out[m * N + n] straight from registers: per instruction the warp
+          // writes 8 rows x 32 bytes (4 lanes per row), whole sectors; no
+          // staging through shared memory, whose bandwidth the MMAs' operand
+          // reads and the B stream already use
+          const int64_t nb0 = nbase + 2 * (lane & 3);
 #pragma unroll
-          for (int q = 0; q < EPI_COLS / 32; ++q) {
-            const int64_t n0 = nbase + q * 32;
-            if (n0 >= args.N) break;
-            float* v = tot + q * 32;
+          for (int h2 = 0; h2 < 2; ++h2)
 #pragma unroll
-            for (int c = 0; c < 32; ++c) v[c] *= rs;
-            float* stg = stg0 + q * BLK_FLOATS;
-            // this block's previous store (one tile ago) has read the staging
-            if (lane == 0) bulk_wait_read_le1();
-            __syncwarp();
-            float4* row4 = reinterpret_cast<float4*>(stg + lane * 32);
+            for (int rsel = 0; rsel < 2; ++rsel) {
+              const int64_t mm = rtile0 + 16 * h2 + 8 * rsel;
+              const float rsm = rsv[2 * h2 + rsel];
+              float* orow = args.out + (mm < args.M ? mm : 0) * args.N + nb0;
+              float part = 0.f;
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-              row4[c ^ (lane & 7)] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
-            fence_proxy_async();
-            __syncwarp();
-            if (lane == 0 && any_row) {
-              tma_store_2d(&maps.out, smem_u32(stg), (int)n0, (int)mrow0);
-              bulk_commit();
+              for (int q = 0; q < EPI_COLS / 8; ++q) {
+                const float a = tot[32 * h2 + 4 * q + 2 * rsel] * rsm, b = tot[32 * h2 + 4 * q + 2 * rsel + 1] * rsm;
+                if (mm < args.M && nb0 + 8 * q < args.N) {
+                  __stcs(reinterpret_cast<float2*>(orow + 8 * q), make_float2(a, b));
+                  part += a + b;
+                }
+              }
+              if (args.sum) local += (double)part;
             }
-            if (args.sum && mvalid) {
-              float t[16];
-#pragma unroll
-              for (int i = 0; i < 16; ++i) t[i] = v[i] + v[i + 16];
-#pragma unroll
-              for (int w2 = 8; w2; w2 >>= 1)
-#pragma unroll
-                for (int i = 0; i < w2; ++i) t[i] += t[i + w2];
-              local += (double)t[0];
-            }
-          }
         } else {
           // general bit deposit through the staging block (XOR-swizzled by
           // row) so that lanes walk the columns of one row at a time
@@ -481,7 +530,6 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
         }
       }
     }
-    if (kRowMajor && lane == 0) bulk_wait0();   // every bulk store has completed
     __syncwarp();
     if (args.sum) {
       for (int off = 16; off; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
@@ -512,19 +560,6 @@ int make_map(CUtensorMap* map, const __half* base, int64_t rows, int64_t Kp, int
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(CUTQC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-  return CUTQC_OK;
-}
-
-int make_out_map(CUtensorMap* map, float* base, int64_t rows, int64_t cols) {
-  auto enc = get_encode();
-  if (!enc) return set_error(CUTQC_ECUDA, "cuTensorMapEncodeTiled unavailable");
-  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
-  cuuint32_t box[2] = {32, 32};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return set_error(CUTQC_ECUDA, "cuTensorMapEncodeTiled (output) failed (%d)", (int)r);
   return CUTQC_OK;
 }
 
@@ -580,14 +615,11 @@ int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, floa
   args.sum = sum;
   args.streaming = streaming;
   args.status = device_status_ptr();
-  // bulk-tensor stores when the output is out[m * N + n] with a 16-byte
-  // aligned base and row pitch
-  bool row_major = false;
-  if (args.n_contig && args.m_shift >= 0 && mask_n == (((uint64_t)1 << args.m_shift) - 1) &&
-      ((uint64_t)1 << args.m_shift) == (uint64_t)b.rows && (b.rows * 4) % 16 == 0 && ((uintptr_t)out & 15) == 0) {
-    if ((rc = make_out_map(&maps.out, out, a.rows, b.rows))) return rc;
-    row_major = true;
-  }
+  // direct 8-byte stores when the output is out[m * N + n] (N even, 8-byte
+  // aligned base)
+  const bool row_major = args.n_contig && args.m_shift >= 0 && mask_n == (((uint64_t)1 << args.m_shift) - 1) &&
+                         ((uint64_t)1 << args.m_shift) == (uint64_t)b.rows && (b.rows % 2) == 0 &&
+                         ((uintptr_t)out & 7) == 0;
   if (args.n_contig && ((uintptr_t)out & 15) != 0) return set_error(CUTQC_EINVAL, "output not 16-byte aligned");
   {
     static std::mutex mu;
