@@ -218,9 +218,10 @@ int cutqc_dd_step(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bi
  *     levels.  The jobs of one level run as one batch.
  * jobs (host, [max_jobs]) receives one record per job in execution order;
  * bins_dev receives each job's 2^n_active bins at jobs[j].bins_offset
- * (floats), bins_capacity floats in all.  Synchronises `stream` once per
- * level (the selection is read on the host).  Limits: n <= 128, M <= 30,
- * T <= 32.  Workspace: cutqc_dd_run_workspace_size bytes.                   */
+ * (floats), bins_capacity floats in all.  BFS, and DFS with T <= 1 (the same
+ * schedule), select on the device and synchronise `stream` once at the end;
+ * DFS with T > 1 reads each recursion's selection on the host.  Limits:
+ * n <= 128, M <= 30, T <= 32.  Workspace: cutqc_dd_run_workspace_size bytes. */
 typedef struct cutqc_dd_job_result {
   int32_t level;            /* recursion (DFS) or level (BFS) index */
   int32_t depth;            /* qubits below depth * M are zoomed */
@@ -242,6 +243,21 @@ int cutqc_dd_run(int n_sub, const cutqc_subcircuit* s, const float* const* attri
                  int n_qubits, int M, int R, int T, int strategy, int max_jobs,
                  cutqc_dd_job_result* jobs, int* n_jobs_out, float* bins_dev, int64_t bins_capacity,
                  void* ws_dev, size_t ws_bytes, void* stream);
+/* Algorithm 1, level by level (strategy 1 above; with T = 1 also the depth
+ * first order), enqueued without any host synchronisation or host copy, so
+ * that it can be captured in a CUDA graph and replayed: level 0 has one job,
+ * every later level T jobs (the T largest bins of the previous level, chosen
+ * on the device); at most min(R, ceil(n / M)) levels.
+ *   jobs_dev    device [max_jobs] records, written in level order; a record
+ *               with level < 0 is a placeholder (fewer than T bins to expand)
+ *   n_jobs_dev  device int32, set to the number of records written
+ * The bins of record r are at bins_dev + jobs_dev[r].bins_offset.  Host
+ * arguments are read during the call only.  Errors as cutqc_dd_run;
+ * workspace: cutqc_dd_run_workspace_size bytes (more than this call uses).  */
+int cutqc_dd_run_async(int n_sub, const cutqc_subcircuit* s, const float* const* attributed_dev,
+                       int n_qubits, int M, int R, int T, int max_jobs, cutqc_dd_job_result* jobs_dev,
+                       int32_t* n_jobs_dev, float* bins_dev, int64_t bins_capacity, void* ws_dev,
+                       size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------- reductions
  * sum_dev (device float64 scalar) += sum of x_dev[0..n) in float64.          */

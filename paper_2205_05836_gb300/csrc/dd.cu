@@ -33,12 +33,16 @@ struct Kahan {
   }
 };
 
-// grid: x = merged row a, y = job.  zoom value of job j: zoom_dev ? zoom_dev[j]
-// : zoom_val.  Threads split columns and, when there are few columns, the
-// merged index range; slices are combined through shared memory.
+// grid: x = merged row a, y = job, z = slice of the merged index range
+// (2^log_slices slices; slice s writes its partial sums to
+// out + s * n_jobs * rows_a * C, reduced by dd_merge_reduce when there are
+// several).  zoom value of job j: zoom_dev ? zoom_dev[j] : zoom_val.  Threads
+// split columns and, when there are few columns, the slice's merged indices;
+// sub-slices are combined through shared memory.
 __global__ void __launch_bounds__(256)
 dd_merge_kernel(const float* __restrict__ att, int k, uint64_t act_mask, uint64_t merged_mask, uint64_t zoom_mask,
-                uint64_t zoom_val, const uint64_t* __restrict__ zoom_dev, int n_merged, float* __restrict__ out) {
+                uint64_t zoom_val, const uint64_t* __restrict__ zoom_dev, int n_merged, int log_slices,
+                float* __restrict__ out) {
   __shared__ float red[256];
   const int64_t C = (int64_t)1 << (2 * k);
   const int a = blockIdx.x;
@@ -46,8 +50,9 @@ dd_merge_kernel(const float* __restrict__ att, int k, uint64_t act_mask, uint64_
   const int64_t rows_a = (int64_t)gridDim.x;
   const uint64_t z = (zoom_dev ? __ldg(zoom_dev + job) : zoom_val) & zoom_mask;
   const uint64_t base = pdep64((uint64_t)a, act_mask) | z;
-  const int64_t M = (int64_t)1 << n_merged;
-  float* dst = out + ((int64_t)job * rows_a + a) * C;
+  const int64_t Mper = (int64_t)1 << (n_merged - log_slices);
+  const int64_t m0 = (int64_t)blockIdx.z * Mper;
+  float* dst = out + (((int64_t)blockIdx.z * gridDim.y + job) * rows_a + a) * C;
   const int cw = (int)(C < 256 ? C : 256);
   const int slices = 256 / cw;
   const int c_local = threadIdx.x % cw;
@@ -55,7 +60,7 @@ dd_merge_kernel(const float* __restrict__ att, int k, uint64_t act_mask, uint64_
   for (int64_t c0 = 0; c0 < C; c0 += cw) {
     Kahan acc;
     if (slice < slices)
-      for (int64_t m = slice; m < M; m += slices) {
+      for (int64_t m = m0 + slice; m < m0 + Mper; m += slices) {
         const uint64_t x = base | pdep64((uint64_t)m, merged_mask);
         acc.add(__ldg(att + (int64_t)x * C + c0 + c_local));
       }
@@ -67,6 +72,15 @@ dd_merge_kernel(const float* __restrict__ att, int k, uint64_t act_mask, uint64_
       dst[c0 + c_local] = s;
     }
     __syncthreads();
+  }
+}
+
+// out[e] = sum over the S slices of part[s * E + e], in slice order.
+__global__ void dd_merge_reduce(const float* __restrict__ part, int S, int64_t E, float* __restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    Kahan acc;
+    for (int q = 0; q < S; ++q) acc.add(__ldg(part + (int64_t)q * E + e));
+    out[e] = acc.s;
   }
 }
 
@@ -165,8 +179,8 @@ int launch_merge(const cutqc_subcircuit* s, const float* att, uint64_t act, uint
   if (a > 30) return set_error(CUTQC_EUNSUPPORTED, "too many active bits");
   if ((int64_t)1 << a > 0x7fffffffLL) return set_error(CUTQC_EUNSUPPORTED, "too many rows");
   if (n_jobs < 1 || n_jobs > 65535) return set_error(CUTQC_EINVAL, "n_jobs out of range");
-  dd_merge_kernel<<<dim3(1u << a, n_jobs), 256, 0, st>>>(att, k, act, mrg, zm, zv, zoom_dev, __builtin_popcountll(mrg),
-                                                          out);
+  dd_merge_kernel<<<dim3(1u << a, n_jobs, 1), 256, 0, st>>>(att, k, act, mrg, zm, zv, zoom_dev,
+                                                             __builtin_popcountll(mrg), 0, out);
   CUTQC_LAUNCH_CHECK("dd_merge_kernel");
   return CUTQC_OK;
 }
@@ -301,6 +315,126 @@ extern "C" int cutqc_sum_f64(const float* x, int64_t n, double* sum, void* strea
 namespace cutqc {
 namespace {
 
+// Subcircuit output qubits for the device-side selection (kernel parameter).
+struct DDTables {
+  int n_sub;
+  int8_t o[64];
+  int8_t outq[64][32];
+};
+struct ZoomPtrs {
+  uint64_t* p[64];
+};
+
+// Zoom value of every job of a level for every subcircuit: bit t of
+// zoom[i][j] = the fixed value of subcircuit i's output qubit t, for the
+// qubits below lo (the zoomed ones).
+__global__ void dd_zoom_kernel(const __grid_constant__ DDTables tab, const cutqc_dd_job_result* __restrict__ jobs,
+                               int nj, int lo, const __grid_constant__ ZoomPtrs zp) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= tab.n_sub * nj) return;
+  const int i = idx / nj, j = idx % nj;
+  const cutqc_dd_job_result& J = jobs[j];
+  uint64_t z = 0;
+  for (int t = 0; t < tab.o[i]; ++t) {
+    const int q = tab.outq[i][t];
+    if (q < lo && ((J.zoom_val[q >> 6] >> (q & 63)) & 1)) z |= (uint64_t)1 << t;
+  }
+  zp.p[i][j] = z;
+}
+
+struct LevelInfo {
+  int level, depth, n_active;
+  int8_t active[32];
+};
+
+// One thread.  Completes the records of this level's jobs (bin totals, the
+// T largest bins, bin offsets) and, when merged qubits remain, writes the
+// records of the next level: the T largest bins over all valid jobs of this
+// level, ordered by value (stable: job order, then each job's own order, for
+// equal values) -- Algorithm 1's list L truncated to T.  Records past the
+// candidates are placeholders (level -1).
+__global__ void dd_select_kernel(cutqc_dd_job_result* __restrict__ jobs, int job0, int nj, LevelInfo L,
+                                 int64_t bins_off0, int64_t nb, const double* __restrict__ bsum,
+                                 const int32_t* __restrict__ tidx, const float* __restrict__ tval, int T,
+                                 int has_children, int n_next, int32_t* __restrict__ n_jobs_dev) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int j = 0; j < nj; ++j) {
+    cutqc_dd_job_result& J = jobs[job0 + j];
+    const bool valid = J.level >= 0;
+    J.n_active = L.n_active;
+    for (int a = 0; a < 32; ++a) J.active[a] = a < L.n_active ? L.active[a] : 0;
+    J.bin_sum = valid ? bsum[j] : 0.0;
+    for (int t = 0; t < 32; ++t) {
+      J.top_idx[t] = (valid && t < T) ? tidx[(int64_t)j * T + t] : -1;
+      J.top_val[t] = (valid && t < T && J.top_idx[t] >= 0) ? tval[(int64_t)j * T + t] : 0.f;
+    }
+    J.bins_offset = bins_off0 + (int64_t)j * nb;
+  }
+  if (has_children) {
+    int cj[32], cb[32];
+    float cv[32];
+    int cnt = 0;
+    for (int j = 0; j < nj; ++j) {
+      if (jobs[job0 + j].level < 0) continue;
+      for (int t = 0; t < T; ++t) {
+        const int b = tidx[(int64_t)j * T + t];
+        if (b < 0) continue;
+        const float v = tval[(int64_t)j * T + t];
+        int pos = cnt;
+        while (pos > 0 && cv[pos - 1] < v) --pos;     // after every entry of equal value
+        if (pos >= T) continue;
+        const int last = cnt < T ? cnt : T - 1;
+        for (int u = last; u > pos; --u) { cv[u] = cv[u - 1]; cj[u] = cj[u - 1]; cb[u] = cb[u - 1]; }
+        cv[pos] = v;
+        cj[pos] = j;
+        cb[pos] = b;
+        if (cnt < T) ++cnt;
+      }
+    }
+    const int next0 = job0 + nj;
+    for (int c = 0; c < n_next; ++c) {
+      cutqc_dd_job_result& R = jobs[next0 + c];
+      R.n_active = 0;
+      R.bin_sum = 0.0;
+      R.bins_offset = 0;
+      for (int t = 0; t < 32; ++t) { R.top_idx[t] = -1; R.top_val[t] = 0.f; R.active[t] = 0; }
+      if (c < cnt) {
+        const cutqc_dd_job_result& P = jobs[job0 + cj[c]];
+        R.level = L.level + 1;
+        R.depth = L.depth + 1;
+        R.parent = job0 + cj[c];
+        R.parent_bin = cb[c];
+        for (int w = 0; w < 2; ++w) { R.zoom_mask[w] = P.zoom_mask[w]; R.zoom_val[w] = P.zoom_val[w]; }
+        for (int a = 0; a < L.n_active; ++a) {
+          const int q = L.active[a];
+          R.zoom_mask[q >> 6] |= (uint64_t)1 << (q & 63);
+          if ((cb[c] >> a) & 1) R.zoom_val[q >> 6] |= (uint64_t)1 << (q & 63);
+        }
+      } else {
+        R.level = -1;
+        R.depth = L.depth + 1;
+        R.parent = -1;
+        R.parent_bin = -1;
+        for (int w = 0; w < 2; ++w) { R.zoom_mask[w] = 0; R.zoom_val[w] = 0; }
+      }
+    }
+    *n_jobs_dev = next0 + n_next;
+  } else {
+    *n_jobs_dev = job0 + nj;
+  }
+}
+
+// The first job: nothing zoomed.
+__global__ void dd_first_job_kernel(cutqc_dd_job_result* __restrict__ jobs) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  cutqc_dd_job_result& J = jobs[0];
+  J.level = 0;
+  J.depth = 0;
+  J.parent = -1;
+  J.parent_bin = -1;
+  for (int w = 0; w < 2; ++w) { J.zoom_mask[w] = 0; J.zoom_val[w] = 0; }
+}
+
 struct LevelShape {
   int depth = 0;
   std::vector<int> active;                 // qubits, ascending
@@ -338,6 +472,8 @@ int level_shape(int n_sub, const cutqc_subcircuit* s, int n, int M, int depth, L
 struct RunLayout {
   size_t merged_off[64];
   size_t zoom_off[64];
+  size_t part_off[64];      // partial sums of the slices (when log_slices > 0)
+  int log_slices[64];
   size_t step_off = 0, top_idx_off = 0, top_val_off = 0, sum_off = 0;
   size_t total = 0;
 };
@@ -348,8 +484,17 @@ int level_layout(int n_sub, const cutqc_subcircuit* s, const LevelShape& L, int 
   auto take = [&](size_t b) { size_t o = ws; ws = align_up(ws + b, 256); return o; };
   for (int i = 0; i < n_sub; ++i) {
     const int k = s[i].k_in + s[i].k_out;
-    R->merged_off[i] = take((size_t)n_jobs * ((size_t)1 << L.active_bits[i]) * ((size_t)1 << (2 * k)) * sizeof(float));
+    const size_t elems = (size_t)n_jobs * ((size_t)1 << L.active_bits[i]) * ((size_t)1 << (2 * k));
+    R->merged_off[i] = take(elems * sizeof(float));
     R->zoom_off[i] = take((size_t)n_jobs * sizeof(uint64_t));
+    // split the merged range so that about 1024 CTAs share the merge, each
+    // slice at least 64 merged indices long
+    const int o = s[i].w - s[i].k_out;
+    const int n_merged = o - L.active_bits[i] - __builtin_popcountll(L.zoom_mask[i]);
+    int ls = 0;
+    while (ls < n_merged - 6 && ((int64_t)n_jobs << (L.active_bits[i] + ls + 1)) <= 1024) ++ls;
+    R->log_slices[i] = ls;
+    R->part_off[i] = ls ? take(elems * ((size_t)1 << ls) * sizeof(float)) : 0;
   }
   size_t step = 0;
   int rc = cutqc_dd_step_workspace_size(n_sub, s, L.active_bits.data(), n_jobs, &step);
@@ -380,22 +525,143 @@ int validate_run(int n_sub, const cutqc_subcircuit* s, int n, int M, int T) {
 }  // namespace
 }  // namespace cutqc
 
+namespace cutqc {
+namespace {
+
+// Level workspace (reused by every level) and, after it, room for the job
+// records of a level-synchronous run (used by cutqc_dd_run).
+int run_ws(int n_sub, const cutqc_subcircuit* s, int n, int M, int T, size_t* level_bytes, size_t* total) {
+  size_t best = 0;
+  const int depths = (n + M - 1) / M;
+  for (int d = 0; d < depths; ++d) {
+    LevelShape L;
+    int rc = level_shape(n_sub, s, n, M, d, &L);
+    if (rc) return rc;
+    RunLayout R;
+    if ((rc = level_layout(n_sub, s, L, std::max(1, T), &R))) return rc;
+    best = std::max(best, R.total);
+  }
+  const size_t records = 1 + (size_t)(depths - 1) * std::max(1, T);
+  *level_bytes = align_up(best, 256);
+  *total = *level_bytes + align_up(records * sizeof(cutqc_dd_job_result), 256) + 256;
+  return CUTQC_OK;
+}
+
+// Enqueue a level-synchronous run: no host synchronisation, no host copies.
+int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att, int n, int M, int Rmax, int T,
+                   int max_jobs, cutqc_dd_job_result* jobs_dev, int32_t* n_jobs_dev, float* bins, int64_t bins_cap,
+                   uint8_t* ws, size_t ws_bytes, cudaStream_t st) {
+  DDTables tab{};
+  tab.n_sub = n_sub;
+  for (int i = 0; i < n_sub; ++i) {
+    const int o = s[i].w - s[i].k_out;
+    if (o > 32) return set_error(CUTQC_EUNSUPPORTED, "more than 32 outputs in a subcircuit");
+    tab.o[i] = (int8_t)o;
+    for (int t = 0; t < o; ++t) tab.outq[i][t] = (int8_t)s[i].out_qubit[t];
+  }
+  const int depths = (n + M - 1) / M;
+  const int levels = std::min(Rmax, depths);
+  const int Tn = std::max(1, T);
+  // sizes first: every level's jobs and bins must fit
+  {
+    int64_t jobs_total = 0, bins_total = 0;
+    for (int level = 0; level < levels; ++level) {
+      const int nj = level == 0 ? 1 : Tn;
+      const int na = std::min(n, level * M + M) - level * M;
+      jobs_total += nj;
+      bins_total += (int64_t)nj << na;
+    }
+    if (jobs_total > max_jobs) return set_error(CUTQC_ENOMEM, "a run of %d levels needs %lld job records", levels,
+                                                (long long)jobs_total);
+    if (bins_total > bins_cap) return set_error(CUTQC_ENOMEM, "bins_capacity too small (%lld needed)",
+                                                (long long)bins_total);
+  }
+  dd_first_job_kernel<<<1, 32, 0, st>>>(jobs_dev);
+  CUTQC_LAUNCH_CHECK("dd_first_job_kernel");
+  int job0 = 0;
+  int64_t bins_off = 0;
+  for (int level = 0; level < levels; ++level) {
+    const int nj = level == 0 ? 1 : Tn;
+    LevelShape L;
+    int rc = level_shape(n_sub, s, n, M, level, &L);
+    if (rc) return rc;
+    RunLayout lay;
+    if ((rc = level_layout(n_sub, s, L, nj, &lay))) return rc;
+    if (lay.total > ws_bytes) return set_error(CUTQC_ENOMEM, "DD workspace too small for a level");
+    ZoomPtrs zp{};
+    for (int i = 0; i < n_sub; ++i) zp.p[i] = (uint64_t*)(ws + lay.zoom_off[i]);
+    const int nthr = n_sub * nj;
+    dd_zoom_kernel<<<(nthr + 127) / 128, 128, 0, st>>>(tab, jobs_dev + job0, nj, level * M, zp);
+    CUTQC_LAUNCH_CHECK("dd_zoom_kernel");
+    std::vector<const float*> merged(n_sub);
+    for (int i = 0; i < n_sub; ++i) {
+      float* mdev = (float*)(ws + lay.merged_off[i]);
+      const int o = s[i].w - s[i].k_out;
+      const uint64_t all = o >= 64 ? ~0ull : (((uint64_t)1 << o) - 1);
+      const uint64_t mrg = all & ~L.act_mask[i] & ~L.zoom_mask[i];
+      const int k = s[i].k_in + s[i].k_out;
+      const int a = __builtin_popcountll(L.act_mask[i]);
+      const int ls = lay.log_slices[i];
+      float* part = ls ? (float*)(ws + lay.part_off[i]) : mdev;
+      dd_merge_kernel<<<dim3(1u << a, nj, 1u << ls), 256, 0, st>>>(att[i], k, L.act_mask[i], mrg, L.zoom_mask[i], 0,
+                                                                   zp.p[i], __builtin_popcountll(mrg), ls, part);
+      CUTQC_LAUNCH_CHECK("dd_merge_kernel");
+      if (ls) {
+        const int64_t E = ((int64_t)nj << a) << (2 * k);
+        const int blocks = (int)std::min<int64_t>((E + 255) / 256, (int64_t)sm_count() * 8);
+        dd_merge_reduce<<<blocks, 256, 0, st>>>(part, 1 << ls, E, mdev);
+        CUTQC_LAUNCH_CHECK("dd_merge_reduce");
+      }
+      merged[i] = mdev;
+    }
+    const int64_t nb = (int64_t)1 << L.active.size();
+    int32_t* tidx = (int32_t*)(ws + lay.top_idx_off);
+    float* tval = (float*)(ws + lay.top_val_off);
+    double* bsum = (double*)(ws + lay.sum_off);
+    if ((rc = cutqc_dd_step(n_sub, s, L.active_bits.data(), L.bin_bit.data(), nj, merged.data(), bins + bins_off, bsum,
+                            T, tidx, tval, ws + lay.step_off, lay.total - lay.step_off, st)))
+      return rc;
+    LevelInfo li{};
+    li.level = level;
+    li.depth = level;
+    li.n_active = (int)L.active.size();
+    for (int a = 0; a < li.n_active; ++a) li.active[a] = (int8_t)L.active[a];
+    const int has_children = level + 1 < levels && T > 0;
+    dd_select_kernel<<<1, 32, 0, st>>>(jobs_dev, job0, nj, li, bins_off, nb, bsum, tidx, tval, T, has_children,
+                                       has_children ? Tn : 0, n_jobs_dev);
+    CUTQC_LAUNCH_CHECK("dd_select_kernel");
+    job0 += nj;
+    bins_off += nj * nb;
+  }
+  return CUTQC_OK;
+}
+
+}  // namespace
+}  // namespace cutqc
+
 extern "C" int cutqc_dd_run_workspace_size(int n_sub, const cutqc_subcircuit* s, int n, int M, int T,
                                            size_t* bytes) {
   int rc = validate_run(n_sub, s, n, M, T);
   if (rc) return rc;
   if (!bytes) return set_error(CUTQC_EINVAL, "null bytes");
-  size_t best = 0;
-  const int depths = (n + M - 1) / M;
-  for (int d = 0; d < depths; ++d) {
-    LevelShape L;
-    if ((rc = level_shape(n_sub, s, n, M, d, &L))) return rc;
-    RunLayout R;
-    if ((rc = level_layout(n_sub, s, L, std::max(1, T), &R))) return rc;
-    best = std::max(best, R.total);
-  }
-  *bytes = best;
-  return CUTQC_OK;
+  size_t level = 0;
+  return run_ws(n_sub, s, n, M, T, &level, bytes);
+}
+
+extern "C" int cutqc_dd_run_async(int n_sub, const cutqc_subcircuit* s, const float* const* att, int n, int M, int Rmax,
+                                  int T, int max_jobs, cutqc_dd_job_result* jobs_dev, int32_t* n_jobs_dev, float* bins,
+                                  int64_t bins_cap, void* ws_dev, size_t ws_bytes, void* stream) {
+  int rc = validate_run(n_sub, s, n, M, T);
+  if (rc) return rc;
+  if (!att || !jobs_dev || !n_jobs_dev || !bins || !ws_dev || max_jobs < 1 || Rmax < 1)
+    return set_error(CUTQC_EINVAL, "bad arguments");
+  for (int i = 0; i < n_sub; ++i)
+    if (!att[i]) return set_error(CUTQC_EINVAL, "null attributed tensor");
+  size_t level = 0, total = 0;
+  if ((rc = run_ws(n_sub, s, n, M, T, &level, &total))) return rc;
+  if (ws_bytes < level) return set_error(CUTQC_ENOMEM, "DD workspace needs %zu bytes", level);
+  return enqueue_levels(n_sub, s, att, n, M, Rmax, T, max_jobs, jobs_dev, n_jobs_dev, bins, bins_cap,
+                        (uint8_t*)ws_dev, ws_bytes, (cudaStream_t)stream);
 }
 
 extern "C" int cutqc_dd_run(int n_sub, const cutqc_subcircuit* s, const float* const* att, int n, int M, int Rmax,
@@ -406,11 +672,42 @@ extern "C" int cutqc_dd_run(int n_sub, const cutqc_subcircuit* s, const float* c
   if (!att || !jobs || !n_jobs_out || !bins || max_jobs < 1 || Rmax < 1)
     return set_error(CUTQC_EINVAL, "bad arguments");
   if (strategy != 0 && strategy != 1) return set_error(CUTQC_EINVAL, "strategy must be 0 (DFS) or 1 (BFS)");
-  size_t need = 0;
-  if ((rc = cutqc_dd_run_workspace_size(n_sub, s, n, M, T, &need))) return rc;
+  size_t level_bytes = 0, need = 0;
+  if ((rc = run_ws(n_sub, s, n, M, T, &level_bytes, &need))) return rc;
   if (ws_bytes < need || !ws_dev) return set_error(CUTQC_ENOMEM, "DD workspace needs %zu bytes", need);
   cudaStream_t st = (cudaStream_t)stream;
   uint8_t* ws = (uint8_t*)ws_dev;
+  if (strategy == 1 || T <= 1) {
+    // level-synchronous (depth first with T <= 1 is the same schedule): the
+    // selection runs on the device, the records come back once at the end
+    const int depths = (n + M - 1) / M;
+    const size_t records = 1 + (size_t)(depths - 1) * std::max(1, T);
+    cutqc_dd_job_result* jdev = (cutqc_dd_job_result*)(ws + level_bytes);
+    int32_t* ndev = (int32_t*)(ws + level_bytes + align_up(records * sizeof(cutqc_dd_job_result), 256));
+    if ((rc = enqueue_levels(n_sub, s, att, n, M, Rmax, T, (int)records, jdev, ndev, bins, bins_cap, ws, level_bytes,
+                             st)))
+      return rc;
+    int32_t nrec = 0;
+    std::vector<cutqc_dd_job_result> host(records);
+    CUTQC_CUDA_TRY(cudaMemcpyAsync(&nrec, ndev, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUTQC_CUDA_TRY(cudaMemcpyAsync(host.data(), jdev, records * sizeof(cutqc_dd_job_result), cudaMemcpyDeviceToHost, st));
+    CUTQC_CUDA_TRY(cudaStreamSynchronize(st));
+    int out = 0;
+    for (int r = 0; r < nrec && r < (int)records; ++r) {
+      if (host[r].level < 0) continue;
+      if (out >= max_jobs) return set_error(CUTQC_ENOMEM, "more than max_jobs jobs");
+      cutqc_dd_job_result J = host[r];
+      jobs[out++] = J;
+    }
+    // parents index the compacted list
+    std::vector<int> remap(records, -1);
+    for (int r = 0, k = 0; r < nrec && r < (int)records; ++r)
+      if (host[r].level >= 0) remap[r] = k++;
+    for (int j = 0; j < out; ++j)
+      if (jobs[j].parent >= 0) jobs[j].parent = remap[jobs[j].parent];
+    *n_jobs_out = out;
+    return CUTQC_OK;
+  }
   int n_jobs = 0;
   int64_t bins_used = 0;
   struct Pending { double value; int parent; int bin; int depth; uint64_t zm[2], zv[2]; };

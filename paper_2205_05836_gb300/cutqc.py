@@ -285,6 +285,50 @@ def cutqc_dd_run(subs, attributed, n_qubits, M, R, T, strategy, max_jobs=256, bi
     return [jobs[i] for i in range(nj.value)], bins
 
 
+def cutqc_dd_run_async(subs, attributed, n_qubits, M, R, T, max_jobs=256, jobs=None, n_jobs=None, bins=None, ws=None,
+                       stream=None):
+    """Level-by-level Algorithm 1 enqueued without host synchronisation (CUDA
+    graph capturable).  jobs: device uint8 tensor of max_jobs records, n_jobs:
+    device int32[1]; returns (jobs, n_jobs, bins).  Use dd_jobs_from_device to
+    read the records."""
+    import torch
+    arr, keep = _subs(subs)
+    dev = attributed[0].device
+    rec = ctypes.sizeof(DDJob)
+    if jobs is None:
+        jobs = torch.empty(max_jobs * rec, dtype=torch.uint8, device=dev)
+    if n_jobs is None:
+        n_jobs = torch.zeros(1, dtype=torch.int32, device=dev)
+    if bins is None:
+        bins = torch.empty(max_jobs << min(M, n_qubits), dtype=torch.float32, device=dev)
+    need = cutqc_dd_run_workspace_size(subs, n_qubits, M, T)
+    if ws is None:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    ptrs = (c_void_p * len(attributed))(*[t.data_ptr() for t in attributed])
+    _check(lib().cutqc_dd_run_async(c_int(len(subs)), arr, ptrs, c_int(n_qubits), c_int(M), c_int(R), c_int(T),
+                                    c_int(jobs.numel() // rec), _ptr(jobs), _ptr(n_jobs), _ptr(bins),
+                                    c_int64(bins.numel()), _ptr(ws), c_size_t(ws.numel()), _stream(stream)))
+    return jobs, n_jobs, bins
+
+
+def dd_jobs_from_device(jobs, n_jobs):
+    """Records written by cutqc_dd_run_async (placeholders dropped, parents
+    re-indexed into the returned list)."""
+    n = int(n_jobs.item())
+    raw = jobs.cpu().numpy().tobytes()
+    rec = ctypes.sizeof(DDJob)
+    allj = [DDJob.from_buffer_copy(raw[i * rec:(i + 1) * rec]) for i in range(n)]
+    keep = [i for i, J in enumerate(allj) if J.level >= 0]
+    remap = {r: k for k, r in enumerate(keep)}
+    out = []
+    for r in keep:
+        J = allj[r]
+        if J.parent >= 0:
+            J.parent = remap[J.parent]
+        out.append(J)
+    return out
+
+
 def declared_symbols(headers=None):
     """Function names declared in include/*.h."""
     import re

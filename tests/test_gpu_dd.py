@@ -137,3 +137,38 @@ def test_dd_step_any_bin_order(cq, kind):
         got = bins[0].cpu().numpy().astype(np.float64)[idx]
         assert np.abs(got - p).max() <= 1e-6
         assert abs(total.item() - 1.0) <= 1e-6
+
+
+@pytest.mark.parametrize("kind,M,T", [("brickwall", 4, 3), ("aqft", 4, 2), ("bv", 5, 1)])
+def test_dd_run_async_in_cuda_graph(cq, kind, M, T):
+    """The enqueue-only level-by-level run, captured in a CUDA graph and
+    replayed twice, gives the records and bins of the synchronous run."""
+    import torch
+    cut = _cut(kind)
+    subs, A, At = _setup(cut)
+    n = cut.circuit.n
+    R = 6
+    ref_jobs, ref_bins = cq.cutqc_dd_run(subs, At, n, M, R, T, 1)
+    torch.cuda.synchronize()
+    jobs, n_jobs, bins = cq.cutqc_dd_run_async(subs, At, n, M, R, T)   # first call outside capture
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        cq.cutqc_dd_run_async(subs, At, n, M, R, T, jobs=jobs, n_jobs=n_jobs, bins=bins)
+    for _ in range(2):
+        jobs.zero_()
+        bins.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        got = cq.dd_jobs_from_device(jobs, n_jobs)
+        assert len(got) == len(ref_jobs)
+        for J, Rj in zip(got, ref_jobs):
+            assert (J.level, J.depth, J.parent, J.parent_bin, J.n_active) == \
+                (Rj.level, Rj.depth, Rj.parent, Rj.parent_bin, Rj.n_active)
+            assert J.zoom() == Rj.zoom()
+            assert list(J.top_idx) == list(Rj.top_idx)
+            assert abs(J.bin_sum - Rj.bin_sum) <= 1e-12   # float64 totals: atomic order may differ
+            nb = 1 << J.n_active
+            assert torch.equal(bins[J.bins_offset:J.bins_offset + nb], ref_bins[Rj.bins_offset:Rj.bins_offset + nb])
+    assert cq.cutqc_device_status() == 0
