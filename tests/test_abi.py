@@ -74,3 +74,54 @@ def test_host_validation_without_gpu(built):
     assert cutqc.cutqc_fd_shape([U, V]) == (4, 8)
     with pytest.raises(cutqc.CutqcError):      # edge 0 measured twice
         cutqc.cutqc_fd_shape([U, U])
+
+
+def _sub(w, in_local=(), out_local=(), in_edge=(), out_edge=(), out_qubit=None):
+    class S:
+        pass
+    s = S()
+    s.w, s.in_local, s.out_local, s.in_edge, s.out_edge = w, list(in_local), list(out_local), list(in_edge), list(out_edge)
+    s.out_qubit = list(out_qubit) if out_qubit is not None else list(range(w - len(out_local)))
+    return s
+
+
+def test_validation_error_codes(built):
+    """Shape, size and workspace queries reject malformed descriptors with the
+    documented codes, on the host."""
+    cq = built
+    # an initialised edge with no measured partner
+    with pytest.raises(cq.CutqcError) as e:
+        cq.cutqc_fd_shape([_sub(3, in_local=[0], in_edge=[5])])
+    assert e.value.code == cq.EINVAL
+    # width beyond the limit
+    with pytest.raises(cq.CutqcError) as e:
+        cq.cutqc_attribute_workspace_size(_sub(31))
+    assert e.value.code == cq.EINVAL
+    # unknown precision
+    a = _sub(3, out_local=[2], out_edge=[0], out_qubit=[0, 1])
+    b = _sub(3, in_local=[0], in_edge=[0], out_qubit=[2, 3, 4])
+    with pytest.raises(cq.CutqcError) as e:
+        cq.cutqc_reconstruct_fd_workspace_size([a, b], 7)
+    assert e.value.code == cq.EINVAL
+    assert cq.cutqc_reconstruct_fd_workspace_size([a, b], cq.PREC_FP16X3_TC) > 0
+    # DD: outputs must cover n, M and T within limits
+    with pytest.raises(cq.CutqcError) as e:
+        cq.cutqc_dd_run_workspace_size([a, b], 6, 2, 2)
+    assert e.value.code == cq.EINVAL
+    with pytest.raises(cq.CutqcError) as e:
+        cq.cutqc_dd_run_workspace_size([a, b], 5, 31, 2)
+    assert e.value.code == cq.EUNSUPPORTED
+    with pytest.raises(cq.CutqcError) as e:
+        cq.cutqc_dd_run_workspace_size([a, b], 5, 2, 33)
+    assert e.value.code == cq.EUNSUPPORTED
+    assert cq.cutqc_dd_run_workspace_size([a, b], 5, 2, 2) > 0
+
+
+def test_mlp_queries(built):
+    cq = built
+    n = ctypes.c_int64(0)
+    assert cq.lib().cutqc_mlp_param_count(ctypes.byref(n)) == 0
+    assert n.value == 64 * 256 + 256 + 256 * 256 + 256 + 256 + 1
+    b = ctypes.c_size_t(0)
+    assert cq.lib().cutqc_mlp_workspace_size(0, ctypes.byref(b)) == cq.EINVAL
+    assert cq.lib().cutqc_mlp_workspace_size(100, ctypes.byref(b)) == 0 and b.value > 0

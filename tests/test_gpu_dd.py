@@ -172,3 +172,21 @@ def test_dd_run_async_in_cuda_graph(cq, kind, M, T):
             nb = 1 << J.n_active
             assert torch.equal(bins[J.bins_offset:J.bins_offset + nb], ref_bins[Rj.bins_offset:Rj.bins_offset + nb])
     assert cq.cutqc_device_status() == 0
+
+
+def test_dd_single_subcircuit(cq):
+    """Degenerate case K = 0: dynamic definition over one subcircuit gives the
+    marginals of its own distribution."""
+    from oracle import dd
+    from workloads import circuits as C
+    from workloads.cutting import Dag, build_cut
+    c = C.brickwall(9, 3, 5)
+    cut = build_cut(c, [0] * Dag(c).nv)
+    subs, A, At = _setup(cut)
+    n, M, R, T = c.n, 4, 4, 2
+    jobs, bins = cq.cutqc_dd_run(subs, At, n, M, R, T, 1)
+    ref = dd.run(A, [s.out_qubit for s in subs], [s.edges for s in subs], 0, n, M, R, T, strategy="bfs")
+    assert len(jobs) == len(ref)
+    for J, rj in zip(jobs, ref):
+        b = bins[J.bins_offset:J.bins_offset + (1 << J.n_active)].cpu().numpy().astype(np.float64)
+        assert np.abs(b - rj["bins"]).max() <= 1e-6

@@ -180,3 +180,56 @@ def test_fd_chain_32q_full_size(cq):
         tv_est = 0.5 * (1 << w.n) * err.mean()
         assert tv_est <= TV_GATE, tv_est
     assert cq.cutqc_device_status() == 0
+
+
+def _single_sub_cut():
+    from workloads import circuits as C
+    from workloads.cutting import Dag, build_cut
+    c = C.brickwall(7, 4, 21)
+    return build_cut(c, [0] * Dag(c).nv)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["simt", "tc"])
+@pytest.mark.parametrize("order", [0, 1], ids=["kron", "original"])
+def test_fd_single_subcircuit_no_cuts(cq, precision, order):
+    """Degenerate case K = 0: the reconstruction is the subcircuit's own
+    distribution (in the requested order)."""
+    import torch
+    from oracle import metrics, statevector
+    from workloads.simulate import simulate_variants
+    cut = _single_sub_cut()
+    assert cut.K == 0 and len(cut.subcircuits) == 1
+    subs = cut.subcircuits
+    att = _gpu_att(cq, subs, [simulate_variants(s) for s in subs])
+    total = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out, _ = cq.cutqc_reconstruct_fd(subs, att, order, precision, sum_out=total)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    ref = statevector.probabilities(cut.circuit)
+    # one subcircuit: the Kronecker order is its local output order, which
+    # is ascending qubit order, so both orders give the uncut distribution
+    assert list(subs[0].out_qubit) == list(range(cut.circuit.n))
+    assert metrics.tv(got, ref) <= TV_GATE
+    assert abs(total.item() - 1.0) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["simt", "tc"])
+def test_fd_empty_row_range(cq, precision):
+    """An empty row range writes nothing and adds nothing to the sum."""
+    import torch
+    from workloads import circuits as C
+    from workloads.cutting import search_cut
+    from workloads.simulate import simulate_variants
+    cut = search_cut(C.supremacy(3, 4, 8, 1), 8, 2, restarts=4)
+    subs = cut.subcircuits
+    att = _gpu_att(cq, subs, [simulate_variants(s) for s in subs])
+    rows, cols = cq.cutqc_fd_shape(subs)
+    sentinel = torch.full((cols,), 7.0, device="cuda")
+    total = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out, _ = cq.cutqc_reconstruct_fd(subs, att, 0, precision, row_begin=2, row_end=2, out=sentinel, sum_out=total)
+    torch.cuda.synchronize()
+    assert torch.all(sentinel == 7.0) and total.item() == 0.0
+    with pytest.raises(cq.CutqcError) as e:
+        cq.cutqc_reconstruct_fd(subs, att, 0, precision, row_begin=3, row_end=2, out=sentinel)
+    assert e.value.code == cq.EINVAL
+    assert cq.cutqc_device_status() == 0
