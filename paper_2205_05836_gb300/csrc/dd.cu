@@ -84,31 +84,45 @@ __global__ void dd_merge_reduce(const float* __restrict__ part, int S, int64_t E
   }
 }
 
-// One CTA per job: top-T bins by (value desc, index asc), and the float64
-// bin total is left in bin_sum by the reconstruction's epilogue.
+// One CTA per job: the T largest bins by (value desc, index asc); the float64
+// bin total is left in bin_sum by the reconstruction's epilogue.  One pass
+// over the bins: each thread keeps its own best TCAP (sorted, earlier index
+// first among equal values, since a thread visits indices in increasing
+// order); then T rounds pick the block's best head and advance its owner.
+template <int TCAP>
 __global__ void __launch_bounds__(1024)
 dd_topk_kernel(const float* __restrict__ bins, int64_t nb, int T, int32_t* __restrict__ top_idx,
                float* __restrict__ top_val) {
   __shared__ float sv[32];
-  __shared__ int64_t si[32];
-  __shared__ float pick_v;
-  __shared__ int64_t pick_i;
+  __shared__ int si[32];
+  __shared__ int win_i;
   const float* b = bins + (int64_t)blockIdx.x * nb;
-  float pv = INFINITY;
-  int64_t pi = -1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float lv[TCAP];
+  int li[TCAP];
+  int cnt = 0;
+  for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) {
+    const float v = __ldg(b + i);
+    if (cnt == T && !(v > lv[T - 1])) continue;   // equal value: the earlier index stays
+    int pos = cnt < T ? cnt : T - 1;
+#pragma unroll
+    for (int u = TCAP - 1; u > 0; --u)
+      if (u <= pos && lv[u - 1] < v) { lv[u] = lv[u - 1]; li[u] = li[u - 1]; pos = u - 1; }
+    // pos is now the first slot whose left neighbour is >= v (or 0)
+    lv[pos] = v;
+    li[pos] = (int)i;
+    if (cnt < T) ++cnt;
+  }
+  int head = 0;
   for (int t = 0; t < T; ++t) {
     float bv = -INFINITY;
-    int64_t bi = -1;
-    for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) {
-      float v = b[i];
-      bool after = (v < pv) || (v == pv && i > pi);   // strictly after the previous pick
-      if (!after) continue;
-      if (bi < 0 || v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
-    }
+    int bi = -1;
+#pragma unroll
+    for (int u = 0; u < TCAP; ++u)
+      if (u == head && head < cnt) { bv = lv[u]; bi = li[u]; }
     for (int off = 16; off; off >>= 1) {
-      float ov = __shfl_xor_sync(0xffffffffu, bv, off);
-      int64_t oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
       if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
     }
     if (lane == 0) { sv[warp] = bv; si[warp] = bi; }
@@ -118,20 +132,25 @@ dd_topk_kernel(const float* __restrict__ bins, int64_t nb, int T, int32_t* __res
       bv = lane < nw ? sv[lane] : -INFINITY;
       bi = lane < nw ? si[lane] : -1;
       for (int off = 16; off; off >>= 1) {
-        float ov = __shfl_xor_sync(0xffffffffu, bv, off);
-        int64_t oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
         if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
       }
       if (lane == 0) {
-        pick_v = bv;
-        pick_i = bi;
-        top_idx[(int64_t)blockIdx.x * T + t] = (int32_t)bi;
+        win_i = bi;
+        top_idx[(int64_t)blockIdx.x * T + t] = bi;
         top_val[(int64_t)blockIdx.x * T + t] = bi >= 0 ? bv : 0.f;
       }
     }
     __syncthreads();
-    pv = pick_v;
-    pi = pick_i;
+    // the owner of the winning index advances (indices are distinct)
+    if (head < cnt && win_i >= 0) {
+      int cur = -1;
+#pragma unroll
+      for (int u = 0; u < TCAP; ++u)
+        if (u == head) cur = li[u];
+      if (cur == win_i) ++head;
+    }
     __syncthreads();
   }
 }
@@ -295,7 +314,8 @@ extern "C" int cutqc_dd_step(int n_sub, const cutqc_subcircuit* s, const int32_t
   if (rc) return rc;
   if (topk > 0) {
     int threads = (int)std::min<int64_t>(1024, std::max<int64_t>(32, (nb + 31) / 32 * 32));
-    dd_topk_kernel<<<n_jobs, threads, 0, st>>>(bins, nb, topk, top_idx, top_val);
+    if (topk <= 4) dd_topk_kernel<4><<<n_jobs, threads, 0, st>>>(bins, nb, topk, top_idx, top_val);
+    else dd_topk_kernel<32><<<n_jobs, threads, 0, st>>>(bins, nb, topk, top_idx, top_val);
     CUTQC_LAUNCH_CHECK("dd_topk_kernel");
   }
   return CUTQC_OK;
@@ -347,31 +367,38 @@ struct LevelInfo {
   int8_t active[32];
 };
 
-// One thread.  Completes the records of this level's jobs (bin totals, the
-// T largest bins, bin offsets) and, when merged qubits remain, writes the
+// One warp.  Completes the records of this level's jobs (bin totals, the T
+// largest bins, bin offsets) and, when merged qubits remain, writes the
 // records of the next level: the T largest bins over all valid jobs of this
 // level, ordered by value (stable: job order, then each job's own order, for
 // equal values) -- Algorithm 1's list L truncated to T.  Records past the
-// candidates are placeholders (level -1).
+// candidates are placeholders (level -1).  Lane 0 ranks the candidates; the
+// 32-entry arrays of a record are written one entry per lane.
 __global__ void dd_select_kernel(cutqc_dd_job_result* __restrict__ jobs, int job0, int nj, LevelInfo L,
                                  int64_t bins_off0, int64_t nb, const double* __restrict__ bsum,
                                  const int32_t* __restrict__ tidx, const float* __restrict__ tval, int T,
                                  int has_children, int n_next, int32_t* __restrict__ n_jobs_dev) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
   for (int j = 0; j < nj; ++j) {
     cutqc_dd_job_result& J = jobs[job0 + j];
     const bool valid = J.level >= 0;
-    J.n_active = L.n_active;
-    for (int a = 0; a < 32; ++a) J.active[a] = a < L.n_active ? L.active[a] : 0;
-    J.bin_sum = valid ? bsum[j] : 0.0;
-    for (int t = 0; t < 32; ++t) {
-      J.top_idx[t] = (valid && t < T) ? tidx[(int64_t)j * T + t] : -1;
-      J.top_val[t] = (valid && t < T && J.top_idx[t] >= 0) ? tval[(int64_t)j * T + t] : 0.f;
+    const int32_t ti = (valid && lane < T) ? tidx[(int64_t)j * T + lane] : -1;
+    J.top_idx[lane] = ti;
+    J.top_val[lane] = ti >= 0 ? tval[(int64_t)j * T + lane] : 0.f;
+    J.active[lane] = lane < L.n_active ? L.active[lane] : 0;
+    if (lane == 0) {
+      J.n_active = L.n_active;
+      J.bin_sum = valid ? bsum[j] : 0.0;
+      J.bins_offset = bins_off0 + (int64_t)j * nb;
     }
-    J.bins_offset = bins_off0 + (int64_t)j * nb;
   }
-  if (has_children) {
-    int cj[32], cb[32];
+  if (!has_children) {
+    if (lane == 0) *n_jobs_dev = job0 + nj;
+    return;
+  }
+  __shared__ int cj[32], cb[32], cnt_s;
+  if (lane == 0) {
     float cv[32];
     int cnt = 0;
     for (int j = 0; j < nj; ++j) {
@@ -391,17 +418,24 @@ __global__ void dd_select_kernel(cutqc_dd_job_result* __restrict__ jobs, int job
         if (cnt < T) ++cnt;
       }
     }
-    const int next0 = job0 + nj;
-    for (int c = 0; c < n_next; ++c) {
-      cutqc_dd_job_result& R = jobs[next0 + c];
+    cnt_s = cnt;
+  }
+  __syncwarp();
+  const int cnt = cnt_s;
+  const int next0 = job0 + nj;
+  for (int c = 0; c < n_next; ++c) {
+    cutqc_dd_job_result& R = jobs[next0 + c];
+    R.top_idx[lane] = -1;
+    R.top_val[lane] = 0.f;
+    R.active[lane] = 0;
+    if (lane == 0) {
       R.n_active = 0;
       R.bin_sum = 0.0;
       R.bins_offset = 0;
-      for (int t = 0; t < 32; ++t) { R.top_idx[t] = -1; R.top_val[t] = 0.f; R.active[t] = 0; }
+      R.depth = L.depth + 1;
       if (c < cnt) {
         const cutqc_dd_job_result& P = jobs[job0 + cj[c]];
         R.level = L.level + 1;
-        R.depth = L.depth + 1;
         R.parent = job0 + cj[c];
         R.parent_bin = cb[c];
         for (int w = 0; w < 2; ++w) { R.zoom_mask[w] = P.zoom_mask[w]; R.zoom_val[w] = P.zoom_val[w]; }
@@ -412,16 +446,13 @@ __global__ void dd_select_kernel(cutqc_dd_job_result* __restrict__ jobs, int job
         }
       } else {
         R.level = -1;
-        R.depth = L.depth + 1;
         R.parent = -1;
         R.parent_bin = -1;
         for (int w = 0; w < 2; ++w) { R.zoom_mask[w] = 0; R.zoom_val[w] = 0; }
       }
     }
-    *n_jobs_dev = next0 + n_next;
-  } else {
-    *n_jobs_dev = job0 + nj;
   }
+  if (lane == 0) *n_jobs_dev = next0 + n_next;
 }
 
 // The first job: nothing zoomed.
