@@ -537,8 +537,10 @@ def dd_extras(dev, cq, M=16, R=6, T=4, reps=5):
     (breadth first), 16 active qubits per recursion, the top-4 bins of each
     level expanded in the next.  All levels of all three circuits are
     enqueued without host synchronisation (the selection runs on the device)
-    and captured in one CUDA graph; bins/s = bins of one replay / its time."""
+    and captured in one CUDA graph; bins/s = bins of one replay / its time.
+    Launch shapes per circuit are chosen by the autotuner (tune.py) first."""
     import torch
+    from paper_2205_05836_gb300.tune import tune_dd
     from workloads.configs import dd_batched
     runs = []
     for w in dd_batched():
@@ -546,8 +548,9 @@ def dd_extras(dev, cq, M=16, R=6, T=4, reps=5):
         subs = w.subcircuits
         att = [cq.cutqc_attribute(s, torch.from_numpy(v).to(dev)) for s, v in zip(subs, w.variants())]
         ws = torch.empty(cq.cutqc_dd_run_workspace_size(subs, w.n, M, T), dtype=torch.uint8, device=dev)
-        jobs, n_jobs, bins = cq.cutqc_dd_run_async(subs, att, w.n, M, R, T, max_jobs=64, ws=ws)
-        runs.append((w, subs, att, jobs, n_jobs, bins, ws))
+        opt, trials = tune_dd(subs, att, w.n, M, R, T)
+        jobs, n_jobs, bins = cq.cutqc_dd_run_async(subs, att, w.n, M, R, T, max_jobs=64, ws=ws, options=opt)
+        runs.append((w, subs, att, jobs, n_jobs, bins, ws, opt, trials))
     torch.cuda.synchronize()
     # one graph: the three circuits' runs on three streams (independent work)
     side = torch.cuda.Stream(dev)
@@ -557,10 +560,11 @@ def dd_extras(dev, cq, M=16, R=6, T=4, reps=5):
         fork = torch.cuda.Event()
         fork.record(side)
         joins = []
-        for st, (w, subs, att, jobs, n_jobs, bins, ws) in zip(streams, runs):
+        for st, (w, subs, att, jobs, n_jobs, bins, ws, opt, trials) in zip(streams, runs):
             st.wait_event(fork)
             with torch.cuda.stream(st):
-                cq.cutqc_dd_run_async(subs, att, w.n, M, R, T, jobs=jobs, n_jobs=n_jobs, bins=bins, ws=ws)
+                cq.cutqc_dd_run_async(subs, att, w.n, M, R, T, jobs=jobs, n_jobs=n_jobs, bins=bins, ws=ws,
+                                      options=opt)
                 ev = torch.cuda.Event()
                 ev.record(st)
                 joins.append(ev)
@@ -576,12 +580,13 @@ def dd_extras(dev, cq, M=16, R=6, T=4, reps=5):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     out, tot_bins = [], 0
-    for w, subs, att, jobs, n_jobs, bins, ws in runs:
+    for w, subs, att, jobs, n_jobs, bins, ws, opt, trials in runs:
         js = cq.dd_jobs_from_device(jobs, n_jobs)
         nb = sum(1 << j.n_active for j in js)
         tot_bins += nb
         out.append({"circuit": w.name, "n": w.n, "subcircuits": len(subs), "K": w.K, "jobs": len(js), "bins": nb,
-                    "root_sum_error": abs(js[0].bin_sum - 1.0)})
+                    "root_sum_error": abs(js[0].bin_sum - 1.0), "options": opt,
+                    "tuning_ms": {f"{o['merge_ctas']}/{o['topk_threads']}": round(ms, 4) for ms, o, ok in trials if ok}})
     return {"M": M, "R": R, "T": T, "strategy": "bfs", "circuits": out, "graph_ms": ms,
             "bins_per_s": tot_bins / (ms * 1e-3),
             "note": "all levels of the three circuits in one captured CUDA graph (one stream per circuit); "

@@ -243,6 +243,18 @@ int cutqc_dd_run(int n_sub, const cutqc_subcircuit* s, const float* const* attri
                  int n_qubits, int M, int R, int T, int strategy, int max_jobs,
                  cutqc_dd_job_result* jobs, int* n_jobs_out, float* bins_dev, int64_t bins_capacity,
                  void* ws_dev, size_t ws_bytes, void* stream);
+/* Launch-shape options of cutqc_dd_run_async (results agree within float32
+ * rounding of the merge sums across settings; zero fields take defaults):
+ *   merge_ctas    about how many CTAs share one subcircuit's merge: the
+ *                 merged index range is cut into slices of >= 64 indices
+ *                 whose partial sums a second pass adds in a fixed order
+ *                 (default 1024, at most 4096)
+ *   topk_threads  threads per job of the top-T pass (default up to 1024)  */
+typedef struct cutqc_dd_options {
+  int32_t merge_ctas;
+  int32_t topk_threads;
+} cutqc_dd_options;
+
 /* Algorithm 1, level by level (strategy 1 above; with T = 1 also the depth
  * first order), enqueued without any host synchronisation or host copy, so
  * that it can be captured in a CUDA graph and replayed: level 0 has one job,
@@ -251,13 +263,14 @@ int cutqc_dd_run(int n_sub, const cutqc_subcircuit* s, const float* const* attri
  *   jobs_dev    device [max_jobs] records, written in level order; a record
  *               with level < 0 is a placeholder (fewer than T bins to expand)
  *   n_jobs_dev  device int32, set to the number of records written
- * The bins of record r are at bins_dev + jobs_dev[r].bins_offset.  Host
- * arguments are read during the call only.  Errors as cutqc_dd_run;
- * workspace: cutqc_dd_run_workspace_size bytes (more than this call uses).  */
+ * The bins of record r are at bins_dev + jobs_dev[r].bins_offset.  opt
+ * (host, nullable) chooses launch shapes.  Host arguments are read during the
+ * call only.  Errors as cutqc_dd_run; workspace: cutqc_dd_run_workspace_size
+ * bytes (enough for any options).                                            */
 int cutqc_dd_run_async(int n_sub, const cutqc_subcircuit* s, const float* const* attributed_dev,
                        int n_qubits, int M, int R, int T, int max_jobs, cutqc_dd_job_result* jobs_dev,
-                       int32_t* n_jobs_dev, float* bins_dev, int64_t bins_capacity, void* ws_dev,
-                       size_t ws_bytes, void* stream);
+                       int32_t* n_jobs_dev, float* bins_dev, int64_t bins_capacity,
+                       const cutqc_dd_options* opt, void* ws_dev, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------- reductions
  * sum_dev (device float64 scalar) += sum of x_dev[0..n) in float64.          */

@@ -287,9 +287,11 @@ extern "C" int cutqc_dd_step_workspace_size(int n_sub, const cutqc_subcircuit* s
   return CUTQC_OK;
 }
 
-extern "C" int cutqc_dd_step(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, const int32_t* bin_bit,
-                             int n_jobs, const float* const* merged, float* bins, double* bin_sum, int topk,
-                             int32_t* top_idx, float* top_val, void* ws_dev, size_t ws_bytes, void* stream) {
+// topk_threads: threads per job of the top-T pass (0: up to 1024)
+static int dd_step_impl(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, const int32_t* bin_bit,
+                        int n_jobs, const float* const* merged, float* bins, double* bin_sum, int topk,
+                        int32_t* top_idx, float* top_val, void* ws_dev, size_t ws_bytes, void* stream,
+                        int topk_threads) {
   std::vector<TensorDesc> in;
   int tot = 0;
   int rc = dd_inputs(n_sub, s, active_bits, bin_bit, &in, &tot);
@@ -313,12 +315,20 @@ extern "C" int cutqc_dd_step(int n_sub, const cutqc_subcircuit* s, const int32_t
                 CUTQC_PREC_FP32_SIMT, 0, -1, (uint8_t*)ws_dev, st);
   if (rc) return rc;
   if (topk > 0) {
-    int threads = (int)std::min<int64_t>(1024, std::max<int64_t>(32, (nb + 31) / 32 * 32));
+    const int64_t cap = topk_threads > 0 ? std::min(1024, std::max(32, topk_threads / 32 * 32)) : 1024;
+    int threads = (int)std::min<int64_t>(cap, std::max<int64_t>(32, (nb + 31) / 32 * 32));
     if (topk <= 4) dd_topk_kernel<4><<<n_jobs, threads, 0, st>>>(bins, nb, topk, top_idx, top_val);
     else dd_topk_kernel<32><<<n_jobs, threads, 0, st>>>(bins, nb, topk, top_idx, top_val);
     CUTQC_LAUNCH_CHECK("dd_topk_kernel");
   }
   return CUTQC_OK;
+}
+
+extern "C" int cutqc_dd_step(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, const int32_t* bin_bit,
+                             int n_jobs, const float* const* merged, float* bins, double* bin_sum, int topk,
+                             int32_t* top_idx, float* top_val, void* ws_dev, size_t ws_bytes, void* stream) {
+  return dd_step_impl(n_sub, s, active_bits, bin_bit, n_jobs, merged, bins, bin_sum, topk, top_idx, top_val, ws_dev,
+                      ws_bytes, stream, 0);
 }
 
 extern "C" int cutqc_sum_f64(const float* x, int64_t n, double* sum, void* stream) {
@@ -510,7 +520,12 @@ struct RunLayout {
 };
 
 // Workspace for one level of n_jobs jobs.
-int level_layout(int n_sub, const cutqc_subcircuit* s, const LevelShape& L, int n_jobs, RunLayout* R) {
+constexpr int kMergeCtasDefault = 1024, kMergeCtasMax = 4096;
+
+// merge_ctas: about how many CTAs share one subcircuit's merge (slices of the
+// merged index range, each at least 64 long)
+int level_layout(int n_sub, const cutqc_subcircuit* s, const LevelShape& L, int n_jobs, RunLayout* R,
+                 int merge_ctas = kMergeCtasDefault) {
   size_t ws = 0;
   auto take = [&](size_t b) { size_t o = ws; ws = align_up(ws + b, 256); return o; };
   for (int i = 0; i < n_sub; ++i) {
@@ -518,12 +533,10 @@ int level_layout(int n_sub, const cutqc_subcircuit* s, const LevelShape& L, int 
     const size_t elems = (size_t)n_jobs * ((size_t)1 << L.active_bits[i]) * ((size_t)1 << (2 * k));
     R->merged_off[i] = take(elems * sizeof(float));
     R->zoom_off[i] = take((size_t)n_jobs * sizeof(uint64_t));
-    // split the merged range so that about 1024 CTAs share the merge, each
-    // slice at least 64 merged indices long
     const int o = s[i].w - s[i].k_out;
     const int n_merged = o - L.active_bits[i] - __builtin_popcountll(L.zoom_mask[i]);
     int ls = 0;
-    while (ls < n_merged - 6 && ((int64_t)n_jobs << (L.active_bits[i] + ls + 1)) <= 1024) ++ls;
+    while (ls < n_merged - 6 && ((int64_t)n_jobs << (L.active_bits[i] + ls + 1)) <= merge_ctas) ++ls;
     R->log_slices[i] = ls;
     R->part_off[i] = ls ? take(elems * ((size_t)1 << ls) * sizeof(float)) : 0;
   }
@@ -569,7 +582,7 @@ int run_ws(int n_sub, const cutqc_subcircuit* s, int n, int M, int T, size_t* le
     int rc = level_shape(n_sub, s, n, M, d, &L);
     if (rc) return rc;
     RunLayout R;
-    if ((rc = level_layout(n_sub, s, L, std::max(1, T), &R))) return rc;
+    if ((rc = level_layout(n_sub, s, L, std::max(1, T), &R, kMergeCtasMax))) return rc;
     best = std::max(best, R.total);
   }
   const size_t records = 1 + (size_t)(depths - 1) * std::max(1, T);
@@ -581,7 +594,14 @@ int run_ws(int n_sub, const cutqc_subcircuit* s, int n, int M, int T, size_t* le
 // Enqueue a level-synchronous run: no host synchronisation, no host copies.
 int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att, int n, int M, int Rmax, int T,
                    int max_jobs, cutqc_dd_job_result* jobs_dev, int32_t* n_jobs_dev, float* bins, int64_t bins_cap,
-                   uint8_t* ws, size_t ws_bytes, cudaStream_t st) {
+                   uint8_t* ws, size_t ws_bytes, cudaStream_t st, const cutqc_dd_options* opt) {
+  int merge_ctas = kMergeCtasDefault, topk_threads = 0;
+  if (opt) {
+    if (opt->merge_ctas < 0 || opt->merge_ctas > kMergeCtasMax || opt->topk_threads < 0 || opt->topk_threads > 1024)
+      return set_error(CUTQC_EINVAL, "options out of range (merge_ctas <= %d, topk_threads <= 1024)", kMergeCtasMax);
+    if (opt->merge_ctas) merge_ctas = opt->merge_ctas;
+    topk_threads = opt->topk_threads;
+  }
   DDTables tab{};
   tab.n_sub = n_sub;
   for (int i = 0; i < n_sub; ++i) {
@@ -617,7 +637,7 @@ int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att
     int rc = level_shape(n_sub, s, n, M, level, &L);
     if (rc) return rc;
     RunLayout lay;
-    if ((rc = level_layout(n_sub, s, L, nj, &lay))) return rc;
+    if ((rc = level_layout(n_sub, s, L, nj, &lay, merge_ctas))) return rc;
     if (lay.total > ws_bytes) return set_error(CUTQC_ENOMEM, "DD workspace too small for a level");
     ZoomPtrs zp{};
     for (int i = 0; i < n_sub; ++i) zp.p[i] = (uint64_t*)(ws + lay.zoom_off[i]);
@@ -649,8 +669,8 @@ int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att
     int32_t* tidx = (int32_t*)(ws + lay.top_idx_off);
     float* tval = (float*)(ws + lay.top_val_off);
     double* bsum = (double*)(ws + lay.sum_off);
-    if ((rc = cutqc_dd_step(n_sub, s, L.active_bits.data(), L.bin_bit.data(), nj, merged.data(), bins + bins_off, bsum,
-                            T, tidx, tval, ws + lay.step_off, lay.total - lay.step_off, st)))
+    if ((rc = dd_step_impl(n_sub, s, L.active_bits.data(), L.bin_bit.data(), nj, merged.data(), bins + bins_off, bsum,
+                           T, tidx, tval, ws + lay.step_off, lay.total - lay.step_off, st, topk_threads)))
       return rc;
     LevelInfo li{};
     li.level = level;
@@ -681,7 +701,8 @@ extern "C" int cutqc_dd_run_workspace_size(int n_sub, const cutqc_subcircuit* s,
 
 extern "C" int cutqc_dd_run_async(int n_sub, const cutqc_subcircuit* s, const float* const* att, int n, int M, int Rmax,
                                   int T, int max_jobs, cutqc_dd_job_result* jobs_dev, int32_t* n_jobs_dev, float* bins,
-                                  int64_t bins_cap, void* ws_dev, size_t ws_bytes, void* stream) {
+                                  int64_t bins_cap, const cutqc_dd_options* opt, void* ws_dev, size_t ws_bytes,
+                                  void* stream) {
   int rc = validate_run(n_sub, s, n, M, T);
   if (rc) return rc;
   if (!att || !jobs_dev || !n_jobs_dev || !bins || !ws_dev || max_jobs < 1 || Rmax < 1)
@@ -692,7 +713,7 @@ extern "C" int cutqc_dd_run_async(int n_sub, const cutqc_subcircuit* s, const fl
   if ((rc = run_ws(n_sub, s, n, M, T, &level, &total))) return rc;
   if (ws_bytes < level) return set_error(CUTQC_ENOMEM, "DD workspace needs %zu bytes", level);
   return enqueue_levels(n_sub, s, att, n, M, Rmax, T, max_jobs, jobs_dev, n_jobs_dev, bins, bins_cap,
-                        (uint8_t*)ws_dev, ws_bytes, (cudaStream_t)stream);
+                        (uint8_t*)ws_dev, ws_bytes, (cudaStream_t)stream, opt);
 }
 
 extern "C" int cutqc_dd_run(int n_sub, const cutqc_subcircuit* s, const float* const* att, int n, int M, int Rmax,
@@ -716,7 +737,7 @@ extern "C" int cutqc_dd_run(int n_sub, const cutqc_subcircuit* s, const float* c
     cutqc_dd_job_result* jdev = (cutqc_dd_job_result*)(ws + level_bytes);
     int32_t* ndev = (int32_t*)(ws + level_bytes + align_up(records * sizeof(cutqc_dd_job_result), 256));
     if ((rc = enqueue_levels(n_sub, s, att, n, M, Rmax, T, (int)records, jdev, ndev, bins, bins_cap, ws, level_bytes,
-                             st)))
+                             st, nullptr)))
       return rc;
     int32_t nrec = 0;
     std::vector<cutqc_dd_job_result> host(records);

@@ -285,8 +285,12 @@ def cutqc_dd_run(subs, attributed, n_qubits, M, R, T, strategy, max_jobs=256, bi
     return [jobs[i] for i in range(nj.value)], bins
 
 
+class DDOptions(ctypes.Structure):
+    _fields_ = [("merge_ctas", c_int32), ("topk_threads", c_int32)]
+
+
 def cutqc_dd_run_async(subs, attributed, n_qubits, M, R, T, max_jobs=256, jobs=None, n_jobs=None, bins=None, ws=None,
-                       stream=None):
+                       stream=None, options=None):
     """Level-by-level Algorithm 1 enqueued without host synchronisation (CUDA
     graph capturable).  jobs: device uint8 tensor of max_jobs records, n_jobs:
     device int32[1]; returns (jobs, n_jobs, bins).  Use dd_jobs_from_device to
@@ -305,9 +309,12 @@ def cutqc_dd_run_async(subs, attributed, n_qubits, M, R, T, max_jobs=256, jobs=N
     if ws is None:
         ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
     ptrs = (c_void_p * len(attributed))(*[t.data_ptr() for t in attributed])
+    opt = None
+    if options is not None:
+        opt = ctypes.byref(DDOptions(int(options.get("merge_ctas", 0)), int(options.get("topk_threads", 0))))
     _check(lib().cutqc_dd_run_async(c_int(len(subs)), arr, ptrs, c_int(n_qubits), c_int(M), c_int(R), c_int(T),
                                     c_int(jobs.numel() // rec), _ptr(jobs), _ptr(n_jobs), _ptr(bins),
-                                    c_int64(bins.numel()), _ptr(ws), c_size_t(ws.numel()), _stream(stream)))
+                                    c_int64(bins.numel()), opt, _ptr(ws), c_size_t(ws.numel()), _stream(stream)))
     return jobs, n_jobs, bins
 
 

@@ -190,3 +190,22 @@ def test_dd_single_subcircuit(cq):
     for J, rj in zip(jobs, ref):
         b = bins[J.bins_offset:J.bins_offset + (1 << J.n_active)].cpu().numpy().astype(np.float64)
         assert np.abs(b - rj["bins"]).max() <= 1e-6
+
+
+def test_autotuned_dd_options_match_oracle(cq):
+    """The autotuner returns one of its candidate launch shapes, and the run
+    with it still matches the FP64 oracle."""
+    from oracle import dd
+    from paper_2205_05836_gb300.tune import CANDIDATES, tune_dd
+    cut = _cut("brickwall")
+    subs, A, At = _setup(cut)
+    n, M, R, T = cut.circuit.n, 4, 6, 3
+    best, trials = tune_dd(subs, At, n, M, R, T, reps=2)
+    assert best in CANDIDATES and len(trials) == len(CANDIDATES) and trials[0][2]
+    jobs, n_jobs, bins = cq.cutqc_dd_run_async(subs, At, n, M, R, T, options=best)
+    got = cq.dd_jobs_from_device(jobs, n_jobs)
+    ref = dd.run(A, [s.out_qubit for s in subs], [s.edges for s in subs], cut.K, n, M, R, T, strategy="bfs")
+    assert len(got) == len(ref)
+    for J, rj in zip(got, ref):
+        b = bins[J.bins_offset:J.bins_offset + (1 << J.n_active)].cpu().numpy().astype(np.float64)
+        assert np.abs(b - rj["bins"]).max() <= 1e-6
