@@ -62,6 +62,9 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int64_t C = (int64_t)1 << (2 * v.k);
   const bool contig = v.n_open == 0 && v.shared_dmask == (uint64_t)(C - 1);
+  // the shared digits are the lowest digit positions: row r's K values are
+  // consecutive from obase (the open digits sit above them)
+  const bool low_shared = v.shared_dmask == (((uint64_t)1 << (2 * v.n_shared)) - 1);
   float wmax = 0.f;    // mode 2: this warp's running max
   for (int64_t r = warp; r < rows; r += nwarps) {
     const int64_t m = r + row0;
@@ -85,8 +88,9 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
       }
       continue;
     }
-    if (contig && (K & 3) == 0 && K <= 128 * PREP_VEC_MAX && ((reinterpret_cast<uintptr_t>(row) & 15) == 0)) {
-      const float4* row4 = reinterpret_cast<const float4*>(row);
+    if (low_shared && hi && (K & 3) == 0 && K <= 128 * PREP_VEC_MAX &&
+        ((reinterpret_cast<uintptr_t>(row + obase) & 15) == 0)) {
+      const float4* row4 = reinterpret_cast<const float4*>(row + obase);
       const int64_t K4 = K >> 2, Kp4 = Kp >> 2;
       float4 val[PREP_VEC_MAX];
       float mx = 0.f;

@@ -102,6 +102,7 @@ struct PairArgs {
   uint64_t mask_m, mask_n;
   int n_contig;
   int m_shift;
+  int m_low5;           // mask_m holds address bits 0..4 (rows 32-aligned are consecutive)
   float* out;
   double* sum;
   int streaming;
@@ -499,10 +500,28 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
               if (args.sum) local += (double)part;
             }
         } else {
-          // general bit deposit through the staging block (XOR-swizzled by
-          // row) so that lanes walk the columns of one row at a time
           const uint64_t roff =
               mvalid ? (args.m_shift >= 0 ? ((uint64_t)m << args.m_shift) : pdep64((uint64_t)m, args.mask_m)) : 0;
+          if (args.m_low5) {
+            // the low 5 bits of the row index are the low 5 address bits:
+            // for each column the warp's 32 rows are 32 consecutive floats
+            // (thread = row), stored column by column without staging
+#pragma unroll 4
+            for (int c = 0; c < EPI_COLS; ++c) {
+              const int64_t n = nbase + c;
+              if (n >= args.N) break;
+              const uint64_t coff = args.n_contig ? (uint64_t)n : pdep64((uint64_t)n, args.mask_n);
+              const float val = tot[c] * rs;
+              if (mvalid) {
+                float* ptr = args.out + (roff | coff);
+                if (args.streaming) __stcs(ptr, val); else *ptr = val;
+                if (args.sum) local += (double)val;
+              }
+            }
+            continue;
+          }
+          // general bit deposit through the staging block (XOR-swizzled by
+          // row) so that lanes walk the columns of one row at a time
 #pragma unroll
           for (int q = 0; q < EPI_COLS / 32; ++q) {
             const int64_t n0 = nbase + q * 32;
@@ -611,6 +630,7 @@ int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, floa
   args.mask_n = mask_n;
   args.n_contig = mask_is_low(mask_n) ? 1 : 0;
   args.m_shift = mask_contig_shift(mask_m);
+  args.m_low5 = (mask_m & 31) == 31 ? 1 : 0;
   args.out = out;
   args.sum = sum;
   args.streaming = streaming;
