@@ -47,18 +47,87 @@ def peaks():
     return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, source="fallback")
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (SM clock, its maximum, clock
+    event reasons, power).  Nothing here changes a GPU setting."""
+    SM = 1
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, device_index):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        uuid = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+        except Exception:
+            uuid = None
+        ok = False
+        if uuid:
+            u = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            ok = self.lib.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(self.h)) == 0
+        if not ok and self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(device_index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle")
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = fn if fn is not None else self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        v = ctypes.c_uint()
+        self.sm_max = float(v.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, ctypes.byref(v)) == 0 \
+            else None
+
+    def sample(self):
+        c = self.c
+        mhz, mw, r = c.c_uint(), c.c_uint(), c.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, c.byref(mhz)) != 0:
+            return None
+        self.reasons_fn(self.h, c.byref(r))
+        self.lib.nvmlDeviceGetPowerUsage(self.h, c.byref(mw))
+        return float(mhz.value), int(r.value), mw.value / 1000.0
+
+
 class ClockSampler:
-    """nvidia-smi sampling during the timed region."""
+    """SM clock and clock event reasons sampled DURING the timed region: a
+    thread polls NVML (read-only, through ctypes) every millisecond, so even
+    a region of a few tens of milliseconds gets samples; without NVML,
+    nvidia-smi every 200 ms (which may see none in a short region)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index=0):
+    def __init__(self, index=0, period_s=0.001):
         self.index = index
+        self.period = period_s
         self.proc = None
+        self.nvml = None
+        self.samples = []
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        try:
+            self.nvml = _Nvml(index)
+        except Exception:
+            self.nvml = None
+
+    def _poll(self):
+        while not self._stop.is_set():
+            s = self.nvml.sample()
+            if s is not None:
+                self.samples.append(s)
+            self._stop.wait(self.period)
 
     def __enter__(self):
+        if self.nvml is not None:
+            import threading
+            self._stop = threading.Event()
+            self.samples = []
+            first = self.nvml.sample()
+            if first is not None:
+                self.samples.append(first)
+            self._thread = threading.Thread(target=self._poll, daemon=True)
+            self._thread.start()
+            return self
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
@@ -70,6 +139,13 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
+        if self.nvml is not None:
+            self._stop.set()
+            self._thread.join(timeout=5)
+            last = self.nvml.sample()
+            if last is not None:
+                self.samples.append(last)
+            return
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -79,6 +155,18 @@ class ClockSampler:
             self.f.close()
 
     def summary(self):
+        if self.nvml is not None:
+            if not self.samples:
+                return {"sm_mhz": None, "sm_max_mhz": self.nvml.sm_max, "reasons": ["unsampled"]}
+            reasons = set()
+            for _, r, _ in self.samples:
+                for bit, nm in _Nvml.REASONS.items():
+                    if r & bit:
+                        reasons.add(nm)
+            return {"sm_mhz": statistics.median(s[0] for s in self.samples), "sm_max_mhz": self.nvml.sm_max,
+                    "sm_min_mhz": min(s[0] for s in self.samples), "reasons": sorted(reasons),
+                    "power_w_max": max(s[2] for s in self.samples), "samples": len(self.samples),
+                    "source": "nvml, 1 ms"}
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm, smax, reasons = [], [], set()
@@ -98,7 +186,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, 200 ms"}
 
 
 def dist_setup():
@@ -526,12 +614,14 @@ def fd_chain_extras(dev, cq, steps=10, warmup=3):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         k = steps if name == "tc" else 3
-        e0.record(stream)
-        for _ in range(k):
-            g.replay()
-        e1.record(stream)
-        torch.cuda.synchronize()
+        with ClockSampler(dev.index or 0) as clk:
+            e0.record(stream)
+            for _ in range(k):
+                g.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
         res[name + "_ms"] = e0.elapsed_time(e1) / k
+        res[name + "_clocks"] = clk.summary()
         res[name + "_sum_p_error"] = abs(total.item() - 1.0)
         del g, fws
     pk = peaks()

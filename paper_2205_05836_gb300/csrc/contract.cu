@@ -15,6 +15,10 @@
 #include "internal.cuh"
 #include "contract.cuh"
 
+#include <algorithm>
+#include <mutex>
+#include <set>
+
 namespace cutqc {
 
 // ----------------------------------------------------------------- prep
@@ -164,6 +168,101 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
   }
 }
 
+// Transposing variant for operands whose open digits are the lowest digits
+// of the source columns (n_open >= 3): for a fixed source row x and shared
+// index s, the operand rows (x, open) and (x, open + 1) are adjacent in
+// memory, while one operand row's K values are 4^n_open floats apart.  A
+// block takes 32 consecutive operand rows (one source row x, 32 consecutive
+// open values): its warps read the tile [K][32] with one coalesced 128-byte
+// load per s (each warp a contiguous run of s, the source column advanced by
+// a submask increment), stage it in shared memory ([K][33], conflict-free
+// both ways), then write the rows K-major exactly as prep_kernel does.
+// Requires row0 % 32 == 0 so that a tile never straddles two source rows.
+__global__ void prep_tr_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows, int64_t K, int64_t Kp,
+                               float* __restrict__ out32, __half* __restrict__ hi, __half* __restrict__ lo,
+                               float* __restrict__ scale, int64_t src_bstride, int64_t dst_bstride, int mode,
+                               unsigned int* __restrict__ gmax) {
+  extern __shared__ float tile[];   // [K][33]
+  v.src += (int64_t)blockIdx.y * src_bstride;
+  if (out32) out32 += (int64_t)blockIdx.y * dst_bstride * Kp;
+  if (hi) {
+    hi += (int64_t)blockIdx.y * dst_bstride * Kp;
+    lo += (int64_t)blockIdx.y * dst_bstride * Kp;
+    scale += (int64_t)blockIdx.y * dst_bstride;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t C = (int64_t)1 << (2 * v.k);
+  const int ob = 2 * v.n_open;
+  const int64_t per = (K + nw - 1) / nw;
+  const int64_t s_lo = warp * per < K ? warp * per : K;
+  const int64_t s_hi = s_lo + per < K ? s_lo + per : K;
+  const uint64_t smask = v.shared_dmask;
+  const uint64_t col_lo = pdep64((uint64_t)s_lo, smask);
+  const int64_t ntiles = (rows + 31) >> 5;
+  float wmax = 0.f;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = t << 5;
+    const int64_t m0 = r0 + row0;
+    const uint64_t xp = (uint64_t)m0 >> ob;
+    uint64_t x = xp;
+    if (rm.permute) {
+      x = 0;
+      for (int j = 0; j < rm.n; ++j) x |= ((xp >> j) & 1) << rm.bit[j];
+    }
+    const uint64_t open0 = (uint64_t)m0 & (((uint64_t)1 << ob) - 1);
+    const bool rvalid = r0 + lane < rows;
+    const float* base = v.src + (int64_t)x * C + (int64_t)open0 + lane;
+    uint64_t col = col_lo;
+#pragma unroll 8
+    for (int64_t s = s_lo; s < s_hi; ++s) {
+      const float val = rvalid ? __ldg(base + col) : 0.f;
+      if (mode == 2) wmax = fmaxf(wmax, fabsf(val));
+      else tile[s * 33 + lane] = val;
+      col = ((col | ~smask) + 1) & smask;     // next submask of smask in increasing order
+    }
+    if (mode == 2) continue;
+    __syncthreads();
+    for (int rr = warp; rr < 32; rr += nw) {
+      const int64_t r = r0 + rr;
+      if (r >= rows) break;
+      if (out32) {
+        for (int64_t s = lane; s < Kp; s += 32) out32[r * Kp + s] = s < K ? tile[s * 33 + rr] : 0.f;
+        continue;
+      }
+      float mx = 0.f;
+      if (mode == 1) {
+        mx = __uint_as_float(*gmax);
+      } else {
+        for (int64_t s = lane; s < K; s += 32) mx = fmaxf(mx, fabsf(tile[s * 33 + rr]));
+        for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      }
+      const float sc = pow2_scale(mx);
+      const float inv = 1.f / sc;   // exact: power of two
+      if (lane == 0 && (mode == 0 || r == 0)) scale[mode == 0 ? r : 0] = sc;
+      for (int64_t s = lane; s < Kp; s += 32) {
+        const float y = s < K ? tile[s * 33 + rr] * inv : 0.f;
+        const __half h = __float2half_rn(y);
+        hi[r * Kp + s] = h;
+        lo[r * Kp + s] = __float2half_rn(y - __half2float(h));
+      }
+    }
+    __syncthreads();
+  }
+  if (mode == 2) {
+    for (int off = 16; off; off >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, off));
+    __shared__ float bmax[32];
+    if (lane == 0) bmax[warp] = wmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float m = 0.f;
+      for (int w = 0; w < nw; ++w) m = fmaxf(m, bmax[w]);
+      atomicMax(gmax, __float_as_uint(m));
+    }
+  }
+}
+
+constexpr int64_t PREP_TR_MAX_K = 1024;   // staged tile [K][33] floats: 132 KiB at most
+
 int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int64_t row0, int64_t rows,
                      int64_t Kp, float* out32, __half* hi, __half* lo, float* scale, cudaStream_t st,
                      int batch, int64_t src_bstride, unsigned int* gmax) {
@@ -180,6 +279,39 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
   int blocks = (int)std::min<int64_t>((rows * 32 + 255) / 256, (int64_t)sm_count() * 16);
   if (blocks < 1) blocks = 1;
   if (batch < 1 || batch > 65535) return set_error(CUTQC_EUNSUPPORTED, "batch %d out of range", batch);
+  const bool low_open = v.open_dmask == (((uint64_t)1 << (2 * v.n_open)) - 1);
+  if (v.n_open >= 3 && low_open && v.n_shared > 0 && K <= PREP_TR_MAX_K && row0 % 32 == 0) {
+    // strided rows: transpose through shared memory (prep_tr_kernel)
+    static std::mutex mu;
+    static std::set<int> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (!done.count(dev)) {
+        CUTQC_CUDA_TRY(cudaFuncSetAttribute(prep_tr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(PREP_TR_MAX_K * 33 * sizeof(float))));
+        done.insert(dev);
+      }
+    }
+    const size_t smem = (size_t)K * 33 * sizeof(float);
+    const int per_sm = std::max(1, std::min(8, (int)((200 * 1024) / smem)));
+    const int tblocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 31) / 32, (int64_t)sm_count() * per_sm));
+    if (gmax) {
+      if (batch != 1) return set_error(CUTQC_EINVAL, "internal: operand-wide scale needs batch 1");
+      CUTQC_CUDA_TRY(cudaMemsetAsync(gmax, 0, sizeof(unsigned int), st));
+      prep_tr_kernel<<<dim3(tblocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride,
+                                                       rows, 2, gmax);
+      CUTQC_LAUNCH_CHECK("prep_tr_kernel (max)");
+      prep_tr_kernel<<<dim3(tblocks, 1), 256, smem, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale,
+                                                          src_bstride, rows, 1, gmax);
+    } else {
+      prep_tr_kernel<<<dim3(tblocks, batch), 256, smem, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale,
+                                                              src_bstride, rows, 0, nullptr);
+    }
+    CUTQC_LAUNCH_CHECK("prep_tr_kernel");
+    return CUTQC_OK;
+  }
   if (gmax) {
     // one scale for the whole operand: max pass, then the split
     if (batch != 1) return set_error(CUTQC_EINVAL, "internal: operand-wide scale needs batch 1");

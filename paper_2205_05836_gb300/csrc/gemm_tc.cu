@@ -326,6 +326,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
           const int64_t n = n0 + lane;
           const bool nvalid = n < args.N;
           const uint64_t coff = args.n_contig ? (uint64_t)n : pdep64((uint64_t)n, args.mask_n);
+          float part = 0.f;     // float over 32 rows, float64 across blocks
 #pragma unroll 4
           for (int r = 0; r < 32; ++r) {
             const uint64_t roff_r = __shfl_sync(0xffffffffu, roff, r);
@@ -334,9 +335,10 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
             if (mv_r && nvalid) {
               float* ptr = args.out + (roff_r | coff);
               if (args.streaming) __stcs(ptr, val); else *ptr = val;
-              if (args.sum) local += (double)val;
+              part += val;
             }
           }
+          if (args.sum) local += (double)part;
         }
       }
     }

@@ -103,6 +103,7 @@ struct PairArgs {
   int n_contig;
   int m_shift;
   int m_low5;           // mask_m holds address bits 0..4 (rows 32-aligned are consecutive)
+  uint64_t coff_lo[64]; // pdep(c, mask_n) for c < 64: column offsets inside a 64-aligned group
   float* out;
   double* sum;
   int streaming;
@@ -481,6 +482,7 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
           // staging through shared memory, whose bandwidth the MMAs' operand
           // reads and the B stream already use
           const int64_t nb0 = nbase + 2 * (lane & 3);
+          float part = 0.f;     // this thread's 64 outputs of the tile; float64 across tiles
 #pragma unroll
           for (int h2 = 0; h2 < 2; ++h2)
 #pragma unroll
@@ -488,7 +490,6 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
               const int64_t mm = rtile0 + 16 * h2 + 8 * rsel;
               const float rsm = rsv[2 * h2 + rsel];
               float* orow = args.out + (mm < args.M ? mm : 0) * args.N + nb0;
-              float part = 0.f;
 #pragma unroll
               for (int q = 0; q < EPI_COLS / 8; ++q) {
                 const float a = tot[32 * h2 + 4 * q + 2 * rsel] * rsm, b = tot[32 * h2 + 4 * q + 2 * rsel + 1] * rsm;
@@ -497,27 +498,31 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
                   part += a + b;
                 }
               }
-              if (args.sum) local += (double)part;
             }
+          if (args.sum) local += (double)part;
         } else {
           const uint64_t roff =
               mvalid ? (args.m_shift >= 0 ? ((uint64_t)m << args.m_shift) : pdep64((uint64_t)m, args.mask_m)) : 0;
           if (args.m_low5) {
             // the low 5 bits of the row index are the low 5 address bits:
             // for each column the warp's 32 rows are 32 consecutive floats
-            // (thread = row), stored column by column without staging
-#pragma unroll 4
+            // (thread = row), stored column by column without staging.
+            // nbase is a multiple of 64, so pdep(nbase + c) = pdep(nbase) |
+            // pdep(c), the second term a constant of the launch.
+            const uint64_t cbase = args.n_contig ? (uint64_t)nbase : pdep64((uint64_t)nbase, args.mask_n);
+            float* const obase = args.out + (mvalid ? roff : 0);
+            float part = 0.f;
+#pragma unroll
             for (int c = 0; c < EPI_COLS; ++c) {
-              const int64_t n = nbase + c;
-              if (n >= args.N) break;
-              const uint64_t coff = args.n_contig ? (uint64_t)n : pdep64((uint64_t)n, args.mask_n);
+              if (nbase + c >= args.N) break;
               const float val = tot[c] * rs;
               if (mvalid) {
-                float* ptr = args.out + (roff | coff);
+                float* ptr = obase + (cbase | args.coff_lo[c]);
                 if (args.streaming) __stcs(ptr, val); else *ptr = val;
-                if (args.sum) local += (double)val;
+                part += val;
               }
             }
+            if (args.sum) local += (double)part;
             continue;
           }
           // general bit deposit through the staging block (XOR-swizzled by
@@ -534,6 +539,7 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
             const int64_t n = n0 + lane;
             const bool nvalid = n < args.N;
             const uint64_t coff = args.n_contig ? (uint64_t)n : pdep64((uint64_t)n, args.mask_n);
+            float part = 0.f;
 #pragma unroll 4
             for (int r = 0; r < 32; ++r) {
               const uint64_t roff_r = __shfl_sync(0xffffffffu, roff, r);
@@ -542,9 +548,10 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
               if (mv_r && nvalid) {
                 float* ptr = args.out + (roff_r | coff);
                 if (args.streaming) __stcs(ptr, val); else *ptr = val;
-                if (args.sum) local += (double)val;
+                part += val;
               }
             }
+            if (args.sum) local += (double)part;
           }
         }
       }
@@ -631,6 +638,7 @@ int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, floa
   args.n_contig = mask_is_low(mask_n) ? 1 : 0;
   args.m_shift = mask_contig_shift(mask_m);
   args.m_low5 = (mask_m & 31) == 31 ? 1 : 0;
+  for (int c = 0; c < 64; ++c) args.coff_lo[c] = pdep64((uint64_t)c, mask_n);
   args.out = out;
   args.sum = sum;
   args.streaming = streaming;

@@ -96,6 +96,71 @@ def test_fd_matches_oracle(cq, name, cut, precision, order):
     assert cq.cutqc_device_status() == 0
 
 
+def _synthetic_chain(o0, o1, o2, k01, k12, seed):
+    """Three structural subcircuits in a chain, s0 -(k01 cuts)- s1 -(k12
+    cuts)- s2, with seeded random attributed tensors (Eq. 1 is bilinear in
+    them, so any values exercise the contraction).  s0 measures edges
+    0..k01-1, s1 initialises them and measures the next k12, s2 initialises
+    those; output qubits are a seeded permutation of 0..n-1."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(seed)
+    n = o0 + o1 + o2
+    perm = [int(q) for q in rng.permutation(n)]
+    e01 = list(range(k01))
+    e12 = list(range(k01, k01 + k12))
+    s0 = SimpleNamespace(w=o0 + k01, in_local=[], in_edge=[], out_local=list(range(o0, o0 + k01)), out_edge=e01,
+                         out_qubit=perm[:o0], edges=e01, o=o0)
+    s1 = SimpleNamespace(w=o1 + k12, in_local=list(range(k01)), in_edge=e01,
+                         out_local=list(range(o1, o1 + k12)), out_edge=e12, out_qubit=perm[o0:o0 + o1],
+                         edges=e01 + e12, o=o1)
+    s2 = SimpleNamespace(w=o2, in_local=list(range(k12)), in_edge=e12, out_local=[], out_edge=[],
+                         out_qubit=perm[o0 + o1:], edges=e12, o=o2)
+    subs = [s0, s1, s2]
+    # magnitudes spread over a few decades per row, both signs
+    A = [rng.standard_normal((1 << s.o, 4 ** len(s.edges))) * 10.0 ** rng.uniform(-3, 0, size=(1 << s.o, 1))
+         for s in subs]
+    return subs, A
+
+
+_SYN_CACHE = {}
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["simt", "tc"])
+@pytest.mark.parametrize("order", [0, 1], ids=["kron", "original"])
+@pytest.mark.parametrize("shape", [(5, 6, 4, 3, 3), (5, 5, 4, 3, 4), (6, 5, 3, 2, 3)],
+                         ids=["open3", "open4", "open3_k2"])
+def test_fd_synthetic_chain_layouts(cq, shape, order, precision):
+    """Chains whose middle tensor is contracted first over its high cut
+    digits, its open digits lowest (operand rows gathered through the
+    shared-memory transpose, intermediate rows stored column by column),
+    then joined with the first: every output against the FP64 oracle, to a
+    bound relative to the sum of |terms| (the oracle on |A|)."""
+    import torch
+    from oracle import fd
+    if shape not in _SYN_CACHE:
+        o0, o1, o2, k01, k12 = shape
+        subs, A = _synthetic_chain(o0, o1, o2, k01, k12, seed=sum(shape))
+        # the float32 copy of A is the kernels' input: the oracle runs on it
+        A = [a.astype(np.float32).astype(np.float64) for a in A]
+        edges = [s.edges for s in subs]
+        K = k01 + k12
+        _SYN_CACHE[shape] = (subs, A, fd.reconstruct_kron(A, edges, K),
+                             fd.reconstruct_kron([np.abs(a) for a in A], edges, K))
+    subs, A, ref, bound = _SYN_CACHE[shape]
+    if order == 1:
+        ref = fd.kron_to_original(ref, [s.out_qubit for s in subs])
+        bound = fd.kron_to_original(bound, [s.out_qubit for s in subs])
+    att = [torch.from_numpy(a.astype(np.float32)).cuda() for a in A]
+    total = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out, _ = cq.cutqc_reconstruct_fd(subs, att, order, precision, sum_out=total)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    err = np.abs(got - ref)
+    assert (err <= 2.0 ** -16 * bound + 1e-30).all(), (err / (bound + 1e-300)).max()
+    assert abs(total.item() - got.sum()) <= 2.0 ** -20 * np.abs(got).sum()
+    assert cq.cutqc_device_status() == 0
+
+
 def test_fd_row_split_reassembles(cq):
     """Offset/stride sharding: row ranges written separately equal the whole."""
     import torch
