@@ -490,7 +490,16 @@ def run(args):
         torch.cuda.empty_cache()
         _log("FD chain extras done")
         line["dd_batched"] = dd_extras(dev, cq)
+        tc = dd_extras(dev, cq, precision=1)
+        line["dd_batched"]["split_precision"] = {
+            "graph_ms": tc["graph_ms"], "bins_per_s": tc["bins_per_s"],
+            "root_sum_error": max(c["root_sum_error"] for c in tc["circuits"]),
+            "options": {c["circuit"]: c["options"] for c in tc["circuits"]}}
         _log("DD extras done")
+        torch.cuda.empty_cache()
+        line["dd_dense"] = dd_dense_extras(dev, cq)
+        torch.cuda.empty_cache()
+        _log("DD dense extras done")
         line["learned"] = learned_extras(dev, cq)
         _log("cut-scorer extras done")
     if rank == 0:
@@ -640,14 +649,16 @@ def fd_chain_extras(dev, cq, steps=10, warmup=3):
     return res
 
 
-def dd_extras(dev, cq, M=16, R=6, T=4, reps=5):
+def dd_extras(dev, cq, M=16, R=6, T=4, reps=5, precision=0):
     """Dynamic definition on the three blocked brick-wall circuits (40, 50
     and 60 qubits, subcircuits <= 15 qubits): Algorithm 1 level by level
     (breadth first), 16 active qubits per recursion, the top-4 bins of each
     level expanded in the next.  All levels of all three circuits are
     enqueued without host synchronisation (the selection runs on the device)
     and captured in one CUDA graph; bins/s = bins of one replay / its time.
-    Launch shapes per circuit are chosen by the autotuner (tune.py) first."""
+    Launch shapes per circuit are chosen by the autotuner (tune.py) first.
+    precision: bin reconstruction in FP32 (0) or on the split-precision
+    tensor-core path (1)."""
     import torch
     from paper_2205_05836_gb300.tune import tune_dd
     from workloads.configs import dd_batched
@@ -657,7 +668,7 @@ def dd_extras(dev, cq, M=16, R=6, T=4, reps=5):
         subs = w.subcircuits
         att = [cq.cutqc_attribute(s, torch.from_numpy(v).to(dev)) for s, v in zip(subs, w.variants())]
         ws = torch.empty(cq.cutqc_dd_run_workspace_size(subs, w.n, M, T), dtype=torch.uint8, device=dev)
-        opt, trials = tune_dd(subs, att, w.n, M, R, T)
+        opt, trials = tune_dd(subs, att, w.n, M, R, T, precision=precision)
         jobs, n_jobs, bins = cq.cutqc_dd_run_async(subs, att, w.n, M, R, T, max_jobs=64, ws=ws, options=opt)
         runs.append((w, subs, att, jobs, n_jobs, bins, ws, opt, trials))
     torch.cuda.synchronize()
@@ -696,10 +707,52 @@ def dd_extras(dev, cq, M=16, R=6, T=4, reps=5):
         out.append({"circuit": w.name, "n": w.n, "subcircuits": len(subs), "K": w.K, "jobs": len(js), "bins": nb,
                     "root_sum_error": abs(js[0].bin_sum - 1.0), "options": opt,
                     "tuning_ms": {f"{o['merge_ctas']}/{o['topk_threads']}": round(ms, 4) for ms, o, ok in trials if ok}})
-    return {"M": M, "R": R, "T": T, "strategy": "bfs", "circuits": out, "graph_ms": ms,
-            "bins_per_s": tot_bins / (ms * 1e-3),
+    return {"M": M, "R": R, "T": T, "strategy": "bfs", "precision": "tc" if precision else "fp32",
+            "circuits": out, "graph_ms": ms, "bins_per_s": tot_bins / (ms * 1e-3),
             "note": "all levels of the three circuits in one captured CUDA graph (one stream per circuit); "
                     "selection on the device"}
+
+
+def dd_dense_extras(dev, cq, M=30, T=4, reps=5):
+    """One dense recursion (the paper's per-recursion workload of 2^30 bins):
+    the 60-qubit blocked brick-wall circuit (5 subcircuits <= 15 qubits,
+    K = 6), qubits 0..29 active, 30..59 merged; merge, bin reconstruction
+    and top-T selection as one captured CUDA graph, FP32 and split-precision
+    tensor cores; bins/s = 2^30 / time."""
+    import torch
+    from workloads.configs import dd_batched
+    w = [x for x in dd_batched() if x.n == 60][0]
+    subs = w.subcircuits
+    att = [cq.cutqc_attribute(s, torch.from_numpy(v).to(dev)) for s, v in zip(subs, w.variants())]
+    ws = torch.empty(cq.cutqc_dd_run_workspace_size(subs, w.n, M, T), dtype=torch.uint8, device=dev)
+    bins = torch.empty(1 << M, dtype=torch.float32, device=dev)
+    res = {"circuit": w.name, "n": w.n, "subcircuits": len(subs), "K": w.K, "active": M, "bins": 1 << M, "T": T}
+    for name, prec in (("fp32", 0), ("tc", 1)):
+        opt = {"precision": prec}
+        jobs, n_jobs, _ = cq.cutqc_dd_run_async(subs, att, w.n, M, 1, T, max_jobs=4, bins=bins, ws=ws, options=opt)
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream(dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            cq.cutqc_dd_run_async(subs, att, w.n, M, 1, T, jobs=jobs, n_jobs=n_jobs, bins=bins, ws=ws, options=opt)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev.index or 0) as clk:
+            e0.record()
+            for _ in range(reps):
+                g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        js = cq.dd_jobs_from_device(jobs, n_jobs)
+        res[name] = {"ms": ms, "bins_per_s": (1 << M) / (ms * 1e-3), "root_sum_error": abs(js[0].bin_sum - 1.0),
+                     "top_idx": [int(i) for i in js[0].top_idx[:T]], "clocks": clk.summary()}
+        del g
+    pk = peaks()
+    res["hbm_bound_ms"] = 4.0 * (1 << M) / (pk["hbm_gbs"] * 1e9) * 1e3
+    res["speedup_tc_over_fp32"] = res["fp32"]["ms"] / res["tc"]["ms"]
+    return res
 
 
 def run_profile_case(args):

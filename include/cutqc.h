@@ -243,16 +243,24 @@ int cutqc_dd_run(int n_sub, const cutqc_subcircuit* s, const float* const* attri
                  int n_qubits, int M, int R, int T, int strategy, int max_jobs,
                  cutqc_dd_job_result* jobs, int* n_jobs_out, float* bins_dev, int64_t bins_capacity,
                  void* ws_dev, size_t ws_bytes, void* stream);
-/* Launch-shape options of cutqc_dd_run_async (results agree within float32
- * rounding of the merge sums across settings; zero fields take defaults):
+/* Options of cutqc_dd_run_async (zero fields take defaults).  Launch shapes
+ * (results agree within float32 rounding of the merge sums across settings):
  *   merge_ctas    about how many CTAs share one subcircuit's merge: the
  *                 merged index range is cut into slices of >= 64 indices
  *                 whose partial sums a second pass adds in a fixed order
  *                 (default 1024, at most 4096)
- *   topk_threads  threads per job of the top-T pass (default up to 1024)  */
+ *   topk_threads  threads per job of the top-T pass (default up to 1024)
+ * Arithmetic of the bin reconstruction (Eq. 1 on the merged tensors):
+ *   precision     CUTQC_PREC_FP32_SIMT (default) or CUTQC_PREC_FP16X3_TC,
+ *                 the FD tensor-core path; levels whose jobs have fewer than
+ *                 4 bins, or whose bins do not start 16-byte aligned, run
+ *                 in FP32.  Bin totals are float64 either way.
+ * Jobs of more than 2^16 bins select their top T in two passes (chunks of
+ * the bins, then the chunks' candidates), with the same order.            */
 typedef struct cutqc_dd_options {
   int32_t merge_ctas;
   int32_t topk_threads;
+  int32_t precision;
 } cutqc_dd_options;
 
 /* Algorithm 1, level by level (strategy 1 above; with T = 1 also the depth

@@ -84,33 +84,48 @@ __global__ void dd_merge_reduce(const float* __restrict__ part, int S, int64_t E
   }
 }
 
-// One CTA per job: the T largest bins by (value desc, index asc); the float64
-// bin total is left in bin_sum by the reconstruction's epilogue.  One pass
-// over the bins: each thread keeps its own best TCAP (sorted, earlier index
-// first among equal values, since a thread visits indices in increasing
-// order); then T rounds pick the block's best head and advance its owner.
-template <int TCAP>
+// The T largest bins of each job by (value desc, index asc); the float64 bin
+// total is left in bin_sum by the reconstruction's epilogue.  CTA (job j,
+// chunk c) scans entries [c * chunk_len, (c + 1) * chunk_len) of job j's n
+// entries and writes its T best to slot (j * gridDim.y + c).  kCand = false:
+// the entries are bins and an entry's index is its position; kCand = true:
+// the entries are (value, index) candidates of an earlier pass (index -1 =
+// none), which is how large jobs are finished (chunked pass, then one CTA
+// per job over the chunks' candidates).  One pass: each thread keeps its
+// own best TCAP (sorted), then T rounds pick the block's best head and
+// advance its owner.
+__device__ __forceinline__ bool dd_better(float v, int i, float w, int j) {
+  return v > w || (v == w && i < j);
+}
+
+template <int TCAP, bool kCand>
 __global__ void __launch_bounds__(1024)
-dd_topk_kernel(const float* __restrict__ bins, int64_t nb, int T, int32_t* __restrict__ top_idx,
-               float* __restrict__ top_val) {
+dd_topk_kernel(const float* __restrict__ vals, const int32_t* __restrict__ cidx, int64_t n, int64_t chunk_len, int T,
+               int32_t* __restrict__ top_idx, float* __restrict__ top_val) {
   __shared__ float sv[32];
   __shared__ int si[32];
   __shared__ int win_i;
-  const float* b = bins + (int64_t)blockIdx.x * nb;
+  const float* b = vals + (int64_t)blockIdx.x * n;
+  const int32_t* ci = kCand ? cidx + (int64_t)blockIdx.x * n : nullptr;
+  const int64_t lo = (int64_t)blockIdx.y * chunk_len;
+  const int64_t hi = lo + chunk_len < n ? lo + chunk_len : n;
+  const int64_t slot = ((int64_t)blockIdx.x * gridDim.y + blockIdx.y) * T;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float lv[TCAP];
   int li[TCAP];
   int cnt = 0;
-  for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) {
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const float v = __ldg(b + i);
-    if (cnt == T && !(v > lv[T - 1])) continue;   // equal value: the earlier index stays
+    const int idx = kCand ? __ldg(ci + i) : (int)i;
+    if (kCand && idx < 0) continue;
+    if (cnt == T && !dd_better(v, idx, lv[T - 1], li[T - 1])) continue;
     int pos = cnt < T ? cnt : T - 1;
 #pragma unroll
     for (int u = TCAP - 1; u > 0; --u)
-      if (u <= pos && lv[u - 1] < v) { lv[u] = lv[u - 1]; li[u] = li[u - 1]; pos = u - 1; }
-    // pos is now the first slot whose left neighbour is >= v (or 0)
+      if (u <= pos && dd_better(v, idx, lv[u - 1], li[u - 1])) { lv[u] = lv[u - 1]; li[u] = li[u - 1]; pos = u - 1; }
+    // pos is now the first slot whose left neighbour ranks before (v, idx)
     lv[pos] = v;
-    li[pos] = (int)i;
+    li[pos] = idx;
     if (cnt < T) ++cnt;
   }
   int head = 0;
@@ -138,8 +153,8 @@ dd_topk_kernel(const float* __restrict__ bins, int64_t nb, int T, int32_t* __res
       }
       if (lane == 0) {
         win_i = bi;
-        top_idx[(int64_t)blockIdx.x * T + t] = bi;
-        top_val[(int64_t)blockIdx.x * T + t] = bi >= 0 ? bv : 0.f;
+        top_idx[slot + t] = bi;
+        top_val[slot + t] = bi >= 0 ? bv : 0.f;
       }
     }
     __syncthreads();
@@ -153,6 +168,19 @@ dd_topk_kernel(const float* __restrict__ bins, int64_t nb, int T, int32_t* __res
     }
     __syncthreads();
   }
+}
+
+// Large jobs: chunks of the chunked first pass of the top-T selection.
+constexpr int64_t kTopkChunkMin = (int64_t)1 << 16;   // bins per chunk at least
+constexpr int64_t kTopkChunksMax = 2048;
+inline int64_t topk_chunks(int64_t nb) {
+  if (nb <= kTopkChunkMin) return 1;
+  return std::min<int64_t>(kTopkChunksMax, (nb + kTopkChunkMin - 1) / kTopkChunkMin);
+}
+// candidate scratch of the chunked pass for n_jobs jobs of nb bins (bytes)
+inline size_t topk_scratch(int64_t nb, int n_jobs) {
+  const int64_t c = topk_chunks(nb);
+  return c > 1 ? align_up((size_t)n_jobs * c * 32 * (sizeof(int32_t) + sizeof(float)), 256) : 0;
 }
 
 __global__ void sum_f64_kernel(const float* __restrict__ x, int64_t n, double* __restrict__ sum) {
@@ -268,8 +296,10 @@ extern "C" int cutqc_dd_merge_batch(const cutqc_subcircuit* s, const float* attr
   return launch_merge(s, attributed, active_mask, mrg, zoom_mask, 0, zoom_dev, n_jobs, merged, (cudaStream_t)stream);
 }
 
-extern "C" int cutqc_dd_step_workspace_size(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits,
-                                            int n_jobs, size_t* bytes) {
+// Workspace of one step: the contraction plan's (for the given precision;
+// for FP32 sized for any bin order) and the chunked top-T candidates.
+static int dd_step_ws(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, int n_jobs, int precision,
+                      size_t* bytes) {
   if (!bytes) return set_error(CUTQC_EINVAL, "null bytes");
   std::vector<TensorDesc> in;
   int tot = 0;
@@ -282,16 +312,23 @@ extern "C" int cutqc_dd_step_workspace_size(int n_sub, const cutqc_subcircuit* s
   if (rc) return rc;
   if (n_jobs < 1) return set_error(CUTQC_EINVAL, "n_jobs must be >= 1");
   ContractionPlan plan;
-  if ((rc = plan_contraction_batched(in, CUTQC_PREC_FP32_SIMT, n_jobs, &plan, true))) return rc;
-  *bytes = plan.ws_bytes;
+  if ((rc = plan_contraction_batched(in, precision, n_jobs, &plan, true))) return rc;
+  *bytes = align_up(plan.ws_bytes, 256) + topk_scratch((int64_t)1 << tot, n_jobs);
   return CUTQC_OK;
 }
 
-// topk_threads: threads per job of the top-T pass (0: up to 1024)
+extern "C" int cutqc_dd_step_workspace_size(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits,
+                                            int n_jobs, size_t* bytes) {
+  return dd_step_ws(n_sub, s, active_bits, n_jobs, CUTQC_PREC_FP32_SIMT, bytes);
+}
+
+// topk_threads: threads per job of the top-T pass (0: up to 1024).
+// precision: CUTQC_PREC_FP32_SIMT, or CUTQC_PREC_FP16X3_TC for jobs of at
+// least 4 bins whose bins start 16-byte aligned (smaller ones take FP32).
 static int dd_step_impl(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, const int32_t* bin_bit,
                         int n_jobs, const float* const* merged, float* bins, double* bin_sum, int topk,
                         int32_t* top_idx, float* top_val, void* ws_dev, size_t ws_bytes, void* stream,
-                        int topk_threads) {
+                        int topk_threads, int precision = CUTQC_PREC_FP32_SIMT) {
   std::vector<TensorDesc> in;
   int tot = 0;
   int rc = dd_inputs(n_sub, s, active_bits, bin_bit, &in, &tot);
@@ -302,23 +339,49 @@ static int dd_step_impl(int n_sub, const cutqc_subcircuit* s, const int32_t* act
     if (!merged[i]) return set_error(CUTQC_EINVAL, "null merged tensor");
   if (topk < 0 || topk > 32) return set_error(CUTQC_EUNSUPPORTED, "topk must be in 0..32");
   if (topk > 0 && (!top_idx || !top_val)) return set_error(CUTQC_EINVAL, "null top-k outputs");
+  if (precision != CUTQC_PREC_FP32_SIMT && precision != CUTQC_PREC_FP16X3_TC)
+    return set_error(CUTQC_EINVAL, "unknown precision %d", precision);
+  const int64_t nb = (int64_t)1 << tot;
+  if (precision == CUTQC_PREC_FP16X3_TC && (nb < 4 || ((uintptr_t)bins & 15) != 0)) precision = CUTQC_PREC_FP32_SIMT;
   ContractionPlan plan;
-  if ((rc = plan_contraction_batched(in, CUTQC_PREC_FP32_SIMT, n_jobs, &plan))) return rc;
-  if (ws_bytes < plan.ws_bytes || (plan.ws_bytes && !ws_dev))
-    return set_error(CUTQC_ENOMEM, "DD workspace needs %zu bytes", plan.ws_bytes);
+  if ((rc = plan_contraction_batched(in, precision, n_jobs, &plan))) return rc;
+  const size_t plan_ws = align_up(plan.ws_bytes, 256);
+  const size_t need = plan_ws + topk_scratch(nb, n_jobs);
+  if (ws_bytes < need || (need && !ws_dev)) return set_error(CUTQC_ENOMEM, "DD workspace needs %zu bytes", need);
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<int64_t> bstride(n_sub);
   for (int i = 0; i < n_sub; ++i) bstride[i] = ((int64_t)1 << in[i].o) << (2 * in[i].edges.size());
-  const int64_t nb = (int64_t)1 << tot;
   if (bin_sum) CUTQC_CUDA_TRY(cudaMemsetAsync(bin_sum, 0, sizeof(double) * n_jobs, st));
-  rc = run_plan(plan, merged, bstride.data(), n_jobs, bins, nb, bin_sum, std::ldexp(1.0f, -plan.K),
-                CUTQC_PREC_FP32_SIMT, 0, -1, (uint8_t*)ws_dev, st);
+  rc = run_plan(plan, merged, bstride.data(), n_jobs, bins, nb, bin_sum, std::ldexp(1.0f, -plan.K), precision, 0, -1,
+                (uint8_t*)ws_dev, st);
   if (rc) return rc;
   if (topk > 0) {
     const int64_t cap = topk_threads > 0 ? std::min(1024, std::max(32, topk_threads / 32 * 32)) : 1024;
-    int threads = (int)std::min<int64_t>(cap, std::max<int64_t>(32, (nb + 31) / 32 * 32));
-    if (topk <= 4) dd_topk_kernel<4><<<n_jobs, threads, 0, st>>>(bins, nb, topk, top_idx, top_val);
-    else dd_topk_kernel<32><<<n_jobs, threads, 0, st>>>(bins, nb, topk, top_idx, top_val);
+    const int64_t chunks = topk_chunks(nb);
+    if (chunks == 1) {
+      const int threads = (int)std::min<int64_t>(cap, std::max<int64_t>(32, (nb + 31) / 32 * 32));
+      if (topk <= 4)
+        dd_topk_kernel<4, false><<<dim3(n_jobs, 1), threads, 0, st>>>(bins, nullptr, nb, nb, topk, top_idx, top_val);
+      else
+        dd_topk_kernel<32, false><<<dim3(n_jobs, 1), threads, 0, st>>>(bins, nullptr, nb, nb, topk, top_idx, top_val);
+    } else {
+      // chunked pass into the candidate scratch, then one CTA per job
+      int32_t* cidx = (int32_t*)((uint8_t*)ws_dev + plan_ws);
+      float* cval = (float*)(cidx + (size_t)n_jobs * chunks * 32);
+      const int64_t clen = (nb + chunks - 1) / chunks;
+      const int64_t ncand = chunks * topk;
+      if (topk <= 4) {
+        dd_topk_kernel<4, false><<<dim3(n_jobs, (unsigned)chunks), (int)cap, 0, st>>>(bins, nullptr, nb, clen, topk,
+                                                                                     cidx, cval);
+        CUTQC_LAUNCH_CHECK("dd_topk_kernel (chunks)");
+        dd_topk_kernel<4, true><<<dim3(n_jobs, 1), 1024, 0, st>>>(cval, cidx, ncand, ncand, topk, top_idx, top_val);
+      } else {
+        dd_topk_kernel<32, false><<<dim3(n_jobs, (unsigned)chunks), (int)cap, 0, st>>>(bins, nullptr, nb, clen, topk,
+                                                                                      cidx, cval);
+        CUTQC_LAUNCH_CHECK("dd_topk_kernel (chunks)");
+        dd_topk_kernel<32, true><<<dim3(n_jobs, 1), 1024, 0, st>>>(cval, cidx, ncand, ncand, topk, top_idx, top_val);
+      }
+    }
     CUTQC_LAUNCH_CHECK("dd_topk_kernel");
   }
   return CUTQC_OK;
@@ -540,9 +603,11 @@ int level_layout(int n_sub, const cutqc_subcircuit* s, const LevelShape& L, int 
     R->log_slices[i] = ls;
     R->part_off[i] = ls ? take(elems * ((size_t)1 << ls) * sizeof(float)) : 0;
   }
-  size_t step = 0;
-  int rc = cutqc_dd_step_workspace_size(n_sub, s, L.active_bits.data(), n_jobs, &step);
+  size_t step = 0, step_tc = 0;
+  int rc = dd_step_ws(n_sub, s, L.active_bits.data(), n_jobs, CUTQC_PREC_FP32_SIMT, &step);
   if (rc) return rc;
+  if ((rc = dd_step_ws(n_sub, s, L.active_bits.data(), n_jobs, CUTQC_PREC_FP16X3_TC, &step_tc))) return rc;
+  step = std::max(step, step_tc);
   R->step_off = take(step);
   R->top_idx_off = take((size_t)n_jobs * 32 * sizeof(int32_t));
   R->top_val_off = take((size_t)n_jobs * 32 * sizeof(float));
@@ -595,12 +660,15 @@ int run_ws(int n_sub, const cutqc_subcircuit* s, int n, int M, int T, size_t* le
 int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att, int n, int M, int Rmax, int T,
                    int max_jobs, cutqc_dd_job_result* jobs_dev, int32_t* n_jobs_dev, float* bins, int64_t bins_cap,
                    uint8_t* ws, size_t ws_bytes, cudaStream_t st, const cutqc_dd_options* opt) {
-  int merge_ctas = kMergeCtasDefault, topk_threads = 0;
+  int merge_ctas = kMergeCtasDefault, topk_threads = 0, precision = CUTQC_PREC_FP32_SIMT;
   if (opt) {
     if (opt->merge_ctas < 0 || opt->merge_ctas > kMergeCtasMax || opt->topk_threads < 0 || opt->topk_threads > 1024)
       return set_error(CUTQC_EINVAL, "options out of range (merge_ctas <= %d, topk_threads <= 1024)", kMergeCtasMax);
+    if (opt->precision != CUTQC_PREC_FP32_SIMT && opt->precision != CUTQC_PREC_FP16X3_TC)
+      return set_error(CUTQC_EINVAL, "options: unknown precision %d", opt->precision);
     if (opt->merge_ctas) merge_ctas = opt->merge_ctas;
     topk_threads = opt->topk_threads;
+    precision = opt->precision;
   }
   DDTables tab{};
   tab.n_sub = n_sub;
@@ -670,7 +738,8 @@ int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att
     float* tval = (float*)(ws + lay.top_val_off);
     double* bsum = (double*)(ws + lay.sum_off);
     if ((rc = dd_step_impl(n_sub, s, L.active_bits.data(), L.bin_bit.data(), nj, merged.data(), bins + bins_off, bsum,
-                           T, tidx, tval, ws + lay.step_off, lay.total - lay.step_off, st, topk_threads)))
+                           T, tidx, tval, ws + lay.step_off, lay.total - lay.step_off, st, topk_threads,
+                           precision)))
       return rc;
     LevelInfo li{};
     li.level = level;

@@ -16,8 +16,9 @@ CANDIDATES = [dict(merge_ctas=m, topk_threads=t) for m in (1024, 256, 4096) for 
 _CACHE = {}
 
 
-def shape_key(subs, n, M, R, T):
-    return (n, M, R, T, tuple((int(s.w), len(s.in_local), len(s.out_local), tuple(s.out_qubit)) for s in subs))
+def shape_key(subs, n, M, R, T, precision=0):
+    return (n, M, R, T, precision,
+            tuple((int(s.w), len(s.in_local), len(s.out_local), tuple(s.out_qubit)) for s in subs))
 
 
 def _time_graph(run, reps):
@@ -37,10 +38,12 @@ def _time_graph(run, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def tune_dd(subs, attributed, n, M, R, T, max_jobs=64, reps=5, candidates=None, atol=1e-6):
-    """Returns (best options dict, [(ms, options, matches_default), ...])."""
+def tune_dd(subs, attributed, n, M, R, T, max_jobs=64, reps=5, candidates=None, atol=1e-6, precision=0):
+    """Returns (best options dict, [(ms, options, matches_default), ...]).
+    ``precision`` (0 FP32, 1 split-precision tensor cores) is fixed; only the
+    launch shapes are searched."""
     import torch
-    key = shape_key(subs, n, M, R, T)
+    key = shape_key(subs, n, M, R, T, precision)
     if key in _CACHE:
         return _CACHE[key]
     dev = attributed[0].device
@@ -48,6 +51,7 @@ def tune_dd(subs, attributed, n, M, R, T, max_jobs=64, reps=5, candidates=None, 
     ref = None
     results = []
     for opt in candidates or CANDIDATES:
+        opt = dict(opt, precision=precision)
         jobs, n_jobs, bins = cq.cutqc_dd_run_async(subs, attributed, n, M, R, T, max_jobs=max_jobs, ws=ws,
                                                    options=opt)
         torch.cuda.synchronize()

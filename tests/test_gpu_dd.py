@@ -201,7 +201,9 @@ def test_autotuned_dd_options_match_oracle(cq):
     subs, A, At = _setup(cut)
     n, M, R, T = cut.circuit.n, 4, 6, 3
     best, trials = tune_dd(subs, At, n, M, R, T, reps=2)
-    assert best in CANDIDATES and len(trials) == len(CANDIDATES) and trials[0][2]
+    assert best.get("precision") == 0
+    assert {k: v for k, v in best.items() if k != "precision"} in CANDIDATES
+    assert len(trials) == len(CANDIDATES) and trials[0][2]
     jobs, n_jobs, bins = cq.cutqc_dd_run_async(subs, At, n, M, R, T, options=best)
     got = cq.dd_jobs_from_device(jobs, n_jobs)
     ref = dd.run(A, [s.out_qubit for s in subs], [s.edges for s in subs], cut.K, n, M, R, T, strategy="bfs")
@@ -209,3 +211,101 @@ def test_autotuned_dd_options_match_oracle(cq):
     for J, rj in zip(got, ref):
         b = bins[J.bins_offset:J.bins_offset + (1 << J.n_active)].cpu().numpy().astype(np.float64)
         assert np.abs(b - rj["bins"]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("kind,M,T", [("brickwall", 4, 3), ("aqft", 6, 1), ("brickwall", 10, 2), ("bv", 5, 1)])
+def test_dd_split_precision_matches_oracle(cq, kind, M, T):
+    """Bin reconstruction on the tensor-core path (FP16 hi/lo split, the FD
+    GEMM) inside the enqueue-only run: bins and totals against the FP64
+    oracle, and the same jobs (levels of fewer than 4 bins per job take
+    FP32).  The cases are ones whose expanded bins are separated from the
+    next by far more than rounding (an AQFT level with exactly equal bins
+    may expand either of them)."""
+    import torch
+    from oracle import dd
+    cut = _cut(kind)
+    subs, A, At = _setup(cut)
+    n, R = cut.circuit.n, 6
+    jobs, n_jobs, bins = cq.cutqc_dd_run_async(subs, At, n, M, R, T, options={"precision": 1})
+    got = cq.dd_jobs_from_device(jobs, n_jobs)
+    ref = dd.run(A, [s.out_qubit for s in subs], [s.edges for s in subs], cut.K, n, M, R, T, strategy="bfs")
+    assert len(got) == len(ref)
+    for J, rj in zip(got, ref):
+        assert list(J.active[:J.n_active]) == rj["active"]
+        assert J.zoom() == rj["zoom"]
+        b = bins[J.bins_offset:J.bins_offset + (1 << J.n_active)].cpu().numpy().astype(np.float64)
+        assert np.abs(b - rj["bins"]).max() <= 1e-6
+        assert abs(J.bin_sum - rj["bins"].sum()) <= 1e-6
+        top = [i for i in J.top_idx[:T] if i >= 0]
+        if rj["top"]:
+            np.testing.assert_allclose(sorted(rj["bins"][top]), sorted(rj["bins"][rj["top"]]), atol=1e-6)
+    assert cq.cutqc_device_status() == 0
+
+
+@pytest.mark.parametrize("T", [1, 4, 17])
+def test_dd_topk_large_job_with_ties(cq, T):
+    """Selection on jobs of more than 2^16 bins (chunked first pass, then the
+    chunks' candidates): one subcircuit without cuts, so the bins are its
+    merged tensor as given; values drawn from a few levels, so that ties
+    cross chunk boundaries.  The T best must be exactly the first T of the
+    order (value descending, index ascending)."""
+    import torch
+    from types import SimpleNamespace
+    o = 19
+    sub = SimpleNamespace(w=o, in_local=[], in_edge=[], out_local=[], out_edge=[], out_qubit=list(range(o)))
+    rng = np.random.default_rng(T)
+    n_jobs = 3
+    vals = rng.integers(0, 40, size=(n_jobs, 1 << o)).astype(np.float32) / 8.0
+    vals[1, :] = 1.0                        # one job: every bin ties
+    vals[2, rng.integers(0, 1 << o, size=5)] = 99.0
+    merged = torch.from_numpy(vals.reshape(n_jobs, 1 << o, 1)).cuda()
+    bins = torch.empty((n_jobs, 1 << o), dtype=torch.float32, device="cuda")
+    tidx = torch.empty((n_jobs, T), dtype=torch.int32, device="cuda")
+    tval = torch.empty((n_jobs, T), dtype=torch.float32, device="cuda")
+    cq.cutqc_dd_step([sub], [o], list(range(o)), [merged], bins, topk=T, top_idx=tidx, top_val=tval)
+    torch.cuda.synchronize()
+    assert torch.equal(bins.cpu(), torch.from_numpy(vals))
+    for j in range(n_jobs):
+        order = np.lexsort((np.arange(1 << o), -vals[j].astype(np.float64)))[:T]
+        assert tidx[j].cpu().tolist() == [int(i) for i in order]
+        assert np.array_equal(tval[j].cpu().numpy(), vals[j][order])
+
+
+@pytest.mark.parametrize("precision", [1, 0], ids=["tc", "fp32"])
+def test_dd_dense_recursion_full_size(cq, precision):
+    """One dense recursion, the paper's per-recursion workload: 30 active
+    qubits of the 60-qubit blocked brick-wall circuit (2^30 bins, 4 GiB),
+    30 merged.  4096 seeded sampled bins against the FP64 oracle (merge,
+    then Eq. 1 entry by entry), the float64 bin total against 1, and the
+    top-4 selection against torch.topk on the same bins."""
+    import torch
+    from oracle import attribution, dd, fd
+    from workloads.configs import dd_batched
+    w = [x for x in dd_batched() if x.n == 60][0]
+    subs = w.subcircuits
+    var = w.variants()
+    A64 = [attribution.attribute(v, s.w, s.in_local, s.out_local, s.in_edge, s.out_edge) for s, v in zip(subs, var)]
+    att = [cq.cutqc_attribute(s, torch.from_numpy(v).cuda()) for s, v in zip(subs, var)]
+    M, T = 30, 4
+    bins = torch.empty(1 << M, dtype=torch.float32, device="cuda")
+    jobs, n_jobs, _ = cq.cutqc_dd_run_async(subs, att, w.n, M, 1, T, max_jobs=4, bins=bins,
+                                            options={"precision": precision})
+    js = cq.dd_jobs_from_device(jobs, n_jobs)
+    assert len(js) == 1 and js[0].n_active == M
+    assert abs(js[0].bin_sum - 1.0) <= 1e-6
+    active = list(range(M))
+    merged = [dd.merge(a, s.out_qubit, set(active), {}) for a, s in zip(A64, subs)]
+    rng = np.random.default_rng(30)
+    idx = np.unique(rng.integers(0, 1 << M, size=4096))
+    parts = fd.split_original_index(idx, [[q for q in s.out_qubit if q < M] for s in subs])
+    ref = fd.entries(merged, [s.edges for s in subs], w.K, parts)
+    got = bins[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+    err = np.abs(got - ref)
+    assert err.max() <= 1e-6, err.max()
+    assert 0.5 * (1 << M) * err.mean() <= 1e-6
+    tv, ti = torch.topk(bins, T)
+    top_idx = [int(i) for i in js[0].top_idx[:T]]
+    top_val = [float(v) for v in js[0].top_val[:T]]
+    assert top_val == tv.cpu().tolist()
+    assert [float(bins[i]) for i in top_idx] == top_val
+    assert cq.cutqc_device_status() == 0
