@@ -114,11 +114,8 @@ dd_topk_kernel(const float* __restrict__ vals, const int32_t* __restrict__ cidx,
   float lv[TCAP];
   int li[TCAP];
   int cnt = 0;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const float v = __ldg(b + i);
-    const int idx = kCand ? __ldg(ci + i) : (int)i;
-    if (kCand && idx < 0) continue;
-    if (cnt == T && !dd_better(v, idx, lv[T - 1], li[T - 1])) continue;
+  auto offer = [&](float v, int idx) {
+    if (cnt == T && !dd_better(v, idx, lv[T - 1], li[T - 1])) return;
     int pos = cnt < T ? cnt : T - 1;
 #pragma unroll
     for (int u = TCAP - 1; u > 0; --u)
@@ -127,6 +124,37 @@ dd_topk_kernel(const float* __restrict__ vals, const int32_t* __restrict__ cidx,
     lv[pos] = v;
     li[pos] = idx;
     if (cnt < T) ++cnt;
+  };
+  int64_t tail0 = lo;
+  if (!kCand && (((uintptr_t)(b + lo)) & 15) == 0) {
+    // bins: float4 loads, four in flight per thread (the order in which a
+    // thread offers entries does not matter: ties compare indices)
+    constexpr int U = 4;
+    const float4* p4 = reinterpret_cast<const float4*>(b + lo);
+    const int64_t n4 = (hi - lo) >> 2;
+    for (int64_t q = threadIdx.x; q < n4; q += U * (int64_t)blockDim.x) {
+      float4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t qu = q + u * (int64_t)blockDim.x;
+        v[u] = qu < n4 ? __ldg(p4 + qu) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t qu = q + u * (int64_t)blockDim.x;
+        if (qu < n4) {
+          const int i0 = (int)(lo + 4 * qu);
+          offer(v[u].x, i0); offer(v[u].y, i0 + 1); offer(v[u].z, i0 + 2); offer(v[u].w, i0 + 3);
+        }
+      }
+    }
+    tail0 = lo + 4 * n4;
+  }
+  for (int64_t i = tail0 + threadIdx.x; i < hi; i += blockDim.x) {
+    const float v = __ldg(b + i);
+    const int idx = kCand ? __ldg(ci + i) : (int)i;
+    if (kCand && idx < 0) continue;
+    offer(v, idx);
   }
   int head = 0;
   for (int t = 0; t < T; ++t) {
@@ -370,14 +398,15 @@ static int dd_step_impl(int n_sub, const cutqc_subcircuit* s, const int32_t* act
       float* cval = (float*)(cidx + (size_t)n_jobs * chunks * 32);
       const int64_t clen = (nb + chunks - 1) / chunks;
       const int64_t ncand = chunks * topk;
+      const int64_t cthreads = std::min<int64_t>(cap, 512);   // several CTAs per SM: more loads in flight
       if (topk <= 4) {
-        dd_topk_kernel<4, false><<<dim3(n_jobs, (unsigned)chunks), (int)cap, 0, st>>>(bins, nullptr, nb, clen, topk,
-                                                                                     cidx, cval);
+        dd_topk_kernel<4, false><<<dim3(n_jobs, (unsigned)chunks), (int)cthreads, 0, st>>>(bins, nullptr, nb, clen,
+                                                                                          topk, cidx, cval);
         CUTQC_LAUNCH_CHECK("dd_topk_kernel (chunks)");
         dd_topk_kernel<4, true><<<dim3(n_jobs, 1), 1024, 0, st>>>(cval, cidx, ncand, ncand, topk, top_idx, top_val);
       } else {
-        dd_topk_kernel<32, false><<<dim3(n_jobs, (unsigned)chunks), (int)cap, 0, st>>>(bins, nullptr, nb, clen, topk,
-                                                                                      cidx, cval);
+        dd_topk_kernel<32, false><<<dim3(n_jobs, (unsigned)chunks), (int)cthreads, 0, st>>>(bins, nullptr, nb, clen,
+                                                                                           topk, cidx, cval);
         CUTQC_LAUNCH_CHECK("dd_topk_kernel (chunks)");
         dd_topk_kernel<32, true><<<dim3(n_jobs, 1), 1024, 0, st>>>(cval, cidx, ncand, ncand, topk, top_idx, top_val);
       }
