@@ -55,6 +55,16 @@ extern "C" {
 #define CUTQC_PREC_FP16X3_TC 1  /* tcgen05 tensor cores: FP16 hi/lo split operands with
                                    per-row power-of-two scales, hi*hi + hi*lo + lo*hi,
                                    FP32 accumulation in tensor memory */
+#define CUTQC_PREC_FP16X3_TC_PRUNE 2
+                                /* as CUTQC_PREC_FP16X3_TC, and the last contraction
+                                   skips cut terms of negligible weight: term k (an
+                                   assignment of the digits it sums over) is bounded by
+                                   w_k = 2^-K sum_m |A[m][k]| sum_n |B[n][k]| in L1 over
+                                   the outputs; the terms of smallest w_k are skipped
+                                   while their total stays <= CUTQC_PRUNE_TOL, so the
+                                   output moves by at most that in L1 (TV by half).
+                                   The kept terms are chosen on the device. */
+#define CUTQC_PRUNE_TOL 9.313225746154785e-10  /* 2^-30 */
 
 /* Limits of this build. */
 #define CUTQC_MAX_QUBITS 34     /* n of an FD reconstruction (2^34 outputs) */

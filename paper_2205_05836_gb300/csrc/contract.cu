@@ -52,7 +52,8 @@ constexpr int PREP_VEC_MAX = 8;   // float4 per lane kept in registers (K <= 102
 __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows, int64_t K, int64_t Kp,
                             float* __restrict__ out32, __half* __restrict__ hi,
                             __half* __restrict__ lo, float* __restrict__ scale, int64_t src_bstride,
-                            int64_t dst_bstride, int mode, unsigned int* __restrict__ gmax) {
+                            int64_t dst_bstride, int mode, unsigned int* __restrict__ gmax,
+                            const int* __restrict__ cols, const int* __restrict__ meta) {
   // batch item blockIdx.y: source and destinations offset by their strides
   v.src += (int64_t)blockIdx.y * src_bstride;
   if (out32) out32 += (int64_t)blockIdx.y * dst_bstride * Kp;
@@ -68,7 +69,18 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
   const bool contig = v.n_open == 0 && v.shared_dmask == (uint64_t)(C - 1);
   // the shared digits are the lowest digit positions: row r's K values are
   // consecutive from obase (the open digits sit above them)
-  const bool low_shared = v.shared_dmask == (((uint64_t)1 << (2 * v.n_shared)) - 1);
+  const bool low_shared = cols == nullptr && v.shared_dmask == (((uint64_t)1 << (2 * v.n_shared)) - 1);
+  // column list (cut-term pruning): operand column s < meta[0] is source
+  // column cols[s]; columns [meta[0], meta[2]) are zero; the rest of the row
+  // is not written (the GEMM reads meta[2] / 64 k-blocks)
+  int64_t Kw = Kp;      // columns written per row (the row stride stays Kp)
+  __shared__ int scols[kPruneMaxK];
+  if (cols) {
+    K = __ldg(meta);
+    Kw = __ldg(meta + 2);
+    for (int64_t s = threadIdx.x; s < K; s += blockDim.x) scols[s] = __ldg(cols + s);
+    __syncthreads();
+  }
   float wmax = 0.f;    // mode 2: this warp's running max
   for (int64_t r = warp; r < rows; r += nwarps) {
     const int64_t m = r + row0;
@@ -82,10 +94,11 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
     const uint64_t obase = pdep64(open, v.open_dmask);
     const float* row = v.src + (int64_t)x * C;
     auto col = [&](int64_t s) -> int64_t {
+      if (cols) s = scols[s];
       return contig ? s : (int64_t)(obase | pdep64((uint64_t)s, v.shared_dmask));
     };
     if (out32) {
-      for (int64_t s = lane; s < Kp; s += 32) {
+      for (int64_t s = lane; s < Kw; s += 32) {
         float val = 0.f;
         if (s < K) val = __ldg(row + col(s));
         out32[r * Kp + s] = val;
@@ -95,7 +108,7 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
     if (low_shared && hi && (K & 3) == 0 && K <= 128 * PREP_VEC_MAX &&
         ((reinterpret_cast<uintptr_t>(row + obase) & 15) == 0)) {
       const float4* row4 = reinterpret_cast<const float4*>(row + obase);
-      const int64_t K4 = K >> 2, Kp4 = Kp >> 2;
+      const int64_t K4 = K >> 2, Kp4 = Kw >> 2;
       float4 val[PREP_VEC_MAX];
       float mx = 0.f;
 #pragma unroll
@@ -136,6 +149,7 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
     if (mode == 1) {
       mx = __uint_as_float(*gmax);
     } else {
+#pragma unroll 4
       for (int64_t s = lane; s < K; s += 32) mx = fmaxf(mx, fabsf(__ldg(row + col(s))));
       for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
       if (mode == 2) {
@@ -146,13 +160,23 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
     const float sc = pow2_scale(mx);
     const float inv = 1.f / sc;   // exact: power of two
     if (lane == 0 && (mode == 0 || r == 0)) scale[mode == 0 ? r : 0] = sc;
-    for (int64_t s = lane; s < Kp; s += 32) {
-      float y = 0.f;
-      if (s < K) y = __ldg(row + col(s)) * inv;
-      __half h = __float2half_rn(y);
-      __half l = __float2half_rn(y - __half2float(h));
-      hi[r * Kp + s] = h;
-      lo[r * Kp + s] = l;
+    // four gathered loads in flight per lane, then the splits and stores
+    for (int64_t s0 = lane; s0 < Kw; s0 += 128) {
+      float y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t s = s0 + 32 * u;
+        y[u] = s < K ? __ldg(row + col(s)) * inv : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t s = s0 + 32 * u;
+        if (s < Kw) {
+          const __half h = __float2half_rn(y[u]);
+          hi[r * Kp + s] = h;
+          lo[r * Kp + s] = __float2half_rn(y[u] - __half2float(h));
+        }
+      }
     }
   }
   if (mode == 2) {
@@ -261,11 +285,192 @@ __global__ void prep_tr_kernel(OperandView v, RowMap rm, int64_t row0, int64_t r
   }
 }
 
+// ------------------------------------------------ cut-term pruning
+// Term k of a contraction (one assignment of the shared cut digits)
+// contributes alpha * A[m][k] * B[n][k] to output (m, n); summed over the
+// outputs, its absolute contribution is at most
+//   w_k = alpha * sum_m |A[m][k]| * sum_n |B[n][k]|.
+// colw_kernel accumulates sum_rows |operand[row][k]| and max_rows
+// |operand[row][k]| (warp per row, the columns a lane owns in registers --
+// float4 loads when a row's K values are contiguous -- then a block
+// reduction and one atomic per column and block); prune_select_kernel drops
+// the terms of smallest w_k while their total stays <= tol and writes the
+// kept columns in ascending order.  Dropping them changes the output by at
+// most tol in L1 (TV by tol / 2).
+template <int NPL>
+__global__ void __launch_bounds__(256)
+colw_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows, int64_t K, float* __restrict__ colw,
+            unsigned int* __restrict__ colmax) {
+  extern __shared__ float part[];   // [K] sums, then [K] maxima (float bits)
+  unsigned int* pmax = reinterpret_cast<unsigned int*>(part + K);
+  for (int64_t s = threadIdx.x; s < K; s += blockDim.x) {
+    part[s] = 0.f;
+    pmax[s] = 0u;
+  }
+  __syncthreads();
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int64_t C = (int64_t)1 << (2 * v.k);
+  const bool contig = v.n_open == 0 && v.shared_dmask == (uint64_t)(C - 1);
+  const bool low_shared = v.shared_dmask == (((uint64_t)1 << (2 * v.n_shared)) - 1);
+  const bool vec = low_shared && (K & 127) == 0 && ((reinterpret_cast<uintptr_t>(v.src) & 15) == 0);
+  float acc[NPL], mx[NPL];
+#pragma unroll
+  for (int i = 0; i < NPL; ++i) acc[i] = mx[i] = 0.f;
+  for (int64_t r = warp; r < rows; r += nwarps) {
+    const int64_t m = r + row0;
+    const uint64_t xp = (uint64_t)m >> (2 * v.n_open);
+    uint64_t x = xp;
+    if (rm.permute) {
+      x = 0;
+      for (int j = 0; j < rm.n; ++j) x |= ((xp >> j) & 1) << rm.bit[j];
+    }
+    const uint64_t open = (uint64_t)m & (((uint64_t)1 << (2 * v.n_open)) - 1);
+    const uint64_t obase = pdep64(open, v.open_dmask);
+    const float* row = v.src + (int64_t)x * C;
+    if (vec) {
+      // lane owns columns 4 (lane + 32 j) .. +3, j < K / 128
+      const float4* row4 = reinterpret_cast<const float4*>(row + obase);
+#pragma unroll
+      for (int j = 0; j < NPL / 4; ++j) {
+        if (128 * j < K) {
+          const float4 q = __ldg(row4 + lane + 32 * j);
+          const float e[4] = {fabsf(q.x), fabsf(q.y), fabsf(q.z), fabsf(q.w)};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            acc[4 * j + t] += e[t];
+            mx[4 * j + t] = fmaxf(mx[4 * j + t], e[t]);
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < NPL; ++i) {
+        const int64_t s = lane + 32 * i;
+        if (s < K) {
+          const float e = fabsf(__ldg(row + (contig ? s : (int64_t)(obase | pdep64((uint64_t)s, v.shared_dmask)))));
+          acc[i] += e;
+          mx[i] = fmaxf(mx[i], e);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NPL; ++i) {
+    const int64_t s = vec ? 4 * (lane + 32 * (i / 4)) + (i % 4) : lane + 32 * i;
+    if (s < K) {
+      atomicAdd(&part[s], acc[i]);
+      atomicMax(&pmax[s], __float_as_uint(mx[i]));   // non-negative floats order as integers
+    }
+  }
+  __syncthreads();
+  for (int64_t s = threadIdx.x; s < K; s += blockDim.x) {
+    atomicAdd(colw + s, part[s]);
+    if (colmax) atomicMax(colmax + s, pmax[s]);
+  }
+}
+
+constexpr int PRUNE_MAX_K = (int)kPruneMaxK;
+
+// One CTA of 1024 threads (K <= 1024): rank the terms by (w_k, k), prefix
+// sums of the sorted weights, the cut, and the compaction of the kept
+// columns, all by parallel scans in shared memory.  Also the largest |B|
+// over the kept columns (the column operand's scale), into *gmax_b.
+__global__ void __launch_bounds__(1024)
+prune_select_kernel(const float* __restrict__ wa, const float* __restrict__ wb,
+                    const unsigned int* __restrict__ bmax, int K, float alpha, float tol, int* __restrict__ cols,
+                    int* __restrict__ meta, unsigned int* __restrict__ gmax_b) {
+  __shared__ float w[PRUNE_MAX_K];
+  __shared__ float scan[PRUNE_MAX_K];
+  __shared__ int iscan[PRUNE_MAX_K];
+  __shared__ int cut;
+  __shared__ unsigned int kmax;
+  const int k = threadIdx.x;
+  if (k == 0) { cut = 0; kmax = 0u; }
+  if (k < K) w[k] = alpha * wa[k] * wb[k];
+  __syncthreads();
+  int rank = 0;
+  if (k < K) {
+    const float wk = w[k];
+    for (int j = 0; j < K; ++j) {
+      const float wj = w[j];
+      rank += (wj < wk || (wj == wk && j < k)) ? 1 : 0;
+    }
+    scan[rank] = wk;
+  }
+  __syncthreads();
+  // inclusive prefix sums of the ascending weights
+  for (int off = 1; off < K; off <<= 1) {
+    const float add = (k < K && k >= off) ? scan[k - off] : 0.f;
+    __syncthreads();
+    if (k < K) scan[k] += add;
+    __syncthreads();
+  }
+  // the prefix sums are non-decreasing: cut = how many of them are <= tol
+  if (k < K && scan[k] <= tol && (k + 1 == K || scan[k + 1] > tol)) cut = k + 1;
+  __syncthreads();
+  const int keep = (k < K && rank >= cut) ? 1 : 0;
+  if (keep && bmax) atomicMax(&kmax, bmax[k]);
+  if (k < PRUNE_MAX_K) iscan[k] = keep;
+  __syncthreads();
+  for (int off = 1; off < K; off <<= 1) {
+    const int add = (k < K && k >= off) ? iscan[k - off] : 0;
+    __syncthreads();
+    if (k < K) iscan[k] += add;
+    __syncthreads();
+  }
+  if (keep) cols[iscan[k] - 1] = k;
+  if (k == 0) {
+    const int n = K > 0 ? iscan[K - 1] : 0;
+    const int nkb = n > 0 ? (n + 63) / 64 : 1;
+    meta[0] = n;
+    meta[1] = nkb;
+    meta[2] = nkb * 64;
+    meta[3] = cut;
+    if (gmax_b) *gmax_b = kmax;
+  }
+}
+
+int launch_prune_select(const OperandView& va, const int* a_bits, int a_nbits, int64_t a_row0, int64_t a_rows,
+                        const OperandView& vb, const int* b_bits, int b_nbits, int64_t b_rows, float alpha,
+                        double tol, float* colw, int* cols, int* meta, unsigned int* gmax_b, cudaStream_t st) {
+  const int64_t K = va.kdim();
+  if (K > PRUNE_MAX_K) return set_error(CUTQC_EUNSUPPORTED, "cut-term pruning needs K <= %d", PRUNE_MAX_K);
+  // colw: [K] sums of A, [K] sums of B, [K] maxima of B
+  unsigned int* bmax = reinterpret_cast<unsigned int*>(colw + 2 * K);
+  CUTQC_CUDA_TRY(cudaMemsetAsync(colw, 0, 3 * K * sizeof(float), st));
+  auto one = [&](const OperandView& v, const int* bits, int nbits, int64_t row0, int64_t rows, float* out,
+                 unsigned int* omax) -> int {
+    if (rows <= 0) return CUTQC_OK;
+    RowMap rm{};
+    rm.n = nbits;
+    for (int j = 0; j < nbits; ++j) {
+      rm.bit[j] = (int8_t)bits[j];
+      if (bits[j] != j) rm.permute = 1;
+    }
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows * 32 + 255) / 256, (int64_t)sm_count() * 8));
+    const size_t smem = 2 * (size_t)K * sizeof(float);
+    if (K <= 256) colw_kernel<8><<<blocks, 256, smem, st>>>(v, rm, row0, rows, K, out, omax);
+    else colw_kernel<32><<<blocks, 256, smem, st>>>(v, rm, row0, rows, K, out, omax);
+    CUTQC_LAUNCH_CHECK("colw_kernel");
+    return CUTQC_OK;
+  };
+  int rc = one(va, a_bits, a_nbits, a_row0, a_rows, colw, nullptr);
+  if (!rc) rc = one(vb, b_bits, b_nbits, 0, b_rows, colw + K, bmax);
+  if (rc) return rc;
+  // float prefix sums: a margin keeps the exact total of the dropped bounds <= tol
+  prune_select_kernel<<<1, 1024, 0, st>>>(colw, colw + K, bmax, (int)K, alpha, (float)(tol * (1.0 - 1e-5)), cols, meta,
+                                          gmax_b);
+  CUTQC_LAUNCH_CHECK("prune_select_kernel");
+  return CUTQC_OK;
+}
+
 constexpr int64_t PREP_TR_MAX_K = 1024;   // staged tile [K][33] floats: 132 KiB at most
 
 int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int64_t row0, int64_t rows,
                      int64_t Kp, float* out32, __half* hi, __half* lo, float* scale, cudaStream_t st,
-                     int batch, int64_t src_bstride, unsigned int* gmax) {
+                     int batch, int64_t src_bstride, unsigned int* gmax, const int* cols, const int* meta) {
   if (rows <= 0) return CUTQC_OK;
   RowMap rm{};
   rm.n = n_bits;
@@ -280,7 +485,7 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
   if (blocks < 1) blocks = 1;
   if (batch < 1 || batch > 65535) return set_error(CUTQC_EUNSUPPORTED, "batch %d out of range", batch);
   const bool low_open = v.open_dmask == (((uint64_t)1 << (2 * v.n_open)) - 1);
-  if (v.n_open >= 3 && low_open && v.n_shared > 0 && K <= PREP_TR_MAX_K && row0 % 32 == 0) {
+  if (!cols && v.n_open >= 3 && low_open && v.n_shared > 0 && K <= PREP_TR_MAX_K && row0 % 32 == 0) {
     // strided rows: transpose through shared memory (prep_tr_kernel)
     static std::mutex mu;
     static std::set<int> done;
@@ -313,17 +518,20 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
     return CUTQC_OK;
   }
   if (gmax) {
-    // one scale for the whole operand: max pass, then the split
+    // one scale for the whole operand: max pass, then the split (with a
+    // column list the max over the kept columns is already in *gmax)
     if (batch != 1) return set_error(CUTQC_EINVAL, "internal: operand-wide scale needs batch 1");
-    CUTQC_CUDA_TRY(cudaMemsetAsync(gmax, 0, sizeof(unsigned int), st));
-    prep_kernel<<<dim3(blocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride, rows, 2,
-                                                 gmax);
-    CUTQC_LAUNCH_CHECK("prep_kernel (max)");
+    if (!cols) {
+      CUTQC_CUDA_TRY(cudaMemsetAsync(gmax, 0, sizeof(unsigned int), st));
+      prep_kernel<<<dim3(blocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride, rows,
+                                                   2, gmax, cols, meta);
+      CUTQC_LAUNCH_CHECK("prep_kernel (max)");
+    }
     prep_kernel<<<dim3(blocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride, rows, 1,
-                                                 gmax);
+                                                 gmax, cols, meta);
   } else {
     prep_kernel<<<dim3(blocks, batch), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride,
-                                                     rows, 0, nullptr);
+                                                     rows, 0, nullptr, cols, meta);
   }
   CUTQC_LAUNCH_CHECK("prep_kernel");
   return CUTQC_OK;

@@ -34,9 +34,27 @@ struct RowMap {
 // elements (rows scales) further per item.  gmax != null (half mode, batch
 // 1): one scale for the whole operand, written to scale[0]; gmax is a device
 // word of scratch.
+// cols/meta (device, nullable): gather only operand columns cols[0..meta[0])
+// (cut-term pruning), zero-fill to meta[2], leave the rest of each row.
 int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int64_t row0, int64_t rows,
                      int64_t Kp, float* out32, __half* hi, __half* lo, float* scale, cudaStream_t st,
-                     int batch = 1, int64_t src_bstride = 0, unsigned int* gmax = nullptr);
+                     int batch = 1, int64_t src_bstride = 0, unsigned int* gmax = nullptr,
+                     const int* cols = nullptr, const int* meta = nullptr);
+
+// Cut-term pruning of one contraction (row operand rows [a_row0, +a_rows),
+// column operand all b_rows rows): per term k the bound w_k = alpha *
+// sum|A[.][k]| * sum|B[.][k]|; the terms of smallest bound whose total is
+// <= tol are dropped.  colw: 3K floats of scratch; cols: K ints (kept terms,
+// ascending); meta: 4 ints {kept, k-blocks, kept rounded up to 64, dropped};
+// gmax_b: the largest |B| over the kept columns (float bits), the column
+// operand's scale for launch_prep_rows with that column list.
+constexpr int64_t kPruneMaxK = 1024;   // larger contractions are not pruned
+inline size_t prune_scratch_bytes(int64_t K) {
+  return align_up((size_t)K * (3 * sizeof(float) + sizeof(int)) + 4 * sizeof(int), 256);
+}
+int launch_prune_select(const OperandView& va, const int* a_bits, int a_nbits, int64_t a_row0, int64_t a_rows,
+                        const OperandView& vb, const int* b_bits, int b_nbits, int64_t b_rows, float alpha,
+                        double tol, float* colw, int* cols, int* meta, unsigned int* gmax_b, cudaStream_t st);
 
 // float32 CUDA-core GEMM with bit-deposit epilogue.
 // batch > 1: item b uses A + b*a_bstride, B + b*b_bstride, out + b*out_bstride,
@@ -70,6 +88,7 @@ struct PlanStage {
   uint64_t mask_m = 0, mask_n = 0;
   size_t off_result = 0;
   size_t result_elems = 0;
+  size_t off_prune = 0;     // cut-term pruning scratch of the last step (per batch item)
 };
 
 struct ContractionPlan {
@@ -109,9 +128,13 @@ struct TcOperand {
 };
 // Pairs of SMs (tcgen05 cta_group::2) with A resident, for Kp <= 256.
 bool tc_pair_supported(int64_t Kp);
+// num_kb_dev (nullable, device): the number of 64-wide k-blocks to use,
+// read by the kernel (at most Kp / 64); the operands' row stride stays Kp.
 int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
-                        uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st);
+                        uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st,
+                        const int* num_kb_dev = nullptr);
 int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
-                   uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st);
+                   uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st,
+                   const int* num_kb_dev = nullptr);
 
 }  // namespace cutqc

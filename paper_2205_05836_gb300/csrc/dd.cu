@@ -351,8 +351,9 @@ extern "C" int cutqc_dd_step_workspace_size(int n_sub, const cutqc_subcircuit* s
 }
 
 // topk_threads: threads per job of the top-T pass (0: up to 1024).
-// precision: CUTQC_PREC_FP32_SIMT, or CUTQC_PREC_FP16X3_TC for jobs of at
-// least 4 bins whose bins start 16-byte aligned (smaller ones take FP32).
+// precision: CUTQC_PREC_FP32_SIMT, or CUTQC_PREC_FP16X3_TC(_PRUNE) for jobs
+// of at least 4 bins whose bins start 16-byte aligned (smaller ones take
+// FP32).
 static int dd_step_impl(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, const int32_t* bin_bit,
                         int n_jobs, const float* const* merged, float* bins, double* bin_sum, int topk,
                         int32_t* top_idx, float* top_val, void* ws_dev, size_t ws_bytes, void* stream,
@@ -367,10 +368,10 @@ static int dd_step_impl(int n_sub, const cutqc_subcircuit* s, const int32_t* act
     if (!merged[i]) return set_error(CUTQC_EINVAL, "null merged tensor");
   if (topk < 0 || topk > 32) return set_error(CUTQC_EUNSUPPORTED, "topk must be in 0..32");
   if (topk > 0 && (!top_idx || !top_val)) return set_error(CUTQC_EINVAL, "null top-k outputs");
-  if (precision != CUTQC_PREC_FP32_SIMT && precision != CUTQC_PREC_FP16X3_TC)
+  if (precision != CUTQC_PREC_FP32_SIMT && precision != CUTQC_PREC_FP16X3_TC && precision != CUTQC_PREC_FP16X3_TC_PRUNE)
     return set_error(CUTQC_EINVAL, "unknown precision %d", precision);
   const int64_t nb = (int64_t)1 << tot;
-  if (precision == CUTQC_PREC_FP16X3_TC && (nb < 4 || ((uintptr_t)bins & 15) != 0)) precision = CUTQC_PREC_FP32_SIMT;
+  if (precision != CUTQC_PREC_FP32_SIMT && (nb < 4 || ((uintptr_t)bins & 15) != 0)) precision = CUTQC_PREC_FP32_SIMT;
   ContractionPlan plan;
   if ((rc = plan_contraction_batched(in, precision, n_jobs, &plan))) return rc;
   const size_t plan_ws = align_up(plan.ws_bytes, 256);
@@ -635,7 +636,7 @@ int level_layout(int n_sub, const cutqc_subcircuit* s, const LevelShape& L, int 
   size_t step = 0, step_tc = 0;
   int rc = dd_step_ws(n_sub, s, L.active_bits.data(), n_jobs, CUTQC_PREC_FP32_SIMT, &step);
   if (rc) return rc;
-  if ((rc = dd_step_ws(n_sub, s, L.active_bits.data(), n_jobs, CUTQC_PREC_FP16X3_TC, &step_tc))) return rc;
+  if ((rc = dd_step_ws(n_sub, s, L.active_bits.data(), n_jobs, CUTQC_PREC_FP16X3_TC_PRUNE, &step_tc))) return rc;
   step = std::max(step, step_tc);
   R->step_off = take(step);
   R->top_idx_off = take((size_t)n_jobs * 32 * sizeof(int32_t));
@@ -693,7 +694,8 @@ int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att
   if (opt) {
     if (opt->merge_ctas < 0 || opt->merge_ctas > kMergeCtasMax || opt->topk_threads < 0 || opt->topk_threads > 1024)
       return set_error(CUTQC_EINVAL, "options out of range (merge_ctas <= %d, topk_threads <= 1024)", kMergeCtasMax);
-    if (opt->precision != CUTQC_PREC_FP32_SIMT && opt->precision != CUTQC_PREC_FP16X3_TC)
+    if (opt->precision != CUTQC_PREC_FP32_SIMT && opt->precision != CUTQC_PREC_FP16X3_TC &&
+        opt->precision != CUTQC_PREC_FP16X3_TC_PRUNE)
       return set_error(CUTQC_EINVAL, "options: unknown precision %d", opt->precision);
     if (opt->merge_ctas) merge_ctas = opt->merge_ctas;
     topk_threads = opt->topk_threads;

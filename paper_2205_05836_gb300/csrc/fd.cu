@@ -92,7 +92,7 @@ uint64_t digit_mask(const std::vector<int>& all_edges, const std::vector<int>& s
 int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precision, int batch,
                              ContractionPlan* plan, bool ws_upper_bound) {
   if (inputs.empty()) return set_error(CUTQC_EINVAL, "no tensors");
-  if (precision != CUTQC_PREC_FP32_SIMT && precision != CUTQC_PREC_FP16X3_TC)
+  if (precision != CUTQC_PREC_FP32_SIMT && precision != CUTQC_PREC_FP16X3_TC && precision != CUTQC_PREC_FP16X3_TC_PRUNE)
     return set_error(CUTQC_EINVAL, "unknown precision %d", precision);
   std::map<int, int> uses;
   int n = 0;
@@ -203,7 +203,7 @@ int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precisio
       R.pos = B.pos;
       R.pos.insert(R.pos.end(), A.pos.begin(), A.pos.end());
     }
-    if (precision == CUTQC_PREC_FP16X3_TC) {
+    if (precision != CUTQC_PREC_FP32_SIMT) {
       st.Kp = (int64_t)align_up((size_t)st.K, 64);
       for (PlanOperand* op : {&st.opa, &st.opb}) {
         int64_t rows = op->view.rows();
@@ -211,6 +211,8 @@ int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precisio
         op->off_lo = take((size_t)rows * st.Kp * sizeof(__half));
         op->off_scale = take((size_t)rows * sizeof(float) + 16);
       }
+      if (precision == CUTQC_PREC_FP16X3_TC_PRUNE && final_stage && st.K <= kPruneMaxK)
+        st.off_prune = take(prune_scratch_bytes(st.K));
     } else {
       st.Kp = st.K;
       for (PlanOperand* op : {&st.opa, &st.opb})
@@ -305,7 +307,9 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
     const float alpha = stg.final_stage ? alpha_final : 1.0f;
     double* sum_ptr = stg.final_stage ? sum : nullptr;
     const int streaming = stg.final_stage ? 1 : 0;
-    if (precision == CUTQC_PREC_FP16X3_TC) {
+    if (precision != CUTQC_PREC_FP32_SIMT) {
+      const bool prune = precision == CUTQC_PREC_FP16X3_TC_PRUNE && stg.final_stage && stg.K <= kPruneMaxK;
+      const size_t prune_bytes = prune_scratch_bytes(stg.K);
       for (int b = 0; b < batch; ++b) {
         OperandView va = stg.opa.view, vb = stg.opb.view;
         va.src += b * sa_b;
@@ -316,15 +320,28 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
         __half* bh = (__half*)(ws + stg.opb.off_hi) + (size_t)b * stg.N * stg.Kp;
         __half* bl = (__half*)(ws + stg.opb.off_lo) + (size_t)b * stg.N * stg.Kp;
         float* bs = (float*)(ws + stg.opb.off_scale) + (size_t)b * stg.N;
+        int* cols = nullptr;
+        int* meta = nullptr;
+        if (prune) {
+          // the kept terms of this item, chosen on the device
+          uint8_t* pb = ws + stg.off_prune + (size_t)b * prune_bytes;
+          float* colw = (float*)pb;
+          cols = (int*)(colw + 3 * stg.K);
+          meta = cols + stg.K;
+          rc = launch_prune_select(va, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, vb,
+                                   stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), stg.N, alpha,
+                                   CUTQC_PRUNE_TOL, colw, cols, meta, reinterpret_cast<unsigned int*>(bs + 1), st);
+          if (rc) return rc;
+        }
         rc = launch_prep_rows(va, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, stg.Kp, nullptr, ah,
-                              al, as, st);
+                              al, as, st, 1, 0, nullptr, cols, meta);
         if (rc) return rc;
         rc = launch_prep_rows(vb, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp, nullptr,
-                              bh, bl, bs, st, 1, 0, reinterpret_cast<unsigned int*>(bs + 1));
+                              bh, bl, bs, st, 1, 0, reinterpret_cast<unsigned int*>(bs + 1), cols, meta);
         if (rc) return rc;
         TcOperand ta{ah, al, as, M}, tb{bh, bl, bs, stg.N};
         rc = launch_tc_gemm(ta, tb, stg.Kp, alpha, stg.mask_m, stg.mask_n, dst + b * dst_b,
-                            sum_ptr ? sum_ptr + b : nullptr, streaming, st);
+                            sum_ptr ? sum_ptr + b : nullptr, streaming, st, prune ? meta + 1 : nullptr);
         if (rc) return rc;
       }
       continue;

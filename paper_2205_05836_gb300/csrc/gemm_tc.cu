@@ -72,6 +72,7 @@ struct TcArgs {
   const float* sb;
   int64_t M, N;
   int num_kb;
+  const int* num_kb_dev;  // nullable: k-blocks in use, read on the device (<= num_kb)
   int num_m_blk;
   int64_t num_tiles;
   float alpha;
@@ -124,6 +125,9 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
   SmemTail* tail = reinterpret_cast<SmemTail*>(smem + STAGES * STAGE_BYTES + STG_BYTES);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  // k-blocks in use: a count chosen on the device (cut-term pruning) when
+  // given, never more than the operands hold
+  const int num_kb = args.num_kb_dev ? max(1, min(args.num_kb, __ldg(args.num_kb_dev))) : args.num_kb;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -166,7 +170,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
         const int mb = (int)(tile % args.num_m_blk);
         const int nb = (int)(tile / args.num_m_blk);
         bool ok = true;
-        for (int kb = 0; kb < args.num_kb; ++kb) {
+        for (int kb = 0; kb < num_kb; ++kb) {
           if (!mbar_wait(smem_u32(&tail->empty[stage]), phase ^ 1u, abort_flag)) { fail(); ok = false; break; }
           uint8_t* st = smem + stage * STAGE_BYTES;
           const uint32_t bar = smem_u32(&tail->full[stage]);
@@ -196,7 +200,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
       bool any = false;
       for (int64_t tile = blockIdx.x; tile < args.num_tiles && !*abort_flag; tile += gridDim.x) {
         bool ok = true;
-        for (int kb = 0; kb < args.num_kb; ++kb) {
+        for (int kb = 0; kb < num_kb; ++kb) {
           const int ks = kb % KB_PER_CHUNK;
           if (ks == 0) {
             if (!mbar_wait(smem_u32(&tail->cempty[buf]), buf_phase ^ 1u, abort_flag)) { fail(); ok = false; break; }
@@ -218,7 +222,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
           }
           any = true;
           umma_commit(smem_u32(&tail->empty[stage]));
-          if (ks == KB_PER_CHUNK - 1 || kb == args.num_kb - 1) {
+          if (ks == KB_PER_CHUNK - 1 || kb == num_kb - 1) {
             umma_commit(smem_u32(&tail->cfull[buf]));
             if (++buf == NBUF) { buf = 0; buf_phase ^= 1u; }
           }
@@ -240,7 +244,7 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
     uint32_t buf_phase = 0;
     double local = 0.0;
     const int row = g * 32 + lane;
-    const int num_chunks = (args.num_kb + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
+    const int num_chunks = (num_kb + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
     const float sbg = __ldg(args.sb);
     float* stg0 = stg_all + warp * (EPI_COLS / 32) * BLK_FLOATS;
     float tot[EPI_COLS];
@@ -389,9 +393,10 @@ int make_map(CUtensorMap* map, const __half* base, int64_t rows, int64_t Kp, int
 }  // namespace
 
 int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
-                   uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st) {
+                   uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st, const int* num_kb_dev) {
   if (a.rows <= 0 || b.rows <= 0) return CUTQC_OK;
-  if (tc_pair_supported(Kp)) return launch_tc_pair_gemm(a, b, Kp, alpha, mask_m, mask_n, out, sum, streaming, st);
+  if (tc_pair_supported(Kp))
+    return launch_tc_pair_gemm(a, b, Kp, alpha, mask_m, mask_n, out, sum, streaming, st, num_kb_dev);
   if (Kp % BK != 0 || Kp <= 0) return set_error(CUTQC_EINVAL, "tensor-core K must be a multiple of %d", BK);
   if (Kp / BK > (1 << 20)) return set_error(CUTQC_EUNSUPPORTED, "K too large");
   TcMaps maps;
@@ -406,6 +411,7 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alp
   args.M = a.rows;
   args.N = b.rows;
   args.num_kb = (int)(Kp / BK);
+  args.num_kb_dev = num_kb_dev;
   const int64_t mblk = (a.rows + BM - 1) / BM, nblk = (b.rows + BN - 1) / BN;
   if (mblk > 0x7fffffff || nblk > 0x7fffffff) return set_error(CUTQC_EUNSUPPORTED, "too many tiles");
   args.num_m_blk = (int)mblk;

@@ -94,6 +94,7 @@ struct PairArgs {
   const float* sb;
   int64_t M, N;
   int num_kb;
+  const int* num_kb_dev;  // nullable: k-blocks in use, read on the device (<= num_kb)
   int num_mp;           // 256-row blocks of A
   int64_t num_nt;       // 128-column tiles
   int64_t tiles_per_item;
@@ -230,6 +231,9 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
   Tail* tail = reinterpret_cast<Tail*>(smem + ALO_BYTES + STAGES * STAGE_BYTES + STG_BYTES);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  // k-blocks in use: a count chosen on the device (cut-term pruning) when
+  // given, never more than the operands hold
+  const int num_kb = args.num_kb_dev ? max(1, min(args.num_kb, __ldg(args.num_kb_dev))) : args.num_kb;
   const uint32_t rank = cta_rank();
   const int64_t pair = blockIdx.x >> 1;
   const int64_t num_pairs = gridDim.x >> 1;
@@ -282,7 +286,7 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
         for (int64_t nt = t0; nt < t1 && ok; ++nt) {
           int brow = (int)(nt * BN) + (int)rank * BNH;
           if (brow >= args.N) brow = 0;     // columns beyond N are never stored
-          for (int kb = 0; kb < args.num_kb; ++kb) {
+          for (int kb = 0; kb < num_kb; ++kb) {
             if (!mbar_wait(smem_u32(&tail->empty[stage]), phase ^ 1u, abort_flag)) { fail(); ok = false; break; }
             uint8_t* st = b_smem + stage * STAGE_BYTES;
             const uint32_t lead_full = map_to_rank(smem_u32(&tail->full[stage]), 0);
@@ -322,8 +326,8 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
         aphase ^= 1u;
         tc_fence_after();
         for (int64_t nt = t0; nt < t1 && ok; ++nt) {
-          for (int kb0 = 0; kb0 < args.num_kb; kb0 += KB_PER_CHUNK, ++c) {
-            const int nkb = args.num_kb - kb0 < KB_PER_CHUNK ? args.num_kb - kb0 : KB_PER_CHUNK;
+          for (int kb0 = 0; kb0 < num_kb; kb0 += KB_PER_CHUNK, ++c) {
+            const int nkb = num_kb - kb0 < KB_PER_CHUNK ? num_kb - kb0 : KB_PER_CHUNK;
             if ((int)(c & 1) != j) { g += nkb; continue; }
             const int buf = (int)(c % NBUF);
             const uint32_t buf_phase = (uint32_t)((c / NBUF) & 1);
@@ -413,13 +417,13 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
         // loads rows from 0, which are never stored)
         int arow = mp * 2 * BM + (int)rank * BM;
         if (arow >= args.M) arow = 0;
-        for (int kb = 0; kb < args.num_kb; ++kb)
+        for (int kb = 0; kb < num_kb; ++kb)
           tma_load_pair(smem_u32(alo_smem + kb * A_KB_BYTES), &maps.a_lo, kb * BK, arow, lead_afull);
       }
       {
         const uint4* row = reinterpret_cast<const uint4*>(args.a_hi + (mvalid ? m : 0) * args.Kp);
         const uint32_t tbase = tmem_base + ((uint32_t)(g * 32) << 16);
-        for (int kb = h; kb < args.num_kb; kb += 2) {
+        for (int kb = h; kb < num_kb; kb += 2) {
           uint32_t r[32];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
@@ -438,14 +442,14 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
       if (lane == 0) {
         // CTA 0's warp 0 arrives with the byte count of both CTAs' A lo loads
         if (rank == 0 && warp == 0)
-          mbar_expect_tx(smem_u32(&tail->afull), (uint32_t)(2 * args.num_kb * A_KB_BYTES));
+          mbar_expect_tx(smem_u32(&tail->afull), (uint32_t)(2 * num_kb * A_KB_BYTES));
         else
           remote_arrive_release_cluster(lead_afull);
       }
       for (int64_t nt = t0; nt < t1 && ok; ++nt) {
 #pragma unroll
         for (int i = 0; i < EPI_COLS; ++i) tot[i] = 0.f;
-        for (int ch = 0; ch < (args.num_kb + KB_PER_CHUNK - 1) / KB_PER_CHUNK; ++ch) {
+        for (int ch = 0; ch < (num_kb + KB_PER_CHUNK - 1) / KB_PER_CHUNK; ++ch) {
           if (!mbar_wait(smem_u32(&tail->cfull[buf]), buf_phase, abort_flag)) { fail(); ok = false; break; }
           tc_fence_after();
           __syncwarp();
@@ -608,7 +612,8 @@ int64_t pick_tiles_per_item(int64_t num_mp, int64_t num_nt, int64_t pairs) {
 bool tc_pair_supported(int64_t Kp) { return Kp > 0 && Kp % BK == 0 && Kp / BK <= MAX_KB; }
 
 int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
-                        uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st) {
+                        uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st,
+                        const int* num_kb_dev) {
   if (a.rows <= 0 || b.rows <= 0) return CUTQC_OK;
   if (!tc_pair_supported(Kp)) return set_error(CUTQC_EINVAL, "paired tensor-core K must be 64..256, a multiple of 64");
   if (a.rows >= ((int64_t)1 << 30) || b.rows >= ((int64_t)1 << 30)) return set_error(CUTQC_EUNSUPPORTED, "too many rows");
@@ -626,6 +631,7 @@ int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, floa
   args.M = a.rows;
   args.N = b.rows;
   args.num_kb = (int)(Kp / BK);
+  args.num_kb_dev = num_kb_dev;
   const int64_t num_mp = (a.rows + 2 * BM - 1) / (2 * BM);
   args.num_mp = (int)num_mp;
   args.num_nt = (b.rows + BN - 1) / BN;

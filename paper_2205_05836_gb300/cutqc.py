@@ -19,7 +19,8 @@ HEADERS = [HEADER, os.path.join(os.path.dirname(HERE), "include", "cutqc_mlp.h")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 F64, F32 = 0, 1
 ORDER_KRON, ORDER_ORIGINAL = 0, 1
-PREC_FP32_SIMT, PREC_FP16X3_TC = 0, 1
+PREC_FP32_SIMT, PREC_FP16X3_TC, PREC_FP16X3_TC_PRUNE = 0, 1, 2
+PRUNE_TOL = 2.0 ** -30   # L1 bound of the cut terms the pruned precision may skip
 
 
 class CutqcError(RuntimeError):

@@ -68,7 +68,7 @@ def test_attribution_matches_oracle(cq, name, cut):
             assert np.abs(g - r).max() <= 4e-7 * scale, name
 
 
-@pytest.mark.parametrize("precision", [0, 1], ids=["simt", "tc"])
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["simt", "tc", "tc_prune"])
 @pytest.mark.parametrize("order", [0, 1], ids=["kron", "original"])
 @pytest.mark.parametrize("name,cut", CASES, ids=[c[0] for c in CASES])
 def test_fd_matches_oracle(cq, name, cut, precision, order):
@@ -214,9 +214,10 @@ def test_fd_two_subcircuit_30q_full_size(cq):
 
 def test_fd_chain_32q_full_size(cq):
     """32-qubit AQFT chain (4 subcircuits, K = 12, 2^32 outputs = 16 GiB) on
-    the tensor-core path, in both output orders: sum p against 1, and 2^14
-    seeded uniformly sampled outputs against the FP64 oracle (max error, and
-    the total variation they estimate)."""
+    the tensor-core path, with and without cut-term pruning, in both output
+    orders: sum p against 1, and 2^14 seeded uniformly sampled outputs
+    against the FP64 oracle (max error, and the total variation they
+    estimate)."""
     import torch
     from oracle import fd
     from workloads.configs import fd_chain
@@ -228,9 +229,9 @@ def test_fd_chain_32q_full_size(cq):
     edges = [s.edges for s in subs]
     rng = np.random.default_rng(2024)
     idx = np.unique(rng.integers(0, 1 << w.n, size=1 << 14))
-    for order in (0, 1):
+    for order, precision in ((0, 1), (1, 1), (0, 2), (1, 2)):
         total = torch.zeros(1, dtype=torch.float64, device="cuda")
-        out, _ = cq.cutqc_reconstruct_fd(subs, att, order, 1, sum_out=total)
+        out, _ = cq.cutqc_reconstruct_fd(subs, att, order, precision, sum_out=total)
         torch.cuda.synchronize()
         assert out.numel() == 1 << 32
         assert abs(total.item() - 1.0) <= 1e-6
@@ -297,4 +298,45 @@ def test_fd_empty_row_range(cq, precision):
     with pytest.raises(cq.CutqcError) as e:
         cq.cutqc_reconstruct_fd(subs, att, 0, precision, row_begin=3, row_end=2, out=sentinel)
     assert e.value.code == cq.EINVAL
+    assert cq.cutqc_device_status() == 0
+
+
+@pytest.mark.parametrize("tiny", [1e-24, 1e-3], ids=["negligible", "significant"])
+def test_fd_prune_drops_only_negligible_terms(cq, tiny):
+    """Cut-term pruning on a two-subcircuit contraction whose column operand
+    has most cut-term columns scaled by `tiny`: with 1e-24 those terms weigh
+    far below 2^-30 and are skipped, with 1e-3 they are kept.  Either way
+    every output matches the FP64 oracle of the full Eq. 1 sum within the
+    split-precision bound plus the pruning bound, and the pruned result
+    differs from the unpruned one by at most 2^-30 in L1."""
+    import torch
+    from oracle import fd
+    from types import SimpleNamespace
+    rng = np.random.default_rng(11)
+    k, oa, ob = 4, 9, 12
+    edges = list(range(k))
+    s0 = SimpleNamespace(w=oa + k, in_local=[], in_edge=[], out_local=list(range(oa, oa + k)), out_edge=edges,
+                         out_qubit=list(range(ob, ob + oa)), edges=edges, o=oa)
+    s1 = SimpleNamespace(w=ob, in_local=list(range(k)), in_edge=edges, out_local=[], out_edge=[],
+                         out_qubit=list(range(ob)), edges=edges, o=ob)
+    A0 = np.abs(rng.standard_normal((1 << oa, 4 ** k))) / (1 << oa)
+    A1 = rng.standard_normal((1 << ob, 4 ** k)) / (1 << ob)
+    keep = rng.choice(4 ** k, size=40, replace=False)
+    scale = np.full(4 ** k, tiny)
+    scale[keep] = 1.0
+    A1 = A1 * scale
+    A = [a.astype(np.float32).astype(np.float64) for a in (A0, A1)]
+    ref = fd.reconstruct_kron(A, [edges, edges], k)
+    bound = fd.reconstruct_kron([np.abs(a) for a in A], [edges, edges], k)
+    att = [torch.from_numpy(a.astype(np.float32)).cuda() for a in A]
+    full, _ = cq.cutqc_reconstruct_fd([s0, s1], att, 0, cq.PREC_FP16X3_TC)
+    pruned, _ = cq.cutqc_reconstruct_fd([s0, s1], att, 0, cq.PREC_FP16X3_TC_PRUNE)
+    torch.cuda.synchronize()
+    f = full.cpu().numpy().astype(np.float64)
+    p = pruned.cpu().numpy().astype(np.float64)
+    assert (np.abs(f - ref) <= 2.0 ** -16 * bound + 1e-30).all()
+    assert (np.abs(p - ref) <= 2.0 ** -16 * bound + cq.PRUNE_TOL).all()
+    assert np.abs(p - f).sum() <= cq.PRUNE_TOL + 2.0 ** -16 * bound.sum()
+    if tiny > 1e-10:
+        assert np.array_equal(p, f)      # nothing skipped: the same kernels on the same operands
     assert cq.cutqc_device_status() == 0
