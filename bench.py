@@ -312,7 +312,7 @@ def run(args):
     att_ws = [torch.empty(max(1, cq.cutqc_attribute_workspace_size(s)), dtype=torch.uint8, device=dev) for s in subs]
     n_out = 1 << w.n
     out = torch.empty(n_out, dtype=torch.float32, device=dev)
-    prec = cq.PREC_FP16X3_TC if args.precision == "tc" else cq.PREC_FP32_SIMT
+    prec = {"tc": cq.PREC_FP16X3_TC, "tc_prune": cq.PREC_FP16X3_TC_PRUNE, "simt": cq.PREC_FP32_SIMT}[args.precision]
     fd_ws = torch.empty(max(1, cq.cutqc_reconstruct_fd_workspace_size(subs, prec)), dtype=torch.uint8, device=dev)
     total = torch.zeros(1, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -396,7 +396,7 @@ def run(args):
     M, N = 1 << subs[0].o, 1 << subs[1].o
     Kg = 4 ** w.K
     alg_flops = 2.0 * M * N * Kg                    # Eq. 1, one pass
-    exec_flops = 3 * alg_flops if prec == cq.PREC_FP16X3_TC else alg_flops
+    exec_flops = 3 * alg_flops if prec != cq.PREC_FP32_SIMT else alg_flops   # pruned: an upper bound
     pk = peaks()
     # algorithmic bytes of one FD launch sequence: read both attributed
     # tensors once, write 4 B per probability.  At the peaks these bytes take
@@ -418,10 +418,12 @@ def run(args):
                 "fd_ms": fd_ms, "attribution_ms": att_ms}
     value = ws * n_out / (ms * 1e-3)
     # library kernels per step: one attribution pass per subcircuit side that
-    # carries cuts (init and/or meas), three operand-prep passes and the
-    # tcgen05 GEMM (the FP64 total's zeroing is a torch fill, not counted)
+    # carries cuts (init and/or meas), then the contraction: tc = three
+    # operand-prep passes and the tcgen05 GEMM; tc_prune = two column-weight
+    # passes, the selection, two prep passes and the GEMM; simt = two preps and
+    # the CUDA-core GEMM (the FP64 total's zeroing is a torch fill, not counted)
     launches_per_step = sum((len(s.in_local) > 0) + (len(s.out_local) > 0) for s in subs) + \
-        (4 if prec == cq.PREC_FP16X3_TC else 3)
+        {cq.PREC_FP16X3_TC: 4, cq.PREC_FP16X3_TC_PRUNE: 6, cq.PREC_FP32_SIMT: 3}[prec]
 
     # end to end through the C ABI from pinned host buffers: every step
     # uploads its variants, attributes, reconstructs and downloads the whole
@@ -764,23 +766,69 @@ def dd_dense_extras(dev, cq, M=30, T=4, reps=5):
 
 
 def run_profile_case(args):
-    """The benchmark's kernels on a 2048-row slice of the same workload
-    (1 GiB of output): one warm-up pass and one profiled pass, for ncu."""
+    """The benchmark's kernels once after one warm-up pass, for ncu.
+    Workloads: fd_two_sub -- a row slice (args.profile_rows rows of the last
+    contraction, 1 GiB of output at 2048) of the 30-qubit two-subcircuit
+    reconstruction; fd_chain -- the whole 32-qubit chain (2^32 outputs, 16
+    GiB: for one-pass launch lists only); fd_chain_slice -- a row slice of
+    the chain's last contraction; dd_dense -- one 2^30-bin recursion of the
+    60-qubit DD circuit; dd_batched -- Algorithm 1 on the three DD circuits
+    (16 active qubits, top 4, breadth first)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2205_05836_gb300 import cutqc as cq
-    from workloads.configs import fd_two_sub
-    w = fd_two_sub()
-    subs = w.subcircuits
-    var = [torch.from_numpy(v).cuda() for v in w.variants()]
-    prec = cq.PREC_FP16X3_TC if args.precision == "tc" else cq.PREC_FP32_SIMT
-    for _ in range(2):
-        att = [cq.cutqc_attribute(s, v) for s, v in zip(subs, var)]
-        out, _ = cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_KRON, prec, row_begin=0, row_end=args.profile_rows)
-    torch.cuda.synchronize()
-    print(json.dumps({"profile_case": WORKLOAD, "rows": args.profile_rows, "outputs": out.numel(),
-                      "sum": float(out.double().sum())}))
+    prec = {"tc": cq.PREC_FP16X3_TC, "tc_prune": cq.PREC_FP16X3_TC_PRUNE, "simt": cq.PREC_FP32_SIMT}[args.precision]
+    wl = args.profile_workload
+    info = {"profile_case": wl, "precision": args.precision}
+    if wl in ("fd_two_sub", "fd_chain", "fd_chain_slice"):
+        from workloads.configs import fd_chain, fd_two_sub
+        w = fd_two_sub() if wl == "fd_two_sub" else fd_chain()
+        subs = w.subcircuits
+        var = [torch.from_numpy(v).cuda() for v in w.variants()]
+        ranged = wl != "fd_chain"
+        out = None
+        if not ranged:
+            out = torch.empty(1 << w.n, dtype=torch.float32, device="cuda")
+        ws = torch.empty(max(1, cq.cutqc_reconstruct_fd_workspace_size(subs, prec)), dtype=torch.uint8, device="cuda")
+        total = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            att = [cq.cutqc_attribute(s, v) for s, v in zip(subs, var)]
+            total.zero_()
+            if ranged:
+                out, _ = cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_KRON, prec, row_begin=0,
+                                                 row_end=args.profile_rows, ws=ws, sum_out=total)
+            else:
+                cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_KRON, prec, out=out, ws=ws, sum_out=total)
+        torch.cuda.synchronize()
+        info.update({"workload": w.name, "rows": args.profile_rows if ranged else None, "outputs": out.numel(),
+                     "sum": total.item()})
+    elif wl == "dd_dense":
+        from workloads.configs import dd_batched
+        w = [x for x in dd_batched() if x.n == 60][0]
+        subs = w.subcircuits
+        att = [cq.cutqc_attribute(s, torch.from_numpy(v).cuda()) for s, v in zip(subs, w.variants())]
+        ws = torch.empty(cq.cutqc_dd_run_workspace_size(subs, w.n, 30, 4), dtype=torch.uint8, device="cuda")
+        bins = torch.empty(1 << 30, dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            jobs, n_jobs, _ = cq.cutqc_dd_run_async(subs, att, w.n, 30, 1, 4, max_jobs=4, bins=bins, ws=ws,
+                                                    options={"precision": prec})
+        js = cq.dd_jobs_from_device(jobs, n_jobs)
+        info.update({"workload": w.name, "bins": 1 << 30, "bin_sum": js[0].bin_sum})
+    else:
+        from workloads.configs import dd_batched
+        runs = []
+        for w in dd_batched():
+            subs = w.subcircuits
+            att = [cq.cutqc_attribute(s, torch.from_numpy(v).cuda()) for s, v in zip(subs, w.variants())]
+            ws = torch.empty(cq.cutqc_dd_run_workspace_size(subs, w.n, 16, 4), dtype=torch.uint8, device="cuda")
+            runs.append((w, subs, att, ws))
+        for _ in range(2):
+            for w, subs, att, ws in runs:
+                cq.cutqc_dd_run_async(subs, att, w.n, 16, 6, 4, max_jobs=64, ws=ws, options={"precision": prec})
+        torch.cuda.synchronize()
+        info.update({"workload": [r[0].name for r in runs]})
+    print(json.dumps(info))
 
 
 def main():
@@ -789,13 +837,15 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tc", choices=["tc", "simt"])
+    ap.add_argument("--precision", default="tc", choices=["tc", "tc_prune", "simt"])
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the DD and cut-scorer measurements")
     ap.add_argument("--profile-case", action="store_true",
                     help="run the kernels once on a row slice (for ncu) and exit")
     ap.add_argument("--profile-rows", type=int, default=2048)
+    ap.add_argument("--profile-workload", default="fd_two_sub",
+                    choices=["fd_two_sub", "fd_chain", "fd_chain_slice", "dd_dense", "dd_batched"])
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
