@@ -33,46 +33,72 @@ struct Kahan {
   }
 };
 
-// grid: x = merged row a, y = job, z = slice of the merged index range
-// (2^log_slices slices; slice s writes its partial sums to
-// out + s * n_jobs * rows_a * C, reduced by dd_merge_reduce when there are
-// several).  zoom value of job j: zoom_dev ? zoom_dev[j] : zoom_val.  Threads
-// split columns and, when there are few columns, the slice's merged indices;
-// sub-slices are combined through shared memory.
+// Zoom source of a merge launch: either a per-job array of zoom values over
+// the subcircuit's output bits (zoom_dev), or the level's job records, from
+// which each job's value is derived (bit t = the fixed value of output qubit
+// outq[t], for the qubits below lo), or one constant (zoom_val).
+struct ZoomFromJobs {
+  const cutqc_dd_job_result* jobs;   // null: not used
+  int o, lo;
+  int8_t outq[32];
+};
+
+__device__ __forceinline__ uint64_t job_zoom(const ZoomFromJobs& zj, int job) {
+  const cutqc_dd_job_result& J = zj.jobs[job];
+  uint64_t z = 0;
+  for (int t = 0; t < zj.o; ++t) {
+    const int q = zj.outq[t];
+    if (q < zj.lo && ((J.zoom_val[q >> 6] >> (q & 63)) & 1)) z |= (uint64_t)1 << t;
+  }
+  return z;
+}
+
+// grid: x = CTAs walking the (merged row a, job) pairs, z = slice of the
+// merged index range (2^log_slices slices; slice s writes its partial sums
+// to out + s * n_jobs * rows_a * C, reduced by dd_merge_reduce when there
+// are several).  Threads split columns and, when there are few columns, the
+// slice's merged indices; sub-slices are combined through shared memory.
 __global__ void __launch_bounds__(256)
 dd_merge_kernel(const float* __restrict__ att, int k, uint64_t act_mask, uint64_t merged_mask, uint64_t zoom_mask,
-                uint64_t zoom_val, const uint64_t* __restrict__ zoom_dev, int n_merged, int log_slices,
-                float* __restrict__ out) {
+                uint64_t zoom_val, const uint64_t* __restrict__ zoom_dev, const ZoomFromJobs zj, int n_jobs,
+                int64_t rows_a, int n_merged, int log_slices, float* __restrict__ out) {
   __shared__ float red[256];
   const int64_t C = (int64_t)1 << (2 * k);
-  const int a = blockIdx.x;
-  const int job = blockIdx.y;
-  const int64_t rows_a = (int64_t)gridDim.x;
-  const uint64_t z = (zoom_dev ? __ldg(zoom_dev + job) : zoom_val) & zoom_mask;
-  const uint64_t base = pdep64((uint64_t)a, act_mask) | z;
   const int64_t Mper = (int64_t)1 << (n_merged - log_slices);
   const int64_t m0 = (int64_t)blockIdx.z * Mper;
-  float* dst = out + (((int64_t)blockIdx.z * gridDim.y + job) * rows_a + a) * C;
   const int cw = (int)(C < 256 ? C : 256);
   const int slices = 256 / cw;
   const int c_local = threadIdx.x % cw;
   const int slice = threadIdx.x / cw;
-  for (int64_t c0 = 0; c0 < C; c0 += cw) {
-    Kahan acc;
-    if (slice < slices)
-      for (int64_t m = m0 + slice; m < m0 + Mper; m += slices) {
-        const uint64_t x = base | pdep64((uint64_t)m, merged_mask);
-        acc.add(__ldg(att + (int64_t)x * C + c0 + c_local));
+  for (int64_t ra = blockIdx.x; ra < rows_a * n_jobs; ra += gridDim.x) {
+    const int job = (int)(ra / rows_a);
+    const int64_t a = ra - (int64_t)job * rows_a;
+    const uint64_t z = (zj.jobs ? job_zoom(zj, job) : zoom_dev ? __ldg(zoom_dev + job) : zoom_val) & zoom_mask;
+    const uint64_t base = pdep64((uint64_t)a, act_mask) | z;
+    float* dst = out + (((int64_t)blockIdx.z * n_jobs + job) * rows_a + a) * C;
+    for (int64_t c0 = 0; c0 < C; c0 += cw) {
+      Kahan acc;
+      if (slice < slices)
+        for (int64_t m = m0 + slice; m < m0 + Mper; m += slices) {
+          const uint64_t x = base | pdep64((uint64_t)m, merged_mask);
+          acc.add(__ldg(att + (int64_t)x * C + c0 + c_local));
+        }
+      red[threadIdx.x] = acc.s;
+      __syncthreads();
+      if (slice == 0) {
+        float s = red[c_local];
+        for (int q = 1; q < slices; ++q) s += red[q * cw + c_local];
+        dst[c0 + c_local] = s;
       }
-    red[threadIdx.x] = acc.s;
-    __syncthreads();
-    if (slice == 0) {
-      float s = red[c_local];
-      for (int q = 1; q < slices; ++q) s += red[q * cw + c_local];
-      dst[c0 + c_local] = s;
+      __syncthreads();
     }
-    __syncthreads();
   }
+}
+
+// CTAs of a merge launch: enough to fill the GPU once, each walking rows
+inline unsigned merge_grid(int64_t rows, int slices) {
+  const int64_t cap = std::max<int64_t>(1, (int64_t)sm_count() * 8 / std::max(1, slices));
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(rows, cap));
 }
 
 // out[e] = sum over the S slices of part[s * E + e], in slice order.
@@ -113,6 +139,8 @@ dd_topk_kernel(const float* __restrict__ vals, const int32_t* __restrict__ cidx,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float lv[TCAP];
   int li[TCAP];
+#pragma unroll
+  for (int u = 0; u < TCAP; ++u) { lv[u] = -INFINITY; li[u] = -1; }   // read only once filled
   int cnt = 0;
   auto offer = [&](float v, int idx) {
     if (cnt == T && !dd_better(v, idx, lv[T - 1], li[T - 1])) return;
@@ -254,8 +282,9 @@ int launch_merge(const cutqc_subcircuit* s, const float* att, uint64_t act, uint
   if (a > 30) return set_error(CUTQC_EUNSUPPORTED, "too many active bits");
   if ((int64_t)1 << a > 0x7fffffffLL) return set_error(CUTQC_EUNSUPPORTED, "too many rows");
   if (n_jobs < 1 || n_jobs > 65535) return set_error(CUTQC_EINVAL, "n_jobs out of range");
-  dd_merge_kernel<<<dim3(1u << a, n_jobs, 1), 256, 0, st>>>(att, k, act, mrg, zm, zv, zoom_dev,
-                                                             __builtin_popcountll(mrg), 0, out);
+  const int64_t rows_a = (int64_t)1 << a;
+  dd_merge_kernel<<<dim3(merge_grid(rows_a * n_jobs, 1), 1, 1), 256, 0, st>>>(
+      att, k, act, mrg, zm, zv, zoom_dev, ZoomFromJobs{}, n_jobs, rows_a, __builtin_popcountll(mrg), 0, out);
   CUTQC_LAUNCH_CHECK("dd_merge_kernel");
   return CUTQC_OK;
 }
@@ -438,33 +467,6 @@ extern "C" int cutqc_sum_f64(const float* x, int64_t n, double* sum, void* strea
 namespace cutqc {
 namespace {
 
-// Subcircuit output qubits for the device-side selection (kernel parameter).
-struct DDTables {
-  int n_sub;
-  int8_t o[64];
-  int8_t outq[64][32];
-};
-struct ZoomPtrs {
-  uint64_t* p[64];
-};
-
-// Zoom value of every job of a level for every subcircuit: bit t of
-// zoom[i][j] = the fixed value of subcircuit i's output qubit t, for the
-// qubits below lo (the zoomed ones).
-__global__ void dd_zoom_kernel(const __grid_constant__ DDTables tab, const cutqc_dd_job_result* __restrict__ jobs,
-                               int nj, int lo, const __grid_constant__ ZoomPtrs zp) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= tab.n_sub * nj) return;
-  const int i = idx / nj, j = idx % nj;
-  const cutqc_dd_job_result& J = jobs[j];
-  uint64_t z = 0;
-  for (int t = 0; t < tab.o[i]; ++t) {
-    const int q = tab.outq[i][t];
-    if (q < lo && ((J.zoom_val[q >> 6] >> (q & 63)) & 1)) z |= (uint64_t)1 << t;
-  }
-  zp.p[i][j] = z;
-}
-
 struct LevelInfo {
   int level, depth, n_active;
   int8_t active[32];
@@ -501,15 +503,27 @@ __global__ void dd_select_kernel(cutqc_dd_job_result* __restrict__ jobs, int job
     return;
   }
   __shared__ int cj[32], cb[32], cnt_s;
+  // the level's candidates (nj * T of them, job order) loaded in parallel
+  __shared__ int kb[1024];
+  __shared__ float kv[1024];
+  const int ncand = nj * T <= 1024 ? nj * T : 1024;
+  for (int q = lane; q < ncand; q += 32) {
+    const int j = q / T;
+    const int b = jobs[job0 + j].level >= 0 ? tidx[q] : -1;
+    kb[q] = b;
+    kv[q] = b >= 0 ? tval[q] : 0.f;
+  }
+  __syncwarp();
   if (lane == 0) {
     float cv[32];
     int cnt = 0;
     for (int j = 0; j < nj; ++j) {
-      if (jobs[job0 + j].level < 0) continue;
       for (int t = 0; t < T; ++t) {
-        const int b = tidx[(int64_t)j * T + t];
+        const int q = j * T + t;
+        if (q >= ncand) break;
+        const int b = kb[q];
         if (b < 0) continue;
-        const float v = tval[(int64_t)j * T + t];
+        const float v = kv[q];
         int pos = cnt;
         while (pos > 0 && cv[pos - 1] < v) --pos;     // after every entry of equal value
         if (pos >= T) continue;
@@ -701,14 +715,8 @@ int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att
     topk_threads = opt->topk_threads;
     precision = opt->precision;
   }
-  DDTables tab{};
-  tab.n_sub = n_sub;
-  for (int i = 0; i < n_sub; ++i) {
-    const int o = s[i].w - s[i].k_out;
-    if (o > 32) return set_error(CUTQC_EUNSUPPORTED, "more than 32 outputs in a subcircuit");
-    tab.o[i] = (int8_t)o;
-    for (int t = 0; t < o; ++t) tab.outq[i][t] = (int8_t)s[i].out_qubit[t];
-  }
+  for (int i = 0; i < n_sub; ++i)
+    if (s[i].w - s[i].k_out > 32) return set_error(CUTQC_EUNSUPPORTED, "more than 32 outputs in a subcircuit");
   const int depths = (n + M - 1) / M;
   const int levels = std::min(Rmax, depths);
   const int Tn = std::max(1, T);
@@ -738,11 +746,6 @@ int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att
     RunLayout lay;
     if ((rc = level_layout(n_sub, s, L, nj, &lay, merge_ctas))) return rc;
     if (lay.total > ws_bytes) return set_error(CUTQC_ENOMEM, "DD workspace too small for a level");
-    ZoomPtrs zp{};
-    for (int i = 0; i < n_sub; ++i) zp.p[i] = (uint64_t*)(ws + lay.zoom_off[i]);
-    const int nthr = n_sub * nj;
-    dd_zoom_kernel<<<(nthr + 127) / 128, 128, 0, st>>>(tab, jobs_dev + job0, nj, level * M, zp);
-    CUTQC_LAUNCH_CHECK("dd_zoom_kernel");
     std::vector<const float*> merged(n_sub);
     for (int i = 0; i < n_sub; ++i) {
       float* mdev = (float*)(ws + lay.merged_off[i]);
@@ -753,8 +756,17 @@ int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att
       const int a = __builtin_popcountll(L.act_mask[i]);
       const int ls = lay.log_slices[i];
       float* part = ls ? (float*)(ws + lay.part_off[i]) : mdev;
-      dd_merge_kernel<<<dim3(1u << a, nj, 1u << ls), 256, 0, st>>>(att[i], k, L.act_mask[i], mrg, L.zoom_mask[i], 0,
-                                                                   zp.p[i], __builtin_popcountll(mrg), ls, part);
+      // each job's zoom value comes from its record (written by the previous
+      // level's selection on the device)
+      ZoomFromJobs zj{};
+      zj.jobs = jobs_dev + job0;
+      zj.o = o;
+      zj.lo = level * M;
+      for (int t = 0; t < o; ++t) zj.outq[t] = (int8_t)s[i].out_qubit[t];
+      const int64_t rows_a = (int64_t)1 << a;
+      dd_merge_kernel<<<dim3(merge_grid(rows_a * nj, 1 << ls), 1, 1u << ls), 256, 0, st>>>(
+          att[i], k, L.act_mask[i], mrg, L.zoom_mask[i], 0, nullptr, zj, nj, rows_a, __builtin_popcountll(mrg), ls,
+          part);
       CUTQC_LAUNCH_CHECK("dd_merge_kernel");
       if (ls) {
         const int64_t E = ((int64_t)nj << a) << (2 * k);

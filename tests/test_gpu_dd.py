@@ -213,8 +213,9 @@ def test_autotuned_dd_options_match_oracle(cq):
         assert np.abs(b - rj["bins"]).max() <= 1e-6
 
 
+@pytest.mark.parametrize("precision", [1, 2], ids=["tc", "tc_prune"])
 @pytest.mark.parametrize("kind,M,T", [("brickwall", 4, 3), ("aqft", 6, 1), ("brickwall", 10, 2), ("bv", 5, 1)])
-def test_dd_split_precision_matches_oracle(cq, kind, M, T):
+def test_dd_split_precision_matches_oracle(cq, kind, M, T, precision):
     """Bin reconstruction on the tensor-core path (FP16 hi/lo split, the FD
     GEMM) inside the enqueue-only run: bins and totals against the FP64
     oracle, and the same jobs (levels of fewer than 4 bins per job take
@@ -226,7 +227,7 @@ def test_dd_split_precision_matches_oracle(cq, kind, M, T):
     cut = _cut(kind)
     subs, A, At = _setup(cut)
     n, R = cut.circuit.n, 6
-    jobs, n_jobs, bins = cq.cutqc_dd_run_async(subs, At, n, M, R, T, options={"precision": 1})
+    jobs, n_jobs, bins = cq.cutqc_dd_run_async(subs, At, n, M, R, T, options={"precision": precision})
     got = cq.dd_jobs_from_device(jobs, n_jobs)
     ref = dd.run(A, [s.out_qubit for s in subs], [s.edges for s in subs], cut.K, n, M, R, T, strategy="bfs")
     assert len(got) == len(ref)

@@ -340,3 +340,54 @@ def test_fd_prune_drops_only_negligible_terms(cq, tiny):
     if tiny > 1e-10:
         assert np.array_equal(p, f)      # nothing skipped: the same kernels on the same operands
     assert cq.cutqc_device_status() == 0
+
+
+def _synthetic_pair(oa, ob, k, seed):
+    """Two structural subcircuits joined by k cuts (s0 measures them, s1
+    initialises them) with seeded random attributed tensors."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(seed)
+    edges = list(range(k))
+    s0 = SimpleNamespace(w=oa + k, in_local=[], in_edge=[], out_local=list(range(oa, oa + k)), out_edge=edges,
+                         out_qubit=list(range(ob, ob + oa)), edges=edges, o=oa)
+    s1 = SimpleNamespace(w=max(ob, k), in_local=list(range(k)), in_edge=edges, out_local=[], out_edge=[],
+                         out_qubit=list(range(ob)), edges=edges, o=ob)
+    A0 = rng.standard_normal((1 << oa, 4 ** k)) / (1 << oa)
+    A1 = rng.standard_normal((1 << ob, 4 ** k)) / (1 << ob)
+    return [s0, s1], [a.astype(np.float32).astype(np.float64) for a in (A0, A1)]
+
+
+def test_fd_prune_everything_negligible(cq):
+    """Every cut term below the bound: all are skipped and the output is
+    exactly zero, within 2^-30 in L1 of the full sum."""
+    import torch
+    from oracle import fd
+    subs, A = _synthetic_pair(8, 9, 3, 5)
+    A[1] = A[1] * 1e-30
+    A = [a.astype(np.float32).astype(np.float64) for a in A]
+    ref = fd.reconstruct_kron(A, [s.edges for s in subs], 3)
+    att = [torch.from_numpy(a.astype(np.float32)).cuda() for a in A]
+    out, _ = cq.cutqc_reconstruct_fd(subs, att, 0, cq.PREC_FP16X3_TC_PRUNE)
+    got = out.cpu().numpy().astype(np.float64)
+    assert not got.any()
+    assert np.abs(got - ref).sum() <= cq.PRUNE_TOL
+    assert cq.cutqc_device_status() == 0
+
+
+def test_fd_prune_not_applied_above_1024_terms(cq):
+    """A last contraction of 4^6 = 4096 terms (the K > 256 tensor-core
+    kernel) is not pruned: the pruned precision gives the same bits as the
+    plain split precision, and both match the FP64 oracle."""
+    import torch
+    from oracle import fd
+    subs, A = _synthetic_pair(7, 8, 6, 9)
+    ref = fd.reconstruct_kron(A, [s.edges for s in subs], 6)
+    bound = fd.reconstruct_kron([np.abs(a) for a in A], [s.edges for s in subs], 6)
+    att = [torch.from_numpy(a.astype(np.float32)).cuda() for a in A]
+    a, _ = cq.cutqc_reconstruct_fd(subs, att, 0, cq.PREC_FP16X3_TC)
+    b, _ = cq.cutqc_reconstruct_fd(subs, att, 0, cq.PREC_FP16X3_TC_PRUNE)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    got = a.cpu().numpy().astype(np.float64)
+    assert (np.abs(got - ref) <= 2.0 ** -16 * bound + 1e-30).all()
+    assert cq.cutqc_device_status() == 0
