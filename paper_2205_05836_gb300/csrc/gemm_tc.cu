@@ -12,7 +12,9 @@
 // which over a long chain of signed terms leaves a negative bias (about
 // -1.5e-6 in sum p on the 30-qubit workload).  Every 64 values of k are
 // therefore accumulated in a fresh TMEM accumulator (a "chunk", 12 MMAs),
-// and the chunks are added in registers with round-to-nearest.
+// and the chunks are added in registers with round-to-nearest; from 4^6
+// values of k on (64 chunks and more) that sum is compensated (Kahan), so
+// that the rounding of a long chain of chunk totals does not grow with K.
 //
 // Kernel organisation (one CTA per SM, persistent over 128 x 128 tiles):
 //   warp 8       TMA producer: per 64-wide k-block loads A_hi, A_lo, B_hi,
@@ -57,6 +59,7 @@ constexpr int B_TILE = BN * BK * 2;                      // 16 KiB
 constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;     // 64 KiB
 constexpr int TMEM_COLS = NBUF * BN;                     // 512
 constexpr int NUM_THREADS = 320;
+constexpr int kCompensatedMinKb = 64;   // k-blocks (4^6 = 4096 values of k) from which chunk sums are compensated
 constexpr int EPI_THREADS = 256;
 constexpr int EPI_COLS = 64;                             // columns per epilogue warp
 constexpr int BLK_FLOATS = 32 * 32;                      // one 32 x 32 staging block
@@ -116,7 +119,7 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
 }
-template <bool kRowMajor>
+template <bool kRowMajor, bool kCompensated>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
   extern __shared__ uint8_t smem_raw[];
@@ -248,24 +251,47 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args) {
     const float sbg = __ldg(args.sb);
     float* stg0 = stg_all + warp * (EPI_COLS / 32) * BLK_FLOATS;
     float tot[EPI_COLS];
+    // long chunk chains (kCompensated): compensated (Kahan) float32 sums of
+    // the chunks, the rounding error of each add carried in comp
+    float comp[kCompensated ? EPI_COLS : 1];
     for (int64_t tile = blockIdx.x; tile < args.num_tiles && !*abort_flag; tile += gridDim.x) {
       const int mb = (int)(tile % args.num_m_blk);
       const int nb = (int)(tile / args.num_m_blk);
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) tot[i] = 0.f;
+      if constexpr (kCompensated) {
+#pragma unroll
+        for (int i = 0; i < EPI_COLS; ++i) comp[i] = 0.f;
+      }
       bool ok = true;
       for (int ch = 0; ch < num_chunks; ++ch) {
         if (!mbar_wait(smem_u32(&tail->cfull[buf]), buf_phase, abort_flag)) { fail(); ok = false; break; }
         tc_fence_after();
         __syncwarp();
-        uint32_t r0[32], r1[32];
         const uint32_t taddr = tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(buf * BN + h * EPI_COLS);
-        tmem_ld32(taddr, r0);
-        tmem_ld32(taddr + 32, r1);
+        if constexpr (kCompensated) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          tot[i] += __uint_as_float(r0[i]);
-          tot[32 + i] += __uint_as_float(r1[i]);
+          for (int half = 0; half < 2; ++half) {
+            uint32_t r0[32];
+            tmem_ld32(taddr + 32 * half, r0);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const int j = 32 * half + i;
+              const float y = __uint_as_float(r0[i]) - comp[j];
+              const float t = tot[j] + y;
+              comp[j] = (t - tot[j]) - y;
+              tot[j] = t;
+            }
+          }
+        } else {
+          uint32_t r0[32], r1[32];
+          tmem_ld32(taddr, r0);
+          tmem_ld32(taddr + 32, r1);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            tot[i] += __uint_as_float(r0[i]);
+            tot[32 + i] += __uint_as_float(r1[i]);
+          }
         }
         tc_fence_before();
         mbar_arrive(smem_u32(&tail->cempty[buf]));
@@ -442,14 +468,28 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alp
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(mu);
     if (!done.count(dev)) {
-      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)SMEM_BYTES));
+      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)SMEM_BYTES));
+      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)SMEM_BYTES));
+      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)SMEM_BYTES));
       done.insert(dev);
     }
   }
   const int grid = (int)std::min<int64_t>(args.num_tiles, (int64_t)sm_count());
-  if (args.row_major) tc_gemm_kernel<true><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
-  else tc_gemm_kernel<false><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
+  // 4^6 terms or more (64+ chunks, e.g. the 4^K sum of K >= 8 cuts): the
+  // chunk totals are added with compensation
+  const bool comp = args.num_kb >= kCompensatedMinKb;
+  if (args.row_major) {
+    if (comp) tc_gemm_kernel<true, true><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
+    else tc_gemm_kernel<true, false><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
+  } else {
+    if (comp) tc_gemm_kernel<false, true><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
+    else tc_gemm_kernel<false, false><<<grid, NUM_THREADS, SMEM_BYTES, st>>>(maps, args);
+  }
   CUTQC_LAUNCH_CHECK("tc_gemm_kernel");
   return CUTQC_OK;
 }

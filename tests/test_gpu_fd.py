@@ -391,3 +391,27 @@ def test_fd_prune_not_applied_above_1024_terms(cq):
     got = a.cpu().numpy().astype(np.float64)
     assert (np.abs(got - ref) <= 2.0 ** -16 * bound + 1e-30).all()
     assert cq.cutqc_device_status() == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["simt", "tc"])
+def test_fd_eight_cuts_long_term_chain(cq, precision):
+    """A last contraction over 8 cuts (4^8 = 65,536 terms, 1,024 chunks of
+    the tensor-core kernel, summed with compensation): every output against
+    the FP64 oracle within 2^-16 of the sum of |terms|, and the float64 total
+    against the oracle's."""
+    import torch
+    from oracle import fd
+    if "eight" not in _SYN_CACHE:
+        subs, A = _synthetic_pair(6, 8, 8, 17)
+        edges = [s.edges for s in subs]
+        _SYN_CACHE["eight"] = (subs, A, fd.reconstruct_kron(A, edges, 8),
+                               fd.reconstruct_kron([np.abs(a) for a in A], edges, 8))
+    subs, A, ref, bound = _SYN_CACHE["eight"]
+    att = [torch.from_numpy(a.astype(np.float32)).cuda() for a in A]
+    total = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out, _ = cq.cutqc_reconstruct_fd(subs, att, 0, precision, sum_out=total)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    assert (np.abs(got - ref) <= 2.0 ** -16 * bound + 1e-30).all(), (np.abs(got - ref) / bound).max()
+    assert abs(total.item() - ref.sum()) <= 2.0 ** -16 * bound.sum()
+    assert cq.cutqc_device_status() == 0
