@@ -310,3 +310,28 @@ def test_dd_dense_recursion_full_size(cq, precision):
     assert top_val == tv.cpu().tolist()
     assert [float(bins[i]) for i in top_idx] == top_val
     assert cq.cutqc_device_status() == 0
+
+
+@pytest.mark.parametrize("kind,M,T", [("brickwall", 4, 3), ("aqft", 6, 1)])
+def test_sharded_dd_driver_on_one_gpu(cq, kind, M, T):
+    """The multi-GPU breadth-first driver (a level's jobs split over ranks,
+    one all-gather of candidates per level), run as a single rank on this
+    GPU through cutqc_dd_merge_batch and cutqc_dd_step: the same jobs as the
+    single-GPU level-synchronous run, bins within float32 rounding."""
+    import torch
+    from paper_2205_05836_gb300.shard import dd_run_sharded, gpu_level_executor
+    cut = _cut(kind)
+    subs, A, At = _setup(cut)
+    n, R = cut.circuit.n, 6
+    recs = dd_run_sharded(gpu_level_executor(cq, subs, At, n, M, T), n, M, R, T)
+    ref_jobs, ref_bins = cq.cutqc_dd_run(subs, At, n, M, R, T, 1)
+    torch.cuda.synchronize()
+    assert len(recs) == len(ref_jobs)
+    for r, J in zip(recs, ref_jobs):
+        assert r["active"] == list(J.active[:J.n_active])
+        assert r["zoom"] == J.zoom()
+        assert (r["parent"], r["parent_bin"]) == (J.parent, J.parent_bin)
+        nb = 1 << J.n_active
+        assert torch.allclose(r["bins"], ref_bins[J.bins_offset:J.bins_offset + nb], atol=1e-7, rtol=0)
+        assert abs(r["bin_sum"] - J.bin_sum) <= 1e-9
+    assert cq.cutqc_device_status() == 0

@@ -75,3 +75,89 @@ def test_row_range_covers_rows():
             assert got[0][0] == 0 and got[-1][1] == rows
             assert all(a[1] == b[0] for a, b in zip(got, got[1:]))
             assert max(b - a for a, b in got) - min(b - a for a, b in got) <= 1
+
+
+def _oracle_level_executor(A, subs, K):
+    """execute_level for the sharded DD driver built on the FP64 oracle (the
+    CPU stand-in for a rank's GPU in these tests)."""
+    from oracle import dd
+
+    def run(level, jobs):
+        out = []
+        for jb in jobs:
+            bins = dd.reconstruct_bins(A, [s.out_qubit for s in subs], [s.edges for s in subs], K, jb["active"],
+                                       jb["zoom"])
+            n = sum(s.o for s in subs)
+            has_merged = jb["active"][-1] + 1 < n
+            top = [(float(bins[b]), int(b)) for b in dd._top(bins, _T, has_merged)]
+            out.append(dict(bin_sum=float(bins.sum()), top=top))
+        return out
+    return run
+
+
+_T = 3
+
+
+def _dd_worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle import attribution
+        from paper_2205_05836_gb300.shard import dd_run_sharded
+        from workloads import circuits as C
+        from workloads.cutting import search_cut
+        from workloads.simulate import simulate_variants
+        cut = search_cut(C.brickwall(10, 4, 11), 7, 2, restarts=4)
+        subs = cut.subcircuits
+        A = [attribution.attribute(simulate_variants(s), s.w, s.in_local, s.out_local, s.in_edge, s.out_edge)
+             for s in subs]
+        recs = dd_run_sharded(_oracle_level_executor(A, subs, cut.K), cut.circuit.n, 4, 6, _T)
+        q.put((rank, [(r["level"], r["parent"], r["parent_bin"], sorted(r["zoom"].items()), r["bin_sum"],
+                       r["top"]) for r in recs]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_dd_levels_match_single_process():
+    """Breadth-first Algorithm 1 with each level's jobs split over two gloo
+    ranks (one all-gather of (value, bin) candidates per level): both ranks
+    get the job records of the single-process FP64 oracle run."""
+    import torch.multiprocessing as mp
+    from oracle import attribution, dd
+    from workloads import circuits as C
+    from workloads.cutting import search_cut
+    from workloads.simulate import simulate_variants
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dd_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=240)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(2))
+    cut = search_cut(C.brickwall(10, 4, 11), 7, 2, restarts=4)
+    subs = cut.subcircuits
+    A = [attribution.attribute(simulate_variants(s), s.w, s.in_local, s.out_local, s.in_edge, s.out_edge)
+         for s in subs]
+    ref = dd.run(A, [s.out_qubit for s in subs], [s.edges for s in subs], cut.K, cut.circuit.n, 4, 6, _T,
+                 strategy="bfs")
+    assert got[0] == got[1]
+    assert len(got[0]) == len(ref) > 1
+    for (lvl, parent, pbin, zoom, bsum, top), r in zip(got[0], ref):
+        assert zoom == sorted(r["zoom"].items())
+        assert abs(bsum - r["bins"].sum()) <= 1e-12
+        assert [b for _, b in top] == r["top"]
+
+
+def test_merge_level_candidates_order():
+    """The next level's jobs: larger values first; equal values keep job
+    order, then each job's own order."""
+    from paper_2205_05836_gb300.shard import merge_level_candidates
+    tops = [[(0.5, 7), (0.25, 3)], [(0.5, 1), (0.75, 9)], [], [(0.25, 0)]]
+    assert merge_level_candidates(tops, 4) == [(1, 9), (0, 7), (1, 1), (0, 3)]
+    assert merge_level_candidates(tops, 10)[-1] == (3, 0)
+    assert merge_level_candidates([[], []], 3) == []
