@@ -502,6 +502,8 @@ def run(args):
         line["dd_dense"] = dd_dense_extras(dev, cq)
         torch.cuda.empty_cache()
         _log("DD dense extras done")
+        line["finite_shots"] = finite_shot_extras(dev, cq)
+        _log("finite-shot extras done")
         line["learned"] = learned_extras(dev, cq)
         _log("cut-scorer extras done")
     if rank == 0:
@@ -721,6 +723,48 @@ def dd_extras(dev, cq, M=16, R=6, T=4, reps=5, precision=0):
             "circuits": out, "graph_ms": ms, "bins_per_s": tot_bins / (ms * 1e-3),
             "note": "all levels of the three circuits in one captured CUDA graph (one stream per circuit); "
                     "selection on the device"}
+
+
+def finite_shot_extras(dev, cq, shots=(10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6), seed=7):
+    """The paper's shot-based mode on the 8-qubit brick-wall workload: every
+    subcircuit variant sampled with S shots (seeded multinomial), attributed
+    and reconstructed on the GPU, and Eq. 3 (chi^2) against the reconstruction
+    from exact variants (which the tests pin to the uncut circuit's exact
+    distribution).  Beside it, chi^2 of the uncut circuit sampled directly
+    with the same total number of shots (no device noise in either)."""
+    import torch
+    from workloads.configs import fd_plain
+    from workloads.simulate import sample_distribution, sample_variants
+    w = fd_plain()
+    subs = w.subcircuits
+    exact = w.variants()
+
+    def rec(vs):
+        att = [cq.cutqc_attribute(s, torch.from_numpy(v).to(dev)) for s, v in zip(subs, vs)]
+        out, _ = cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_ORIGINAL, cq.PREC_FP16X3_TC)
+        return out.double()
+
+    def chi2(a, b):       # Eq. 3 over the terms with a_i + b_i != 0
+        s = a + b
+        m = s != 0
+        return float(((a[m] - b[m]) ** 2 / s[m]).sum())
+
+    def clip(a):          # Eq. 3 is for distributions: negatives to 0, total 1
+        a = a.clamp(min=0)
+        return a / a.sum()
+    truth = rec(exact)
+    runs = sum(v.shape[0] * v.shape[1] for v in exact)
+    res = {"workload": w.name, "n_qubits": w.n, "cuts": w.K, "variant_runs": int(runs), "per_shots": {}}
+    for i, S in enumerate(shots):
+        a = rec([sample_variants(v, S, seed + 10 * i + j) for j, v in enumerate(exact)])
+        direct = torch.from_numpy(sample_distribution(truth.cpu().numpy(), S * runs, seed + 10 * i + 9)).to(dev)
+        res["per_shots"][str(S)] = {"chi2_cut": chi2(clip(a), truth),
+                                    "chi2_direct_same_total_shots": chi2(direct, truth),
+                                    "tv_cut": 0.5 * float((a - truth).abs().sum()),
+                                    "tv_direct_same_total_shots": 0.5 * float((direct - truth).abs().sum()),
+                                    "negative_mass": float(-a[a < 0].sum())}
+    res["note"] = "chi2_cut: the reconstruction with negative entries clipped to 0 and renormalised"
+    return res
 
 
 def dd_dense_extras(dev, cq, M=30, T=4, reps=5):

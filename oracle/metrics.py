@@ -26,3 +26,11 @@ def norm_error(p):
 
 def max_abs(p, q):
     return float(np.abs(np.asarray(p, np.float64) - np.asarray(q, np.float64)).max())
+
+
+def clip_renormalise(p):
+    """A reconstruction from finite-shot variants has negative entries; Eq. 3
+    is stated for probability distributions, so the chi^2 reading here clips
+    the negatives to 0 and rescales to total 1 first."""
+    q = np.clip(np.asarray(p, np.float64), 0.0, None)
+    return q / q.sum()

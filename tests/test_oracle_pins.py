@@ -336,3 +336,93 @@ def test_planted_order_swap_is_caught():
     subs = cut.subcircuits
     wrong = fd.kron_to_original(pk, [s.out_qubit for s in reversed(subs)])
     assert metrics.max_abs(wrong, statevector.probabilities(c)) > 1e-4
+
+
+def test_adder_closed_form():
+    """The Adder benchmark (ripple-carry, one ancilla): register a in uniform
+    superposition, b a seeded constant; the exact output is uniform over a of
+    the basis state (a, a + b mod 2^m, carry), ancilla 0 -- the statevector
+    simulator reproduces it to rounding."""
+    from oracle import statevector
+    from workloads import circuits as C
+    for n, seed in ((6, 1), (10, 3)):
+        c = C.adder(n, seed)
+        m, b = c.meta["m"], c.meta["b"]
+        ref = np.zeros(1 << n)
+        for a in range(1 << m):
+            s = a + b
+            idx = (((s >> m) & 1) << c.meta["carry_qubit"])
+            for i in range(m):
+                idx |= ((a >> i) & 1) << c.meta["a_qubits"][i]
+                idx |= ((s >> i) & 1) << c.meta["b_qubits"][i]
+            ref[idx] = 2.0 ** -m
+        assert np.abs(statevector.probabilities(c) - ref).max() < 1e-12
+    with pytest.raises(ValueError):
+        C.adder(7, 0)
+
+
+def test_fd_oracle_on_cut_adder_matches_statevector():
+    """A 12-qubit adder cut into a chain of three subcircuits (K = 4): the
+    oracle's Eq. 1 reconstruction equals the uncut circuit's distribution."""
+    from oracle import attribution, fd, metrics, statevector
+    from workloads import circuits as C
+    from workloads.cutting import search_cut
+    from workloads.simulate import simulate_variants
+    c = C.adder(12, 3)
+    cut = search_cut(c, 7, 3, restarts=4)
+    subs = cut.subcircuits
+    assert len(subs) == 3 and cut.K >= 2
+    A = [attribution.attribute(simulate_variants(s), s.w, s.in_local, s.out_local, s.in_edge, s.out_edge)
+         for s in subs]
+    p = fd.kron_to_original(fd.reconstruct_kron(A, [s.edges for s in subs], cut.K), [s.out_qubit for s in subs])
+    assert metrics.tv(p, statevector.probabilities(c)) < 1e-12
+
+
+def test_sampled_variants_are_distributions():
+    """Finite-shot variants: every row sums to 1, seeded draws repeat, and
+    their frequencies approach the exact outcome probabilities (within six
+    binomial standard deviations at 10^6 shots)."""
+    from workloads import circuits as C
+    from workloads.cutting import search_cut
+    from workloads.simulate import sample_variants, simulate_variants
+    cut = search_cut(C.brickwall(8, 6, 0), 7, 2, restarts=4)
+    v = simulate_variants(cut.subcircuits[0])
+    s1 = sample_variants(v, 10 ** 6, 5)
+    assert s1.shape == v.shape
+    assert np.allclose(s1.sum(-1), 1.0)
+    assert np.array_equal(s1, sample_variants(v, 10 ** 6, 5))
+    assert not np.array_equal(s1, sample_variants(v, 10 ** 6, 6))
+    sd = np.sqrt(v * (1 - v) / 1e6)
+    assert (np.abs(s1 - v) <= 6 * sd + 1e-12).all()
+
+
+def test_chi2_falls_with_shots():
+    """Eq. 3 between the reconstruction from finite-shot variants (negative
+    entries clipped, renormalised) and the exact distribution shrinks as the
+    shots grow (about as 1 / shots; checked loosely: two decades of shots give
+    at least a 20-fold drop), TV about as 1 / sqrt(shots), and chi^2 is 0 for
+    exact variants."""
+    from oracle import attribution, fd, metrics, statevector
+    from workloads import circuits as C
+    from workloads.cutting import search_cut
+    from workloads.simulate import sample_variants, simulate_variants
+    c = C.brickwall(8, 6, 0)
+    cut = search_cut(c, 7, 2, restarts=4)
+    subs = cut.subcircuits
+    truth = statevector.probabilities(c)
+    var = [simulate_variants(s) for s in subs]
+
+    def rec(vs):
+        A = [attribution.attribute(v, s.w, s.in_local, s.out_local, s.in_edge, s.out_edge) for s, v in zip(subs, vs)]
+        return fd.kron_to_original(fd.reconstruct_kron(A, [s.edges for s in subs], cut.K), [s.out_qubit for s in subs])
+    assert metrics.chi2(rec(var), truth) < 1e-20
+    # Eq. 3 by hand: (0.5-1)^2/1.5 + (0.5-0)^2/0.5 = 1/6 + 1/2; the 0/0 term is left out
+    assert abs(metrics.chi2([0.5, 0.5, 0.0], [1.0, 0.0, 0.0]) - (1 / 6 + 1 / 2)) < 1e-15
+    recs = [rec([sample_variants(v, S, 11 + i) for i, v in enumerate(var)]) for S in (10 ** 3, 10 ** 5)]
+    x = [metrics.chi2(metrics.clip_renormalise(r), truth) for r in recs]
+    assert x[1] < x[0] / 20, x
+    t = [metrics.tv(r, truth) for r in recs]
+    assert t[1] < t[0] / 4, t       # TV falls about as 1 / sqrt(shots)
+    # the clipped, renormalised reconstruction is a distribution
+    q = metrics.clip_renormalise(recs[0])
+    assert (q >= 0).all() and abs(q.sum() - 1) < 1e-12

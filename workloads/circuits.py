@@ -1,5 +1,5 @@
 """Seeded synthetic circuit generators (the benchmark families of the paper's
-Methodology section: BV, AQFT, Supremacy, plus the brick-wall family).
+Methodology section: BV, Adder, AQFT, Supremacy, plus the brick-wall family).
 
 A circuit is an ordered gate list on ``n`` qubits.  Each gate is a tuple
 ``(name, qubits, params)``.  The gate names and their matrices are fixed here;
@@ -259,6 +259,73 @@ def bv(n, seed, hidden=None):
         c.add("h", (q,))
     c.add("h", (anc,))
     c.meta.update(kind="bv", seed=seed, hidden=hidden)
+    return c
+
+
+def _toffoli(c, a, b, t):
+    """Toffoli with controls a, b and target t, in the gate set here: the
+    standard decomposition into 6 CNOTs, H and T / T^dagger (T = Rz(pi/4) up
+    to a global phase, which no probability sees)."""
+    T, Td = (math.pi / 4,), (-math.pi / 4,)
+    c.add("h", (t,))
+    c.add("cx", (b, t))
+    c.add("rz", (t,), Td)
+    c.add("cx", (a, t))
+    c.add("rz", (t,), T)
+    c.add("cx", (b, t))
+    c.add("rz", (t,), Td)
+    c.add("cx", (a, t))
+    c.add("rz", (b,), T)
+    c.add("rz", (t,), T)
+    c.add("h", (t,))
+    c.add("cx", (a, b))
+    c.add("rz", (a,), T)
+    c.add("rz", (b,), Td)
+    c.add("cx", (a, b))
+
+
+def adder(n, seed):
+    """Ripple-carry adder (the paper's Adder benchmark: one ancilla, linear
+    depth, two registers of the same width, so n is even): m = (n - 2) / 2
+    bit registers a and b, the ancilla carry-in c0 (qubit 0) and the carry
+    out z (qubit n - 1), laid out c0, b0, a0, b1, a1, ..., b_{m-1}, a_{m-1}, z.
+    The carry ripples up through MAJ blocks stored in a, z takes the top
+    carry, and UMA blocks ripple back down, leaving b = a + b mod 2^m and a
+    restored (the majority / unmajority-and-add construction of a
+    ripple-carry adder with one ancilla).  Inputs: a in uniform superposition
+    (H on each a_i), b a seeded classical value, so the output is uniform
+    over the 2^m values of a: (a, a + b mod 2^m, carry), c0 = 0."""
+    if n < 4 or n % 2:
+        raise ValueError("the adder needs an even n >= 4")
+    m = (n - 2) // 2
+    rng = np.random.default_rng(seed)
+    bval = int(rng.integers(0, 1 << m))
+    c0, z = 0, n - 1
+    bq = [1 + 2 * i for i in range(m)]
+    aq = [2 + 2 * i for i in range(m)]
+    c = Circuit(n, name=f"adder_n{n}_s{seed}")
+    for i in range(m):
+        c.add("h", (aq[i],))
+        if (bval >> i) & 1:
+            c.add("x", (bq[i],))
+
+    def maj(x, y, w):      # carry x, b bit y, a bit w -> w = majority
+        c.add("cx", (w, y))
+        c.add("cx", (w, x))
+        _toffoli(c, x, y, w)
+
+    def uma(x, y, w):      # undo maj and write the sum bit into y
+        _toffoli(c, x, y, w)
+        c.add("cx", (w, x))
+        c.add("cx", (x, y))
+
+    carry = [c0] + aq[:-1]
+    for i in range(m):
+        maj(carry[i], bq[i], aq[i])
+    c.add("cx", (aq[m - 1], z))
+    for i in reversed(range(m)):
+        uma(carry[i], bq[i], aq[i])
+    c.meta.update(kind="adder", seed=seed, m=m, b=bval, a_qubits=aq, b_qubits=bq, carry_qubit=z)
     return c
 
 

@@ -95,3 +95,27 @@ def simulate_variants(sub: Subcircuit, dtype=np.float64):
         psi = np.moveaxis(psi, 0, kin)                   # meas axis after init axes
     probs = (psi.real ** 2 + psi.imag ** 2).astype(dtype)
     return probs.reshape(4 ** kin, 3 ** kout, 2 ** w)
+
+
+def sample_variants(variants, shots, seed):
+    """Finite-shot stand-in for running the variants on a QPU: each variant's
+    outcome distribution (the last axis, 2^w outcomes) is replaced by the
+    frequencies of `shots` seeded draws from it (a multinomial sample, as a
+    device's shots give: the paper's shot-based evaluation mode).  Same shape
+    and dtype float64; every row sums to 1."""
+    rng = np.random.default_rng(seed)
+    v = np.asarray(variants, np.float64)
+    flat = v.reshape(-1, v.shape[-1])
+    out = np.empty_like(flat)
+    for i, p in enumerate(flat):
+        p = np.clip(p, 0.0, None)
+        out[i] = rng.multinomial(int(shots), p / p.sum()) / float(shots)
+    return out.reshape(v.shape)
+
+
+def sample_distribution(p, shots, seed):
+    """Frequencies of `shots` seeded draws from the distribution p (the uncut
+    circuit run on a device with that many shots)."""
+    rng = np.random.default_rng(seed)
+    p = np.clip(np.asarray(p, np.float64), 0.0, None)
+    return rng.multinomial(int(shots), p / p.sum()) / float(shots)
