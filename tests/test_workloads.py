@@ -115,3 +115,36 @@ def test_features_shape_and_permutation_invariance():
     perm = rng.permutation(7)
     f2 = CandidateSet(dag, perm[A], 12).features()
     np.testing.assert_array_equal(f, f2)
+
+
+def test_exact_cut_is_optimal_by_enumeration():
+    """The branch-and-bound cut search against plain enumeration of every
+    assignment of the two-qubit gates to 2 or 3 clusters: the same minimal
+    number of cuts under the width limit."""
+    import itertools
+    from workloads import circuits as C
+    from workloads.cutting import Dag, build_cut, exact_cut
+    for c, w, ns in ((C.brickwall(6, 3, 2), 4, 2), (C.aqft(6, 1, max_dist=2), 4, 3), (C.bv(7, 2), 4, 2)):
+        nv = Dag(c).nv
+        assert ns ** nv <= 200_000
+        best = None
+        for cl in itertools.product(range(ns), repeat=nv):
+            cut = build_cut(c, list(cl), w_max=w)
+            if all(s.w <= w for s in cut.subcircuits):
+                best = cut.K if best is None else min(best, cut.K)
+        ex, full = exact_cut(c, w, ns)
+        assert full and ex is not None
+        assert ex.K == best, (c.name, ex.K, best)
+        assert all(s.w <= w for s in ex.subcircuits)
+
+
+def test_local_search_reaches_exact_optimum_on_small_circuits():
+    """The simulated-annealing cut search finds the exact minimum number of
+    cuts (branch and bound) on small instances of every benchmark family."""
+    from workloads import circuits as C
+    from workloads.cutting import exact_cut, search_cut
+    for c, w, ns in ((C.brickwall(8, 6, 0), 7, 2), (C.aqft(8, 2, max_dist=2), 5, 2), (C.adder(10, 3), 6, 3),
+                     (C.bv(10, 4), 5, 3), (C.supremacy(3, 3, 6, 1), 6, 2), (C.brickwall(10, 4, 11), 7, 2)):
+        ex, full = exact_cut(c, w, ns)
+        assert full
+        assert search_cut(c, w, ns, restarts=4).K == ex.K, c.name

@@ -515,3 +515,75 @@ def grid_orders(rows, cols):
     rm = list(range(rows * cols))
     cm = [r * cols + c for c in range(cols) for r in range(rows)]
     return [rm, cm]
+
+
+# --------------------------------------------------------------------------
+# exact search (branch and bound) for small circuits
+# --------------------------------------------------------------------------
+
+def exact_cut(circuit: Circuit, w_max, n_sub, max_nodes=2_000_000):
+    """Branch and bound over the clusterings of the two-qubit gates into at
+    most ``n_sub`` clusters with every width <= w_max (the two constraints of
+    the paper's cut searcher), minimising the number of cuts K, ties broken
+    by the contraction cost.  Gates are assigned in program order, so each
+    qubit's wire is extended one gate at a time: a gate placed in a cluster
+    other than its qubit's previous one cuts the wire there and opens a new
+    wire segment in that cluster (width + 1); a qubit's first gate opens its
+    original input.  Widths and cuts only grow along a branch, which gives
+    the bound.  Clusters are introduced in order (symmetry).  Returns
+    (Cut, exhaustive) -- exhaustive False when the node budget ran out first
+    (the Cut is then the best found) -- or (None, ...) when nothing fits."""
+    dag = Dag(circuit)
+    nv = dag.nv
+    n_free = len(dag.free_qubits)
+    best = {"K": None, "leaves": []}
+    assign = [0] * nv
+    last = [-1] * dag.n          # cluster of each qubit's latest assigned gate
+    width = [0] * n_sub
+    nodes = [0]
+
+    def rec(v, used, cuts):
+        nodes[0] += 1
+        if nodes[0] > max_nodes:
+            return False
+        if best["K"] is not None and cuts > best["K"]:
+            return True
+        if v == nv:
+            if best["K"] is None or cuts < best["K"]:
+                best["K"], best["leaves"] = cuts, []
+            if len(best["leaves"]) < 64:
+                best["leaves"].append(list(assign))
+            return True
+        q0, q1 = dag.vq[v]
+        for c in range(min(used + 1, n_sub)):
+            dc = 0
+            opened = []
+            for q in (q0, q1):
+                if last[q] != c:
+                    if last[q] >= 0:
+                        dc += 1
+                    opened.append(q)
+            if width[c] + len(opened) > w_max:
+                continue
+            saved = (last[q0], last[q1])
+            width[c] += len(opened)
+            last[q0] = last[q1] = c
+            assign[v] = c
+            ok = rec(v + 1, max(used, c + 1), cuts + dc)
+            last[q0], last[q1] = saved
+            width[c] -= len(opened)
+            if not ok:
+                return False
+        return True
+
+    exhaustive = rec(0, 0, 0) if nv else True
+    if best["K"] is None:
+        return None, exhaustive
+    cands = []
+    for cl in best["leaves"]:
+        cut = build_cut(circuit, cl, w_max=w_max)
+        if all(s.w <= w_max for s in cut.subcircuits) and len(cut.subcircuits) <= n_sub + n_free:
+            cands.append(((cut.K, contraction_cost(cut)), cut))
+    if not cands:
+        return None, exhaustive
+    return min(cands, key=lambda x: x[0])[1], exhaustive
