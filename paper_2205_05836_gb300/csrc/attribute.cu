@@ -189,8 +189,9 @@ attr_init_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p,
 // X: X basis; Y: Y basis) and the sign of outcome 1 (+ for I, - otherwise):
 //   out[d] = sum_{b in {0,1}^KOUT} (-1)^{popcount(b & nonI(d))} V[run(d)][b]
 // with V[m][b] the run-m probability of outcome bits b of the measured cuts.
-// Shared memory: V as [(m << KOUT) | b][R + 1] for R consecutive output rows
-// x_out and fixed init digits `dinit` (blockIdx.y).
+// Shared memory: V as [m][b][R + 1] (each run's block padded by one float)
+// for R consecutive output rows x_out and fixed init digits `dinit`
+// (blockIdx.y).
 template <typename T, int KOUT>
 __global__ void __launch_bounds__(kMeasThreads)
 attr_meas_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p) {
@@ -198,10 +199,14 @@ attr_meas_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p)
   constexpr int F = NM << KOUT;
   constexpr int R = meas_rows_for(F);
   constexpr int RS = R + 1;
+  // one run's [2^KOUT][RS] block plus one float: consecutive runs start in
+  // different banks, so the combine step (threads over basis digits) reads
+  // without bank conflicts
+  constexpr int PITCH = (1 << KOUT) * RS + 1;
   constexpr int G = 1 << (2 * KOUT);
   extern __shared__ float sm[];
-  float* buf = sm;                                                     // [F][RS]
-  int64_t* rowbase = reinterpret_cast<int64_t*>(buf + ((F * RS + 1) & ~1));   // [R]
+  float* buf = sm;                                                     // [NM][PITCH]
+  int64_t* rowbase = reinterpret_cast<int64_t*>(buf + ((NM * PITCH + 1) & ~1));   // [R]
   int64_t* bpart = rowbase + R;                                       // [2^KOUT]
   int* runoff = reinterpret_cast<int*>(bpart + (1 << KOUT));          // [G]: (run << KOUT) * RS
   int* nonI = runoff + G;                                             // [G]
@@ -228,7 +233,7 @@ attr_meas_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p)
       if (dj) mask |= 1 << j;
       c |= dj << p.col_shift_out[j];
     }
-    runoff[d] = (run << KOUT) * RS;
+    runoff[d] = run * PITCH;
     nonI[d] = mask;
     colm[d] = c;
   }
@@ -247,7 +252,10 @@ attr_meas_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p)
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
       const int i = i0 + u * kMeasThreads + threadIdx.x;
-      if (i < F * R) buf[(i / R) * RS + i % R] = v[u];
+      if (i < F * R) {
+        const int e = i / R;
+        buf[(e >> KOUT) * PITCH + (e & ((1 << KOUT) - 1)) * RS + i % R] = v[u];
+      }
     }
   }
   __syncthreads();
@@ -274,7 +282,9 @@ template <typename T, int KOUT>
 size_t meas_smem() {
   constexpr int F = pow3(KOUT) << KOUT;
   constexpr int R = meas_rows_for(F);
-  return (((size_t)F * (R + 1) + 1) & ~(size_t)1) * 4 + (size_t)(R + (1 << KOUT)) * 8 + 3 * ((size_t)1 << (2 * KOUT)) * 4;
+  constexpr size_t PITCH = ((size_t)1 << KOUT) * (R + 1) + 1;
+  return (((size_t)pow3(KOUT) * PITCH + 1) & ~(size_t)1) * 4 + (size_t)(R + (1 << KOUT)) * 8 +
+         3 * ((size_t)1 << (2 * KOUT)) * 4;
 }
 
 // k == 0: plain conversion to float32.
