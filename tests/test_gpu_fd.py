@@ -443,3 +443,36 @@ def test_fd_from_finite_shot_variants(cq):
         # Eq. 3 divides by a_i + b_i, which finite shots bring near 0 (1.8e-5 here): loose
         assert abs(metrics.chi2(got, truth) - metrics.chi2(ref, truth)) <= 1e-2 * metrics.chi2(ref, truth)
     assert (ref < 0).any()        # finite shots: the reconstruction is not a distribution
+
+
+@pytest.mark.parametrize("precision", [1, 2], ids=["tc", "tc_prune"])
+def test_fd_captured_in_cuda_graph(cq, precision):
+    """The reconstruction enqueues without host synchronisation (pruning
+    chooses its terms on the device): captured in a CUDA graph and replayed
+    twice it gives the eager call's bits and FP64 total."""
+    import torch
+    from workloads import circuits as C
+    from workloads.cutting import search_cut
+    from workloads.simulate import simulate_variants
+    cut = search_cut(C.aqft(12, 3, max_dist=3), 7, 3, restarts=4)
+    subs = cut.subcircuits
+    att = _gpu_att(cq, subs, [simulate_variants(s) for s in subs])
+    ref_total = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ref, _ = cq.cutqc_reconstruct_fd(subs, att, 1, precision, sum_out=ref_total)
+    out = torch.empty_like(ref)
+    total = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ws = torch.empty(max(1, cq.cutqc_reconstruct_fd_workspace_size(subs, precision)), dtype=torch.uint8,
+                     device="cuda")
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        total.zero_()
+        cq.cutqc_reconstruct_fd(subs, att, 1, precision, out=out, sum_out=total, ws=ws)
+    for _ in range(2):
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+        assert abs(total.item() - ref_total.item()) <= 1e-12
+    assert cq.cutqc_device_status() == 0
