@@ -3,6 +3,7 @@
 
 #include "internal.cuh"
 
+#include <mutex>
 #include <vector>
 
 namespace cutqc {
@@ -63,6 +64,20 @@ int launch_sgemm(const float* A, int64_t lda, const float* B, int64_t ldb, int64
                  int64_t K, float alpha, uint64_t mask_m, uint64_t mask_n, float* out, double* sum,
                  int streaming, cudaStream_t st, int batch = 1, int64_t a_bstride = 0, int64_t b_bstride = 0,
                  int64_t out_bstride = 0);
+
+// Side streams per (device, caller stream) for independent work inside one
+// call (a level's merges, independent contraction steps), forked from and
+// joined back into the caller's stream with events (a CUDA graph capture
+// records them as edges).  Hold `mu` from the fork to the join.
+constexpr int kSideStreams = 8;
+constexpr int kSideEvents = 64;
+struct SideStreams {
+  std::mutex mu;
+  cudaStream_t s[kSideStreams];
+  cudaEvent_t fork, join[kSideStreams];
+  cudaEvent_t done[kSideEvents];   // per contraction step
+};
+int side_streams(cudaStream_t caller, SideStreams** out);
 
 // ------------------------------------------------------- contraction plans
 // A tensor [2^o][4^|edges|] whose row bit b lands at output position pos[b].

@@ -96,40 +96,6 @@ dd_merge_kernel(const float* __restrict__ att, int k, uint64_t act_mask, uint64_
   }
 }
 
-// Side streams per (device, caller stream), created once and kept for the
-// process: a level's merges are independent and run on them, forked from
-// and joined back into the caller's stream with events, which a CUDA graph
-// capture records as edges.  Separate sets per caller stream keep runs on
-// different streams independent; the set's mutex is held from the fork to
-// the join so that two host threads never interleave on its events.
-constexpr int kSideStreams = 8;
-struct SideStreams {
-  std::mutex mu;
-  cudaStream_t s[kSideStreams];
-  cudaEvent_t fork, join[kSideStreams];
-};
-static int side_streams(cudaStream_t caller, SideStreams** out) {
-  static std::mutex mu;
-  static std::map<std::pair<int, cudaStream_t>, SideStreams*> pool;
-  int dev = 0;
-  CUTQC_CUDA_TRY(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lk(mu);
-  auto key = std::make_pair(dev, caller);
-  if (pool.size() >= 64 && !pool.count(key)) key.second = nullptr;   // many streams: share one set
-  auto it = pool.find(key);
-  if (it == pool.end()) {
-    SideStreams* p = new SideStreams();
-    for (int i = 0; i < kSideStreams; ++i) {
-      CUTQC_CUDA_TRY(cudaStreamCreateWithFlags(&p->s[i], cudaStreamNonBlocking));
-      CUTQC_CUDA_TRY(cudaEventCreateWithFlags(&p->join[i], cudaEventDisableTiming));
-    }
-    CUTQC_CUDA_TRY(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
-    it = pool.emplace(key, p).first;
-  }
-  *out = it->second;
-  return CUTQC_OK;
-}
-
 // CTAs of a merge launch: enough to fill the GPU once, each walking rows
 inline unsigned merge_grid(int64_t rows, int slices) {
   const int64_t cap = std::max<int64_t>(1, (int64_t)sm_count() * 8 / std::max(1, slices));
@@ -786,43 +752,45 @@ int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att
     // streams, join before the reconstruction
     SideStreams* ss = nullptr;
     if ((rc = side_streams(st, &ss))) return rc;
-    std::lock_guard<std::mutex> side_lock(ss->mu);
-    const int nside = std::min(n_sub, kSideStreams);
-    CUTQC_CUDA_TRY(cudaEventRecord(ss->fork, st));
-    for (int j = 0; j < nside; ++j) CUTQC_CUDA_TRY(cudaStreamWaitEvent(ss->s[j], ss->fork, 0));
-    for (int i = 0; i < n_sub; ++i) {
-      cudaStream_t ms = ss->s[i % nside];
-      float* mdev = (float*)(ws + lay.merged_off[i]);
-      const int o = s[i].w - s[i].k_out;
-      const uint64_t all = o >= 64 ? ~0ull : (((uint64_t)1 << o) - 1);
-      const uint64_t mrg = all & ~L.act_mask[i] & ~L.zoom_mask[i];
-      const int k = s[i].k_in + s[i].k_out;
-      const int a = __builtin_popcountll(L.act_mask[i]);
-      const int ls = lay.log_slices[i];
-      float* part = ls ? (float*)(ws + lay.part_off[i]) : mdev;
-      // each job's zoom value comes from its record (written by the previous
-      // level's selection on the device)
-      ZoomFromJobs zj{};
-      zj.jobs = jobs_dev + job0;
-      zj.o = o;
-      zj.lo = level * M;
-      for (int t = 0; t < o; ++t) zj.outq[t] = (int8_t)s[i].out_qubit[t];
-      const int64_t rows_a = (int64_t)1 << a;
-      dd_merge_kernel<<<dim3(merge_grid(rows_a * nj, 1 << ls), 1, 1u << ls), 256, 0, ms>>>(
-          att[i], k, L.act_mask[i], mrg, L.zoom_mask[i], 0, nullptr, zj, nj, rows_a, __builtin_popcountll(mrg), ls,
-          part);
-      CUTQC_LAUNCH_CHECK("dd_merge_kernel");
-      if (ls) {
-        const int64_t E = ((int64_t)nj << a) << (2 * k);
-        const int blocks = (int)std::min<int64_t>((E + 255) / 256, (int64_t)sm_count() * 8);
-        dd_merge_reduce<<<blocks, 256, 0, ms>>>(part, 1 << ls, E, mdev);
-        CUTQC_LAUNCH_CHECK("dd_merge_reduce");
+    {
+      std::lock_guard<std::mutex> side_lock(ss->mu);
+      const int nside = std::min(n_sub, kSideStreams);
+      CUTQC_CUDA_TRY(cudaEventRecord(ss->fork, st));
+      for (int j = 0; j < nside; ++j) CUTQC_CUDA_TRY(cudaStreamWaitEvent(ss->s[j], ss->fork, 0));
+      for (int i = 0; i < n_sub; ++i) {
+        cudaStream_t ms = ss->s[i % nside];
+        float* mdev = (float*)(ws + lay.merged_off[i]);
+        const int o = s[i].w - s[i].k_out;
+        const uint64_t all = o >= 64 ? ~0ull : (((uint64_t)1 << o) - 1);
+        const uint64_t mrg = all & ~L.act_mask[i] & ~L.zoom_mask[i];
+        const int k = s[i].k_in + s[i].k_out;
+        const int a = __builtin_popcountll(L.act_mask[i]);
+        const int ls = lay.log_slices[i];
+        float* part = ls ? (float*)(ws + lay.part_off[i]) : mdev;
+        // each job's zoom value comes from its record (written by the previous
+        // level's selection on the device)
+        ZoomFromJobs zj{};
+        zj.jobs = jobs_dev + job0;
+        zj.o = o;
+        zj.lo = level * M;
+        for (int t = 0; t < o; ++t) zj.outq[t] = (int8_t)s[i].out_qubit[t];
+        const int64_t rows_a = (int64_t)1 << a;
+        dd_merge_kernel<<<dim3(merge_grid(rows_a * nj, 1 << ls), 1, 1u << ls), 256, 0, ms>>>(
+            att[i], k, L.act_mask[i], mrg, L.zoom_mask[i], 0, nullptr, zj, nj, rows_a, __builtin_popcountll(mrg), ls,
+            part);
+        CUTQC_LAUNCH_CHECK("dd_merge_kernel");
+        if (ls) {
+          const int64_t E = ((int64_t)nj << a) << (2 * k);
+          const int blocks = (int)std::min<int64_t>((E + 255) / 256, (int64_t)sm_count() * 8);
+          dd_merge_reduce<<<blocks, 256, 0, ms>>>(part, 1 << ls, E, mdev);
+          CUTQC_LAUNCH_CHECK("dd_merge_reduce");
+        }
+        merged[i] = mdev;
       }
-      merged[i] = mdev;
-    }
-    for (int j = 0; j < nside; ++j) {
-      CUTQC_CUDA_TRY(cudaEventRecord(ss->join[j], ss->s[j]));
-      CUTQC_CUDA_TRY(cudaStreamWaitEvent(st, ss->join[j], 0));
+      for (int j = 0; j < nside; ++j) {
+        CUTQC_CUDA_TRY(cudaEventRecord(ss->join[j], ss->s[j]));
+        CUTQC_CUDA_TRY(cudaStreamWaitEvent(st, ss->join[j], 0));
+      }
     }
     const int64_t nb = (int64_t)1 << L.active.size();
     int32_t* tidx = (int32_t*)(ws + lay.top_idx_off);

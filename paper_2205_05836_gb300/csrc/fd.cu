@@ -73,6 +73,36 @@ int sm_count() {
   return n;
 }
 
+// Side streams per (device, caller stream), created once and kept for the
+// process: a level's merges are independent and run on them, forked from
+// and joined back into the caller's stream with events, which a CUDA graph
+// capture records as edges.  Separate sets per caller stream keep runs on
+// different streams independent; the set's mutex is held from the fork to
+// the join so that two host threads never interleave on its events.
+int side_streams(cudaStream_t caller, SideStreams** out) {
+  static std::mutex mu;
+  static std::map<std::pair<int, cudaStream_t>, SideStreams*> pool;
+  int dev = 0;
+  CUTQC_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_pair(dev, caller);
+  if (pool.size() >= 64 && !pool.count(key)) key.second = nullptr;   // many streams: share one set
+  auto it = pool.find(key);
+  if (it == pool.end()) {
+    SideStreams* p = new SideStreams();
+    for (int i = 0; i < kSideStreams; ++i) {
+      CUTQC_CUDA_TRY(cudaStreamCreateWithFlags(&p->s[i], cudaStreamNonBlocking));
+      CUTQC_CUDA_TRY(cudaEventCreateWithFlags(&p->join[i], cudaEventDisableTiming));
+    }
+    for (int i = 0; i < kSideEvents; ++i)
+      CUTQC_CUDA_TRY(cudaEventCreateWithFlags(&p->done[i], cudaEventDisableTiming));
+    CUTQC_CUDA_TRY(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
+    it = pool.emplace(key, p).first;
+  }
+  *out = it->second;
+  return CUTQC_OK;
+}
+
 // ---------------------------------------------------------------- planning
 
 namespace {
@@ -267,7 +297,7 @@ __global__ void single_copy(const float* __restrict__ T, int64_t rows, uint64_t 
 
 int run_plan(const ContractionPlan& plan, const float* const* inputs, const int64_t* in_bstride, int batch,
              float* out, int64_t out_bstride, double* sum, float alpha_final, int precision, int64_t row_begin,
-             int64_t row_end, uint8_t* ws, cudaStream_t st) {
+             int64_t row_end, uint8_t* ws, cudaStream_t caller) {
   const size_t n_in = plan.stage_of.size() - plan.stages.size();
   if (plan.stages.empty()) {
     const TensorDesc& T = plan.tensors[0];
@@ -275,8 +305,8 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
     for (int b = 0; b < T.o; ++b) mask |= (uint64_t)1 << T.pos[b];
     int64_t rows = (int64_t)1 << T.o;
     int blocks = (int)std::min<int64_t>((rows + 255) / 256, 8192);
-    single_copy<<<dim3(blocks, batch), 256, 0, st>>>(inputs[0], rows, mask, alpha_final, out, sum, in_bstride[0],
-                                                     out_bstride);
+    single_copy<<<dim3(blocks, batch), 256, 0, caller>>>(inputs[0], rows, mask, alpha_final, out, sum, in_bstride[0],
+                                                         out_bstride);
     CUTQC_LAUNCH_CHECK("single_copy");
     return CUTQC_OK;
   }
@@ -292,92 +322,143 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
     return (const float*)(ws + s.off_result);
   };
   int rc;
-  for (const PlanStage& stg0 : plan.stages) {
-    PlanStage stg = stg0;
-    int64_t sa_b = 0, sb_b = 0;
-    stg.opa.view.src = src_of(stg.a, &sa_b);
-    stg.opb.view.src = src_of(stg.b, &sb_b);
-    int64_t r0 = 0, M = stg.M;
-    if (stg.final_stage && partial) {
-      r0 = row_begin;
-      M = row_end - row_begin;
-    }
-    float* dst = stg.final_stage ? out : (float*)(ws + stg.off_result);
-    const int64_t dst_b = stg.final_stage ? out_bstride : (int64_t)stg.result_elems;
-    const float alpha = stg.final_stage ? alpha_final : 1.0f;
-    double* sum_ptr = stg.final_stage ? sum : nullptr;
-    const int streaming = stg.final_stage ? 1 : 0;
-    if (precision != CUTQC_PREC_FP32_SIMT) {
-      const bool prune = precision == CUTQC_PREC_FP16X3_TC_PRUNE && stg.final_stage && stg.K <= kPruneMaxK;
-      const size_t prune_bytes = prune_scratch_bytes(stg.K);
-      for (int b = 0; b < batch; ++b) {
-        OperandView va = stg.opa.view, vb = stg.opb.view;
-        va.src += b * sa_b;
-        vb.src += b * sb_b;
-        __half* ah = (__half*)(ws + stg.opa.off_hi) + (size_t)b * M * stg.Kp;
-        __half* al = (__half*)(ws + stg.opa.off_lo) + (size_t)b * M * stg.Kp;
-        float* as = (float*)(ws + stg.opa.off_scale) + (size_t)b * M;
-        __half* bh = (__half*)(ws + stg.opb.off_hi) + (size_t)b * stg.N * stg.Kp;
-        __half* bl = (__half*)(ws + stg.opb.off_lo) + (size_t)b * stg.N * stg.Kp;
-        float* bs = (float*)(ws + stg.opb.off_scale) + (size_t)b * stg.N;
-        int* cols = nullptr;
-        int* meta = nullptr;
-        if (prune) {
-          // the kept terms of this item, chosen on the device
-          uint8_t* pb = ws + stg.off_prune + (size_t)b * prune_bytes;
-          float* colw = (float*)pb;
-          cols = (int*)(colw + 3 * stg.K);
-          meta = cols + stg.K;
-          rc = launch_prune_select(va, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, vb,
-                                   stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), stg.N, alpha,
-                                   CUTQC_PRUNE_TOL, colw, cols, meta, reinterpret_cast<unsigned int*>(bs + 1), st);
+  auto run_stage = [&](const PlanStage& stg0, cudaStream_t st) -> int {
+      PlanStage stg = stg0;
+      int64_t sa_b = 0, sb_b = 0;
+      stg.opa.view.src = src_of(stg.a, &sa_b);
+      stg.opb.view.src = src_of(stg.b, &sb_b);
+      int64_t r0 = 0, M = stg.M;
+      if (stg.final_stage && partial) {
+        r0 = row_begin;
+        M = row_end - row_begin;
+      }
+      float* dst = stg.final_stage ? out : (float*)(ws + stg.off_result);
+      const int64_t dst_b = stg.final_stage ? out_bstride : (int64_t)stg.result_elems;
+      const float alpha = stg.final_stage ? alpha_final : 1.0f;
+      double* sum_ptr = stg.final_stage ? sum : nullptr;
+      const int streaming = stg.final_stage ? 1 : 0;
+      if (precision != CUTQC_PREC_FP32_SIMT) {
+        const bool prune = precision == CUTQC_PREC_FP16X3_TC_PRUNE && stg.final_stage && stg.K <= kPruneMaxK;
+        const size_t prune_bytes = prune_scratch_bytes(stg.K);
+        for (int b = 0; b < batch; ++b) {
+          OperandView va = stg.opa.view, vb = stg.opb.view;
+          va.src += b * sa_b;
+          vb.src += b * sb_b;
+          __half* ah = (__half*)(ws + stg.opa.off_hi) + (size_t)b * M * stg.Kp;
+          __half* al = (__half*)(ws + stg.opa.off_lo) + (size_t)b * M * stg.Kp;
+          float* as = (float*)(ws + stg.opa.off_scale) + (size_t)b * M;
+          __half* bh = (__half*)(ws + stg.opb.off_hi) + (size_t)b * stg.N * stg.Kp;
+          __half* bl = (__half*)(ws + stg.opb.off_lo) + (size_t)b * stg.N * stg.Kp;
+          float* bs = (float*)(ws + stg.opb.off_scale) + (size_t)b * stg.N;
+          int* cols = nullptr;
+          int* meta = nullptr;
+          if (prune) {
+            // the kept terms of this item, chosen on the device
+            uint8_t* pb = ws + stg.off_prune + (size_t)b * prune_bytes;
+            float* colw = (float*)pb;
+            cols = (int*)(colw + 3 * stg.K);
+            meta = cols + stg.K;
+            rc = launch_prune_select(va, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, vb,
+                                     stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), stg.N, alpha,
+                                     CUTQC_PRUNE_TOL, colw, cols, meta, reinterpret_cast<unsigned int*>(bs + 1), st);
+            if (rc) return rc;
+          }
+          rc = launch_prep_rows(va, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, stg.Kp, nullptr, ah,
+                                al, as, st, 1, 0, nullptr, cols, meta);
+          if (rc) return rc;
+          rc = launch_prep_rows(vb, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp, nullptr,
+                                bh, bl, bs, st, 1, 0, reinterpret_cast<unsigned int*>(bs + 1), cols, meta);
+          if (rc) return rc;
+          TcOperand ta{ah, al, as, M}, tb{bh, bl, bs, stg.N};
+          rc = launch_tc_gemm(ta, tb, stg.Kp, alpha, stg.mask_m, stg.mask_n, dst + b * dst_b,
+                              sum_ptr ? sum_ptr + b : nullptr, streaming, st, prune ? meta + 1 : nullptr);
           if (rc) return rc;
         }
-        rc = launch_prep_rows(va, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, stg.Kp, nullptr, ah,
-                              al, as, st, 1, 0, nullptr, cols, meta);
-        if (rc) return rc;
-        rc = launch_prep_rows(vb, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp, nullptr,
-                              bh, bl, bs, st, 1, 0, reinterpret_cast<unsigned int*>(bs + 1), cols, meta);
-        if (rc) return rc;
-        TcOperand ta{ah, al, as, M}, tb{bh, bl, bs, stg.N};
-        rc = launch_tc_gemm(ta, tb, stg.Kp, alpha, stg.mask_m, stg.mask_n, dst + b * dst_b,
-                            sum_ptr ? sum_ptr + b : nullptr, streaming, st, prune ? meta + 1 : nullptr);
-        if (rc) return rc;
+        return CUTQC_OK;
       }
-      continue;
-    }
-    const float* A;
-    const float* B;
-    int64_t lda, ldb, a_b, b_b;
-    if (stg.opa.trivial) {
-      A = stg.opa.view.src + r0 * stg.K;
-      lda = stg.K;
-      a_b = sa_b;
-    } else {
-      float* a32 = (float*)(ws + stg.opa.off32);
-      rc = launch_prep_rows(stg.opa.view, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, stg.Kp, a32,
-                            nullptr, nullptr, nullptr, st, batch, sa_b);
+      const float* A;
+      const float* B;
+      int64_t lda, ldb, a_b, b_b;
+      if (stg.opa.trivial) {
+        A = stg.opa.view.src + r0 * stg.K;
+        lda = stg.K;
+        a_b = sa_b;
+      } else {
+        float* a32 = (float*)(ws + stg.opa.off32);
+        rc = launch_prep_rows(stg.opa.view, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, stg.Kp, a32,
+                              nullptr, nullptr, nullptr, st, batch, sa_b);
+        if (rc) return rc;
+        A = a32;
+        lda = stg.Kp;
+        a_b = M * stg.Kp;
+      }
+      if (stg.opb.trivial) {
+        B = stg.opb.view.src;
+        ldb = stg.K;
+        b_b = sb_b;
+      } else {
+        float* b32 = (float*)(ws + stg.opb.off32);
+        rc = launch_prep_rows(stg.opb.view, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp,
+                              b32, nullptr, nullptr, nullptr, st, batch, sb_b);
+        if (rc) return rc;
+        B = b32;
+        ldb = stg.Kp;
+        b_b = stg.N * stg.Kp;
+      }
+      rc = launch_sgemm(A, lda, B, ldb, M, stg.N, stg.K, alpha, stg.mask_m, stg.mask_n, dst, sum_ptr, streaming, st,
+                        batch, a_b, b_b, dst_b);
       if (rc) return rc;
-      A = a32;
-      lda = stg.Kp;
-      a_b = M * stg.Kp;
+    return CUTQC_OK;
+  };
+  // A step that does not read the previous step's result can run beside it:
+  // such steps (when large enough to pay for the stream hop: 2^22 outputs
+  // or more; small steps, as in DD levels, gained nothing measurable and
+  // lost to the extra dependencies) go to side streams, after the caller's
+  // earlier work (fork)
+  // and the steps they read; the others stay on the caller's stream in plan
+  // order (waiting for any side step they read), and the side streams join
+  // it at the end.  A plan that is one chain of dependent steps therefore
+  // adds no stream hops.
+  const size_t ns = plan.stages.size();
+  std::vector<char> side(ns, 0);
+  for (size_t si = 1; si < ns && ns <= (size_t)kSideEvents; ++si) {
+    const PlanStage& x = plan.stages[si];
+    const int prev_result = plan.stages[si - 1].result;
+    const bool big = (double)x.M * (double)x.N * batch >= (double)(1 << 22);
+    side[si] = big && !x.final_stage && x.a != prev_result && x.b != prev_result;
+  }
+  const bool par = std::any_of(side.begin(), side.end(), [](char c) { return c != 0; });
+  SideStreams* ss = nullptr;
+  std::unique_lock<std::mutex> side_lock;
+  if (par) {
+    if ((rc = side_streams(caller, &ss))) return rc;
+    side_lock = std::unique_lock<std::mutex>(ss->mu);
+    CUTQC_CUDA_TRY(cudaEventRecord(ss->fork, caller));
+  }
+  int nside = 0;
+  std::vector<char> on_side(ns, 0);
+  for (size_t si = 0; si < ns; ++si) {
+    const PlanStage& stg = plan.stages[si];
+    cudaStream_t st = caller;
+    if (par) {
+      if (side[si]) {
+        st = ss->s[nside % kSideStreams];
+        ++nside;
+        on_side[si] = 1;
+        CUTQC_CUDA_TRY(cudaStreamWaitEvent(st, ss->fork, 0));
+      }
+      for (int t : {stg.a, stg.b}) {
+        const int dep = plan.stage_of[t];
+        if (dep >= 0 && (on_side[dep] || side[si])) CUTQC_CUDA_TRY(cudaStreamWaitEvent(st, ss->done[dep], 0));
+      }
     }
-    if (stg.opb.trivial) {
-      B = stg.opb.view.src;
-      ldb = stg.K;
-      b_b = sb_b;
-    } else {
-      float* b32 = (float*)(ws + stg.opb.off32);
-      rc = launch_prep_rows(stg.opb.view, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp,
-                            b32, nullptr, nullptr, nullptr, st, batch, sb_b);
-      if (rc) return rc;
-      B = b32;
-      ldb = stg.Kp;
-      b_b = stg.N * stg.Kp;
-    }
-    rc = launch_sgemm(A, lda, B, ldb, M, stg.N, stg.K, alpha, stg.mask_m, stg.mask_n, dst, sum_ptr, streaming, st,
-                      batch, a_b, b_b, dst_b);
-    if (rc) return rc;
+    if ((rc = run_stage(stg, st))) return rc;
+    if (par) CUTQC_CUDA_TRY(cudaEventRecord(ss->done[si], st));
+  }
+  nside = std::min(nside, kSideStreams);
+  for (int j = 0; j < nside; ++j) {
+    CUTQC_CUDA_TRY(cudaEventRecord(ss->join[j], ss->s[j]));
+    CUTQC_CUDA_TRY(cudaStreamWaitEvent(caller, ss->join[j], 0));
   }
   return CUTQC_OK;
 }
