@@ -101,6 +101,15 @@ const char* cutqc_version(void);
  * waits (0 = none expired).  Synchronises the device. */
 int cutqc_device_status(int32_t* status_out);
 
+/* Failure-path self test (no paper counterpart): launches one CTA that waits
+ * on an mbarrier nothing arrives on, with the same bounded wait (about 2 s of
+ * clock cycles) as every mbarrier wait in the library's kernels.  When the
+ * bound expires the CTA records CUTQC_ETIMEOUT in the device status word and
+ * returns; the context stays usable.  waited_dev (device int32, nullable)
+ * receives the cycles waited / 2^20.  Asynchronous on `stream`; read the
+ * code with cutqc_device_status().  Nothing faults, traps or hangs.        */
+int cutqc_selftest_wait_timeout(int32_t* waited_dev, void* stream);
+
 /* ------------------------------------------------------------ attribution
  * Circuit Cutting section (Eq. 1 and the worked example: three measurement
  * and four initialisation variants per cut).  With the one-qubit identity

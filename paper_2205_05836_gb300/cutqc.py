@@ -111,6 +111,13 @@ def cutqc_device_status():
     return v.value
 
 
+def cutqc_selftest_wait_timeout(waited=None, stream=None):
+    """Launches the bounded-wait self test (a wait nothing satisfies); the
+    device status word then reads CUTQC_ETIMEOUT (cutqc_device_status)."""
+    _check(lib().cutqc_selftest_wait_timeout(_ptr(waited), _stream(stream)))
+    return waited
+
+
 def cutqc_sum_f64(x, out=None, stream=None):
     import torch
     if out is None:

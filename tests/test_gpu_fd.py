@@ -476,3 +476,28 @@ def test_fd_captured_in_cuda_graph(cq, precision):
         assert torch.equal(out, ref)
         assert abs(total.item() - ref_total.item()) <= 1e-12
     assert cq.cutqc_device_status() == 0
+
+
+def test_bounded_wait_expires_with_status(cq):
+    """Failure path without a GPU fault: a device wait that nothing satisfies
+    gives up after its bound (about 2 s of clock cycles), the status word
+    reads CUTQC_ETIMEOUT (-4) once and is then clear, and the context still
+    runs a reconstruction correctly."""
+    import torch
+    from workloads import circuits as C
+    from workloads.cutting import search_cut
+    from workloads.simulate import simulate_variants
+    from oracle import fd, metrics
+    assert cq.cutqc_device_status() == 0
+    waited = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cq.cutqc_selftest_wait_timeout(waited)
+    assert cq.cutqc_device_status() == -4
+    assert cq.cutqc_device_status() == 0
+    assert waited.item() >= 1000          # >= ~1e9 cycles: the bound, not an early exit
+    cut = search_cut(C.brickwall(8, 6, 0), 7, 2, restarts=4)
+    subs = cut.subcircuits
+    var = [simulate_variants(s) for s in subs]
+    ref = fd.reconstruct_kron(_oracle_att(subs, var), [s.edges for s in subs], cut.K)
+    out, _ = cq.cutqc_reconstruct_fd(subs, _gpu_att(cq, subs, var), 0, 1)
+    assert metrics.tv(out.cpu().numpy().astype(np.float64), ref) <= TV_GATE
+    assert cq.cutqc_device_status() == 0
