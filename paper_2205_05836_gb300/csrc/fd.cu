@@ -323,91 +323,91 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
   };
   int rc;
   auto run_stage = [&](const PlanStage& stg0, cudaStream_t st) -> int {
-      PlanStage stg = stg0;
-      int64_t sa_b = 0, sb_b = 0;
-      stg.opa.view.src = src_of(stg.a, &sa_b);
-      stg.opb.view.src = src_of(stg.b, &sb_b);
-      int64_t r0 = 0, M = stg.M;
-      if (stg.final_stage && partial) {
-        r0 = row_begin;
-        M = row_end - row_begin;
-      }
-      float* dst = stg.final_stage ? out : (float*)(ws + stg.off_result);
-      const int64_t dst_b = stg.final_stage ? out_bstride : (int64_t)stg.result_elems;
-      const float alpha = stg.final_stage ? alpha_final : 1.0f;
-      double* sum_ptr = stg.final_stage ? sum : nullptr;
-      const int streaming = stg.final_stage ? 1 : 0;
-      if (precision != CUTQC_PREC_FP32_SIMT) {
-        const bool prune = precision == CUTQC_PREC_FP16X3_TC_PRUNE && stg.final_stage && stg.K <= kPruneMaxK;
-        const size_t prune_bytes = prune_scratch_bytes(stg.K);
-        for (int b = 0; b < batch; ++b) {
-          OperandView va = stg.opa.view, vb = stg.opb.view;
-          va.src += b * sa_b;
-          vb.src += b * sb_b;
-          __half* ah = (__half*)(ws + stg.opa.off_hi) + (size_t)b * M * stg.Kp;
-          __half* al = (__half*)(ws + stg.opa.off_lo) + (size_t)b * M * stg.Kp;
-          float* as = (float*)(ws + stg.opa.off_scale) + (size_t)b * M;
-          __half* bh = (__half*)(ws + stg.opb.off_hi) + (size_t)b * stg.N * stg.Kp;
-          __half* bl = (__half*)(ws + stg.opb.off_lo) + (size_t)b * stg.N * stg.Kp;
-          float* bs = (float*)(ws + stg.opb.off_scale) + (size_t)b * stg.N;
-          int* cols = nullptr;
-          int* meta = nullptr;
-          if (prune) {
-            // the kept terms of this item, chosen on the device
-            uint8_t* pb = ws + stg.off_prune + (size_t)b * prune_bytes;
-            float* colw = (float*)pb;
-            cols = (int*)(colw + 3 * stg.K);
-            meta = cols + stg.K;
-            rc = launch_prune_select(va, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, vb,
-                                     stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), stg.N, alpha,
-                                     CUTQC_PRUNE_TOL, colw, cols, meta, reinterpret_cast<unsigned int*>(bs + 1), st);
-            if (rc) return rc;
-          }
-          rc = launch_prep_rows(va, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, stg.Kp, nullptr, ah,
-                                al, as, st, 1, 0, nullptr, cols, meta);
-          if (rc) return rc;
-          rc = launch_prep_rows(vb, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp, nullptr,
-                                bh, bl, bs, st, 1, 0, reinterpret_cast<unsigned int*>(bs + 1), cols, meta);
-          if (rc) return rc;
-          TcOperand ta{ah, al, as, M}, tb{bh, bl, bs, stg.N};
-          rc = launch_tc_gemm(ta, tb, stg.Kp, alpha, stg.mask_m, stg.mask_n, dst + b * dst_b,
-                              sum_ptr ? sum_ptr + b : nullptr, streaming, st, prune ? meta + 1 : nullptr);
+    PlanStage stg = stg0;
+    int64_t sa_b = 0, sb_b = 0;
+    stg.opa.view.src = src_of(stg.a, &sa_b);
+    stg.opb.view.src = src_of(stg.b, &sb_b);
+    int64_t r0 = 0, M = stg.M;
+    if (stg.final_stage && partial) {
+      r0 = row_begin;
+      M = row_end - row_begin;
+    }
+    float* dst = stg.final_stage ? out : (float*)(ws + stg.off_result);
+    const int64_t dst_b = stg.final_stage ? out_bstride : (int64_t)stg.result_elems;
+    const float alpha = stg.final_stage ? alpha_final : 1.0f;
+    double* sum_ptr = stg.final_stage ? sum : nullptr;
+    const int streaming = stg.final_stage ? 1 : 0;
+    if (precision != CUTQC_PREC_FP32_SIMT) {
+      const bool prune = precision == CUTQC_PREC_FP16X3_TC_PRUNE && stg.final_stage && stg.K <= kPruneMaxK;
+      const size_t prune_bytes = prune_scratch_bytes(stg.K);
+      for (int b = 0; b < batch; ++b) {
+        OperandView va = stg.opa.view, vb = stg.opb.view;
+        va.src += b * sa_b;
+        vb.src += b * sb_b;
+        __half* ah = (__half*)(ws + stg.opa.off_hi) + (size_t)b * M * stg.Kp;
+        __half* al = (__half*)(ws + stg.opa.off_lo) + (size_t)b * M * stg.Kp;
+        float* as = (float*)(ws + stg.opa.off_scale) + (size_t)b * M;
+        __half* bh = (__half*)(ws + stg.opb.off_hi) + (size_t)b * stg.N * stg.Kp;
+        __half* bl = (__half*)(ws + stg.opb.off_lo) + (size_t)b * stg.N * stg.Kp;
+        float* bs = (float*)(ws + stg.opb.off_scale) + (size_t)b * stg.N;
+        int* cols = nullptr;
+        int* meta = nullptr;
+        if (prune) {
+          // the kept terms of this item, chosen on the device
+          uint8_t* pb = ws + stg.off_prune + (size_t)b * prune_bytes;
+          float* colw = (float*)pb;
+          cols = (int*)(colw + 3 * stg.K);
+          meta = cols + stg.K;
+          rc = launch_prune_select(va, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, vb,
+                                   stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), stg.N, alpha,
+                                   CUTQC_PRUNE_TOL, colw, cols, meta, reinterpret_cast<unsigned int*>(bs + 1), st);
           if (rc) return rc;
         }
-        return CUTQC_OK;
-      }
-      const float* A;
-      const float* B;
-      int64_t lda, ldb, a_b, b_b;
-      if (stg.opa.trivial) {
-        A = stg.opa.view.src + r0 * stg.K;
-        lda = stg.K;
-        a_b = sa_b;
-      } else {
-        float* a32 = (float*)(ws + stg.opa.off32);
-        rc = launch_prep_rows(stg.opa.view, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, stg.Kp, a32,
-                              nullptr, nullptr, nullptr, st, batch, sa_b);
+        rc = launch_prep_rows(va, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, stg.Kp, nullptr, ah,
+                              al, as, st, 1, 0, nullptr, cols, meta);
         if (rc) return rc;
-        A = a32;
-        lda = stg.Kp;
-        a_b = M * stg.Kp;
-      }
-      if (stg.opb.trivial) {
-        B = stg.opb.view.src;
-        ldb = stg.K;
-        b_b = sb_b;
-      } else {
-        float* b32 = (float*)(ws + stg.opb.off32);
-        rc = launch_prep_rows(stg.opb.view, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp,
-                              b32, nullptr, nullptr, nullptr, st, batch, sb_b);
+        rc = launch_prep_rows(vb, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp, nullptr,
+                              bh, bl, bs, st, 1, 0, reinterpret_cast<unsigned int*>(bs + 1), cols, meta);
         if (rc) return rc;
-        B = b32;
-        ldb = stg.Kp;
-        b_b = stg.N * stg.Kp;
+        TcOperand ta{ah, al, as, M}, tb{bh, bl, bs, stg.N};
+        rc = launch_tc_gemm(ta, tb, stg.Kp, alpha, stg.mask_m, stg.mask_n, dst + b * dst_b,
+                            sum_ptr ? sum_ptr + b : nullptr, streaming, st, prune ? meta + 1 : nullptr);
+        if (rc) return rc;
       }
-      rc = launch_sgemm(A, lda, B, ldb, M, stg.N, stg.K, alpha, stg.mask_m, stg.mask_n, dst, sum_ptr, streaming, st,
-                        batch, a_b, b_b, dst_b);
+      return CUTQC_OK;
+    }
+    const float* A;
+    const float* B;
+    int64_t lda, ldb, a_b, b_b;
+    if (stg.opa.trivial) {
+      A = stg.opa.view.src + r0 * stg.K;
+      lda = stg.K;
+      a_b = sa_b;
+    } else {
+      float* a32 = (float*)(ws + stg.opa.off32);
+      rc = launch_prep_rows(stg.opa.view, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, stg.Kp, a32,
+                            nullptr, nullptr, nullptr, st, batch, sa_b);
       if (rc) return rc;
+      A = a32;
+      lda = stg.Kp;
+      a_b = M * stg.Kp;
+    }
+    if (stg.opb.trivial) {
+      B = stg.opb.view.src;
+      ldb = stg.K;
+      b_b = sb_b;
+    } else {
+      float* b32 = (float*)(ws + stg.opb.off32);
+      rc = launch_prep_rows(stg.opb.view, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp,
+                            b32, nullptr, nullptr, nullptr, st, batch, sb_b);
+      if (rc) return rc;
+      B = b32;
+      ldb = stg.Kp;
+      b_b = stg.N * stg.Kp;
+    }
+    rc = launch_sgemm(A, lda, B, ldb, M, stg.N, stg.K, alpha, stg.mask_m, stg.mask_n, dst, sum_ptr, streaming, st,
+                      batch, a_b, b_b, dst_b);
+    if (rc) return rc;
     return CUTQC_OK;
   };
   // A step that does not read the previous step's result can run beside it:
