@@ -335,3 +335,33 @@ def test_sharded_dd_driver_on_one_gpu(cq, kind, M, T):
         assert torch.allclose(r["bins"], ref_bins[J.bins_offset:J.bins_offset + nb], atol=1e-7, rtol=0)
         assert abs(r["bin_sum"] - J.bin_sum) <= 1e-9
     assert cq.cutqc_device_status() == 0
+
+
+def test_dd_batched_60q_full_size(cq):
+    """The bench's DD configuration at full size: the 60-qubit blocked
+    brick-wall circuit (5 subcircuits <= 15 qubits), 16 active qubits per
+    level, breadth first, top 4, 4 levels and 13 jobs, through the
+    enqueue-only run with its default launch shapes: every job's active and
+    zoomed qubits as the FP64 oracle's (the same bins expanded), its bins
+    within 1e-5 of its L1 mass, its float64 total within 1e-6 relatively."""
+    import torch
+    from oracle import attribution, dd
+    from workloads.configs import dd_batched
+    w = [x for x in dd_batched() if x.n == 60][0]
+    subs = w.subcircuits
+    var = w.variants()
+    A = [attribution.attribute(v, s.w, s.in_local, s.out_local, s.in_edge, s.out_edge) for s, v in zip(subs, var)]
+    att = [cq.cutqc_attribute(s, torch.from_numpy(v).cuda()) for s, v in zip(subs, var)]
+    M, R, T = 16, 6, 4
+    jobs, n_jobs, bins = cq.cutqc_dd_run_async(subs, att, w.n, M, R, T, max_jobs=64)
+    got = cq.dd_jobs_from_device(jobs, n_jobs)
+    ref = dd.run(A, [s.out_qubit for s in subs], [s.edges for s in subs], w.K, w.n, M, R, T, strategy="bfs")
+    assert len(got) == len(ref) == 13
+    for J, rj in zip(got, ref):
+        assert list(J.active[:J.n_active]) == rj["active"]
+        assert J.zoom() == rj["zoom"]
+        b = bins[J.bins_offset:J.bins_offset + (1 << J.n_active)].cpu().numpy().astype(np.float64)
+        mass = np.abs(rj["bins"]).sum()
+        assert np.abs(b - rj["bins"]).max() <= 1e-5 * mass
+        assert abs(J.bin_sum - rj["bins"].sum()) <= 1e-6 * mass
+    assert cq.cutqc_device_status() == 0
