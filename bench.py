@@ -17,6 +17,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -104,7 +105,7 @@ class ClockSampler:
         self.proc = None
         self.nvml = None
         self.samples = []
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"cutqc_clocks_{os.getpid()}.csv")
         try:
             self.nvml = _Nvml(index)
         except Exception:
