@@ -655,7 +655,7 @@ def fd_chain_extras(dev, cq, steps=10, warmup=3):
                              "hbm_bound_ms": alg_bytes / (pk["hbm_gbs"] * 1e9) * 1e3,
                              "tensor_bound_ms_executed": 3 * alg_flops / (pk["bf16_tflops"] * 1e12) * 1e3,
                              "algorithmic_flops": alg_flops}})
-    # the roofline as the task states it: the slower of the executed tensor
+    # the roofline taken as the slower of the executed tensor
     # flops at the measured peak and the bytes at the measured bandwidth
     rf = res["roofline"]
     rf["frac_of_slower_bound"] = max(rf["hbm_bound_ms"], rf["tensor_bound_ms_executed"]) / ms

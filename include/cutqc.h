@@ -43,7 +43,7 @@ extern "C" {
 #define CUTQC_ENOMEM (-2)      /* workspace smaller than the size query */
 #define CUTQC_ECUDA (-3)       /* CUDA error (launch or runtime) */
 #define CUTQC_ETIMEOUT (-4)    /* a bounded device-side wait expired */
-#define CUTQC_EUNSUPPORTED (-5)/* valid but outside this build's limits */
+#define CUTQC_EUNSUPPORTED (-5)/* valid but outside the library's limits */
 
 #define CUTQC_F64 0
 #define CUTQC_F32 1
@@ -66,7 +66,7 @@ extern "C" {
                                    The kept terms are chosen on the device. */
 #define CUTQC_PRUNE_TOL 9.313225746154785e-10  /* 2^-30 */
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define CUTQC_MAX_QUBITS 34     /* n of an FD reconstruction (2^34 outputs) */
 #define CUTQC_MAX_CUTS 16       /* K per reconstruction */
 #define CUTQC_MAX_WIDTH 30      /* w of one subcircuit */
