@@ -720,10 +720,54 @@ def dd_extras(dev, cq, M=16, R=6, T=4, reps=5, precision=0):
         out.append({"circuit": w.name, "n": w.n, "subcircuits": len(subs), "K": w.K, "jobs": len(js), "bins": nb,
                     "root_sum_error": abs(js[0].bin_sum - 1.0), "options": opt,
                     "tuning_ms": {f"{o['merge_ctas']}/{o['topk_threads']}": round(ms, 4) for ms, o, ok in trials if ok}})
-    return {"M": M, "R": R, "T": T, "strategy": "bfs", "precision": "tc" if precision else "fp32",
-            "circuits": out, "graph_ms": ms, "bins_per_s": tot_bins / (ms * 1e-3),
-            "note": "all levels of the three circuits in one captured CUDA graph (one stream per circuit); "
-                    "selection on the device"}
+    res = {"M": M, "R": R, "T": T, "strategy": "bfs", "precision": "tc" if precision else "fp32",
+           "circuits": out, "graph_ms": ms, "bins_per_s": tot_bins / (ms * 1e-3),
+           "note": "all levels of the three circuits in one captured CUDA graph (one stream per circuit); "
+                   "selection on the device"}
+    if precision == 0:
+        res["persistent"] = dd_batch_extras(dev, cq, runs, M, R, T, tot_bins, reps)
+    return res
+
+
+def dd_batch_extras(dev, cq, runs, M, R, T, tot_bins, reps):
+    """The same three circuits in ONE persistent cooperative launch
+    (cutqc_dd_batch_*, launch shapes from tune.py), captured in a graph and
+    replayed; its records and bins must equal the level-by-level run's."""
+    import torch
+    from paper_2205_05836_gb300.tune import tune_dd_batch
+    bruns = [cq.dd_batch_run(subs, att, w.n, M, R, T, max_jobs=64) for w, subs, att, *_ in runs]
+    opt, trials = tune_dd_batch(bruns)
+    batch = cq.cutqc_dd_batch_create(bruns, opt)
+    side = torch.cuda.Stream(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        batch.launch(side)
+    g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index or 0) as clk:
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    same = True
+    for (w, subs, att, jobs, n_jobs, bins, *_), b in zip(runs, bruns):
+        ref = cq.dd_jobs_from_device(jobs, n_jobs)
+        got = cq.dd_jobs_from_device(b["jobs"], b["n_jobs"])
+        same &= len(ref) == len(got) and all(
+            (x.parent, x.parent_bin, list(x.top_idx)) == (y.parent, y.parent_bin, list(y.top_idx)) and
+            torch.equal(bins[x.bins_offset:x.bins_offset + (1 << x.n_active)],
+                        b["bins"][y.bins_offset:y.bins_offset + (1 << y.n_active)]) for x, y in zip(ref, got))
+    info = batch.info()
+    return {"ms": ms, "bins_per_s": tot_bins / (ms * 1e-3), "options": opt, "phases": info["phases"],
+            "ops": info["ops"], "ctas": info["ctas"], "matches_level_by_level": bool(same),
+            "device_status": cq.cutqc_device_status(), "clocks": clk.summary(),
+            "tuning_ms": {f"{o['merge_ctas']}/{o['topk_chunk']}": round(t, 4) for t, o, ok in trials if ok},
+            "gpu_launches_per_replay": 1,
+            "note": "one cooperative launch (and one memset) for all levels of the three circuits; "
+                    "grid barriers between phases"}
 
 
 def finite_shot_extras(dev, cq, shots=(10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6), seed=7):
@@ -818,7 +862,8 @@ def run_profile_case(args):
     GiB: for one-pass launch lists only); fd_chain_slice -- a row slice of
     the chain's last contraction; dd_dense -- one 2^30-bin recursion of the
     60-qubit DD circuit; dd_batched -- Algorithm 1 on the three DD circuits
-    (16 active qubits, top 4, breadth first)."""
+    (16 active qubits, top 4, breadth first); dd_persistent -- the same as
+    one persistent launch (cutqc_dd_batch_*)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -860,6 +905,19 @@ def run_profile_case(args):
                                                     options={"precision": prec})
         js = cq.dd_jobs_from_device(jobs, n_jobs)
         info.update({"workload": w.name, "bins": 1 << 30, "bin_sum": js[0].bin_sum})
+    elif wl == "dd_persistent":
+        from workloads.configs import dd_batched
+        runs = []
+        for w in dd_batched():
+            subs = w.subcircuits
+            att = [cq.cutqc_attribute(s, torch.from_numpy(v).cuda()) for s, v in zip(subs, w.variants())]
+            runs.append(cq.dd_batch_run(subs, att, w.n, 16, 6, 4, max_jobs=64))
+        batch = cq.cutqc_dd_batch_create(runs)
+        for _ in range(2):
+            batch.launch()
+        torch.cuda.synchronize()
+        info.update({"workload": [w.name for w in dd_batched()], "batch": batch.info(),
+                     "device_status": cq.cutqc_device_status()})
     else:
         from workloads.configs import dd_batched
         runs = []
@@ -890,7 +948,7 @@ def main():
                     help="run the kernels once on a row slice (for ncu) and exit")
     ap.add_argument("--profile-rows", type=int, default=2048)
     ap.add_argument("--profile-workload", default="fd_two_sub",
-                    choices=["fd_two_sub", "fd_chain", "fd_chain_slice", "dd_dense", "dd_batched"])
+                    choices=["fd_two_sub", "fd_chain", "fd_chain_slice", "dd_dense", "dd_batched", "dd_persistent"])
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)

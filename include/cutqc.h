@@ -286,7 +286,7 @@ typedef struct cutqc_dd_options {
  * first order), enqueued without any host synchronisation or host copy, so
  * that it can be captured in a CUDA graph and replayed: level 0 has one job,
  * every later level T jobs (the T largest bins of the previous level, chosen
- * on the device); at most min(R, ceil(n / M)) levels.
+ * on the device); at most min(R, ceil(n / M)) levels (one when T = 0).
  *   jobs_dev    device [max_jobs] records, written in level order; a record
  *               with level < 0 is a placeholder (fewer than T bins to expand)
  *   n_jobs_dev  device int32, set to the number of records written
@@ -298,6 +298,66 @@ int cutqc_dd_run_async(int n_sub, const cutqc_subcircuit* s, const float* const*
                        int n_qubits, int M, int R, int T, int max_jobs, cutqc_dd_job_result* jobs_dev,
                        int32_t* n_jobs_dev, float* bins_dev, int64_t bins_capacity,
                        const cutqc_dd_options* opt, void* ws_dev, size_t ws_bytes, void* stream);
+
+/* Algorithm 1 (breadth first, as cutqc_dd_run_async) for several circuits in
+ * ONE persistent launch.  The recursion levels of Algorithm 1 (its merge
+ * steps, the bin reconstruction of Eq. 1 on the merged tensors, and the
+ * choice of the bins to expand) are small for each circuit (2^M bins per
+ * job); here every step of every circuit is one phase of a program that a
+ * single cooperative launch walks, with a grid-wide barrier between phases
+ * and the circuits sharing each phase.  Results per run are those of
+ * cutqc_dd_run_async with FP32 reconstruction and the same merge_ctas: the
+ * same job records (bin totals within float64 rounding of their atomic sum),
+ * bins and top-T selections.
+ * One run description per circuit:
+ *   n_sub, subcircuits (host [n_sub]), attributed_dev (host array of n_sub
+ *   device pointers), n_qubits, M, R, T: as cutqc_dd_run_async (n_sub >= 2)
+ *   jobs_dev, n_jobs_dev, bins_dev, bins_capacity, max_jobs: that run's
+ *   outputs, as cutqc_dd_run_async.
+ * Options (zero fields take defaults): merge_ctas as cutqc_dd_options;
+ * topk_chunk bins per task of the chunked top-T pass (a power of two >= 256,
+ * default 2048); ctas caps the grid (default: every CTA that fits at once).
+ * cutqc_dd_batch_create validates the runs, lays out `ws_dev` (at least
+ * cutqc_dd_batch_workspace_size bytes, 256-byte aligned, owned by the caller
+ * and kept alive and untouched while the handle is used) and writes the
+ * program into it with a synchronous copy: call it outside stream capture.
+ * The run descriptions are read during the call only; the device pointers in
+ * them are baked into the program.  cutqc_dd_batch_launch enqueues one
+ * memset and one cooperative launch on `stream` (capturable in a CUDA graph);
+ * launches on one handle must not overlap.  A barrier wait that runs out
+ * (about 2 s) records CUTQC_ETIMEOUT in the device status word
+ * (cutqc_device_status) and ends the launch.  Errors: CUTQC_EINVAL (bad
+ * descriptions or options), CUTQC_EUNSUPPORTED (one subcircuit, more than 32
+ * outputs in a subcircuit, limits of cutqc_dd_run), CUTQC_ENOMEM (records,
+ * bins or workspace too small).                                             */
+typedef struct cutqc_dd_run_desc {
+  int32_t n_sub;
+  const cutqc_subcircuit* subcircuits;
+  const float* const* attributed_dev;
+  int32_t n_qubits, M, R, T;
+  int32_t max_jobs;
+  cutqc_dd_job_result* jobs_dev;
+  int32_t* n_jobs_dev;
+  float* bins_dev;
+  int64_t bins_capacity;
+} cutqc_dd_run_desc;
+
+typedef struct cutqc_dd_batch_options {
+  int32_t merge_ctas;
+  int32_t topk_chunk;
+  int32_t ctas;
+} cutqc_dd_batch_options;
+
+typedef struct cutqc_dd_batch cutqc_dd_batch;
+
+int cutqc_dd_batch_workspace_size(int n_runs, const cutqc_dd_run_desc* runs,
+                                  const cutqc_dd_batch_options* opt, size_t* bytes);
+int cutqc_dd_batch_create(int n_runs, const cutqc_dd_run_desc* runs, const cutqc_dd_batch_options* opt,
+                          void* ws_dev, size_t ws_bytes, cutqc_dd_batch** out);
+int cutqc_dd_batch_launch(const cutqc_dd_batch* batch, void* stream);
+/* Shape of the program: phases (grid barriers + 1), ops, CTAs launched.     */
+int cutqc_dd_batch_info(const cutqc_dd_batch* batch, int32_t* n_phases, int32_t* n_ops, int32_t* grid_ctas);
+int cutqc_dd_batch_destroy(cutqc_dd_batch* batch);
 
 /* ------------------------------------------------------------- reductions
  * sum_dev (device float64 scalar) += sum of x_dev[0..n) in float64.          */

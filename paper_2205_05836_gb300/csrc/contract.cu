@@ -14,6 +14,7 @@
 // the float32 CUDA-core GEMM.  The tensor-core GEMM is in gemm_tc.cu.
 #include "internal.cuh"
 #include "contract.cuh"
+#include "sgemm_tile.cuh"
 
 #include <algorithm>
 #include <mutex>
@@ -538,16 +539,7 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
 }
 
 // ------------------------------------------------------------ SIMT GEMM
-// C[m][n] = sum_s A[m][s] B[n][s], A: [M][lda], B: [N][ldb] (K-major).
-// CTA tile 128 x 128, BK = 16, 256 threads, 8 x 8 outputs per thread split
-// in two 4-wide column groups (tx*4 and 64 + tx*4) and two 4-high row groups.
-
-constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 16;
-
-__device__ __forceinline__ void store_out(float* out, uint64_t idx, float v, int streaming) {
-  if (streaming) __stcs(out + idx, v);
-  else out[idx] = v;
-}
+// (tile body in sgemm_tile.cuh)
 
 __global__ void __launch_bounds__(256)
 sgemm_kernel(const float* __restrict__ A, int64_t lda, const float* __restrict__ B, int64_t ldb,
@@ -555,99 +547,11 @@ sgemm_kernel(const float* __restrict__ A, int64_t lda, const float* __restrict__
              int m_contig_shift, int n_contig, float* __restrict__ out, double* __restrict__ sum,
              int streaming, int64_t a_bstride, int64_t b_bstride, int64_t out_bstride) {
   // batch item blockIdx.z
-  A += (int64_t)blockIdx.z * a_bstride;
-  B += (int64_t)blockIdx.z * b_bstride;
-  out += (int64_t)blockIdx.z * out_bstride;
-  if (sum) sum += blockIdx.z;
-  __shared__ __align__(16) float As[2][SG_BK][SG_BM + 4];
-  __shared__ __align__(16) float Bs[2][SG_BK][SG_BN + 4];
-  const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
-  const int64_t m0 = (int64_t)blockIdx.y * SG_BM;
-  const int64_t n0 = (int64_t)blockIdx.x * SG_BN;
-  // global load mapping: each thread loads 8 values of A and 8 of B per k-tile
-  // (rows lr and lr + 64, k columns lk*4 .. +3)
-  const int lr = tid >> 2, lk = (tid & 3) * 4;
-  float acc[8][8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-
-  float ra[8], rb[8];
-  auto gload = [&](int64_t k0) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      int64_t mr = m0 + lr + 64 * h, nr = n0 + lr + 64 * h;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int64_t kk = k0 + lk + q;
-        ra[h * 4 + q] = (mr < M && kk < K) ? __ldg(A + mr * lda + kk) : 0.f;
-        rb[h * 4 + q] = (nr < N && kk < K) ? __ldg(B + nr * ldb + kk) : 0.f;
-      }
-    }
-  };
-  auto sstore = [&](int buf) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        As[buf][lk + q][lr + 64 * h] = ra[h * 4 + q];
-        Bs[buf][lk + q][lr + 64 * h] = rb[h * 4 + q];
-      }
-  };
-  const int64_t nk = (K + SG_BK - 1) / SG_BK;
-  gload(0);
-  sstore(0);
-  __syncthreads();
-  for (int64_t kt = 0; kt < nk; ++kt) {
-    const int buf = kt & 1;
-    if (kt + 1 < nk) gload((kt + 1) * SG_BK);
-#pragma unroll
-    for (int k = 0; k < SG_BK; ++k) {
-      float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4]);
-      float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + ty * 4]);
-      float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 4]);
-      float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][64 + tx * 4]);
-      float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-    }
-    if (kt + 1 < nk) sstore(buf ^ 1);
-    __syncthreads();
-  }
-  // epilogue
-  double local = 0.0;
-  uint64_t coff[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    int64_t n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
-    coff[j] = n_contig ? (uint64_t)n : pdep64((uint64_t)n, mask_n);
-  }
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    int64_t m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
-    if (m >= M) continue;
-    uint64_t roff = m_contig_shift >= 0 ? ((uint64_t)m << m_contig_shift) : pdep64((uint64_t)m, mask_m);
-    float part[8];      // pairwise float partial per row of 8, float64 across rows
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      int64_t n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
-      part[j] = 0.f;
-      if (n >= N) continue;
-      float v = acc[i][j] * alpha;
-      store_out(out, roff | coff[j], v, streaming);
-      part[j] = v;
-    }
-    local += (double)(((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7])));
-  }
-  if (sum) {
-    for (int off = 16; off; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
-    if ((tid & 31) == 0) atomicAdd(sum, local);
-  }
+  const DenseRows la{A + (int64_t)blockIdx.z * a_bstride, lda};
+  const DenseRows lb{B + (int64_t)blockIdx.z * b_bstride, ldb};
+  sgemm_tile(la, lb, M, N, K, alpha, mask_m, mask_n, m_contig_shift, n_contig,
+             out + (int64_t)blockIdx.z * out_bstride, sum ? sum + blockIdx.z : nullptr, streaming, blockIdx.y,
+             blockIdx.x);
 }
 
 int launch_sgemm(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M, int64_t N,

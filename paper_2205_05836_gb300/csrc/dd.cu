@@ -11,6 +11,8 @@
 // launch per step), and the T largest bins are selected per job.
 #include "internal.cuh"
 #include "contract.cuh"
+#include "dd_kernels.cuh"
+#include "dd_host.cuh"
 
 #include <algorithm>
 #include <cstring>
@@ -23,208 +25,27 @@ namespace cutqc {
 
 namespace {
 
-// Compensated float32 accumulation (Kahan) of one column over the merged rows.
-struct Kahan {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float v) {
-    float y = v - c;
-    float t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-};
-
-// Zoom source of a merge launch: either a per-job array of zoom values over
-// the subcircuit's output bits (zoom_dev), or the level's job records, from
-// which each job's value is derived (bit t = the fixed value of output qubit
-// outq[t], for the qubits below lo), or one constant (zoom_val).
-struct ZoomFromJobs {
-  const cutqc_dd_job_result* jobs;   // null: not used
-  int o, lo;
-  int8_t outq[32];
-};
-
-__device__ __forceinline__ uint64_t job_zoom(const ZoomFromJobs& zj, int job) {
-  const cutqc_dd_job_result& J = zj.jobs[job];
-  uint64_t z = 0;
-  for (int t = 0; t < zj.o; ++t) {
-    const int q = zj.outq[t];
-    if (q < zj.lo && ((J.zoom_val[q >> 6] >> (q & 63)) & 1)) z |= (uint64_t)1 << t;
-  }
-  return z;
-}
-
 // grid: x = CTAs walking the (merged row a, job) pairs, z = slice of the
-// merged index range (2^log_slices slices; slice s writes its partial sums
-// to out + s * n_jobs * rows_a * C, reduced by dd_merge_reduce when there
-// are several).  Threads split columns and, when there are few columns, the
-// slice's merged indices; sub-slices are combined through shared memory.
+// merged index range (body in dd_kernels.cuh).
 __global__ void __launch_bounds__(256)
 dd_merge_kernel(const float* __restrict__ att, int k, uint64_t act_mask, uint64_t merged_mask, uint64_t zoom_mask,
                 uint64_t zoom_val, const uint64_t* __restrict__ zoom_dev, const ZoomFromJobs zj, int n_jobs,
                 int64_t rows_a, int n_merged, int log_slices, float* __restrict__ out) {
-  __shared__ float red[256];
-  const int64_t C = (int64_t)1 << (2 * k);
-  const int64_t Mper = (int64_t)1 << (n_merged - log_slices);
-  const int64_t m0 = (int64_t)blockIdx.z * Mper;
-  const int cw = (int)(C < 256 ? C : 256);
-  const int slices = 256 / cw;
-  const int c_local = threadIdx.x % cw;
-  const int slice = threadIdx.x / cw;
-  for (int64_t ra = blockIdx.x; ra < rows_a * n_jobs; ra += gridDim.x) {
-    const int job = (int)(ra / rows_a);
-    const int64_t a = ra - (int64_t)job * rows_a;
-    const uint64_t z = (zj.jobs ? job_zoom(zj, job) : zoom_dev ? __ldg(zoom_dev + job) : zoom_val) & zoom_mask;
-    const uint64_t base = pdep64((uint64_t)a, act_mask) | z;
-    float* dst = out + (((int64_t)blockIdx.z * n_jobs + job) * rows_a + a) * C;
-    for (int64_t c0 = 0; c0 < C; c0 += cw) {
-      Kahan acc;
-      if (slice < slices)
-        for (int64_t m = m0 + slice; m < m0 + Mper; m += slices) {
-          const uint64_t x = base | pdep64((uint64_t)m, merged_mask);
-          acc.add(__ldg(att + (int64_t)x * C + c0 + c_local));
-        }
-      red[threadIdx.x] = acc.s;
-      __syncthreads();
-      if (slice == 0) {
-        float s = red[c_local];
-        for (int q = 1; q < slices; ++q) s += red[q * cw + c_local];
-        dst[c0 + c_local] = s;
-      }
-      __syncthreads();
-    }
-  }
+  dd_merge_body<false>(att, k, act_mask, merged_mask, zoom_mask, zoom_val, zoom_dev, zj, n_jobs, rows_a, n_merged,
+                       log_slices, out, blockIdx.x, gridDim.x, blockIdx.z);
 }
 
-// CTAs of a merge launch: enough to fill the GPU once, each walking rows
-inline unsigned merge_grid(int64_t rows, int slices) {
-  const int64_t cap = std::max<int64_t>(1, (int64_t)sm_count() * 8 / std::max(1, slices));
-  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(rows, cap));
-}
-
-// out[e] = sum over the S slices of part[s * E + e], in slice order.
 __global__ void dd_merge_reduce(const float* __restrict__ part, int S, int64_t E, float* __restrict__ out) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
-    Kahan acc;
-    for (int q = 0; q < S; ++q) acc.add(__ldg(part + (int64_t)q * E + e));
-    out[e] = acc.s;
-  }
+  dd_merge_reduce_body<false>(part, S, E, out, blockIdx.x, gridDim.x);
 }
 
-// The T largest bins of each job by (value desc, index asc); the float64 bin
-// total is left in bin_sum by the reconstruction's epilogue.  CTA (job j,
-// chunk c) scans entries [c * chunk_len, (c + 1) * chunk_len) of job j's n
-// entries and writes its T best to slot (j * gridDim.y + c).  kCand = false:
-// the entries are bins and an entry's index is its position; kCand = true:
-// the entries are (value, index) candidates of an earlier pass (index -1 =
-// none), which is how large jobs are finished (chunked pass, then one CTA
-// per job over the chunks' candidates).  One pass: each thread keeps its
-// own best TCAP (sorted), then T rounds pick the block's best head and
-// advance its owner.
-__device__ __forceinline__ bool dd_better(float v, int i, float w, int j) {
-  return v > w || (v == w && i < j);
-}
-
+// CTA (job blockIdx.x, chunk blockIdx.y) of the top-T selection.
 template <int TCAP, bool kCand>
 __global__ void __launch_bounds__(1024)
 dd_topk_kernel(const float* __restrict__ vals, const int32_t* __restrict__ cidx, int64_t n, int64_t chunk_len, int T,
                int32_t* __restrict__ top_idx, float* __restrict__ top_val) {
-  __shared__ float sv[32];
-  __shared__ int si[32];
-  __shared__ int win_i;
-  const float* b = vals + (int64_t)blockIdx.x * n;
-  const int32_t* ci = kCand ? cidx + (int64_t)blockIdx.x * n : nullptr;
-  const int64_t lo = (int64_t)blockIdx.y * chunk_len;
-  const int64_t hi = lo + chunk_len < n ? lo + chunk_len : n;
-  const int64_t slot = ((int64_t)blockIdx.x * gridDim.y + blockIdx.y) * T;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float lv[TCAP];
-  int li[TCAP];
-#pragma unroll
-  for (int u = 0; u < TCAP; ++u) { lv[u] = -INFINITY; li[u] = -1; }   // read only once filled
-  int cnt = 0;
-  auto offer = [&](float v, int idx) {
-    if (cnt == T && !dd_better(v, idx, lv[T - 1], li[T - 1])) return;
-    int pos = cnt < T ? cnt : T - 1;
-#pragma unroll
-    for (int u = TCAP - 1; u > 0; --u)
-      if (u <= pos && dd_better(v, idx, lv[u - 1], li[u - 1])) { lv[u] = lv[u - 1]; li[u] = li[u - 1]; pos = u - 1; }
-    // pos is now the first slot whose left neighbour ranks before (v, idx)
-    lv[pos] = v;
-    li[pos] = idx;
-    if (cnt < T) ++cnt;
-  };
-  int64_t tail0 = lo;
-  if (!kCand && (((uintptr_t)(b + lo)) & 15) == 0) {
-    // bins: float4 loads, four in flight per thread (the order in which a
-    // thread offers entries does not matter: ties compare indices)
-    constexpr int U = 4;
-    const float4* p4 = reinterpret_cast<const float4*>(b + lo);
-    const int64_t n4 = (hi - lo) >> 2;
-    for (int64_t q = threadIdx.x; q < n4; q += U * (int64_t)blockDim.x) {
-      float4 v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int64_t qu = q + u * (int64_t)blockDim.x;
-        v[u] = qu < n4 ? __ldg(p4 + qu) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int64_t qu = q + u * (int64_t)blockDim.x;
-        if (qu < n4) {
-          const int i0 = (int)(lo + 4 * qu);
-          offer(v[u].x, i0); offer(v[u].y, i0 + 1); offer(v[u].z, i0 + 2); offer(v[u].w, i0 + 3);
-        }
-      }
-    }
-    tail0 = lo + 4 * n4;
-  }
-  for (int64_t i = tail0 + threadIdx.x; i < hi; i += blockDim.x) {
-    const float v = __ldg(b + i);
-    const int idx = kCand ? __ldg(ci + i) : (int)i;
-    if (kCand && idx < 0) continue;
-    offer(v, idx);
-  }
-  int head = 0;
-  for (int t = 0; t < T; ++t) {
-    float bv = -INFINITY;
-    int bi = -1;
-#pragma unroll
-    for (int u = 0; u < TCAP; ++u)
-      if (u == head && head < cnt) { bv = lv[u]; bi = li[u]; }
-    for (int off = 16; off; off >>= 1) {
-      const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-      if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
-    }
-    if (lane == 0) { sv[warp] = bv; si[warp] = bi; }
-    __syncthreads();
-    if (warp == 0) {
-      const int nw = blockDim.x >> 5;
-      bv = lane < nw ? sv[lane] : -INFINITY;
-      bi = lane < nw ? si[lane] : -1;
-      for (int off = 16; off; off >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
-      }
-      if (lane == 0) {
-        win_i = bi;
-        top_idx[slot + t] = bi;
-        top_val[slot + t] = bi >= 0 ? bv : 0.f;
-      }
-    }
-    __syncthreads();
-    // the owner of the winning index advances (indices are distinct)
-    if (head < cnt && win_i >= 0) {
-      int cur = -1;
-#pragma unroll
-      for (int u = 0; u < TCAP; ++u)
-        if (u == head) cur = li[u];
-      if (cur == win_i) ++head;
-    }
-    __syncthreads();
-  }
+  dd_topk_body<TCAP, kCand, false>(vals, cidx, n, chunk_len, T, top_idx, top_val, blockIdx.x, blockIdx.y,
+                                   gridDim.y);
 }
 
 // Large jobs: chunks of the chunked first pass of the top-T selection.
@@ -290,6 +111,14 @@ int launch_merge(const cutqc_subcircuit* s, const float* att, uint64_t act, uint
   return CUTQC_OK;
 }
 
+}  // namespace
+
+}  // namespace cutqc
+
+// ------------------------------------------------- shapes of a DD level
+// (declared in dd_host.cuh; also used by the persistent kernel's builder)
+namespace cutqc {
+
 int dd_inputs(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, const int32_t* bin_bit,
               std::vector<TensorDesc>* in, int* total_bits) {
   if (n_sub < 1 || !s || !active_bits) return set_error(CUTQC_EINVAL, "bad DD job description");
@@ -324,7 +153,118 @@ int dd_inputs(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, 
   return CUTQC_OK;
 }
 
-}  // namespace
+// Workspace of one step: the contraction plan's (for the given precision;
+// for FP32 sized for any bin order) and the chunked top-T candidates.
+int dd_step_ws(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, int n_jobs, int precision,
+                      size_t* bytes) {
+  if (!bytes) return set_error(CUTQC_EINVAL, "null bytes");
+  std::vector<TensorDesc> in;
+  int tot = 0;
+  // the bin order decides which operands need a gather copy: plan with the
+  // identity order and size for the worst case
+  std::vector<int32_t> ident;
+  for (int i = 0; i < n_sub && active_bits; ++i)
+    for (int b = 0; b < active_bits[i]; ++b) ident.push_back((int32_t)ident.size());
+  int rc = dd_inputs(n_sub, s, active_bits, ident.data(), &in, &tot);
+  if (rc) return rc;
+  if (n_jobs < 1) return set_error(CUTQC_EINVAL, "n_jobs must be >= 1");
+  ContractionPlan plan;
+  if ((rc = plan_contraction_batched(in, precision, n_jobs, &plan, true))) return rc;
+  *bytes = align_up(plan.ws_bytes, 256) + topk_scratch((int64_t)1 << tot, n_jobs);
+  return CUTQC_OK;
+}
+
+int level_shape(int n_sub, const cutqc_subcircuit* s, int n, int M, int depth, LevelShape* L) {
+  L->depth = depth;
+  L->active.clear();
+  for (int q = depth * M; q < std::min(n, depth * M + M); ++q) L->active.push_back(q);
+  const int lo = depth * M, hi = depth * M + (int)L->active.size();
+  L->active_bits.assign(n_sub, 0);
+  L->bin_bit.clear();
+  L->act_mask.assign(n_sub, 0);
+  L->zoom_mask.assign(n_sub, 0);
+  for (int i = 0; i < n_sub; ++i) {
+    const int o = s[i].w - s[i].k_out;
+    for (int t = 0; t < o; ++t) {
+      const int q = s[i].out_qubit[t];
+      if (q < 0 || q >= n) return set_error(CUTQC_EINVAL, "out_qubit %d outside 0..%d", q, n - 1);
+      if (q >= lo && q < hi) {
+        L->act_mask[i] |= (uint64_t)1 << t;
+        L->active_bits[i]++;
+        L->bin_bit.push_back(q - lo);
+      } else if (q < lo) {
+        L->zoom_mask[i] |= (uint64_t)1 << t;
+      }
+    }
+  }
+  return CUTQC_OK;
+}
+
+// Workspace for one level of n_jobs jobs.
+// merge_ctas: about how many CTAs share one subcircuit's merge (slices of the
+// merged index range, each at least 64 long)
+int level_layout(int n_sub, const cutqc_subcircuit* s, const LevelShape& L, int n_jobs, RunLayout* R,
+                 int merge_ctas) {
+  size_t ws = 0;
+  auto take = [&](size_t b) { size_t o = ws; ws = align_up(ws + b, 256); return o; };
+  for (int i = 0; i < n_sub; ++i) {
+    const int k = s[i].k_in + s[i].k_out;
+    const size_t elems = (size_t)n_jobs * ((size_t)1 << L.active_bits[i]) * ((size_t)1 << (2 * k));
+    R->merged_off[i] = take(elems * sizeof(float));
+    R->zoom_off[i] = take((size_t)n_jobs * sizeof(uint64_t));
+    const int o = s[i].w - s[i].k_out;
+    const int n_merged = o - L.active_bits[i] - __builtin_popcountll(L.zoom_mask[i]);
+    int ls = 0;
+    while (ls < n_merged - 6 && ((int64_t)n_jobs << (L.active_bits[i] + ls + 1)) <= merge_ctas) ++ls;
+    R->log_slices[i] = ls;
+    R->part_off[i] = ls ? take(elems * ((size_t)1 << ls) * sizeof(float)) : 0;
+  }
+  size_t step = 0, step_tc = 0;
+  int rc = dd_step_ws(n_sub, s, L.active_bits.data(), n_jobs, CUTQC_PREC_FP32_SIMT, &step);
+  if (rc) return rc;
+  if ((rc = dd_step_ws(n_sub, s, L.active_bits.data(), n_jobs, CUTQC_PREC_FP16X3_TC_PRUNE, &step_tc))) return rc;
+  step = std::max(step, step_tc);
+  R->step_off = take(step);
+  R->top_idx_off = take((size_t)n_jobs * 32 * sizeof(int32_t));
+  R->top_val_off = take((size_t)n_jobs * 32 * sizeof(float));
+  R->sum_off = take((size_t)n_jobs * sizeof(double));
+  R->total = ws;
+  return CUTQC_OK;
+}
+
+int validate_run(int n_sub, const cutqc_subcircuit* s, int n, int M, int T) {
+  if (n_sub < 1 || n_sub > 64) return set_error(CUTQC_EINVAL, "n_sub must be in 1..64");
+  if (n < 1 || n > 128) return set_error(CUTQC_EUNSUPPORTED, "n_qubits must be in 1..128");
+  if (M < 1 || M > 30) return set_error(CUTQC_EUNSUPPORTED, "M must be in 1..30");
+  if (T < 0 || T > 32) return set_error(CUTQC_EUNSUPPORTED, "T must be in 0..32");
+  int tot = 0;
+  for (int i = 0; i < n_sub; ++i) {
+    int rc = validate_subcircuit(&s[i]);
+    if (rc) return rc;
+    tot += s[i].w - s[i].k_out;
+  }
+  if (tot != n) return set_error(CUTQC_EINVAL, "outputs (%d) != n_qubits (%d)", tot, n);
+  return CUTQC_OK;
+}
+
+// Level workspace (reused by every level) and, after it, room for the job
+// records of a level-synchronous run (used by cutqc_dd_run).
+int run_ws(int n_sub, const cutqc_subcircuit* s, int n, int M, int T, size_t* level_bytes, size_t* total) {
+  size_t best = 0;
+  const int depths = (n + M - 1) / M;
+  for (int d = 0; d < depths; ++d) {
+    LevelShape L;
+    int rc = level_shape(n_sub, s, n, M, d, &L);
+    if (rc) return rc;
+    RunLayout R;
+    if ((rc = level_layout(n_sub, s, L, std::max(1, T), &R, kMergeCtasMax))) return rc;
+    best = std::max(best, R.total);
+  }
+  const size_t records = 1 + (size_t)(depths - 1) * std::max(1, T);
+  *level_bytes = align_up(best, 256);
+  *total = *level_bytes + align_up(records * sizeof(cutqc_dd_job_result), 256) + 256;
+  return CUTQC_OK;
+}
 
 }  // namespace cutqc
 
@@ -352,27 +292,6 @@ extern "C" int cutqc_dd_merge_batch(const cutqc_subcircuit* s, const float* attr
   if (active_mask & zoom_mask) return set_error(CUTQC_EINVAL, "a bit cannot be active and zoomed");
   const uint64_t mrg = all & ~active_mask & ~zoom_mask;
   return launch_merge(s, attributed, active_mask, mrg, zoom_mask, 0, zoom_dev, n_jobs, merged, (cudaStream_t)stream);
-}
-
-// Workspace of one step: the contraction plan's (for the given precision;
-// for FP32 sized for any bin order) and the chunked top-T candidates.
-static int dd_step_ws(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, int n_jobs, int precision,
-                      size_t* bytes) {
-  if (!bytes) return set_error(CUTQC_EINVAL, "null bytes");
-  std::vector<TensorDesc> in;
-  int tot = 0;
-  // the bin order decides which operands need a gather copy: plan with the
-  // identity order and size for the worst case
-  std::vector<int32_t> ident;
-  for (int i = 0; i < n_sub && active_bits; ++i)
-    for (int b = 0; b < active_bits[i]; ++b) ident.push_back((int32_t)ident.size());
-  int rc = dd_inputs(n_sub, s, active_bits, ident.data(), &in, &tot);
-  if (rc) return rc;
-  if (n_jobs < 1) return set_error(CUTQC_EINVAL, "n_jobs must be >= 1");
-  ContractionPlan plan;
-  if ((rc = plan_contraction_batched(in, precision, n_jobs, &plan, true))) return rc;
-  *bytes = align_up(plan.ws_bytes, 256) + topk_scratch((int64_t)1 << tot, n_jobs);
-  return CUTQC_OK;
 }
 
 extern "C" int cutqc_dd_step_workspace_size(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits,
@@ -468,212 +387,18 @@ extern "C" int cutqc_sum_f64(const float* x, int64_t n, double* sum, void* strea
 namespace cutqc {
 namespace {
 
-struct LevelInfo {
-  int level, depth, n_active;
-  int8_t active[32];
-};
-
-// One warp.  Completes the records of this level's jobs (bin totals, the T
-// largest bins, bin offsets) and, when merged qubits remain, writes the
-// records of the next level: the T largest bins over all valid jobs of this
-// level, ordered by value (stable: job order, then each job's own order, for
-// equal values) -- Algorithm 1's list L truncated to T.  Records past the
-// candidates are placeholders (level -1).  Lane 0 ranks the candidates; the
-// 32-entry arrays of a record are written one entry per lane.
 __global__ void dd_select_kernel(cutqc_dd_job_result* __restrict__ jobs, int job0, int nj, LevelInfo L,
                                  int64_t bins_off0, int64_t nb, const double* __restrict__ bsum,
                                  const int32_t* __restrict__ tidx, const float* __restrict__ tval, int T,
                                  int has_children, int n_next, int32_t* __restrict__ n_jobs_dev) {
-  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
-  for (int j = 0; j < nj; ++j) {
-    cutqc_dd_job_result& J = jobs[job0 + j];
-    const bool valid = J.level >= 0;
-    const int32_t ti = (valid && lane < T) ? tidx[(int64_t)j * T + lane] : -1;
-    J.top_idx[lane] = ti;
-    J.top_val[lane] = ti >= 0 ? tval[(int64_t)j * T + lane] : 0.f;
-    J.active[lane] = lane < L.n_active ? L.active[lane] : 0;
-    if (lane == 0) {
-      J.n_active = L.n_active;
-      J.bin_sum = valid ? bsum[j] : 0.0;
-      J.bins_offset = bins_off0 + (int64_t)j * nb;
-    }
-  }
-  if (!has_children) {
-    if (lane == 0) *n_jobs_dev = job0 + nj;
-    return;
-  }
-  __shared__ int cj[32], cb[32], cnt_s;
-  // the level's candidates (nj * T of them, job order) loaded in parallel
-  __shared__ int kb[1024];
-  __shared__ float kv[1024];
-  const int ncand = nj * T <= 1024 ? nj * T : 1024;
-  for (int q = lane; q < ncand; q += 32) {
-    const int j = q / T;
-    const int b = jobs[job0 + j].level >= 0 ? tidx[q] : -1;
-    kb[q] = b;
-    kv[q] = b >= 0 ? tval[q] : 0.f;
-  }
-  __syncwarp();
-  if (lane == 0) {
-    float cv[32];
-    int cnt = 0;
-    for (int j = 0; j < nj; ++j) {
-      for (int t = 0; t < T; ++t) {
-        const int q = j * T + t;
-        if (q >= ncand) break;
-        const int b = kb[q];
-        if (b < 0) continue;
-        const float v = kv[q];
-        int pos = cnt;
-        while (pos > 0 && cv[pos - 1] < v) --pos;     // after every entry of equal value
-        if (pos >= T) continue;
-        const int last = cnt < T ? cnt : T - 1;
-        for (int u = last; u > pos; --u) { cv[u] = cv[u - 1]; cj[u] = cj[u - 1]; cb[u] = cb[u - 1]; }
-        cv[pos] = v;
-        cj[pos] = j;
-        cb[pos] = b;
-        if (cnt < T) ++cnt;
-      }
-    }
-    cnt_s = cnt;
-  }
-  __syncwarp();
-  const int cnt = cnt_s;
-  const int next0 = job0 + nj;
-  for (int c = 0; c < n_next; ++c) {
-    cutqc_dd_job_result& R = jobs[next0 + c];
-    R.top_idx[lane] = -1;
-    R.top_val[lane] = 0.f;
-    R.active[lane] = 0;
-    if (lane == 0) {
-      R.n_active = 0;
-      R.bin_sum = 0.0;
-      R.bins_offset = 0;
-      R.depth = L.depth + 1;
-      if (c < cnt) {
-        const cutqc_dd_job_result& P = jobs[job0 + cj[c]];
-        R.level = L.level + 1;
-        R.parent = job0 + cj[c];
-        R.parent_bin = cb[c];
-        for (int w = 0; w < 2; ++w) { R.zoom_mask[w] = P.zoom_mask[w]; R.zoom_val[w] = P.zoom_val[w]; }
-        for (int a = 0; a < L.n_active; ++a) {
-          const int q = L.active[a];
-          R.zoom_mask[q >> 6] |= (uint64_t)1 << (q & 63);
-          if ((cb[c] >> a) & 1) R.zoom_val[q >> 6] |= (uint64_t)1 << (q & 63);
-        }
-      } else {
-        R.level = -1;
-        R.parent = -1;
-        R.parent_bin = -1;
-        for (int w = 0; w < 2; ++w) { R.zoom_mask[w] = 0; R.zoom_val[w] = 0; }
-      }
-    }
-  }
-  if (lane == 0) *n_jobs_dev = next0 + n_next;
+  if (blockIdx.x != 0) return;
+  dd_select_body<false>(jobs, job0, nj, L, bins_off0, nb, bsum, tidx, tval, T, has_children, n_next, n_jobs_dev);
 }
 
 // The first job: nothing zoomed.
 __global__ void dd_first_job_kernel(cutqc_dd_job_result* __restrict__ jobs) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  cutqc_dd_job_result& J = jobs[0];
-  J.level = 0;
-  J.depth = 0;
-  J.parent = -1;
-  J.parent_bin = -1;
-  for (int w = 0; w < 2; ++w) { J.zoom_mask[w] = 0; J.zoom_val[w] = 0; }
-}
-
-struct LevelShape {
-  int depth = 0;
-  std::vector<int> active;                 // qubits, ascending
-  std::vector<int32_t> active_bits;        // per subcircuit
-  std::vector<int32_t> bin_bit;            // subcircuit-major
-  std::vector<uint64_t> act_mask, zoom_mask;   // per subcircuit, over output bits
-};
-
-int level_shape(int n_sub, const cutqc_subcircuit* s, int n, int M, int depth, LevelShape* L) {
-  L->depth = depth;
-  L->active.clear();
-  for (int q = depth * M; q < std::min(n, depth * M + M); ++q) L->active.push_back(q);
-  const int lo = depth * M, hi = depth * M + (int)L->active.size();
-  L->active_bits.assign(n_sub, 0);
-  L->bin_bit.clear();
-  L->act_mask.assign(n_sub, 0);
-  L->zoom_mask.assign(n_sub, 0);
-  for (int i = 0; i < n_sub; ++i) {
-    const int o = s[i].w - s[i].k_out;
-    for (int t = 0; t < o; ++t) {
-      const int q = s[i].out_qubit[t];
-      if (q < 0 || q >= n) return set_error(CUTQC_EINVAL, "out_qubit %d outside 0..%d", q, n - 1);
-      if (q >= lo && q < hi) {
-        L->act_mask[i] |= (uint64_t)1 << t;
-        L->active_bits[i]++;
-        L->bin_bit.push_back(q - lo);
-      } else if (q < lo) {
-        L->zoom_mask[i] |= (uint64_t)1 << t;
-      }
-    }
-  }
-  return CUTQC_OK;
-}
-
-struct RunLayout {
-  size_t merged_off[64];
-  size_t zoom_off[64];
-  size_t part_off[64];      // partial sums of the slices (when log_slices > 0)
-  int log_slices[64];
-  size_t step_off = 0, top_idx_off = 0, top_val_off = 0, sum_off = 0;
-  size_t total = 0;
-};
-
-// Workspace for one level of n_jobs jobs.
-constexpr int kMergeCtasDefault = 1024, kMergeCtasMax = 4096;
-
-// merge_ctas: about how many CTAs share one subcircuit's merge (slices of the
-// merged index range, each at least 64 long)
-int level_layout(int n_sub, const cutqc_subcircuit* s, const LevelShape& L, int n_jobs, RunLayout* R,
-                 int merge_ctas = kMergeCtasDefault) {
-  size_t ws = 0;
-  auto take = [&](size_t b) { size_t o = ws; ws = align_up(ws + b, 256); return o; };
-  for (int i = 0; i < n_sub; ++i) {
-    const int k = s[i].k_in + s[i].k_out;
-    const size_t elems = (size_t)n_jobs * ((size_t)1 << L.active_bits[i]) * ((size_t)1 << (2 * k));
-    R->merged_off[i] = take(elems * sizeof(float));
-    R->zoom_off[i] = take((size_t)n_jobs * sizeof(uint64_t));
-    const int o = s[i].w - s[i].k_out;
-    const int n_merged = o - L.active_bits[i] - __builtin_popcountll(L.zoom_mask[i]);
-    int ls = 0;
-    while (ls < n_merged - 6 && ((int64_t)n_jobs << (L.active_bits[i] + ls + 1)) <= merge_ctas) ++ls;
-    R->log_slices[i] = ls;
-    R->part_off[i] = ls ? take(elems * ((size_t)1 << ls) * sizeof(float)) : 0;
-  }
-  size_t step = 0, step_tc = 0;
-  int rc = dd_step_ws(n_sub, s, L.active_bits.data(), n_jobs, CUTQC_PREC_FP32_SIMT, &step);
-  if (rc) return rc;
-  if ((rc = dd_step_ws(n_sub, s, L.active_bits.data(), n_jobs, CUTQC_PREC_FP16X3_TC_PRUNE, &step_tc))) return rc;
-  step = std::max(step, step_tc);
-  R->step_off = take(step);
-  R->top_idx_off = take((size_t)n_jobs * 32 * sizeof(int32_t));
-  R->top_val_off = take((size_t)n_jobs * 32 * sizeof(float));
-  R->sum_off = take((size_t)n_jobs * sizeof(double));
-  R->total = ws;
-  return CUTQC_OK;
-}
-
-int validate_run(int n_sub, const cutqc_subcircuit* s, int n, int M, int T) {
-  if (n_sub < 1 || n_sub > 64) return set_error(CUTQC_EINVAL, "n_sub must be in 1..64");
-  if (n < 1 || n > 128) return set_error(CUTQC_EUNSUPPORTED, "n_qubits must be in 1..128");
-  if (M < 1 || M > 30) return set_error(CUTQC_EUNSUPPORTED, "M must be in 1..30");
-  if (T < 0 || T > 32) return set_error(CUTQC_EUNSUPPORTED, "T must be in 0..32");
-  int tot = 0;
-  for (int i = 0; i < n_sub; ++i) {
-    int rc = validate_subcircuit(&s[i]);
-    if (rc) return rc;
-    tot += s[i].w - s[i].k_out;
-  }
-  if (tot != n) return set_error(CUTQC_EINVAL, "outputs (%d) != n_qubits (%d)", tot, n);
-  return CUTQC_OK;
+  dd_first_job_body(jobs);
 }
 
 }  // namespace
@@ -681,25 +406,6 @@ int validate_run(int n_sub, const cutqc_subcircuit* s, int n, int M, int T) {
 
 namespace cutqc {
 namespace {
-
-// Level workspace (reused by every level) and, after it, room for the job
-// records of a level-synchronous run (used by cutqc_dd_run).
-int run_ws(int n_sub, const cutqc_subcircuit* s, int n, int M, int T, size_t* level_bytes, size_t* total) {
-  size_t best = 0;
-  const int depths = (n + M - 1) / M;
-  for (int d = 0; d < depths; ++d) {
-    LevelShape L;
-    int rc = level_shape(n_sub, s, n, M, d, &L);
-    if (rc) return rc;
-    RunLayout R;
-    if ((rc = level_layout(n_sub, s, L, std::max(1, T), &R, kMergeCtasMax))) return rc;
-    best = std::max(best, R.total);
-  }
-  const size_t records = 1 + (size_t)(depths - 1) * std::max(1, T);
-  *level_bytes = align_up(best, 256);
-  *total = *level_bytes + align_up(records * sizeof(cutqc_dd_job_result), 256) + 256;
-  return CUTQC_OK;
-}
 
 // Enqueue a level-synchronous run: no host synchronisation, no host copies.
 int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att, int n, int M, int Rmax, int T,
@@ -719,7 +425,7 @@ int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att
   for (int i = 0; i < n_sub; ++i)
     if (s[i].w - s[i].k_out > 32) return set_error(CUTQC_EUNSUPPORTED, "more than 32 outputs in a subcircuit");
   const int depths = (n + M - 1) / M;
-  const int levels = std::min(Rmax, depths);
+  const int levels = T > 0 ? std::min(Rmax, depths) : 1;   // T = 0 expands nothing
   const int Tn = std::max(1, T);
   // sizes first: every level's jobs and bins must fit
   {

@@ -1,0 +1,689 @@
+// Algorithm 1 (breadth first) for several circuits in one persistent launch.
+//
+// The level-by-level path (dd.cu) enqueues a chain of small launches per
+// level: merges, slice reductions, one GEMM per contraction step, top-T, the
+// level selection.  Those jobs are small (2^16 bins at M = 16), so the chain
+// is bound by launch latency and by each launch's ramp and tail, not by the
+// GPU.  Here the whole run of every circuit is one program of phases; one
+// cooperative launch of a grid that fits on the GPU at once walks it, with a
+// grid-wide barrier between phases.  Phase p holds the p-th step of every
+// circuit, so the circuits fill the GPU together:
+//   merge (+ zero the bin totals)  ->  slice reduction (when sliced)  ->
+//   one phase per depth of the contraction plan (independent steps share a
+//   phase; the operands are gathered on the fly by the GEMM tile, no staging
+//   copy)  ->  chunked top-T of each job's bins  ->  the level selection
+//   (each job's top T from its chunks' candidates, then Algorithm 1's list L
+//   truncated to T, written as the next level's job records).
+// Within a phase a CTA takes tasks (merge walkers, GEMM tiles, top-T chunks)
+// in a fixed stride; the results are those of the level-by-level path: the
+// same merge slicing and partial-sum order, the same GEMM tile and k order,
+// the same selection order (bin totals are float64 atomics in both).
+//
+// Memory ordering: data written in one phase is read in a later one by other
+// CTAs, after a barrier whose arrival is preceded and whose exit is followed
+// by a device-scope fence; those reads use ld.global.cg (through L2), never
+// the non-coherent read-only path.  Every barrier wait is bounded: a CTA that
+// waits too long records CUTQC_ETIMEOUT in the device status word and raises
+// an abort flag, and every CTA then returns.
+#include "internal.cuh"
+#include "contract.cuh"
+#include "dd_kernels.cuh"
+#include "dd_host.cuh"
+#include "sgemm_tile.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace cutqc {
+namespace {
+
+constexpr long long kBarrierTimeoutCycles = 4000000000LL;   // ~2 s at 2 GHz
+constexpr int kThreads = 256;
+constexpr int kTopkChunkDefault = 2048;
+
+// A contraction operand read in place: operand row m = (xp, open) with xp
+// the high bits (moved to source row bits bit[j] when permute) and open the
+// low 2 * n_open bits; element s = source column pdep(open, open_dmask) |
+// pdep(s, shared_dmask) (s itself when contig).  The same map as the staged
+// gather of the level-by-level path.
+struct GView {
+  const float* src;
+  int64_t bstride;       // floats between batch items (jobs)
+  int64_t C;             // source columns, 4^k
+  uint64_t open_dmask, shared_dmask;
+  int n_open, contig, permute, nbits;
+  int8_t bit[40];
+};
+
+template <bool kCoherent>
+struct GatherRows {
+  const float* src;      // this batch item's source
+  int64_t C;
+  uint64_t open_dmask, shared_dmask;
+  int n_open, contig;
+  const GView* v;        // row bit map (read twice per tile)
+  __device__ __forceinline__ GatherRows(const GView& g, int64_t b)
+      : src(g.src + b * g.bstride), C(g.C), open_dmask(g.open_dmask), shared_dmask(g.shared_dmask),
+        n_open(g.n_open), contig(g.contig), v(&g) {}
+  struct Row {
+    const float* p;
+    uint64_t obase;
+  };
+  __device__ __forceinline__ Row row(int64_t m) const {
+    const uint64_t xp = (uint64_t)m >> (2 * n_open);
+    uint64_t x = xp;
+    if (v->permute) {
+      x = 0;
+      const int nb = v->nbits;
+      for (int j = 0; j < nb; ++j) x |= ((xp >> j) & 1) << v->bit[j];
+    }
+    const uint64_t open = (uint64_t)m & (((uint64_t)1 << (2 * n_open)) - 1);
+    return Row{src + (int64_t)x * C, pdep64(open, open_dmask)};
+  }
+  __device__ __forceinline__ float at(const Row& r, int64_t s) const {
+    const int64_t c = contig ? s : (int64_t)(r.obase | pdep64((uint64_t)s, shared_dmask));
+    return ldx<kCoherent>(r.p + c);
+  }
+};
+
+enum OpType : int { OP_ZERO = 0, OP_MERGE, OP_REDUCE, OP_GEMM, OP_TOPK, OP_SELECT };
+
+struct ZeroOp {          // bin totals of a level (and the first job record)
+  double* p;
+  int n;
+  cutqc_dd_job_result* first_job;
+};
+struct MergeOp {
+  const float* att;
+  float* out;
+  ZoomFromJobs zj;
+  uint64_t act, mrg, zm;
+  int64_t rows_a;
+  int k, n_jobs, n_merged, log_slices, nx;
+};
+struct ReduceOp {
+  const float* part;
+  float* out;
+  int64_t E;
+  int S, nblocks;
+};
+struct GemmOp {
+  GView a, b;
+  int64_t M, N, K;
+  float alpha;
+  uint64_t mask_m, mask_n;
+  int m_shift, n_contig, streaming, gm, gn;
+  float* out;
+  int64_t out_bstride;
+  double* sum;
+};
+struct TopkOp {
+  const float* vals;
+  int32_t* cidx;
+  float* cval;
+  int64_t n, clen;
+  int T, chunks;
+};
+struct SelectOp {
+  cutqc_dd_job_result* jobs;
+  LevelInfo L;
+  int64_t bins_off0, nb;
+  const double* bsum;
+  const int32_t* cidx;
+  const float* cval;
+  int32_t* tidx;
+  float* tval;
+  int32_t* n_jobs_dev;
+  int job0, nj, ncand, T, has_children, n_next;
+};
+struct Op {
+  int type, task0, ntasks;
+  union {
+    ZeroOp zero;
+    MergeOp merge;
+    ReduceOp reduce;
+    GemmOp gemm;
+    TopkOp topk;
+    SelectOp select;
+  } u;
+};
+
+struct GridBar {
+  unsigned int arrived;
+  unsigned int gen;
+  int abort;
+};
+
+struct Program {
+  const Op* ops;
+  const int* phase_op;       // [n_phases + 1]: ops of phase p
+  const int* phase_tasks;    // [n_phases]
+  int n_phases;
+  GridBar* bar;
+  int* status;
+};
+
+// Grid-wide barrier of a cooperative launch (every CTA resident).  Returns
+// false when the run is aborted (a wait ran out, here or in another CTA).
+__device__ bool grid_barrier(GridBar* g, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int res = 1;
+    volatile unsigned int* vgen = &g->gen;
+    volatile int* vabort = &g->abort;
+    const unsigned int my_gen = *vgen;
+    __threadfence();
+    if (atomicAdd(&g->arrived, 1u) == gridDim.x - 1) {
+      atomicExch(&g->arrived, 0u);
+      __threadfence();
+      atomicAdd(&g->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == my_gen) {
+        if (*vabort) { res = 0; break; }
+        if (clock64() - t0 > kBarrierTimeoutCycles) {
+          atomicExch(&g->abort, 1);
+          record_status(status, CUTQC_ETIMEOUT);
+          res = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = res && !*vabort;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <int TCAP>
+__device__ __forceinline__ void select_task(const SelectOp& s) {
+  // each job's T best from its chunks' candidates, then the level selection
+  if (s.T > 0)
+    for (int j = 0; j < s.nj; ++j)
+      dd_topk_body<TCAP, true, true>(s.cval, s.cidx, s.ncand, s.ncand, s.T, s.tidx, s.tval, j, 0, 1);
+  dd_select_body<true>(s.jobs, s.job0, s.nj, s.L, s.bins_off0, s.nb, s.bsum, s.tidx, s.tval, s.T, s.has_children,
+                       s.n_next, s.n_jobs_dev);
+}
+
+__device__ __forceinline__ void run_task(const Op& op, int t) {
+  switch (op.type) {
+    case OP_ZERO: {
+      const ZeroOp& z = op.u.zero;
+      for (int i = threadIdx.x; i < z.n; i += blockDim.x) z.p[i] = 0.0;
+      if (z.first_job && threadIdx.x == 0) dd_first_job_body(z.first_job);
+      break;
+    }
+    case OP_MERGE: {
+      const MergeOp& m = op.u.merge;
+      dd_merge_body<true>(m.att, m.k, m.act, m.mrg, m.zm, 0, nullptr, m.zj, m.n_jobs, m.rows_a, m.n_merged,
+                          m.log_slices, m.out, t % m.nx, m.nx, t / m.nx);
+      break;
+    }
+    case OP_REDUCE: {
+      const ReduceOp& r = op.u.reduce;
+      dd_merge_reduce_body<true>(r.part, r.S, r.E, r.out, t, r.nblocks);
+      break;
+    }
+    case OP_GEMM: {
+      const GemmOp& g = op.u.gemm;
+      const int per = g.gm * g.gn;
+      const int b = t / per, rem = t - b * per;
+      const GatherRows<true> la(g.a, b), lb(g.b, b);
+      sgemm_tile(la, lb, g.M, g.N, g.K, g.alpha, g.mask_m, g.mask_n, g.m_shift, g.n_contig,
+                 g.out + (int64_t)b * g.out_bstride, g.sum ? g.sum + b : nullptr, g.streaming, rem / g.gn,
+                 rem % g.gn);
+      break;
+    }
+    case OP_TOPK: {
+      const TopkOp& k = op.u.topk;
+      if (k.T <= 4)
+        dd_topk_body<4, false, true>(k.vals, nullptr, k.n, k.clen, k.T, k.cidx, k.cval, t / k.chunks, t % k.chunks,
+                                     k.chunks);
+      else
+        dd_topk_body<32, false, true>(k.vals, nullptr, k.n, k.clen, k.T, k.cidx, k.cval, t / k.chunks,
+                                      t % k.chunks, k.chunks);
+      break;
+    }
+    case OP_SELECT: {
+      const SelectOp& s = op.u.select;
+      if (s.T <= 4) select_task<4>(s);
+      else select_task<32>(s);
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) dd_persistent_kernel(const Program pg) {
+  for (int p = 0; p < pg.n_phases; ++p) {
+    const int o0 = __ldg(pg.phase_op + p), o1 = __ldg(pg.phase_op + p + 1);
+    const int nt = __ldg(pg.phase_tasks + p);
+    int oi = o0;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+      while (oi + 1 < o1 && t >= pg.ops[oi + 1].task0) ++oi;   // tasks ascend with the op index
+      run_task(pg.ops[oi], t - pg.ops[oi].task0);
+      __syncthreads();
+    }
+    if (p + 1 < pg.n_phases && !grid_barrier(pg.bar, pg.status)) return;
+  }
+}
+
+// ------------------------------------------------------------------ host
+
+struct BatchOpts {
+  int merge_ctas = kMergeCtasDefault;
+  int topk_chunk = kTopkChunkDefault;
+  int ctas = 0;   // 0: every CTA that fits at once
+};
+
+int read_opts(const cutqc_dd_batch_options* o, BatchOpts* b) {
+  *b = BatchOpts{};
+  if (!o) return CUTQC_OK;
+  if (o->merge_ctas < 0 || o->merge_ctas > kMergeCtasMax)
+    return set_error(CUTQC_EINVAL, "merge_ctas must be in 0..%d", kMergeCtasMax);
+  if (o->topk_chunk < 0 || (o->topk_chunk && (o->topk_chunk < 256 || (o->topk_chunk & (o->topk_chunk - 1)))))
+    return set_error(CUTQC_EINVAL, "topk_chunk must be 0 or a power of two >= 256");
+  if (o->ctas < 0) return set_error(CUTQC_EINVAL, "ctas must be >= 0");
+  if (o->merge_ctas) b->merge_ctas = o->merge_ctas;
+  if (o->topk_chunk) b->topk_chunk = o->topk_chunk;
+  b->ctas = o->ctas;
+  return CUTQC_OK;
+}
+
+struct Built {
+  std::vector<Op> ops;
+  std::vector<int> phase_op, phase_tasks;
+  size_t ops_off = 0, phase_off = 0, tasks_off = 0, total = 0;
+};
+
+// Builds the program of all runs for a workspace at `base` (nullptr: sizes
+// only; the layout does not depend on the address).
+int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& opt, uint8_t* base, Built* out) {
+  if (n_runs < 1 || !runs) return set_error(CUTQC_EINVAL, "no runs");
+  std::vector<std::vector<std::vector<Op>>> phases(n_runs);   // [run][phase] ops
+  std::vector<size_t> run_bytes(n_runs), run_topk_off(n_runs);
+  // pass 1: per-run workspace sizes (level workspace + top-T candidates)
+  for (int r = 0; r < n_runs; ++r) {
+    const cutqc_dd_run_desc& R = runs[r];
+    int rc = validate_run(R.n_sub, R.subcircuits, R.n_qubits, R.M, R.T);
+    if (rc) return rc;
+    if (R.n_sub < 2) return set_error(CUTQC_EUNSUPPORTED, "run %d: one subcircuit (no contraction)", r);
+    if (!R.attributed_dev || !R.jobs_dev || !R.n_jobs_dev || !R.bins_dev || R.max_jobs < 1 || R.R < 1)
+      return set_error(CUTQC_EINVAL, "run %d: bad arguments", r);
+    for (int i = 0; i < R.n_sub; ++i) {
+      if (!R.attributed_dev[i]) return set_error(CUTQC_EINVAL, "run %d: null attributed tensor", r);
+      if (R.subcircuits[i].w - R.subcircuits[i].k_out > 32)
+        return set_error(CUTQC_EUNSUPPORTED, "run %d: more than 32 outputs in a subcircuit", r);
+    }
+    const int depths = (R.n_qubits + R.M - 1) / R.M;
+    const int levels = R.T > 0 ? std::min(R.R, depths) : 1;   // T = 0 expands nothing
+    const int Tn = std::max(1, R.T);
+    size_t lvl = 0, topk = 0;
+    int64_t jobs_total = 0, bins_total = 0;
+    for (int level = 0; level < levels; ++level) {
+      const int nj = level == 0 ? 1 : Tn;
+      LevelShape L;
+      if ((rc = level_shape(R.n_sub, R.subcircuits, R.n_qubits, R.M, level, &L))) return rc;
+      RunLayout lay;
+      if ((rc = level_layout(R.n_sub, R.subcircuits, L, nj, &lay, opt.merge_ctas))) return rc;
+      lvl = std::max(lvl, lay.total);
+      const int64_t nb = (int64_t)1 << L.active.size();
+      const int64_t chunks = (nb + opt.topk_chunk - 1) / opt.topk_chunk;
+      topk = std::max(topk, (size_t)nj * chunks * Tn * (sizeof(int32_t) + sizeof(float)));
+      jobs_total += nj;
+      bins_total += (int64_t)nj * nb;
+    }
+    if (jobs_total > R.max_jobs)
+      return set_error(CUTQC_ENOMEM, "run %d: %d levels need %lld job records", r, levels, (long long)jobs_total);
+    if (bins_total > R.bins_capacity)
+      return set_error(CUTQC_ENOMEM, "run %d: bins_capacity too small (%lld needed)", r, (long long)bins_total);
+    run_topk_off[r] = align_up(lvl, 256);
+    run_bytes[r] = run_topk_off[r] + align_up(topk, 256);
+  }
+  size_t off = align_up(sizeof(GridBar), 256);
+  std::vector<size_t> run_off(n_runs);
+  for (int r = 0; r < n_runs; ++r) {
+    run_off[r] = off;
+    off += run_bytes[r];
+  }
+  const size_t data_end = off;
+  // pass 2: the phases of each run
+  for (int r = 0; r < n_runs; ++r) {
+    const cutqc_dd_run_desc& R = runs[r];
+    const cutqc_subcircuit* s = R.subcircuits;
+    uint8_t* ws = base ? base + run_off[r] : nullptr;
+    int32_t* cidx = ws ? (int32_t*)(ws + run_topk_off[r]) : nullptr;
+    const int depths = (R.n_qubits + R.M - 1) / R.M;
+    const int levels = R.T > 0 ? std::min(R.R, depths) : 1;
+    const int Tn = std::max(1, R.T);
+    auto& ph = phases[r];
+    auto phase = [&](size_t p) -> std::vector<Op>& {
+      if (ph.size() <= p) ph.resize(p + 1);
+      return ph[p];
+    };
+    int job0 = 0;
+    int64_t bins_off = 0;
+    for (int level = 0; level < levels; ++level) {
+      const int nj = level == 0 ? 1 : Tn;
+      LevelShape L;
+      int rc = level_shape(R.n_sub, s, R.n_qubits, R.M, level, &L);
+      if (rc) return rc;
+      RunLayout lay;
+      if ((rc = level_layout(R.n_sub, s, L, nj, &lay, opt.merge_ctas))) return rc;
+      const int64_t nb = (int64_t)1 << L.active.size();
+      double* bsum = ws ? (double*)(ws + lay.sum_off) : nullptr;
+      // phase: zero the bin totals (and write the first record), merges
+      const size_t p_merge = ph.size();
+      {
+        Op z{};
+        z.type = OP_ZERO;
+        z.ntasks = 1;
+        z.u.zero.p = bsum;
+        z.u.zero.n = nj;
+        z.u.zero.first_job = level == 0 ? R.jobs_dev : nullptr;
+        phase(p_merge).push_back(z);
+      }
+      std::vector<const float*> merged(R.n_sub);
+      bool any_slices = false;
+      for (int i = 0; i < R.n_sub; ++i) {
+        const int o = s[i].w - s[i].k_out;
+        const uint64_t all = o >= 64 ? ~0ull : (((uint64_t)1 << o) - 1);
+        const uint64_t mrg = all & ~L.act_mask[i] & ~L.zoom_mask[i];
+        const int k = s[i].k_in + s[i].k_out;
+        const int a = __builtin_popcountll(L.act_mask[i]);
+        const int ls = lay.log_slices[i];
+        float* mdev = ws ? (float*)(ws + lay.merged_off[i]) : nullptr;
+        float* part = ls ? (ws ? (float*)(ws + lay.part_off[i]) : nullptr) : mdev;
+        const int64_t rows_a = (int64_t)1 << a;
+        Op m{};
+        m.type = OP_MERGE;
+        MergeOp& mo = m.u.merge;
+        mo.att = R.attributed_dev[i];
+        mo.out = part;
+        mo.zj.jobs = R.jobs_dev + job0;
+        mo.zj.o = o;
+        mo.zj.lo = level * R.M;
+        for (int t = 0; t < o; ++t) mo.zj.outq[t] = (int8_t)s[i].out_qubit[t];
+        mo.act = L.act_mask[i];
+        mo.mrg = mrg;
+        mo.zm = L.zoom_mask[i];
+        mo.rows_a = rows_a;
+        mo.k = k;
+        mo.n_jobs = nj;
+        mo.n_merged = __builtin_popcountll(mrg);
+        mo.log_slices = ls;
+        mo.nx = (int)merge_grid(rows_a * nj, 1 << ls);
+        m.ntasks = mo.nx << ls;
+        phase(p_merge).push_back(m);
+        if (ls) {
+          any_slices = true;
+          const int64_t E = ((int64_t)nj << a) << (2 * k);
+          Op q{};
+          q.type = OP_REDUCE;
+          q.u.reduce.part = part;
+          q.u.reduce.out = mdev;
+          q.u.reduce.E = E;
+          q.u.reduce.S = 1 << ls;
+          q.u.reduce.nblocks = (int)std::min<int64_t>((E + kThreads - 1) / kThreads, (int64_t)sm_count() * 8);
+          q.ntasks = q.u.reduce.nblocks;
+          phase(p_merge + 1).push_back(q);
+        }
+        merged[i] = mdev;
+      }
+      const size_t p_contract = p_merge + (any_slices ? 2 : 1);
+      // the bin reconstruction: the planner's steps, one phase per depth
+      std::vector<TensorDesc> in;
+      int tot = 0;
+      if ((rc = dd_inputs(R.n_sub, s, L.active_bits.data(), L.bin_bit.data(), &in, &tot))) return rc;
+      ContractionPlan plan;
+      if ((rc = plan_contraction_batched(in, CUTQC_PREC_FP32_SIMT, nj, &plan))) return rc;
+      if (plan.stages.empty()) return set_error(CUTQC_EUNSUPPORTED, "run %d: nothing to contract", r);
+      uint8_t* step = ws ? ws + lay.step_off : nullptr;
+      const size_t n_in = in.size();
+      std::vector<int> depth(plan.tensors.size(), 0);
+      int max_depth = 0;
+      for (const PlanStage& stg : plan.stages) {
+        const int d = 1 + std::max(depth[stg.a], depth[stg.b]);
+        depth[stg.result] = d;
+        max_depth = std::max(max_depth, d);
+        auto view_of = [&](const PlanOperand& op, int t, GView* g) -> int {
+          const OperandView& v = op.view;
+          if (t < (int)n_in) {
+            g->src = merged[t];
+            g->bstride = ((int64_t)1 << in[t].o) << (2 * in[t].edges.size());
+          } else {
+            const PlanStage& prod = plan.stages[plan.stage_of[t]];
+            g->src = step ? (const float*)(step + prod.off_result) : nullptr;
+            g->bstride = (int64_t)prod.result_elems;
+          }
+          g->C = (int64_t)1 << (2 * v.k);
+          g->open_dmask = v.open_dmask;
+          g->shared_dmask = v.shared_dmask;
+          g->n_open = v.n_open;
+          g->contig = v.n_open == 0 && v.shared_dmask == (uint64_t)(g->C - 1);
+          g->nbits = (int)op.row_bits.size();
+          if (g->nbits > (int)sizeof(g->bit)) return set_error(CUTQC_EUNSUPPORTED, "too many row bits");
+          g->permute = 0;
+          for (int j = 0; j < g->nbits; ++j) {
+            g->bit[j] = (int8_t)op.row_bits[j];
+            if (op.row_bits[j] != j) g->permute = 1;
+          }
+          return CUTQC_OK;
+        };
+        Op g{};
+        g.type = OP_GEMM;
+        GemmOp& go = g.u.gemm;
+        if ((rc = view_of(stg.opa, stg.a, &go.a)) || (rc = view_of(stg.opb, stg.b, &go.b))) return rc;
+        go.M = stg.M;
+        go.N = stg.N;
+        go.K = stg.K;
+        go.mask_m = stg.mask_m;
+        go.mask_n = stg.mask_n;
+        go.m_shift = mask_contig_shift(stg.mask_m);
+        go.n_contig = mask_is_low(stg.mask_n);
+        const int64_t gm = (stg.M + SG_BM - 1) / SG_BM, gn = (stg.N + SG_BN - 1) / SG_BN;
+        if (gm * gn * nj > 0x3fffffff) return set_error(CUTQC_EUNSUPPORTED, "run %d: too many GEMM tiles", r);
+        go.gm = (int)gm;
+        go.gn = (int)gn;
+        if (stg.final_stage) {
+          go.alpha = std::ldexp(1.0f, -plan.K);
+          go.out = R.bins_dev + bins_off;
+          go.out_bstride = nb;
+          go.sum = bsum;
+          go.streaming = 1;
+        } else {
+          go.alpha = 1.0f;
+          go.out = step ? (float*)(step + stg.off_result) : nullptr;
+          go.out_bstride = (int64_t)stg.result_elems;
+          go.sum = nullptr;
+          go.streaming = 0;
+        }
+        g.ntasks = (int)(gm * gn * nj);
+        phase(p_contract + d - 1).push_back(g);
+      }
+      size_t p_next = p_contract + max_depth;
+      // chunked top-T, then the selection
+      const int64_t chunks = (nb + opt.topk_chunk - 1) / opt.topk_chunk;
+      float* cval = cidx ? (float*)(cidx + (size_t)nj * chunks * Tn) : nullptr;
+      if (R.T > 0) {
+        Op k{};
+        k.type = OP_TOPK;
+        k.u.topk.vals = R.bins_dev + bins_off;
+        k.u.topk.cidx = cidx;
+        k.u.topk.cval = cval;
+        k.u.topk.n = nb;
+        k.u.topk.clen = std::min<int64_t>(nb, opt.topk_chunk);
+        k.u.topk.T = R.T;
+        k.u.topk.chunks = (int)chunks;
+        k.ntasks = (int)(nj * chunks);
+        phase(p_next++).push_back(k);
+      }
+      {
+        Op q{};
+        q.type = OP_SELECT;
+        q.ntasks = 1;
+        SelectOp& so = q.u.select;
+        so.jobs = R.jobs_dev;
+        so.L.level = level;
+        so.L.depth = level;
+        so.L.n_active = (int)L.active.size();
+        for (int a = 0; a < so.L.n_active; ++a) so.L.active[a] = (int8_t)L.active[a];
+        so.bins_off0 = bins_off;
+        so.nb = nb;
+        so.bsum = bsum;
+        so.cidx = cidx;
+        so.cval = cval;
+        so.tidx = ws ? (int32_t*)(ws + lay.top_idx_off) : nullptr;
+        so.tval = ws ? (float*)(ws + lay.top_val_off) : nullptr;
+        so.n_jobs_dev = R.n_jobs_dev;
+        so.job0 = job0;
+        so.nj = nj;
+        so.ncand = (int)(chunks * R.T);
+        so.T = R.T;
+        so.has_children = level + 1 < levels && R.T > 0;
+        so.n_next = so.has_children ? Tn : 0;
+        phase(p_next).push_back(q);
+      }
+      job0 += nj;
+      bins_off += (int64_t)nj * nb;
+    }
+  }
+  // merge the runs phase by phase
+  size_t n_phases = 0;
+  for (auto& ph : phases) n_phases = std::max(n_phases, ph.size());
+  out->ops.clear();
+  out->phase_op.assign(1, 0);
+  out->phase_tasks.clear();
+  for (size_t p = 0; p < n_phases; ++p) {
+    int64_t tasks = 0;
+    for (auto& ph : phases) {
+      if (p >= ph.size()) continue;
+      for (Op op : ph[p]) {
+        op.task0 = (int)tasks;
+        tasks += op.ntasks;
+        out->ops.push_back(op);
+      }
+    }
+    if (tasks > 0x7fffffff) return set_error(CUTQC_EUNSUPPORTED, "too many tasks in one phase");
+    out->phase_op.push_back((int)out->ops.size());
+    out->phase_tasks.push_back((int)tasks);
+  }
+  size_t o = align_up(data_end, 256);
+  out->ops_off = o;
+  o = align_up(o + out->ops.size() * sizeof(Op), 256);
+  out->phase_off = o;
+  o = align_up(o + out->phase_op.size() * sizeof(int), 256);
+  out->tasks_off = o;
+  o = align_up(o + out->phase_tasks.size() * sizeof(int), 256);
+  out->total = o;
+  return CUTQC_OK;
+}
+
+int max_resident_ctas(int* out) {
+  int per_sm = 0;
+  CUTQC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dd_persistent_kernel, kThreads, 0));
+  if (per_sm < 1) return set_error(CUTQC_EUNSUPPORTED, "the persistent DD kernel does not fit on an SM");
+  *out = per_sm * sm_count();
+  return CUTQC_OK;
+}
+
+}  // namespace
+}  // namespace cutqc
+
+struct cutqc_dd_batch {
+  cutqc::Program pg;
+  int grid;
+  int n_ops;
+  int device;
+};
+
+using namespace cutqc;
+
+extern "C" int cutqc_dd_batch_workspace_size(int n_runs, const cutqc_dd_run_desc* runs,
+                                             const cutqc_dd_batch_options* opt, size_t* bytes) {
+  if (!bytes) return set_error(CUTQC_EINVAL, "null bytes");
+  BatchOpts o;
+  int rc = read_opts(opt, &o);
+  if (rc) return rc;
+  Built b;
+  if ((rc = build_program(n_runs, runs, o, nullptr, &b))) return rc;
+  *bytes = b.total;
+  return CUTQC_OK;
+}
+
+extern "C" int cutqc_dd_batch_create(int n_runs, const cutqc_dd_run_desc* runs, const cutqc_dd_batch_options* opt,
+                                     void* ws_dev, size_t ws_bytes, cutqc_dd_batch** out) {
+  if (!out) return set_error(CUTQC_EINVAL, "null handle");
+  *out = nullptr;
+  if (!ws_dev) return set_error(CUTQC_EINVAL, "null workspace");
+  if (((uintptr_t)ws_dev & 255) != 0) return set_error(CUTQC_EINVAL, "workspace must be 256-byte aligned");
+  BatchOpts o;
+  int rc = read_opts(opt, &o);
+  if (rc) return rc;
+  Built b;
+  if ((rc = build_program(n_runs, runs, o, (uint8_t*)ws_dev, &b))) return rc;
+  if (ws_bytes < b.total) return set_error(CUTQC_ENOMEM, "DD batch workspace needs %zu bytes", b.total);
+  int grid = 0;
+  if ((rc = max_resident_ctas(&grid))) return rc;
+  if (o.ctas > 0) grid = std::min(grid, o.ctas);
+  uint8_t* ws = (uint8_t*)ws_dev;
+  CUTQC_CUDA_TRY(cudaMemcpy(ws + b.ops_off, b.ops.data(), b.ops.size() * sizeof(Op), cudaMemcpyHostToDevice));
+  CUTQC_CUDA_TRY(cudaMemcpy(ws + b.phase_off, b.phase_op.data(), b.phase_op.size() * sizeof(int),
+                            cudaMemcpyHostToDevice));
+  CUTQC_CUDA_TRY(cudaMemcpy(ws + b.tasks_off, b.phase_tasks.data(), b.phase_tasks.size() * sizeof(int),
+                            cudaMemcpyHostToDevice));
+  int* status = device_status_ptr();
+  if (!status) return set_error(CUTQC_ECUDA, "no device status word");
+  cutqc_dd_batch* h = new (std::nothrow) cutqc_dd_batch;
+  if (!h) return set_error(CUTQC_ENOMEM, "host allocation");
+  h->pg.ops = (const Op*)(ws + b.ops_off);
+  h->pg.phase_op = (const int*)(ws + b.phase_off);
+  h->pg.phase_tasks = (const int*)(ws + b.tasks_off);
+  h->pg.n_phases = (int)b.phase_tasks.size();
+  h->pg.bar = (GridBar*)ws;
+  h->pg.status = status;
+  h->grid = grid;
+  h->n_ops = (int)b.ops.size();
+  cudaGetDevice(&h->device);
+  *out = h;
+  return CUTQC_OK;
+}
+
+extern "C" int cutqc_dd_batch_launch(const cutqc_dd_batch* b, void* stream) {
+  if (!b) return set_error(CUTQC_EINVAL, "null handle");
+  cudaStream_t st = (cudaStream_t)stream;
+  CUTQC_CUDA_TRY(cudaMemsetAsync(b->pg.bar, 0, sizeof(GridBar), st));
+  if (b->pg.n_phases == 0) return CUTQC_OK;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)b->grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CUTQC_CUDA_TRY(cudaLaunchKernelEx(&cfg, dd_persistent_kernel, b->pg));
+  return CUTQC_OK;
+}
+
+extern "C" int cutqc_dd_batch_info(const cutqc_dd_batch* b, int32_t* n_phases, int32_t* n_ops, int32_t* grid_ctas) {
+  if (!b) return set_error(CUTQC_EINVAL, "null handle");
+  if (n_phases) *n_phases = b->pg.n_phases;
+  if (n_ops) *n_ops = b->n_ops;
+  if (grid_ctas) *grid_ctas = b->grid;
+  return CUTQC_OK;
+}
+
+extern "C" int cutqc_dd_batch_destroy(cutqc_dd_batch* b) {
+  delete b;
+  return CUTQC_OK;
+}

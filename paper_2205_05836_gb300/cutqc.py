@@ -345,6 +345,114 @@ def dd_jobs_from_device(jobs, n_jobs):
     return out
 
 
+class _DDRunDesc(ctypes.Structure):
+    _fields_ = [("n_sub", c_int32), ("subcircuits", POINTER(_Sub)), ("attributed_dev", POINTER(c_void_p)),
+                ("n_qubits", c_int32), ("M", c_int32), ("R", c_int32), ("T", c_int32), ("max_jobs", c_int32),
+                ("jobs_dev", c_void_p), ("n_jobs_dev", c_void_p), ("bins_dev", c_void_p),
+                ("bins_capacity", c_int64)]
+
+
+class DDBatchOptions(ctypes.Structure):
+    _fields_ = [("merge_ctas", c_int32), ("topk_chunk", c_int32), ("ctas", c_int32)]
+
+
+def _batch_descs(runs):
+    """runs: dicts with subs, attributed, n_qubits, M, R, T, jobs, n_jobs,
+    bins (device tensors as cutqc_dd_run_async takes them)."""
+    keep, descs = [], (_DDRunDesc * len(runs))()
+    rec = ctypes.sizeof(DDJob)
+    for i, r in enumerate(runs):
+        arr, k = _subs(r["subs"])
+        ptrs = (c_void_p * len(r["attributed"]))(*[t.data_ptr() for t in r["attributed"]])
+        keep += [arr, k, ptrs]
+        descs[i] = _DDRunDesc(len(r["subs"]), ctypes.cast(arr, POINTER(_Sub)), ctypes.cast(ptrs, POINTER(c_void_p)),
+                              int(r["n_qubits"]), int(r["M"]), int(r["R"]), int(r["T"]), r["jobs"].numel() // rec,
+                              r["jobs"].data_ptr(), r["n_jobs"].data_ptr(), r["bins"].data_ptr(), r["bins"].numel())
+    return descs, keep
+
+
+def _batch_opts(options):
+    if options is None:
+        return None
+    return ctypes.byref(DDBatchOptions(int(options.get("merge_ctas", 0)), int(options.get("topk_chunk", 0)),
+                                       int(options.get("ctas", 0))))
+
+
+def cutqc_dd_batch_workspace_size(runs, options=None):
+    descs, keep = _batch_descs(runs)
+    n = c_size_t(0)
+    _check(lib().cutqc_dd_batch_workspace_size(c_int(len(runs)), descs, _batch_opts(options), ctypes.byref(n)))
+    return n.value
+
+
+class DDBatch:
+    """Handle of cutqc_dd_batch_create: the runs' program, written into `ws`
+    (a device uint8 tensor this object keeps alive).  launch() enqueues the
+    persistent launch; the records land in each run's jobs / n_jobs / bins."""
+
+    def __init__(self, runs, options=None, ws=None):
+        import torch
+        descs, keep = _batch_descs(runs)
+        need = cutqc_dd_batch_workspace_size(runs, options)
+        dev = runs[0]["bins"].device
+        if ws is None:
+            ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+            off = (-ws.data_ptr()) % 256
+            ws = ws[off:off + need]
+        self.ws = ws
+        self.runs = runs
+        self._h = c_void_p(0)
+        _check(lib().cutqc_dd_batch_create(c_int(len(runs)), descs, _batch_opts(options), _ptr(ws),
+                                           c_size_t(ws.numel()), ctypes.byref(self._h)))
+
+    def launch(self, stream=None):
+        _check(lib().cutqc_dd_batch_launch(self._h, _stream(stream)))
+
+    def info(self):
+        p, o, g = c_int32(0), c_int32(0), c_int32(0)
+        _check(lib().cutqc_dd_batch_info(self._h, ctypes.byref(p), ctypes.byref(o), ctypes.byref(g)))
+        return {"phases": p.value, "ops": o.value, "ctas": g.value}
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().cutqc_dd_batch_destroy(self._h)
+            self._h = c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cutqc_dd_batch_create(runs, options=None, ws=None):
+    """Several circuits' Algorithm 1 (BFS) as one persistent launch; returns a
+    DDBatch (call .launch(stream))."""
+    return DDBatch(runs, options, ws)
+
+
+def cutqc_dd_batch_launch(batch, stream=None):
+    batch.launch(stream)
+
+
+def cutqc_dd_batch_info(batch):
+    return batch.info()
+
+
+def cutqc_dd_batch_destroy(batch):
+    batch.close()
+
+
+def dd_batch_run(subs, attributed, n_qubits, M, R, T, max_jobs=256):
+    """Device buffers of one run of a batch (dict for cutqc_dd_batch_create)."""
+    import torch
+    dev = attributed[0].device
+    return dict(subs=subs, attributed=attributed, n_qubits=n_qubits, M=M, R=R, T=T,
+                jobs=torch.empty(max_jobs * ctypes.sizeof(DDJob), dtype=torch.uint8, device=dev),
+                n_jobs=torch.zeros(1, dtype=torch.int32, device=dev),
+                bins=torch.empty(max_jobs << min(M, n_qubits), dtype=torch.float32, device=dev))
+
+
 def declared_symbols(headers=None):
     """Function names declared in include/*.h."""
     import re

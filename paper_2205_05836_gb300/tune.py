@@ -75,3 +75,52 @@ def tune_dd(subs, attributed, n, M, R, T, max_jobs=64, reps=5, candidates=None, 
     best = min((r for r in results if r[2]), key=lambda r: r[0])[1]
     _CACHE[key] = (best, results)
     return best, results
+
+
+# ------------------------------------------------- the persistent DD batch
+# One launch for several circuits (cutqc_dd_batch_*): the shape options are
+# the merge slicing (merge_ctas), the bins per top-T task (topk_chunk) and the
+# grid (ctas, 0 = every CTA that fits at once).  Each candidate builds the
+# batch over the caller's runs (fresh output buffers), replays it as a
+# captured graph, and is kept only if its records and bins match the first
+# candidate's.
+
+BATCH_CANDIDATES = [dict(merge_ctas=m, topk_chunk=c, ctas=0) for m in (1024, 256) for c in (2048, 1024, 4096)]
+
+
+def batch_shape_key(runs):
+    return tuple(shape_key(r["subs"], r["n_qubits"], r["M"], r["R"], r["T"]) for r in runs)
+
+
+def tune_dd_batch(runs, reps=5, candidates=None, atol=1e-6):
+    """runs: dicts for cq.cutqc_dd_batch_create (their buffers are not
+    touched: each candidate gets its own).  Returns (best options dict,
+    [(ms, options, matches_first), ...])."""
+    import torch
+    key = batch_shape_key(runs)
+    if key in _CACHE:
+        return _CACHE[key]
+    ref = None
+    results = []
+    for opt in candidates or BATCH_CANDIDATES:
+        mine = [cq.dd_batch_run(r["subs"], r["attributed"], r["n_qubits"], r["M"], r["R"], r["T"],
+                                max_jobs=r["jobs"].numel() // cq.ctypes.sizeof(cq.DDJob)) for r in runs]
+        batch = cq.cutqc_dd_batch_create(mine, opt)
+        ms = _time_graph(lambda b=batch: b.launch(torch.cuda.current_stream()), reps)
+        recs = [cq.dd_jobs_from_device(m["jobs"], m["n_jobs"]) for m in mine]
+        if ref is None:
+            ref = (recs, [m["bins"].clone() for m in mine])
+            ok = True
+        else:
+            ok = all(
+                len(rs) == len(rr) and all(
+                    (a.parent, a.parent_bin, a.n_active) == (b.parent, b.parent_bin, b.n_active) and
+                    bool(torch.allclose(mb[a.bins_offset:a.bins_offset + (1 << a.n_active)],
+                                        rb[b.bins_offset:b.bins_offset + (1 << b.n_active)], atol=atol, rtol=0))
+                    for a, b in zip(rs, rr))
+                for rs, rr, mb, rb in zip(recs, ref[0], [m["bins"] for m in mine], ref[1]))
+        results.append((ms, dict(opt), ok))
+        batch.close()
+    best = min((r for r in results if r[2]), key=lambda r: r[0])[1]
+    _CACHE[key] = (best, results)
+    return best, results

@@ -125,3 +125,42 @@ def test_mlp_queries(built):
     b = ctypes.c_size_t(0)
     assert cq.lib().cutqc_mlp_workspace_size(0, ctypes.byref(b)) == cq.EINVAL
     assert cq.lib().cutqc_mlp_workspace_size(100, ctypes.byref(b)) == 0 and b.value > 0
+
+
+def test_dd_batch_validation_without_gpu(built):
+    """The persistent DD batch sizes its workspace and rejects bad runs and
+    options on the host (the device pointers are only recorded, never read)."""
+    import torch
+    cq = built
+    a = _sub(3, out_local=[2], out_edge=[0], out_qubit=[0, 1])
+    b = _sub(3, in_local=[0], in_edge=[0], out_qubit=[2, 3, 4])
+    att = [torch.zeros(4, 4), torch.zeros(8, 4)]       # host stand-ins: not dereferenced here
+
+    def run(subs=(a, b), n=5, M=2, R=3, T=2, max_jobs=8, bins=64):
+        return dict(subs=list(subs), attributed=att, n_qubits=n, M=M, R=R, T=T,
+                    jobs=torch.zeros(max_jobs * ctypes.sizeof(cq.DDJob), dtype=torch.uint8),
+                    n_jobs=torch.zeros(1, dtype=torch.int32), bins=torch.zeros(bins))
+    one = cq.cutqc_dd_batch_workspace_size([run()])
+    two = cq.cutqc_dd_batch_workspace_size([run(), run(T=1)])
+    assert one > 0 and two > one
+    cases = [
+        ([run(subs=(_sub(3, out_qubit=[0, 1, 2]),), n=3)], None, cq.EUNSUPPORTED),   # nothing to contract
+        ([run(max_jobs=2)], None, cq.ENOMEM),          # 1 + 2 + 1 records needed
+        ([run(bins=8)], None, cq.ENOMEM),
+        ([run(n=6)], None, cq.EINVAL),                 # outputs do not cover n
+        ([run(T=33)], None, cq.EUNSUPPORTED),
+        ([run()], {"topk_chunk": 300}, cq.EINVAL),     # not a power of two
+        ([run()], {"topk_chunk": 128}, cq.EINVAL),
+        ([run()], {"merge_ctas": 5000}, cq.EINVAL),
+        ([run()], {"ctas": -1}, cq.EINVAL),
+        ([], None, cq.EINVAL),
+    ]
+    for runs, opt, code in cases:
+        if not runs:
+            n = ctypes.c_size_t(0)
+            rc = cq.lib().cutqc_dd_batch_workspace_size(0, None, None, ctypes.byref(n))
+            assert rc == code
+            continue
+        with pytest.raises(cq.CutqcError) as e:
+            cq.cutqc_dd_batch_workspace_size(runs, opt)
+        assert e.value.code == code, (opt, cq.cutqc_last_error())
