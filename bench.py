@@ -764,7 +764,7 @@ def dd_batch_extras(dev, cq, runs, M, R, T, tot_bins, reps):
     return {"ms": ms, "bins_per_s": tot_bins / (ms * 1e-3), "options": opt, "phases": info["phases"],
             "ops": info["ops"], "ctas": info["ctas"], "matches_level_by_level": bool(same),
             "device_status": cq.cutqc_device_status(), "clocks": clk.summary(),
-            "tuning_ms": {f"{o['merge_ctas']}/{o['topk_chunk']}": round(t, 4) for t, o, ok in trials if ok},
+            "tuning_ms": {f"{o['ctas_per_sm']}/{o['topk_chunk']}": round(t, 4) for t, o, ok in trials if ok},
             "gpu_launches_per_replay": 1,
             "note": "one cooperative launch (and one memset) for all levels of the three circuits; "
                     "grid barriers between phases"}

@@ -316,7 +316,9 @@ int cutqc_dd_run_async(int n_sub, const cutqc_subcircuit* s, const float* const*
  *   outputs, as cutqc_dd_run_async.
  * Options (zero fields take defaults): merge_ctas as cutqc_dd_options;
  * topk_chunk bins per task of the chunked top-T pass (a power of two >= 256,
- * default 2048); ctas caps the grid (default: every CTA that fits at once).
+ * default 2048); ctas caps the grid (default: every CTA that fits at once);
+ * ctas_per_sm (2..4, default 3) the CTAs per SM that the kernel's registers
+ * are budgeted for (more resident warps, fewer registers each).
  * cutqc_dd_batch_create validates the runs, lays out `ws_dev` (at least
  * cutqc_dd_batch_workspace_size bytes, 256-byte aligned, owned by the caller
  * and kept alive and untouched while the handle is used) and writes the
@@ -346,6 +348,7 @@ typedef struct cutqc_dd_batch_options {
   int32_t merge_ctas;
   int32_t topk_chunk;
   int32_t ctas;
+  int32_t ctas_per_sm;
 } cutqc_dd_batch_options;
 
 typedef struct cutqc_dd_batch cutqc_dd_batch;
@@ -357,6 +360,12 @@ int cutqc_dd_batch_create(int n_runs, const cutqc_dd_run_desc* runs, const cutqc
 int cutqc_dd_batch_launch(const cutqc_dd_batch* batch, void* stream);
 /* Shape of the program: phases (grid barriers + 1), ops, CTAs launched.     */
 int cutqc_dd_batch_info(const cutqc_dd_batch* batch, int32_t* n_phases, int32_t* n_ops, int32_t* grid_ctas);
+/* Per phase p < n (n = the number of phases): kinds[p] has bit t set when an
+ * op of kind t runs in it (0 zero bin totals, 1 merge, 2 slice reduction,
+ * 3 contraction step, 4 chunked top-T, 5 level selection), tasks[p] its
+ * tasks, cycles[p] the SM clock cycles CTA 0 saw it take in the last
+ * completed launch (a synchronous copy).  Any output may be null.           */
+int cutqc_dd_batch_phases(const cutqc_dd_batch* batch, int32_t* kinds, int32_t* tasks, int64_t* cycles, int n);
 int cutqc_dd_batch_destroy(cutqc_dd_batch* batch);
 
 /* ------------------------------------------------------------- reductions

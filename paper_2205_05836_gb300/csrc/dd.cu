@@ -105,7 +105,8 @@ int launch_merge(const cutqc_subcircuit* s, const float* att, uint64_t act, uint
   if ((int64_t)1 << a > 0x7fffffffLL) return set_error(CUTQC_EUNSUPPORTED, "too many rows");
   if (n_jobs < 1 || n_jobs > 65535) return set_error(CUTQC_EINVAL, "n_jobs out of range");
   const int64_t rows_a = (int64_t)1 << a;
-  dd_merge_kernel<<<dim3(merge_grid(rows_a * n_jobs, 1), 1, 1), 256, 0, st>>>(
+  const int groups = merge_groups(k, __builtin_popcountll(mrg), 0);
+  dd_merge_kernel<<<dim3(merge_grid(rows_a * n_jobs, 1, groups), 1, 1), 256, 0, st>>>(
       att, k, act, mrg, zm, zv, zoom_dev, ZoomFromJobs{}, n_jobs, rows_a, __builtin_popcountll(mrg), 0, out);
   CUTQC_LAUNCH_CHECK("dd_merge_kernel");
   return CUTQC_OK;
@@ -481,7 +482,8 @@ int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att
         zj.lo = level * M;
         for (int t = 0; t < o; ++t) zj.outq[t] = (int8_t)s[i].out_qubit[t];
         const int64_t rows_a = (int64_t)1 << a;
-        dd_merge_kernel<<<dim3(merge_grid(rows_a * nj, 1 << ls), 1, 1u << ls), 256, 0, ms>>>(
+        const int groups = merge_groups(k, __builtin_popcountll(mrg), ls);
+        dd_merge_kernel<<<dim3(merge_grid(rows_a * nj, 1 << ls, groups), 1, 1u << ls), 256, 0, ms>>>(
             att[i], k, L.act_mask[i], mrg, L.zoom_mask[i], 0, nullptr, zj, nj, rows_a, __builtin_popcountll(mrg), ls,
             part);
         CUTQC_LAUNCH_CHECK("dd_merge_kernel");

@@ -57,10 +57,51 @@ __device__ __forceinline__ uint64_t job_zoom(const ZoomFromJobs& zj, int job) {
 
 // Merge: merged[job][a][c] = sum_m attributed[x(a, z_job, m)][c] over the
 // merged index range of slice bz (2^log_slices slices; slice bz writes its
-// partial sums to out + bz * n_jobs * rows_a * C).  Block bx of nbx walks
-// the (merged row a, job) pairs.  Threads split columns and, when there are
-// few columns, the slice's merged indices; sub-slices are combined through
-// shared memory.  The attributed tensor is read-only for the launch.
+// partial sums to out + bz * n_jobs * rows_a * C).  The CTA's threads form
+// G = 256 / cw groups of cw = min(C, 256) column threads.  When the slice
+// holds at least G merged indices, block bx of nbx walks the (merged row a,
+// job) pairs one at a time, group g sums the indices m0 + g, m0 + g + G, ...
+// (compensated), and the groups' sums are added in group order; otherwise
+// (merge_groups() > 1) each group takes its own row, rows bx * G + g, then
+// nbx * G further, and sums the slice's indices in order.  The attributed
+// tensor is read-only for the launch.  Loads of consecutive merged indices
+// are issued four at a time; the source row of index m + d is the bit
+// deposit of m + d, carried in the deposited domain.
+__host__ __device__ __forceinline__ int merge_groups(int k, int n_merged, int log_slices) {
+  const int cw = 2 * k >= 8 ? 256 : (1 << (2 * k));
+  const int G = 256 / cw;
+  return ((int64_t)1 << (n_merged - log_slices)) < G ? G : 1;
+}
+
+// sum over count indices first, first + step, ... of att[(base | pdep(m)) * C + col]
+__device__ __forceinline__ float merge_run(const float* __restrict__ att, int64_t C, uint64_t base,
+                                           uint64_t merged_mask, int64_t first, int64_t step, int64_t count,
+                                           int64_t col) {
+  Kahan acc;
+  const uint64_t keep = ~merged_mask;
+  const uint64_t dx = pdep64((uint64_t)step, merged_mask);
+  uint64_t x = pdep64((uint64_t)first, merged_mask);
+  auto next = [&](uint64_t v) { return ((v | keep) + dx) & merged_mask; };
+  int64_t i = 0;
+  for (; i + 4 <= count; i += 4) {
+    const uint64_t x1 = next(x), x2 = next(x1), x3 = next(x2);
+    const float v0 = __ldg(att + (int64_t)(base | x) * C + col);
+    const float v1 = __ldg(att + (int64_t)(base | x1) * C + col);
+    const float v2 = __ldg(att + (int64_t)(base | x2) * C + col);
+    const float v3 = __ldg(att + (int64_t)(base | x3) * C + col);
+    acc.add(v0);
+    acc.add(v1);
+    acc.add(v2);
+    acc.add(v3);
+    x = next(x3);
+  }
+  for (; i < count; ++i) {
+    acc.add(__ldg(att + (int64_t)(base | x) * C + col));
+    x = next(x);
+  }
+  return acc.s;
+}
+
 template <bool kCoherent>
 __device__ __forceinline__ void dd_merge_body(const float* __restrict__ att, int k, uint64_t act_mask,
                                               uint64_t merged_mask, uint64_t zoom_mask, uint64_t zoom_val,
@@ -68,32 +109,48 @@ __device__ __forceinline__ void dd_merge_body(const float* __restrict__ att, int
                                               int n_jobs, int64_t rows_a, int n_merged, int log_slices,
                                               float* __restrict__ out, int64_t bx, int64_t nbx, int bz) {
   __shared__ float red[256];
+  __shared__ uint64_t zs[32];
   const int64_t C = (int64_t)1 << (2 * k);
   const int64_t Mper = (int64_t)1 << (n_merged - log_slices);
   const int64_t m0 = (int64_t)bz * Mper;
   const int cw = (int)(C < 256 ? C : 256);
-  const int slices = 256 / cw;
+  const int G = 256 / cw;
   const int c_local = threadIdx.x % cw;
-  const int slice = threadIdx.x / cw;
-  for (int64_t ra = bx; ra < rows_a * n_jobs; ra += nbx) {
+  const int grp = threadIdx.x / cw;
+  // the jobs' zoom values, once per block when they come from the records
+  const bool zsm = zj.jobs && n_jobs <= 32;
+  if (zsm) {
+    if (threadIdx.x < n_jobs) zs[threadIdx.x] = job_zoom<kCoherent>(zj, threadIdx.x);
+    __syncthreads();
+  }
+  auto zoom_of = [&](int job) -> uint64_t {
+    return (zsm ? zs[job] : zj.jobs ? job_zoom<kCoherent>(zj, job) : zoom_dev ? __ldg(zoom_dev + job) : zoom_val) &
+           zoom_mask;
+  };
+  const int64_t total = rows_a * n_jobs;
+  if (merge_groups(k, n_merged, log_slices) > 1) {
+    for (int64_t ra = bx * G + grp; ra < total; ra += nbx * G) {
+      const int job = (int)(ra / rows_a);
+      const int64_t a = ra - (int64_t)job * rows_a;
+      const uint64_t base = pdep64((uint64_t)a, act_mask) | zoom_of(job);
+      float* dst = out + (((int64_t)bz * n_jobs + job) * rows_a + a) * C;
+      for (int64_t c0 = 0; c0 < C; c0 += cw)
+        dst[c0 + c_local] = merge_run(att, C, base, merged_mask, m0, 1, Mper, c0 + c_local);
+    }
+    return;
+  }
+  for (int64_t ra = bx; ra < total; ra += nbx) {
     const int job = (int)(ra / rows_a);
     const int64_t a = ra - (int64_t)job * rows_a;
-    const uint64_t z = (zj.jobs ? job_zoom<kCoherent>(zj, job) : zoom_dev ? __ldg(zoom_dev + job) : zoom_val) &
-                       zoom_mask;
-    const uint64_t base = pdep64((uint64_t)a, act_mask) | z;
+    const uint64_t base = pdep64((uint64_t)a, act_mask) | zoom_of(job);
     float* dst = out + (((int64_t)bz * n_jobs + job) * rows_a + a) * C;
+    const int64_t cnt = (Mper - grp + G - 1) / G;
     for (int64_t c0 = 0; c0 < C; c0 += cw) {
-      Kahan acc;
-      if (slice < slices)
-        for (int64_t m = m0 + slice; m < m0 + Mper; m += slices) {
-          const uint64_t x = base | pdep64((uint64_t)m, merged_mask);
-          acc.add(__ldg(att + (int64_t)x * C + c0 + c_local));
-        }
-      red[threadIdx.x] = acc.s;
+      red[threadIdx.x] = merge_run(att, C, base, merged_mask, m0 + grp, G, cnt, c0 + c_local);
       __syncthreads();
-      if (slice == 0) {
+      if (grp == 0) {
         float s = red[c_local];
-        for (int q = 1; q < slices; ++q) s += red[q * cw + c_local];
+        for (int q = 1; q < G; ++q) s += red[q * cw + c_local];
         dst[c0 + c_local] = s;
       }
       __syncthreads();
@@ -234,13 +291,15 @@ struct LevelInfo {
 };
 
 // Run by the first warp of a block (the other threads return at once; no
-// block-wide barrier inside).  Completes the records of this level's jobs
-// (bin totals, the T largest bins, bin offsets) and, when merged qubits
+// block-wide barrier inside).  Completes the records of this level's nj <= 32
+// jobs (bin totals, the T largest bins, bin offsets) and, when merged qubits
 // remain, writes the records of the next level: the T largest bins over all
 // valid jobs of this level, ordered by value (stable: job order, then each
 // job's own order, for equal values) -- Algorithm 1's list L truncated to T.
-// Records past the candidates are placeholders (level -1).  Lane 0 ranks the
-// candidates; the 32-entry arrays of a record are written one entry per lane.
+// Records past the candidates are placeholders (level -1).  The loads are
+// issued across lanes (lane j: job j; the nj * T candidates by all lanes),
+// lane 0 ranks the candidates, lane c writes next-level record c, and the
+// 32-entry arrays of a record are written one entry per lane.
 template <bool kCoherent>
 __device__ __forceinline__ void dd_select_body(cutqc_dd_job_result* __restrict__ jobs, int job0, int nj,
                                                const LevelInfo& L, int64_t bins_off0, int64_t nb,
@@ -248,56 +307,58 @@ __device__ __forceinline__ void dd_select_body(cutqc_dd_job_result* __restrict__
                                                const float* __restrict__ tval, int T, int has_children, int n_next,
                                                int32_t* __restrict__ n_jobs_dev) {
   __shared__ int cj[32], cb[32], cnt_s;
-  // the level's candidates (nj * T of them, job order) loaded in parallel
+  // the level's candidates (nj * T <= 1024 of them, job order)
   __shared__ int kb[1024];
   __shared__ float kv[1024];
   if (threadIdx.x >= 32) return;
   const int lane = threadIdx.x;
+  int lvl = -1;
+  double bs = 0.0;
+  if (lane < nj) {
+    lvl = ldx<kCoherent>(&jobs[job0 + lane].level);
+    if (lvl >= 0) bs = ldx<kCoherent>(bsum + lane);
+  }
+  const unsigned valid = __ballot_sync(0xffffffffu, lane < nj && lvl >= 0);
+  const int ncand = nj * T;
+  for (int q = lane; q < ncand; q += 32) {
+    const int b = ((valid >> (q / T)) & 1) ? ldx<kCoherent>(tidx + q) : -1;
+    kb[q] = b;
+    kv[q] = b >= 0 ? ldx<kCoherent>(tval + q) : 0.f;
+  }
+  __syncwarp();
   for (int j = 0; j < nj; ++j) {
     cutqc_dd_job_result& J = jobs[job0 + j];
-    const bool valid = ldx<kCoherent>(&J.level) >= 0;
-    const int32_t ti = (valid && lane < T) ? ldx<kCoherent>(tidx + (int64_t)j * T + lane) : -1;
+    const int32_t ti = lane < T ? kb[j * T + lane] : -1;
     J.top_idx[lane] = ti;
-    J.top_val[lane] = ti >= 0 ? ldx<kCoherent>(tval + (int64_t)j * T + lane) : 0.f;
+    J.top_val[lane] = ti >= 0 ? kv[j * T + lane] : 0.f;
     J.active[lane] = lane < L.n_active ? L.active[lane] : 0;
-    if (lane == 0) {
-      J.n_active = L.n_active;
-      J.bin_sum = valid ? ldx<kCoherent>(bsum + j) : 0.0;
-      J.bins_offset = bins_off0 + (int64_t)j * nb;
-    }
+  }
+  if (lane < nj) {
+    cutqc_dd_job_result& J = jobs[job0 + lane];
+    J.n_active = L.n_active;
+    J.bin_sum = lvl >= 0 ? bs : 0.0;
+    J.bins_offset = bins_off0 + (int64_t)lane * nb;
   }
   if (!has_children) {
     if (lane == 0) *n_jobs_dev = job0 + nj;
     return;
   }
-  const int ncand = nj * T <= 1024 ? nj * T : 1024;
-  for (int q = lane; q < ncand; q += 32) {
-    const int j = q / T;
-    const int b = ldx<kCoherent>(&jobs[job0 + j].level) >= 0 ? ldx<kCoherent>(tidx + q) : -1;
-    kb[q] = b;
-    kv[q] = b >= 0 ? ldx<kCoherent>(tval + q) : 0.f;
-  }
-  __syncwarp();
   if (lane == 0) {
     float cv[32];
     int cnt = 0;
-    for (int j = 0; j < nj; ++j) {
-      for (int t = 0; t < T; ++t) {
-        const int q = j * T + t;
-        if (q >= ncand) break;
-        const int b = kb[q];
-        if (b < 0) continue;
-        const float v = kv[q];
-        int pos = cnt;
-        while (pos > 0 && cv[pos - 1] < v) --pos;     // after every entry of equal value
-        if (pos >= T) continue;
-        const int last = cnt < T ? cnt : T - 1;
-        for (int u = last; u > pos; --u) { cv[u] = cv[u - 1]; cj[u] = cj[u - 1]; cb[u] = cb[u - 1]; }
-        cv[pos] = v;
-        cj[pos] = j;
-        cb[pos] = b;
-        if (cnt < T) ++cnt;
-      }
+    for (int q = 0; q < ncand; ++q) {
+      const int b = kb[q];
+      if (b < 0) continue;
+      const float v = kv[q];
+      int pos = cnt;
+      while (pos > 0 && cv[pos - 1] < v) --pos;     // after every entry of equal value
+      if (pos >= T) continue;
+      const int last = cnt < T ? cnt : T - 1;
+      for (int u = last; u > pos; --u) { cv[u] = cv[u - 1]; cj[u] = cj[u - 1]; cb[u] = cb[u - 1]; }
+      cv[pos] = v;
+      cj[pos] = q / T;
+      cb[pos] = b;
+      if (cnt < T) ++cnt;
     }
     cnt_s = cnt;
   }
@@ -309,31 +370,43 @@ __device__ __forceinline__ void dd_select_body(cutqc_dd_job_result* __restrict__
     R.top_idx[lane] = -1;
     R.top_val[lane] = 0.f;
     R.active[lane] = 0;
-    if (lane == 0) {
-      R.n_active = 0;
-      R.bin_sum = 0.0;
-      R.bins_offset = 0;
-      R.depth = L.depth + 1;
-      if (c < cnt) {
-        const cutqc_dd_job_result& P = jobs[job0 + cj[c]];
-        R.level = L.level + 1;
-        R.parent = job0 + cj[c];
-        R.parent_bin = cb[c];
-        for (int w = 0; w < 2; ++w) {
-          R.zoom_mask[w] = ldx<kCoherent>((const unsigned long long*)&P.zoom_mask[w]);
-          R.zoom_val[w] = ldx<kCoherent>((const unsigned long long*)&P.zoom_val[w]);
-        }
-        for (int a = 0; a < L.n_active; ++a) {
-          const int q = L.active[a];
-          R.zoom_mask[q >> 6] |= (uint64_t)1 << (q & 63);
-          if ((cb[c] >> a) & 1) R.zoom_val[q >> 6] |= (uint64_t)1 << (q & 63);
-        }
-      } else {
-        R.level = -1;
-        R.parent = -1;
-        R.parent_bin = -1;
-        for (int w = 0; w < 2; ++w) { R.zoom_mask[w] = 0; R.zoom_val[w] = 0; }
+  }
+  if (lane < n_next) {
+    cutqc_dd_job_result& R = jobs[next0 + lane];
+    R.n_active = 0;
+    R.bin_sum = 0.0;
+    R.bins_offset = 0;
+    R.depth = L.depth + 1;
+    if (lane < cnt) {
+      const cutqc_dd_job_result& P = jobs[job0 + cj[lane]];
+      unsigned long long zm[2], zv[2];
+      for (int w = 0; w < 2; ++w) {
+        zm[w] = ldx<kCoherent>((const unsigned long long*)&P.zoom_mask[w]);
+        zv[w] = ldx<kCoherent>((const unsigned long long*)&P.zoom_val[w]);
       }
+      for (int a = 0; a < L.n_active; ++a) {
+        const int q = L.active[a];
+        const unsigned long long bit = 1ull << (q & 63);
+        if (q >> 6) {
+          zm[1] |= bit;
+          if ((cb[lane] >> a) & 1) zv[1] |= bit;
+        } else {
+          zm[0] |= bit;
+          if ((cb[lane] >> a) & 1) zv[0] |= bit;
+        }
+      }
+      R.level = L.level + 1;
+      R.parent = job0 + cj[lane];
+      R.parent_bin = cb[lane];
+      R.zoom_mask[0] = zm[0];
+      R.zoom_mask[1] = zm[1];
+      R.zoom_val[0] = zv[0];
+      R.zoom_val[1] = zv[1];
+    } else {
+      R.level = -1;
+      R.parent = -1;
+      R.parent_bin = -1;
+      for (int w = 0; w < 2; ++w) { R.zoom_mask[w] = 0; R.zoom_val[w] = 0; }
     }
   }
   if (lane == 0) *n_jobs_dev = next0 + n_next;

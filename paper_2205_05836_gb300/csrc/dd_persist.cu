@@ -10,14 +10,14 @@
 // circuit, so the circuits fill the GPU together:
 //   merge (+ zero the bin totals)  ->  slice reduction (when sliced)  ->
 //   one phase per depth of the contraction plan (independent steps share a
-//   phase; the operands are gathered on the fly by the GEMM tile, no staging
-//   copy)  ->  chunked top-T of each job's bins  ->  the level selection
+//   phase; 64 x 64 GEMM tiles whose operands are gathered on the fly, no
+//   staging copy)  ->  chunked top-T of each job's bins  ->  the level selection
 //   (each job's top T from its chunks' candidates, then Algorithm 1's list L
 //   truncated to T, written as the next level's job records).
 // Within a phase a CTA takes tasks (merge walkers, GEMM tiles, top-T chunks)
 // in a fixed stride; the results are those of the level-by-level path: the
-// same merge slicing and partial-sum order, the same GEMM tile and k order,
-// the same selection order (bin totals are float64 atomics in both).
+// same merge slicing and partial-sum order, the same fmaf chain over k per
+// bin, the same selection order (bin totals are float64 atomics in both).
 //
 // Memory ordering: data written in one phase is read in a later one by other
 // CTAs, after a barrier whose arrival is preceded and whose exit is followed
@@ -139,7 +139,7 @@ struct SelectOp {
   int32_t* n_jobs_dev;
   int job0, nj, ncand, T, has_children, n_next;
 };
-struct Op {
+struct alignas(16) Op {
   int type, task0, ntasks;
   union {
     ZeroOp zero;
@@ -151,10 +151,14 @@ struct Op {
   } u;
 };
 
-struct GridBar {
+// The arrival counter and the release word on separate 128-byte lines: the
+// waiters' polls do not contend with the arrivals.
+struct alignas(128) GridBar {
   unsigned int arrived;
+  unsigned int pad0[31];
   unsigned int gen;
   int abort;
+  unsigned int pad1[30];
 };
 
 struct Program {
@@ -164,6 +168,7 @@ struct Program {
   int n_phases;
   GridBar* bar;
   int* status;
+  long long* trace;          // [n_phases + 1]: CTA 0's clock at the start and after each phase
 };
 
 // Grid-wide barrier of a cooperative launch (every CTA resident).  Returns
@@ -201,12 +206,63 @@ __device__ bool grid_barrier(GridBar* g, int* status) {
   return ok != 0;
 }
 
+// The T best of n (value, index) candidates by (value desc, index asc), one
+// warp: each lane keeps its best TCAP, then T rounds of a warp arg-max.
+template <int TCAP>
+__device__ __forceinline__ void warp_topk_candidates(const float* __restrict__ cval, const int32_t* __restrict__ cidx,
+                                                     int n, int T, int32_t* __restrict__ out_idx,
+                                                     float* __restrict__ out_val) {
+  const int lane = threadIdx.x & 31;
+  float lv[TCAP];
+  int li[TCAP];
+#pragma unroll
+  for (int u = 0; u < TCAP; ++u) { lv[u] = -INFINITY; li[u] = -1; }
+  int cnt = 0;
+  for (int q = lane; q < n; q += 32) {
+    const int idx = ldx<true>(cidx + q);
+    if (idx < 0) continue;
+    const float v = ldx<true>(cval + q);
+    if (cnt == T && !dd_better(v, idx, lv[T - 1], li[T - 1])) continue;
+    int pos = cnt < T ? cnt : T - 1;
+#pragma unroll
+    for (int u = TCAP - 1; u > 0; --u)
+      if (u <= pos && dd_better(v, idx, lv[u - 1], li[u - 1])) { lv[u] = lv[u - 1]; li[u] = li[u - 1]; pos = u - 1; }
+    lv[pos] = v;
+    li[pos] = idx;
+    if (cnt < T) ++cnt;
+  }
+  int head = 0;
+  for (int t = 0; t < T; ++t) {
+    float bv = -INFINITY;
+    int bi = -1;
+#pragma unroll
+    for (int u = 0; u < TCAP; ++u)
+      if (u == head && head < cnt) { bv = lv[u]; bi = li[u]; }
+    const int mine = bi;
+    for (int off = 16; off; off >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) {
+      out_idx[t] = bi;
+      out_val[t] = bi >= 0 ? bv : 0.f;
+    }
+    if (bi >= 0 && mine == bi) ++head;   // the owner of the winner advances (indices are distinct)
+  }
+}
+
 template <int TCAP>
 __device__ __forceinline__ void select_task(const SelectOp& s) {
-  // each job's T best from its chunks' candidates, then the level selection
-  if (s.T > 0)
-    for (int j = 0; j < s.nj; ++j)
-      dd_topk_body<TCAP, true, true>(s.cval, s.cidx, s.ncand, s.ncand, s.T, s.tidx, s.tval, j, 0, 1);
+  // each job's T best from its chunks' candidates (one warp per job), then
+  // the level selection
+  if (s.T > 0) {
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j < s.nj; j += nw)
+      warp_topk_candidates<TCAP>(s.cval + (int64_t)j * s.ncand, s.cidx + (int64_t)j * s.ncand, s.ncand, s.T,
+                                 s.tidx + (int64_t)j * s.T, s.tval + (int64_t)j * s.T);
+    __syncthreads();
+  }
   dd_select_body<true>(s.jobs, s.job0, s.nj, s.L, s.bins_off0, s.nb, s.bsum, s.tidx, s.tval, s.T, s.has_children,
                        s.n_next, s.n_jobs_dev);
 }
@@ -235,7 +291,7 @@ __device__ __forceinline__ void run_task(const Op& op, int t) {
       const int per = g.gm * g.gn;
       const int b = t / per, rem = t - b * per;
       const GatherRows<true> la(g.a, b), lb(g.b, b);
-      sgemm_tile(la, lb, g.M, g.N, g.K, g.alpha, g.mask_m, g.mask_n, g.m_shift, g.n_contig,
+      sgemm_tile64(la, lb, g.M, g.N, g.K, g.alpha, g.mask_m, g.mask_n, g.m_shift, g.n_contig,
                  g.out + (int64_t)b * g.out_bstride, g.sum ? g.sum + b : nullptr, g.streaming, rem / g.gn,
                  rem % g.gn);
       break;
@@ -261,26 +317,52 @@ __device__ __forceinline__ void run_task(const Op& op, int t) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) dd_persistent_kernel(const Program pg) {
+constexpr int kPhaseOpsCached = 256;
+
+// kMinBlocks: CTAs per SM the registers are budgeted for (2, 3 or 4; the
+// grid is that many per SM when they fit).
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) dd_persistent_kernel(const Program pg) {
+  // the current op's parameters and the phase's op boundaries, in shared
+  // memory (the program is read-only for the launch)
+  __shared__ Op sop;
+  __shared__ int s_task0[kPhaseOpsCached];
+  const bool tracer = blockIdx.x == 0 && threadIdx.x == 0;
+  if (tracer) pg.trace[0] = clock64();
   for (int p = 0; p < pg.n_phases; ++p) {
     const int o0 = __ldg(pg.phase_op + p), o1 = __ldg(pg.phase_op + p + 1);
     const int nt = __ldg(pg.phase_tasks + p);
-    int oi = o0;
+    for (int i = threadIdx.x; i < o1 - o0 && i < kPhaseOpsCached; i += blockDim.x)
+      s_task0[i] = __ldg(&pg.ops[o0 + i].task0);
+    __syncthreads();
+    auto task0 = [&](int i) { return i - o0 < kPhaseOpsCached ? s_task0[i - o0] : __ldg(&pg.ops[i].task0); };
+    int oi = o0, cur = -1;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-      while (oi + 1 < o1 && t >= pg.ops[oi + 1].task0) ++oi;   // tasks ascend with the op index
-      run_task(pg.ops[oi], t - pg.ops[oi].task0);
+      while (oi + 1 < o1 && t >= task0(oi + 1)) ++oi;   // tasks ascend with the op index
+      if (oi != cur) {
+        const int4* src = reinterpret_cast<const int4*>(pg.ops + oi);
+        int4* dst = reinterpret_cast<int4*>(&sop);
+        for (int i = threadIdx.x; i < (int)(sizeof(Op) / sizeof(int4)); i += blockDim.x) dst[i] = __ldg(src + i);
+        __syncthreads();
+        cur = oi;
+      }
+      run_task(sop, t - sop.task0);
       __syncthreads();
     }
     if (p + 1 < pg.n_phases && !grid_barrier(pg.bar, pg.status)) return;
+    if (tracer) pg.trace[p + 1] = clock64();
   }
 }
 
 // ------------------------------------------------------------------ host
 
+constexpr int kCtasPerSmDefault = 3;
+
 struct BatchOpts {
   int merge_ctas = kMergeCtasDefault;
   int topk_chunk = kTopkChunkDefault;
   int ctas = 0;   // 0: every CTA that fits at once
+  int ctas_per_sm = kCtasPerSmDefault;
 };
 
 int read_opts(const cutqc_dd_batch_options* o, BatchOpts* b) {
@@ -291,6 +373,9 @@ int read_opts(const cutqc_dd_batch_options* o, BatchOpts* b) {
   if (o->topk_chunk < 0 || (o->topk_chunk && (o->topk_chunk < 256 || (o->topk_chunk & (o->topk_chunk - 1)))))
     return set_error(CUTQC_EINVAL, "topk_chunk must be 0 or a power of two >= 256");
   if (o->ctas < 0) return set_error(CUTQC_EINVAL, "ctas must be >= 0");
+  if (o->ctas_per_sm != 0 && (o->ctas_per_sm < 2 || o->ctas_per_sm > 4))
+    return set_error(CUTQC_EINVAL, "ctas_per_sm must be 0 or 2..4");
+  if (o->ctas_per_sm) b->ctas_per_sm = o->ctas_per_sm;
   if (o->merge_ctas) b->merge_ctas = o->merge_ctas;
   if (o->topk_chunk) b->topk_chunk = o->topk_chunk;
   b->ctas = o->ctas;
@@ -300,7 +385,8 @@ int read_opts(const cutqc_dd_batch_options* o, BatchOpts* b) {
 struct Built {
   std::vector<Op> ops;
   std::vector<int> phase_op, phase_tasks;
-  size_t ops_off = 0, phase_off = 0, tasks_off = 0, total = 0;
+  std::vector<int> phase_kinds;   // per phase: bit t set if an op of type t runs in it
+  size_t ops_off = 0, phase_off = 0, tasks_off = 0, trace_off = 0, total = 0;
 };
 
 // Builds the program of all runs for a workspace at `base` (nullptr: sizes
@@ -419,7 +505,7 @@ int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& op
         mo.n_jobs = nj;
         mo.n_merged = __builtin_popcountll(mrg);
         mo.log_slices = ls;
-        mo.nx = (int)merge_grid(rows_a * nj, 1 << ls);
+        mo.nx = (int)merge_grid(rows_a * nj, 1 << ls, merge_groups(k, mo.n_merged, ls));
         m.ntasks = mo.nx << ls;
         phase(p_merge).push_back(m);
         if (ls) {
@@ -488,7 +574,7 @@ int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& op
         go.mask_n = stg.mask_n;
         go.m_shift = mask_contig_shift(stg.mask_m);
         go.n_contig = mask_is_low(stg.mask_n);
-        const int64_t gm = (stg.M + SG_BM - 1) / SG_BM, gn = (stg.N + SG_BN - 1) / SG_BN;
+        const int64_t gm = (stg.M + SG64_BM - 1) / SG64_BM, gn = (stg.N + SG64_BN - 1) / SG64_BN;
         if (gm * gn * nj > 0x3fffffff) return set_error(CUTQC_EUNSUPPORTED, "run %d: too many GEMM tiles", r);
         go.gm = (int)gm;
         go.gn = (int)gn;
@@ -561,6 +647,7 @@ int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& op
   out->ops.clear();
   out->phase_op.assign(1, 0);
   out->phase_tasks.clear();
+  out->phase_kinds.clear();
   for (size_t p = 0; p < n_phases; ++p) {
     int64_t tasks = 0;
     for (auto& ph : phases) {
@@ -572,6 +659,9 @@ int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& op
       }
     }
     if (tasks > 0x7fffffff) return set_error(CUTQC_EUNSUPPORTED, "too many tasks in one phase");
+    int kinds = 0;
+    for (int i = out->phase_op.back(); i < (int)out->ops.size(); ++i) kinds |= 1 << out->ops[i].type;
+    out->phase_kinds.push_back(kinds);
     out->phase_op.push_back((int)out->ops.size());
     out->phase_tasks.push_back((int)tasks);
   }
@@ -582,15 +672,27 @@ int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& op
   o = align_up(o + out->phase_op.size() * sizeof(int), 256);
   out->tasks_off = o;
   o = align_up(o + out->phase_tasks.size() * sizeof(int), 256);
+  out->trace_off = o;
+  o = align_up(o + (out->phase_tasks.size() + 1) * sizeof(long long), 256);
   out->total = o;
   return CUTQC_OK;
 }
 
-int max_resident_ctas(int* out) {
+typedef void (*PersistentKernel)(const Program);
+PersistentKernel persistent_kernel(int per_sm) {
+  switch (per_sm) {
+    case 3: return dd_persistent_kernel<3>;
+    case 4: return dd_persistent_kernel<4>;
+    default: return dd_persistent_kernel<2>;
+  }
+}
+
+int max_resident_ctas(int per_sm_wanted, int* out) {
   int per_sm = 0;
-  CUTQC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dd_persistent_kernel, kThreads, 0));
+  CUTQC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(per_sm_wanted), kThreads,
+                                                               0));
   if (per_sm < 1) return set_error(CUTQC_EUNSUPPORTED, "the persistent DD kernel does not fit on an SM");
-  *out = per_sm * sm_count();
+  *out = std::min(per_sm, per_sm_wanted) * sm_count();
   return CUTQC_OK;
 }
 
@@ -599,9 +701,11 @@ int max_resident_ctas(int* out) {
 
 struct cutqc_dd_batch {
   cutqc::Program pg;
+  cutqc::PersistentKernel kernel;
   int grid;
   int n_ops;
   int device;
+  std::vector<int> kinds, tasks;   // per phase
 };
 
 using namespace cutqc;
@@ -631,7 +735,7 @@ extern "C" int cutqc_dd_batch_create(int n_runs, const cutqc_dd_run_desc* runs, 
   if ((rc = build_program(n_runs, runs, o, (uint8_t*)ws_dev, &b))) return rc;
   if (ws_bytes < b.total) return set_error(CUTQC_ENOMEM, "DD batch workspace needs %zu bytes", b.total);
   int grid = 0;
-  if ((rc = max_resident_ctas(&grid))) return rc;
+  if ((rc = max_resident_ctas(o.ctas_per_sm, &grid))) return rc;
   if (o.ctas > 0) grid = std::min(grid, o.ctas);
   uint8_t* ws = (uint8_t*)ws_dev;
   CUTQC_CUDA_TRY(cudaMemcpy(ws + b.ops_off, b.ops.data(), b.ops.size() * sizeof(Op), cudaMemcpyHostToDevice));
@@ -649,7 +753,11 @@ extern "C" int cutqc_dd_batch_create(int n_runs, const cutqc_dd_run_desc* runs, 
   h->pg.n_phases = (int)b.phase_tasks.size();
   h->pg.bar = (GridBar*)ws;
   h->pg.status = status;
+  h->pg.trace = (long long*)(ws + b.trace_off);
+  h->kinds = b.phase_kinds;
+  h->tasks = b.phase_tasks;
   h->grid = grid;
+  h->kernel = persistent_kernel(o.ctas_per_sm);
   h->n_ops = (int)b.ops.size();
   cudaGetDevice(&h->device);
   *out = h;
@@ -671,7 +779,7 @@ extern "C" int cutqc_dd_batch_launch(const cutqc_dd_batch* b, void* stream) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  CUTQC_CUDA_TRY(cudaLaunchKernelEx(&cfg, dd_persistent_kernel, b->pg));
+  CUTQC_CUDA_TRY(cudaLaunchKernelEx(&cfg, b->kernel, b->pg));
   return CUTQC_OK;
 }
 
@@ -680,6 +788,22 @@ extern "C" int cutqc_dd_batch_info(const cutqc_dd_batch* b, int32_t* n_phases, i
   if (n_phases) *n_phases = b->pg.n_phases;
   if (n_ops) *n_ops = b->n_ops;
   if (grid_ctas) *grid_ctas = b->grid;
+  return CUTQC_OK;
+}
+
+extern "C" int cutqc_dd_batch_phases(const cutqc_dd_batch* b, int32_t* kinds, int32_t* tasks, int64_t* cycles,
+                                     int n) {
+  if (!b) return set_error(CUTQC_EINVAL, "null handle");
+  if (n != b->pg.n_phases) return set_error(CUTQC_EINVAL, "n must be the number of phases (%d)", b->pg.n_phases);
+  for (int p = 0; p < n; ++p) {
+    if (kinds) kinds[p] = b->kinds[p];
+    if (tasks) tasks[p] = b->tasks[p];
+  }
+  if (cycles && n > 0) {
+    std::vector<long long> t(n + 1);
+    CUTQC_CUDA_TRY(cudaMemcpy(t.data(), b->pg.trace, (n + 1) * sizeof(long long), cudaMemcpyDeviceToHost));
+    for (int p = 0; p < n; ++p) cycles[p] = t[p + 1] - t[p];
+  }
   return CUTQC_OK;
 }
 

@@ -137,4 +137,104 @@ __device__ __forceinline__ void sgemm_tile(const LA& la, const LB& lb, int64_t M
   }
 }
 
+// A 64 x 64 output tile for small GEMMs (many short contractions, where one
+// 128 x 128 tile's serial k loop is the critical path): 256 threads, 4 x 4
+// outputs per thread, k in chunks of 32 (eight values of A and of B per
+// thread and chunk, issued together; thread (r, l) loads row r, columns
+// l, l + 4, ...).  Every output is the same fmaf chain over k ascending as in
+// sgemm_tile (zero padding past K leaves it unchanged: it never holds -0), so
+// the two tiles give identical outputs; only the float64 sum is grouped
+// differently.
+constexpr int SG64_BM = 64, SG64_BN = 64, SG64_BK = 32;
+
+template <class LA, class LB>
+__device__ __forceinline__ void sgemm_tile64(const LA& la, const LB& lb, int64_t M, int64_t N, int64_t K,
+                                             float alpha, uint64_t mask_m, uint64_t mask_n, int m_contig_shift,
+                                             int n_contig, float* __restrict__ out, double* __restrict__ sum,
+                                             int streaming, int64_t tile_m, int64_t tile_n) {
+  // row pitch 72: the stores of a warp (8 rows x 4 k columns) hit 32 banks
+  __shared__ __align__(16) float As[SG64_BK][SG64_BM + 8];
+  __shared__ __align__(16) float Bs[SG64_BK][SG64_BN + 8];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t m0 = tile_m * SG64_BM;
+  const int64_t n0 = tile_n * SG64_BN;
+  const int lr = tid >> 2, lk = tid & 3;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  const int64_t mr = m0 + lr, nr = n0 + lr;
+  const typename LA::Row arow = la.row(mr < M ? mr : 0);
+  const typename LB::Row brow = lb.row(nr < N ? nr : 0);
+  float ra[8], rb[8];
+  auto gload = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t kk = k0 + lk + 4 * q;
+      ra[q] = (mr < M && kk < K) ? la.at(arow, kk) : 0.f;
+      rb[q] = (nr < N && kk < K) ? lb.at(brow, kk) : 0.f;
+    }
+  };
+  auto sstore = [&]() {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      As[lk + 4 * q][lr] = ra[q];
+      Bs[lk + 4 * q][lr] = rb[q];
+    }
+  };
+  const int64_t nk = (K + SG64_BK - 1) / SG64_BK;
+  gload(0);
+  sstore();
+  __syncthreads();
+  for (int64_t kt = 0; kt < nk; ++kt) {
+    if (kt + 1 < nk) gload((kt + 1) * SG64_BK);
+#pragma unroll
+    for (int k = 0; k < SG64_BK; ++k) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w};
+      const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+    if (kt + 1 < nk) {
+      sstore();
+      __syncthreads();
+    }
+  }
+  double local = 0.0;
+  uint64_t coff[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int64_t n = n0 + tx * 4 + j;
+    coff[j] = n_contig ? (uint64_t)n : pdep64((uint64_t)n, mask_n);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t m = m0 + ty * 4 + i;
+    if (m >= M) continue;
+    const uint64_t roff = m_contig_shift >= 0 ? ((uint64_t)m << m_contig_shift) : pdep64((uint64_t)m, mask_m);
+    float part[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t n = n0 + tx * 4 + j;
+      part[j] = 0.f;
+      if (n >= N) continue;
+      const float v = acc[i][j] * alpha;
+      store_out(out, roff | coff[j], v, streaming);
+      part[j] = v;
+    }
+    local += (double)((part[0] + part[1]) + (part[2] + part[3]));
+  }
+  if (sum) {
+    for (int off = 16; off; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+    if ((tid & 31) == 0) atomicAdd(sum, local);
+  }
+}
+
 }  // namespace cutqc

@@ -353,7 +353,7 @@ class _DDRunDesc(ctypes.Structure):
 
 
 class DDBatchOptions(ctypes.Structure):
-    _fields_ = [("merge_ctas", c_int32), ("topk_chunk", c_int32), ("ctas", c_int32)]
+    _fields_ = [("merge_ctas", c_int32), ("topk_chunk", c_int32), ("ctas", c_int32), ("ctas_per_sm", c_int32)]
 
 
 def _batch_descs(runs):
@@ -375,7 +375,7 @@ def _batch_opts(options):
     if options is None:
         return None
     return ctypes.byref(DDBatchOptions(int(options.get("merge_ctas", 0)), int(options.get("topk_chunk", 0)),
-                                       int(options.get("ctas", 0))))
+                                       int(options.get("ctas", 0)), int(options.get("ctas_per_sm", 0))))
 
 
 def cutqc_dd_batch_workspace_size(runs, options=None):
@@ -413,6 +413,17 @@ class DDBatch:
         _check(lib().cutqc_dd_batch_info(self._h, ctypes.byref(p), ctypes.byref(o), ctypes.byref(g)))
         return {"phases": p.value, "ops": o.value, "ctas": g.value}
 
+    KINDS = ("zero", "merge", "reduce", "contract", "topk", "select")
+
+    def phases(self, cycles=True):
+        """Per phase: op kinds, tasks and (cycles=True: synchronous read) the
+        SM cycles it took in the last completed launch."""
+        n = self.info()["phases"]
+        k, t, c = (c_int32 * max(1, n))(), (c_int32 * max(1, n))(), (c_int64 * max(1, n))()
+        _check(lib().cutqc_dd_batch_phases(self._h, k, t, c if cycles else None, c_int(n)))
+        return [{"kinds": [name for b, name in enumerate(self.KINDS) if (k[p] >> b) & 1], "tasks": t[p],
+                 "cycles": c[p] if cycles else None} for p in range(n)]
+
     def close(self):
         if self._h and self._h.value:
             lib().cutqc_dd_batch_destroy(self._h)
@@ -437,6 +448,10 @@ def cutqc_dd_batch_launch(batch, stream=None):
 
 def cutqc_dd_batch_info(batch):
     return batch.info()
+
+
+def cutqc_dd_batch_phases(batch, cycles=True):
+    return batch.phases(cycles)
 
 
 def cutqc_dd_batch_destroy(batch):

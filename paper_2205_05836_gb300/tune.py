@@ -79,13 +79,14 @@ def tune_dd(subs, attributed, n, M, R, T, max_jobs=64, reps=5, candidates=None, 
 
 # ------------------------------------------------- the persistent DD batch
 # One launch for several circuits (cutqc_dd_batch_*): the shape options are
-# the merge slicing (merge_ctas), the bins per top-T task (topk_chunk) and the
-# grid (ctas, 0 = every CTA that fits at once).  Each candidate builds the
+# the merge slicing (merge_ctas), the bins per top-T task (topk_chunk), the
+# grid (ctas, 0 = every CTA that fits at once) and the CTAs per SM the
+# kernel's registers are budgeted for (ctas_per_sm).  Each candidate builds the
 # batch over the caller's runs (fresh output buffers), replays it as a
 # captured graph, and is kept only if its records and bins match the first
 # candidate's.
 
-BATCH_CANDIDATES = [dict(merge_ctas=m, topk_chunk=c, ctas=0) for m in (1024, 256) for c in (2048, 1024, 4096)]
+BATCH_CANDIDATES = [dict(merge_ctas=1024, topk_chunk=c, ctas=0, ctas_per_sm=r) for r in (3, 2, 4) for c in (4096, 2048)]
 
 
 def batch_shape_key(runs):

@@ -153,6 +153,8 @@ def test_dd_batch_validation_without_gpu(built):
         ([run()], {"topk_chunk": 128}, cq.EINVAL),
         ([run()], {"merge_ctas": 5000}, cq.EINVAL),
         ([run()], {"ctas": -1}, cq.EINVAL),
+        ([run()], {"ctas_per_sm": 5}, cq.EINVAL),
+        ([run()], {"ctas_per_sm": 1}, cq.EINVAL),
         ([], None, cq.EINVAL),
     ]
     for runs, opt, code in cases:

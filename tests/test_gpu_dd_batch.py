@@ -45,10 +45,15 @@ def _same_records(cq, got, ref, bins, ref_bins):
         assert J.zoom() == Rj.zoom()
         assert list(J.top_idx) == list(Rj.top_idx)
         assert list(J.top_val) == list(Rj.top_val)
-        assert abs(J.bin_sum - Rj.bin_sum) <= 1e-12   # float64 totals: atomic order may differ
         nb = 1 << J.n_active
-        # same merge slices, GEMM tiles and k order: the bins are identical
-        assert torch.equal(bins[J.bins_offset:J.bins_offset + nb], ref_bins[Rj.bins_offset:Rj.bins_offset + nb])
+        b = bins[J.bins_offset:J.bins_offset + nb]
+        # same merge slices and the same fmaf chain over k per bin: identical bins
+        assert torch.equal(b, ref_bins[Rj.bins_offset:Rj.bins_offset + nb])
+        # the float64 totals add float partials of 4 (persistent tile) or 8 bins
+        # (level-by-level tile), each rounded by at most 3 * 2^-24 of its size,
+        # in atomic order: they agree within that bound on both sides
+        mass = float(b.double().abs().sum())
+        assert abs(J.bin_sum - Rj.bin_sum) <= 6 * 2.0 ** -24 * mass + 1e-12
 
 
 def _reference(cq, subs, At, n, M, R, T, options=None):
@@ -58,8 +63,9 @@ def _reference(cq, subs, At, n, M, R, T, options=None):
     return cq.dd_jobs_from_device(jobs, n_jobs), bins
 
 
-@pytest.mark.parametrize("options", [None, {"topk_chunk": 256}, {"ctas": 7}, {"merge_ctas": 64, "topk_chunk": 512}],
-                         ids=["default", "chunk256", "ctas7", "merge64"])
+@pytest.mark.parametrize("options", [None, {"topk_chunk": 256}, {"ctas": 7}, {"merge_ctas": 64, "topk_chunk": 512},
+                                     {"ctas_per_sm": 2}, {"ctas_per_sm": 4}],
+                         ids=["default", "chunk256", "ctas7", "merge64", "per_sm2", "per_sm4"])
 def test_batch_matches_level_by_level_and_oracle(cq, options):
     """Three circuits in one persistent launch: every run's records, bins and
     selections equal those of its own level-by-level run (same merge slicing),
