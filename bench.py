@@ -916,8 +916,9 @@ def run_profile_case(args):
         for _ in range(2):
             batch.launch()
         torch.cuda.synchronize()
+        # per-phase durations of the last launch (SM cycles of CTA 0 between barriers)
         info.update({"workload": [w.name for w in dd_batched()], "batch": batch.info(),
-                     "device_status": cq.cutqc_device_status()})
+                     "phases": batch.phases(), "device_status": cq.cutqc_device_status()})
     else:
         from workloads.configs import dd_batched
         runs = []

@@ -315,8 +315,9 @@ int cutqc_dd_run_async(int n_sub, const cutqc_subcircuit* s, const float* const*
  *   jobs_dev, n_jobs_dev, bins_dev, bins_capacity, max_jobs: that run's
  *   outputs, as cutqc_dd_run_async.
  * Options (zero fields take defaults): merge_ctas as cutqc_dd_options;
- * topk_chunk bins per task of the chunked top-T pass (a power of two >= 256,
- * default 2048); ctas caps the grid (default: every CTA that fits at once);
+ * topk_chunk bins per task of the chunked top-T phase (a power of two >=
+ * 256, default 2048); ctas caps the grid (default: every CTA that fits at
+ * once);
  * ctas_per_sm (2..4, default 3) the CTAs per SM that the kernel's registers
  * are budgeted for (more resident warps, fewer registers each).
  * cutqc_dd_batch_create validates the runs, lays out `ws_dev` (at least
@@ -363,9 +364,11 @@ int cutqc_dd_batch_info(const cutqc_dd_batch* batch, int32_t* n_phases, int32_t*
 /* Per phase p < n (n = the number of phases): kinds[p] has bit t set when an
  * op of kind t runs in it (0 zero bin totals, 1 merge, 2 slice reduction,
  * 3 contraction step, 4 chunked top-T, 5 level selection), tasks[p] its
- * tasks, cycles[p] the SM clock cycles CTA 0 saw it take in the last
+ * tasks, fma[p] the multiply-adds of its contraction steps (M * N * K per
+ * job), cycles[p] the SM clock cycles CTA 0 saw it take in the last
  * completed launch (a synchronous copy).  Any output may be null.           */
-int cutqc_dd_batch_phases(const cutqc_dd_batch* batch, int32_t* kinds, int32_t* tasks, int64_t* cycles, int n);
+int cutqc_dd_batch_phases(const cutqc_dd_batch* batch, int32_t* kinds, int32_t* tasks, int64_t* fma,
+                          int64_t* cycles, int n);
 int cutqc_dd_batch_destroy(cutqc_dd_batch* batch);
 
 /* ------------------------------------------------------------- reductions

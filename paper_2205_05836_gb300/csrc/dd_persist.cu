@@ -267,7 +267,7 @@ __device__ __forceinline__ void select_task(const SelectOp& s) {
                        s.n_next, s.n_jobs_dev);
 }
 
-__device__ __forceinline__ void run_task(const Op& op, int t) {
+__device__ __forceinline__ void run_task(const Op& op, int t, Tile64Smem& tsm) {
   switch (op.type) {
     case OP_ZERO: {
       const ZeroOp& z = op.u.zero;
@@ -292,8 +292,8 @@ __device__ __forceinline__ void run_task(const Op& op, int t) {
       const int b = t / per, rem = t - b * per;
       const GatherRows<true> la(g.a, b), lb(g.b, b);
       sgemm_tile64(la, lb, g.M, g.N, g.K, g.alpha, g.mask_m, g.mask_n, g.m_shift, g.n_contig,
-                 g.out + (int64_t)b * g.out_bstride, g.sum ? g.sum + b : nullptr, g.streaming, rem / g.gn,
-                 rem % g.gn);
+                   g.out + (int64_t)b * g.out_bstride, g.sum ? g.sum + b : nullptr, g.streaming, rem / g.gn,
+                   rem % g.gn, tsm);
       break;
     }
     case OP_TOPK: {
@@ -318,7 +318,6 @@ __device__ __forceinline__ void run_task(const Op& op, int t) {
 }
 
 constexpr int kPhaseOpsCached = 256;
-
 // kMinBlocks: CTAs per SM the registers are budgeted for (2, 3 or 4; the
 // grid is that many per SM when they fit).
 template <int kMinBlocks>
@@ -327,6 +326,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) dd_persistent_kernel(con
   // memory (the program is read-only for the launch)
   __shared__ Op sop;
   __shared__ int s_task0[kPhaseOpsCached];
+  __shared__ Tile64Smem tsm;
   const bool tracer = blockIdx.x == 0 && threadIdx.x == 0;
   if (tracer) pg.trace[0] = clock64();
   for (int p = 0; p < pg.n_phases; ++p) {
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) dd_persistent_kernel(con
         __syncthreads();
         cur = oi;
       }
-      run_task(sop, t - sop.task0);
+      run_task(sop, t - sop.task0, tsm);
       __syncthreads();
     }
     if (p + 1 < pg.n_phases && !grid_barrier(pg.bar, pg.status)) return;
@@ -386,6 +386,7 @@ struct Built {
   std::vector<Op> ops;
   std::vector<int> phase_op, phase_tasks;
   std::vector<int> phase_kinds;   // per phase: bit t set if an op of type t runs in it
+  std::vector<int64_t> phase_fma; // per phase: multiply-adds of its contraction steps (M N K per job)
   size_t ops_off = 0, phase_off = 0, tasks_off = 0, trace_off = 0, total = 0;
 };
 
@@ -535,6 +536,29 @@ int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& op
       const size_t n_in = in.size();
       std::vector<int> depth(plan.tensors.size(), 0);
       int max_depth = 0;
+      // the level selection (its candidates are filled in below)
+      Op q{};
+      q.type = OP_SELECT;
+      q.ntasks = 1;
+      {
+        SelectOp& so = q.u.select;
+        so.jobs = R.jobs_dev;
+        so.L.level = level;
+        so.L.depth = level;
+        so.L.n_active = (int)L.active.size();
+        for (int a = 0; a < so.L.n_active; ++a) so.L.active[a] = (int8_t)L.active[a];
+        so.bins_off0 = bins_off;
+        so.nb = nb;
+        so.bsum = bsum;
+        so.tidx = ws ? (int32_t*)(ws + lay.top_idx_off) : nullptr;
+        so.tval = ws ? (float*)(ws + lay.top_val_off) : nullptr;
+        so.n_jobs_dev = R.n_jobs_dev;
+        so.job0 = job0;
+        so.nj = nj;
+        so.T = R.T;
+        so.has_children = level + 1 < levels && R.T > 0;
+        so.n_next = so.has_children ? Tn : 0;
+      }
       for (const PlanStage& stg : plan.stages) {
         const int d = 1 + std::max(depth[stg.a], depth[stg.b]);
         depth[stg.result] = d;
@@ -611,32 +635,10 @@ int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& op
         k.ntasks = (int)(nj * chunks);
         phase(p_next++).push_back(k);
       }
-      {
-        Op q{};
-        q.type = OP_SELECT;
-        q.ntasks = 1;
-        SelectOp& so = q.u.select;
-        so.jobs = R.jobs_dev;
-        so.L.level = level;
-        so.L.depth = level;
-        so.L.n_active = (int)L.active.size();
-        for (int a = 0; a < so.L.n_active; ++a) so.L.active[a] = (int8_t)L.active[a];
-        so.bins_off0 = bins_off;
-        so.nb = nb;
-        so.bsum = bsum;
-        so.cidx = cidx;
-        so.cval = cval;
-        so.tidx = ws ? (int32_t*)(ws + lay.top_idx_off) : nullptr;
-        so.tval = ws ? (float*)(ws + lay.top_val_off) : nullptr;
-        so.n_jobs_dev = R.n_jobs_dev;
-        so.job0 = job0;
-        so.nj = nj;
-        so.ncand = (int)(chunks * R.T);
-        so.T = R.T;
-        so.has_children = level + 1 < levels && R.T > 0;
-        so.n_next = so.has_children ? Tn : 0;
-        phase(p_next).push_back(q);
-      }
+      q.u.select.cidx = cidx;
+      q.u.select.cval = cval;
+      q.u.select.ncand = (int)(chunks * R.T);
+      phase(p_next).push_back(q);
       job0 += nj;
       bins_off += (int64_t)nj * nb;
     }
@@ -648,6 +650,7 @@ int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& op
   out->phase_op.assign(1, 0);
   out->phase_tasks.clear();
   out->phase_kinds.clear();
+  out->phase_fma.clear();
   for (size_t p = 0; p < n_phases; ++p) {
     int64_t tasks = 0;
     for (auto& ph : phases) {
@@ -660,8 +663,15 @@ int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& op
     }
     if (tasks > 0x7fffffff) return set_error(CUTQC_EUNSUPPORTED, "too many tasks in one phase");
     int kinds = 0;
-    for (int i = out->phase_op.back(); i < (int)out->ops.size(); ++i) kinds |= 1 << out->ops[i].type;
+    int64_t fma = 0;
+    for (int i = out->phase_op.back(); i < (int)out->ops.size(); ++i) {
+      const Op& op = out->ops[i];
+      kinds |= 1 << op.type;
+      if (op.type == OP_GEMM)
+        fma += op.u.gemm.M * op.u.gemm.N * op.u.gemm.K * (op.ntasks / (op.u.gemm.gm * op.u.gemm.gn));
+    }
     out->phase_kinds.push_back(kinds);
+    out->phase_fma.push_back(fma);
     out->phase_op.push_back((int)out->ops.size());
     out->phase_tasks.push_back((int)tasks);
   }
@@ -706,6 +716,7 @@ struct cutqc_dd_batch {
   int n_ops;
   int device;
   std::vector<int> kinds, tasks;   // per phase
+  std::vector<int64_t> fma;
 };
 
 using namespace cutqc;
@@ -756,6 +767,7 @@ extern "C" int cutqc_dd_batch_create(int n_runs, const cutqc_dd_run_desc* runs, 
   h->pg.trace = (long long*)(ws + b.trace_off);
   h->kinds = b.phase_kinds;
   h->tasks = b.phase_tasks;
+  h->fma = b.phase_fma;
   h->grid = grid;
   h->kernel = persistent_kernel(o.ctas_per_sm);
   h->n_ops = (int)b.ops.size();
@@ -791,13 +803,14 @@ extern "C" int cutqc_dd_batch_info(const cutqc_dd_batch* b, int32_t* n_phases, i
   return CUTQC_OK;
 }
 
-extern "C" int cutqc_dd_batch_phases(const cutqc_dd_batch* b, int32_t* kinds, int32_t* tasks, int64_t* cycles,
-                                     int n) {
+extern "C" int cutqc_dd_batch_phases(const cutqc_dd_batch* b, int32_t* kinds, int32_t* tasks, int64_t* fma,
+                                     int64_t* cycles, int n) {
   if (!b) return set_error(CUTQC_EINVAL, "null handle");
   if (n != b->pg.n_phases) return set_error(CUTQC_EINVAL, "n must be the number of phases (%d)", b->pg.n_phases);
   for (int p = 0; p < n; ++p) {
     if (kinds) kinds[p] = b->kinds[p];
     if (tasks) tasks[p] = b->tasks[p];
+    if (fma) fma[p] = b->fma[p];
   }
   if (cycles && n > 0) {
     std::vector<long long> t(n + 1);

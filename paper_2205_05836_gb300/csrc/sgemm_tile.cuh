@@ -147,14 +147,20 @@ __device__ __forceinline__ void sgemm_tile(const LA& la, const LB& lb, int64_t M
 // differently.
 constexpr int SG64_BM = 64, SG64_BN = 64, SG64_BK = 32;
 
+// The tile's staging arrays (one per block, shared by every instantiation).
+// Row pitch 72: the stores of a warp (8 rows x 4 k columns) hit 32 banks.
+struct Tile64Smem {
+  __align__(16) float A[SG64_BK][SG64_BM + 8];
+  __align__(16) float B[SG64_BK][SG64_BN + 8];
+};
+
 template <class LA, class LB>
 __device__ __forceinline__ void sgemm_tile64(const LA& la, const LB& lb, int64_t M, int64_t N, int64_t K,
                                              float alpha, uint64_t mask_m, uint64_t mask_n, int m_contig_shift,
                                              int n_contig, float* __restrict__ out, double* __restrict__ sum,
-                                             int streaming, int64_t tile_m, int64_t tile_n) {
-  // row pitch 72: the stores of a warp (8 rows x 4 k columns) hit 32 banks
-  __shared__ __align__(16) float As[SG64_BK][SG64_BM + 8];
-  __shared__ __align__(16) float Bs[SG64_BK][SG64_BN + 8];
+                                             int streaming, int64_t tile_m, int64_t tile_n, Tile64Smem& sm) {
+  auto& As = sm.A;
+  auto& Bs = sm.B;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t m0 = tile_m * SG64_BM;

@@ -416,13 +416,15 @@ class DDBatch:
     KINDS = ("zero", "merge", "reduce", "contract", "topk", "select")
 
     def phases(self, cycles=True):
-        """Per phase: op kinds, tasks and (cycles=True: synchronous read) the
-        SM cycles it took in the last completed launch."""
+        """Per phase: op kinds, tasks, contraction multiply-adds and
+        (cycles=True: synchronous read) the SM cycles it took in the last
+        completed launch."""
         n = self.info()["phases"]
-        k, t, c = (c_int32 * max(1, n))(), (c_int32 * max(1, n))(), (c_int64 * max(1, n))()
-        _check(lib().cutqc_dd_batch_phases(self._h, k, t, c if cycles else None, c_int(n)))
+        k, t = (c_int32 * max(1, n))(), (c_int32 * max(1, n))()
+        f, c = (c_int64 * max(1, n))(), (c_int64 * max(1, n))()
+        _check(lib().cutqc_dd_batch_phases(self._h, k, t, f, c if cycles else None, c_int(n)))
         return [{"kinds": [name for b, name in enumerate(self.KINDS) if (k[p] >> b) & 1], "tasks": t[p],
-                 "cycles": c[p] if cycles else None} for p in range(n)]
+                 "fma": f[p], "cycles": c[p] if cycles else None} for p in range(n)]
 
     def close(self):
         if self._h and self._h.value:

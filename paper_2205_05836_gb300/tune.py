@@ -86,7 +86,7 @@ def tune_dd(subs, attributed, n, M, R, T, max_jobs=64, reps=5, candidates=None, 
 # captured graph, and is kept only if its records and bins match the first
 # candidate's.
 
-BATCH_CANDIDATES = [dict(merge_ctas=1024, topk_chunk=c, ctas=0, ctas_per_sm=r) for r in (3, 2, 4) for c in (4096, 2048)]
+BATCH_CANDIDATES = [dict(merge_ctas=1024, topk_chunk=c, ctas=0, ctas_per_sm=r) for r in (3, 2, 4) for c in (2048, 4096)]
 
 
 def batch_shape_key(runs):

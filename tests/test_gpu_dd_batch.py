@@ -64,8 +64,8 @@ def _reference(cq, subs, At, n, M, R, T, options=None):
 
 
 @pytest.mark.parametrize("options", [None, {"topk_chunk": 256}, {"ctas": 7}, {"merge_ctas": 64, "topk_chunk": 512},
-                                     {"ctas_per_sm": 2}, {"ctas_per_sm": 4}],
-                         ids=["default", "chunk256", "ctas7", "merge64", "per_sm2", "per_sm4"])
+                                     {"ctas_per_sm": 2}, {"ctas_per_sm": 4}, {"ctas": 3, "ctas_per_sm": 3}],
+                         ids=["default", "chunk256", "ctas7", "merge64", "per_sm2", "per_sm4", "ctas3"])
 def test_batch_matches_level_by_level_and_oracle(cq, options):
     """Three circuits in one persistent launch: every run's records, bins and
     selections equal those of its own level-by-level run (same merge slicing),
@@ -100,6 +100,25 @@ def test_batch_matches_level_by_level_and_oracle(cq, options):
             b = r["bins"][J.bins_offset:J.bins_offset + (1 << J.n_active)].cpu().numpy().astype(np.float64)
             assert np.abs(b - o["bins"]).max() <= 1e-6
             assert abs(J.bin_sum - o["bins"].sum()) <= 1e-6
+
+
+@pytest.mark.parametrize("topk_chunk", [256, 2048])
+def test_batch_wide_selection(cq, topk_chunk):
+    """T = 6 (each chunk's list wider than 4) on two circuits: records and
+    bins equal the level-by-level run's."""
+    import torch
+    runs, refs = [], []
+    for cut, M, _ in _cuts()[:2]:
+        subs, A, At = _setup(cut)
+        n = cut.circuit.n
+        refs.append(_reference(cq, subs, At, n, M, 4, 6))
+        runs.append(cq.dd_batch_run(subs, At, n, M, 4, 6, max_jobs=64))
+    batch = cq.cutqc_dd_batch_create(runs, {"topk_chunk": topk_chunk})
+    batch.launch()
+    torch.cuda.synchronize()
+    for r, (ref_jobs, ref_bins) in zip(runs, refs):
+        _same_records(cq, cq.dd_jobs_from_device(r["jobs"], r["n_jobs"]), ref_jobs, r["bins"], ref_bins)
+    assert cq.cutqc_device_status() == 0
 
 
 def test_batch_in_cuda_graph_replays(cq):
