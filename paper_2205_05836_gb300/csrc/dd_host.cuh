@@ -29,10 +29,12 @@ struct RunLayout {
 
 constexpr int kMergeCtasDefault = 1024, kMergeCtasMax = 4096;
 
-// CTAs of a merge launch: enough to fill the GPU once, each walking rows
-// (`groups` rows at a time: merge_groups in dd_kernels.cuh)
-inline unsigned merge_grid(int64_t rows, int slices, int groups = 1) {
-  const int64_t cap = std::max<int64_t>(1, (int64_t)sm_count() * 8 / std::max(1, slices));
+// CTAs of a merge launch: enough to fill the GPU once (`ctas` of them, by
+// default 8 per SM), each walking rows (`groups` rows at a time:
+// merge_groups in dd_kernels.cuh)
+inline unsigned merge_grid(int64_t rows, int slices, int groups = 1, int64_t ctas = 0) {
+  if (ctas <= 0) ctas = (int64_t)sm_count() * 8;
+  const int64_t cap = std::max<int64_t>(1, ctas / std::max(1, slices));
   const int64_t walk = (rows + groups - 1) / std::max(1, groups);
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(walk, cap));
 }

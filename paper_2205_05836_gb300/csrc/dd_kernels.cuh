@@ -198,23 +198,38 @@ __device__ __forceinline__ void dd_merge_reduce_body(const float* __restrict__ p
   }
 }
 
-// Selection order of bins: larger value first, then lower index.
+// The T largest entries of one job by (value desc, index asc).  Block (job,
+// chunk) of (., nchunks) scans entries [chunk * chunk_len, (chunk + 1) *
+// chunk_len) of job `job`'s n entries and writes its T best to slot (job *
+// nchunks + chunk).  kCand = false: the entries are bins and an entry's index
+// is its position; kCand = true: the entries are (value, index) candidates of
+// an earlier pass (index -1 = none), which is how large jobs are finished
+// (chunked pass, then one block per job over the chunks' candidates).  One
+// pass: each thread keeps its own best TCAP (sorted), then T rounds pick the
+// block's best head and advance its owner.
 __device__ __forceinline__ bool dd_better(float v, int i, float w, int j) {
   return v > w || (v == w && i < j);
 }
 
-// A thread's best TCAP entries so far (T <= TCAP of them kept), sorted by
-// dd_better; slots past cnt are never read.
-template <int TCAP>
-struct TopList {
+template <int TCAP, bool kCand, bool kCoherent>
+__device__ __forceinline__ void dd_topk_body(const float* __restrict__ vals, const int32_t* __restrict__ cidx,
+                                             int64_t n, int64_t chunk_len, int T, int32_t* __restrict__ top_idx,
+                                             float* __restrict__ top_val, int job, int chunk, int nchunks) {
+  __shared__ float sv[32];
+  __shared__ int si[32];
+  __shared__ int win_i;
+  const float* b = vals + (int64_t)job * n;
+  const int32_t* ci = kCand ? cidx + (int64_t)job * n : nullptr;
+  const int64_t lo = (int64_t)chunk * chunk_len;
+  const int64_t hi = lo + chunk_len < n ? lo + chunk_len : n;
+  const int64_t slot = ((int64_t)job * nchunks + chunk) * T;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float lv[TCAP];
   int li[TCAP];
-  int cnt;
-  __device__ __forceinline__ TopList() : cnt(0) {
 #pragma unroll
-    for (int u = 0; u < TCAP; ++u) { lv[u] = -INFINITY; li[u] = -1; }
-  }
-  __device__ __forceinline__ void offer(float v, int idx, int T) {
+  for (int u = 0; u < TCAP; ++u) { lv[u] = -INFINITY; li[u] = -1; }   // read only once filled
+  int cnt = 0;
+  auto offer = [&](float v, int idx) {
     if (cnt == T && !dd_better(v, idx, lv[T - 1], li[T - 1])) return;
     int pos = cnt < T ? cnt : T - 1;
 #pragma unroll
@@ -224,79 +239,7 @@ struct TopList {
     lv[pos] = v;
     li[pos] = idx;
     if (cnt < T) ++cnt;
-  }
-};
-
-// The block's T best over its threads' lists: T rounds pick the best head
-// (warp shuffles, then one warp over the warps' winners) and advance its
-// owner (indices are distinct).  Every thread of the block calls it; thread 0
-// writes top_idx[0..T) / top_val[0..T) (-1 / 0 past the entries).
-template <int TCAP>
-__device__ __forceinline__ void block_top_rounds(const TopList<TCAP>& L, int T, int32_t* __restrict__ top_idx,
-                                                 float* __restrict__ top_val) {
-  __shared__ float sv[32];
-  __shared__ int si[32];
-  __shared__ int win_i;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int head = 0;
-  for (int t = 0; t < T; ++t) {
-    float bv = -INFINITY;
-    int bi = -1;
-#pragma unroll
-    for (int u = 0; u < TCAP; ++u)
-      if (u == head && head < L.cnt) { bv = L.lv[u]; bi = L.li[u]; }
-    for (int off = 16; off; off >>= 1) {
-      const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-      if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
-    }
-    if (lane == 0) { sv[warp] = bv; si[warp] = bi; }
-    __syncthreads();
-    if (warp == 0) {
-      const int nw = blockDim.x >> 5;
-      bv = lane < nw ? sv[lane] : -INFINITY;
-      bi = lane < nw ? si[lane] : -1;
-      for (int off = 16; off; off >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
-      }
-      if (lane == 0) {
-        win_i = bi;
-        top_idx[t] = bi;
-        top_val[t] = bi >= 0 ? bv : 0.f;
-      }
-    }
-    __syncthreads();
-    if (head < L.cnt && win_i >= 0) {
-      int cur = -1;
-#pragma unroll
-      for (int u = 0; u < TCAP; ++u)
-        if (u == head) cur = L.li[u];
-      if (cur == win_i) ++head;
-    }
-    __syncthreads();
-  }
-}
-
-// The T largest entries of one job by (value desc, index asc).  Block (job,
-// chunk) of (., nchunks) scans entries [chunk * chunk_len, (chunk + 1) *
-// chunk_len) of job `job`'s n entries and writes its T best to slot (job *
-// nchunks + chunk).  kCand = false: the entries are bins and an entry's index
-// is its position; kCand = true: the entries are (value, index) candidates of
-// an earlier pass (index -1 = none), which is how large jobs are finished
-// (chunked pass, then one block per job over the chunks' candidates).  One
-// pass: each thread keeps its own best TCAP (sorted), then block_top_rounds.
-template <int TCAP, bool kCand, bool kCoherent>
-__device__ __forceinline__ void dd_topk_body(const float* __restrict__ vals, const int32_t* __restrict__ cidx,
-                                             int64_t n, int64_t chunk_len, int T, int32_t* __restrict__ top_idx,
-                                             float* __restrict__ top_val, int job, int chunk, int nchunks) {
-  const float* b = vals + (int64_t)job * n;
-  const int32_t* ci = kCand ? cidx + (int64_t)job * n : nullptr;
-  const int64_t lo = (int64_t)chunk * chunk_len;
-  const int64_t hi = lo + chunk_len < n ? lo + chunk_len : n;
-  const int64_t slot = ((int64_t)job * nchunks + chunk) * T;
-  TopList<TCAP> L;
+  };
   int64_t tail0 = lo;
   if (!kCand && (((uintptr_t)(b + lo)) & 15) == 0) {
     // bins: float4 loads, four in flight per thread (the order in which a
@@ -316,7 +259,7 @@ __device__ __forceinline__ void dd_topk_body(const float* __restrict__ vals, con
         const int64_t qu = q + u * (int64_t)blockDim.x;
         if (qu < n4) {
           const int i0 = (int)(lo + 4 * qu);
-          L.offer(v[u].x, i0, T); L.offer(v[u].y, i0 + 1, T); L.offer(v[u].z, i0 + 2, T); L.offer(v[u].w, i0 + 3, T);
+          offer(v[u].x, i0); offer(v[u].y, i0 + 1); offer(v[u].z, i0 + 2); offer(v[u].w, i0 + 3);
         }
       }
     }
@@ -326,9 +269,48 @@ __device__ __forceinline__ void dd_topk_body(const float* __restrict__ vals, con
     const float v = ldx<kCoherent>(b + i);
     const int idx = kCand ? ldx<kCoherent>(ci + i) : (int)i;
     if (kCand && idx < 0) continue;
-    L.offer(v, idx, T);
+    offer(v, idx);
   }
-  block_top_rounds<TCAP>(L, T, top_idx + slot, top_val + slot);
+  int head = 0;
+  for (int t = 0; t < T; ++t) {
+    float bv = -INFINITY;
+    int bi = -1;
+#pragma unroll
+    for (int u = 0; u < TCAP; ++u)
+      if (u == head && head < cnt) { bv = lv[u]; bi = li[u]; }
+    for (int off = 16; off; off >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { sv[warp] = bv; si[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      const int nw = blockDim.x >> 5;
+      bv = lane < nw ? sv[lane] : -INFINITY;
+      bi = lane < nw ? si[lane] : -1;
+      for (int off = 16; off; off >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) {
+        win_i = bi;
+        top_idx[slot + t] = bi;
+        top_val[slot + t] = bi >= 0 ? bv : 0.f;
+      }
+    }
+    __syncthreads();
+    // the owner of the winning index advances (indices are distinct)
+    if (head < cnt && win_i >= 0) {
+      int cur = -1;
+#pragma unroll
+      for (int u = 0; u < TCAP; ++u)
+        if (u == head) cur = li[u];
+      if (cur == win_i) ++head;
+    }
+    __syncthreads();
+  }
 }
 
 struct LevelInfo {

@@ -116,6 +116,7 @@ struct GemmOp {
   float alpha;
   uint64_t mask_m, mask_n;
   int m_shift, n_contig, streaming, gm, gn;
+  int narrow;            // 256 x 16 tiles (N <= 16), else 64 x 64
   float* out;
   int64_t out_bstride;
   double* sum;
@@ -171,24 +172,39 @@ struct Program {
   long long* trace;          // [n_phases + 1]: CTA 0's clock at the start and after each phase
 };
 
-// Grid-wide barrier of a cooperative launch (every CTA resident).  Returns
-// false when the run is aborted (a wait ran out, here or in another CTA).
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_add_release(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident).  Thread 0
+// of each CTA arrives with an acquire-release add (after the block barrier,
+// so the CTA's writes are ordered before it); the last arriver resets the
+// count and releases the generation word, which the others poll with acquire
+// loads.  Returns false when the run is aborted (a wait ran out, here or in
+// another CTA).
 __device__ bool grid_barrier(GridBar* g, int* status) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int res = 1;
-    volatile unsigned int* vgen = &g->gen;
     volatile int* vabort = &g->abort;
-    const unsigned int my_gen = *vgen;
-    __threadfence();
-    if (atomicAdd(&g->arrived, 1u) == gridDim.x - 1) {
+    const unsigned int my_gen = ld_acquire(&g->gen);
+    if (atom_add_acq_rel(&g->arrived, 1u) == gridDim.x - 1) {
       atomicExch(&g->arrived, 0u);
-      __threadfence();
-      atomicAdd(&g->gen, 1u);
+      red_add_release(&g->gen, 1u);
     } else {
       const long long t0 = clock64();
-      while (*vgen == my_gen) {
+      while (ld_acquire(&g->gen) == my_gen) {
         if (*vabort) { res = 0; break; }
         if (clock64() - t0 > kBarrierTimeoutCycles) {
           atomicExch(&g->abort, 1);
@@ -196,10 +212,9 @@ __device__ bool grid_barrier(GridBar* g, int* status) {
           res = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
-    __threadfence();
     ok = res && !*vabort;
   }
   __syncthreads();
@@ -291,9 +306,14 @@ __device__ __forceinline__ void run_task(const Op& op, int t, Tile64Smem& tsm) {
       const int per = g.gm * g.gn;
       const int b = t / per, rem = t - b * per;
       const GatherRows<true> la(g.a, b), lb(g.b, b);
-      sgemm_tile64(la, lb, g.M, g.N, g.K, g.alpha, g.mask_m, g.mask_n, g.m_shift, g.n_contig,
-                   g.out + (int64_t)b * g.out_bstride, g.sum ? g.sum + b : nullptr, g.streaming, rem / g.gn,
-                   rem % g.gn, tsm);
+      float* out = g.out + (int64_t)b * g.out_bstride;
+      double* sum = g.sum ? g.sum + b : nullptr;
+      if (g.narrow)
+        sgemm_tile_narrow(la, lb, g.M, g.N, g.K, g.alpha, g.mask_m, g.mask_n, g.m_shift, g.n_contig, out, sum,
+                          g.streaming, rem / g.gn, rem % g.gn, tsm);
+      else
+        sgemm_tile64(la, lb, g.M, g.N, g.K, g.alpha, g.mask_m, g.mask_n, g.m_shift, g.n_contig, out, sum,
+                     g.streaming, rem / g.gn, rem % g.gn, tsm);
       break;
     }
     case OP_TOPK: {
@@ -506,7 +526,9 @@ int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& op
         mo.n_jobs = nj;
         mo.n_merged = __builtin_popcountll(mrg);
         mo.log_slices = ls;
-        mo.nx = (int)merge_grid(rows_a * nj, 1 << ls, merge_groups(k, mo.n_merged, ls));
+        // walkers: at most one per CTA of the grid (fewer, longer tasks)
+        mo.nx = (int)merge_grid(rows_a * nj, 1 << ls, merge_groups(k, mo.n_merged, ls),
+                                (int64_t)sm_count() * opt.ctas_per_sm);
         m.ntasks = mo.nx << ls;
         phase(p_merge).push_back(m);
         if (ls) {
@@ -598,7 +620,9 @@ int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& op
         go.mask_n = stg.mask_n;
         go.m_shift = mask_contig_shift(stg.mask_m);
         go.n_contig = mask_is_low(stg.mask_n);
-        const int64_t gm = (stg.M + SG64_BM - 1) / SG64_BM, gn = (stg.N + SG64_BN - 1) / SG64_BN;
+        go.narrow = stg.N <= SGN_BN;
+        const int64_t tm = go.narrow ? SGN_BM : SG64_BM, tn = go.narrow ? SGN_BN : SG64_BN;
+        const int64_t gm = (stg.M + tm - 1) / tm, gn = (stg.N + tn - 1) / tn;
         if (gm * gn * nj > 0x3fffffff) return set_error(CUTQC_EUNSUPPORTED, "run %d: too many GEMM tiles", r);
         go.gm = (int)gm;
         go.gn = (int)gn;

@@ -147,11 +147,27 @@ __device__ __forceinline__ void sgemm_tile(const LA& la, const LB& lb, int64_t M
 // differently.
 constexpr int SG64_BM = 64, SG64_BN = 64, SG64_BK = 32;
 
-// The tile's staging arrays (one per block, shared by every instantiation).
-// Row pitch 72: the stores of a warp (8 rows x 4 k columns) hit 32 banks.
+// A 256 x 16 tile for contractions with few columns (N <= 16, where a 64 x 64
+// tile would leave most of its outputs out of range): k in chunks of 16,
+// thread t stages row t of A and element t of B's 16 x 16 chunk, and
+// computes rows 4 (t >> 2) .. + 3, columns 4 (t & 3) .. + 3.  Same fmaf
+// chains, so the same outputs as the other tiles.
+constexpr int SGN_BM = 256, SGN_BN = 16, SGN_BK = 16;
+
+// The tiles' staging arrays (one per block, shared by every instantiation).
+// Row pitch 72 in the 64 x 64 tile: the stores of a warp (8 rows x 4 k
+// columns) hit 32 banks.
 struct Tile64Smem {
-  __align__(16) float A[SG64_BK][SG64_BM + 8];
-  __align__(16) float B[SG64_BK][SG64_BN + 8];
+  union {
+    struct {
+      __align__(16) float A[SG64_BK][SG64_BM + 8];
+      __align__(16) float B[SG64_BK][SG64_BN + 8];
+    } sq;
+    struct {
+      __align__(16) float A[SGN_BK][SGN_BM + 4];
+      __align__(16) float B[SGN_BK][SGN_BN + 4];
+    } narrow;
+  };
 };
 
 template <class LA, class LB>
@@ -159,8 +175,8 @@ __device__ __forceinline__ void sgemm_tile64(const LA& la, const LB& lb, int64_t
                                              float alpha, uint64_t mask_m, uint64_t mask_n, int m_contig_shift,
                                              int n_contig, float* __restrict__ out, double* __restrict__ sum,
                                              int streaming, int64_t tile_m, int64_t tile_n, Tile64Smem& sm) {
-  auto& As = sm.A;
-  auto& Bs = sm.B;
+  auto& As = sm.sq.A;
+  auto& Bs = sm.sq.B;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t m0 = tile_m * SG64_BM;
@@ -198,6 +214,90 @@ __device__ __forceinline__ void sgemm_tile64(const LA& la, const LB& lb, int64_t
     if (kt + 1 < nk) gload((kt + 1) * SG64_BK);
 #pragma unroll
     for (int k = 0; k < SG64_BK; ++k) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w};
+      const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+    if (kt + 1 < nk) {
+      sstore();
+      __syncthreads();
+    }
+  }
+  double local = 0.0;
+  uint64_t coff[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int64_t n = n0 + tx * 4 + j;
+    coff[j] = n_contig ? (uint64_t)n : pdep64((uint64_t)n, mask_n);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t m = m0 + ty * 4 + i;
+    if (m >= M) continue;
+    const uint64_t roff = m_contig_shift >= 0 ? ((uint64_t)m << m_contig_shift) : pdep64((uint64_t)m, mask_m);
+    float part[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t n = n0 + tx * 4 + j;
+      part[j] = 0.f;
+      if (n >= N) continue;
+      const float v = acc[i][j] * alpha;
+      store_out(out, roff | coff[j], v, streaming);
+      part[j] = v;
+    }
+    local += (double)((part[0] + part[1]) + (part[2] + part[3]));
+  }
+  if (sum) {
+    for (int off = 16; off; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+    if ((tid & 31) == 0) atomicAdd(sum, local);
+  }
+}
+
+template <class LA, class LB>
+__device__ __forceinline__ void sgemm_tile_narrow(const LA& la, const LB& lb, int64_t M, int64_t N, int64_t K,
+                                                  float alpha, uint64_t mask_m, uint64_t mask_n, int m_contig_shift,
+                                                  int n_contig, float* __restrict__ out, double* __restrict__ sum,
+                                                  int streaming, int64_t tile_m, int64_t tile_n, Tile64Smem& sm) {
+  auto& As = sm.narrow.A;
+  auto& Bs = sm.narrow.B;
+  const int tid = threadIdx.x;
+  const int tx = tid & 3, ty = tid >> 2;
+  const int64_t m0 = tile_m * SGN_BM;
+  const int64_t n0 = tile_n * SGN_BN;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  const int64_t mr = m0 + tid;                       // the A row this thread stages
+  const int64_t nr = n0 + (tid >> 4), kb = tid & 15;   // the B element this thread stages
+  const typename LA::Row arow = la.row(mr < M ? mr : 0);
+  const typename LB::Row brow = lb.row(nr < N ? nr : 0);
+  float ra[SGN_BK], rb;
+  auto gload = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < SGN_BK; ++q) ra[q] = (mr < M && k0 + q < K) ? la.at(arow, k0 + q) : 0.f;
+    rb = (nr < N && k0 + kb < K) ? lb.at(brow, k0 + kb) : 0.f;
+  };
+  auto sstore = [&]() {
+#pragma unroll
+    for (int q = 0; q < SGN_BK; ++q) As[q][tid] = ra[q];
+    Bs[kb][tid >> 4] = rb;
+  };
+  const int64_t nk = (K + SGN_BK - 1) / SGN_BK;
+  gload(0);
+  sstore();
+  __syncthreads();
+  for (int64_t kt = 0; kt < nk; ++kt) {
+    if (kt + 1 < nk) gload((kt + 1) * SGN_BK);
+#pragma unroll
+    for (int k = 0; k < SGN_BK; ++k) {
       const float4 a = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
       const float4 b = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
       const float av[4] = {a.x, a.y, a.z, a.w};
