@@ -10,8 +10,9 @@
 // circuit, so the circuits fill the GPU together:
 //   merge (+ zero the bin totals)  ->  slice reduction (when sliced)  ->
 //   one phase per depth of the contraction plan (independent steps share a
-//   phase; 64 x 64 GEMM tiles whose operands are gathered on the fly, no
-//   staging copy)  ->  chunked top-T of each job's bins  ->  the level selection
+//   phase; 64 x 64 GEMM tiles, 256 x 16 for steps of at most 16 columns,
+//   whose operands are gathered on the fly, no staging copy)  ->  chunked
+//   top-T of each job's bins  ->  the level selection
 //   (each job's top T from its chunks' candidates, then Algorithm 1's list L
 //   truncated to T, written as the next level's job records).
 // Within a phase a CTA takes tasks (merge walkers, GEMM tiles, top-T chunks)
@@ -20,9 +21,10 @@
 // bin, the same selection order (bin totals are float64 atomics in both).
 //
 // Memory ordering: data written in one phase is read in a later one by other
-// CTAs, after a barrier whose arrival is preceded and whose exit is followed
-// by a device-scope fence; those reads use ld.global.cg (through L2), never
-// the non-coherent read-only path.  Every barrier wait is bounded: a CTA that
+// CTAs, after a barrier that each CTA enters with a device-scope release (its
+// arrival, after a block barrier) and leaves with a device-scope acquire;
+// those reads use ld.global.cg (through L2), never the non-coherent
+// read-only path.  Every barrier wait is bounded: a CTA that
 // waits too long records CUTQC_ETIMEOUT in the device status word and raises
 // an abort flag, and every CTA then returns.
 #include "internal.cuh"
