@@ -678,14 +678,18 @@ int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& op
   out->phase_kinds.clear();
   out->phase_fma.clear();
   for (size_t p = 0; p < n_phases; ++p) {
+    // ops with few tasks first (a level selection, a few long tiles): CTA i
+    // takes task i first, so they start at once and the many short tasks of
+    // the other ops fill in around them
+    std::vector<Op> ops_p;
+    for (auto& ph : phases)
+      if (p < ph.size()) ops_p.insert(ops_p.end(), ph[p].begin(), ph[p].end());
+    std::stable_sort(ops_p.begin(), ops_p.end(), [](const Op& x, const Op& y) { return x.ntasks < y.ntasks; });
     int64_t tasks = 0;
-    for (auto& ph : phases) {
-      if (p >= ph.size()) continue;
-      for (Op op : ph[p]) {
-        op.task0 = (int)tasks;
-        tasks += op.ntasks;
-        out->ops.push_back(op);
-      }
+    for (Op op : ops_p) {
+      op.task0 = (int)tasks;
+      tasks += op.ntasks;
+      out->ops.push_back(op);
     }
     if (tasks > 0x7fffffff) return set_error(CUTQC_EUNSUPPORTED, "too many tasks in one phase");
     int kinds = 0;
