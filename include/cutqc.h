@@ -356,6 +356,11 @@ typedef struct cutqc_dd_batch cutqc_dd_batch;
 
 int cutqc_dd_batch_workspace_size(int n_runs, const cutqc_dd_run_desc* runs,
                                   const cutqc_dd_batch_options* opt, size_t* bytes);
+/* The program's shape without building it on a device (host only: no device
+ * pointer is read): phases, ops and tasks summed over the phases (the merge
+ * tasks depend on the current device's SM count).                           */
+int cutqc_dd_batch_shape(int n_runs, const cutqc_dd_run_desc* runs, const cutqc_dd_batch_options* opt,
+                         int32_t* n_phases, int32_t* n_ops, int64_t* tasks);
 int cutqc_dd_batch_create(int n_runs, const cutqc_dd_run_desc* runs, const cutqc_dd_batch_options* opt,
                           void* ws_dev, size_t ws_bytes, cutqc_dd_batch** out);
 int cutqc_dd_batch_launch(const cutqc_dd_batch* batch, void* stream);

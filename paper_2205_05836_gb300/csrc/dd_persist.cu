@@ -763,6 +763,23 @@ extern "C" int cutqc_dd_batch_workspace_size(int n_runs, const cutqc_dd_run_desc
   return CUTQC_OK;
 }
 
+extern "C" int cutqc_dd_batch_shape(int n_runs, const cutqc_dd_run_desc* runs, const cutqc_dd_batch_options* opt,
+                                    int32_t* n_phases, int32_t* n_ops, int64_t* tasks) {
+  BatchOpts o;
+  int rc = read_opts(opt, &o);
+  if (rc) return rc;
+  Built b;
+  if ((rc = build_program(n_runs, runs, o, nullptr, &b))) return rc;
+  if (n_phases) *n_phases = (int32_t)b.phase_tasks.size();
+  if (n_ops) *n_ops = (int32_t)b.ops.size();
+  if (tasks) {
+    int64_t t = 0;
+    for (int x : b.phase_tasks) t += x;
+    *tasks = t;
+  }
+  return CUTQC_OK;
+}
+
 extern "C" int cutqc_dd_batch_create(int n_runs, const cutqc_dd_run_desc* runs, const cutqc_dd_batch_options* opt,
                                      void* ws_dev, size_t ws_bytes, cutqc_dd_batch** out) {
   if (!out) return set_error(CUTQC_EINVAL, "null handle");

@@ -385,6 +385,15 @@ def cutqc_dd_batch_workspace_size(runs, options=None):
     return n.value
 
 
+def cutqc_dd_batch_shape(runs, options=None):
+    """Phases, ops and total tasks of the batch program (host only)."""
+    descs, keep = _batch_descs(runs)
+    p, o, t = c_int32(0), c_int32(0), c_int64(0)
+    _check(lib().cutqc_dd_batch_shape(c_int(len(runs)), descs, _batch_opts(options), ctypes.byref(p), ctypes.byref(o),
+                                      ctypes.byref(t)))
+    return {"phases": p.value, "ops": o.value, "tasks": t.value}
+
+
 class DDBatch:
     """Handle of cutqc_dd_batch_create: the runs' program, written into `ws`
     (a device uint8 tensor this object keeps alive).  launch() enqueues the

@@ -166,3 +166,35 @@ def test_dd_batch_validation_without_gpu(built):
         with pytest.raises(cq.CutqcError) as e:
             cq.cutqc_dd_batch_workspace_size(runs, opt)
         assert e.value.code == code, (opt, cq.cutqc_last_error())
+
+
+def test_dd_batch_program_shape_without_gpu(built):
+    """The batch program's structure, counted by hand on a two-subcircuit
+    circuit (5 outputs, one cut, no merge split at these sizes): per level
+    one merge phase (the bin totals' zeroing and one merge per subcircuit),
+    one contraction phase (one step), the chunked top-T phase when T > 0 and
+    the selection phase; levels = min(R, ceil(n / M)), one when T = 0.  Runs
+    share phases (the phase count is the largest run's), ops add up."""
+    import torch
+    cq = built
+    a = _sub(3, out_local=[2], out_edge=[0], out_qubit=[0, 1])
+    b = _sub(3, in_local=[0], in_edge=[0], out_qubit=[2, 3, 4])
+    att = [torch.zeros(4, 4), torch.zeros(8, 4)]
+
+    def run(M, R, T):
+        return dict(subs=[a, b], attributed=att, n_qubits=5, M=M, R=R, T=T,
+                    jobs=torch.zeros(16 * ctypes.sizeof(cq.DDJob), dtype=torch.uint8),
+                    n_jobs=torch.zeros(1, dtype=torch.int32), bins=torch.zeros(256))
+    # T = 0: one level: merge, contraction, selection; ops: zero + 2 merges + step + selection
+    assert {k: v for k, v in cq.cutqc_dd_batch_shape([run(2, 3, 0)]).items() if k != "tasks"} == \
+        {"phases": 3, "ops": 5}
+    # T = 2, M = 2: 3 levels x (merge, contraction, top-T, selection); 6 ops per level
+    s = cq.cutqc_dd_batch_shape([run(2, 3, 2)])
+    assert (s["phases"], s["ops"]) == (12, 18)
+    # R caps the levels; M = 5 gives one level holding every qubit
+    assert cq.cutqc_dd_batch_shape([run(2, 2, 2)])["phases"] == 8
+    assert cq.cutqc_dd_batch_shape([run(5, 3, 2)])["phases"] == 4
+    # runs share phases, ops add up
+    both = cq.cutqc_dd_batch_shape([run(2, 3, 2), run(5, 3, 2)])
+    assert (both["phases"], both["ops"]) == (12, 18 + 6)
+    assert both["tasks"] == s["tasks"] + cq.cutqc_dd_batch_shape([run(5, 3, 2)])["tasks"]
