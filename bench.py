@@ -725,7 +725,14 @@ def dd_extras(dev, cq, M=16, R=6, T=4, reps=5, precision=0):
            "note": "all levels of the three circuits in one captured CUDA graph (one stream per circuit); "
                    "selection on the device"}
     if precision == 0:
-        res["persistent"] = dd_batch_extras(dev, cq, runs, M, R, T, tot_bins, reps)
+        # the headline DD rate is the persistent launch's when it reproduced
+        # the level launches' records and bins; both rates are kept
+        pers = dd_batch_extras(dev, cq, runs, M, R, T, tot_bins, reps)
+        res["persistent"] = pers
+        res["level_launches_bins_per_s"] = res["bins_per_s"]
+        if pers["matches_level_by_level"] and pers["device_status"] == 0:
+            res["bins_per_s"] = pers["bins_per_s"]
+            res["headline"] = "persistent launch"
     return res
 
 
