@@ -732,7 +732,11 @@ def dd_extras(dev, cq, M=16, R=6, T=4, reps=5, precision=0):
         res["level_launches_bins_per_s"] = res["bins_per_s"]
         if pers["matches_level_by_level"] and pers["device_status"] == 0:
             res["bins_per_s"] = pers["bins_per_s"]
+            res["ms"] = pers["ms"]
             res["headline"] = "persistent launch"
+            res["note"] = ("bins_per_s / ms: all levels of the three circuits in one persistent cooperative launch; "
+                           "graph_ms / level_launches_bins_per_s: the same runs as one captured CUDA graph of "
+                           "level launches (one stream per circuit); selection on the device in both")
     return res
 
 
