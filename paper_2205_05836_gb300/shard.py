@@ -152,3 +152,41 @@ def gpu_level_executor(cq, subs, attributed, n, M, T, stream=None):
             out.append(dict(bin_sum=bs[j], top=top, bins=bins[j]))
         return out
     return run
+
+
+# ------------------------------------------------- DD batches over ranks
+# Several circuits' runs are independent: each rank builds one persistent
+# batch (cutqc_dd_batch_*) over its share of the runs, with no collective on
+# the data path.  Shares are balanced by the runs' bin counts (longest first
+# to the least-loaded rank), the same on every rank.
+
+
+def dd_run_bins(n, M, R, T):
+    """Bins a breadth-first run reconstructs: level 0 one job, every later
+    level T jobs, 2^(active qubits) bins each; min(R, ceil(n / M)) levels
+    (one when T = 0)."""
+    depths = -(-n // M)
+    levels = min(R, depths) if T > 0 else 1
+    return sum((1 if lv == 0 else T) << (min(n, lv * M + M) - lv * M) for lv in range(levels))
+
+
+def assign_runs(work, world):
+    """Rank of each run: runs in decreasing work (index order for equal
+    work) each go to the rank with the least work so far (lowest rank for
+    equal loads)."""
+    if world < 1:
+        raise ValueError("bad world")
+    load = [0] * world
+    rank_of = [0] * len(work)
+    for i in sorted(range(len(work)), key=lambda i: (-work[i], i)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        rank_of[i] = r
+        load[r] += work[i]
+    return rank_of
+
+
+def my_runs(runs, world, rank):
+    """Indices of the runs (dicts with n_qubits, M, R, T) this rank builds
+    its batch from."""
+    work = [dd_run_bins(r["n_qubits"], r["M"], r["R"], r["T"]) for r in runs]
+    return [i for i, r in enumerate(assign_runs(work, world)) if r == rank]

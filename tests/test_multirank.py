@@ -161,3 +161,87 @@ def test_merge_level_candidates_order():
     assert merge_level_candidates(tops, 4) == [(1, 9), (0, 7), (1, 1), (0, 3)]
     assert merge_level_candidates(tops, 10)[-1] == (3, 0)
     assert merge_level_candidates([[], []], 3) == []
+
+
+def test_dd_run_bins_and_assignment():
+    """Bin counts of breadth-first runs (the bench's three DD circuits: 9/13/13
+    jobs of up to 2^16 bins) and the balanced, deterministic split of runs
+    over ranks: every run on exactly one rank, the largest load no more than
+    the largest run above the average."""
+    from paper_2205_05836_gb300.shard import assign_runs, dd_run_bins, my_runs
+    assert dd_run_bins(40, 16, 6, 4) == (1 << 16) + 4 * (1 << 16) + 4 * (1 << 8)
+    assert dd_run_bins(60, 16, 6, 4) == (1 << 16) + 2 * 4 * (1 << 16) + 4 * (1 << 12)   # 4 levels, the last 12 wide
+    assert dd_run_bins(60, 16, 6, 0) == 1 << 16
+    assert dd_run_bins(8, 4, 1, 2) == 1 << 4
+    work = [5, 1, 9, 9, 2, 7, 3]
+    for world in (1, 2, 3, 8):
+        ranks = assign_runs(work, world)
+        assert ranks == assign_runs(work, world)
+        loads = [sum(w for w, r in zip(work, ranks) if r == k) for k in range(world)]
+        assert sum(loads) == sum(work)
+        assert max(loads) <= sum(work) / world + max(work)
+    assert assign_runs([4, 4], 2) == [0, 1]
+    runs = [dict(n_qubits=n, M=16, R=6, T=4) for n in (40, 50, 60)]
+    shares = [my_runs(runs, 2, r) for r in range(2)]
+    assert sorted(shares[0] + shares[1]) == [0, 1, 2]
+
+
+def _batch_split_worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle import attribution, dd
+        from paper_2205_05836_gb300.shard import my_runs
+        from workloads import circuits as C
+        from workloads.cutting import search_cut
+        from workloads.simulate import simulate_variants
+        cuts = [search_cut(C.brickwall(10, 4, 11), 7, 2, restarts=4), search_cut(C.bv(12, 9), 5, 5, restarts=4),
+                search_cut(C.aqft(10, 2, max_dist=2), 5, 4, restarts=4)]
+        runs = [dict(n_qubits=c.circuit.n, M=4, R=6, T=2) for c in cuts]
+        out = {}
+        for i in my_runs(runs, world, rank):      # this rank's batch: the FP64 oracle stands in for its GPU
+            c = cuts[i]
+            A = [attribution.attribute(simulate_variants(s), s.w, s.in_local, s.out_local, s.in_edge, s.out_edge)
+                 for s in c.subcircuits]
+            recs = dd.run(A, [s.out_qubit for s in c.subcircuits], [s.edges for s in c.subcircuits], c.K,
+                          c.circuit.n, 4, 6, 2, strategy="bfs")
+            out[i] = [(sorted(r["zoom"].items()), float(r["bins"].sum())) for r in recs]
+        parts = [None] * world
+        dist.all_gather_object(parts, out)
+        if rank == 0:
+            q.put(parts)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_dd_batch_split():
+    """Three DD runs split over two gloo ranks by my_runs: each run is
+    computed by exactly one rank, and the gathered records equal the
+    single-process FP64 oracle runs."""
+    import torch.multiprocessing as mp
+    from oracle import attribution, dd
+    from workloads import circuits as C
+    from workloads.cutting import search_cut
+    from workloads.simulate import simulate_variants
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_batch_split_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=240)
+        assert p.exitcode == 0
+    parts = q.get(timeout=10)
+    assert not set(parts[0]) & set(parts[1]) and sorted(set(parts[0]) | set(parts[1])) == [0, 1, 2]
+    got = {**parts[0], **parts[1]}
+    cuts = [search_cut(C.brickwall(10, 4, 11), 7, 2, restarts=4), search_cut(C.bv(12, 9), 5, 5, restarts=4),
+            search_cut(C.aqft(10, 2, max_dist=2), 5, 4, restarts=4)]
+    for i, c in enumerate(cuts):
+        A = [attribution.attribute(simulate_variants(s), s.w, s.in_local, s.out_local, s.in_edge, s.out_edge)
+             for s in c.subcircuits]
+        ref = dd.run(A, [s.out_qubit for s in c.subcircuits], [s.edges for s in c.subcircuits], c.K, c.circuit.n,
+                     4, 6, 2, strategy="bfs")
+        assert got[i] == [(sorted(r["zoom"].items()), float(r["bins"].sum())) for r in ref]
