@@ -284,7 +284,7 @@ __device__ __forceinline__ void select_task(const SelectOp& s) {
                        s.n_next, s.n_jobs_dev);
 }
 
-__device__ __forceinline__ void run_task(const Op& op, int t, Tile64Smem& tsm) {
+__device__ __forceinline__ void run_task(const Op& op, int t, TileSmem& tsm) {
   switch (op.type) {
     case OP_ZERO: {
       const ZeroOp& z = op.u.zero;
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) dd_persistent_kernel(con
   // memory (the program is read-only for the launch)
   __shared__ Op sop;
   __shared__ int s_task0[kPhaseOpsCached];
-  __shared__ Tile64Smem tsm;
+  __shared__ TileSmem tsm;
   const bool tracer = blockIdx.x == 0 && threadIdx.x == 0;
   if (tracer) pg.trace[0] = clock64();
   for (int p = 0; p < pg.n_phases; ++p) {

@@ -157,7 +157,7 @@ constexpr int SGN_BM = 256, SGN_BN = 16, SGN_BK = 16;
 // The tiles' staging arrays (one per block, shared by every instantiation).
 // Row pitch 72 in the 64 x 64 tile: the stores of a warp (8 rows x 4 k
 // columns) hit 32 banks.
-struct Tile64Smem {
+struct TileSmem {
   union {
     struct {
       __align__(16) float A[SG64_BK][SG64_BM + 8];
@@ -174,7 +174,7 @@ template <class LA, class LB>
 __device__ __forceinline__ void sgemm_tile64(const LA& la, const LB& lb, int64_t M, int64_t N, int64_t K,
                                              float alpha, uint64_t mask_m, uint64_t mask_n, int m_contig_shift,
                                              int n_contig, float* __restrict__ out, double* __restrict__ sum,
-                                             int streaming, int64_t tile_m, int64_t tile_n, Tile64Smem& sm) {
+                                             int streaming, int64_t tile_m, int64_t tile_n, TileSmem& sm) {
   auto& As = sm.sq.A;
   auto& Bs = sm.sq.B;
   const int tid = threadIdx.x;
@@ -263,7 +263,7 @@ template <class LA, class LB>
 __device__ __forceinline__ void sgemm_tile_narrow(const LA& la, const LB& lb, int64_t M, int64_t N, int64_t K,
                                                   float alpha, uint64_t mask_m, uint64_t mask_n, int m_contig_shift,
                                                   int n_contig, float* __restrict__ out, double* __restrict__ sum,
-                                                  int streaming, int64_t tile_m, int64_t tile_n, Tile64Smem& sm) {
+                                                  int streaming, int64_t tile_m, int64_t tile_n, TileSmem& sm) {
   auto& As = sm.narrow.A;
   auto& Bs = sm.narrow.B;
   const int tid = threadIdx.x;
