@@ -198,3 +198,21 @@ def test_dd_batch_program_shape_without_gpu(built):
     both = cq.cutqc_dd_batch_shape([run(2, 3, 2), run(5, 3, 2)])
     assert (both["phases"], both["ops"]) == (12, 18 + 6)
     assert both["tasks"] == s["tasks"] + cq.cutqc_dd_batch_shape([run(5, 3, 2)])["tasks"]
+
+
+def test_dd_batch_many_runs_shape(built):
+    """Sixty runs in one program (phases with more than 256 ops, beyond the
+    kernel's shared-memory op table): the builder's counts still add up."""
+    import torch
+    cq = built
+    a = _sub(3, out_local=[2], out_edge=[0], out_qubit=[0, 1])
+    b = _sub(3, in_local=[0], in_edge=[0], out_qubit=[2, 3, 4])
+    att = [torch.zeros(4, 4), torch.zeros(8, 4)]
+    run = dict(subs=[a, b], attributed=att, n_qubits=5, M=2, R=3, T=2,
+               jobs=torch.zeros(16 * ctypes.sizeof(cq.DDJob), dtype=torch.uint8),
+               n_jobs=torch.zeros(1, dtype=torch.int32), bins=torch.zeros(256))
+    one = cq.cutqc_dd_batch_shape([run])
+    many = cq.cutqc_dd_batch_shape([run] * 60)
+    assert many["phases"] == one["phases"] == 12
+    assert many["ops"] == 60 * one["ops"] and many["tasks"] == 60 * one["tasks"]
+    assert cq.cutqc_dd_batch_workspace_size([run] * 60) > 60 * cq.cutqc_dd_batch_workspace_size([run]) // 2
