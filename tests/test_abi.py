@@ -201,7 +201,7 @@ def test_dd_batch_program_shape_without_gpu(built):
 
 
 def test_dd_batch_many_runs_shape(built):
-    """Sixty runs in one program (phases with more than 256 ops, beyond the
+    """Ninety runs in one program (a merge phase of 270 ops, beyond the
     kernel's shared-memory op table): the builder's counts still add up."""
     import torch
     cq = built
@@ -212,7 +212,7 @@ def test_dd_batch_many_runs_shape(built):
                jobs=torch.zeros(16 * ctypes.sizeof(cq.DDJob), dtype=torch.uint8),
                n_jobs=torch.zeros(1, dtype=torch.int32), bins=torch.zeros(256))
     one = cq.cutqc_dd_batch_shape([run])
-    many = cq.cutqc_dd_batch_shape([run] * 60)
+    many = cq.cutqc_dd_batch_shape([run] * 90)
     assert many["phases"] == one["phases"] == 12
-    assert many["ops"] == 60 * one["ops"] and many["tasks"] == 60 * one["tasks"]
-    assert cq.cutqc_dd_batch_workspace_size([run] * 60) > 60 * cq.cutqc_dd_batch_workspace_size([run]) // 2
+    assert many["ops"] == 90 * one["ops"] and many["tasks"] == 90 * one["tasks"]
+    assert cq.cutqc_dd_batch_workspace_size([run] * 90) > 90 * cq.cutqc_dd_batch_workspace_size([run]) // 2
