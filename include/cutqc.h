@@ -140,7 +140,8 @@ int cutqc_attribute(const cutqc_subcircuit* s, const void* variants_dev, int var
  * allocation's implicit synchronisation is not allowed): same inputs, outputs
  * and results as cutqc_attribute, but the scratch of the two-pass case comes
  * from a static 32 MiB device array of the library (held on every GPU that
- * loads it until the process exits).  The first call on a device looks up
+ * loads it until the process exits).  The first call on a device that needs
+ * scratch (a subcircuit with both initialised and measured cuts) looks up
  * that array's address with that device current; make it before any stream
  * capture.  Calls share the array and it keeps the last call's contents:
  * calls that can overlap on the GPU race and must be ordered by the caller.
@@ -169,6 +170,14 @@ int cutqc_attribute_noalloc(const cutqc_subcircuit* s, const void* variants_dev,
  * order), CUTQC_ENOMEM (workspace), CUTQC_EUNSUPPORTED (limits),
  * CUTQC_ETIMEOUT is reported later through cutqc_device_status().         */
 int cutqc_fd_shape(int n_sub, const cutqc_subcircuit* s, int64_t* rows, int64_t* cols);
+/* Kernel timing (no paper counterpart): the next cutqc_reconstruct_fd made
+ * by the calling thread records start_event just before its last
+ * contraction's GEMM launch and stop_event just after it, on the stream that
+ * launch uses (the caller's), then forgets both; cudaEventElapsedTime gives
+ * that kernel's duration.  Events are cudaEvent_t (created with timing) owned
+ * by the caller; null, null cancels.  Errors: CUTQC_EINVAL if only one event
+ * is given.                                                                 */
+int cutqc_fd_timing_events(void* start_event, void* stop_event);
 int cutqc_reconstruct_fd_workspace_size(int n_sub, const cutqc_subcircuit* s, int precision,
                                         size_t* bytes);
 int cutqc_reconstruct_fd(int n_sub, const cutqc_subcircuit* s, const float* const* attributed_dev,

@@ -131,6 +131,32 @@ def entries(attributed, edge_lists, K, parts, chunk=4096):
     return out * 0.5 ** K
 
 
+def contract_pair(A_i, edges_i, A_j, edges_j):
+    """Eq. 1's sum over the cut edges that subcircuits i and j share, taken
+    for every pair of their outputs at once (the distributive law applied to
+    those edges only; the 2^-K factor is left to the caller).  A_i, A_j are
+    attributed tensors ([2^o][4^k], column = sum_t d_t 4^t over the edges in
+    ascending order).  Returns (T, open_edges): T is [2^(o_i + o_j)][4^m] in
+    the same layout, row = x_i * 2^o_j + x_j (Kronecker order, i first),
+    columns over the m edges that touch exactly one of the two, ascending.
+    A library einsum (a tensor contraction) is the step; nothing else is
+    rewritten.  Treated as one subcircuit, T gives the same entries as the
+    pair it replaces."""
+    shared = set(edges_i) & set(edges_j)
+    open_edges = sorted(set(edges_i) ^ set(edges_j))
+    labels = sorted(set(edges_i) | set(edges_j))
+    letter = {e: chr(ord("a") + t) for t, e in enumerate(labels)}
+    ti = A_i.reshape((A_i.shape[0],) + (4,) * len(edges_i))
+    tj = A_j.reshape((A_j.shape[0],) + (4,) * len(edges_j))
+    # axes after the row axis: the highest digit first (edges descending)
+    spec_i = "Y" + "".join(letter[e] for e in reversed(edges_i))
+    spec_j = "Z" + "".join(letter[e] for e in reversed(edges_j))
+    spec_o = "YZ" + "".join(letter[e] for e in reversed(open_edges))
+    assert all(letter[e] not in "YZ" for e in labels) and len(shared) + len(open_edges) == len(labels)
+    t = np.einsum(f"{spec_i},{spec_j}->{spec_o}", ti, tj, optimize=True)
+    return t.reshape(A_i.shape[0] * A_j.shape[0], 4 ** len(open_edges)), open_edges
+
+
 def total_probability(attributed, edge_lists, K):
     """sum_x P(x) = 2^-K sum_e prod_i (sum_x A_i[x, c_i(e)]) (each Kronecker
     term sums to the product of its factors' sums)."""

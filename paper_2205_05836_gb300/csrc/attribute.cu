@@ -482,8 +482,9 @@ extern "C" int cutqc_attribute(const cutqc_subcircuit* s, const void* variants_d
 // The array is kNoAllocScratchBytes (32 MiB) of device memory on every GPU
 // that loads this library, held until the process exits.  Its device
 // address is looked up once per device (cudaGetSymbolAddress) on the first
-// call made with that device current, so that first call should come before
-// any stream capture.  All calls share the one array and it keeps whatever
+// call that needs scratch (a subcircuit with both kinds of cut) made with
+// that device current, so that first call should come before any stream
+// capture.  All calls share the one array and it keeps whatever
 // the last call left there: calls that may overlap on the GPU (different
 // streams, no ordering between them) race on it and must not be issued that
 // way.  Nothing in it needs to start at zero: the pass that writes it covers
@@ -528,8 +529,9 @@ extern "C" int cutqc_attribute_noalloc(const cutqc_subcircuit* s, const void* va
                      "this subcircuit needs %zu bytes of scratch; the no-allocation variant has %zu "
                      "(use cutqc_attribute with a workspace)",
                      need, kNoAllocScratchBytes);
+  // subcircuits with one kind of cut need no scratch: no symbol lookup then
   void* scratch = nullptr;
-  if ((rc = noalloc_scratch(&scratch))) return rc;
+  if (need > 0 && (rc = noalloc_scratch(&scratch))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   if (dtype == CUTQC_F64)
     return launch_attr<double>(s, (const double*)variants_dev, attributed_dev, (float*)scratch, st);

@@ -516,7 +516,9 @@ int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& op
         MergeOp& mo = m.u.merge;
         mo.att = R.attributed_dev[i];
         mo.out = part;
-        mo.zj.jobs = R.jobs_dev + job0;
+        // level 0 zooms nothing: its merges read no job record (the record
+        // they would read is written by this phase's zero op), zoom value 0
+        mo.zj.jobs = level == 0 ? nullptr : R.jobs_dev + job0;
         mo.zj.o = o;
         mo.zj.lo = level * R.M;
         for (int t = 0; t < o; ++t) mo.zj.outq[t] = (int8_t)s[i].out_qubit[t];

@@ -29,6 +29,10 @@ namespace cutqc {
 
 static thread_local std::string g_last_error;
 
+// Events that the next reconstruction on this thread records around its last
+// contraction's GEMM launch (then clears): see cutqc_fd_timing_events.
+static thread_local cudaEvent_t g_gemm_start = nullptr, g_gemm_stop = nullptr;
+
 int set_error(int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -370,9 +374,15 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
                               bh, bl, bs, st, 1, 0, reinterpret_cast<unsigned int*>(bs + 1), cols, meta);
         if (rc) return rc;
         TcOperand ta{ah, al, as, M}, tb{bh, bl, bs, stg.N};
+        const bool timed = stg.final_stage && g_gemm_start && b == 0;
+        if (timed) CUTQC_CUDA_TRY(cudaEventRecord(g_gemm_start, st));
         rc = launch_tc_gemm(ta, tb, stg.Kp, alpha, stg.mask_m, stg.mask_n, dst + b * dst_b,
                             sum_ptr ? sum_ptr + b : nullptr, streaming, st, prune ? meta + 1 : nullptr);
         if (rc) return rc;
+        if (stg.final_stage && g_gemm_start && b == batch - 1) {
+          CUTQC_CUDA_TRY(cudaEventRecord(g_gemm_stop, st));
+          g_gemm_start = g_gemm_stop = nullptr;
+        }
       }
       return CUTQC_OK;
     }
@@ -405,9 +415,15 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
       ldb = stg.Kp;
       b_b = stg.N * stg.Kp;
     }
+    const bool timed = stg.final_stage && g_gemm_start;
+    if (timed) CUTQC_CUDA_TRY(cudaEventRecord(g_gemm_start, st));
     rc = launch_sgemm(A, lda, B, ldb, M, stg.N, stg.K, alpha, stg.mask_m, stg.mask_n, dst, sum_ptr, streaming, st,
                       batch, a_b, b_b, dst_b);
     if (rc) return rc;
+    if (timed) {
+      CUTQC_CUDA_TRY(cudaEventRecord(g_gemm_stop, st));
+      g_gemm_start = g_gemm_stop = nullptr;
+    }
     return CUTQC_OK;
   };
   // A step that does not read the previous step's result can run beside it:
@@ -529,6 +545,14 @@ extern "C" int cutqc_device_status(int32_t* status_out) {
   CUTQC_CUDA_TRY(cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost));
   CUTQC_CUDA_TRY(cudaMemset(p, 0, sizeof(int)));
   *status_out = v;
+  return CUTQC_OK;
+}
+
+extern "C" int cutqc_fd_timing_events(void* start_event, void* stop_event) {
+  if ((start_event == nullptr) != (stop_event == nullptr))
+    return set_error(CUTQC_EINVAL, "give both events or neither");
+  g_gemm_start = (cudaEvent_t)start_event;
+  g_gemm_stop = (cudaEvent_t)stop_event;
   return CUTQC_OK;
 }
 

@@ -158,6 +158,15 @@ def cutqc_attribute_noalloc(sub, variants, out, stream=None):
     output tensor; the library's static scratch array is used."""
     import torch
     d, keep = make_sub(sub)
+    kin, kout = len(sub.in_local), len(sub.out_local)
+    shape = (1 << (int(sub.w) - kout), 4 ** (kin + kout))
+    if variants.dtype not in (torch.float64, torch.float32):
+        raise TypeError("variants must be float64 or float32")
+    if not variants.is_contiguous() or variants.numel() != 4 ** kin * 3 ** kout * (1 << int(sub.w)):
+        raise ValueError("variants must be a contiguous [4^k_in, 3^k_out, 2^w] tensor")
+    if (out.dtype != torch.float32 or not out.is_contiguous() or out.device != variants.device
+            or tuple(out.shape) != shape):
+        raise ValueError(f"out must be a contiguous float32 tensor of shape {shape} on {variants.device}")
     dtype = F64 if variants.dtype == torch.float64 else F32
     _check(lib().cutqc_attribute_noalloc(ctypes.byref(d), _ptr(variants), c_int(dtype), _ptr(out), _stream(stream)))
     return out
@@ -170,6 +179,19 @@ def cutqc_fd_shape(subs):
     r, c = c_int64(0), c_int64(0)
     _check(lib().cutqc_fd_shape(c_int(len(subs)), arr, ctypes.byref(r), ctypes.byref(c)))
     return r.value, c.value
+
+
+def cutqc_fd_timing_events(start=None, stop=None):
+    """The next cutqc_reconstruct_fd on this thread records the two
+    torch.cuda.Event objects (created with enable_timing=True) around its
+    last contraction's GEMM launch; None, None cancels."""
+    if start is None and stop is None:
+        _check(lib().cutqc_fd_timing_events(None, None))
+        return
+    for e in (start, stop):
+        if not e.cuda_event:          # torch creates the CUDA event on first record
+            e.record()
+    _check(lib().cutqc_fd_timing_events(c_void_p(start.cuda_event), c_void_p(stop.cuda_event)))
 
 
 def cutqc_reconstruct_fd_workspace_size(subs, precision):

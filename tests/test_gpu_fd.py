@@ -216,9 +216,12 @@ def test_fd_two_subcircuit_30q_full_size(cq):
 def test_fd_chain_32q_full_size(cq):
     """32-qubit AQFT chain (4 subcircuits, K = 12, 2^32 outputs = 16 GiB) on
     the tensor-core path, with and without cut-term pruning, in both output
-    orders: sum p against 1, and 2^14 seeded uniformly sampled outputs
-    against the FP64 oracle (max error, and the total variation they
-    estimate)."""
+    orders: sum p against 1, and 2^20 seeded uniformly sampled outputs (the
+    sample size the 32-qubit configuration states) against the FP64 oracle
+    (max error, and the total variation they estimate).  The oracle sums the
+    edges inside the pairs (C0, C1) and (C2, C3) for all their outputs first
+    (fd.contract_pair), then Eq. 1 over the four edges between the pairs at
+    each sampled output."""
     import torch
     from oracle import fd
     from workloads.configs import fd_chain
@@ -227,9 +230,11 @@ def test_fd_chain_32q_full_size(cq):
     var = w.variants()
     A64 = _oracle_att(subs, var)
     att = _gpu_att(cq, subs, var)
-    edges = [s.edges for s in subs]
+    L, eL = fd.contract_pair(A64[0], subs[0].edges, A64[1], subs[1].edges)
+    R, eR = fd.contract_pair(A64[2], subs[2].edges, A64[3], subs[3].edges)
     rng = np.random.default_rng(2024)
-    idx = np.unique(rng.integers(0, 1 << w.n, size=1 << 14))
+    idx = np.unique(rng.integers(0, 1 << w.n, size=1 << 20))
+    assert len(idx) > (1 << 20) - 1000
     for order, precision in ((0, 1), (1, 1), (0, 2), (1, 2)):
         total = torch.zeros(1, dtype=torch.float64, device="cuda")
         out, _ = cq.cutqc_reconstruct_fd(subs, att, order, precision, sum_out=total)
@@ -241,7 +246,8 @@ def test_fd_chain_32q_full_size(cq):
         torch.cuda.empty_cache()
         parts = fd.split_kron_index(idx, [s.o for s in subs]) if order == 0 else \
             fd.split_original_index(idx, [s.out_qubit for s in subs])
-        ref = fd.entries(A64, edges, w.K, parts)
+        pairs = [(parts[0] << subs[1].o) | parts[1], (parts[2] << subs[3].o) | parts[3]]
+        ref = fd.entries([L, R], [eL, eR], w.K, pairs)
         err = np.abs(got - ref)
         assert err.max() <= 1e-6, err.max()
         tv_est = 0.5 * (1 << w.n) * err.mean()

@@ -86,6 +86,17 @@ def test_adam_matches_oracle(cq):
     got = net.p.cpu().numpy().astype(np.float64)
     assert np.abs(got - p[0]).max() <= 1e-6 * max(1.0, np.abs(p[0]).max())
     assert torch.equal(net.pb.cpu(), net.p.cpu().to(torch.bfloat16))
+    # the moments after three steps (their history and beta2 matter here,
+    # which the parameters' float32 rounding could hide): float32 relative
+    gm = net.m.cpu().numpy().astype(np.float64)
+    gv = net.v.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(gm - m[0]) <= 1e-6 * np.abs(m[0]) + 1e-30)
+    assert np.all(np.abs(gv - v[0]) <= 1e-6 * np.abs(v[0]) + 1e-30)
+    # and the total update of three steps, per parameter, against the
+    # oracle's: float32 rounding of p (~6e-8 relative) against steps of ~1e-3
+    upd_ref = p[0] - flat.astype(np.float64)
+    upd = got - flat.astype(np.float64)
+    assert np.abs(upd - upd_ref).max() <= 1e-3 * np.abs(upd_ref).max()
 
 
 @pytest.fixture(scope="module")

@@ -163,6 +163,53 @@ def test_fd_matches_bruteforce(name, c, w, nsub):
     np.testing.assert_allclose(fd.entries(A, edges, cut.K, parts), exact[idx], atol=1e-13)
 
 
+@pytest.mark.parametrize("name,c,w,nsub", [x for x in _cases() if x[3] >= 3])
+def test_contract_pair_entries_match_bruteforce(name, c, w, nsub):
+    """Summing a pair's shared edges for all their outputs first
+    (fd.contract_pair), then evaluating Eq. 1 over the remaining edges at
+    every output, gives the uncut circuit's exact distribution; every pair of
+    subcircuits is tried, sharing edges or not."""
+    cut = search_cut(c, w, nsub, restarts=4)
+    subs = cut.subcircuits
+    A = _attr(subs, [simulate_variants(s) for s in subs])
+    exact = statevector.probabilities(c)
+    idx = np.arange(2 ** c.n)
+    kparts = fd.split_kron_index(idx, [s.o for s in subs])
+    # perm[original index] = Kronecker index
+    perm = fd.kron_to_original(idx.astype(np.float64), [s.out_qubit for s in subs]).astype(np.int64)
+    exact_kron = np.empty_like(exact)
+    exact_kron[perm] = exact            # exact distribution in Kronecker order
+    for i in range(len(subs)):
+        j = i + 1
+        if j >= len(subs):
+            break
+        T, open_e = fd.contract_pair(A[i], subs[i].edges, A[j], subs[j].edges)
+        assert T.shape == (2 ** (subs[i].o + subs[j].o), 4 ** len(open_e))
+        tensors = A[:i] + [T] + A[j + 1:]
+        edges = [s.edges for s in subs[:i]] + [open_e] + [s.edges for s in subs[j + 1:]]
+        parts = kparts[:i] + [(kparts[i] << subs[j].o) | kparts[j]] + kparts[j + 1:]
+        got = fd.entries(tensors, edges, cut.K, parts)
+        assert np.abs(got - exact_kron).max() < 1e-12, (name, i)
+
+
+def test_contract_pair_hand_values():
+    """Two one-output subcircuits sharing one edge and keeping one open edge
+    each: T[x_i x_j, (d_a, d_b)] = sum_s A_i[x_i, d_a + 4 s] A_j[x_j, s + 4 d_b]
+    written out for every entry (edges: i = {0 open, 1 shared}, j = {1 shared,
+    2 open})."""
+    rng = np.random.default_rng(3)
+    Ai = rng.normal(size=(2, 16))
+    Aj = rng.normal(size=(2, 16))
+    T, open_e = fd.contract_pair(Ai, [0, 1], Aj, [1, 2])
+    assert open_e == [0, 2] and T.shape == (4, 16)
+    for xi in range(2):
+        for xj in range(2):
+            for da in range(4):
+                for db in range(4):
+                    want = sum(Ai[xi, da + 4 * sh] * Aj[xj, sh + 4 * db] for sh in range(4))
+                    assert abs(T[xi * 2 + xj, da + 4 * db] - want) < 1e-12
+
+
 def test_kron_order_is_numpy_kron():
     """'kron' order = np.kron of the per-subcircuit vectors for one term."""
     a0 = np.array([1.0, 2.0])[:, None]
@@ -296,6 +343,53 @@ def test_adam_first_step_is_signed_lr():
     z = [np.zeros(2)]
     p2, _, _ = omlp.adam_step(p, g, z, z, 1, lr=0.1)
     np.testing.assert_allclose(p2[0], [0.9, -1.9], atol=1e-7)
+
+
+def test_adam_three_steps_against_hand_derivation():
+    """Three Adam steps (Kingma & Ba, bias-corrected; beta1 = 0.9, beta2 =
+    0.999, eps = 1e-8, lr = 0.1), worked out by hand with exact fractions, so
+    that beta2, the bias corrections and the moments carried between steps
+    all matter.
+
+    Element 0, gradients 1, -2, 0 from p = 1:
+      step 1: m = 1/10,  v = 1/1000;          m^ = 1,       v^ = 1
+              p = 1 - 0.1 / (1 + 1e-8)                      = 0.90000000099999999
+      step 2: m = 0.09 - 0.2 = -11/100, v = 0.000999 + 0.004 = 4999/10^6
+              m^ = (-11/100) / (1 - 0.81) = -11/19
+              v^ = (4999/10^6) / (1 - 0.998001) = 4999/1999
+              p -= 0.1 m^ / (sqrt(v^) + 1e-8)               = 0.93661035347207509
+      step 3: m = 0.9 (-11/100) = -99/1000, v = 0.999 * 4999/10^6 = 4994001/10^9
+              m^ = (-99/1000) / (1 - 0.729) = -99/271
+              v^ = (4994001/10^9) / (1 - 0.997002999) = 4994001/2997001
+              p -= 0.1 m^ / (sqrt(v^) + 1e-8)               = 0.96491026200093055
+    (the zero gradient of step 3 still moves p: only the moments' history does.)
+    Element 1, constant gradient 0.5 from p = -2: m^ = 0.5 and v^ = 0.25 at
+    every step, so each step subtracts 0.1 * 0.5 / (0.5 + 1e-8)."""
+    p = [np.array([1.0, -2.0])]
+    m = [np.zeros(2)]
+    v = [np.zeros(2)]
+    for step, g in enumerate(([1.0, 0.5], [-2.0, 0.5], [0.0, 0.5]), start=1):
+        p, m, v = omlp.adam_step(p, [np.array(g)], m, v, step, lr=0.1)
+    np.testing.assert_allclose(m[0], [-99 / 1000, 0.5 * (1 - 0.9 ** 3)], rtol=1e-14)
+    np.testing.assert_allclose(v[0], [4994001 / 10 ** 9, 0.25 * (1 - 0.999 ** 3)], rtol=1e-14)
+    np.testing.assert_allclose(p[0], [0.96491026200093055, -2.299999994000000120], rtol=1e-14)
+
+
+def test_adam_wrong_beta2_or_history_is_caught():
+    """Planted mistakes in the update fail the three-step pin above: a
+    different beta2, or moments restarted every step."""
+    want = 0.96491026200093055
+
+    def run(beta2=0.999, carry=True):
+        p, m, v = [np.array([1.0])], [np.zeros(1)], [np.zeros(1)]
+        for step, g in enumerate((1.0, -2.0, 0.0), start=1):
+            p, m2, v2 = omlp.adam_step(p, [np.array([g])], m, v, step, lr=0.1, beta2=beta2)
+            if carry:
+                m, v = m2, v2
+        return float(p[0][0])
+    assert abs(run() - want) < 1e-12
+    assert abs(run(beta2=0.99) - want) > 1e-5
+    assert abs(run(carry=False) - want) > 1e-4
 
 
 # ------------------------------------------------------------ planted mistakes
