@@ -1,11 +1,19 @@
-"""Benchmark: full-definition reconstruction of the 30-qubit two-subcircuit
-workload (supremacy-family 5x6 grid, depth 10, K = 4 cuts, subcircuits of 17
-and 17 qubits, 2^30 outputs) on GB300.
+"""Benchmark: full-definition reconstruction of the 32-qubit chain workload
+(approximate QFT with controlled phases up to qubit distance 4 and Ry input
+angles, cut into 4 subcircuits of 11 qubits by K = 12 wire cuts, 4 per
+boundary) on GB300: 2^32 float32 probabilities (16 GiB) per step.
 
-One step = attribution of both subcircuits' variant tensors (float64, resident
-in HBM) + the tensor-core FD contraction (FP16 hi/lo split, three products)
-writing all 2^30 float32 probabilities, with the FP64 total.  The 4 GiB output
-is larger than L2, so no flush is needed between steps.
+One step = attribution of the four subcircuits' variant tensors (float64,
+resident in HBM) + the pairwise contraction chain of Eq. 1 on the
+split-precision tensor-core path (FP16 hi/lo operands, three products, every
+cut term evaluated), with the FP64 total.  The 16 GiB output is larger than
+L2, so no flush is needed between steps.  The line carries the total
+variation against the FP64 oracle on 2^20 sampled outputs of the timed
+result.
+
+With N > 1 ranks (torchrun), one reconstruction is split by rows of its last
+contraction (the high output bits): each rank writes its 1/N of the output,
+with no data exchange; the FP64 totals are summed over the ranks.
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
 """
@@ -26,7 +34,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "reconstructed probs/sec (FD) and DD bins/sec at 1 GB300, TV<=1e-6; % of roofline"
-WORKLOAD = "fd_two_sub_supremacy30: 5x6 supremacy-family depth 10, K=4, subcircuits 17+17 -> 2^30 probabilities"
+WORKLOAD = ("fd_chain_aqft32: 32-qubit AQFT (controlled phases to qubit distance 4, input Ry), 4 subcircuits "
+            "of 11 qubits in a chain, K=12 (4 cuts per boundary) -> 2^32 probabilities, every cut term")
+TWO_SUB_WORKLOAD = ("fd_two_sub_supremacy30_bridged: 5x6 supremacy-family depth 10 with the couplers across "
+                    "one split bridged, K=4, subcircuits 17+17 -> 2^30 probabilities")
 
 
 _T0 = time.perf_counter()
@@ -232,32 +243,55 @@ def profiled_traffic(kernel_src, summary):
     return int(t.group(1))
 
 
-def cpu_baseline(w, budget_s=15.0):
-    """FP64 oracle as it stands on the host: attribution of both subcircuits
-    (full) then Eq. 1 at a contiguous sample of outputs; the attribution time
-    is prorated to the sample."""
-    from oracle import attribution, fd
-    subs = w.subcircuits
-    var = w.variants()
-    t0 = time.perf_counter()
-    A = [attribution.attribute(v, s.w, s.in_local, s.out_local, s.in_edge, s.out_edge) for s, v in zip(subs, var)]
-    t_attr = time.perf_counter() - t0
-    edges = [s.edges for s in subs]
-    outs = [s.o for s in subs]
-    n_total = 2 ** w.n
-    S = 1 << 14
+class ChainOracle:
+    """FP64 oracle data for the 32-qubit chain, computed once: attribution of
+    the four subcircuits, then the edges inside the pairs (C0, C1) and (C2,
+    C3) summed for all their outputs (oracle.fd.contract_pair); an output is
+    then Eq. 1 over the four edges between the pairs (oracle.fd.entries).
+    Timings of each part are kept for the CPU baseline."""
+
+    def __init__(self, w):
+        from oracle import attribution, fd
+        self.w = w
+        subs = w.subcircuits
+        var = w.variants()
+        t0 = time.perf_counter()
+        self.A = [attribution.attribute(v, s.w, s.in_local, s.out_local, s.in_edge, s.out_edge)
+                  for s, v in zip(subs, var)]
+        t1 = time.perf_counter()
+        self.L, self.eL = fd.contract_pair(self.A[0], subs[0].edges, self.A[1], subs[1].edges)
+        self.R, self.eR = fd.contract_pair(self.A[2], subs[2].edges, self.A[3], subs[3].edges)
+        t2 = time.perf_counter()
+        self.t_attr, self.t_pairs = t1 - t0, t2 - t1
+
+    def entries(self, idx, order_kron=True):
+        from oracle import fd
+        subs = self.w.subcircuits
+        parts = fd.split_kron_index(idx, [s.o for s in subs]) if order_kron else \
+            fd.split_original_index(idx, [s.out_qubit for s in subs])
+        pairs = [(parts[0] << subs[1].o) | parts[1], (parts[2] << subs[3].o) | parts[3]]
+        return fd.entries([self.L, self.R], [self.eL, self.eR], self.w.K, pairs)
+
+
+def cpu_baseline(oracle, budget_s=15.0, chunk=1 << 16):
+    """The FP64 oracle as it stands on the host cores for the whole-job rate:
+    attribution and the two pair sums (full, prorated over the 2^32 outputs)
+    plus Eq. 1 at contiguous outputs until the budget is spent."""
+    n_total = 2 ** oracle.w.n
     done, t_rec = 0, 0.0
     while t_rec < budget_s and done < n_total:
-        idx = np.arange(done, min(done + S, n_total), dtype=np.int64)
-        parts = fd.split_kron_index(idx, outs)
+        idx = np.arange(done, min(done + chunk, n_total), dtype=np.int64)
         t1 = time.perf_counter()
-        fd.entries(A, edges, w.K, parts)
+        oracle.entries(idx)
         t_rec += time.perf_counter() - t1
         done += len(idx)
-    t = t_rec + t_attr * done / n_total
+    t_setup = oracle.t_attr + oracle.t_pairs
+    t = t_rec + t_setup * done / n_total
     return dict(value=done / t, unit="probs/s", cores=_threads(), kind="oracle",
-                sample=f"FP64 oracle: attribution of both subcircuits (full, {t_attr:.1f} s, prorated) + "
-                       f"Eq. 1 at the first {done} outputs in Kronecker order ({t_rec:.1f} s)")
+                sample=f"FP64 oracle on the 32-qubit chain: attribution of the four subcircuits and the edge sums "
+                       f"inside the pairs (C0,C1), (C2,C3) (full, {t_setup:.1f} s, prorated over 2^32 outputs) + "
+                       f"Eq. 1 over the 4 middle edges at the first {done} outputs in Kronecker order "
+                       f"({t_rec:.1f} s)")
 
 
 def _threads():
@@ -270,26 +304,57 @@ def _threads():
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, same workload and
+    metric; each step a bounded sample of Eq. 1 at contiguous outputs (the
+    attribution and pair sums, done once, are prorated into every step)."""
     ws, rank, _ = dist_setup()
     if rank != 0:
         return
-    from workloads.configs import fd_two_sub
-    w = fd_two_sub()
+    from workloads.configs import fd_chain
+    w = fd_chain()
+    oracle = ChainOracle(w)
+    budget = max(0.5, args.ref_budget / max(1, args.steps))
     for _ in range(args.warmup):
-        pass
-    vals = []
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(w, budget_s=args.ref_budget))
+        cpu_baseline(oracle, budget_s=min(0.5, budget))
+    vals = [cpu_baseline(oracle, budget_s=budget) for _ in range(args.steps)]
     v = statistics.median(x["value"] for x in vals)
     cb = dict(vals[-1])
     cb["value"] = v
     line = {"metric": METRIC, "value": v, "unit": "probs/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 2 ** w.n / v * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference", "config": {"workload": WORKLOAD, "n_qubits": w.n, "cuts": w.K},
             "cpu_baseline": cb,
-            "e2e": {"value": v, "unit": "probs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v, "unit": "probs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": "ms_per_step: the whole 2^32-output job at the sampled rate"}
     print(json.dumps(line), flush=True)
+
+
+def _graph(fn, stream, warmup):
+    """Warm fn up on a side stream, then capture it into a CUDA graph."""
+    import torch
+    side = torch.cuda.Stream(stream.device)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(warmup):
+            fn()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g
+
+
+def _time_graph(g, stream, reps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
 
 
 def run(args):
@@ -300,66 +365,62 @@ def run(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2205_05836_gb300 import cutqc as cq
-    from workloads.configs import fd_two_sub
+    from paper_2205_05836_gb300.shard import row_range
+    from workloads.configs import fd_chain
     _log("library built")
-    w = fd_two_sub()
+    w = fd_chain()
     subs = w.subcircuits
     var_host = w.variants()
     _log("variants simulated")
     var = [torch.from_numpy(v).to(dev) for v in var_host]
-    kin = [len(s.in_local) for s in subs]
     att = [torch.empty((1 << s.o, 4 ** (len(s.in_local) + len(s.out_local))), dtype=torch.float32, device=dev)
            for s in subs]
     att_ws = [torch.empty(max(1, cq.cutqc_attribute_workspace_size(s)), dtype=torch.uint8, device=dev) for s in subs]
-    n_out = 1 << w.n
-    out = torch.empty(n_out, dtype=torch.float32, device=dev)
+    rows, cols = cq.cutqc_fd_shape(subs)
+    r0, r1 = row_range(rows, ws, rank)
+    n_all = 1 << w.n
+    n_out = (r1 - r0) * cols
+    out = torch.empty(max(1, n_out), dtype=torch.float32, device=dev)
     prec = {"tc": cq.PREC_FP16X3_TC, "tc_prune": cq.PREC_FP16X3_TC_PRUNE, "simt": cq.PREC_FP32_SIMT}[args.precision]
     fd_ws = torch.empty(max(1, cq.cutqc_reconstruct_fd_workspace_size(subs, prec)), dtype=torch.uint8, device=dev)
     total = torch.zeros(1, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-
     att_side = torch.cuda.Stream(dev)
 
-    def attribute_all():
-        # the subcircuits' attributions are independent: the first runs on a
-        # second stream, concurrently with the others (joined before the FD)
+    def attribute_all(outs=att):
+        # the subcircuits' attributions are independent: the two middle ones
+        # (the large variant tensors) go to a second stream, joined before FD
         cur = torch.cuda.current_stream(dev)
         fork = torch.cuda.Event()
         fork.record(cur)
         att_side.wait_event(fork)
         with torch.cuda.stream(att_side):
-            cq.cutqc_attribute(subs[0], var[0], out=att[0], ws=att_ws[0])
-        for s, v, a, wsb in zip(subs[1:], var[1:], att[1:], att_ws[1:]):
-            cq.cutqc_attribute(s, v, out=a, ws=wsb)
+            for i in (1, 3):
+                cq.cutqc_attribute(subs[i], var[i], out=outs[i], ws=att_ws[i])
+        for i in (0, 2):
+            cq.cutqc_attribute(subs[i], var[i], out=outs[i], ws=att_ws[i])
         join = torch.cuda.Event()
         join.record(att_side)
         cur.wait_event(join)
 
-    def reconstruct():
-        total.zero_()
-        cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_KRON, prec, out=out, sum_out=total, ws=fd_ws)
+    def reconstruct(dst=out, tot=total):
+        tot.zero_()
+        if n_out > 0:
+            cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_KRON, prec, row_begin=r0, row_end=r1, out=dst,
+                                    sum_out=tot, ws=fd_ws)
 
     def step():
         attribute_all()
         reconstruct()
 
     # one step = one replay of a CUDA graph holding every launch of the step
-    # (host argument checks run once, at capture)
-    side = torch.cuda.Stream(dev)
-    side.wait_stream(stream)
-    with torch.cuda.stream(side):
-        for _ in range(args.warmup):
-            step()
-    stream.wait_stream(side)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        step()
-    g_att, g_fd = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g_att):
-        attribute_all()
-    with torch.cuda.graph(g_fd):
-        reconstruct()
+    # (host argument checks run once, at capture); the library's launch
+    # counter across the capture gives the kernels per step
+    n0 = cq.cutqc_kernel_launches()
+    graph = _graph(step, stream, args.warmup)
+    launches_per_step = (cq.cutqc_kernel_launches() - n0) // (args.warmup + 1)
+    g_att = _graph(attribute_all, stream, 1)
+    g_fd = _graph(reconstruct, stream, 1)
     for _ in range(args.warmup):
         graph.replay()
     torch.cuda.synchronize()
@@ -376,63 +437,87 @@ def run(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, ws, dev)
-    sum_err = abs(total.item() - 1.0)
+    tot_all = total.clone()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(tot_all)            # the FP64 totals of the ranks' row ranges
+    sum_err = abs(tot_all.item() - 1.0)
     status = cq.cutqc_device_status()
+    _log("timed steps done")
 
-    # per-kernel timing of the dominant kernel (the FD contraction), same stream
-    att_ms = []
-    fd_ms = []
-    for _ in range(max(3, args.steps)):
-        a0, a1, f1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        a0.record(stream)
-        g_att.replay()
-        a1.record(stream)
-        g_fd.replay()
-        f1.record(stream)
+    # per-kernel timing on the stream the kernels run on: the attribution and
+    # the FD sequence as graph replays; the dominant kernel (the last
+    # contraction's tcgen05 GEMM) with events the library records around its
+    # launch (eager calls, same stream)
+    att_ms, fd_ms, gemm_ms = [], [], []
+    for _ in range(max(3, min(args.steps, 10))):
+        att_ms.append(_time_graph(g_att, stream, 1))
+        fd_ms.append(_time_graph(g_fd, stream, 1))
+        gs, ge = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cq.cutqc_fd_timing_events(gs, ge)
+        reconstruct()
         torch.cuda.synchronize()
-        att_ms.append(a0.elapsed_time(a1))
-        fd_ms.append(a1.elapsed_time(f1))
-    att_ms = statistics.median(att_ms)
-    fd_ms = statistics.median(fd_ms)
-    M, N = 1 << subs[0].o, 1 << subs[1].o
-    Kg = 4 ** w.K
-    alg_flops = 2.0 * M * N * Kg                    # Eq. 1, one pass
-    exec_flops = 3 * alg_flops if prec != cq.PREC_FP32_SIMT else alg_flops   # pruned: an upper bound
+        gemm_ms.append(gs.elapsed_time(ge))
+    att_ms, fd_ms, gemm_ms = (statistics.median(x) for x in (att_ms, fd_ms, gemm_ms))
+    graph.replay()              # the timed output again (the eager calls rewrote it identically)
+    torch.cuda.synchronize()
+
     pk = peaks()
-    # algorithmic bytes of one FD launch sequence: read both attributed
-    # tensors once, write 4 B per probability.  At the peaks these bytes take
-    # longer than the algorithmic flops, so the bound is HBM.
-    alg_bytes = 4.0 * n_out + sum(a.numel() * 4 for a in att)
-    achieved = alg_bytes / (fd_ms * 1e-3) / 1e9
+    from workloads.cutting import contraction_plan
+    _, alg_flops_all = contraction_plan([s.o for s in subs], [set(s.edges) for s in subs])
+    # the last contraction: rows x cols outputs over 4^(cuts between the
+    # pairs) terms; operands read once, 4 B written per probability
+    k_last = 4 ** 4
+    gemm_out_bytes = 4.0 * n_out
+    gemm_in_bytes = 4.0 * k_last * ((r1 - r0) + cols)
+    gemm_bytes = gemm_out_bytes + gemm_in_bytes
+    gemm_flops = 2.0 * n_out * k_last
+    achieved = gemm_bytes / (gemm_ms * 1e-3) / 1e9
+    fd_bytes = 4.0 * n_out + sum(a.numel() * 4 for a in att)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"],
-                "traffic": profiled_traffic("paper_2205_05836_gb300/csrc/gemm_tc_pair.cu", "profiles/tc_pair_gemm_fd_two_sub.md"),
-                "kernel": "FD contraction (operand prep + tcgen05 GEMM), one launch sequence",
-                "algorithmic_bytes": alg_bytes, "algorithmic_flops": alg_flops,
-                "hbm_bound_ms": alg_bytes / (pk["hbm_gbs"] * 1e9) * 1e3,
-                "tensor_bound_ms_1pass": alg_flops / (pk["bf16_tflops"] * 1e12) * 1e3,
-                "tensor_bound_ms_executed": exec_flops / (pk["bf16_tflops"] * 1e12) * 1e3,
-                "algorithmic_tflops": alg_flops / (fd_ms * 1e-3) / 1e12,
-                "executed_tflops": exec_flops / (fd_ms * 1e-3) / 1e12,
-                "executed_frac_of_bf16_peak": exec_flops / (fd_ms * 1e-3) / 1e12 / pk["bf16_tflops"],
+                "traffic": profiled_traffic("paper_2205_05836_gb300/csrc/gemm_tc_pair.cu",
+                                            "profiles/tc_pair_gemm_fd_chain.md"),
+                "kernel": "tc_pair_gemm_kernel (tcgen05, SM pairs): the last contraction of the chain, "
+                          f"{r1 - r0} x {cols} outputs over {k_last} cut terms, one launch",
+                "kernel_ms": gemm_ms, "algorithmic_bytes": gemm_bytes,
+                "algorithmic_bytes_per_unit": "4 B written per probability + the two operands read once",
+                "hbm_bound_ms": gemm_bytes / (pk["hbm_gbs"] * 1e9) * 1e3,
+                "tensor_bound_ms_1pass": gemm_flops / (pk["bf16_tflops"] * 1e12) * 1e3,
+                "tensor_bound_ms_executed": 3 * gemm_flops / (pk["bf16_tflops"] * 1e12) * 1e3,
+                "executed_tflops": 3 * gemm_flops / (gemm_ms * 1e-3) / 1e12,
                 "peak_source": pk["source"] + " (copy bandwidth; fp16 dense rate = bf16 rate)",
-                "fd_ms": fd_ms, "attribution_ms": att_ms}
-    value = ws * n_out / (ms * 1e-3)
-    # library kernels per step: one attribution pass per subcircuit side that
-    # carries cuts (init and/or meas), then the contraction: tc = three
-    # operand-prep passes and the tcgen05 GEMM; tc_prune = two column-weight
-    # passes, the selection, two prep passes and the GEMM; simt = two preps and
-    # the CUDA-core GEMM (the FP64 total's zeroing is a torch fill, not counted)
-    launches_per_step = sum((len(s.in_local) > 0) + (len(s.out_local) > 0) for s in subs) + \
-        {cq.PREC_FP16X3_TC: 4, cq.PREC_FP16X3_TC_PRUNE: 6, cq.PREC_FP32_SIMT: 3}[prec]
+                "fd_sequence": {"ms": fd_ms, "algorithmic_bytes": fd_bytes,
+                                "frac": fd_bytes / (fd_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                                "note": "all three contractions with their operand preps"},
+                "step_frac": fd_bytes / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                "attribution_ms": att_ms}
+    value = n_all / (ms * 1e-3) if ws > 1 else n_out / (ms * 1e-3)
+
+    # total variation of the timed output against the FP64 oracle on 2^20
+    # seeded uniformly sampled outputs of this rank's rows
+    tv = None
+    if rank == 0 and not args.no_tv:
+        oracle = ChainOracle(w)
+        rng = np.random.default_rng(2024)
+        idx = np.unique(rng.integers(r0 * cols, r1 * cols, size=1 << 20))
+        got = out[torch.from_numpy(idx - r0 * cols).to(dev)].cpu().numpy().astype(np.float64)
+        ref = oracle.entries(idx)
+        err = np.abs(got - ref)
+        tv = {"tv_estimate": 0.5 * n_out * float(err.mean()), "max_abs_error": float(err.max()),
+              "samples": int(len(idx)), "gate": 1e-6,
+              "how": "0.5 * outputs * mean |GPU - FP64 oracle| over seeded uniform samples of the timed output"}
+        _log("sampled TV against the oracle done")
+    else:
+        oracle = None
 
     # end to end through the C ABI from pinned host buffers: every step
-    # uploads its variants, attributes, reconstructs and downloads the whole
-    # distribution and its FP64 total.  Two output buffers let the download of
+    # uploads its variants, attributes, reconstructs and downloads its whole
+    # output and FP64 total.  Two device output buffers let the download of
     # step i (a copy stream) overlap the upload and compute of step i + 1.
     host_var = [torch.from_numpy(v).pin_memory() for v in var_host]
-    host_out = [torch.empty(n_out, dtype=torch.float32).pin_memory() for _ in range(2)]
-    host_total = [torch.zeros(1, dtype=torch.float64).pin_memory() for _ in range(2)]
+    host_out = torch.empty(max(1, n_out), dtype=torch.float32, pin_memory=True)
+    host_total = torch.zeros(1, dtype=torch.float64, pin_memory=True)
     dev_out = [out, torch.empty_like(out)]
     dev_total = [total, torch.zeros_like(total)]
     h2d = sum(v.numel() * v.element_size() for v in host_var)
@@ -447,20 +532,19 @@ def run(args):
         for hv, v in zip(host_var, var):
             v.copy_(hv, non_blocking=True)
         attribute_all()
-        dev_total[b].zero_()
-        cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_KRON, prec, out=dev_out[b], sum_out=dev_total[b], ws=fd_ws)
+        reconstruct(dev_out[b], dev_total[b])
         done = torch.cuda.Event()
         done.record(stream)
         copy_stream.wait_event(done)
         with torch.cuda.stream(copy_stream):
-            host_out[b].copy_(dev_out[b], non_blocking=True)
-            host_total[b].copy_(dev_total[b], non_blocking=True)
+            host_out.copy_(dev_out[b], non_blocking=True)
+            host_total.copy_(dev_total[b], non_blocking=True)
             copied[b] = torch.cuda.Event()
             copied[b].record(copy_stream)
     e2e_step(0)
     e2e_step(1)
     torch.cuda.synchronize()
-    e2e_steps = max(2, min(args.steps, 6))
+    e2e_steps = max(2, min(args.steps, 4))
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g0.record(stream)
     for i in range(e2e_steps):
@@ -469,29 +553,38 @@ def run(args):
     g1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(g0.elapsed_time(g1) / e2e_steps, ws, dev)
+    del host_out, dev_out
+    _log("end-to-end steps done")
 
     line = {"metric": METRIC, "value": value, "unit": "probs/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 (FP16x3 split tensor-core products, FP32 accumulate)" if prec else "f32",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None,
+            "dtype": "f32 (FP16x3 split tensor-core products, FP32 accumulate)" if prec else "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_qubits": w.n, "cuts": w.K, "gemm": [M, N, Kg],
-                       "precision": args.precision, "l2": "output 4 GiB > L2 each step; no flush",
-                       "parallelism": f"{ws} independent reconstructions (one per GPU)"},
-            "sum_p_error": sum_err, "device_status": status,
+            "config": {"workload": WORKLOAD, "n_qubits": w.n, "cuts": w.K,
+                       "subcircuit_widths": [s.w for s in subs], "subcircuit_outputs": [s.o for s in subs],
+                       "last_contraction": [rows, cols, k_last], "precision": args.precision,
+                       "l2": "output 16 GiB > L2 each step; no flush",
+                       "parallelism": f"{ws} rank(s), each writing rows [{r0}, {r1}) of the last contraction"
+                                      if ws > 1 else "one GPU"},
+            "sum_p_error": sum_err, "tv": tv, "device_status": status,
             "roofline": roofline, "clocks": clk.summary(),
-            "e2e": {"value": ws * n_out / (e2e_ms * 1e-3), "unit": "probs/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * launches_per_step}
-    _log("FD step, per-kernel and end-to-end timing done")
+            "e2e": {"value": (n_all if ws > 1 else n_out) / (e2e_ms * 1e-3), "unit": "probs/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "note": "bound by the device-to-host copy of the output"},
+            "gpu_launches": args.steps * launches_per_step, "gpu_launches_per_step": launches_per_step}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, budget_s=args.ref_budget)
+        line["cpu_baseline"] = cpu_baseline(oracle or ChainOracle(w), budget_s=args.ref_budget)
         _log("cpu baseline done")
     if rank == 0 and not args.no_extras:
-        del out, fd_ws, graph, g_att, g_fd, host_out, host_var, dev_out, dev_total
+        del graph, g_att, g_fd
+        line["fd_chain_variants"] = chain_variant_extras(dev, cq, subs, att, out, total, r0, r1, ms)
+        del out, fd_ws, host_var
         torch.cuda.empty_cache()
-        line["fd_chain"] = fd_chain_extras(dev, cq)
+        _log("FD chain variants done")
+        line["fd_two_sub"] = fd_two_sub_extras(dev, cq)
         torch.cuda.empty_cache()
-        _log("FD chain extras done")
+        _log("FD two-subcircuit extras done")
         line["dd_batched"] = dd_extras(dev, cq)
         tc = dd_extras(dev, cq, precision=1)
         line["dd_batched"]["split_precision"] = {
@@ -509,6 +602,94 @@ def run(args):
         _log("cut-scorer extras done")
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def chain_variant_extras(dev, cq, subs, att, out, total, r0, r1, headline_ms, steps=10, warmup=3):
+    """The same chain with cut-term pruning (the last contraction skips cut
+    terms whose summed L1 bound is <= 2^-30) and on FP32 CUDA cores (the
+    speed-up of the tensor-core path), each as a graph of the reconstruction
+    alone; the headline's own reconstruction timed the same way beside them."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    pk = peaks()
+    alg_bytes = 4.0 * out.numel() + sum(a.numel() * 4 for a in att)
+    for name, prec in (("tc", cq.PREC_FP16X3_TC), ("tc_prune", cq.PREC_FP16X3_TC_PRUNE), ("simt", cq.PREC_FP32_SIMT)):
+        fws = torch.empty(max(1, cq.cutqc_reconstruct_fd_workspace_size(subs, prec)), dtype=torch.uint8, device=dev)
+
+        def rec():
+            total.zero_()
+            cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_KRON, prec, row_begin=r0, row_end=r1, out=out,
+                                    sum_out=total, ws=fws)
+        g = _graph(rec, stream, warmup)
+        g.replay()
+        torch.cuda.synchronize()
+        k = 3 if name == "simt" else steps
+        with ClockSampler(dev.index or 0) as clk:
+            ms = _time_graph(g, stream, k)
+        res[name] = {"ms": ms, "probs_per_s": out.numel() / (ms * 1e-3),
+                     "hbm_frac": alg_bytes / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                     "sum_p_error": abs(total.item() - 1.0), "clocks": clk.summary()}
+        del g, fws
+    res["tc_prune"]["note"] = "last contraction skips cut terms whose summed L1 bound is <= 2^-30 (not the headline)"
+    res["speedup_tc_over_simt"] = res["simt"]["ms"] / res["tc"]["ms"]
+    res["speedup_tc_prune_over_simt"] = res["simt"]["ms"] / res["tc_prune"]["ms"]
+    res["note"] = "reconstruction only (no attribution); tc = the headline's arithmetic"
+    return res
+
+
+def fd_two_sub_extras(dev, cq, steps=10, warmup=3):
+    """The 30-qubit two-subcircuit workload (5 x 6 supremacy family, depth 10,
+    the couplers across one split bridged so that K = 4; subcircuits 17 + 17,
+    2^30 outputs): attribution + one tcgen05 contraction per step, timed as a
+    graph; the contraction's own time with the library's events."""
+    import torch
+    from workloads.configs import fd_two_sub
+    w = fd_two_sub()
+    subs = w.subcircuits
+    var = [torch.from_numpy(v).to(dev) for v in w.variants()]
+    att = [torch.empty((1 << s.o, 4 ** (len(s.in_local) + len(s.out_local))), dtype=torch.float32, device=dev)
+           for s in subs]
+    aws = [torch.empty(max(1, cq.cutqc_attribute_workspace_size(s)), dtype=torch.uint8, device=dev) for s in subs]
+    n_out = 1 << w.n
+    out = torch.empty(n_out, dtype=torch.float32, device=dev)
+    fws = torch.empty(max(1, cq.cutqc_reconstruct_fd_workspace_size(subs, cq.PREC_FP16X3_TC)), dtype=torch.uint8,
+                      device=dev)
+    total = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for s, v, a, b in zip(subs, var, att, aws):
+            cq.cutqc_attribute(s, v, out=a, ws=b)
+        total.zero_()
+        cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_KRON, cq.PREC_FP16X3_TC, out=out, sum_out=total, ws=fws)
+    g = _graph(step, stream, warmup)
+    g.replay()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index or 0) as clk:
+        ms = _time_graph(g, stream, steps)
+    gemm = []
+    for _ in range(5):
+        gs, ge = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cq.cutqc_fd_timing_events(gs, ge)
+        step()
+        torch.cuda.synchronize()
+        gemm.append(gs.elapsed_time(ge))
+    gemm_ms = statistics.median(gemm)
+    pk = peaks()
+    M, N = 1 << subs[0].o, 1 << subs[1].o
+    Kg = 4 ** w.K
+    gbytes = 4.0 * n_out + 4.0 * Kg * (M + N)
+    return {"workload": TWO_SUB_WORKLOAD, "n_qubits": w.n, "cuts": w.K, "gemm": [M, N, Kg],
+            "ms_per_step": ms, "probs_per_s": n_out / (ms * 1e-3), "sum_p_error": abs(total.item() - 1.0),
+            "roofline": {"bound": "hbm", "kernel": "tc_pair_gemm_kernel, one launch", "kernel_ms": gemm_ms,
+                         "algorithmic_bytes": gbytes, "achieved": gbytes / (gemm_ms * 1e-3) / 1e9,
+                         "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbytes / (gemm_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                         "traffic": profiled_traffic("paper_2205_05836_gb300/csrc/gemm_tc_pair.cu",
+                                                     "profiles/tc_pair_gemm_fd_two_sub.md"),
+                         "tensor_bound_ms_executed": 3 * 2.0 * n_out * Kg / (pk["bf16_tflops"] * 1e12) * 1e3},
+            "clocks": clk.summary()}
 
 
 def learned_extras(dev, cq, n_circuits=10000, train_steps=4000, batch=1024):
@@ -591,75 +772,20 @@ def learned_extras(dev, cq, n_circuits=10000, train_steps=4000, batch=1024):
                       "bitstring_exact": bool(exact), "p_top": float(b[top])}}
 
 
-def fd_chain_extras(dev, cq, steps=10, warmup=3):
-    """The 32-qubit AQFT chain (4 subcircuits of 11 qubits, K = 12, 2^32
-    float32 outputs = 16 GiB): attribution of the four subcircuits, then the
-    pairwise contraction chain, tensor-core path, timed as one CUDA graph;
-    the FP32 CUDA-core path timed the same way for the speed-up."""
-    import torch
-    from workloads.configs import fd_chain
-    w = fd_chain()
-    subs = w.subcircuits
-    var = [torch.from_numpy(v).to(dev) for v in w.variants()]
-    att = [cq.cutqc_attribute(s, v) for s, v in zip(subs, var)]
-    n_out = 1 << w.n
-    out = torch.empty(n_out, dtype=torch.float32, device=dev)
-    total = torch.zeros(1, dtype=torch.float64, device=dev)
-    res = {"workload": "fd_chain_aqft32: 32-qubit AQFT (phases to distance 4), 4 subcircuits of 11 qubits, K=12",
-           "n_qubits": w.n, "cuts": w.K}
-    stream = torch.cuda.current_stream(dev)
-    for name, prec in (("tc", cq.PREC_FP16X3_TC), ("tc_prune", cq.PREC_FP16X3_TC_PRUNE), ("simt", cq.PREC_FP32_SIMT)):
-        fws = torch.empty(max(1, cq.cutqc_reconstruct_fd_workspace_size(subs, prec)), dtype=torch.uint8, device=dev)
-
-        def rec():
-            total.zero_()
-            cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_KRON, prec, out=out, sum_out=total, ws=fws)
-        side = torch.cuda.Stream(dev)
-        side.wait_stream(stream)
-        with torch.cuda.stream(side):
-            for _ in range(warmup):
-                rec()
-        stream.wait_stream(side)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            rec()
-        g.replay()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        k = 3 if name == "simt" else steps
-        with ClockSampler(dev.index or 0) as clk:
-            e0.record(stream)
-            for _ in range(k):
-                g.replay()
-            e1.record(stream)
-            torch.cuda.synchronize()
-        res[name + "_ms"] = e0.elapsed_time(e1) / k
-        res[name + "_clocks"] = clk.summary()
-        res[name + "_sum_p_error"] = abs(total.item() - 1.0)
-        del g, fws
-    pk = peaks()
-    alg_bytes = 4.0 * n_out + sum(a.numel() * 4 for a in att)
-    # final stage: rows 2^14 x cols 2^18 x 4^4 shared cut digits; the two
-    # intermediate stages add ~1% more
-    from workloads.cutting import contraction_plan
-    _, alg_flops = contraction_plan([s.o for s in subs], [set(s.edges) for s in subs])
-    ms = res["tc_ms"]
-    mp = res["tc_prune_ms"]
-    res["tc_prune"] = {"probs_per_s": n_out / (mp * 1e-3), "speedup_over_simt": res["simt_ms"] / mp,
-                       "hbm_frac": alg_bytes / (mp * 1e-3) / 1e9 / pk["hbm_gbs"],
-                       "note": "last contraction skips cut terms whose summed L1 bound is <= 2^-30"}
-    res.update({"probs_per_s": n_out / (ms * 1e-3), "speedup_tc_over_simt": res["simt_ms"] / ms,
-                "roofline": {"bound": "hbm", "achieved": alg_bytes / (ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
-                             "unit": "GB/s", "frac": alg_bytes / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
-                             "hbm_bound_ms": alg_bytes / (pk["hbm_gbs"] * 1e9) * 1e3,
-                             "tensor_bound_ms_executed": 3 * alg_flops / (pk["bf16_tflops"] * 1e12) * 1e3,
-                             "algorithmic_flops": alg_flops}})
-    # the roofline taken as the slower of the executed tensor
-    # flops at the measured peak and the bytes at the measured bandwidth
-    rf = res["roofline"]
-    rf["frac_of_slower_bound"] = max(rf["hbm_bound_ms"], rf["tensor_bound_ms_executed"]) / ms
-    return res
+def dd_alg_bytes(subs, jobs):
+    """Algorithmic bytes of a set of DD bin jobs: each job reads the slice of
+    every attributed tensor whose zoomed output bits equal its zoom (all 4^k
+    columns of those rows, float32) and writes its 2^active bins (float32);
+    the merged tensors in between are small and L2-resident."""
+    tot = 0
+    for j in jobs:
+        zoom = j.zoom()
+        for s in subs:
+            z = sum(1 for q in s.out_qubit if q in zoom)
+            k = len(s.in_local) + len(s.out_local)
+            tot += (1 << (s.o - z)) * 4 ** k * 4
+        tot += (1 << j.n_active) * 4
+    return tot
 
 
 def dd_extras(dev, cq, M=16, R=6, T=4, reps=5, precision=0):
@@ -712,22 +838,34 @@ def dd_extras(dev, cq, M=16, R=6, T=4, reps=5, precision=0):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
-    out, tot_bins = [], 0
+    out, tot_bins, tot_bytes = [], 0, 0
     for w, subs, att, jobs, n_jobs, bins, ws, opt, trials in runs:
         js = cq.dd_jobs_from_device(jobs, n_jobs)
         nb = sum(1 << j.n_active for j in js)
         tot_bins += nb
+        tot_bytes += dd_alg_bytes(subs, js)
         out.append({"circuit": w.name, "n": w.n, "subcircuits": len(subs), "K": w.K, "jobs": len(js), "bins": nb,
                     "root_sum_error": abs(js[0].bin_sum - 1.0), "options": opt,
                     "tuning_ms": {f"{o['merge_ctas']}/{o['topk_threads']}": round(ms, 4) for ms, o, ok in trials if ok}})
+    pk = peaks()
     res = {"M": M, "R": R, "T": T, "strategy": "bfs", "precision": "tc" if precision else "fp32",
            "circuits": out, "graph_ms": ms, "bins_per_s": tot_bins / (ms * 1e-3),
+           "algorithmic_bytes": tot_bytes,
+           "graph_roofline": {"bound": "hbm", "achieved": tot_bytes / (ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
+                              "unit": "GB/s", "frac": tot_bytes / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]},
            "note": "all levels of the three circuits in one captured CUDA graph (one stream per circuit); "
                    "selection on the device"}
     if precision == 0:
         # the headline DD rate is the persistent launch's when it reproduced
         # the level launches' records and bins; both rates are kept
         pers = dd_batch_extras(dev, cq, runs, M, R, T, tot_bins, reps)
+        pers["roofline"] = {"bound": "hbm", "achieved": tot_bytes / (pers["ms"] * 1e-3) / 1e9,
+                            "peak": pk["hbm_gbs"], "unit": "GB/s",
+                            "frac": tot_bytes / (pers["ms"] * 1e-3) / 1e9 / pk["hbm_gbs"],
+                            "algorithmic_bytes": tot_bytes,
+                            "note": "per job: the zoomed slice of every attributed tensor read once + 4 B per "
+                                    "bin written; the launch is bound by its phases' barrier and dependency "
+                                    "latency, not by bytes"}
         res["persistent"] = pers
         res["level_launches_bins_per_s"] = res["bins_per_s"]
         if pers["matches_level_by_level"] and pers["device_status"] == 0:
@@ -860,8 +998,15 @@ def dd_dense_extras(dev, cq, M=30, T=4, reps=5):
                      "top_idx": [int(i) for i in js[0].top_idx[:T]], "clocks": clk.summary()}
         del g
     pk = peaks()
-    res["hbm_bound_ms"] = 4.0 * (1 << M) / (pk["hbm_gbs"] * 1e9) * 1e3
+    alg = dd_alg_bytes(subs, js)
+    res["algorithmic_bytes"] = alg
+    res["hbm_bound_ms"] = alg / (pk["hbm_gbs"] * 1e9) * 1e3
+    for name in ("fp32", "tc"):
+        a = alg / (res[name]["ms"] * 1e-3) / 1e9
+        res[name]["roofline"] = {"bound": "hbm", "achieved": a, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                 "frac": a / pk["hbm_gbs"]}
     res["speedup_tc_over_fp32"] = res["fp32"]["ms"] / res["tc"]["ms"]
+    res["note"] = "algorithmic bytes: the attributed tensors read once + 4 B per bin written"
     return res
 
 
@@ -955,6 +1100,7 @@ def main():
     ap.add_argument("--precision", default="tc", choices=["tc", "tc_prune", "simt"])
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tv", action="store_true", help="skip the sampled TV of the timed output")
     ap.add_argument("--no-extras", action="store_true", help="skip the DD and cut-scorer measurements")
     ap.add_argument("--profile-case", action="store_true",
                     help="run the kernels once on a row slice (for ncu) and exit")

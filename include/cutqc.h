@@ -101,6 +101,11 @@ const char* cutqc_version(void);
  * waits (0 = none expired).  Synchronises the device. */
 int cutqc_device_status(int32_t* status_out);
 
+/* Number of kernels the library has enqueued in this process so far (a
+ * launch captured into a CUDA graph counts once, at capture; graph replays
+ * do not count).  No paper counterpart: for launch accounting.             */
+int cutqc_kernel_launches(int64_t* count);
+
 /* Failure-path self test (no paper counterpart): launches one CTA that waits
  * on an mbarrier nothing arrives on, with the same bounded wait (about 2 s of
  * clock cycles) as every mbarrier wait in the library's kernels.  When the

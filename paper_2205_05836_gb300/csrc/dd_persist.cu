@@ -841,6 +841,7 @@ extern "C" int cutqc_dd_batch_launch(const cutqc_dd_batch* b, void* stream) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   CUTQC_CUDA_TRY(cudaLaunchKernelEx(&cfg, b->kernel, b->pg));
+  count_launches(1);
   return CUTQC_OK;
 }
 

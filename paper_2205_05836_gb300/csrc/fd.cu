@@ -14,6 +14,7 @@
 #include "contract.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -42,6 +43,10 @@ int set_error(int code, const char* fmt, ...) {
   g_last_error = buf;
   return code;
 }
+
+static std::atomic<long long> g_launches{0};
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int cuda_error(cudaError_t e, const char* where) {
   return set_error(CUTQC_ECUDA, "%s: %s", where, cudaGetErrorString(e));
@@ -545,6 +550,12 @@ extern "C" int cutqc_device_status(int32_t* status_out) {
   CUTQC_CUDA_TRY(cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost));
   CUTQC_CUDA_TRY(cudaMemset(p, 0, sizeof(int)));
   *status_out = v;
+  return CUTQC_OK;
+}
+
+extern "C" int cutqc_kernel_launches(int64_t* count) {
+  if (!count) return set_error(CUTQC_EINVAL, "null count");
+  *count = (int64_t)g_launches.load(std::memory_order_relaxed);
   return CUTQC_OK;
 }
 

@@ -24,8 +24,14 @@ int cuda_error(cudaError_t e, const char* where);
     if (_e != cudaSuccess) return ::cutqc::cuda_error(_e, #expr);     \
   } while (0)
 
+// Kernels enqueued (or captured into a graph) by the library, process-wide:
+// every launch site is followed by one CUTQC_LAUNCH_CHECK, which counts it;
+// a check that covers several launches adds the others with count_launches.
+void count_launches(int n);
+
 #define CUTQC_LAUNCH_CHECK(where)                                     \
   do {                                                                \
+    ::cutqc::count_launches(1);                                       \
     cudaError_t _e = cudaGetLastError();                              \
     if (_e != cudaSuccess) return ::cutqc::cuda_error(_e, where);     \
   } while (0)

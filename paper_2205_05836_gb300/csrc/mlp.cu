@@ -189,6 +189,7 @@ int backward(const __nv_bfloat16* pb, const float* x, const float* t, int B, con
   // dW1 = x^T dz1, db1
   if ((rc = dense<true, false>(x, nullptr, k.g1, nullptr, grad + OFF_W1, nullptr, D0, D1, B, 0, 0, st))) return rc;
   colsum_kernel<<<(D1 + 255) / 256, 256, 0, st>>>(k.g1, B, D1, grad + OFF_B1);
+  count_launches(4);          // the check below covers the five launches above
   CUTQC_LAUNCH_CHECK("mlp backward");
   return CUTQC_OK;
 }

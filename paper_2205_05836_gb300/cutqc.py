@@ -111,6 +111,13 @@ def cutqc_device_status():
     return v.value
 
 
+def cutqc_kernel_launches():
+    """Kernels the library has enqueued (or captured) in this process."""
+    v = c_int64(0)
+    _check(lib().cutqc_kernel_launches(ctypes.byref(v)))
+    return v.value
+
+
 def cutqc_selftest_wait_timeout(waited=None, stream=None):
     """Launches the bounded-wait self test (a wait nothing satisfies); the
     device status word then reads CUTQC_ETIMEOUT (cutqc_device_status)."""

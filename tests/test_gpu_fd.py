@@ -162,6 +162,57 @@ def test_fd_synthetic_chain_layouts(cq, shape, order, precision):
     assert cq.cutqc_device_status() == 0
 
 
+def _wide_range(rng, rows, cols, decades):
+    """Attributed-tensor stand-in whose entries span `decades` decades inside
+    every row and 4 more across rows, both signs, 3% of rows and 5% of
+    entries exactly zero."""
+    a = rng.choice([-1.0, 1.0], size=(rows, cols)) * 10.0 ** rng.uniform(-decades, 0, size=(rows, cols))
+    a *= 10.0 ** rng.uniform(-4, 0, size=(rows, 1))
+    a[rng.random((rows, cols)) < 0.05] = 0.0
+    a[rng.random(rows) < 0.03] = 0.0
+    return a.astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("decades", [8, 10])
+def test_fd_wide_dynamic_range(cq, decades):
+    """Split-precision robustness: two subcircuits joined by 4 cuts (one
+    256-term contraction) whose attributed rows span 8-10 decades, with
+    zeros and sign flips, so that small entries fall into the FP16
+    subnormal range of the lo plane.  Every output is checked against the
+    bound of the FP16 hi/lo split with power-of-two scales (max |x| of a row,
+    or of the whole operand, scaled into [2^14, 2^15)): per product
+    3 * 2^-22 |a b| + 2^-39 (|a| max|B| + |b| max|A|), plus the FP32
+    accumulation (<= 26 truncations of 2^-23 of the running sum); tested
+    with a 4x margin on each term:
+        |P - P_exact| <= 2^-16 sum_k |a_k b_k| + 2^-37 (|A_m|_1 max|B| + |B_n|_1 max|A|)  (times 2^-K)."""
+    import torch
+    from types import SimpleNamespace
+    rng = np.random.default_rng(100 + decades)
+    o0, o1, k = 8, 9, 4
+    e = list(range(k))
+    s0 = SimpleNamespace(w=o0 + k, in_local=[], in_edge=[], out_local=list(range(o0, o0 + k)), out_edge=e,
+                         out_qubit=list(range(o1, o1 + o0)), edges=e, o=o0)
+    s1 = SimpleNamespace(w=o1, in_local=list(range(k)), in_edge=e, out_local=[], out_edge=[],
+                         out_qubit=list(range(o1)), edges=e, o=o1)
+    A = _wide_range(rng, 1 << o0, 4 ** k, decades)
+    B = _wide_range(rng, 1 << o1, 4 ** k, decades)
+    scale = 2.0 ** -k
+    exact = (A @ B.T) * scale                          # [x0][x1]: Kronecker order, s0 most significant
+    absum = (np.abs(A) @ np.abs(B).T) * scale
+    under = (np.abs(A).sum(1)[:, None] * np.abs(B).max() + np.abs(B).sum(1)[None, :] * np.abs(A).max()) * scale
+    bound = 2.0 ** -16 * absum + 2.0 ** -37 * under
+    att = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (A, B)]
+    for prec in (cq.PREC_FP16X3_TC, cq.PREC_FP32_SIMT):
+        out, _ = cq.cutqc_reconstruct_fd([s0, s1], att, cq.ORDER_KRON, prec)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.float64).reshape(1 << o0, 1 << o1)
+        err = np.abs(got - exact)
+        assert (err <= bound).all(), (prec, float((err / bound).max()))
+        # zero rows of either operand give exact zeros
+        assert (got[np.abs(A).sum(1) == 0] == 0).all() and (got[:, np.abs(B).sum(1) == 0] == 0).all()
+    assert cq.cutqc_device_status() == 0
+
+
 def test_fd_row_split_reassembles(cq):
     """Offset/stride sharding: row ranges written separately equal the whole."""
     import torch

@@ -78,11 +78,17 @@ def test_adam_matches_oracle(cq):
     p = [flat.astype(np.float64)]
     m = [np.zeros(flat.size)]
     v = [np.zeros(flat.size)]
+    m_abs = np.zeros(flat.size)          # the first moment of |g|: its terms' magnitude
+    B1, B2 = float(np.float32(0.9)), float(np.float32(0.999))
     for step in (1, 2, 3):
         g = (rng.standard_normal(flat.size) * 10.0 ** rng.integers(-4, 0, flat.size)).astype(np.float32)
         net.grad.copy_(torch.from_numpy(g))
         net.adam(step, 1e-3)
-        p, m, v = omlp.adam_step(p, [g.astype(np.float64)], m, v, step, 1e-3)
+        # the kernel is given beta1 = 0.9f and beta2 = 0.999f: the oracle
+        # takes the same float32 values (beta2 in float32 is 0.999 + 1.3e-8,
+        # which moves 1 - beta2, and so v, by 1.3e-5 relatively)
+        p, m, v = omlp.adam_step(p, [g.astype(np.float64)], m, v, step, 1e-3, beta1=B1, beta2=B2)
+        m_abs = B1 * m_abs + (1 - B1) * np.abs(g.astype(np.float64))
     got = net.p.cpu().numpy().astype(np.float64)
     assert np.abs(got - p[0]).max() <= 1e-6 * max(1.0, np.abs(p[0]).max())
     assert torch.equal(net.pb.cpu(), net.p.cpu().to(torch.bfloat16))
@@ -90,7 +96,7 @@ def test_adam_matches_oracle(cq):
     # which the parameters' float32 rounding could hide): float32 relative
     gm = net.m.cpu().numpy().astype(np.float64)
     gv = net.v.cpu().numpy().astype(np.float64)
-    assert np.all(np.abs(gm - m[0]) <= 1e-6 * np.abs(m[0]) + 1e-30)
+    assert np.all(np.abs(gm - m[0]) <= 1e-6 * m_abs)
     assert np.all(np.abs(gv - v[0]) <= 1e-6 * np.abs(v[0]) + 1e-30)
     # and the total update of three steps, per parameter, against the
     # oracle's: float32 rounding of p (~6e-8 relative) against steps of ~1e-3
