@@ -131,8 +131,9 @@ int cutqc_selftest_wait_timeout(int32_t* waited_dev, void* stream);
  * attributed_dev: [2^o][4^k] float32, o = w - k_out, k = k_in + k_out; row =
  *   output bits (t-th output qubit = bit t), column = sum_j d_j 4^j over the
  *   subcircuit's cut edges sorted by ascending edge id.
- * Workspace: cutqc_attribute_workspace_size bytes of device memory (may be
- * 0 bytes for subcircuits with only one kind of cut).
+ * Workspace: cutqc_attribute_workspace_size bytes of device memory: 2^o *
+ * 4^k * 4 bytes for a subcircuit with both initialised and measured cuts
+ * (the measured side's float32 result), 0 bytes otherwise.
  * Errors: CUTQC_EINVAL on a bad descriptor, CUTQC_ENOMEM if ws_bytes is too
  * small, CUTQC_EUNSUPPORTED if k_in > 6 or k_out > 5.                      */
 int cutqc_attribute_workspace_size(const cutqc_subcircuit* s, size_t* bytes);

@@ -14,8 +14,10 @@
 // fiber of all cut digits for its rows in shared memory (loads coalesced
 // along the outcome index), applies the per-cut maps axis by axis, and
 // writes the result.  Subcircuits with both kinds of cut take two passes
-// (initialised axes first, through a float32 workspace).  Arithmetic is
-// float32 after the (float64 or float32) loads; HBM-bound.
+// through a float32 workspace: the measured axes first (on the variants as
+// given, 3^k_out runs x 2^k_out outcomes -> 4^k_out bases per output row),
+// then the initialised axes along the columns of the smaller result.
+// Arithmetic is float32 after the (float64 or float32) loads; HBM-bound.
 #include "internal.cuh"
 
 #include <algorithm>
@@ -276,6 +278,119 @@ attr_meas_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p)
   }
 }
 
+// Initialised-side map along the columns, for subcircuits with both kinds of
+// cut: the measured-side pass has already produced the attributed layout
+// [2^o][4^k], but with the init cuts' digits still holding their states
+// (|0>, |1>, |+>, |+i>) rather than bases.  For every row x and every value
+// of the measured-cut digits ("fiber"), the 4^KIN values at the init digits'
+// column positions are mapped to bases by the per-cut 4x4 map (init_map4),
+// digit pair by digit pair.  A CTA stages FPB fibers in shared memory (each
+// padded by one float) and writes them to dst at the same positions.  Loads
+// and stores walk the fiber's elements fastest when an init digit holds
+// column bit 0 (ifast), else the fibers (then the measured digits hold it).
+constexpr int kColThreads = 256;
+
+template <int KIN>
+__global__ void __launch_bounds__(kColThreads)
+attr_init_cols(const float* __restrict__ src, float* __restrict__ dst, AttrParams p, int64_t n_fibers, int ifast) {
+  constexpr int F = 1 << (2 * KIN);
+  constexpr int FPB = F >= 4096 ? 1 : 4096 / F;     // 16 KiB of values per CTA
+  constexpr int FS = F + 1;
+  __shared__ float buf[FPB * FS];
+  __shared__ int64_t fbase[FPB];
+  __shared__ int ioff[F];
+  const int64_t f0 = (int64_t)blockIdx.x * FPB;
+  const int64_t C = (int64_t)1 << (2 * p.k);
+  const int mdig = 2 * p.k_out;
+  for (int i = threadIdx.x; i < F; i += kColThreads) {
+    int off = 0;
+#pragma unroll
+    for (int j = 0; j < KIN; ++j) off |= ((i >> (2 * j)) & 3) << p.col_shift_in[j];
+    ioff[i] = off;
+  }
+  for (int i = threadIdx.x; i < FPB; i += kColThreads) {
+    const int64_t f = f0 + i;
+    const int64_t x = f >> mdig;
+    const int mu = (int)(f & ((1 << mdig) - 1));
+    int moff = 0;
+    for (int j = 0; j < p.k_out; ++j) moff |= ((mu >> (2 * j)) & 3) << p.col_shift_out[j];
+    fbase[i] = x * C + moff;
+  }
+  __syncthreads();
+  auto elem = [&](int i, int& fl, int& io) {
+    if (ifast) { fl = i / F; io = i % F; } else { io = i / FPB; fl = i % FPB; }
+  };
+  for (int i0 = 0; i0 < FPB * F; i0 += kColThreads * kBatch) {
+    float v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + u * kColThreads + threadIdx.x;
+      int fl, io;
+      elem(i, fl, io);
+      v[u] = (i < FPB * F && f0 + fl < n_fibers) ? __ldg(src + fbase[fl] + ioff[io]) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + u * kColThreads + threadIdx.x;
+      int fl, io;
+      elem(i, fl, io);
+      if (i < FPB * F) buf[fl * FS + io] = v[u];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < KIN; j += 2) {
+    if (j + 1 < KIN) {
+      constexpr int groups = F >> 4;
+      for (int it = threadIdx.x; it < groups * FPB; it += kColThreads) {
+        const int grp = it % groups, fl = it / groups;
+        const int lowmask = (1 << (2 * j)) - 1;
+        const int base_f = (grp & lowmask) | ((grp >> (2 * j)) << (2 * j + 4));
+        float* fb = buf + fl * FS;
+        float v[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) v[a][b] = fb[base_f | (a << (2 * j)) | (b << (2 * j + 2))];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          float col[4] = {v[0][b], v[1][b], v[2][b], v[3][b]}, o[4];
+          init_map4(col, o);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) v[a][b] = o[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          float o[4];
+          init_map4(v[a], o);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) fb[base_f | (a << (2 * j)) | (b << (2 * j + 2))] = o[b];
+        }
+      }
+    } else {
+      constexpr int groups = F >> 2;
+      for (int it = threadIdx.x; it < groups * FPB; it += kColThreads) {
+        const int grp = it % groups, fl = it / groups;
+        const int lowmask = (1 << (2 * j)) - 1;
+        const int base_f = (grp & lowmask) | ((grp >> (2 * j)) << (2 * j + 2));
+        float* fb = buf + fl * FS;
+        float v[4], o[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) v[a] = fb[base_f | (a << (2 * j))];
+        init_map4(v, o);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) fb[base_f | (a << (2 * j))] = o[a];
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < FPB * F; i += kColThreads) {
+    int fl, io;
+    elem(i, fl, io);
+    if (f0 + fl < n_fibers) dst[fbase[fl] + ioff[io]] = buf[fl * FS + io];
+  }
+}
+
 template <typename T, int KIN>
 size_t init_smem() { return (size_t)(1 << (2 * KIN)) * (rows_for(1 << (2 * KIN)) + 1) * 4 + (2u << (2 * KIN)); }
 template <typename T, int KOUT>
@@ -395,6 +510,32 @@ int dispatch_init(const T* src, float* out, const AttrParams& p, int final_layou
   return set_error(CUTQC_EUNSUPPORTED, "k_in = %d", p.k_in);
 }
 
+template <int KIN>
+int run_init_cols(const float* src, float* out, const AttrParams& p, cudaStream_t st) {
+  constexpr int F = 1 << (2 * KIN);
+  constexpr int FPB = F >= 4096 ? 1 : 4096 / F;
+  const int64_t n_fibers = p.n_rows << (2 * p.k_out);
+  int ifast = 0;
+  for (int j = 0; j < p.k_in; ++j) ifast |= p.col_shift_in[j] == 0;
+  const int64_t blocks = (n_fibers + FPB - 1) / FPB;
+  if (blocks > 0x7fffffffLL) return set_error(CUTQC_EUNSUPPORTED, "attribution tensor too large");
+  attr_init_cols<KIN><<<(unsigned)blocks, kColThreads, 0, st>>>(src, out, p, n_fibers, ifast);
+  CUTQC_LAUNCH_CHECK("attr_init_cols");
+  return CUTQC_OK;
+}
+
+int dispatch_init_cols(const float* src, float* out, const AttrParams& p, cudaStream_t st) {
+  switch (p.k_in) {
+    case 1: return run_init_cols<1>(src, out, p, st);
+    case 2: return run_init_cols<2>(src, out, p, st);
+    case 3: return run_init_cols<3>(src, out, p, st);
+    case 4: return run_init_cols<4>(src, out, p, st);
+    case 5: return run_init_cols<5>(src, out, p, st);
+    case 6: return run_init_cols<6>(src, out, p, st);
+  }
+  return set_error(CUTQC_EUNSUPPORTED, "k_in = %d", p.k_in);
+}
+
 template <typename T>
 int dispatch_meas(const T* src, float* out, const AttrParams& p, cudaStream_t st) {
   switch (p.k_out) {
@@ -419,13 +560,19 @@ int launch_attr(const cutqc_subcircuit* s, const T* src, float* dst, float* tmp,
     CUTQC_LAUNCH_CHECK("attr_copy");
     return CUTQC_OK;
   }
+  if (s->k_in > 0 && s->k_out > 0) {
+    // both kinds of cut: the measured side first, on the variants as given
+    // (the init states stand where the bases will be), which shrinks the
+    // data from 3^k_out * 2^w to 4^k_out * 2^o values per init state; then
+    // the initialised side along the columns, from the workspace into dst
+    p.n_rows = (int64_t)1 << o;
+    int rc = dispatch_meas<T>(src, tmp, p, st);
+    if (rc) return rc;
+    return dispatch_init_cols(tmp, dst, p, st);
+  }
   if (s->k_in > 0) {
     p.n_rows = (int64_t)1 << s->w;
-    const int final_layout = s->k_out == 0;
-    int rc = dispatch_init<T>(src, final_layout ? dst : tmp, p, final_layout, st);
-    if (rc || final_layout) return rc;
-    p.n_rows = (int64_t)1 << o;
-    return dispatch_meas<float>(tmp, dst, p, st);
+    return dispatch_init<T>(src, dst, p, 1, st);
   }
   p.n_rows = (int64_t)1 << o;
   return dispatch_meas<T>(src, dst, p, st);
@@ -446,11 +593,8 @@ extern "C" int cutqc_attribute_workspace_size(const cutqc_subcircuit* s, size_t*
   if (s->k_in > kMaxKin || s->k_out > kMaxKout)
     return set_error(CUTQC_EUNSUPPORTED, "attribution supports k_in <= %d, k_out <= %d", kMaxKin, kMaxKout);
   size_t n = 0;
-  if (s->k_in > 0 && s->k_out > 0) {
-    size_t nm = 1;
-    for (int j = 0; j < s->k_out; ++j) nm *= 3;
-    n = ((size_t)1 << (2 * s->k_in)) * nm * ((size_t)1 << s->w) * sizeof(float);
-  }
+  if (s->k_in > 0 && s->k_out > 0)       // the measured side's output, [2^o][4^k] float32
+    n = ((size_t)1 << (s->w - s->k_out)) * ((size_t)1 << (2 * (s->k_in + s->k_out))) * sizeof(float);
   *bytes = n;
   return CUTQC_OK;
 }

@@ -172,6 +172,19 @@ int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precisio
         if (better) { best_a = alive[x]; best_b = alive[y]; best_share = share; best_cost = cost; }
       }
     const bool final_stage = alive.size() == 2;
+    if (!final_stage) {
+      // the operand holding the lowest open edge goes to the columns: the
+      // result's lowest index bits are then its digits, and the tensor-core
+      // GEMM stores runs of consecutive floats straight from registers
+      const TensorDesc& A = plan->tensors[best_a];
+      const TensorDesc& B = plan->tensors[best_b];
+      std::vector<int> shared2, open2;
+      std::set_intersection(A.edges.begin(), A.edges.end(), B.edges.begin(), B.edges.end(), std::back_inserter(shared2));
+      std::set_symmetric_difference(A.edges.begin(), A.edges.end(), B.edges.begin(), B.edges.end(),
+                                    std::back_inserter(open2));
+      if (!open2.empty() && std::binary_search(A.edges.begin(), A.edges.end(), open2.front()))
+        std::swap(best_a, best_b);
+    }
     if (final_stage) {
       // the operand holding the most significant output bit goes to the rows
       const TensorDesc& A = plan->tensors[best_a];

@@ -54,7 +54,8 @@ def test_host_validation_without_gpu(built):
         in_edge = [0]
         out_edge = [1]
         out_qubit = [0, 1, 2]
-    assert cutqc.cutqc_attribute_workspace_size(T) == 4 * 3 * 16 * 4
+    # the measured side's result: 2^o rows x 4^k columns of float32
+    assert cutqc.cutqc_attribute_workspace_size(T) == 2 ** 3 * 4 ** 2 * 4
 
     class U:
         w = 3

@@ -119,23 +119,43 @@ def test_features_shape_and_permutation_invariance():
 
 def test_exact_cut_is_optimal_by_enumeration():
     """The branch-and-bound cut search against plain enumeration of every
-    assignment of the two-qubit gates to 2 or 3 clusters: the same minimal
-    number of cuts under the width limit."""
+    assignment of the two-qubit gates to 2 or 3 clusters under the width
+    limit: the same minimal Eq. 2 cost, and among the clusterings of that
+    cost the same minimal contraction cost; with and without the local
+    search's cut as the starting incumbent."""
     import itertools
     from workloads import circuits as C
-    from workloads.cutting import Dag, build_cut, exact_cut
-    for c, w, ns in ((C.brickwall(6, 3, 2), 4, 2), (C.aqft(6, 1, max_dist=2), 4, 3), (C.bv(7, 2), 4, 2)):
+    from workloads.cutting import Dag, build_cut, contraction_cost, eq2_cost, exact_cut, search_cut
+    for c, w, ns in ((C.brickwall(6, 3, 2), 4, 2), (C.aqft(6, 1, max_dist=2), 4, 3), (C.bv(7, 2), 4, 2),
+                     (C.brickwall(6, 2, 5), 3, 3), (C.supremacy(2, 3, 4, 1), 3, 3)):
         nv = Dag(c).nv
         assert ns ** nv <= 200_000
         best = None
         for cl in itertools.product(range(ns), repeat=nv):
             cut = build_cut(c, list(cl), w_max=w)
-            if all(s.w <= w for s in cut.subcircuits):
-                best = cut.K if best is None else min(best, cut.K)
-        ex, full = exact_cut(c, w, ns)
-        assert full and ex is not None
-        assert ex.K == best, (c.name, ex.K, best)
-        assert all(s.w <= w for s in ex.subcircuits)
+            if all(s.w <= w for s in cut.subcircuits) and len(cut.subcircuits) <= ns + len(Dag(c).free_qubits):
+                key = (eq2_cost(cut), contraction_cost(cut))
+                best = key if best is None else min(best, key)
+        for inc in (None, search_cut(c, w, ns, restarts=2)):
+            ex, full = exact_cut(c, w, ns, incumbent=inc, max_ties=100_000)
+            assert full and ex is not None
+            assert (eq2_cost(ex), contraction_cost(ex)) == best, (c.name, eq2_cost(ex), best)
+            assert all(s.w <= w for s in ex.subcircuits)
+
+
+def test_exact_cut_bound_is_admissible():
+    """The lookahead bound never prunes the optimum: with the bound on (the
+    default) and with a node budget so large that it is exhaustive either
+    way, the same Eq. 2 cost as a run seeded with an incumbent one cut worse
+    than the optimum.  And it finishes exhaustively on a 20-qubit brick-wall
+    and a 20-qubit AQFT instance within its budget."""
+    from workloads import circuits as C
+    from workloads.cutting import eq2_cost, exact_cut, search_cut
+    for c, w, ns in ((C.brickwall(20, 4, 3), 11, 2), (C.aqft(20, 1, max_dist=2), 11, 2)):
+        ls = search_cut(c, w, ns, restarts=4)
+        ex, full = exact_cut(c, w, ns, incumbent=ls)
+        assert full, c.name
+        assert eq2_cost(ex) <= eq2_cost(ls)
 
 
 def test_local_search_reaches_exact_optimum_on_small_circuits():

@@ -39,9 +39,10 @@ def test_noalloc_attribution_matches_workspace_version():
 
 
 def test_noalloc_attribution_rejects_oversized_scratch():
-    """A subcircuit whose two-pass scratch exceeds the static array (here 16 x
-    9 x 2^16 floats = 36 MiB > 32 MiB) is refused with CUTQC_EUNSUPPORTED
-    before anything is launched: the output keeps its contents."""
+    """A subcircuit whose two-pass scratch exceeds the static array (here its
+    2^16 x 4^4 float32 measured-side result, 64 MiB > 32 MiB) is refused with
+    CUTQC_EUNSUPPORTED before anything is launched: the output keeps its
+    contents."""
     import types
     import torch
     if not torch.cuda.is_available():
@@ -49,11 +50,11 @@ def test_noalloc_attribution_rejects_oversized_scratch():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2205_05836_gb300 import cutqc as cq
-    s = types.SimpleNamespace(w=16, in_local=[0, 1], out_local=[14, 15], in_edge=[0, 1], out_edge=[2, 3],
-                              out_qubit=list(range(14)))
+    s = types.SimpleNamespace(w=18, in_local=[0, 1], out_local=[16, 17], in_edge=[0, 1], out_edge=[2, 3],
+                              out_qubit=list(range(16)))
     assert cq.cutqc_attribute_workspace_size(s) > 32 << 20
-    v = torch.zeros((16, 9, 1 << 16), dtype=torch.float32, device="cuda")
-    out = torch.full((1 << 14, 256), 7.0, dtype=torch.float32, device="cuda")
+    v = torch.zeros((16, 9, 1 << 18), dtype=torch.float32, device="cuda")
+    out = torch.full((1 << 16, 256), 7.0, dtype=torch.float32, device="cuda")
     with pytest.raises(cq.CutqcError) as e:
         cq.cutqc_attribute_noalloc(s, v, out)
     assert e.value.code == cq.EUNSUPPORTED

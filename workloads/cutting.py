@@ -521,69 +521,126 @@ def grid_orders(rows, cols):
 # exact search (branch and bound) for small circuits
 # --------------------------------------------------------------------------
 
-def exact_cut(circuit: Circuit, w_max, n_sub, max_nodes=2_000_000):
-    """Branch and bound over the clusterings of the two-qubit gates into at
-    most ``n_sub`` clusters with every width <= w_max (the two constraints of
-    the paper's cut searcher), minimising the number of cuts K, ties broken
-    by the contraction cost.  Gates are assigned in program order, so each
-    qubit's wire is extended one gate at a time: a gate placed in a cluster
-    other than its qubit's previous one cuts the wire there and opens a new
-    wire segment in that cluster (width + 1); a qubit's first gate opens its
-    original input.  Widths and cuts only grow along a branch, which gives
-    the bound.  Clusters are introduced in order (symmetry).  Returns
-    (Cut, exhaustive) -- exhaustive False when the node budget ran out first
-    (the Cut is then the best found) -- or (None, ...) when nothing fits."""
+def _eq2_from_outputs(K, outs):
+    """Eq. 2 for K cuts and the subcircuits' output counts (ascending order)."""
+    o = sorted(outs)
+    return (4 ** K) * sum(2 ** sum(o[:c]) for c in range(2, len(o) + 1))
+
+
+def exact_cut(circuit: Circuit, w_max, n_sub, max_nodes=2_000_000, incumbent=None, max_ties=64):
+    """Branch and bound for the cut the paper's MIP cut searcher finds: a
+    clustering of the two-qubit gates into at most ``n_sub`` clusters, every
+    width <= w_max (its two constraints), minimising Eq. 2, L = 4^K sum_c
+    prod_{i<=c} 2^{n_i} (``eq2_cost``); among equal L the cheaper contraction
+    (``contraction_cost``) wins.  Gates are assigned in program order, so each
+    qubit's wire grows one gate at a time: a gate placed in a cluster other
+    than its qubit's previous one cuts the wire there and opens a new wire
+    segment in that cluster (width + 1); a qubit's first gate opens its
+    original input.  Clusters are introduced in order (symmetry).  Bound: L >=
+    4^(K_now + k_ahead) 2^n for n_C >= 2, where k_ahead counts the unassigned
+    gates that are the next gate on both of their qubits while those qubits'
+    latest gates sit in different clusters (each must cut one of its two
+    wires, and no two share a wire).  ``incumbent`` (a Cut, e.g. from the
+    local search) seeds the best L so that worse branches are cut from the
+    start.  Returns (Cut, exhaustive) -- exhaustive False when the node
+    budget ran out first (the Cut is then the best found, never worse than
+    the incumbent) -- or (None, exhaustive) when nothing fits."""
     dag = Dag(circuit)
-    nv = dag.nv
-    n_free = len(dag.free_qubits)
-    best = {"K": None, "leaves": []}
+    nv, n = dag.nv, dag.n
+    free = list(dag.free_qubits)
+    nxt_of = [[-1, -1] for _ in range(nv)]       # next gate on each of v's two qubits
+    for v in range(nv):
+        for t, q in enumerate(dag.vq[v]):
+            i = dag.slot[v][q]
+            nxt_of[v][t] = dag.wire[q][i + 1] if i + 1 < len(dag.wire[q]) else -1
+    pos_on = [[dag.slot[v][q] for q in dag.vq[v]] for v in range(nv)]
+    best = {"L": None, "leaves": []}
+    if incumbent is not None and all(sb.w <= w_max for sb in incumbent.subcircuits) \
+            and len(incumbent.subcircuits) <= n_sub + len(free):
+        best["L"] = eq2_cost(incumbent)
     assign = [0] * nv
-    last = [-1] * dag.n          # cluster of each qubit's latest assigned gate
+    last = [-1] * n              # cluster of each qubit's latest assigned gate
+    done_on = [0] * n            # gates assigned on each qubit
     width = [0] * n_sub
     nodes = [0]
+    two_n = 2 ** n
 
-    def rec(v, used, cuts):
+    def ready_conflict(u):
+        if u < 0:
+            return 0
+        a, b = dag.vq[u]
+        if done_on[a] != pos_on[u][0] or done_on[b] != pos_on[u][1]:
+            return 0
+        return 1 if (last[a] >= 0 and last[b] >= 0 and last[a] != last[b]) else 0
+
+    def leaf_L(cuts, used):
+        outs = [0] * used
+        for q in range(n):
+            if last[q] >= 0:
+                outs[last[q]] += 1
+        w = list(width[:used])
+        for _ in free:          # as build_cut: the narrowest cluster with room, else a new one
+            c = min((c for c in range(len(w)) if w[c] < w_max), key=lambda c: (w[c], c), default=None)
+            if c is None:
+                w.append(0)
+                outs.append(0)
+                c = len(w) - 1
+            w[c] += 1
+            outs[c] += 1
+        return _eq2_from_outputs(cuts, outs)
+
+    def rec(v, used, cuts, ahead):
         nodes[0] += 1
         if nodes[0] > max_nodes:
             return False
-        if best["K"] is not None and cuts > best["K"]:
+        if best["L"] is not None and cuts + ahead > 0 and (4 ** (cuts + ahead)) * two_n > best["L"]:
             return True
         if v == nv:
-            if best["K"] is None or cuts < best["K"]:
-                best["K"], best["leaves"] = cuts, []
-            if len(best["leaves"]) < 64:
+            L = leaf_L(cuts, used)
+            if L is None:
+                return True
+            if best["L"] is None or L < best["L"]:
+                best["L"], best["leaves"] = L, []
+            if L == best["L"] and len(best["leaves"]) < max_ties:
                 best["leaves"].append(list(assign))
             return True
         q0, q1 = dag.vq[v]
+        before = ready_conflict(v)
         for c in range(min(used + 1, n_sub)):
             dc = 0
-            opened = []
+            opened = 0
             for q in (q0, q1):
                 if last[q] != c:
                     if last[q] >= 0:
                         dc += 1
-                    opened.append(q)
-            if width[c] + len(opened) > w_max:
+                    opened += 1
+            if width[c] + opened > w_max:
                 continue
             saved = (last[q0], last[q1])
-            width[c] += len(opened)
+            width[c] += opened
             last[q0] = last[q1] = c
+            done_on[q0] += 1
+            done_on[q1] += 1
             assign[v] = c
-            ok = rec(v + 1, max(used, c + 1), cuts + dc)
+            u0, u1 = nxt_of[v]
+            after = ready_conflict(u0) + (ready_conflict(u1) if u1 != u0 else 0)
+            ok = rec(v + 1, max(used, c + 1), cuts + dc, ahead - before + after)
+            done_on[q0] -= 1
+            done_on[q1] -= 1
             last[q0], last[q1] = saved
-            width[c] -= len(opened)
+            width[c] -= opened
             if not ok:
                 return False
         return True
 
-    exhaustive = rec(0, 0, 0) if nv else True
-    if best["K"] is None:
-        return None, exhaustive
+    exhaustive = rec(0, 0, 0, 0) if nv else True
     cands = []
     for cl in best["leaves"]:
         cut = build_cut(circuit, cl, w_max=w_max)
-        if all(s.w <= w_max for s in cut.subcircuits) and len(cut.subcircuits) <= n_sub + n_free:
-            cands.append(((cut.K, contraction_cost(cut)), cut))
+        if all(sb.w <= w_max for sb in cut.subcircuits) and len(cut.subcircuits) <= n_sub + len(free):
+            cands.append(((eq2_cost(cut), contraction_cost(cut)), cut))
+    if incumbent is not None and best["L"] is not None and eq2_cost(incumbent) <= best["L"]:
+        cands.append(((eq2_cost(incumbent), contraction_cost(incumbent)), incumbent))
     if not cands:
         return None, exhaustive
     return min(cands, key=lambda x: x[0])[1], exhaustive

@@ -200,7 +200,8 @@ def candidates(dag: Dag, w_max, count, rng, n_sub_range=None):
     a qubit order (identity, reversed, or breadth-first from a random qubit)
     with jittered block sizes; a gate joins the block of one of its qubits
     (the lower block, the higher, or that of its lower-degree qubit); then a
-    random fraction of gates moves to the block of the other qubit."""
+    random fraction of gates moves to the block of the other qubit.  All
+    candidates are drawn at once (array operations over the candidates)."""
     n = dag.n
     deg = np.array([len(dag.wire[q]) for q in range(n)])
     nv = dag.nv
@@ -208,34 +209,37 @@ def candidates(dag: Dag, w_max, count, rng, n_sub_range=None):
     lo = min(MAX_SUB - 1, max(2, -(-n // max(w_max, 1))))
     if n_sub_range is None:
         n_sub_range = (lo, min(MAX_SUB - 1, lo + 2))
-    out = np.zeros((count, nv), dtype=np.int64)
-    for i in range(count):
-        S = int(rng.integers(n_sub_range[0], n_sub_range[1] + 1))
-        kind = int(rng.integers(3))
-        if kind == 0:
-            order = list(range(n))
-        elif kind == 1:
-            order = list(range(n))[::-1]
-        else:
-            order = _bfs_order(dag, int(rng.integers(n)), rng)
-        sizes = rng.dirichlet(np.full(S, 8.0)) * n
-        bounds = np.cumsum(sizes)
-        rank = np.empty(n, dtype=np.int64)
-        rank[np.asarray(order)] = np.arange(n)
-        block = np.minimum(np.searchsorted(bounds, rank + 0.5), S - 1)
-        b0, b1 = block[vq[:, 0]], block[vq[:, 1]]
-        rule = int(rng.integers(3))
-        if rule == 0:
-            a = np.minimum(b0, b1)
-        elif rule == 1:
-            a = np.maximum(b0, b1)
-        else:
-            a = np.where(deg[vq[:, 0]] <= deg[vq[:, 1]], b0, b1)
-        p = float(rng.choice([0.0, 0.0, 0.02, 0.05, 0.1]))
-        flip = rng.random(nv) < p
-        other = np.where(a == b0, b1, b0)
-        out[i] = np.where(flip, other, a)
-    return out
+    S = rng.integers(n_sub_range[0], n_sub_range[1] + 1, size=count)
+    kind = rng.integers(3, size=count)
+    start = rng.integers(n, size=count)
+    # rank of every qubit in each candidate's order
+    ident = np.arange(n)
+    bfs_rank = {}
+    rank = np.empty((count, n), dtype=np.int64)
+    rank[kind == 0] = ident
+    rank[kind == 1] = ident[::-1]
+    for i in np.nonzero(kind == 2)[0]:
+        q = int(start[i])
+        if q not in bfs_rank:
+            r = np.empty(n, dtype=np.int64)
+            r[np.asarray(_bfs_order(dag, q, rng))] = ident
+            bfs_rank[q] = r
+        rank[i] = bfs_rank[q]
+    # block sizes: Dirichlet(8, ..., 8) over S blocks (gamma draws, masked)
+    s_max = int(S.max())
+    g = rng.gamma(8.0, size=(count, s_max)) * (np.arange(s_max)[None, :] < S[:, None])
+    bounds = np.cumsum(g / g.sum(1, keepdims=True), axis=1) * n
+    block = np.minimum((bounds[:, None, :] < rank[:, :, None] + 0.5).sum(-1), S[:, None] - 1)
+    b0 = np.take_along_axis(block, np.broadcast_to(vq[:, 0], (count, nv)), 1)
+    b1 = np.take_along_axis(block, np.broadcast_to(vq[:, 1], (count, nv)), 1)
+    rule = rng.integers(3, size=count)[:, None]
+    lower_deg = (deg[vq[:, 0]] <= deg[vq[:, 1]])[None, :]
+    a = np.where(rule == 0, np.minimum(b0, b1),
+                 np.where(rule == 1, np.maximum(b0, b1), np.where(lower_deg, b0, b1)))
+    p = rng.choice(np.array([0.0, 0.0, 0.02, 0.05, 0.1]), size=count)[:, None]
+    flip = rng.random((count, nv)) < p
+    other = np.where(a == b0, b1, b0)
+    return np.where(flip, other, a).astype(np.int64)
 
 
 def training_set(n_circuits, per_circuit, seed, n_range=(20, 60)):
