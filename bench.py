@@ -743,7 +743,8 @@ def learned_extras(dev, cq, n_circuits=10000, train_steps=4000, batch=1024):
     t0 = time.perf_counter()
     searched = search_cut(c, w_max, -(-(n + 8) // w_max), restarts=4, seed=5)
     search_s = time.perf_counter() - t0
-    cut, info = propose_cut(c, w_max, net, n_candidates=4096, n_exact=8, seed=0)
+    mlp_only, info0 = propose_cut(c, w_max, net, n_candidates=4096, n_exact=8, seed=0)
+    cut, info = propose_cut(c, w_max, net, n_candidates=4096, n_exact=8, seed=0, check_restarts=4)
     subs = cut.subcircuits
     att = [cq.cutqc_attribute(s, torch.from_numpy(simulate_variants(s)).to(dev)) for s in subs]
     M = 16
@@ -765,8 +766,10 @@ def learned_extras(dev, cq, n_circuits=10000, train_steps=4000, batch=1024):
             "train_steps": train_steps, "batch": batch, "train_ms": train_ms,
             "train_samples_per_s": train_steps * batch / (train_ms * 1e-3), "final_loss": loss,
             "val_mse": val_mse, "val_label_var": float(tv.var()), "infer_4096_ms": infer_ms,
-            "bv100": {"mlp_cut_log2_cost": math.log2(contraction_cost(cut)), "mlp_cut_K": cut.K,
-                      "mlp_seconds": info["seconds"], "feasible_candidates": info["feasible"],
+            "bv100": {"mlp_cut_log2_cost": math.log2(contraction_cost(mlp_only)), "mlp_cut_K": mlp_only.K,
+                      "mlp_seconds": info0["seconds"], "feasible_candidates": info0["feasible"],
+                      "with_search_check": {"log2_cost": math.log2(contraction_cost(cut)), "K": cut.K,
+                                            "fallback": info["fallback"], "seconds": info["seconds"]},
                       "searched_cut_log2_cost": math.log2(contraction_cost(searched)), "searched_cut_K": searched.K,
                       "search_seconds": search_s, "dd_recursions": len(jobs), "dd_seconds": dd_s,
                       "bitstring_exact": bool(exact), "p_top": float(b[top])}}

@@ -10,8 +10,10 @@ candidate is feasible when every
 subcircuit fits the width limit and its variant tensor (4^k_in * 3^k_out *
 2^w entries) stays within a size budget, since every variant has to be
 evaluated; among exactly costed candidates of equal cost the one with the
-smallest total variant volume wins.  When no candidate is feasible the local
-cut search runs instead (the fallback).
+smallest total variant volume wins.  The local cut search stays as the
+fallback: it runs when no candidate is feasible, and (``check_restarts`` >
+0) beside the network's pick, whose cut is replaced by the search's when the
+search's is cheaper in the same exact cost model.
 """
 from __future__ import annotations
 
@@ -19,12 +21,15 @@ import time
 
 import numpy as np
 
-from workloads.cutting import Dag, build_cut, search_cut
+from workloads.cutting import Dag, build_cut, contraction_cost, search_cut
 from workloads.features import LABEL_SCALE, MAX_SUB, CandidateSet, candidates
 
 
-def propose_cut(circuit, w_max, net, n_candidates=4096, n_exact=8, seed=0, max_variant_log2=26):
-    """Returns (Cut, info).  ``net`` is a trained ``cutqc.MLP``."""
+def propose_cut(circuit, w_max, net, n_candidates=4096, n_exact=8, seed=0, max_variant_log2=26, check_restarts=0):
+    """Returns (Cut, info).  ``net`` is a trained ``cutqc.MLP``.  With
+    ``check_restarts`` > 0 the local search (that many restarts) also runs
+    and wins when its cut is cheaper (info: ``fallback`` = "search cheaper");
+    info keeps the network's own pick and time beside it."""
     import torch
     t0 = time.perf_counter()
     dag = Dag(circuit)
@@ -46,7 +51,19 @@ def propose_cut(circuit, w_max, net, n_candidates=4096, n_exact=8, seed=0, max_v
     pick = min(range(len(top)), key=lambda j: (costs[j], volume[j]))
     best = int(top[pick])
     cut = build_cut(circuit, assign[best], w_max=w_max)
-    info.update(fallback=False, seconds=time.perf_counter() - t0,
+    info.update(fallback=False, seconds=time.perf_counter() - t0, mlp_seconds=time.perf_counter() - t0,
                 predicted_log2_cost=float(pred[np.searchsorted(ok, best)] * LABEL_SCALE + circuit.n),
-                exact_cost=int(costs[pick]), variant_entries=volume[pick])
+                exact_cost=int(costs[pick]), mlp_cost=int(costs[pick]), variant_entries=volume[pick])
+    if check_restarts > 0:
+        t1 = time.perf_counter()
+        lo = min(MAX_SUB - 1, max(2, -(-circuit.n // w_max)))
+        alt = search_cut(circuit, w_max, max(lo, len(cut.subcircuits)), restarts=check_restarts, seed=seed)
+        info["search_seconds"] = time.perf_counter() - t1
+        if alt is not None:
+            alt_cost = contraction_cost(alt)
+            info["search_cost"] = int(alt_cost)
+            if alt_cost < costs[pick]:
+                cut = alt
+                info.update(fallback="search cheaper", exact_cost=int(alt_cost))
+        info["seconds"] = time.perf_counter() - t0
     return cut, info

@@ -144,18 +144,26 @@ def test_exact_cut_is_optimal_by_enumeration():
 
 
 def test_exact_cut_bound_is_admissible():
-    """The lookahead bound never prunes the optimum: with the bound on (the
-    default) and with a node budget so large that it is exhaustive either
-    way, the same Eq. 2 cost as a run seeded with an incumbent one cut worse
-    than the optimum.  And it finishes exhaustively on a 20-qubit brick-wall
-    and a 20-qubit AQFT instance within its budget."""
+    """The lookahead bound never prunes the optimum: with and without it the
+    same Eq. 2 cost on small instances.  With the local search's cut as the
+    incumbent the search finishes exhaustively on 20- to 40-qubit instances
+    (their optimum is then proven), never returns a costlier cut than the
+    incumbent, and on a 40-qubit BV instance finds a cut with fewer cuts than
+    the local search."""
     from workloads import circuits as C
     from workloads.cutting import eq2_cost, exact_cut, search_cut
-    for c, w, ns in ((C.brickwall(20, 4, 3), 11, 2), (C.aqft(20, 1, max_dist=2), 11, 2)):
+    for c, w, ns in ((C.brickwall(8, 4, 1), 6, 2), (C.aqft(8, 2, max_dist=2), 5, 2), (C.supremacy(2, 4, 5, 2), 5, 2)):
+        a, fa = exact_cut(c, w, ns)
+        b, fb = exact_cut(c, w, ns, lookahead=False)
+        assert fa and fb and eq2_cost(a) == eq2_cost(b), c.name
+    for c, w, ns in ((C.brickwall(20, 4, 3), 12, 2), (C.aqft(20, 1, max_dist=2), 11, 2),
+                     (C.supremacy(4, 5, 6, 1), 12, 2), (C.aqft(40, 2, max_dist=2), 21, 2), (C.bv(40, 3), 11, 4)):
         ls = search_cut(c, w, ns, restarts=4)
-        ex, full = exact_cut(c, w, ns, incumbent=ls)
+        ex, full = exact_cut(c, w, ns, incumbent=ls, max_nodes=300_000)
         assert full, c.name
-        assert eq2_cost(ex) <= eq2_cost(ls)
+        assert eq2_cost(ex) <= eq2_cost(ls), c.name
+        if c.name.startswith("bv"):
+            assert ex.K < ls.K
 
 
 def test_local_search_reaches_exact_optimum_on_small_circuits():
@@ -168,3 +176,28 @@ def test_local_search_reaches_exact_optimum_on_small_circuits():
         ex, full = exact_cut(c, w, ns)
         assert full
         assert search_cut(c, w, ns, restarts=4).K == ex.K, c.name
+
+
+def test_scorer_falls_back_to_the_search_when_it_is_cheaper():
+    """The learned proposal keeps the local search as its fallback: with a
+    stand-in scorer that ranks the candidates worst first (by their Eq. 2
+    feature, negated) the network's pick is costlier than the search's cut,
+    so the search's cut is returned; with the check off the network's pick is
+    returned as it is.  No GPU: the stand-in scores on the CPU."""
+    import torch
+    from paper_2205_05836_gb300.scorer import propose_cut
+    from workloads import circuits as C
+    from workloads.cutting import contraction_cost
+
+    class WorstFirst:
+        device = "cpu"
+
+        def forward(self, x):
+            return -x[:, 6]          # column 6: log2 Eq. 2 of the candidate (scaled)
+    c, w = C.aqft(30, 1, max_dist=2), 11
+    mlp_cut, info0 = propose_cut(c, w, WorstFirst(), n_candidates=512, n_exact=1, seed=0)
+    assert info0["fallback"] is False and contraction_cost(mlp_cut) == info0["mlp_cost"]
+    cut, info = propose_cut(c, w, WorstFirst(), n_candidates=512, n_exact=1, seed=0, check_restarts=2)
+    assert info["fallback"] == "search cheaper"
+    assert info["search_cost"] < info["mlp_cost"]
+    assert contraction_cost(cut) == info["search_cost"] == info["exact_cost"]

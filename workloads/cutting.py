@@ -527,7 +527,7 @@ def _eq2_from_outputs(K, outs):
     return (4 ** K) * sum(2 ** sum(o[:c]) for c in range(2, len(o) + 1))
 
 
-def exact_cut(circuit: Circuit, w_max, n_sub, max_nodes=2_000_000, incumbent=None, max_ties=64):
+def exact_cut(circuit: Circuit, w_max, n_sub, max_nodes=2_000_000, incumbent=None, max_ties=64, lookahead=True):
     """Branch and bound for the cut the paper's MIP cut searcher finds: a
     clustering of the two-qubit gates into at most ``n_sub`` clusters, every
     width <= w_max (its two constraints), minimising Eq. 2, L = 4^K sum_c
@@ -542,7 +542,8 @@ def exact_cut(circuit: Circuit, w_max, n_sub, max_nodes=2_000_000, incumbent=Non
     latest gates sit in different clusters (each must cut one of its two
     wires, and no two share a wire).  ``incumbent`` (a Cut, e.g. from the
     local search) seeds the best L so that worse branches are cut from the
-    start.  Returns (Cut, exhaustive) -- exhaustive False when the node
+    start (``lookahead=False`` drops k_ahead from the bound).  Returns
+    (Cut, exhaustive) -- exhaustive False when the node
     budget ran out first (the Cut is then the best found, never worse than
     the incumbent) -- or (None, exhaustive) when nothing fits."""
     dag = Dag(circuit)
@@ -624,7 +625,7 @@ def exact_cut(circuit: Circuit, w_max, n_sub, max_nodes=2_000_000, incumbent=Non
             assign[v] = c
             u0, u1 = nxt_of[v]
             after = ready_conflict(u0) + (ready_conflict(u1) if u1 != u0 else 0)
-            ok = rec(v + 1, max(used, c + 1), cuts + dc, ahead - before + after)
+            ok = rec(v + 1, max(used, c + 1), cuts + dc, (ahead - before + after) if lookahead else 0)
             done_on[q0] -= 1
             done_on[q1] -= 1
             last[q0], last[q1] = saved
