@@ -413,6 +413,18 @@ def run(args):
         attribute_all()
         reconstruct()
 
+    # the contraction's work-item size, autotuned on this data (outputs must
+    # be bit-identical across the candidates); set before the graphs capture
+    # the launches
+    tuned = None
+    if ws == 1 and prec != cq.PREC_FP32_SIMT:
+        from paper_2205_05836_gb300.tune import tune_fd
+        attribute_all()
+        best, trials = tune_fd(subs, att, prec, out=out, ws=fd_ws)
+        tuned = {"tiles_per_item": best, "trials_ms": {str(t): round(m, 4) for m, t, same in trials if same},
+                 "all_identical": all(same for _, _, same in trials)}
+        _log(f"work-item size tuned: {best}")
+
     # one step = one replay of a CUDA graph holding every launch of the step
     # (host argument checks run once, at capture); the library's launch
     # counter across the capture gives the kernels per step
@@ -564,6 +576,7 @@ def run(args):
             "config": {"workload": WORKLOAD, "n_qubits": w.n, "cuts": w.K,
                        "subcircuit_widths": [s.w for s in subs], "subcircuit_outputs": [s.o for s in subs],
                        "last_contraction": [rows, cols, k_last], "precision": args.precision,
+                       "tuned": tuned,
                        "l2": "output 16 GiB > L2 each step; no flush",
                        "parallelism": f"{ws} rank(s), each writing rows [{r0}, {r1}) of the last contraction"
                                       if ws > 1 else "one GPU"},
@@ -663,6 +676,9 @@ def fd_two_sub_extras(dev, cq, steps=10, warmup=3):
             cq.cutqc_attribute(s, v, out=a, ws=b)
         total.zero_()
         cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_KRON, cq.PREC_FP16X3_TC, out=out, sum_out=total, ws=fws)
+    from paper_2205_05836_gb300.tune import tune_fd
+    step()
+    best, _ = tune_fd(subs, att, cq.PREC_FP16X3_TC, out=out, ws=fws)
     g = _graph(step, stream, warmup)
     g.replay()
     torch.cuda.synchronize()
@@ -676,11 +692,12 @@ def fd_two_sub_extras(dev, cq, steps=10, warmup=3):
         torch.cuda.synchronize()
         gemm.append(gs.elapsed_time(ge))
     gemm_ms = statistics.median(gemm)
+    cq.cutqc_fd_set_tiles_per_item(0)
     pk = peaks()
     M, N = 1 << subs[0].o, 1 << subs[1].o
     Kg = 4 ** w.K
     gbytes = 4.0 * n_out + 4.0 * Kg * (M + N)
-    return {"workload": TWO_SUB_WORKLOAD, "n_qubits": w.n, "cuts": w.K, "gemm": [M, N, Kg],
+    return {"workload": TWO_SUB_WORKLOAD, "n_qubits": w.n, "cuts": w.K, "gemm": [M, N, Kg], "tiles_per_item": best,
             "ms_per_step": ms, "probs_per_s": n_out / (ms * 1e-3), "sum_p_error": abs(total.item() - 1.0),
             "roofline": {"bound": "hbm", "kernel": "tc_pair_gemm_kernel, one launch", "kernel_ms": gemm_ms,
                          "algorithmic_bytes": gbytes, "achieved": gbytes / (gemm_ms * 1e-3) / 1e9,
@@ -916,7 +933,9 @@ def dd_batch_extras(dev, cq, runs, M, R, T, tot_bins, reps):
     return {"ms": ms, "bins_per_s": tot_bins / (ms * 1e-3), "options": opt, "phases": info["phases"],
             "ops": info["ops"], "ctas": info["ctas"], "matches_level_by_level": bool(same),
             "device_status": cq.cutqc_device_status(), "clocks": clk.summary(),
-            "tuning_ms": {f"{o['ctas_per_sm']}/{o['topk_chunk']}": round(t, 4) for t, o, ok in trials if ok},
+            "tuning_ms": {f"{o['ctas_per_sm']}/{o['topk_chunk']}/{o['narrow_max_n']}": round(t, 4)
+                          for t, o, ok in trials if ok},
+            "tuning_key": "ctas_per_sm/topk_chunk/narrow_max_n",
             "gpu_launches_per_replay": 1,
             "note": "one cooperative launch (and one memset) for all levels of the three circuits; "
                     "grid barriers between phases"}

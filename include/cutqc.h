@@ -184,6 +184,13 @@ int cutqc_fd_shape(int n_sub, const cutqc_subcircuit* s, int64_t* rows, int64_t*
  * by the caller; null, null cancels.  Errors: CUTQC_EINVAL if only one event
  * is given.                                                                 */
 int cutqc_fd_timing_events(void* start_event, void* stop_event);
+/* Launch shape of the tensor-core contraction on SM pairs (process-wide; no
+ * paper counterpart): each pair takes work items of one 256-row block of the
+ * row operand and up to this many consecutive 128-column tiles (0, the
+ * default: chosen per launch to balance the pairs).  Results do not depend
+ * on it, only the time and the order of the float64 total's additions.  For
+ * autotuning.  Errors: CUTQC_EINVAL outside 0..4096.                       */
+int cutqc_fd_set_tiles_per_item(int tiles_per_item);
 int cutqc_reconstruct_fd_workspace_size(int n_sub, const cutqc_subcircuit* s, int precision,
                                         size_t* bytes);
 int cutqc_reconstruct_fd(int n_sub, const cutqc_subcircuit* s, const float* const* attributed_dev,
@@ -334,7 +341,8 @@ int cutqc_dd_run_async(int n_sub, const cutqc_subcircuit* s, const float* const*
  * 256, default 2048); ctas caps the grid (default: every CTA that fits at
  * once);
  * ctas_per_sm (2..4, default 3) the CTAs per SM that the kernel's registers
- * are budgeted for (more resident warps, fewer registers each).
+ * are budgeted for (more resident warps, fewer registers each); narrow_max_n
+ * the tile shape of the contraction steps (below).
  * cutqc_dd_batch_create validates the runs, lays out `ws_dev` (at least
  * cutqc_dd_batch_workspace_size bytes, 256-byte aligned, owned by the caller
  * and kept alive and untouched while the handle is used) and writes the
@@ -365,6 +373,12 @@ typedef struct cutqc_dd_batch_options {
   int32_t topk_chunk;
   int32_t ctas;
   int32_t ctas_per_sm;
+  int32_t narrow_max_n;   /* GEMM tiles of the bin reconstruction: contraction
+                             steps of at most this many columns take 256 x 16
+                             tiles, the others 64 x 64 (16, 32 or 64; 0:
+                             default 16; -1: never 256 x 16).  Results are the
+                             same for every setting (each bin is the same
+                             fmaf chain over k).                          */
 } cutqc_dd_batch_options;
 
 typedef struct cutqc_dd_batch cutqc_dd_batch;

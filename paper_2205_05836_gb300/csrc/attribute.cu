@@ -60,11 +60,16 @@ __device__ __forceinline__ void init_map4(const float (&p)[4], float (&o)[4]) {
   o[3] = p[0] - p[1];
 }
 
-// Rows per CTA of the measured-side pass: as many as fit a 96 KiB padded
-// [F][R + 1] block (two CTAs per SM), at most 32.
+// Rows per CTA of the measured-side pass: as many as fit a padded [F][R + 1]
+// block of 48 KiB (four CTAs per SM, so that some CTAs load while others
+// combine and store), at most 32; when that leaves fewer than 8 rows (runs
+// of loads too short to coalesce), as many as fit 96 KiB (two CTAs per SM).
+__host__ __device__ constexpr int rows_within(int F, int bytes) {
+  return F * 33 * 4 <= bytes ? 32 : F * 17 * 4 <= bytes ? 16 : F * 9 * 4 <= bytes ? 8
+       : F * 5 * 4 <= bytes ? 4 : F * 3 * 4 <= bytes ? 2 : 1;
+}
 __host__ __device__ constexpr int meas_rows_for(int F) {
-  return F * 33 * 4 <= 96 * 1024 ? 32 : F * 17 * 4 <= 96 * 1024 ? 16 : F * 9 * 4 <= 96 * 1024 ? 8
-       : F * 5 * 4 <= 96 * 1024 ? 4 : F * 3 * 4 <= 96 * 1024 ? 2 : 1;
+  return rows_within(F, 48 * 1024) >= 8 ? rows_within(F, 48 * 1024) : rows_within(F, 96 * 1024);
 }
 // Rows per CTA of the initialised-side pass: as many as fit a 72 KiB padded
 // [F][R + 1] block (three CTAs per SM), at most 64 (512-byte runs of float64).
@@ -196,7 +201,7 @@ attr_init_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p,
 // (blockIdx.y).
 template <typename T, int KOUT>
 __global__ void __launch_bounds__(kMeasThreads)
-attr_meas_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p) {
+attr_meas_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, int staged) {
   constexpr int NM = pow3(KOUT);
   constexpr int F = NM << KOUT;
   constexpr int R = meas_rows_for(F);
@@ -274,32 +279,35 @@ attr_meas_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p)
       const float v = vb[b * RS];
       acc += (__popc(b & mask) & 1) ? -v : v;
     }
-    dst[(x0 + r) * C + (cin | colm[g])] = acc;
+    // staged: W[init index][x][g], contiguous for the CTA (the initialised
+    // side follows); else the attributed layout
+    if (staged) dst[((int64_t)dinit * p.n_rows + x0 + r) * G + g] = acc;
+    else dst[(x0 + r) * C + (cin | colm[g])] = acc;
   }
 }
 
-// Initialised-side map along the columns, for subcircuits with both kinds of
-// cut: the measured-side pass has already produced the attributed layout
-// [2^o][4^k], but with the init cuts' digits still holding their states
-// (|0>, |1>, |+>, |+i>) rather than bases.  For every row x and every value
-// of the measured-cut digits ("fiber"), the 4^KIN values at the init digits'
-// column positions are mapped to bases by the per-cut 4x4 map (init_map4),
-// digit pair by digit pair.  A CTA stages FPB fibers in shared memory (each
-// padded by one float) and writes them to dst at the same positions.  Loads
-// and stores walk the fiber's elements fastest when an init digit holds
-// column bit 0 (ifast), else the fibers (then the measured digits hold it).
+// Initialised-side map for subcircuits with both kinds of cut.  The
+// measured-side pass left W[s][x][mu] in the workspace (s: the init cuts'
+// states |0>, |1>, |+>, |+i> as digits, x: output row, mu: the measured cuts'
+// bases as digits, dense).  Every fiber W[.][x][mu] over the 4^KIN states is
+// mapped to bases by the per-cut 4x4 map (init_map4), digit pair by digit
+// pair, and written to the attributed layout A[x][col], col holding each
+// cut's digit at its edge's rank.  A CTA takes P consecutive (x, mu) and all
+// states: loads are runs of P floats, fibers sit in shared memory as
+// [P][F + 1] (conflict-free both ways), and stores walk the fiber fastest
+// when an init digit holds column bit 0 (ifast), else the (x, mu) index.
 constexpr int kColThreads = 256;
 
 template <int KIN>
 __global__ void __launch_bounds__(kColThreads)
 attr_init_cols(const float* __restrict__ src, float* __restrict__ dst, AttrParams p, int64_t n_fibers, int ifast) {
   constexpr int F = 1 << (2 * KIN);
-  constexpr int FPB = F >= 4096 ? 1 : 4096 / F;     // 16 KiB of values per CTA
+  constexpr int P = F >= 4096 ? 1 : (4096 / F > 64 ? 64 : 4096 / F);   // fibers per CTA
   constexpr int FS = F + 1;
-  __shared__ float buf[FPB * FS];
-  __shared__ int64_t fbase[FPB];
+  __shared__ float buf[P * FS];
+  __shared__ int64_t fbase[P];
   __shared__ int ioff[F];
-  const int64_t f0 = (int64_t)blockIdx.x * FPB;
+  const int64_t f0 = (int64_t)blockIdx.x * P;
   const int64_t C = (int64_t)1 << (2 * p.k);
   const int mdig = 2 * p.k_out;
   for (int i = threadIdx.x; i < F; i += kColThreads) {
@@ -308,7 +316,7 @@ attr_init_cols(const float* __restrict__ src, float* __restrict__ dst, AttrParam
     for (int j = 0; j < KIN; ++j) off |= ((i >> (2 * j)) & 3) << p.col_shift_in[j];
     ioff[i] = off;
   }
-  for (int i = threadIdx.x; i < FPB; i += kColThreads) {
+  for (int i = threadIdx.x; i < P; i += kColThreads) {
     const int64_t f = f0 + i;
     const int64_t x = f >> mdig;
     const int mu = (int)(f & ((1 << mdig) - 1));
@@ -316,25 +324,19 @@ attr_init_cols(const float* __restrict__ src, float* __restrict__ dst, AttrParam
     for (int j = 0; j < p.k_out; ++j) moff |= ((mu >> (2 * j)) & 3) << p.col_shift_out[j];
     fbase[i] = x * C + moff;
   }
-  __syncthreads();
-  auto elem = [&](int i, int& fl, int& io) {
-    if (ifast) { fl = i / F; io = i % F; } else { io = i / FPB; fl = i % FPB; }
-  };
-  for (int i0 = 0; i0 < FPB * F; i0 += kColThreads * kBatch) {
+  // loads: state s, fiber pl (pl fastest: runs of P consecutive floats)
+  for (int i0 = 0; i0 < P * F; i0 += kColThreads * kBatch) {
     float v[kBatch];
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
       const int i = i0 + u * kColThreads + threadIdx.x;
-      int fl, io;
-      elem(i, fl, io);
-      v[u] = (i < FPB * F && f0 + fl < n_fibers) ? __ldg(src + fbase[fl] + ioff[io]) : 0.f;
+      const int sidx = i / P, pl = i % P;
+      v[u] = (i < P * F && f0 + pl < n_fibers) ? __ldg(src + (int64_t)sidx * n_fibers + f0 + pl) : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
       const int i = i0 + u * kColThreads + threadIdx.x;
-      int fl, io;
-      elem(i, fl, io);
-      if (i < FPB * F) buf[fl * FS + io] = v[u];
+      if (i < P * F) buf[(i % P) * FS + i / P] = v[u];
     }
   }
   __syncthreads();
@@ -342,7 +344,7 @@ attr_init_cols(const float* __restrict__ src, float* __restrict__ dst, AttrParam
   for (int j = 0; j < KIN; j += 2) {
     if (j + 1 < KIN) {
       constexpr int groups = F >> 4;
-      for (int it = threadIdx.x; it < groups * FPB; it += kColThreads) {
+      for (int it = threadIdx.x; it < groups * P; it += kColThreads) {
         const int grp = it % groups, fl = it / groups;
         const int lowmask = (1 << (2 * j)) - 1;
         const int base_f = (grp & lowmask) | ((grp >> (2 * j)) << (2 * j + 4));
@@ -369,7 +371,7 @@ attr_init_cols(const float* __restrict__ src, float* __restrict__ dst, AttrParam
       }
     } else {
       constexpr int groups = F >> 2;
-      for (int it = threadIdx.x; it < groups * FPB; it += kColThreads) {
+      for (int it = threadIdx.x; it < groups * P; it += kColThreads) {
         const int grp = it % groups, fl = it / groups;
         const int lowmask = (1 << (2 * j)) - 1;
         const int base_f = (grp & lowmask) | ((grp >> (2 * j)) << (2 * j + 2));
@@ -384,9 +386,9 @@ attr_init_cols(const float* __restrict__ src, float* __restrict__ dst, AttrParam
     }
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < FPB * F; i += kColThreads) {
+  for (int i = threadIdx.x; i < P * F; i += kColThreads) {
     int fl, io;
-    elem(i, fl, io);
+    if (ifast) { fl = i / F; io = i % F; } else { io = i / P; fl = i % P; }
     if (f0 + fl < n_fibers) dst[fbase[fl] + ioff[io]] = buf[fl * FS + io];
   }
 }
@@ -486,13 +488,13 @@ int run_init(const T* src, float* out, const AttrParams& p, int final_layout, cu
 }
 
 template <typename T, int KOUT>
-int run_meas(const T* src, float* out, const AttrParams& p, cudaStream_t st) {
+int run_meas(const T* src, float* out, const AttrParams& p, int staged, cudaStream_t st) {
   constexpr int F = pow3(KOUT) << KOUT;
   constexpr int R = meas_rows_for(F);
   const size_t smem = meas_smem<T, KOUT>();
   dim3 grid((unsigned)((p.n_rows + R - 1) / R), 1u << (2 * p.k_in));
   CUTQC_CUDA_TRY(set_max_smem((const void*)attr_meas_pass<T, KOUT>));
-  attr_meas_pass<T, KOUT><<<grid, kMeasThreads, smem, st>>>(src, out, p);
+  attr_meas_pass<T, KOUT><<<grid, kMeasThreads, smem, st>>>(src, out, p, staged);
   CUTQC_LAUNCH_CHECK("attr_meas_pass");
   return CUTQC_OK;
 }
@@ -513,11 +515,11 @@ int dispatch_init(const T* src, float* out, const AttrParams& p, int final_layou
 template <int KIN>
 int run_init_cols(const float* src, float* out, const AttrParams& p, cudaStream_t st) {
   constexpr int F = 1 << (2 * KIN);
-  constexpr int FPB = F >= 4096 ? 1 : 4096 / F;
+  constexpr int P = F >= 4096 ? 1 : (4096 / F > 64 ? 64 : 4096 / F);
   const int64_t n_fibers = p.n_rows << (2 * p.k_out);
   int ifast = 0;
   for (int j = 0; j < p.k_in; ++j) ifast |= p.col_shift_in[j] == 0;
-  const int64_t blocks = (n_fibers + FPB - 1) / FPB;
+  const int64_t blocks = (n_fibers + P - 1) / P;
   if (blocks > 0x7fffffffLL) return set_error(CUTQC_EUNSUPPORTED, "attribution tensor too large");
   attr_init_cols<KIN><<<(unsigned)blocks, kColThreads, 0, st>>>(src, out, p, n_fibers, ifast);
   CUTQC_LAUNCH_CHECK("attr_init_cols");
@@ -537,13 +539,13 @@ int dispatch_init_cols(const float* src, float* out, const AttrParams& p, cudaSt
 }
 
 template <typename T>
-int dispatch_meas(const T* src, float* out, const AttrParams& p, cudaStream_t st) {
+int dispatch_meas(const T* src, float* out, const AttrParams& p, int staged, cudaStream_t st) {
   switch (p.k_out) {
-    case 1: return run_meas<T, 1>(src, out, p, st);
-    case 2: return run_meas<T, 2>(src, out, p, st);
-    case 3: return run_meas<T, 3>(src, out, p, st);
-    case 4: return run_meas<T, 4>(src, out, p, st);
-    case 5: return run_meas<T, 5>(src, out, p, st);
+    case 1: return run_meas<T, 1>(src, out, p, staged, st);
+    case 2: return run_meas<T, 2>(src, out, p, staged, st);
+    case 3: return run_meas<T, 3>(src, out, p, staged, st);
+    case 4: return run_meas<T, 4>(src, out, p, staged, st);
+    case 5: return run_meas<T, 5>(src, out, p, staged, st);
   }
   return set_error(CUTQC_EUNSUPPORTED, "k_out = %d", p.k_out);
 }
@@ -566,7 +568,7 @@ int launch_attr(const cutqc_subcircuit* s, const T* src, float* dst, float* tmp,
     // data from 3^k_out * 2^w to 4^k_out * 2^o values per init state; then
     // the initialised side along the columns, from the workspace into dst
     p.n_rows = (int64_t)1 << o;
-    int rc = dispatch_meas<T>(src, tmp, p, st);
+    int rc = dispatch_meas<T>(src, tmp, p, 1, st);
     if (rc) return rc;
     return dispatch_init_cols(tmp, dst, p, st);
   }
@@ -575,7 +577,7 @@ int launch_attr(const cutqc_subcircuit* s, const T* src, float* dst, float* tmp,
     return dispatch_init<T>(src, dst, p, 1, st);
   }
   p.n_rows = (int64_t)1 << o;
-  return dispatch_meas<T>(src, dst, p, st);
+  return dispatch_meas<T>(src, dst, p, 0, st);
 }
 
 }  // namespace

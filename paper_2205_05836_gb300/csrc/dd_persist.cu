@@ -385,6 +385,7 @@ struct BatchOpts {
   int topk_chunk = kTopkChunkDefault;
   int ctas = 0;   // 0: every CTA that fits at once
   int ctas_per_sm = kCtasPerSmDefault;
+  int narrow_max_n = SGN_BN;   // contraction steps of at most this many columns take 256 x 16 tiles
 };
 
 int read_opts(const cutqc_dd_batch_options* o, BatchOpts* b) {
@@ -397,6 +398,10 @@ int read_opts(const cutqc_dd_batch_options* o, BatchOpts* b) {
   if (o->ctas < 0) return set_error(CUTQC_EINVAL, "ctas must be >= 0");
   if (o->ctas_per_sm != 0 && (o->ctas_per_sm < 2 || o->ctas_per_sm > 4))
     return set_error(CUTQC_EINVAL, "ctas_per_sm must be 0 or 2..4");
+  if (o->narrow_max_n != 0 && o->narrow_max_n != -1 && o->narrow_max_n != 16 && o->narrow_max_n != 32 &&
+      o->narrow_max_n != 64)
+    return set_error(CUTQC_EINVAL, "narrow_max_n must be 0 (default), -1 (never), 16, 32 or 64");
+  if (o->narrow_max_n) b->narrow_max_n = o->narrow_max_n < 0 ? 0 : o->narrow_max_n;
   if (o->ctas_per_sm) b->ctas_per_sm = o->ctas_per_sm;
   if (o->merge_ctas) b->merge_ctas = o->merge_ctas;
   if (o->topk_chunk) b->topk_chunk = o->topk_chunk;
@@ -624,7 +629,7 @@ int build_program(int n_runs, const cutqc_dd_run_desc* runs, const BatchOpts& op
         go.mask_n = stg.mask_n;
         go.m_shift = mask_contig_shift(stg.mask_m);
         go.n_contig = mask_is_low(stg.mask_n);
-        go.narrow = stg.N <= SGN_BN;
+        go.narrow = stg.N <= opt.narrow_max_n;
         const int64_t tm = go.narrow ? SGN_BM : SG64_BM, tn = go.narrow ? SGN_BN : SG64_BN;
         const int64_t gm = (stg.M + tm - 1) / tm, gn = (stg.N + tn - 1) / tn;
         if (gm * gn * nj > 0x3fffffff) return set_error(CUTQC_EUNSUPPORTED, "run %d: too many GEMM tiles", r);

@@ -244,16 +244,26 @@ int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precisio
       R.pos = B.pos;
       R.pos.insert(R.pos.end(), A.pos.begin(), A.pos.end());
     } else {
+      // result rows above the open digits: the operand whose rows hold the
+      // lower output positions takes the lower row bits (whichever operand
+      // is in the GEMM's rows), so that a later step gathers whole rows in
+      // order
       const int E2 = 2 * (int)uni_open.size();
+      const int min_a = A.o ? *std::min_element(A.pos.begin(), A.pos.end()) : 1 << 30;
+      const int min_b = B.o ? *std::min_element(B.pos.begin(), B.pos.end()) : 1 << 30;
+      const bool a_low = min_a < min_b;
+      const int base_a = E2 + (a_low ? 0 : B.o), base_b = E2 + (a_low ? A.o : 0);
       uint64_t mm = 0, mn = 0;
-      for (int b = 0; b < A.o; ++b) mm |= (uint64_t)1 << (E2 + B.o + b);
-      for (int b = 0; b < B.o; ++b) mn |= (uint64_t)1 << (E2 + b);
+      for (int b = 0; b < A.o; ++b) mm |= (uint64_t)1 << (base_a + b);
+      for (int b = 0; b < B.o; ++b) mn |= (uint64_t)1 << (base_b + b);
       mm |= digit_mask(uni_open, open_a);
       mn |= digit_mask(uni_open, open_b);
       st.mask_m = mm;
       st.mask_n = mn;
-      R.pos = B.pos;
-      R.pos.insert(R.pos.end(), A.pos.begin(), A.pos.end());
+      const TensorDesc& lo_t = a_low ? A : B;
+      const TensorDesc& hi_t = a_low ? B : A;
+      R.pos = lo_t.pos;
+      R.pos.insert(R.pos.end(), hi_t.pos.begin(), hi_t.pos.end());
     }
     if (precision != CUTQC_PREC_FP32_SIMT) {
       st.Kp = (int64_t)align_up((size_t)st.K, 64);

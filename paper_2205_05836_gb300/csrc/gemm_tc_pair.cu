@@ -51,6 +51,7 @@
 #include "tc_ptx.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <set>
 
@@ -611,6 +612,9 @@ int make_map(CUtensorMap* map, const __half* base, int64_t rows, int64_t Kp, int
   return CUTQC_OK;
 }
 
+// Tiles per work item set by cutqc_fd_set_tiles_per_item (0: chosen below).
+std::atomic<int> g_tiles_per_item{0};
+
 // Tiles per work item: the fewest tile slots on the busiest pair, counting
 // an A load as about one tile of time.
 int64_t pick_tiles_per_item(int64_t num_mp, int64_t num_nt, int64_t pairs) {
@@ -628,6 +632,12 @@ int64_t pick_tiles_per_item(int64_t num_mp, int64_t num_nt, int64_t pairs) {
 }  // namespace
 
 bool tc_pair_supported(int64_t Kp) { return Kp > 0 && Kp % BK == 0 && Kp / BK <= MAX_KB; }
+
+int set_pair_tiles_per_item(int t) {
+  if (t < 0 || t > 4096) return set_error(CUTQC_EINVAL, "tiles per item must be in 0..4096");
+  g_tiles_per_item.store(t, std::memory_order_relaxed);
+  return CUTQC_OK;
+}
 
 int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
                         uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st,
@@ -654,7 +664,9 @@ int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, floa
   args.num_mp = (int)num_mp;
   args.num_nt = (b.rows + BN - 1) / BN;
   const int64_t pairs_avail = std::max(1, sm_count() / 2);
-  args.tiles_per_item = pick_tiles_per_item(num_mp, args.num_nt, pairs_avail);
+  const int forced = g_tiles_per_item.load(std::memory_order_relaxed);
+  args.tiles_per_item = forced > 0 ? std::min<int64_t>(forced, args.num_nt)
+                                   : pick_tiles_per_item(num_mp, args.num_nt, pairs_avail);
   args.num_items = num_mp * ((args.num_nt + args.tiles_per_item - 1) / args.tiles_per_item);
   args.alpha = alpha;
   args.mask_m = mask_m;
@@ -696,3 +708,7 @@ int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, floa
 }
 
 }  // namespace cutqc
+
+extern "C" int cutqc_fd_set_tiles_per_item(int tiles_per_item) {
+  return cutqc::set_pair_tiles_per_item(tiles_per_item);
+}

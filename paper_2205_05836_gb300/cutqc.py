@@ -201,6 +201,11 @@ def cutqc_fd_timing_events(start=None, stop=None):
     _check(lib().cutqc_fd_timing_events(c_void_p(start.cuda_event), c_void_p(stop.cuda_event)))
 
 
+def cutqc_fd_set_tiles_per_item(tiles_per_item=0):
+    """Work-item size of the tensor-core contraction (0: automatic)."""
+    _check(lib().cutqc_fd_set_tiles_per_item(c_int(int(tiles_per_item))))
+
+
 def cutqc_reconstruct_fd_workspace_size(subs, precision):
     arr, keep = _subs(subs)
     n = c_size_t(0)
@@ -382,7 +387,8 @@ class _DDRunDesc(ctypes.Structure):
 
 
 class DDBatchOptions(ctypes.Structure):
-    _fields_ = [("merge_ctas", c_int32), ("topk_chunk", c_int32), ("ctas", c_int32), ("ctas_per_sm", c_int32)]
+    _fields_ = [("merge_ctas", c_int32), ("topk_chunk", c_int32), ("ctas", c_int32), ("ctas_per_sm", c_int32),
+                ("narrow_max_n", c_int32)]
 
 
 def _batch_descs(runs):
@@ -404,7 +410,8 @@ def _batch_opts(options):
     if options is None:
         return None
     return ctypes.byref(DDBatchOptions(int(options.get("merge_ctas", 0)), int(options.get("topk_chunk", 0)),
-                                       int(options.get("ctas", 0)), int(options.get("ctas_per_sm", 0))))
+                                       int(options.get("ctas", 0)), int(options.get("ctas_per_sm", 0)),
+                                       int(options.get("narrow_max_n", 0))))
 
 
 def cutqc_dd_batch_workspace_size(runs, options=None):

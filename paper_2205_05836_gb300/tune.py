@@ -80,13 +80,17 @@ def tune_dd(subs, attributed, n, M, R, T, max_jobs=64, reps=5, candidates=None, 
 # ------------------------------------------------- the persistent DD batch
 # One launch for several circuits (cutqc_dd_batch_*): the shape options are
 # the merge slicing (merge_ctas), the bins per top-T task (topk_chunk), the
-# grid (ctas, 0 = every CTA that fits at once) and the CTAs per SM the
-# kernel's registers are budgeted for (ctas_per_sm).  Each candidate builds the
+# grid (ctas, 0 = every CTA that fits at once), the CTAs per SM the
+# kernel's registers are budgeted for (ctas_per_sm) and the GEMM tile shape of
+# the contraction steps (narrow_max_n).  Each candidate builds the
 # batch over the caller's runs (fresh output buffers), replays it as a
 # captured graph, and is kept only if its records and bins match the first
 # candidate's.
 
-BATCH_CANDIDATES = [dict(merge_ctas=1024, topk_chunk=c, ctas=0, ctas_per_sm=r) for r in (3, 2, 4) for c in (2048, 4096)]
+# tile shapes: narrow_max_n = the most columns a contraction step may have
+# and still take 256 x 16 tiles (-1: every step takes 64 x 64 tiles)
+BATCH_CANDIDATES = [dict(merge_ctas=1024, topk_chunk=c, ctas=0, ctas_per_sm=r, narrow_max_n=nm)
+                    for r in (3, 2, 4) for c in (2048, 4096) for nm in (16, -1, 64)]
 
 
 def batch_shape_key(runs):
@@ -123,5 +127,54 @@ def tune_dd_batch(runs, reps=5, candidates=None, atol=1e-6):
         results.append((ms, dict(opt), ok))
         batch.close()
     best = min((r for r in results if r[2]), key=lambda r: r[0])[1]
+    _CACHE[key] = (best, results)
+    return best, results
+
+
+# ---------------------------------------------------------------- FD
+# The tensor-core contraction on SM pairs: the work-item size (consecutive
+# 128-column tiles per 256-row block of the row operand; 0 = chosen per launch
+# to balance the pairs).  Each candidate reconstructs the caller's own
+# subcircuits as a captured graph; its output must equal the default's bit
+# for bit (the tiling changes no output, only the float64 total's order).
+
+FD_CANDIDATES = [0, 16, 32, 48, 64, 96, 128]
+
+
+def tune_fd(subs, attributed, precision=1, reps=5, candidates=None, out=None, ws=None):
+    """Returns (best tiles_per_item, [(ms, tiles_per_item, identical), ...])
+    and leaves the best one set (cutqc_fd_set_tiles_per_item).  out / ws:
+    optional buffers for the trial reconstructions (2^n floats; the FD
+    workspace)."""
+    import torch
+    key = ("fd", precision, tuple((int(s.w), len(s.in_local), len(s.out_local), tuple(s.out_qubit)) for s in subs))
+    if key in _CACHE:
+        best, results = _CACHE[key]
+        cq.cutqc_fd_set_tiles_per_item(best)
+        return best, results
+    dev = attributed[0].device
+    n = sum(int(s.w) - len(s.out_local) for s in subs)
+    if out is None:
+        out = torch.empty(1 << n, dtype=torch.float32, device=dev)
+    ref = None
+    if ws is None:
+        ws = torch.empty(max(1, cq.cutqc_reconstruct_fd_workspace_size(subs, precision)), dtype=torch.uint8,
+                         device=dev)
+    results = []
+    for t in candidates or FD_CANDIDATES:
+        cq.cutqc_fd_set_tiles_per_item(t)
+        cq.cutqc_reconstruct_fd(subs, attributed, cq.ORDER_KRON, precision, out=out, ws=ws)
+        torch.cuda.synchronize()
+        ms = _time_graph(lambda: cq.cutqc_reconstruct_fd(subs, attributed, cq.ORDER_KRON, precision, out=out, ws=ws),
+                         reps)
+        if ref is None:
+            ref = out.clone()
+            same = True
+        else:
+            same = bool(torch.equal(out, ref))
+        results.append((ms, t, same))
+    del ref
+    best = min((r for r in results if r[2]), key=lambda r: r[0])[1]
+    cq.cutqc_fd_set_tiles_per_item(best)
     _CACHE[key] = (best, results)
     return best, results

@@ -380,3 +380,37 @@ def test_dd_batched_full_size(cq, n_qubits, n_jobs):
         b = bins[J.bins_offset:J.bins_offset + (1 << J.n_active)].cpu().numpy().astype(np.float64)
         _gate_job(b, rj["bins"], J.bin_sum)
     assert cq.cutqc_device_status() == 0
+
+
+@pytest.mark.parametrize("T", [1, 4])
+def test_dd_dense_topk_candidates_with_ties(cq, T):
+    """One dense job (every output active, 2^18 bins: the selection takes
+    the chunked two-pass route) on the tensor-core path: two synthetic
+    subcircuits joined by one cut, attributed entries small integers (the
+    FP16 hi/lo products and sums are then exact), so many bins tie.  The T
+    selected bins must be exactly the first T of the order (value
+    descending, bin index ascending) over the bins written."""
+    import torch
+    from types import SimpleNamespace
+    o0, o1 = 9, 9
+    s0 = SimpleNamespace(w=o0 + 1, in_local=[], in_edge=[], out_local=[o0], out_edge=[0],
+                         out_qubit=list(range(o1, o1 + o0)), edges=[0], o=o0)
+    s1 = SimpleNamespace(w=o1, in_local=[0], in_edge=[0], out_local=[], out_edge=[],
+                         out_qubit=list(range(o1)), edges=[0], o=o1)
+    rng = np.random.default_rng(40 + T)
+    att = [torch.from_numpy(rng.integers(0, 3, size=(1 << s.o, 4)).astype(np.float32)).cuda() for s in (s0, s1)]
+    n = o0 + o1
+    jobs, n_jobs, bins = cq.cutqc_dd_run_async([s0, s1], att, n, n, 1, T, max_jobs=2,
+                                               options={"precision": 1})
+    js = cq.dd_jobs_from_device(jobs, n_jobs)
+    assert len(js) == 1 and js[0].n_active == n
+    b = bins[:1 << n].cpu().numpy().astype(np.float64)
+    A0, A1 = (a.cpu().numpy().astype(np.float64) for a in att)
+    # bin index: bit j = active qubit j; s1 owns qubits 0..8, s0 owns 9..17
+    ref = (A0 @ A1.T).reshape(-1) * 0.5
+    assert np.array_equal(b, ref)
+    order = np.lexsort((np.arange(1 << n), -b))[:T]
+    assert list(js[0].top_idx[:T]) == [int(i) for i in order]
+    assert [float(v) for v in js[0].top_val[:T]] == [float(b[i]) for i in order]
+    assert len(np.unique(b)) < (1 << n) // 100          # ties are plentiful
+    assert cq.cutqc_device_status() == 0

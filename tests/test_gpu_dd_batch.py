@@ -64,8 +64,10 @@ def _reference(cq, subs, At, n, M, R, T, options=None):
 
 
 @pytest.mark.parametrize("options", [None, {"topk_chunk": 256}, {"ctas": 7}, {"merge_ctas": 64, "topk_chunk": 512},
-                                     {"ctas_per_sm": 2}, {"ctas_per_sm": 4}, {"ctas": 3, "ctas_per_sm": 3}],
-                         ids=["default", "chunk256", "ctas7", "merge64", "per_sm2", "per_sm4", "ctas3"])
+                                     {"ctas_per_sm": 2}, {"ctas_per_sm": 4}, {"ctas": 3, "ctas_per_sm": 3},
+                                     {"narrow_max_n": -1}, {"narrow_max_n": 64}],
+                         ids=["default", "chunk256", "ctas7", "merge64", "per_sm2", "per_sm4", "ctas3",
+                              "tiles64x64", "narrow64"])
 def test_batch_matches_level_by_level_and_oracle(cq, options):
     """Three circuits in one persistent launch: every run's records, bins and
     selections equal those of its own level-by-level run (same merge slicing),
@@ -211,3 +213,34 @@ def test_batch_three_dd_circuits_full_size(cq):
             tv = 0.5 * float(np.abs(b - rj["bins"]).sum())
             assert tv <= 1e-6, (w.n, tv)
             assert abs(J.bin_sum - float(rj["bins"].sum())) <= 1e-6, w.n
+
+
+def test_tuned_batch_options_match_oracle(cq):
+    """The persistent batch's autotuner (launch shapes and GEMM tile shapes)
+    returns one of its candidates, every candidate it kept reproduced the
+    first one's records and bins, and the batch built with the tuned options
+    matches the FP64 oracle (TV <= 1e-6 per job)."""
+    import torch
+    from oracle import dd
+    from paper_2205_05836_gb300.tune import BATCH_CANDIDATES, tune_dd_batch
+    R = 6
+    runs, oracle = [], []
+    for cut, M, T in _cuts():
+        subs, A, At = _setup(cut)
+        n = cut.circuit.n
+        runs.append(cq.dd_batch_run(subs, At, n, M, R, T, max_jobs=64))
+        oracle.append(dd.run(A, [s.out_qubit for s in subs], [s.edges for s in subs], cut.K, n, M, R, T,
+                             strategy="bfs"))
+    best, trials = tune_dd_batch(runs, reps=2)
+    assert best in BATCH_CANDIDATES and len(trials) == len(BATCH_CANDIDATES)
+    assert all(ok for _, _, ok in trials)
+    batch = cq.cutqc_dd_batch_create(runs, best)
+    batch.launch()
+    torch.cuda.synchronize()
+    assert cq.cutqc_device_status() == 0
+    for r, rj in zip(runs, oracle):
+        got = cq.dd_jobs_from_device(r["jobs"], r["n_jobs"])
+        assert len(got) == len(rj)
+        for J, o in zip(got, rj):
+            b = r["bins"][J.bins_offset:J.bins_offset + (1 << J.n_active)].cpu().numpy().astype(np.float64)
+            assert 0.5 * float(np.abs(b - o["bins"]).sum()) <= 1e-6

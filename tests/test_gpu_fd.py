@@ -213,6 +213,39 @@ def test_fd_wide_dynamic_range(cq, decades):
     assert cq.cutqc_device_status() == 0
 
 
+def test_tuned_fd_work_items_match_oracle(cq):
+    """The FD autotuner (work-item size of the SM-pair contraction): every
+    candidate's output is bit-identical to the default's, and the tuned
+    setting's reconstruction matches the FP64 oracle (TV <= 1e-6) on a
+    synthetic two-subcircuit contraction of 256 terms and 2^24 outputs."""
+    import torch
+    from types import SimpleNamespace
+    from paper_2205_05836_gb300.tune import FD_CANDIDATES, tune_fd
+    rng = np.random.default_rng(77)
+    o0, o1, k = 10, 14, 4
+    e = list(range(k))
+    s0 = SimpleNamespace(w=o0 + k, in_local=[], in_edge=[], out_local=list(range(o0, o0 + k)), out_edge=e,
+                         out_qubit=list(range(o1, o1 + o0)), edges=e, o=o0)
+    s1 = SimpleNamespace(w=o1, in_local=list(range(k)), in_edge=e, out_local=[], out_edge=[],
+                         out_qubit=list(range(o1)), edges=e, o=o1)
+    A = [rng.standard_normal((1 << s.o, 4 ** k)).astype(np.float32) for s in (s0, s1)]
+    att = [torch.from_numpy(a).cuda() for a in A]
+    try:
+        best, trials = tune_fd([s0, s1], att, reps=2)
+        assert best in FD_CANDIDATES and len(trials) == len(FD_CANDIDATES)
+        assert all(same for _, _, same in trials)
+        out, _ = cq.cutqc_reconstruct_fd([s0, s1], att, cq.ORDER_KRON, cq.PREC_FP16X3_TC)
+        torch.cuda.synchronize()
+    finally:
+        cq.cutqc_fd_set_tiles_per_item(0)
+    got = out.cpu().numpy().astype(np.float64).reshape(1 << o0, 1 << o1)
+    ref = (A[0].astype(np.float64) @ A[1].astype(np.float64).T) * 2.0 ** -k
+    bound = (np.abs(A[0]).astype(np.float64) @ np.abs(A[1]).astype(np.float64).T) * 2.0 ** -k
+    assert np.all(np.abs(got - ref) <= 2.0 ** -16 * bound)
+    assert 0.5 * float(np.abs(got - ref).sum()) <= 1e-6 * float(bound.sum())
+    assert cq.cutqc_device_status() == 0
+
+
 def test_fd_row_split_reassembles(cq):
     """Offset/stride sharding: row ranges written separately equal the whole."""
     import torch

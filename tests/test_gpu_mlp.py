@@ -127,7 +127,7 @@ def test_training_gain_over_unscored_pick(cq, trained):
     import torch
     from workloads.features import LABEL_SCALE, training_set
     net, l0 = trained
-    xv, tv, gv = training_set(80, 32, seed=99)
+    xv, tv, gv = training_set(300, 32, seed=99)     # ~200 held-out circuits with >= 4 candidates
     pv = net.forward(torch.from_numpy(xv).cuda()).cpu().numpy()
     mse = float(((pv - tv) ** 2).mean())
     assert mse < 0.1 * float(tv.var()) and mse < 0.01 * l0, (mse, float(tv.var()), l0)
@@ -141,7 +141,7 @@ def test_training_gain_over_unscored_pick(cq, trained):
         reg_mlp.append(cost[pv[s].argmin()] - best)
         reg_rand.append(cost.mean() - best)
         reg_eq2.append(cost[xv[s][:, 6].argmin()] - best)
-    assert len(reg_mlp) >= 40
+    assert len(reg_mlp) >= 150
     assert np.mean(reg_mlp) < 0.25 * np.mean(reg_rand), (np.mean(reg_mlp), np.mean(reg_rand))
     assert np.mean(reg_mlp) < np.mean(reg_eq2), (np.mean(reg_mlp), np.mean(reg_eq2))
     assert cq.cutqc_device_status() == 0

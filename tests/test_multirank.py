@@ -16,7 +16,7 @@ def _free_port():
     return p
 
 
-def _worker(rank, world, port, q):
+def _worker(rank, world, port, q, case):
     import torch
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
@@ -24,19 +24,24 @@ def _worker(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         from oracle import attribution, fd
+        from paper_2205_05836_gb300 import cutqc
         from paper_2205_05836_gb300.shard import max_over_ranks, row_range
         from workloads import circuits as C
         from workloads.cutting import search_cut
         from workloads.simulate import simulate_variants
-        cut = search_cut(C.supremacy(3, 4, 8, 1), 8, 2, restarts=4)
+        cut = search_cut(*case, restarts=4)
         subs = cut.subcircuits
         A = [attribution.attribute(simulate_variants(s), s.w, s.in_local, s.out_local, s.in_edge, s.out_edge)
              for s in subs]
-        rows = A[0].shape[0]
+        # the library's own split (host-side planner, no device): rows of its
+        # last contraction = the high output bits in Kronecker order
+        rows, cols = cutqc.cutqc_fd_shape(subs)
+        assert rows * cols == 2 ** cut.circuit.n
         r0, r1 = row_range(rows, world, rank)
-        # this rank's rows of the final contraction: Eq. 1 restricted to them
-        part = (A[0][r0:r1] @ A[1].T) * 0.5 ** cut.K
-        t = torch.from_numpy(np.ascontiguousarray(part.reshape(-1)))
+        # this rank's outputs [r0 * cols, r1 * cols): Eq. 1 at each of them
+        idx = np.arange(r0 * cols, r1 * cols, dtype=np.int64)
+        part = fd.entries(A, [s.edges for s in subs], cut.K, fd.split_kron_index(idx, [s.o for s in subs]))
+        t = torch.from_numpy(np.ascontiguousarray(part))
         sizes = [None] * world
         dist.all_gather_object(sizes, t.numel())
         bufs = [torch.zeros(n, dtype=t.dtype) for n in sizes]
@@ -50,12 +55,23 @@ def _worker(rank, world, port, q):
         dist.destroy_process_group()
 
 
-def test_two_rank_row_split():
+def _cases():
+    from workloads import circuits as C
+    return [(C.supremacy(3, 4, 8, 1), 8, 2), (C.aqft(10, 6, max_dist=2), 5, 4)]
+
+
+@pytest.mark.parametrize("ci", [0, 1], ids=["two_sub", "four_sub"])
+def test_two_rank_row_split(ci):
+    """Each rank computes the outputs of its rows of the library's last
+    contraction (cutqc_fd_shape, shard.row_range) with the FP64 oracle; the
+    gathered ranks equal the single-process reconstruction."""
+    import __graft_entry__
+    __graft_entry__.build()
     import torch.multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q, _cases()[ci])) for r in range(2)]
     for p in procs:
         p.start()
     for p in procs:
@@ -64,7 +80,7 @@ def test_two_rank_row_split():
     err, tmax, sizes = q.get(timeout=10)
     assert err < 1e-15
     assert tmax == 2.0
-    assert len(sizes) == 2 and abs(sizes[0] - sizes[1]) <= 2 ** 8
+    assert len(sizes) == 2 and abs(sizes[0] - sizes[1]) <= max(sizes) // 2
 
 
 def test_row_range_covers_rows():
