@@ -9,15 +9,19 @@
 //     I = sum_m pZ(m), X = sum_m (-1)^m pX(m), Y = sum_m (-1)^m pY(m),
 //     Z = sum_m (-1)^m pZ(m)
 //
-// The map is a tensor product of one small map per cut.  A CTA owns R
-// consecutive outcome rows and one value of the "other" index, stages the
-// fiber of all cut digits for its rows in shared memory (loads coalesced
-// along the outcome index), applies the per-cut maps axis by axis, and
-// writes the result.  Subcircuits with both kinds of cut take two passes
-// through a float32 workspace: the measured axes first (on the variants as
-// given, 3^k_out runs x 2^k_out outcomes -> 4^k_out bases per output row),
-// then the initialised axes along the columns of the smaller result.
-// Arithmetic is float32 after the (float64 or float32) loads; HBM-bound.
+// The map is a tensor product of one small map per cut.  Initialised side
+// (attr_init_pass): a CTA owns R consecutive outcome rows and one measurement
+// run, stages the fiber of the init digits for its rows in shared memory
+// (loads coalesced along the outcome index) and applies the per-cut maps
+// axis by axis.  Measured side (attr_meas_run): a CTA owns one measurement
+// run and 128 output rows, each thread takes the Walsh-Hadamard transform of
+// its row's 2^k_out outcomes in registers and writes the basis strings that
+// run serves.  Subcircuits with both kinds of cut take two passes through a
+// float32 workspace: the measured side first, on the variants as given
+// (3^k_out runs x 2^k_out outcomes -> 4^k_out bases per output row), then the
+// initialised side along the columns of the smaller result
+// (attr_init_cols).  Arithmetic is float32 after the (float64 or float32)
+// loads; HBM-bound.
 #include "internal.cuh"
 
 #include <algorithm>
@@ -33,7 +37,6 @@ namespace {
 constexpr int kMaxKin = 6;
 constexpr int kMaxKout = 5;
 constexpr int kThreads = 512;
-constexpr int kMeasThreads = 512;
 constexpr int kBatch = 8;            // loads in flight per thread
 
 struct AttrParams {
@@ -60,17 +63,6 @@ __device__ __forceinline__ void init_map4(const float (&p)[4], float (&o)[4]) {
   o[3] = p[0] - p[1];
 }
 
-// Rows per CTA of the measured-side pass: as many as fit a padded [F][R + 1]
-// block of 48 KiB (four CTAs per SM, so that some CTAs load while others
-// combine and store), at most 32; when that leaves fewer than 8 rows (runs
-// of loads too short to coalesce), as many as fit 96 KiB (two CTAs per SM).
-__host__ __device__ constexpr int rows_within(int F, int bytes) {
-  return F * 33 * 4 <= bytes ? 32 : F * 17 * 4 <= bytes ? 16 : F * 9 * 4 <= bytes ? 8
-       : F * 5 * 4 <= bytes ? 4 : F * 3 * 4 <= bytes ? 2 : 1;
-}
-__host__ __device__ constexpr int meas_rows_for(int F) {
-  return rows_within(F, 48 * 1024) >= 8 ? rows_within(F, 48 * 1024) : rows_within(F, 96 * 1024);
-}
 // Rows per CTA of the initialised-side pass: as many as fit a 72 KiB padded
 // [F][R + 1] block (three CTAs per SM), at most 64 (512-byte runs of float64).
 __host__ __device__ constexpr int rows_for(int F) {
@@ -191,105 +183,10 @@ attr_init_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p,
   }
 }
 
-// Measured-side pass (KOUT measured cuts, compile time).  For each measured
-// cut the basis digit d selects the measurement run (I, Z: computational;
-// X: X basis; Y: Y basis) and the sign of outcome 1 (+ for I, - otherwise):
-//   out[d] = sum_{b in {0,1}^KOUT} (-1)^{popcount(b & nonI(d))} V[run(d)][b]
-// with V[m][b] the run-m probability of outcome bits b of the measured cuts.
-// Shared memory: V as [m][b][R + 1] (each run's block padded by one float)
-// for R consecutive output rows x_out and fixed init digits `dinit`
-// (blockIdx.y).
-template <typename T, int KOUT>
-__global__ void __launch_bounds__(kMeasThreads)
-attr_meas_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, int staged) {
-  constexpr int NM = pow3(KOUT);
-  constexpr int F = NM << KOUT;
-  constexpr int R = meas_rows_for(F);
-  constexpr int RS = R + 1;
-  // one run's [2^KOUT][RS] block plus one float: consecutive runs start in
-  // different banks, so the combine step (threads over basis digits) reads
-  // without bank conflicts
-  constexpr int PITCH = (1 << KOUT) * RS + 1;
-  constexpr int G = 1 << (2 * KOUT);
-  extern __shared__ float sm[];
-  float* buf = sm;                                                     // [NM][PITCH]
-  int64_t* rowbase = reinterpret_cast<int64_t*>(buf + ((NM * PITCH + 1) & ~1));   // [R]
-  int64_t* bpart = rowbase + R;                                       // [2^KOUT]
-  int* runoff = reinterpret_cast<int*>(bpart + (1 << KOUT));          // [G]: (run << KOUT) * RS
-  int* nonI = runoff + G;                                             // [G]
-  int* colm = nonI + G;                                               // [G]: column of the measured digits
-  const int64_t x0 = (int64_t)blockIdx.x * R;
-  const int dinit = blockIdx.y;
-  const int64_t W = (int64_t)1 << p.w;
-  const int rows = (int)(p.n_rows - x0 < R ? p.n_rows - x0 : R);
-  for (int r = threadIdx.x; r < R; r += kMeasThreads) rowbase[r] = (int64_t)pdep64((uint64_t)(x0 + r), p.out_mask);
-  for (int b = threadIdx.x; b < (1 << KOUT); b += kMeasThreads) {
-    uint64_t v = 0;
-#pragma unroll
-    for (int j = 0; j < KOUT; ++j)
-      if ((b >> j) & 1) v |= p.meas_mask[j];
-    bpart[b] = (int64_t)v;
-  }
-  for (int d = threadIdx.x; d < G; d += kMeasThreads) {
-    int run = 0, w3 = 1, mask = 0, c = 0;
-#pragma unroll
-    for (int j = 0; j < KOUT; ++j) {
-      const int dj = (d >> (2 * j)) & 3;          // I, X, Y, Z
-      run += (dj == 3 ? 0 : dj) * w3;             // Z shares the computational run
-      w3 *= 3;
-      if (dj) mask |= 1 << j;
-      c |= dj << p.col_shift_out[j];
-    }
-    runoff[d] = run * PITCH;
-    nonI[d] = mask;
-    colm[d] = c;
-  }
-  __syncthreads();
-  const T* base = src + (int64_t)dinit * NM * W;
-  // loads in batches of kBatch per thread (all issued before any store)
-  for (int i0 = 0; i0 < F * R; i0 += kMeasThreads * kBatch) {
-    float v[kBatch];
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int i = i0 + u * kMeasThreads + threadIdx.x;
-      const int e = i / R, r = i % R;
-      const int m = e >> KOUT, b = e & ((1 << KOUT) - 1);
-      v[u] = (i < F * R && r < rows) ? load_val(base + (int64_t)m * W + (rowbase[r] | bpart[b])) : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int i = i0 + u * kMeasThreads + threadIdx.x;
-      if (i < F * R) {
-        const int e = i / R;
-        buf[(e >> KOUT) * PITCH + (e & ((1 << KOUT) - 1)) * RS + i % R] = v[u];
-      }
-    }
-  }
-  __syncthreads();
-  const int64_t C = (int64_t)1 << (2 * p.k);
-  int cin = 0;
-  for (int j = 0; j < p.k_in; ++j) cin |= ((dinit >> (2 * j)) & 3) << p.col_shift_in[j];
-  for (int i = threadIdx.x; i < rows * G; i += kMeasThreads) {
-    const int r = i / G, g = i % G;
-    const float* vb = buf + runoff[g] + r;
-    const int mask = nonI[g];
-    float acc = 0.f;
-#pragma unroll
-    for (int b = 0; b < (1 << KOUT); ++b) {
-      const float v = vb[b * RS];
-      acc += (__popc(b & mask) & 1) ? -v : v;
-    }
-    // staged: W[init index][x][g], contiguous for the CTA (the initialised
-    // side follows); else the attributed layout
-    if (staged) dst[((int64_t)dinit * p.n_rows + x0 + r) * G + g] = acc;
-    else dst[(x0 + r) * C + (cin | colm[g])] = acc;
-  }
-}
-
 // Initialised-side map for subcircuits with both kinds of cut.  The
-// measured-side pass left W[s][x][mu] in the workspace (s: the init cuts'
-// states |0>, |1>, |+>, |+i> as digits, x: output row, mu: the measured cuts'
-// bases as digits, dense).  Every fiber W[.][x][mu] over the 4^KIN states is
+// measured-side pass left W[s][mu][x] in the workspace (s: the init cuts'
+// states |0>, |1>, |+>, |+i> as digits, mu: the measured cuts' bases as
+// digits, x: output row, dense).  Every fiber W[.][mu][x] over the 4^KIN states is
 // mapped to bases by the per-cut 4x4 map (init_map4), digit pair by digit
 // pair, and written to the attributed layout A[x][col], col holding each
 // cut's digit at its edge's rank.  A CTA takes P consecutive (x, mu) and all
@@ -302,14 +199,13 @@ template <int KIN>
 __global__ void __launch_bounds__(kColThreads)
 attr_init_cols(const float* __restrict__ src, float* __restrict__ dst, AttrParams p, int64_t n_fibers, int ifast) {
   constexpr int F = 1 << (2 * KIN);
-  constexpr int P = F >= 4096 ? 1 : (4096 / F > 64 ? 64 : 4096 / F);   // fibers per CTA
+  constexpr int P = F >= 4096 ? 1 : (8192 / F > 64 ? 64 : 8192 / F);   // fibers per CTA (128-byte runs at F = 256)
   constexpr int FS = F + 1;
   __shared__ float buf[P * FS];
   __shared__ int64_t fbase[P];
   __shared__ int ioff[F];
   const int64_t f0 = (int64_t)blockIdx.x * P;
   const int64_t C = (int64_t)1 << (2 * p.k);
-  const int mdig = 2 * p.k_out;
   for (int i = threadIdx.x; i < F; i += kColThreads) {
     int off = 0;
 #pragma unroll
@@ -317,9 +213,9 @@ attr_init_cols(const float* __restrict__ src, float* __restrict__ dst, AttrParam
     ioff[i] = off;
   }
   for (int i = threadIdx.x; i < P; i += kColThreads) {
-    const int64_t f = f0 + i;
-    const int64_t x = f >> mdig;
-    const int mu = (int)(f & ((1 << mdig) - 1));
+    const int64_t f = f0 + i;           // fiber = g * 2^o + x
+    const int64_t x = f % p.n_rows;
+    const int mu = (int)(f / p.n_rows);
     int moff = 0;
     for (int j = 0; j < p.k_out; ++j) moff |= ((mu >> (2 * j)) & 3) << p.col_shift_out[j];
     fbase[i] = x * C + moff;
@@ -343,7 +239,7 @@ attr_init_cols(const float* __restrict__ src, float* __restrict__ dst, AttrParam
 #pragma unroll
   for (int j = 0; j < KIN; j += 2) {
     if (j + 1 < KIN) {
-      constexpr int groups = F >> 4;
+      constexpr int groups = F >= 16 ? F >> 4 : 1;      // (this branch needs KIN >= 2)
       for (int it = threadIdx.x; it < groups * P; it += kColThreads) {
         const int grp = it % groups, fl = it / groups;
         const int lowmask = (1 << (2 * j)) - 1;
@@ -395,14 +291,6 @@ attr_init_cols(const float* __restrict__ src, float* __restrict__ dst, AttrParam
 
 template <typename T, int KIN>
 size_t init_smem() { return (size_t)(1 << (2 * KIN)) * (rows_for(1 << (2 * KIN)) + 1) * 4 + (2u << (2 * KIN)); }
-template <typename T, int KOUT>
-size_t meas_smem() {
-  constexpr int F = pow3(KOUT) << KOUT;
-  constexpr int R = meas_rows_for(F);
-  constexpr size_t PITCH = ((size_t)1 << KOUT) * (R + 1) + 1;
-  return (((size_t)pow3(KOUT) * PITCH + 1) & ~(size_t)1) * 4 + (size_t)(R + (1 << KOUT)) * 8 +
-         3 * ((size_t)1 << (2 * KOUT)) * 4;
-}
 
 // k == 0: plain conversion to float32.
 template <typename T>
@@ -487,17 +375,6 @@ int run_init(const T* src, float* out, const AttrParams& p, int final_layout, cu
   return CUTQC_OK;
 }
 
-template <typename T, int KOUT>
-int run_meas(const T* src, float* out, const AttrParams& p, int staged, cudaStream_t st) {
-  constexpr int F = pow3(KOUT) << KOUT;
-  constexpr int R = meas_rows_for(F);
-  const size_t smem = meas_smem<T, KOUT>();
-  dim3 grid((unsigned)((p.n_rows + R - 1) / R), 1u << (2 * p.k_in));
-  CUTQC_CUDA_TRY(set_max_smem((const void*)attr_meas_pass<T, KOUT>));
-  attr_meas_pass<T, KOUT><<<grid, kMeasThreads, smem, st>>>(src, out, p, staged);
-  CUTQC_LAUNCH_CHECK("attr_meas_pass");
-  return CUTQC_OK;
-}
 
 template <typename T>
 int dispatch_init(const T* src, float* out, const AttrParams& p, int final_layout, cudaStream_t st) {
@@ -515,7 +392,7 @@ int dispatch_init(const T* src, float* out, const AttrParams& p, int final_layou
 template <int KIN>
 int run_init_cols(const float* src, float* out, const AttrParams& p, cudaStream_t st) {
   constexpr int F = 1 << (2 * KIN);
-  constexpr int P = F >= 4096 ? 1 : (4096 / F > 64 ? 64 : 4096 / F);
+  constexpr int P = F >= 4096 ? 1 : (8192 / F > 64 ? 64 : 8192 / F);
   const int64_t n_fibers = p.n_rows << (2 * p.k_out);
   int ifast = 0;
   for (int j = 0; j < p.k_in; ++j) ifast |= p.col_shift_in[j] == 0;
@@ -538,14 +415,101 @@ int dispatch_init_cols(const float* src, float* out, const AttrParams& p, cudaSt
   return set_error(CUTQC_EUNSUPPORTED, "k_in = %d", p.k_in);
 }
 
+
+// Measured side of a subcircuit with both kinds of cut, one measurement run
+// at a time.  CTA (x block, run m, init state s): each thread loads the
+// 2^KOUT outcome values of one output row x of run m (a warp's loads are
+// runs of consecutive values when the output qubits are the low local bits),
+// takes their
+// Walsh-Hadamard transform over the outcomes in registers (entry `mask` =
+// sum_b (-1)^popcount(b & mask) V[b]), and writes the basis strings g whose
+// run is m -- a measured cut's digit is X or Y where the run measured in that
+// basis, I or Z where it measured in the computational basis -- to
+// W[s][g][x], x fastest (coalesced).
+constexpr int kRunRows = 128;
+
+template <typename T, int KOUT>
+__global__ void __launch_bounds__(kRunRows)
+attr_meas_run(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, int staged) {
+  constexpr int NB = 1 << KOUT;
+  constexpr int NM = pow3(KOUT);
+  constexpr int G = 1 << (2 * KOUT);
+  const int64_t x0 = (int64_t)blockIdx.x * kRunRows;
+  const int m = blockIdx.y, s = blockIdx.z;
+  const int rows = (int)(p.n_rows - x0 < kRunRows ? p.n_rows - x0 : kRunRows);
+  const int64_t W = (int64_t)1 << p.w;
+  const T* base = src + ((int64_t)s * NM + m) * W;
+  const int r = threadIdx.x;
+  const int64_t rb = r < rows ? (int64_t)pdep64((uint64_t)(x0 + r), p.out_mask) : 0;
+  float v[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    uint64_t bp = 0;
+#pragma unroll
+    for (int j = 0; j < KOUT; ++j)
+      if ((b >> j) & 1) bp |= p.meas_mask[j];
+    v[b] = r < rows ? load_val(base + (rb | (int64_t)bp)) : 0.f;
+  }
+  // Walsh-Hadamard transform over the outcome bits: v[mask] = sum_b
+  // (-1)^popcount(b & mask) V[b]
+#pragma unroll
+  for (int h = 1; h < NB; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+      if ((i & h) == 0) {
+        const float a = v[i], c = v[i | h];
+        v[i] = a + c;
+        v[i | h] = a - c;
+      }
+  if (r >= rows) return;
+  // run m's digits (base 3): 0 computational, 1 X, 2 Y
+  int md[KOUT];
+  int fixed = 0, comp = 0, gx = 0;
+#pragma unroll
+  for (int j = 0, mm = m; j < KOUT; ++j, mm /= 3) {
+    md[j] = mm % 3;
+    if (md[j]) { fixed |= 1 << j; gx |= md[j] << (2 * j); } else comp |= 1 << j;
+  }
+  // every subset z of the computational digits: Z there (mask bit set), I elsewhere
+  for (int z = comp;; z = (z - 1) & comp) {
+    int g = gx;
+#pragma unroll
+    for (int j = 0; j < KOUT; ++j)
+      if ((z >> j) & 1) g |= 3 << (2 * j);
+    float out = 0.f;
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+      if (i == (fixed | z)) out = v[i];
+    if (staged) {
+      dst[((int64_t)s * G + g) * p.n_rows + x0 + r] = out;
+    } else {     // no init cut: the attributed layout, row x, the measured digits' columns
+      int col = 0;
+#pragma unroll
+      for (int j = 0; j < KOUT; ++j) col |= ((g >> (2 * j)) & 3) << p.col_shift_out[j];
+      dst[(x0 + r) * (int64_t)G + col] = out;
+    }
+    if (z == 0) break;
+  }
+}
+
+template <typename T, int KOUT>
+int run_meas_run(const T* src, float* out, const AttrParams& p, int staged, cudaStream_t st) {
+  const int64_t xb = (p.n_rows + kRunRows - 1) / kRunRows;
+  if (xb > 0x7fffffffLL) return set_error(CUTQC_EUNSUPPORTED, "attribution tensor too large");
+  dim3 grid((unsigned)xb, pow3(KOUT), 1u << (2 * p.k_in));
+  attr_meas_run<T, KOUT><<<grid, kRunRows, 0, st>>>(src, out, p, staged);
+  CUTQC_LAUNCH_CHECK("attr_meas_run");
+  return CUTQC_OK;
+}
+
 template <typename T>
-int dispatch_meas(const T* src, float* out, const AttrParams& p, int staged, cudaStream_t st) {
+int dispatch_meas_run(const T* src, float* out, const AttrParams& p, int staged, cudaStream_t st) {
   switch (p.k_out) {
-    case 1: return run_meas<T, 1>(src, out, p, staged, st);
-    case 2: return run_meas<T, 2>(src, out, p, staged, st);
-    case 3: return run_meas<T, 3>(src, out, p, staged, st);
-    case 4: return run_meas<T, 4>(src, out, p, staged, st);
-    case 5: return run_meas<T, 5>(src, out, p, staged, st);
+    case 1: return run_meas_run<T, 1>(src, out, p, staged, st);
+    case 2: return run_meas_run<T, 2>(src, out, p, staged, st);
+    case 3: return run_meas_run<T, 3>(src, out, p, staged, st);
+    case 4: return run_meas_run<T, 4>(src, out, p, staged, st);
+    case 5: return run_meas_run<T, 5>(src, out, p, staged, st);
   }
   return set_error(CUTQC_EUNSUPPORTED, "k_out = %d", p.k_out);
 }
@@ -568,7 +532,7 @@ int launch_attr(const cutqc_subcircuit* s, const T* src, float* dst, float* tmp,
     // data from 3^k_out * 2^w to 4^k_out * 2^o values per init state; then
     // the initialised side along the columns, from the workspace into dst
     p.n_rows = (int64_t)1 << o;
-    int rc = dispatch_meas<T>(src, tmp, p, 1, st);
+    int rc = dispatch_meas_run<T>(src, tmp, p, 1, st);
     if (rc) return rc;
     return dispatch_init_cols(tmp, dst, p, st);
   }
@@ -577,7 +541,7 @@ int launch_attr(const cutqc_subcircuit* s, const T* src, float* dst, float* tmp,
     return dispatch_init<T>(src, dst, p, 1, st);
   }
   p.n_rows = (int64_t)1 << o;
-  return dispatch_meas<T>(src, dst, p, 0, st);
+  return dispatch_meas_run<T>(src, dst, p, 0, st);
 }
 
 }  // namespace

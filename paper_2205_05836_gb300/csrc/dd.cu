@@ -347,30 +347,17 @@ static int dd_step_impl(int n_sub, const cutqc_subcircuit* s, const int32_t* act
       // chunked pass into the candidate scratch, then one CTA per job
       int32_t* cidx = (int32_t*)((uint8_t*)ws_dev + plan_ws);
       float* cval = (float*)(cidx + (size_t)n_jobs * chunks * 32);
+      const int64_t clen = (nb + chunks - 1) / chunks;
+      const int64_t ncand = chunks * topk;
       const int64_t cthreads = std::min<int64_t>(cap, 512);   // several CTAs per SM: more loads in flight
-      // one job: whole waves of resident CTAs (a last, partial wave of 2 MiB
-      // chunks left the pass a third idle); chunks stay float4-aligned
-      int64_t nch = chunks;
-      if (n_jobs == 1) {
-        int per_sm = 0;
-        if (topk <= 4)
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dd_topk_kernel<4, false>, (int)cthreads, 0);
-        else
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dd_topk_kernel<32, false>, (int)cthreads, 0);
-        const int64_t wave = (int64_t)std::max(1, per_sm) * sm_count();
-        if (nch > wave) nch = nch / wave * wave;
-      }
-      const int64_t clen = ((nb + nch - 1) / nch + 3) / 4 * 4;
-      const int64_t nch_used = (nb + clen - 1) / clen;
-      const int64_t ncand = nch_used * topk;
       if (topk <= 4) {
-        dd_topk_kernel<4, false><<<dim3(n_jobs, (unsigned)nch_used), (int)cthreads, 0, st>>>(bins, nullptr, nb, clen,
-                                                                                            topk, cidx, cval);
+        dd_topk_kernel<4, false><<<dim3(n_jobs, (unsigned)chunks), (int)cthreads, 0, st>>>(bins, nullptr, nb, clen,
+                                                                                          topk, cidx, cval);
         CUTQC_LAUNCH_CHECK("dd_topk_kernel (chunks)");
         dd_topk_kernel<4, true><<<dim3(n_jobs, 1), 1024, 0, st>>>(cval, cidx, ncand, ncand, topk, top_idx, top_val);
       } else {
-        dd_topk_kernel<32, false><<<dim3(n_jobs, (unsigned)nch_used), (int)cthreads, 0, st>>>(bins, nullptr, nb,
-                                                                                             clen, topk, cidx, cval);
+        dd_topk_kernel<32, false><<<dim3(n_jobs, (unsigned)chunks), (int)cthreads, 0, st>>>(bins, nullptr, nb, clen,
+                                                                                           topk, cidx, cval);
         CUTQC_LAUNCH_CHECK("dd_topk_kernel (chunks)");
         dd_topk_kernel<32, true><<<dim3(n_jobs, 1), 1024, 0, st>>>(cval, cidx, ncand, ncand, topk, top_idx, top_val);
       }

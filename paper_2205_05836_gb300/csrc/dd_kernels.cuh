@@ -243,18 +243,11 @@ __device__ __forceinline__ void dd_topk_body(const float* __restrict__ vals, con
   int64_t tail0 = lo;
   if (!kCand && (((uintptr_t)(b + lo)) & 15) == 0) {
     // bins: float4 loads, four in flight per thread (the order in which a
-    // thread offers entries does not matter: ties compare indices).  The
-    // blocks of U * blockDim float4 are visited in bit-reversed order when
-    // their count is a power of two: bins that grow along the index would
-    // otherwise displace a thread's list at almost every offer
+    // thread offers entries does not matter: ties compare indices)
     constexpr int U = 4;
     const float4* p4 = reinterpret_cast<const float4*>(b + lo);
     const int64_t n4 = (hi - lo) >> 2;
-    const int64_t blk = U * (int64_t)blockDim.x;
-    const int64_t nblk = (n4 + blk - 1) / blk;
-    const int lg = (nblk & (nblk - 1)) == 0 && nblk > 1 ? 63 - __clzll(nblk) : 0;
-    for (int64_t it = 0; it < nblk; ++it) {
-      const int64_t q = (lg ? (int64_t)(__brevll((unsigned long long)it) >> (64 - lg)) : it) * blk + threadIdx.x;
+    for (int64_t q = threadIdx.x; q < n4; q += U * (int64_t)blockDim.x) {
       float4 v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
