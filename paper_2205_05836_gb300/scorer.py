@@ -43,11 +43,13 @@ def propose_cut(circuit, w_max, net, n_candidates=4096, n_exact=8, seed=0, max_v
         cut = search_cut(circuit, w_max, lo, restarts=4, seed=seed)
         info.update(fallback=True, seconds=time.perf_counter() - t0)
         return cut, info
-    x = torch.from_numpy(np.ascontiguousarray(cs.features()[ok])).to(net.device)
+    feas = cs.subset(ok)
+    x = torch.from_numpy(np.ascontiguousarray(feas.features())).to(net.device)
     pred = net.forward(x).cpu().numpy()
-    top = ok[np.argsort(pred, kind="stable")[:n_exact]]
-    costs = [cs.exact_cost(int(i)) for i in top]
-    volume = [float(np.exp2(cs.variant_log2[i][cs.used[i]]).sum()) for i in top]
+    order = np.argsort(pred, kind="stable")[:n_exact]
+    top = ok[order]
+    costs = [feas.exact_cost(int(j)) for j in order]
+    volume = [float(np.exp2(feas.variant_log2[j][feas.used[j]]).sum()) for j in order]
     pick = min(range(len(top)), key=lambda j: (costs[j], volume[j]))
     best = int(top[pick])
     cut = build_cut(circuit, assign[best], w_max=w_max)

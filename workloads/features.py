@@ -54,10 +54,12 @@ class CandidateSet:
         start = first[None] | (cl != prev)
         end = last[None] | (cl != nxt)
         cut_at = start & ~first[None]          # a cut edge enters a run here
-        oh = cl[..., None] == np.arange(S)     # [C, L, S]
-        w = (start[..., None] & oh).sum(1)
-        k_in = (cut_at[..., None] & oh).sum(1)
-        k_out = ((end & ~last[None])[..., None] & oh).sum(1)
+        # per (candidate, cluster) counts of run starts, cut entries and cut exits
+        flat = np.arange(C, dtype=np.int64)[:, None] * S + cl
+        count = lambda m: np.bincount(flat[m], minlength=C * S).reshape(C, S)
+        w = count(start)
+        k_in = count(cut_at)
+        k_out = count(end & ~last[None])
         # free qubits, placed as build_cut places them
         overflow = np.zeros(C, dtype=bool)
         for _ in dag.free_qubits:
@@ -88,6 +90,22 @@ class CandidateSet:
         # variant tensor entries 4^k_in * 3^k_out * 2^w per subcircuit (log2)
         vlog = 2.0 * k_in + math.log2(3.0) * k_out + w
         self.variant_log2 = np.where(self.used, vlog, -np.inf)
+
+    def subset(self, idx):
+        """The candidates ``idx`` (in that order) as a CandidateSet of their
+        own, without recomputing their structure."""
+        idx = np.asarray(idx, dtype=np.int64)
+        sub = object.__new__(CandidateSet)
+        sub.dag, sub.n, sub.w_max, sub.C = self.dag, self.n, self.w_max, len(idx)
+        for name in ("w", "k_in", "k_out", "o", "used", "K", "pair", "feasible", "variant_log2"):
+            setattr(sub, name, getattr(self, name)[idx])
+        pos = np.full(self.C, -1, dtype=np.int64)
+        pos[idx] = np.arange(len(idx))
+        keep = pos[self._edge_c] >= 0
+        sub._edge_c = pos[self._edge_c[keep]]
+        sub._edge_a = self._edge_a[keep]
+        sub._edge_b = self._edge_b[keep]
+        return sub
 
     # ------------------------------------------------------------------
     def features(self):
@@ -161,14 +179,16 @@ class CandidateSet:
 
 
 def eq2_log2(o, used, K):
-    """log2 of Eq. 2 (subcircuits in ascending output count), per candidate."""
+    """log2 of Eq. 2 (subcircuits in ascending output count), per candidate:
+    2 K + log2 sum_{c >= 2} 2^(o_(1) + ... + o_(c)) over the used slots in
+    ascending order (array operations over the candidates)."""
     C, S = o.shape
-    out = np.zeros(C)
-    for c in range(C):
-        oo = sorted(int(x) for x, u in zip(o[c], used[c]) if u)
-        tot = sum(2.0 ** sum(oo[:k]) for k in range(2, len(oo) + 1))
-        out[c] = 2.0 * K[c] + (math.log2(tot) if tot > 0 else 0.0)
-    return out
+    oo = np.sort(np.where(used, o, np.inf).astype(np.float64), axis=1)
+    valid = np.isfinite(oo)
+    prefix = np.cumsum(np.where(valid, oo, 0.0), axis=1)
+    terms = np.where(valid & (np.arange(S)[None, :] >= 1), np.exp2(prefix), 0.0)
+    tot = terms.sum(1)
+    return 2.0 * np.asarray(K, dtype=np.float64) + np.where(tot > 0, np.log2(np.where(tot > 0, tot, 1.0)), 0.0)
 
 
 # --------------------------------------------------------------------------
@@ -259,8 +279,9 @@ def training_set(n_circuits, per_circuit, seed, n_range=(20, 60)):
         ok = np.nonzero(cs.feasible)[0][:per_circuit]
         if len(ok) == 0:
             continue
-        xs.append(cs.features()[ok])
-        ts.append(cs.labels(ok))
+        sub = cs.subset(ok)
+        xs.append(sub.features())
+        ts.append(sub.labels())
         gs.append(np.full(len(ok), g))
     return np.concatenate(xs), np.concatenate(ts), np.concatenate(gs)
 
