@@ -37,7 +37,7 @@ namespace {
 constexpr int kMaxKin = 6;
 constexpr int kMaxKout = 5;
 constexpr int kThreads = 512;
-constexpr int kBatch = 8;            // loads in flight per thread
+constexpr int kBatch = 16;           // loads in flight per thread
 
 struct AttrParams {
   int w, k_in, k_out;
@@ -432,7 +432,8 @@ int dispatch_init_cols(const float* src, float* out, const AttrParams& p, cudaSt
 // run is m -- a measured cut's digit is X or Y where the run measured in that
 // basis, I or Z where it measured in the computational basis -- to
 // W[s][g][x], x fastest (coalesced).
-constexpr int kRunRows = 128;
+constexpr int kRunRows = 128;     // threads per CTA
+constexpr int kRunRpt = 1;        // rows per thread (2 measured slower: 157 against 76 us on the chain, half the occupancy)
 
 template <typename T, int KOUT>
 __global__ void __launch_bounds__(kRunRows)
@@ -441,27 +442,39 @@ attr_meas_run(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, 
   constexpr int NM = pow3(KOUT);
   constexpr int G = 1 << (2 * KOUT);
   const int64_t W = (int64_t)1 << p.w;
-  const int64_t ntask = n_xb * NM << (2 * p.k_in);
-  // tasks: x block fastest, then the run, then the init state (consecutive
-  // CTAs read neighbouring blocks of the variants)
-  for (int64_t task = blockIdx.x; task < ntask; task += gridDim.x) {
-    const int64_t xb = task % n_xb;
-    const int m = (int)((task / n_xb) % NM);
-    const int s = (int)(task / n_xb / NM);
-    const int64_t x0 = xb * kRunRows;
-    const int rows = (int)(p.n_rows - x0 < kRunRows ? p.n_rows - x0 : kRunRows);
-    const T* base = src + ((int64_t)s * NM + m) * W;
-    const int r = threadIdx.x;
-    const int64_t rb = r < rows ? (int64_t)pdep64((uint64_t)(x0 + r), p.out_mask) : 0;
-    float v[NB];
+  // task: x block (kRunRows * kRunRpt rows) fastest, then the run, then the
+  // init state (consecutive CTAs read neighbouring blocks of the variants)
+  const int64_t task = blockIdx.x;
+  const int64_t xb = task % n_xb;
+  const int m = (int)((task / n_xb) % NM);
+  const int s = (int)(task / n_xb / NM);
+  const T* base = src + ((int64_t)s * NM + m) * W;
+  // every thread loads all outcomes of its kRunRpt rows before any arithmetic
+  float v[kRunRpt][NB];
+  int64_t xr[kRunRpt];
+#pragma unroll
+  for (int t = 0; t < kRunRpt; ++t) {
+    xr[t] = xb * (kRunRows * kRunRpt) + t * kRunRows + threadIdx.x;
+    const bool ok = xr[t] < p.n_rows;
+    const int64_t rb = ok ? (int64_t)pdep64((uint64_t)xr[t], p.out_mask) : 0;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       uint64_t bp = 0;
 #pragma unroll
       for (int j = 0; j < KOUT; ++j)
         if ((b >> j) & 1) bp |= p.meas_mask[j];
-      v[b] = r < rows ? load_val(base + (rb | (int64_t)bp)) : 0.f;
+      v[t][b] = ok ? load_val(base + (rb | (int64_t)bp)) : 0.f;
     }
+  }
+  // run m's digits (base 3): 0 computational, 1 X, 2 Y
+  int fixed = 0, comp = 0, gx = 0;
+#pragma unroll
+  for (int j = 0, mm = m; j < KOUT; ++j, mm /= 3) {
+    const int md = mm % 3;
+    if (md) { fixed |= 1 << j; gx |= md << (2 * j); } else comp |= 1 << j;
+  }
+#pragma unroll
+  for (int t = 0; t < kRunRpt; ++t) {
     // Walsh-Hadamard transform over the outcome bits: v[mask] = sum_b
     // (-1)^popcount(b & mask) V[b]
 #pragma unroll
@@ -469,18 +482,11 @@ attr_meas_run(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, 
 #pragma unroll
       for (int i = 0; i < NB; ++i)
         if ((i & h) == 0) {
-          const float a = v[i], c = v[i | h];
-          v[i] = a + c;
-          v[i | h] = a - c;
+          const float a = v[t][i], c = v[t][i | h];
+          v[t][i] = a + c;
+          v[t][i | h] = a - c;
         }
-    if (r >= rows) continue;
-    // run m's digits (base 3): 0 computational, 1 X, 2 Y
-    int fixed = 0, comp = 0, gx = 0;
-#pragma unroll
-    for (int j = 0, mm = m; j < KOUT; ++j, mm /= 3) {
-      const int md = mm % 3;
-      if (md) { fixed |= 1 << j; gx |= md << (2 * j); } else comp |= 1 << j;
-    }
+    if (xr[t] >= p.n_rows) continue;
     // every subset z of the computational digits: Z there (mask bit set), I elsewhere
     for (int z = comp;; z = (z - 1) & comp) {
       int g = gx;
@@ -490,14 +496,14 @@ attr_meas_run(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, 
       float out = 0.f;
 #pragma unroll
       for (int i = 0; i < NB; ++i)
-        if (i == (fixed | z)) out = v[i];
+        if (i == (fixed | z)) out = v[t][i];
       if (staged) {
-        dst[((int64_t)s * G + g) * p.n_rows + x0 + r] = out;
+        dst[((int64_t)s * G + g) * p.n_rows + xr[t]] = out;
       } else {     // no init cut: the attributed layout, row x, the measured digits' columns
         int col = 0;
 #pragma unroll
         for (int j = 0; j < KOUT; ++j) col |= ((g >> (2 * j)) & 3) << p.col_shift_out[j];
-        dst[(x0 + r) * (int64_t)G + col] = out;
+        dst[xr[t] * (int64_t)G + col] = out;
       }
       if (z == 0) break;
     }
@@ -506,7 +512,7 @@ attr_meas_run(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, 
 
 template <typename T, int KOUT>
 int run_meas_run(const T* src, float* out, const AttrParams& p, int staged, cudaStream_t st) {
-  const int64_t xb = (p.n_rows + kRunRows - 1) / kRunRows;
+  const int64_t xb = (p.n_rows + kRunRows * kRunRpt - 1) / (kRunRows * kRunRpt);
   const int64_t ntask = xb * pow3(KOUT) << (2 * p.k_in);
   // one task per CTA (a grid of resident CTAs walking the tasks measured
   // slower: 86 against 76 us on the 32-qubit chain's middle subcircuits)
