@@ -194,12 +194,17 @@ attr_init_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p,
 // [P][F + 1] (conflict-free both ways), and stores walk the fiber fastest
 // when an init digit holds column bit 0 (ifast), else the (x, mu) index.
 constexpr int kColThreads = 256;
+// Fibers per CTA: 4096 values (16 KiB) per CTA, runs of 64 bytes per state at
+// F = 256; small blocks so that the grid spans several waves (a 32-fiber
+// block left the 1,024-CTA grid of an 11-qubit subcircuit with four cuts of
+// each kind a nearly empty second wave).
+__host__ __device__ constexpr int cols_fibers(int F) { return F >= 4096 ? 1 : (4096 / F > 64 ? 64 : 4096 / F); }
 
 template <int KIN>
 __global__ void __launch_bounds__(kColThreads)
 attr_init_cols(const float* __restrict__ src, float* __restrict__ dst, AttrParams p, int64_t n_fibers, int ifast) {
   constexpr int F = 1 << (2 * KIN);
-  constexpr int P = F >= 4096 ? 1 : (8192 / F > 64 ? 64 : 8192 / F);   // fibers per CTA (128-byte runs at F = 256)
+  constexpr int P = cols_fibers(F);
   constexpr int FS = F + 1;
   constexpr int LB = 16;                                                // loads in flight per thread
   __shared__ float buf[P * FS];
@@ -397,7 +402,7 @@ int dispatch_init(const T* src, float* out, const AttrParams& p, int final_layou
 template <int KIN>
 int run_init_cols(const float* src, float* out, const AttrParams& p, cudaStream_t st) {
   constexpr int F = 1 << (2 * KIN);
-  constexpr int P = F >= 4096 ? 1 : (8192 / F > 64 ? 64 : 8192 / F);
+  constexpr int P = cols_fibers(F);
   const int64_t n_fibers = p.n_rows << (2 * p.k_out);
   int ifast = 0;
   for (int j = 0; j < p.k_in; ++j) ifast |= p.col_shift_in[j] == 0;

@@ -145,11 +145,29 @@ struct TcOperand {
 bool tc_pair_supported(int64_t Kp);
 // num_kb_dev (nullable, device): the number of 64-wide k-blocks to use,
 // read by the kernel (at most Kp / 64); the operands' row stride stays Kp.
+// cmax (nullable, device, paired kernel only): for each 32-row x 64-column
+// block of the M x N result (stripe r = m / 32, block c = n / 64) its largest
+// value at cmax[r * ceil(N / 64) + c].
 int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
                         uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st,
-                        const int* num_kb_dev = nullptr);
+                        const int* num_kb_dev = nullptr, float* cmax = nullptr);
 int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
                    uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st,
-                   const int* num_kb_dev = nullptr);
+                   const int* num_kb_dev = nullptr, float* cmax = nullptr);
+
+// Block maxima of the final step's output (DD's top-T selection).  Set on
+// the calling thread around run_plan: when the final step runs on the paired
+// tensor-core GEMM over the full row range with M >= 32, N >= 64 and
+// ceil(M/32) * ceil(N/64) == per_item, it writes item b's block maxima at
+// cmax + b * per_item (layout as for launch_tc_pair_gemm) and records the
+// output geometry; otherwise `written` stays false.
+struct BlockMaxSink {
+  float* cmax = nullptr;
+  int64_t per_item = 0;
+  bool written = false;
+  int64_t M = 0, N = 0;
+  uint64_t mask_m = 0, mask_n = 0;
+};
+void set_block_max_sink(BlockMaxSink* sink);   // nullptr: none
 
 }  // namespace cutqc

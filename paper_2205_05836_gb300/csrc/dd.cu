@@ -39,26 +39,111 @@ __global__ void dd_merge_reduce(const float* __restrict__ part, int S, int64_t E
   dd_merge_reduce_body<false>(part, S, E, out, blockIdx.x, gridDim.x);
 }
 
-// CTA (job blockIdx.x, chunk blockIdx.y) of the top-T selection.
+// CTA (job blockIdx.x, chunk blockIdx.y) of the top-T selection.  gate
+// (nullable): the job is skipped unless gate[job] > gate_cap.
 template <int TCAP, bool kCand>
 __global__ void __launch_bounds__(1024)
 dd_topk_kernel(const float* __restrict__ vals, const int32_t* __restrict__ cidx, int64_t n, int64_t chunk_len, int T,
-               int32_t* __restrict__ top_idx, float* __restrict__ top_val) {
+               int32_t* __restrict__ top_idx, float* __restrict__ top_val, const int* __restrict__ gate = nullptr,
+               int gate_cap = 0) {
+  if (gate && __ldg(gate + blockIdx.x) <= gate_cap) return;
   dd_topk_body<TCAP, kCand, false>(vals, cidx, n, chunk_len, T, top_idx, top_val, blockIdx.x, blockIdx.y,
                                    gridDim.y);
 }
 
+// Top-T from block maxima.  The output of the final GEMM is cut into blocks
+// (32 rows x 64 columns), and the GEMM wrote each block's largest value.  Let
+// v* be the T-th largest of the block maxima: T distinct bins are >= v*, so
+// every bin among the T largest is >= v*, and so is the maximum of its block.
+// The blocks whose maximum is >= v* therefore hold all of the T largest bins
+// (exactly T blocks unless maxima tie at v*); only they are read again.
+constexpr int kBlockRows = 32, kBlockCols = 64, kBlockBins = kBlockRows * kBlockCols;
+constexpr int kBlockCap = 32;                         // blocks read again per job, at most
+constexpr int64_t kBlockMaxMinBins = (int64_t)1 << 22;   // smaller jobs scan their bins
+constexpr int64_t kBlockMaxChunk = (int64_t)1 << 12;      // block maxima per chunk of their scan
+
+// Blocks of job blockIdx.y whose maximum is >= v* (the T-th entry of the
+// job's top-T over its block maxima; -inf when it has fewer than T blocks).
+// count[job] may exceed cap: only the first cap are listed.
+__global__ void dd_block_collect(const float* __restrict__ cmax, int64_t C, const int32_t* __restrict__ kidx,
+                                 const float* __restrict__ kval, int T, int cap, int* __restrict__ count,
+                                 int32_t* __restrict__ list) {
+  const int job = blockIdx.y;
+  const float thr = kidx[(int64_t)job * T + T - 1] >= 0 ? kval[(int64_t)job * T + T - 1] : -INFINITY;
+  const float* c = cmax + (int64_t)job * C;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < C; i += (int64_t)gridDim.x * blockDim.x) {
+    if (__ldg(c + i) >= thr) {
+      const int p = atomicAdd(count + job, 1);
+      if (p < cap) list[(int64_t)job * cap + p] = (int32_t)i;
+    }
+  }
+}
+
+// CTA (slot blockIdx.x, job blockIdx.y): copies listed block `slot` of the
+// job as (value, bin index) pairs; unused slots get index -1.  The bin index
+// of output (m, n) is pdep(m, mask_m) | pdep(n, mask_n).
+__global__ void dd_block_gather(const float* __restrict__ bins, int64_t nb, const int* __restrict__ count,
+                                const int32_t* __restrict__ list, int cap, int64_t cols, int64_t M, int64_t N,
+                                uint64_t mask_m, uint64_t mask_n, float* __restrict__ gv, int32_t* __restrict__ gi) {
+  const int job = blockIdx.y, slot = blockIdx.x;
+  const int used = min(__ldg(count + job), cap);
+  float* ov = gv + ((int64_t)job * cap + slot) * kBlockBins;
+  int32_t* oi = gi + ((int64_t)job * cap + slot) * kBlockBins;
+  if (slot >= used) {
+    for (int e = threadIdx.x; e < kBlockBins; e += blockDim.x) oi[e] = -1;
+    return;
+  }
+  const int64_t blk = __ldg(list + (int64_t)job * cap + slot);
+  const int64_t r0 = (blk / cols) * kBlockRows, c0 = (blk % cols) * kBlockCols;
+  // the block's row and column offsets, deposited once; -1: beyond M or N
+  __shared__ int64_t roff[kBlockRows], coff[kBlockCols];
+  for (int t = threadIdx.x; t < kBlockRows + kBlockCols; t += blockDim.x) {
+    if (t < kBlockRows) {
+      const int64_t m = r0 + t;
+      roff[t] = m < M ? (int64_t)pdep64((uint64_t)m, mask_m) : -1;
+    } else {
+      const int64_t n = c0 + (t - kBlockRows);
+      coff[t - kBlockRows] = n < N ? (int64_t)pdep64((uint64_t)n, mask_n) : -1;
+    }
+  }
+  __syncthreads();
+  const float* b = bins + (int64_t)job * nb;
+  for (int e = threadIdx.x; e < kBlockBins; e += blockDim.x) {
+    const int64_t ro = roff[e / kBlockCols], co = coff[e % kBlockCols];
+    if (ro >= 0 && co >= 0) {
+      const int64_t off = ro | co;
+      ov[e] = __ldg(b + off);
+      oi[e] = (int32_t)off;
+    } else {
+      oi[e] = -1;
+    }
+  }
+}
+
+
 // Large jobs: chunks of the chunked first pass of the top-T selection.
 constexpr int64_t kTopkChunkMin = (int64_t)1 << 16;   // bins per chunk at least
 constexpr int64_t kTopkChunksMax = 2048;
-inline int64_t topk_chunks(int64_t nb) {
-  if (nb <= kTopkChunkMin) return 1;
-  return std::min<int64_t>(kTopkChunksMax, (nb + kTopkChunkMin - 1) / kTopkChunkMin);
+inline int64_t topk_chunks(int64_t nb, int64_t min_chunk = kTopkChunkMin) {
+  if (nb <= min_chunk) return 1;
+  return std::min<int64_t>(kTopkChunksMax, (nb + min_chunk - 1) / min_chunk);
 }
 // candidate scratch of the chunked pass for n_jobs jobs of nb bins (bytes)
-inline size_t topk_scratch(int64_t nb, int n_jobs) {
-  const int64_t c = topk_chunks(nb);
+inline size_t topk_scratch(int64_t nb, int n_jobs, int64_t min_chunk = kTopkChunkMin) {
+  const int64_t c = topk_chunks(nb, min_chunk);
   return c > 1 ? align_up((size_t)n_jobs * c * 32 * (sizeof(int32_t) + sizeof(float)), 256) : 0;
+}
+
+// scratch of the block-maximum selection for n_jobs jobs of nb bins (bytes)
+inline size_t block_max_scratch(int64_t nb, int n_jobs) {
+  if (nb < kBlockMaxMinBins) return 0;
+  const int64_t C = nb / kBlockBins;
+  const size_t per = sizeof(int32_t) + sizeof(float);
+  return align_up((size_t)n_jobs * C * sizeof(float), 256) + topk_scratch(C, n_jobs, kBlockMaxChunk) +
+         align_up((size_t)n_jobs * 32 * per, 256) + align_up((size_t)n_jobs * sizeof(int), 256) +
+         align_up((size_t)n_jobs * kBlockCap * sizeof(int32_t), 256) +
+         align_up((size_t)n_jobs * kBlockCap * kBlockBins * per, 256) +
+         align_up((size_t)n_jobs * kBlockCap * 32 * per, 256);
 }
 
 __global__ void sum_f64_kernel(const float* __restrict__ x, int64_t n, double* __restrict__ sum) {
@@ -171,7 +256,8 @@ int dd_step_ws(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits,
   if (n_jobs < 1) return set_error(CUTQC_EINVAL, "n_jobs must be >= 1");
   ContractionPlan plan;
   if ((rc = plan_contraction_batched(in, precision, n_jobs, &plan, true))) return rc;
-  *bytes = align_up(plan.ws_bytes, 256) + topk_scratch((int64_t)1 << tot, n_jobs);
+  *bytes = align_up(plan.ws_bytes, 256) + topk_scratch((int64_t)1 << tot, n_jobs) +
+           (precision != CUTQC_PREC_FP32_SIMT ? block_max_scratch((int64_t)1 << tot, n_jobs) : 0);
   return CUTQC_OK;
 }
 
@@ -300,6 +386,48 @@ extern "C" int cutqc_dd_step_workspace_size(int n_sub, const cutqc_subcircuit* s
   return dd_step_ws(n_sub, s, active_bits, n_jobs, CUTQC_PREC_FP32_SIMT, bytes);
 }
 
+// The T largest of each job's nb entries (vals + job * nb) into top_idx /
+// top_val [n_jobs][T]: one CTA per job, or for large jobs a chunked pass
+// into the candidate scratch cand (topk_scratch(nb, n_jobs) bytes) and one
+// CTA per job over the chunks' candidates.  gate: as for dd_topk_kernel.
+static int launch_topk_scan(const float* vals, int64_t nb, int n_jobs, int topk, int cap, int32_t* cand,
+                            int32_t* top_idx, float* top_val, const int* gate, int gate_cap, cudaStream_t st,
+                            int64_t min_chunk = kTopkChunkMin) {
+  const int64_t chunks = topk_chunks(nb, min_chunk);
+  if (chunks == 1) {
+    const int threads = (int)std::min<int64_t>(cap, std::max<int64_t>(32, (nb + 31) / 32 * 32));
+    if (topk <= 4)
+      dd_topk_kernel<4, false><<<dim3(n_jobs, 1), threads, 0, st>>>(vals, nullptr, nb, nb, topk, top_idx, top_val,
+                                                                    gate, gate_cap);
+    else
+      dd_topk_kernel<32, false><<<dim3(n_jobs, 1), threads, 0, st>>>(vals, nullptr, nb, nb, topk, top_idx, top_val,
+                                                                     gate, gate_cap);
+  } else {
+    int32_t* cidx = cand;
+    float* cval = (float*)(cidx + (size_t)n_jobs * chunks * 32);
+    const int64_t clen = (nb + chunks - 1) / chunks;
+    const int64_t ncand = chunks * topk;
+    const int64_t cthreads = std::min<int64_t>(cap, 512);   // several CTAs per SM: more loads in flight
+    if (topk <= 4) {
+      dd_topk_kernel<4, false><<<dim3(n_jobs, (unsigned)chunks), (int)cthreads, 0, st>>>(vals, nullptr, nb, clen,
+                                                                                        topk, cidx, cval, gate,
+                                                                                        gate_cap);
+      CUTQC_LAUNCH_CHECK("dd_topk_kernel (chunks)");
+      dd_topk_kernel<4, true><<<dim3(n_jobs, 1), 1024, 0, st>>>(cval, cidx, ncand, ncand, topk, top_idx, top_val,
+                                                                gate, gate_cap);
+    } else {
+      dd_topk_kernel<32, false><<<dim3(n_jobs, (unsigned)chunks), (int)cthreads, 0, st>>>(vals, nullptr, nb, clen,
+                                                                                         topk, cidx, cval, gate,
+                                                                                         gate_cap);
+      CUTQC_LAUNCH_CHECK("dd_topk_kernel (chunks)");
+      dd_topk_kernel<32, true><<<dim3(n_jobs, 1), 1024, 0, st>>>(cval, cidx, ncand, ncand, topk, top_idx, top_val,
+                                                                 gate, gate_cap);
+    }
+  }
+  CUTQC_LAUNCH_CHECK("dd_topk_kernel");
+  return CUTQC_OK;
+}
+
 // topk_threads: threads per job of the top-T pass (0: up to 1024).
 // precision: CUTQC_PREC_FP32_SIMT, or CUTQC_PREC_FP16X3_TC(_PRUNE) for jobs
 // of at least 4 bins whose bins start 16-byte aligned (smaller ones take
@@ -325,44 +453,77 @@ static int dd_step_impl(int n_sub, const cutqc_subcircuit* s, const int32_t* act
   ContractionPlan plan;
   if ((rc = plan_contraction_batched(in, precision, n_jobs, &plan))) return rc;
   const size_t plan_ws = align_up(plan.ws_bytes, 256);
-  const size_t need = plan_ws + topk_scratch(nb, n_jobs);
+  const size_t topk_ws = topk_scratch(nb, n_jobs);
+  const size_t bmax_ws = precision != CUTQC_PREC_FP32_SIMT && topk > 0 ? block_max_scratch(nb, n_jobs) : 0;
+  const size_t need = plan_ws + topk_ws + bmax_ws;
   if (ws_bytes < need || (need && !ws_dev)) return set_error(CUTQC_ENOMEM, "DD workspace needs %zu bytes", need);
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<int64_t> bstride(n_sub);
   for (int i = 0; i < n_sub; ++i) bstride[i] = ((int64_t)1 << in[i].o) << (2 * in[i].edges.size());
   if (bin_sum) CUTQC_CUDA_TRY(cudaMemsetAsync(bin_sum, 0, sizeof(double) * n_jobs, st));
+  uint8_t* bm = (uint8_t*)ws_dev + plan_ws + topk_ws;
+  BlockMaxSink sink;
+  if (bmax_ws) {
+    sink.cmax = (float*)bm;
+    sink.per_item = nb / kBlockBins;
+    set_block_max_sink(&sink);
+  }
   rc = run_plan(plan, merged, bstride.data(), n_jobs, bins, nb, bin_sum, std::ldexp(1.0f, -plan.K), precision, 0, -1,
                 (uint8_t*)ws_dev, st);
+  set_block_max_sink(nullptr);
   if (rc) return rc;
   if (topk > 0) {
-    const int64_t cap = topk_threads > 0 ? std::min(1024, std::max(32, topk_threads / 32 * 32)) : 1024;
-    const int64_t chunks = topk_chunks(nb);
-    if (chunks == 1) {
-      const int threads = (int)std::min<int64_t>(cap, std::max<int64_t>(32, (nb + 31) / 32 * 32));
-      if (topk <= 4)
-        dd_topk_kernel<4, false><<<dim3(n_jobs, 1), threads, 0, st>>>(bins, nullptr, nb, nb, topk, top_idx, top_val);
-      else
-        dd_topk_kernel<32, false><<<dim3(n_jobs, 1), threads, 0, st>>>(bins, nullptr, nb, nb, topk, top_idx, top_val);
+    const int threads = topk_threads > 0 ? std::min(1024, std::max(32, topk_threads / 32 * 32)) : 1024;
+    int32_t* cidx = (int32_t*)((uint8_t*)ws_dev + plan_ws);
+    if (!sink.written) {
+      if ((rc = launch_topk_scan(bins, nb, n_jobs, topk, threads, cidx, top_idx, top_val, nullptr, 0, st))) return rc;
+      return CUTQC_OK;
+    }
+    // block maxima: the T largest of them, the blocks at or above the T-th,
+    // their bins; the full scan runs only for jobs with more than
+    // kBlockCap such blocks (maxima tied at the threshold)
+    const int64_t C = sink.per_item;
+    const size_t per = sizeof(int32_t) + sizeof(float);
+    uint8_t* p = bm + align_up((size_t)n_jobs * C * sizeof(float), 256);
+    int32_t* k1 = (int32_t*)p;
+    p += topk_scratch(C, n_jobs, kBlockMaxChunk);
+    int32_t* kidx = (int32_t*)p;
+    float* kval = (float*)(kidx + (size_t)n_jobs * 32);
+    p += align_up((size_t)n_jobs * 32 * per, 256);
+    int* count = (int*)p;
+    p += align_up((size_t)n_jobs * sizeof(int), 256);
+    int32_t* list = (int32_t*)p;
+    p += align_up((size_t)n_jobs * kBlockCap * sizeof(int32_t), 256);
+    float* gv = (float*)p;
+    int32_t* gi = (int32_t*)(gv + (size_t)n_jobs * kBlockCap * kBlockBins);
+    p += align_up((size_t)n_jobs * kBlockCap * kBlockBins * per, 256);
+    int32_t* bidx = (int32_t*)p;
+    float* bval = (float*)(bidx + (size_t)n_jobs * kBlockCap * 32);
+    if ((rc = launch_topk_scan(sink.cmax, C, n_jobs, topk, threads, k1, kidx, kval, nullptr, 0, st, kBlockMaxChunk)))
+      return rc;
+    CUTQC_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int) * n_jobs, st));
+    const int64_t cblocks = std::min<int64_t>((C + 255) / 256, (int64_t)sm_count() * 4);
+    dd_block_collect<<<dim3((unsigned)cblocks, n_jobs), 256, 0, st>>>(sink.cmax, C, kidx, kval, topk, kBlockCap, count,
+                                                                     list);
+    CUTQC_LAUNCH_CHECK("dd_block_collect");
+    dd_block_gather<<<dim3(kBlockCap, n_jobs), 256, 0, st>>>(bins, nb, count, list, kBlockCap,
+                                                            (sink.N + kBlockCols - 1) / kBlockCols, sink.M, sink.N,
+                                                            sink.mask_m, sink.mask_n, gv, gi);
+    CUTQC_LAUNCH_CHECK("dd_block_gather");
+    const int64_t gn = (int64_t)kBlockCap * kBlockBins, bn = (int64_t)kBlockCap * topk;
+    if (topk <= 4) {
+      dd_topk_kernel<4, true><<<dim3(n_jobs, kBlockCap), 256, 0, st>>>(gv, gi, gn, kBlockBins, topk, bidx, bval);
+      CUTQC_LAUNCH_CHECK("dd_topk_kernel (blocks)");
+      dd_topk_kernel<4, true><<<dim3(n_jobs, 1), 256, 0, st>>>(bval, bidx, bn, bn, topk, top_idx, top_val);
     } else {
-      // chunked pass into the candidate scratch, then one CTA per job
-      int32_t* cidx = (int32_t*)((uint8_t*)ws_dev + plan_ws);
-      float* cval = (float*)(cidx + (size_t)n_jobs * chunks * 32);
-      const int64_t clen = (nb + chunks - 1) / chunks;
-      const int64_t ncand = chunks * topk;
-      const int64_t cthreads = std::min<int64_t>(cap, 512);   // several CTAs per SM: more loads in flight
-      if (topk <= 4) {
-        dd_topk_kernel<4, false><<<dim3(n_jobs, (unsigned)chunks), (int)cthreads, 0, st>>>(bins, nullptr, nb, clen,
-                                                                                          topk, cidx, cval);
-        CUTQC_LAUNCH_CHECK("dd_topk_kernel (chunks)");
-        dd_topk_kernel<4, true><<<dim3(n_jobs, 1), 1024, 0, st>>>(cval, cidx, ncand, ncand, topk, top_idx, top_val);
-      } else {
-        dd_topk_kernel<32, false><<<dim3(n_jobs, (unsigned)chunks), (int)cthreads, 0, st>>>(bins, nullptr, nb, clen,
-                                                                                           topk, cidx, cval);
-        CUTQC_LAUNCH_CHECK("dd_topk_kernel (chunks)");
-        dd_topk_kernel<32, true><<<dim3(n_jobs, 1), 1024, 0, st>>>(cval, cidx, ncand, ncand, topk, top_idx, top_val);
-      }
+      dd_topk_kernel<32, true><<<dim3(n_jobs, kBlockCap), 256, 0, st>>>(gv, gi, gn, kBlockBins, topk, bidx, bval);
+      CUTQC_LAUNCH_CHECK("dd_topk_kernel (blocks)");
+      dd_topk_kernel<32, true><<<dim3(n_jobs, 1), 256, 0, st>>>(bval, bidx, bn, bn, topk, top_idx, top_val);
     }
     CUTQC_LAUNCH_CHECK("dd_topk_kernel");
+    // jobs whose maxima tied beyond the cap: the full scan, gated on the device
+    if ((rc = launch_topk_scan(bins, nb, n_jobs, topk, threads, cidx, top_idx, top_val, count, kBlockCap, st)))
+      return rc;
   }
   return CUTQC_OK;
 }

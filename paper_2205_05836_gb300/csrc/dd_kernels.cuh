@@ -211,6 +211,64 @@ __device__ __forceinline__ bool dd_better(float v, int i, float w, int j) {
   return v > w || (v == w && i < j);
 }
 
+// One thread's best T <= TCAP entries, sorted.  Short lists insert by a
+// compare-and-swap chain over the kept slots: every index is a compile-time
+// constant, so the list lives in registers.  Once the list is full, thr/thri
+// hold its T-th entry and an entry enters only if it ranks before that one.
+template <int TCAP>
+struct TopList {
+  float lv[TCAP];
+  int li[TCAP];
+  int cnt;
+  float thr;
+  int thri;
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int u = 0; u < TCAP; ++u) { lv[u] = -INFINITY; li[u] = -1; }   // read only once filled
+    cnt = 0;
+    thr = -INFINITY;
+    thri = -1;
+  }
+  // long lists: shift the worse entries right and write the new one at a
+  // computed slot (the list sits in local memory; insertions are rare, so
+  // one out-of-line copy serves every call site)
+  __device__ __noinline__ void insert_long(float v, int idx, int T) {
+    int pos = cnt < T ? cnt : T - 1;
+#pragma unroll
+    for (int u = TCAP - 1; u > 0; --u)
+      if (u <= pos && dd_better(v, idx, lv[u - 1], li[u - 1])) { lv[u] = lv[u - 1]; li[u] = li[u - 1]; pos = u - 1; }
+    lv[pos] = v;
+    li[pos] = idx;
+  }
+  __device__ __forceinline__ void offer(float v, int idx, int T) {
+    if (cnt == T && !dd_better(v, idx, thr, thri)) return;
+    if constexpr (TCAP <= 8) {
+      float cv = v;
+      int cix = idx;
+#pragma unroll
+      for (int u = 0; u < TCAP; ++u) {
+        if (u < cnt) {
+          if (dd_better(cv, cix, lv[u], li[u])) {
+            const float tv = lv[u];
+            const int ti = li[u];
+            lv[u] = cv; li[u] = cix; cv = tv; cix = ti;
+          }
+        } else if (u == cnt && u < T) {
+          lv[u] = cv; li[u] = cix;
+        }
+      }
+    } else {
+      insert_long(v, idx, T);
+    }
+    if (cnt < T) ++cnt;
+    if (cnt == T) {
+#pragma unroll
+      for (int u = 0; u < TCAP; ++u)
+        if (u == T - 1) { thr = lv[u]; thri = li[u]; }
+    }
+  }
+};
+
 template <int TCAP, bool kCand, bool kCoherent>
 __device__ __forceinline__ void dd_topk_body(const float* __restrict__ vals, const int32_t* __restrict__ cidx,
                                              int64_t n, int64_t chunk_len, int T, int32_t* __restrict__ top_idx,
@@ -224,26 +282,15 @@ __device__ __forceinline__ void dd_topk_body(const float* __restrict__ vals, con
   const int64_t hi = lo + chunk_len < n ? lo + chunk_len : n;
   const int64_t slot = ((int64_t)job * nchunks + chunk) * T;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float lv[TCAP];
-  int li[TCAP];
-#pragma unroll
-  for (int u = 0; u < TCAP; ++u) { lv[u] = -INFINITY; li[u] = -1; }   // read only once filled
-  int cnt = 0;
-  auto offer = [&](float v, int idx) {
-    if (cnt == T && !dd_better(v, idx, lv[T - 1], li[T - 1])) return;
-    int pos = cnt < T ? cnt : T - 1;
-#pragma unroll
-    for (int u = TCAP - 1; u > 0; --u)
-      if (u <= pos && dd_better(v, idx, lv[u - 1], li[u - 1])) { lv[u] = lv[u - 1]; li[u] = li[u - 1]; pos = u - 1; }
-    // pos is now the first slot whose left neighbour ranks before (v, idx)
-    lv[pos] = v;
-    li[pos] = idx;
-    if (cnt < T) ++cnt;
-  };
+  TopList<TCAP> L;
+  L.init();
+  auto offer = [&](float v, int idx) { L.offer(v, idx, T); };
   int64_t tail0 = lo;
   if (!kCand && (((uintptr_t)(b + lo)) & 15) == 0) {
-    // bins: float4 loads, four in flight per thread (the order in which a
-    // thread offers entries does not matter: ties compare indices)
+    // bins: float4 loads, four in flight per thread.  A thread offers its
+    // entries in increasing index order, so once its list is full an entry
+    // equal to the T-th kept value never enters and a float4 whose largest
+    // lane is <= thr is skipped whole.
     constexpr int U = 4;
     const float4* p4 = reinterpret_cast<const float4*>(b + lo);
     const int64_t n4 = (hi - lo) >> 2;
@@ -257,7 +304,8 @@ __device__ __forceinline__ void dd_topk_body(const float* __restrict__ vals, con
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int64_t qu = q + u * (int64_t)blockDim.x;
-        if (qu < n4) {
+        const float m = fmaxf(fmaxf(v[u].x, v[u].y), fmaxf(v[u].z, v[u].w));
+        if (qu < n4 && (L.cnt < T || m > L.thr)) {
           const int i0 = (int)(lo + 4 * qu);
           offer(v[u].x, i0); offer(v[u].y, i0 + 1); offer(v[u].z, i0 + 2); offer(v[u].w, i0 + 3);
         }
@@ -277,7 +325,7 @@ __device__ __forceinline__ void dd_topk_body(const float* __restrict__ vals, con
     int bi = -1;
 #pragma unroll
     for (int u = 0; u < TCAP; ++u)
-      if (u == head && head < cnt) { bv = lv[u]; bi = li[u]; }
+      if (u == head && head < L.cnt) { bv = L.lv[u]; bi = L.li[u]; }
     for (int off = 16; off; off >>= 1) {
       const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
@@ -302,11 +350,11 @@ __device__ __forceinline__ void dd_topk_body(const float* __restrict__ vals, con
     }
     __syncthreads();
     // the owner of the winning index advances (indices are distinct)
-    if (head < cnt && win_i >= 0) {
+    if (head < L.cnt && win_i >= 0) {
       int cur = -1;
 #pragma unroll
       for (int u = 0; u < TCAP; ++u)
-        if (u == head) cur = li[u];
+        if (u == head) cur = L.li[u];
       if (cur == win_i) ++head;
     }
     __syncthreads();

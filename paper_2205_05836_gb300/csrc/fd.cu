@@ -34,6 +34,10 @@ static thread_local std::string g_last_error;
 // contraction's GEMM launch (then clears): see cutqc_fd_timing_events.
 static thread_local cudaEvent_t g_gemm_start = nullptr, g_gemm_stop = nullptr;
 
+// Block maxima requested for the next final step on this thread.
+static thread_local BlockMaxSink* g_bmax = nullptr;
+void set_block_max_sink(BlockMaxSink* sink) { g_bmax = sink; }
+
 int set_error(int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -404,8 +408,20 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
         TcOperand ta{ah, al, as, M}, tb{bh, bl, bs, stg.N};
         const bool timed = stg.final_stage && g_gemm_start && b == 0;
         if (timed) CUTQC_CUDA_TRY(cudaEventRecord(g_gemm_start, st));
+        float* cmax = nullptr;
+        if (stg.final_stage && g_bmax && g_bmax->cmax && !partial && tc_pair_supported(stg.Kp) && M >= 32 &&
+            stg.N >= 64 && ((M + 31) / 32) * ((stg.N + 63) / 64) == g_bmax->per_item) {
+          cmax = g_bmax->cmax + (size_t)b * g_bmax->per_item;
+          if (b == batch - 1) {
+            g_bmax->written = true;
+            g_bmax->M = M;
+            g_bmax->N = stg.N;
+            g_bmax->mask_m = stg.mask_m;
+            g_bmax->mask_n = stg.mask_n;
+          }
+        }
         rc = launch_tc_gemm(ta, tb, stg.Kp, alpha, stg.mask_m, stg.mask_n, dst + b * dst_b,
-                            sum_ptr ? sum_ptr + b : nullptr, streaming, st, prune ? meta + 1 : nullptr);
+                            sum_ptr ? sum_ptr + b : nullptr, streaming, st, prune ? meta + 1 : nullptr, cmax);
         if (rc) return rc;
         if (stg.final_stage && g_gemm_start && b == batch - 1) {
           CUTQC_CUDA_TRY(cudaEventRecord(g_gemm_stop, st));

@@ -115,6 +115,8 @@ struct PairArgs {
   uint64_t coff_lo[64]; // pdep(c, mask_n) for c < 64: column offsets inside a 64-aligned group
   float* out;
   double* sum;
+  float* cmax;          // nullable: largest value of each 32-row x 64-column block of the output
+  int64_t cmax_cols;    // blocks per 32-row stripe: ceil(N / 64)
   int streaming;
   int* status;
 };
@@ -231,7 +233,7 @@ __device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
       : "memory");
 }
 
-template <bool kRowMajor>
+template <bool kRowMajor, bool kMax>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) {
   constexpr int STAGES = Cfg<kRowMajor>::STAGES;
@@ -404,6 +406,13 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
     const uint32_t lead_afull = map_to_rank(smem_u32(&tail->afull), 0);
     float tot[EPI_COLS];
     bool ok = true;
+    static_assert(EPI_COLS == 64, "block maxima cover one warp's 32 rows x 64 columns");
+    // the warp's block of a tile (rows row0 .. +31, columns col0 .. +63):
+    // its largest value, for the top-T selection of the caller
+    auto put_cmax = [&](float mx, int64_t row0, int64_t col0) {
+      for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      if (lane == 0 && row0 < args.M && col0 < args.N) args.cmax[(row0 >> 5) * args.cmax_cols + (col0 >> 6)] = mx;
+    };
     for (int64_t item = pair; item < args.num_items && ok && !*abort_flag; item += num_pairs) {
       const int mp = (int)(item % args.num_mp);
       const int64_t t0 = (item / args.num_mp) * args.tiles_per_item;
@@ -506,6 +515,7 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
           const int64_t nb0 = nbase + 2 * (lane & 3);
           const int64_t cb = (args.n_contig ? nbase : (int64_t)pdep64((uint64_t)nbase, args.mask_n)) + 2 * (lane & 3);
           float part = 0.f;     // this thread's 64 outputs of the tile; float64 across tiles
+          [[maybe_unused]] float mx = -INFINITY;
 #pragma unroll
           for (int h2 = 0; h2 < 2; ++h2)
 #pragma unroll
@@ -519,10 +529,12 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
                 if (mm < args.M && nb0 + 8 * q < args.N) {
                   __stcs(reinterpret_cast<float2*>(orow + 8 * q), make_float2(a, b));
                   part += a + b;
+                  if constexpr (kMax) mx = fmaxf(mx, fmaxf(a, b));
                 }
               }
             }
           if (args.sum) local += (double)part;
+          if constexpr (kMax) put_cmax(mx, mrow0, nbase);
         } else {
           const uint64_t roff =
               mvalid ? (args.m_shift >= 0 ? ((uint64_t)m << args.m_shift) : pdep64((uint64_t)m, args.mask_m)) : 0;
@@ -535,6 +547,7 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
             const uint64_t cbase = args.n_contig ? (uint64_t)nbase : pdep64((uint64_t)nbase, args.mask_n);
             float* const obase = args.out + (mvalid ? roff : 0);
             float part = 0.f;
+            [[maybe_unused]] float mx = -INFINITY;
 #pragma unroll
             for (int c = 0; c < EPI_COLS; ++c) {
               if (nbase + c >= args.N) break;
@@ -543,13 +556,16 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
                 float* ptr = obase + (cbase | args.coff_lo[c]);
                 if (args.streaming) __stcs(ptr, val); else *ptr = val;
                 part += val;
+                if constexpr (kMax) mx = fmaxf(mx, val);
               }
             }
             if (args.sum) local += (double)part;
+            if constexpr (kMax) put_cmax(mx, mrow0, nbase);
             continue;
           }
           // general bit deposit through the staging block (XOR-swizzled by
           // row) so that lanes walk the columns of one row at a time
+          [[maybe_unused]] float mx = -INFINITY;
 #pragma unroll
           for (int q = 0; q < EPI_COLS / 32; ++q) {
             const int64_t n0 = nbase + q * 32;
@@ -572,10 +588,12 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
                 float* ptr = args.out + (roff_r | coff);
                 if (args.streaming) __stcs(ptr, val); else *ptr = val;
                 part += val;
+                if constexpr (kMax) mx = fmaxf(mx, val);
               }
             }
             if (args.sum) local += (double)part;
           }
+          if constexpr (kMax) put_cmax(mx, mrow0, nbase);
         }
       }
     }
@@ -641,7 +659,7 @@ int set_pair_tiles_per_item(int t) {
 
 int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
                         uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st,
-                        const int* num_kb_dev) {
+                        const int* num_kb_dev, float* cmax) {
   if (a.rows <= 0 || b.rows <= 0) return CUTQC_OK;
   if (!tc_pair_supported(Kp)) return set_error(CUTQC_EINVAL, "paired tensor-core K must be 64..256, a multiple of 64");
   if (a.rows >= ((int64_t)1 << 30) || b.rows >= ((int64_t)1 << 30)) return set_error(CUTQC_EUNSUPPORTED, "too many rows");
@@ -677,6 +695,8 @@ int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, floa
   for (int c = 0; c < 64; ++c) args.coff_lo[c] = pdep64((uint64_t)c, mask_n);
   args.out = out;
   args.sum = sum;
+  args.cmax = cmax;
+  args.cmax_cols = (b.rows + 63) / 64;
   args.streaming = streaming;
   args.status = device_status_ptr();
   // direct 8-byte stores from registers when column bits 0..5 are output
@@ -692,17 +712,26 @@ int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, floa
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(mu);
     if (!done.count(dev)) {
-      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_pair_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem_bytes<true>()));
-      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_pair_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem_bytes<false>()));
+      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_pair_gemm_kernel<true, false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<true>()));
+      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_pair_gemm_kernel<false, false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<false>()));
+      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_pair_gemm_kernel<true, true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<true>()));
+      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_pair_gemm_kernel<false, true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<false>()));
       done.insert(dev);
     }
   }
   const int64_t pairs = std::min<int64_t>(args.num_items, pairs_avail);
   const int grid = (int)(2 * pairs);
-  if (row_major) tc_pair_gemm_kernel<true><<<grid, NUM_THREADS, smem_bytes<true>(), st>>>(maps, args);
-  else tc_pair_gemm_kernel<false><<<grid, NUM_THREADS, smem_bytes<false>(), st>>>(maps, args);
+  if (row_major) {
+    if (cmax) tc_pair_gemm_kernel<true, true><<<grid, NUM_THREADS, smem_bytes<true>(), st>>>(maps, args);
+    else tc_pair_gemm_kernel<true, false><<<grid, NUM_THREADS, smem_bytes<true>(), st>>>(maps, args);
+  } else {
+    if (cmax) tc_pair_gemm_kernel<false, true><<<grid, NUM_THREADS, smem_bytes<false>(), st>>>(maps, args);
+    else tc_pair_gemm_kernel<false, false><<<grid, NUM_THREADS, smem_bytes<false>(), st>>>(maps, args);
+  }
   CUTQC_LAUNCH_CHECK("tc_pair_gemm_kernel");
   return CUTQC_OK;
 }

@@ -414,3 +414,92 @@ def test_dd_dense_topk_candidates_with_ties(cq, T):
     assert [float(v) for v in js[0].top_val[:T]] == [float(b[i]) for i in order]
     assert len(np.unique(b)) < (1 << n) // 100          # ties are plentiful
     assert cq.cutqc_device_status() == 0
+
+
+def _two_sub_dense_job(cq, o0, o1, T, A0, A1):
+    """A dense job of two synthetic subcircuits joined by one cut (every
+    output active, 2^(o0+o1) bins) on the tensor-core path.  Returns the
+    job record and the bins written."""
+    import torch
+    from types import SimpleNamespace
+    s0 = SimpleNamespace(w=o0 + 1, in_local=[], in_edge=[], out_local=[o0], out_edge=[0],
+                         out_qubit=list(range(o1, o1 + o0)), edges=[0], o=o0)
+    s1 = SimpleNamespace(w=o1, in_local=[0], in_edge=[0], out_local=[], out_edge=[],
+                         out_qubit=list(range(o1)), edges=[0], o=o1)
+    att = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda() for a in (A0, A1)]
+    n = o0 + o1
+    jobs, n_jobs, bins = cq.cutqc_dd_run_async([s0, s1], att, n, n, 1, T, max_jobs=2, options={"precision": 1})
+    js = cq.dd_jobs_from_device(jobs, n_jobs)
+    assert len(js) == 1 and js[0].n_active == n
+    return js[0], bins[:1 << n].cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case,T", [("uniform", 1), ("uniform", 4), ("uniform", 32), ("planted", 4),
+                                    ("planted", 8), ("small_ints", 4)])
+def test_dd_topk_from_block_maxima(cq, case, T):
+    """Jobs of 2^24 bins on the tensor-core path, where the final GEMM also
+    writes the largest value of each 32 x 64 block of its output and the
+    selection reads again only the blocks whose maximum reaches the T-th
+    largest block maximum.  Cases: distinct uniform values (exactly T
+    blocks); five planted bins of one top value in separate blocks (T = 4:
+    five blocks tie at the threshold; T = 8: the threshold value is held by
+    about a hundred bins, more blocks than are read again, so the full scan
+    runs); small-integer entries (every top value tied across many blocks).
+    The T selected bins must be exactly the first T of the order (value
+    descending, bin index ascending) over the bins written."""
+    o0 = o1 = 12
+    rng = np.random.default_rng(700 + T + len(case))
+    if case == "uniform":
+        A0 = rng.random((1 << o0, 4))
+        A1 = rng.random((1 << o1, 4))
+    else:
+        A0 = rng.integers(0, 3, size=(1 << o0, 4)).astype(np.float64)
+        A1 = rng.integers(0, 3, size=(1 << o1, 4)).astype(np.float64)
+        if case == "planted":
+            r = int(rng.integers(0, 1 << o0))
+            cols = rng.choice(1 << o1, size=5, replace=False)
+            A0[r] = 3.0
+            A1[cols] = 3.0
+            assert len(set(int(c) // 64 for c in cols)) == 5      # five separate blocks
+    job, b = _two_sub_dense_job(cq, o0, o1, T, A0, A1)
+    if case != "uniform":
+        assert np.array_equal(b, (A0 @ A1.T).reshape(-1) * 0.5)   # exact: small integers
+    order = np.lexsort((np.arange(b.size), -b))[:T]
+    assert list(job.top_idx[:T]) == [int(i) for i in order]
+    assert [float(v) for v in job.top_val[:T]] == [float(b[i]) for i in order]
+    if case == "planted":
+        assert np.sum(b == b.max()) == 5
+    assert cq.cutqc_device_status() == 0
+
+
+@pytest.mark.gpu
+def test_dd_topk_from_block_maxima_batched_level(cq):
+    """A second level of four jobs of 2^22 bins each (two synthetic
+    subcircuits of 22 outputs joined by one cut, M = 22): the level's GEMM
+    runs once per job with each job's block maxima at its own offset.  Each
+    job's T selected bins must be the first T of the order (value
+    descending, index ascending) over that job's bins."""
+    import torch
+    from types import SimpleNamespace
+    o0 = o1 = 22
+    T = 4
+    s0 = SimpleNamespace(w=o0 + 1, in_local=[], in_edge=[], out_local=[o0], out_edge=[0],
+                         out_qubit=list(range(o1, o1 + o0)), edges=[0], o=o0)
+    s1 = SimpleNamespace(w=o1, in_local=[0], in_edge=[0], out_local=[], out_edge=[],
+                         out_qubit=list(range(o1)), edges=[0], o=o1)
+    rng = np.random.default_rng(722)
+    att = [torch.from_numpy(rng.random((1 << o, 4), dtype=np.float32)).cuda() for o in (o0, o1)]
+    n = o0 + o1
+    jobs, n_jobs, bins = cq.cutqc_dd_run_async([s0, s1], att, n, 22, 2, T, max_jobs=1 + T,
+                                               options={"precision": 1})
+    js = cq.dd_jobs_from_device(jobs, n_jobs)
+    level1 = [j for j in js if j.level == 1]
+    assert len(level1) == T
+    for j in level1:
+        assert j.n_active == 22
+        b = bins[j.bins_offset:j.bins_offset + (1 << 22)].cpu().numpy().astype(np.float64)
+        order = np.lexsort((np.arange(b.size), -b))[:T]
+        assert list(j.top_idx[:T]) == [int(i) for i in order]
+        assert [float(v) for v in j.top_val[:T]] == [float(b[i]) for i in order]
+    assert cq.cutqc_device_status() == 0
