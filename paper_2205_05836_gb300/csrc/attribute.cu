@@ -194,11 +194,9 @@ attr_init_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p,
 // [P][F + 1] (conflict-free both ways), and stores walk the fiber fastest
 // when an init digit holds column bit 0 (ifast), else the (x, mu) index.
 constexpr int kColThreads = 256;
-// Fibers per CTA: 4096 values (16 KiB) per CTA, runs of 64 bytes per state at
-// F = 256; small blocks so that the grid spans several waves (a 32-fiber
-// block left the 1,024-CTA grid of an 11-qubit subcircuit with four cuts of
-// each kind a nearly empty second wave).
-__host__ __device__ constexpr int cols_fibers(int F) { return F >= 4096 ? 1 : (4096 / F > 64 ? 64 : 4096 / F); }
+// Fibers per CTA: 8192 values (32 KiB) per CTA, runs of 128 bytes per state
+// at F = 256.  (16 KiB blocks, twice the CTAs, measured the same.)
+__host__ __device__ constexpr int cols_fibers(int F) { return F >= 4096 ? 1 : (8192 / F > 64 ? 64 : 8192 / F); }
 
 template <int KIN>
 __global__ void __launch_bounds__(kColThreads)
