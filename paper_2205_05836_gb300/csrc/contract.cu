@@ -193,6 +193,38 @@ __global__ void prep_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows
   }
 }
 
+// max |x| over n contiguous floats into *gmax (float bits; the values are
+// non-negative, so the integer max orders them): float4 loads, four in
+// flight per thread, one atomic per block.  Stands in for the max pass of an
+// operand-wide scale when the operand covers its whole source tensor (every
+// row, every column: the same set of values).
+__global__ void __launch_bounds__(256) absmax_kernel(const float* __restrict__ x, int64_t n,
+                                                     unsigned int* __restrict__ gmax) {
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  const int64_t n4 = n >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  float mx = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += 4 * stride) {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = i + u * stride < n4 ? __ldg(x4 + i + u * stride) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
+  }
+  for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    mx = fmaxf(mx, fabsf(__ldg(x + i)));
+  for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  __shared__ float bmax[8];
+  if ((threadIdx.x & 31) == 0) bmax[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, bmax[w]);
+    atomicMax(gmax, __float_as_uint(m));
+  }
+}
+
 // Short rows (Kp = 8 G <= 128 half columns, K <= Kp values, K % 4 == 0, the
 // shared digits the lowest of the source columns): G lanes per row, each
 // lane loading its 8 columns (two float4, zeros past K) and writing them as
@@ -561,6 +593,18 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
   }
   const int64_t K = v.kdim();
   int blocks = (int)std::min<int64_t>((rows * 32 + 255) / 256, (int64_t)sm_count() * 16);
+  // the max pass of an operand-wide scale: when the operand is its whole
+  // source tensor (all rows, no column list) a plain reduction over the
+  // tensor's floats gives the same max
+  const bool whole = !cols && row0 == 0 && rows == v.rows() && v.n_open + v.n_shared == v.k &&
+                     ((uintptr_t)v.src & 15) == 0;
+  auto absmax_pass = [&]() -> int {
+    const int64_t n = ((int64_t)1 << v.o) << (2 * v.k);
+    const int ab = (int)std::max<int64_t>(1, std::min<int64_t>((n / 4 + 1023) / 1024, (int64_t)sm_count() * 8));
+    absmax_kernel<<<ab, 256, 0, st>>>(v.src, n, gmax);
+    CUTQC_LAUNCH_CHECK("absmax_kernel");
+    return CUTQC_OK;
+  };
   if (blocks < 1) blocks = 1;
   if (batch < 1 || batch > 65535) return set_error(CUTQC_EUNSUPPORTED, "batch %d out of range", batch);
   const bool low_open = v.open_dmask == (((uint64_t)1 << (2 * v.n_open)) - 1);
@@ -584,9 +628,14 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
     if (gmax) {
       if (batch != 1) return set_error(CUTQC_EINVAL, "internal: operand-wide scale needs batch 1");
       CUTQC_CUDA_TRY(cudaMemsetAsync(gmax, 0, sizeof(unsigned int), st));
-      prep_tr_kernel<<<dim3(tblocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride,
-                                                       rows, 2, gmax);
-      CUTQC_LAUNCH_CHECK("prep_tr_kernel (max)");
+      if (whole) {
+        int rc = absmax_pass();
+        if (rc) return rc;
+      } else {
+        prep_tr_kernel<<<dim3(tblocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride,
+                                                         rows, 2, gmax);
+        CUTQC_LAUNCH_CHECK("prep_tr_kernel (max)");
+      }
       prep_tr_kernel<<<dim3(tblocks, 1), 256, smem, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale,
                                                           src_bstride, rows, 1, gmax);
     } else {
@@ -612,8 +661,13 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
     if (gmax) {
       if (batch != 1) return set_error(CUTQC_EINVAL, "internal: operand-wide scale needs batch 1");
       CUTQC_CUDA_TRY(cudaMemsetAsync(gmax, 0, sizeof(unsigned int), st));
-      launch(2);
-      CUTQC_LAUNCH_CHECK("prep_small_kernel (max)");
+      if (whole) {
+        int rc = absmax_pass();
+        if (rc) return rc;
+      } else {
+        launch(2);
+        CUTQC_LAUNCH_CHECK("prep_small_kernel (max)");
+      }
       launch(1);
     } else {
       launch(0);
@@ -627,9 +681,14 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
     if (batch != 1) return set_error(CUTQC_EINVAL, "internal: operand-wide scale needs batch 1");
     if (!cols) {
       CUTQC_CUDA_TRY(cudaMemsetAsync(gmax, 0, sizeof(unsigned int), st));
-      prep_kernel<<<dim3(blocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride, rows,
-                                                   2, gmax, cols, meta);
-      CUTQC_LAUNCH_CHECK("prep_kernel (max)");
+      if (whole) {
+        int rc = absmax_pass();
+        if (rc) return rc;
+      } else {
+        prep_kernel<<<dim3(blocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride,
+                                                     rows, 2, gmax, cols, meta);
+        CUTQC_LAUNCH_CHECK("prep_kernel (max)");
+      }
     }
     prep_kernel<<<dim3(blocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride, rows, 1,
                                                  gmax, cols, meta);
