@@ -385,23 +385,27 @@ def run(args):
     fd_ws = torch.empty(max(1, cq.cutqc_reconstruct_fd_workspace_size(subs, prec)), dtype=torch.uint8, device=dev)
     total = torch.zeros(1, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    att_side = torch.cuda.Stream(dev)
+    att_side = [torch.cuda.Stream(dev) for _ in range(2)]
 
     def attribute_all(outs=att):
         # the subcircuits' attributions are independent: the two middle ones
-        # (the large variant tensors) go to a second stream, joined before FD
+        # (the large variant tensors) go to two side streams of their own,
+        # the end ones stay on the caller's stream; all joined before FD
         cur = torch.cuda.current_stream(dev)
         fork = torch.cuda.Event()
         fork.record(cur)
-        att_side.wait_event(fork)
-        with torch.cuda.stream(att_side):
-            for i in (1, 3):
+        joins = []
+        for i, side in zip((1, 2), att_side):
+            side.wait_event(fork)
+            with torch.cuda.stream(side):
                 cq.cutqc_attribute(subs[i], var[i], out=outs[i], ws=att_ws[i])
-        for i in (0, 2):
+            ev = torch.cuda.Event()
+            ev.record(side)
+            joins.append(ev)
+        for i in (0, 3):
             cq.cutqc_attribute(subs[i], var[i], out=outs[i], ws=att_ws[i])
-        join = torch.cuda.Event()
-        join.record(att_side)
-        cur.wait_event(join)
+        for ev in joins:
+            cur.wait_event(ev)
 
     def reconstruct(dst=out, tot=total):
         tot.zero_()
@@ -678,7 +682,7 @@ def fd_two_sub_extras(dev, cq, steps=10, warmup=3):
         cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_KRON, cq.PREC_FP16X3_TC, out=out, sum_out=total, ws=fws)
     from paper_2205_05836_gb300.tune import tune_fd
     step()
-    best, _ = tune_fd(subs, att, cq.PREC_FP16X3_TC, out=out, ws=fws)
+    best, trials = tune_fd(subs, att, cq.PREC_FP16X3_TC, out=out, ws=fws)
     g = _graph(step, stream, warmup)
     g.replay()
     torch.cuda.synchronize()
@@ -698,6 +702,7 @@ def fd_two_sub_extras(dev, cq, steps=10, warmup=3):
     Kg = 4 ** w.K
     gbytes = 4.0 * n_out + 4.0 * Kg * (M + N)
     return {"workload": TWO_SUB_WORKLOAD, "n_qubits": w.n, "cuts": w.K, "gemm": [M, N, Kg], "tiles_per_item": best,
+            "tiles_per_item_trials_ms": {str(t): round(m, 4) for m, t, same in trials if same},
             "ms_per_step": ms, "probs_per_s": n_out / (ms * 1e-3), "sum_p_error": abs(total.item() - 1.0),
             "roofline": {"bound": "hbm", "kernel": "tc_pair_gemm_kernel, one launch", "kernel_ms": gemm_ms,
                          "algorithmic_bytes": gbytes, "achieved": gbytes / (gemm_ms * 1e-3) / 1e9,
