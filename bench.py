@@ -316,17 +316,23 @@ def run_reference(args):
     budget = max(0.5, args.ref_budget / max(1, args.steps))
     for _ in range(args.warmup):
         cpu_baseline(oracle, budget_s=min(0.5, budget))
-    vals = [cpu_baseline(oracle, budget_s=budget) for _ in range(args.steps)]
+    vals, step_s = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        vals.append(cpu_baseline(oracle, budget_s=budget))
+        step_s.append(time.perf_counter() - t0)
     v = statistics.median(x["value"] for x in vals)
     cb = dict(vals[-1])
     cb["value"] = v
     line = {"metric": METRIC, "value": v, "unit": "probs/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 2 ** w.n / v * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": statistics.median(step_s) * 1e3, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference", "config": {"workload": WORKLOAD, "n_qubits": w.n, "cuts": w.K},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "probs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "note": "ms_per_step: the whole 2^32-output job at the sampled rate"}
+            "full_job_s_at_this_rate": 2 ** w.n / v,
+            "note": "each timed step is a bounded sample of the job (ms_per_step is its wall time); value is the "
+                    "whole-job rate of the samples, the attribution and pair sums prorated"}
     print(json.dumps(line), flush=True)
 
 
