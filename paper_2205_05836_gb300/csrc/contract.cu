@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) absmax_kernel(const float* __restrict__ x
   }
 }
 
-// Short rows (Kp = 8 G <= 128 half columns, K <= Kp values, K % 4 == 0, the
+// Short rows (Kp = 8 G half columns, K <= Kp values, K % 4 == 0, the
 // shared digits the lowest of the source columns): G lanes per row, each
 // lane loading its 8 columns (two float4, zeros past K) and writing them as
 // one 16-byte vector of hi and one of lo; a warp takes 32 / G rows at once
@@ -646,17 +646,14 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
     return CUTQC_OK;
   }
   const bool low_shared = v.shared_dmask == (((uint64_t)1 << (2 * v.n_shared)) - 1);
-  if (!cols && !out32 && hi && low_shared && K % 4 == 0 && K <= Kp && (Kp == 64 || Kp == 128) &&
+  if (!cols && !out32 && hi && low_shared && K % 4 == 0 && K <= Kp && Kp == 64 &&
       ((uintptr_t)v.src & 15) == 0 && src_bstride % 4 == 0) {
-    const int G = (int)(Kp / 8), rpb = 256 / G;
+    // (Kp is 64 here: K is a power of four, padded to a multiple of 64)
+    constexpr int G = 8, rpb = 256 / G;
     const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + rpb - 1) / rpb, (int64_t)sm_count() * 8));
     auto launch = [&](int mode) {
-      if (G == 8)
-        prep_small_kernel<8><<<dim3(sblocks, mode == 0 ? batch : 1), 256, 0, st>>>(v, rm, row0, rows, K, hi, lo, scale,
-                                                                                  src_bstride, rows, mode, gmax);
-      else
-        prep_small_kernel<16><<<dim3(sblocks, mode == 0 ? batch : 1), 256, 0, st>>>(v, rm, row0, rows, K, hi, lo,
-                                                                                   scale, src_bstride, rows, mode, gmax);
+      prep_small_kernel<G><<<dim3(sblocks, mode == 0 ? batch : 1), 256, 0, st>>>(v, rm, row0, rows, K, hi, lo, scale,
+                                                                                src_bstride, rows, mode, gmax);
     };
     if (gmax) {
       if (batch != 1) return set_error(CUTQC_EINVAL, "internal: operand-wide scale needs batch 1");
