@@ -351,45 +351,27 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) dd_persistent_kernel(con
   __shared__ TileSmem tsm;
   const bool tracer = blockIdx.x == 0 && threadIdx.x == 0;
   if (tracer) pg.trace[0] = clock64();
-  int o0 = 0, o1 = 0, nt = 0, cur = -1;
-  auto task0 = [&](int i) { return i - o0 < kPhaseOpsCached ? s_task0[i - o0] : __ldg(&pg.ops[i].task0); };
-  auto load_op = [&](int oi) {
-    const int4* src = reinterpret_cast<const int4*>(pg.ops + oi);
-    int4* dst = reinterpret_cast<int4*>(&sop);
-    for (int i = threadIdx.x; i < (int)(sizeof(Op) / sizeof(int4)); i += blockDim.x) dst[i] = __ldg(src + i);
-    __syncthreads();
-    cur = oi;
-  };
-  // Phase p's op boundaries, task offsets and this CTA's first op into
-  // shared memory.  The program is read-only for the launch, so the next
-  // phase is staged before the grid barrier, off the phase-to-phase path.
-  auto stage_phase = [&](int p) {
-    o0 = __ldg(pg.phase_op + p);
-    o1 = __ldg(pg.phase_op + p + 1);
-    nt = __ldg(pg.phase_tasks + p);
+  for (int p = 0; p < pg.n_phases; ++p) {
+    const int o0 = __ldg(pg.phase_op + p), o1 = __ldg(pg.phase_op + p + 1);
+    const int nt = __ldg(pg.phase_tasks + p);
     for (int i = threadIdx.x; i < o1 - o0 && i < kPhaseOpsCached; i += blockDim.x)
       s_task0[i] = __ldg(&pg.ops[o0 + i].task0);
     __syncthreads();
-    cur = -1;
-    if ((int)blockIdx.x < nt) {    // the same for every thread of the CTA
-      int oi = o0;
-      while (oi + 1 < o1 && (int)blockIdx.x >= task0(oi + 1)) ++oi;
-      load_op(oi);
-    }
-  };
-  stage_phase(0);
-  for (int p = 0; p < pg.n_phases; ++p) {
-    int oi = o0;
+    auto task0 = [&](int i) { return i - o0 < kPhaseOpsCached ? s_task0[i - o0] : __ldg(&pg.ops[i].task0); };
+    int oi = o0, cur = -1;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
       while (oi + 1 < o1 && t >= task0(oi + 1)) ++oi;   // tasks ascend with the op index
-      if (oi != cur) load_op(oi);
+      if (oi != cur) {
+        const int4* src = reinterpret_cast<const int4*>(pg.ops + oi);
+        int4* dst = reinterpret_cast<int4*>(&sop);
+        for (int i = threadIdx.x; i < (int)(sizeof(Op) / sizeof(int4)); i += blockDim.x) dst[i] = __ldg(src + i);
+        __syncthreads();
+        cur = oi;
+      }
       run_task(sop, t - sop.task0, tsm);
       __syncthreads();
     }
-    if (p + 1 < pg.n_phases) {
-      stage_phase(p + 1);
-      if (!grid_barrier(pg.bar, pg.status)) return;
-    }
+    if (p + 1 < pg.n_phases && !grid_barrier(pg.bar, pg.status)) return;
     if (tracer) pg.trace[p + 1] = clock64();
   }
 }
