@@ -579,9 +579,14 @@ int launch_prune_select(const OperandView& va, const int* a_bits, int a_nbits, i
 
 constexpr int64_t PREP_TR_MAX_K = 1024;   // staged tile [K][33] floats: 132 KiB at most
 
+bool prep_covers_source(const OperandView& v, int64_t row0, int64_t rows) {
+  return row0 == 0 && rows == v.rows() && v.n_open + v.n_shared == v.k && ((uintptr_t)v.src & 15) == 0;
+}
+
 int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int64_t row0, int64_t rows,
                      int64_t Kp, float* out32, __half* hi, __half* lo, float* scale, cudaStream_t st,
-                     int batch, int64_t src_bstride, unsigned int* gmax, const int* cols, const int* meta) {
+                     int batch, int64_t src_bstride, unsigned int* gmax, const int* cols, const int* meta,
+                     bool gmax_ready) {
   if (rows <= 0) return CUTQC_OK;
   RowMap rm{};
   rm.n = n_bits;
@@ -596,14 +601,22 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
   // the max pass of an operand-wide scale: when the operand is its whole
   // source tensor (all rows, no column list) a plain reduction over the
   // tensor's floats gives the same max
-  const bool whole = !cols && row0 == 0 && rows == v.rows() && v.n_open + v.n_shared == v.k &&
-                     ((uintptr_t)v.src & 15) == 0;
-  auto absmax_pass = [&]() -> int {
-    const int64_t n = ((int64_t)1 << v.o) << (2 * v.k);
-    const int ab = (int)std::max<int64_t>(1, std::min<int64_t>((n / 4 + 1023) / 1024, (int64_t)sm_count() * 8));
-    absmax_kernel<<<ab, 256, 0, st>>>(v.src, n, gmax);
-    CUTQC_LAUNCH_CHECK("absmax_kernel");
-    return CUTQC_OK;
+  const bool whole = !cols && prep_covers_source(v, row0, rows);
+  if (gmax_ready && (!gmax || !whole)) return set_error(CUTQC_EINVAL, "internal: a ready max needs the whole tensor");
+  // *gmax = max |x| of the operand: nothing when the producer already wrote
+  // it, else zeroed and reduced over the whole source tensor when the operand
+  // covers it, else by the view's own max pass (view_max)
+  auto max_pass = [&](auto&& view_max) -> int {
+    if (gmax_ready) return CUTQC_OK;
+    CUTQC_CUDA_TRY(cudaMemsetAsync(gmax, 0, sizeof(unsigned int), st));
+    if (whole) {
+      const int64_t n = ((int64_t)1 << v.o) << (2 * v.k);
+      const int ab = (int)std::max<int64_t>(1, std::min<int64_t>((n / 4 + 1023) / 1024, (int64_t)sm_count() * 8));
+      absmax_kernel<<<ab, 256, 0, st>>>(v.src, n, gmax);
+      CUTQC_LAUNCH_CHECK("absmax_kernel");
+      return CUTQC_OK;
+    }
+    return view_max();
   };
   if (blocks < 1) blocks = 1;
   if (batch < 1 || batch > 65535) return set_error(CUTQC_EUNSUPPORTED, "batch %d out of range", batch);
@@ -627,15 +640,13 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
     const int tblocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 31) / 32, (int64_t)sm_count() * per_sm));
     if (gmax) {
       if (batch != 1) return set_error(CUTQC_EINVAL, "internal: operand-wide scale needs batch 1");
-      CUTQC_CUDA_TRY(cudaMemsetAsync(gmax, 0, sizeof(unsigned int), st));
-      if (whole) {
-        int rc = absmax_pass();
-        if (rc) return rc;
-      } else {
+      int rc = max_pass([&]() -> int {
         prep_tr_kernel<<<dim3(tblocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride,
                                                          rows, 2, gmax);
         CUTQC_LAUNCH_CHECK("prep_tr_kernel (max)");
-      }
+        return CUTQC_OK;
+      });
+      if (rc) return rc;
       prep_tr_kernel<<<dim3(tblocks, 1), 256, smem, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale,
                                                           src_bstride, rows, 1, gmax);
     } else {
@@ -657,14 +668,12 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
     };
     if (gmax) {
       if (batch != 1) return set_error(CUTQC_EINVAL, "internal: operand-wide scale needs batch 1");
-      CUTQC_CUDA_TRY(cudaMemsetAsync(gmax, 0, sizeof(unsigned int), st));
-      if (whole) {
-        int rc = absmax_pass();
-        if (rc) return rc;
-      } else {
+      int rc = max_pass([&]() -> int {
         launch(2);
         CUTQC_LAUNCH_CHECK("prep_small_kernel (max)");
-      }
+        return CUTQC_OK;
+      });
+      if (rc) return rc;
       launch(1);
     } else {
       launch(0);
@@ -677,15 +686,13 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
     // column list the max over the kept columns is already in *gmax)
     if (batch != 1) return set_error(CUTQC_EINVAL, "internal: operand-wide scale needs batch 1");
     if (!cols) {
-      CUTQC_CUDA_TRY(cudaMemsetAsync(gmax, 0, sizeof(unsigned int), st));
-      if (whole) {
-        int rc = absmax_pass();
-        if (rc) return rc;
-      } else {
+      int rc = max_pass([&]() -> int {
         prep_kernel<<<dim3(blocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride,
                                                      rows, 2, gmax, cols, meta);
         CUTQC_LAUNCH_CHECK("prep_kernel (max)");
-      }
+        return CUTQC_OK;
+      });
+      if (rc) return rc;
     }
     prep_kernel<<<dim3(blocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride, rows, 1,
                                                  gmax, cols, meta);

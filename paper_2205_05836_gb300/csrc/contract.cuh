@@ -37,10 +37,17 @@ struct RowMap {
 // word of scratch.
 // cols/meta (device, nullable): gather only operand columns cols[0..meta[0])
 // (cut-term pruning), zero-fill to meta[2], leave the rest of each row.
+// gmax_ready: *gmax already holds the operand's max |x| (written by the
+// GEMM that produced the source tensor), so the max pass is skipped; only
+// for an operand that covers its source tensor (prep_covers_source).
 int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int64_t row0, int64_t rows,
                      int64_t Kp, float* out32, __half* hi, __half* lo, float* scale, cudaStream_t st,
                      int batch = 1, int64_t src_bstride = 0, unsigned int* gmax = nullptr,
-                     const int* cols = nullptr, const int* meta = nullptr);
+                     const int* cols = nullptr, const int* meta = nullptr, bool gmax_ready = false);
+// True when operand rows [row0, row0 + rows) of the view are every element of
+// its source tensor, each once (all rows; the open and shared digits are all
+// of the source's digits; a 16-byte aligned source).
+bool prep_covers_source(const OperandView& v, int64_t row0, int64_t rows);
 
 // Cut-term pruning of one contraction (row operand rows [a_row0, +a_rows),
 // column operand all b_rows rows): per term k the bound w_k = alpha *
@@ -147,13 +154,15 @@ bool tc_pair_supported(int64_t Kp);
 // read by the kernel (at most Kp / 64); the operands' row stride stays Kp.
 // cmax (nullable, device, paired kernel only): for each 32-row x 64-column
 // block of the M x N result (stripe r = m / 32, block c = n / 64) its largest
-// value at cmax[r * ceil(N / 64) + c].
+// value at cmax[r * ceil(N / 64) + c].  amax (nullable, device, paired kernel
+// only, not with cmax): atomicMax of the float bits of every |output| (the
+// caller zeroes it first).
 int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
                         uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st,
-                        const int* num_kb_dev = nullptr, float* cmax = nullptr);
+                        const int* num_kb_dev = nullptr, float* cmax = nullptr, unsigned int* amax = nullptr);
 int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
                    uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st,
-                   const int* num_kb_dev = nullptr, float* cmax = nullptr);
+                   const int* num_kb_dev = nullptr, float* cmax = nullptr, unsigned int* amax = nullptr);
 
 // Block maxima of the final step's output (DD's top-T selection).  Set on
 // the calling thread around run_plan: when the final step runs on the paired

@@ -358,7 +358,26 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
     return (const float*)(ws + s.off_result);
   };
   int rc;
-  auto run_stage = [&](const PlanStage& stg0, cudaStream_t st) -> int {
+  const size_t ns_all = plan.stages.size();
+  // Column operands with an operand-wide scale need the max |x| of their
+  // source.  When that source is an earlier step's result, covered whole by
+  // the operand, the paired GEMM that writes it also reduces its max into the
+  // operand's max word (the consumer's scale slot 1), and the consumer's prep
+  // skips its max pass.  max_into[s] = the consuming step, or -1.
+  std::vector<int> max_into(ns_all, -1);
+  if (precision != CUTQC_PREC_FP32_SIMT) {
+    for (size_t c = 0; c < ns_all; ++c) {
+      const PlanStage& cs = plan.stages[c];
+      const int dep = plan.stage_of[cs.b];
+      if (dep < 0) continue;
+      const bool pruned = precision == CUTQC_PREC_FP16X3_TC_PRUNE && cs.final_stage && cs.K <= kPruneMaxK;
+      OperandView vb = cs.opb.view;
+      vb.src = (const float*)(ws + plan.stages[dep].off_result);
+      if (!pruned && tc_pair_supported(plan.stages[dep].Kp) && prep_covers_source(vb, 0, cs.N))
+        max_into[dep] = (int)c;
+    }
+  }
+  auto run_stage = [&](const PlanStage& stg0, cudaStream_t st, size_t si) -> int {
     PlanStage stg = stg0;
     int64_t sa_b = 0, sb_b = 0;
     stg.opa.view.src = src_of(stg.a, &sa_b);
@@ -402,8 +421,10 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
         rc = launch_prep_rows(va, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, stg.Kp, nullptr, ah,
                               al, as, st, 1, 0, nullptr, cols, meta);
         if (rc) return rc;
+        const int bdep = plan.stage_of[stg.b];
+        const bool max_ready = bdep >= 0 && max_into[bdep] == (int)si;
         rc = launch_prep_rows(vb, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp, nullptr,
-                              bh, bl, bs, st, 1, 0, reinterpret_cast<unsigned int*>(bs + 1), cols, meta);
+                              bh, bl, bs, st, 1, 0, reinterpret_cast<unsigned int*>(bs + 1), cols, meta, max_ready);
         if (rc) return rc;
         TcOperand ta{ah, al, as, M}, tb{bh, bl, bs, stg.N};
         const bool timed = stg.final_stage && g_gemm_start && b == 0;
@@ -420,8 +441,15 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
             g_bmax->mask_n = stg.mask_n;
           }
         }
+        unsigned int* amax = nullptr;
+        if (max_into[si] >= 0) {
+          // the consuming step's column-operand max word for this item
+          const PlanStage& cs = plan.stages[max_into[si]];
+          amax = reinterpret_cast<unsigned int*>((float*)(ws + cs.opb.off_scale) + (size_t)b * cs.N + 1);
+          CUTQC_CUDA_TRY(cudaMemsetAsync(amax, 0, sizeof(unsigned int), st));
+        }
         rc = launch_tc_gemm(ta, tb, stg.Kp, alpha, stg.mask_m, stg.mask_n, dst + b * dst_b,
-                            sum_ptr ? sum_ptr + b : nullptr, streaming, st, prune ? meta + 1 : nullptr, cmax);
+                            sum_ptr ? sum_ptr + b : nullptr, streaming, st, prune ? meta + 1 : nullptr, cmax, amax);
         if (rc) return rc;
         if (stg.final_stage && g_gemm_start && b == batch - 1) {
           CUTQC_CUDA_TRY(cudaEventRecord(g_gemm_stop, st));
@@ -512,7 +540,7 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
         if (dep >= 0 && (on_side[dep] || side[si])) CUTQC_CUDA_TRY(cudaStreamWaitEvent(st, ss->done[dep], 0));
       }
     }
-    if ((rc = run_stage(stg, st))) return rc;
+    if ((rc = run_stage(stg, st, si))) return rc;
     if (par) CUTQC_CUDA_TRY(cudaEventRecord(ss->done[si], st));
   }
   nside = std::min(nside, kSideStreams);

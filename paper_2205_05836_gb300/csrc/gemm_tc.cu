@@ -420,10 +420,11 @@ int make_map(CUtensorMap* map, const __half* base, int64_t rows, int64_t Kp, int
 
 int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
                    uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st, const int* num_kb_dev,
-                   float* cmax) {
+                   float* cmax, unsigned int* amax) {
   if (a.rows <= 0 || b.rows <= 0) return CUTQC_OK;
   if (tc_pair_supported(Kp))
-    return launch_tc_pair_gemm(a, b, Kp, alpha, mask_m, mask_n, out, sum, streaming, st, num_kb_dev, cmax);
+    return launch_tc_pair_gemm(a, b, Kp, alpha, mask_m, mask_n, out, sum, streaming, st, num_kb_dev, cmax, amax);
+  if (amax) return set_error(CUTQC_EINVAL, "internal: output max needs the paired kernel");
   if (Kp % BK != 0 || Kp <= 0) return set_error(CUTQC_EINVAL, "tensor-core K must be a multiple of %d", BK);
   if (Kp / BK > (1 << 20)) return set_error(CUTQC_EUNSUPPORTED, "K too large");
   TcMaps maps;

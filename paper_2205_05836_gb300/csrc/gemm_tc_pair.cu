@@ -80,6 +80,7 @@ static_assert(ACC_COL0 + NBUF * BN <= TMEM_COLS, "tensor memory budget");
 constexpr int NUM_THREADS = 352;
 constexpr int EPI_WARPS = 8;
 constexpr int EPI_COLS = 64;                             // columns per epilogue warp
+constexpr int kStatBlockMax = 1, kStatAbsMax = 2;        // epilogue statistics (tc_pair_gemm_kernel)
 constexpr int BLK_FLOATS = 32 * 32;                      // one 32 x 32 staging block
 constexpr int EPI_STG_BYTES = EPI_WARPS * (EPI_COLS / 32) * BLK_FLOATS * 4;   // 64 KiB
 // Direct stores need no staging block: its 64 KiB go to five more B stages,
@@ -116,6 +117,7 @@ struct PairArgs {
   float* out;
   double* sum;
   float* cmax;          // nullable: largest value of each 32-row x 64-column block of the output
+  unsigned int* amax;   // nullable: largest |output| of the launch (float bits, atomicMax)
   int64_t cmax_cols;    // blocks per 32-row stripe: ceil(N / 64)
   int streaming;
   int* status;
@@ -233,7 +235,11 @@ __device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
       : "memory");
 }
 
-template <bool kRowMajor, bool kMax>
+// kStat: 0 nothing more; kStatBlockMax: each epilogue warp's 32 x 64 block
+// maximum per tile into args.cmax; kStatAbsMax: the largest |output| of the
+// launch into *args.amax (float bits; the values are non-negative, so the
+// integer max orders them).
+template <bool kRowMajor, int kStat>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
 tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) {
   constexpr int STAGES = Cfg<kRowMajor>::STAGES;
@@ -401,6 +407,7 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
     uint32_t buf_phase = 0;
     uint32_t aphase = 0;
     double local = 0.0;
+    [[maybe_unused]] float amx = 0.f;    // kStatAbsMax: this thread's largest |output|
     const float sbg = __ldg(args.sb);
     float* stg0 = stg_all + warp * (EPI_COLS / 32) * BLK_FLOATS;
     const uint32_t lead_afull = map_to_rank(smem_u32(&tail->afull), 0);
@@ -529,12 +536,13 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
                 if (mm < args.M && nb0 + 8 * q < args.N) {
                   __stcs(reinterpret_cast<float2*>(orow + 8 * q), make_float2(a, b));
                   part += a + b;
-                  if constexpr (kMax) mx = fmaxf(mx, fmaxf(a, b));
+                  if constexpr (kStat == kStatBlockMax) mx = fmaxf(mx, fmaxf(a, b));
+                  if constexpr (kStat == kStatAbsMax) amx = fmaxf(amx, fmaxf(fabsf(a), fabsf(b)));
                 }
               }
             }
           if (args.sum) local += (double)part;
-          if constexpr (kMax) put_cmax(mx, mrow0, nbase);
+          if constexpr (kStat == kStatBlockMax) put_cmax(mx, mrow0, nbase);
         } else {
           const uint64_t roff =
               mvalid ? (args.m_shift >= 0 ? ((uint64_t)m << args.m_shift) : pdep64((uint64_t)m, args.mask_m)) : 0;
@@ -556,11 +564,12 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
                 float* ptr = obase + (cbase | args.coff_lo[c]);
                 if (args.streaming) __stcs(ptr, val); else *ptr = val;
                 part += val;
-                if constexpr (kMax) mx = fmaxf(mx, val);
+                if constexpr (kStat == kStatBlockMax) mx = fmaxf(mx, val);
+                if constexpr (kStat == kStatAbsMax) amx = fmaxf(amx, fabsf(val));
               }
             }
             if (args.sum) local += (double)part;
-            if constexpr (kMax) put_cmax(mx, mrow0, nbase);
+            if constexpr (kStat == kStatBlockMax) put_cmax(mx, mrow0, nbase);
             continue;
           }
           // general bit deposit through the staging block (XOR-swizzled by
@@ -588,12 +597,13 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
                 float* ptr = args.out + (roff_r | coff);
                 if (args.streaming) __stcs(ptr, val); else *ptr = val;
                 part += val;
-                if constexpr (kMax) mx = fmaxf(mx, val);
+                if constexpr (kStat == kStatBlockMax) mx = fmaxf(mx, val);
+                if constexpr (kStat == kStatAbsMax) amx = fmaxf(amx, fabsf(val));
               }
             }
             if (args.sum) local += (double)part;
           }
-          if constexpr (kMax) put_cmax(mx, mrow0, nbase);
+          if constexpr (kStat == kStatBlockMax) put_cmax(mx, mrow0, nbase);
         }
       }
     }
@@ -601,6 +611,10 @@ tc_pair_gemm_kernel(const __grid_constant__ PairMaps maps, const PairArgs args) 
     if (args.sum) {
       for (int off = 16; off; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
       if (lane == 0) atomicAdd(args.sum, local);
+    }
+    if constexpr (kStat == kStatAbsMax) {
+      for (int off = 16; off; off >>= 1) amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, off));
+      if (lane == 0) atomicMax(args.amax, __float_as_uint(amx));
     }
   }
 
@@ -659,7 +673,7 @@ int set_pair_tiles_per_item(int t) {
 
 int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alpha, uint64_t mask_m,
                         uint64_t mask_n, float* out, double* sum, int streaming, cudaStream_t st,
-                        const int* num_kb_dev, float* cmax) {
+                        const int* num_kb_dev, float* cmax, unsigned int* amax) {
   if (a.rows <= 0 || b.rows <= 0) return CUTQC_OK;
   if (!tc_pair_supported(Kp)) return set_error(CUTQC_EINVAL, "paired tensor-core K must be 64..256, a multiple of 64");
   if (a.rows >= ((int64_t)1 << 30) || b.rows >= ((int64_t)1 << 30)) return set_error(CUTQC_EUNSUPPORTED, "too many rows");
@@ -695,7 +709,9 @@ int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, floa
   for (int c = 0; c < 64; ++c) args.coff_lo[c] = pdep64((uint64_t)c, mask_n);
   args.out = out;
   args.sum = sum;
+  if (cmax && amax) return set_error(CUTQC_EINVAL, "internal: one epilogue statistic per launch");
   args.cmax = cmax;
+  args.amax = amax;
   args.cmax_cols = (b.rows + 63) / 64;
   args.streaming = streaming;
   args.status = device_status_ptr();
@@ -712,25 +728,28 @@ int launch_tc_pair_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, floa
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(mu);
     if (!done.count(dev)) {
-      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_pair_gemm_kernel<true, false>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<true>()));
-      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_pair_gemm_kernel<false, false>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<false>()));
-      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_pair_gemm_kernel<true, true>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<true>()));
-      CUTQC_CUDA_TRY(cudaFuncSetAttribute(tc_pair_gemm_kernel<false, true>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<false>()));
+      const void* fns[6] = {(const void*)tc_pair_gemm_kernel<true, 0>, (const void*)tc_pair_gemm_kernel<true, 1>,
+                            (const void*)tc_pair_gemm_kernel<true, 2>, (const void*)tc_pair_gemm_kernel<false, 0>,
+                            (const void*)tc_pair_gemm_kernel<false, 1>, (const void*)tc_pair_gemm_kernel<false, 2>};
+      for (int i = 0; i < 6; ++i)
+        CUTQC_CUDA_TRY(cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(i < 3 ? smem_bytes<true>() : smem_bytes<false>())));
       done.insert(dev);
     }
   }
   const int64_t pairs = std::min<int64_t>(args.num_items, pairs_avail);
   const int grid = (int)(2 * pairs);
+  const int stat = cmax ? kStatBlockMax : amax ? kStatAbsMax : 0;
   if (row_major) {
-    if (cmax) tc_pair_gemm_kernel<true, true><<<grid, NUM_THREADS, smem_bytes<true>(), st>>>(maps, args);
-    else tc_pair_gemm_kernel<true, false><<<grid, NUM_THREADS, smem_bytes<true>(), st>>>(maps, args);
+    const size_t sm = smem_bytes<true>();
+    if (stat == kStatBlockMax) tc_pair_gemm_kernel<true, kStatBlockMax><<<grid, NUM_THREADS, sm, st>>>(maps, args);
+    else if (stat == kStatAbsMax) tc_pair_gemm_kernel<true, kStatAbsMax><<<grid, NUM_THREADS, sm, st>>>(maps, args);
+    else tc_pair_gemm_kernel<true, 0><<<grid, NUM_THREADS, sm, st>>>(maps, args);
   } else {
-    if (cmax) tc_pair_gemm_kernel<false, true><<<grid, NUM_THREADS, smem_bytes<false>(), st>>>(maps, args);
-    else tc_pair_gemm_kernel<false, false><<<grid, NUM_THREADS, smem_bytes<false>(), st>>>(maps, args);
+    const size_t sm = smem_bytes<false>();
+    if (stat == kStatBlockMax) tc_pair_gemm_kernel<false, kStatBlockMax><<<grid, NUM_THREADS, sm, st>>>(maps, args);
+    else if (stat == kStatAbsMax) tc_pair_gemm_kernel<false, kStatAbsMax><<<grid, NUM_THREADS, sm, st>>>(maps, args);
+    else tc_pair_gemm_kernel<false, 0><<<grid, NUM_THREADS, sm, st>>>(maps, args);
   }
   CUTQC_LAUNCH_CHECK("tc_pair_gemm_kernel");
   return CUTQC_OK;
