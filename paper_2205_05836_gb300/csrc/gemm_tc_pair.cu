@@ -648,14 +648,18 @@ int make_map(CUtensorMap* map, const __half* base, int64_t rows, int64_t Kp, int
 std::atomic<int> g_tiles_per_item{0};
 
 // Tiles per work item: the fewest tile slots on the busiest pair, counting
-// an A load as about one tile of time.
+// an A load (the pipe drains, the new A block lands) as about two tiles of
+// time.  (One tile undercounted it where tiles are short: the dense DD
+// recursion's one-k-block GEMM, 1024 row blocks x 32 column tiles, ran 3%
+// faster with whole-row-block items than with the 16-tile items that
+// weight picked; the FD picks are the same under both.)
 int64_t pick_tiles_per_item(int64_t num_mp, int64_t num_nt, int64_t pairs) {
   int64_t best_t = 1;
   double best = 1e300;
   for (int64_t t = 4; t <= 64; ++t) {
     const int64_t items = num_mp * ((num_nt + t - 1) / t);
     const int64_t per_pair = (items + pairs - 1) / pairs;
-    const double cost = (double)per_pair * ((double)std::min(t, num_nt) + 1.0);
+    const double cost = (double)per_pair * ((double)std::min(t, num_nt) + 2.0);
     if (cost < best) { best = cost; best_t = t; }
   }
   return std::min(best_t, num_nt);
