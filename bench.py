@@ -208,6 +208,8 @@ def dist_setup():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)    # the rank's GPU current before NCCL binds to it
         backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend)
     return ws, rank, local
