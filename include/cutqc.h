@@ -295,7 +295,11 @@ int cutqc_dd_run(int n_sub, const cutqc_subcircuit* s, const float* const* attri
  *   precision     CUTQC_PREC_FP32_SIMT (default) or CUTQC_PREC_FP16X3_TC,
  *                 the FD tensor-core path; levels whose jobs have fewer than
  *                 4 bins, or whose bins do not start 16-byte aligned, run
- *                 in FP32.  Bin totals are float64 either way.
+ *                 in FP32, and so does every contraction step with fewer
+ *                 than 2^20 outputs over the level's jobs (FP32 on CUDA
+ *                 cores is the faster and no less accurate choice there;
+ *                 tc_min_outputs moves that floor).
+ *                 Bin totals are float64 either way.
  * Jobs of more than 2^16 bins select their top T in two passes (chunks of
  * the bins, then the chunks' candidates), with the same order.  On the
  * tensor-core path, jobs of at least 2^22 bins whose last GEMM runs on SM
@@ -308,6 +312,9 @@ typedef struct cutqc_dd_options {
   int32_t merge_ctas;
   int32_t topk_threads;
   int32_t precision;
+  int32_t tc_min_outputs;   /* 0: steps below 2^20 outputs run in FP32; b > 0: the
+                               floor is 2^(b-1) outputs (1: every step on the
+                               split path) */
 } cutqc_dd_options;
 
 /* Algorithm 1, level by level (strategy 1 above; with T = 1 also the depth

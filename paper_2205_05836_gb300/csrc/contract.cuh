@@ -105,6 +105,7 @@ struct PlanOperand {
 struct PlanStage {
   int a = -1, b = -1, result = -1;
   bool final_stage = false;
+  bool tc = false;          // tensor-core split path (else FP32 on CUDA cores)
   PlanOperand opa, opb;
   int64_t M = 0, N = 0, K = 0, Kp = 0;
   uint64_t mask_m = 0, mask_n = 0;
@@ -128,8 +129,12 @@ struct ContractionPlan {
 int plan_contraction(const std::vector<TensorDesc>& inputs, int precision, ContractionPlan* plan);
 // ws_upper_bound: size the workspace as if every operand needed its gather
 // copy, so that the size holds for any output-bit order of the inputs.
+// min_tc_outputs: under a tensor-core precision, steps with fewer outputs
+// over all batch items (M * N * batch) run in FP32 on CUDA cores (at least
+// as accurate; for small steps the split's operand preps cost more than the
+// GEMM saves).
 int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precision, int batch,
-                             ContractionPlan* plan, bool ws_upper_bound = false);
+                             ContractionPlan* plan, bool ws_upper_bound = false, int64_t min_tc_outputs = 0);
 
 // Runs the plan for `batch` independent items: input i of item b at
 // inputs[i] + b * in_bstride[i]; output of item b at out + b * out_bstride;

@@ -122,6 +122,12 @@ __global__ void dd_block_gather(const float* __restrict__ bins, int64_t nb, cons
 
 
 // Large jobs: chunks of the chunked first pass of the top-T selection.
+// Under a tensor-core precision, a level's contraction steps with fewer
+// outputs (all jobs together) run in FP32 on CUDA cores: at DD's usual
+// 2^16-bin jobs the split's per-job operand preps and launches cost more
+// than its GEMMs save (three 16-active-qubit circuits: 1.5 ms against
+// 0.39 ms), and FP32 is at least as accurate.
+constexpr int64_t kDdMinTcOutputs = (int64_t)1 << 20;
 constexpr int64_t kTopkChunkMin = (int64_t)1 << 16;   // bins per chunk at least
 constexpr int64_t kTopkChunksMax = 2048;
 inline int64_t topk_chunks(int64_t nb, int64_t min_chunk = kTopkChunkMin) {
@@ -242,7 +248,8 @@ int dd_inputs(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, 
 // Workspace of one step: the contraction plan's (for the given precision;
 // for FP32 sized for any bin order) and the chunked top-T candidates.
 int dd_step_ws(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, int n_jobs, int precision,
-                      size_t* bytes) {
+                      size_t* bytes, int64_t min_tc_outputs) {
+  if (min_tc_outputs < 0) min_tc_outputs = kDdMinTcOutputs;
   if (!bytes) return set_error(CUTQC_EINVAL, "null bytes");
   std::vector<TensorDesc> in;
   int tot = 0;
@@ -255,7 +262,7 @@ int dd_step_ws(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits,
   if (rc) return rc;
   if (n_jobs < 1) return set_error(CUTQC_EINVAL, "n_jobs must be >= 1");
   ContractionPlan plan;
-  if ((rc = plan_contraction_batched(in, precision, n_jobs, &plan, true))) return rc;
+  if ((rc = plan_contraction_batched(in, precision, n_jobs, &plan, true, min_tc_outputs))) return rc;
   *bytes = align_up(plan.ws_bytes, 256) + topk_scratch((int64_t)1 << tot, n_jobs) +
            (precision != CUTQC_PREC_FP32_SIMT ? block_max_scratch((int64_t)1 << tot, n_jobs) : 0);
   return CUTQC_OK;
@@ -306,11 +313,15 @@ int level_layout(int n_sub, const cutqc_subcircuit* s, const LevelShape& L, int 
     R->log_slices[i] = ls;
     R->part_off[i] = ls ? take(elems * ((size_t)1 << ls) * sizeof(float)) : 0;
   }
-  size_t step = 0, step_tc = 0;
+  // enough for either precision and any tensor-core size floor (the
+  // default one, or every step on the split path)
+  size_t step = 0, step_tc = 0, step_all_tc = 0;
   int rc = dd_step_ws(n_sub, s, L.active_bits.data(), n_jobs, CUTQC_PREC_FP32_SIMT, &step);
   if (rc) return rc;
   if ((rc = dd_step_ws(n_sub, s, L.active_bits.data(), n_jobs, CUTQC_PREC_FP16X3_TC_PRUNE, &step_tc))) return rc;
-  step = std::max(step, step_tc);
+  if ((rc = dd_step_ws(n_sub, s, L.active_bits.data(), n_jobs, CUTQC_PREC_FP16X3_TC_PRUNE, &step_all_tc, 0)))
+    return rc;
+  step = std::max(step, std::max(step_tc, step_all_tc));
   R->step_off = take(step);
   R->top_idx_off = take((size_t)n_jobs * 32 * sizeof(int32_t));
   R->top_val_off = take((size_t)n_jobs * 32 * sizeof(float));
@@ -435,7 +446,8 @@ static int launch_topk_scan(const float* vals, int64_t nb, int n_jobs, int topk,
 static int dd_step_impl(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, const int32_t* bin_bit,
                         int n_jobs, const float* const* merged, float* bins, double* bin_sum, int topk,
                         int32_t* top_idx, float* top_val, void* ws_dev, size_t ws_bytes, void* stream,
-                        int topk_threads, int precision = CUTQC_PREC_FP32_SIMT) {
+                        int topk_threads, int precision = CUTQC_PREC_FP32_SIMT,
+                        int64_t min_tc_outputs = kDdMinTcOutputs) {
   std::vector<TensorDesc> in;
   int tot = 0;
   int rc = dd_inputs(n_sub, s, active_bits, bin_bit, &in, &tot);
@@ -451,7 +463,7 @@ static int dd_step_impl(int n_sub, const cutqc_subcircuit* s, const int32_t* act
   const int64_t nb = (int64_t)1 << tot;
   if (precision != CUTQC_PREC_FP32_SIMT && (nb < 4 || ((uintptr_t)bins & 15) != 0)) precision = CUTQC_PREC_FP32_SIMT;
   ContractionPlan plan;
-  if ((rc = plan_contraction_batched(in, precision, n_jobs, &plan))) return rc;
+  if ((rc = plan_contraction_batched(in, precision, n_jobs, &plan, false, min_tc_outputs))) return rc;
   const size_t plan_ws = align_up(plan.ws_bytes, 256);
   const size_t topk_ws = topk_scratch(nb, n_jobs);
   const size_t bmax_ws = precision != CUTQC_PREC_FP32_SIMT && topk > 0 ? block_max_scratch(nb, n_jobs) : 0;
@@ -574,6 +586,7 @@ int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att
                    int max_jobs, cutqc_dd_job_result* jobs_dev, int32_t* n_jobs_dev, float* bins, int64_t bins_cap,
                    uint8_t* ws, size_t ws_bytes, cudaStream_t st, const cutqc_dd_options* opt) {
   int merge_ctas = kMergeCtasDefault, topk_threads = 0, precision = CUTQC_PREC_FP32_SIMT;
+  int64_t min_tc_outputs = kDdMinTcOutputs;
   if (opt) {
     if (opt->merge_ctas < 0 || opt->merge_ctas > kMergeCtasMax || opt->topk_threads < 0 || opt->topk_threads > 1024)
       return set_error(CUTQC_EINVAL, "options out of range (merge_ctas <= %d, topk_threads <= 1024)", kMergeCtasMax);
@@ -583,6 +596,9 @@ int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att
     if (opt->merge_ctas) merge_ctas = opt->merge_ctas;
     topk_threads = opt->topk_threads;
     precision = opt->precision;
+    if (opt->tc_min_outputs < 0 || opt->tc_min_outputs > 62)
+      return set_error(CUTQC_EINVAL, "options: tc_min_outputs must be in 0..62");
+    if (opt->tc_min_outputs) min_tc_outputs = (int64_t)1 << (opt->tc_min_outputs - 1);
   }
   for (int i = 0; i < n_sub; ++i)
     if (s[i].w - s[i].k_out > 32) return set_error(CUTQC_EUNSUPPORTED, "more than 32 outputs in a subcircuit");
@@ -667,7 +683,7 @@ int enqueue_levels(int n_sub, const cutqc_subcircuit* s, const float* const* att
     double* bsum = (double*)(ws + lay.sum_off);
     if ((rc = dd_step_impl(n_sub, s, L.active_bits.data(), L.bin_bit.data(), nj, merged.data(), bins + bins_off, bsum,
                            T, tidx, tval, ws + lay.step_off, lay.total - lay.step_off, st, topk_threads,
-                           precision)))
+                           precision, min_tc_outputs)))
       return rc;
     LevelInfo li{};
     li.level = level;

@@ -44,8 +44,9 @@ inline unsigned merge_grid(int64_t rows, int slices, int groups = 1, int64_t cta
 int dd_inputs(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, const int32_t* bin_bit,
               std::vector<TensorDesc>* in, int* total_bits);
 // Workspace of one step of n_jobs jobs (contraction plan and top-T scratch).
+// min_tc_outputs: as plan_contraction_batched (-1: the library's default).
 int dd_step_ws(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits, int n_jobs, int precision,
-               size_t* bytes);
+               size_t* bytes, int64_t min_tc_outputs = -1);
 // Active qubits, per-subcircuit active/zoom masks and bin bits at a depth.
 int level_shape(int n_sub, const cutqc_subcircuit* s, int n, int M, int depth, LevelShape* L);
 // Workspace layout of one level of n_jobs jobs (merge_ctas: about how many

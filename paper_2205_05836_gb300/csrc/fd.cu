@@ -133,7 +133,7 @@ uint64_t digit_mask(const std::vector<int>& all_edges, const std::vector<int>& s
 }  // namespace
 
 int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precision, int batch,
-                             ContractionPlan* plan, bool ws_upper_bound) {
+                             ContractionPlan* plan, bool ws_upper_bound, int64_t min_tc_outputs) {
   if (inputs.empty()) return set_error(CUTQC_EINVAL, "no tensors");
   if (precision != CUTQC_PREC_FP32_SIMT && precision != CUTQC_PREC_FP16X3_TC && precision != CUTQC_PREC_FP16X3_TC_PRUNE)
     return set_error(CUTQC_EINVAL, "unknown precision %d", precision);
@@ -269,7 +269,8 @@ int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precisio
       R.pos = lo_t.pos;
       R.pos.insert(R.pos.end(), hi_t.pos.begin(), hi_t.pos.end());
     }
-    if (precision != CUTQC_PREC_FP32_SIMT) {
+    st.tc = precision != CUTQC_PREC_FP32_SIMT && (double)st.M * (double)st.N * batch >= (double)min_tc_outputs;
+    if (st.tc) {
       st.Kp = (int64_t)align_up((size_t)st.K, 64);
       for (PlanOperand* op : {&st.opa, &st.opb}) {
         int64_t rows = op->view.rows();
@@ -369,7 +370,7 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
     for (size_t c = 0; c < ns_all; ++c) {
       const PlanStage& cs = plan.stages[c];
       const int dep = plan.stage_of[cs.b];
-      if (dep < 0) continue;
+      if (dep < 0 || !cs.tc || !plan.stages[dep].tc) continue;
       const bool pruned = precision == CUTQC_PREC_FP16X3_TC_PRUNE && cs.final_stage && cs.K <= kPruneMaxK;
       OperandView vb = cs.opb.view;
       vb.src = (const float*)(ws + plan.stages[dep].off_result);
@@ -392,7 +393,7 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
     const float alpha = stg.final_stage ? alpha_final : 1.0f;
     double* sum_ptr = stg.final_stage ? sum : nullptr;
     const int streaming = stg.final_stage ? 1 : 0;
-    if (precision != CUTQC_PREC_FP32_SIMT) {
+    if (stg.tc) {
       const bool prune = precision == CUTQC_PREC_FP16X3_TC_PRUNE && stg.final_stage && stg.K <= kPruneMaxK;
       const size_t prune_bytes = prune_scratch_bytes(stg.K);
       for (int b = 0; b < batch; ++b) {

@@ -328,7 +328,8 @@ def cutqc_dd_run(subs, attributed, n_qubits, M, R, T, strategy, max_jobs=256, bi
 
 
 class DDOptions(ctypes.Structure):
-    _fields_ = [("merge_ctas", c_int32), ("topk_threads", c_int32), ("precision", c_int32)]
+    _fields_ = [("merge_ctas", c_int32), ("topk_threads", c_int32), ("precision", c_int32),
+                ("tc_min_outputs", c_int32)]
 
 
 def cutqc_dd_run_async(subs, attributed, n_qubits, M, R, T, max_jobs=256, jobs=None, n_jobs=None, bins=None, ws=None,
@@ -354,7 +355,7 @@ def cutqc_dd_run_async(subs, attributed, n_qubits, M, R, T, max_jobs=256, jobs=N
     opt = None
     if options is not None:
         opt = ctypes.byref(DDOptions(int(options.get("merge_ctas", 0)), int(options.get("topk_threads", 0)),
-                                     int(options.get("precision", 0))))
+                                     int(options.get("precision", 0)), int(options.get("tc_min_outputs", 0))))
     _check(lib().cutqc_dd_run_async(c_int(len(subs)), arr, ptrs, c_int(n_qubits), c_int(M), c_int(R), c_int(T),
                                     c_int(jobs.numel() // rec), _ptr(jobs), _ptr(n_jobs), _ptr(bins),
                                     c_int64(bins.numel()), opt, _ptr(ws), c_size_t(ws.numel()), _stream(stream)))

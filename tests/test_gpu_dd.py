@@ -232,17 +232,19 @@ def test_autotuned_dd_options_match_oracle(cq):
 @pytest.mark.parametrize("kind,M,T", [("brickwall", 4, 3), ("aqft", 6, 1), ("brickwall", 10, 2), ("bv", 5, 1)])
 def test_dd_split_precision_matches_oracle(cq, kind, M, T, precision):
     """Bin reconstruction on the tensor-core path (FP16 hi/lo split, the FD
-    GEMM) inside the enqueue-only run: bins and totals against the FP64
-    oracle, and the same jobs (levels of fewer than 4 bins per job take
-    FP32).  The cases are ones whose expanded bins are separated from the
-    next by far more than rounding (an AQFT level with exactly equal bins
-    may expand either of them)."""
+    GEMM) inside the enqueue-only run, every step on the split path
+    (tc_min_outputs = 1; by default steps this small take FP32): bins and
+    totals against the FP64 oracle, and the same jobs (levels of fewer than
+    4 bins per job take FP32).  The cases are ones whose expanded bins are
+    separated from the next by far more than rounding (an AQFT level with
+    exactly equal bins may expand either of them)."""
     import torch
     from oracle import dd
     cut = _cut(kind)
     subs, A, At = _setup(cut)
     n, R = cut.circuit.n, 6
-    jobs, n_jobs, bins = cq.cutqc_dd_run_async(subs, At, n, M, R, T, options={"precision": precision})
+    jobs, n_jobs, bins = cq.cutqc_dd_run_async(subs, At, n, M, R, T,
+                                               options={"precision": precision, "tc_min_outputs": 1})
     got = cq.dd_jobs_from_device(jobs, n_jobs)
     ref = dd.run(A, [s.out_qubit for s in subs], [s.edges for s in subs], cut.K, n, M, R, T, strategy="bfs")
     assert len(got) == len(ref)
@@ -255,6 +257,29 @@ def test_dd_split_precision_matches_oracle(cq, kind, M, T, precision):
         top = [i for i in J.top_idx[:T] if i >= 0]
         if rj["top"]:
             np.testing.assert_allclose(sorted(rj["bins"][top]), sorted(rj["bins"][rj["top"]]), atol=1e-6)
+    assert cq.cutqc_device_status() == 0
+
+
+@pytest.mark.parametrize("kind,M,T", [("brickwall", 10, 2), ("aqft", 6, 1)])
+def test_dd_split_precision_small_steps_take_fp32(cq, kind, M, T):
+    """Under the tensor-core precision with the default floor, a level whose
+    contraction steps have fewer than 2^20 outputs runs them in FP32 on CUDA
+    cores: the records and bins equal the FP32 run's bit for bit (the
+    float64 totals to rounding)."""
+    cut = _cut(kind)
+    subs, A, At = _setup(cut)
+    n, R = cut.circuit.n, 6
+    runs = []
+    for prec in (0, 1):
+        jobs, n_jobs, bins = cq.cutqc_dd_run_async(subs, At, n, M, R, T, options={"precision": prec})
+        js = cq.dd_jobs_from_device(jobs, n_jobs)
+        runs.append([(list(j.active[:j.n_active]), j.zoom(), list(j.top_idx[:T]), j.bin_sum,
+                      bins[j.bins_offset:j.bins_offset + (1 << j.n_active)].cpu().numpy()) for j in js])
+    assert len(runs[0]) == len(runs[1])
+    for a, b in zip(*runs):
+        assert a[:3] == b[:3]
+        assert np.array_equal(a[4], b[4])
+        assert abs(a[3] - b[3]) <= 1e-12       # float64 totals: atomics add warps' sums in any order
     assert cq.cutqc_device_status() == 0
 
 
@@ -384,7 +409,7 @@ def test_dd_batched_full_size(cq, n_qubits, n_jobs):
 
 @pytest.mark.parametrize("T", [1, 4])
 def test_dd_dense_topk_candidates_with_ties(cq, T):
-    """One dense job (every output active, 2^18 bins: the selection takes
+    """One dense job (every output active, 2^20 bins: the selection takes
     the chunked two-pass route) on the tensor-core path: two synthetic
     subcircuits joined by one cut, attributed entries small integers (the
     FP16 hi/lo products and sums are then exact), so many bins tie.  The T
@@ -392,7 +417,7 @@ def test_dd_dense_topk_candidates_with_ties(cq, T):
     descending, bin index ascending) over the bins written."""
     import torch
     from types import SimpleNamespace
-    o0, o1 = 9, 9
+    o0, o1 = 10, 10
     s0 = SimpleNamespace(w=o0 + 1, in_local=[], in_edge=[], out_local=[o0], out_edge=[0],
                          out_qubit=list(range(o1, o1 + o0)), edges=[0], o=o0)
     s1 = SimpleNamespace(w=o1, in_local=[0], in_edge=[0], out_local=[], out_edge=[],
@@ -406,7 +431,7 @@ def test_dd_dense_topk_candidates_with_ties(cq, T):
     assert len(js) == 1 and js[0].n_active == n
     b = bins[:1 << n].cpu().numpy().astype(np.float64)
     A0, A1 = (a.cpu().numpy().astype(np.float64) for a in att)
-    # bin index: bit j = active qubit j; s1 owns qubits 0..8, s0 owns 9..17
+    # bin index: bit j = active qubit j; s1 owns qubits 0..9, s0 owns 10..19
     ref = (A0 @ A1.T).reshape(-1) * 0.5
     assert np.array_equal(b, ref)
     order = np.lexsort((np.arange(1 << n), -b))[:T]
