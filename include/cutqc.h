@@ -301,13 +301,15 @@ int cutqc_dd_run(int n_sub, const cutqc_subcircuit* s, const float* const* attri
  *                 tc_min_outputs moves that floor).
  *                 Bin totals are float64 either way.
  * Jobs of more than 2^16 bins select their top T in two passes (chunks of
- * the bins, then the chunks' candidates), with the same order.  On the
- * tensor-core path, jobs of at least 2^22 bins whose last GEMM runs on SM
- * pairs take it from block maxima instead: that GEMM also writes the largest
- * value of each 32 x 64 block of its output, and only the blocks whose
- * maximum reaches the T-th largest block maximum are read again (every bin
- * among the T largest lies in one of them); a job where more than 32 blocks
- * reach it takes the two-pass scan.  The result is the same.               */
+ * the bins, then the chunks' candidates), with the same order.  Jobs of at
+ * least 2^22 bins whose last contraction step runs on SM pairs (tensor-core
+ * path) or as FP32 outer products (a last step over at most 16 cut terms,
+ * any precision) take it from block maxima instead: that step also writes
+ * the largest value of each 32 x 64 block of its output, and only the
+ * blocks whose maximum reaches the T-th largest block maximum are read
+ * again (every bin among the T largest lies in one of them); a job where
+ * more than 32 blocks reach it takes the two-pass scan.  The result is the
+ * same.                                                                     */
 typedef struct cutqc_dd_options {
   int32_t merge_ctas;
   int32_t topk_threads;

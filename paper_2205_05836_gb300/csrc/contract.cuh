@@ -106,6 +106,7 @@ struct PlanStage {
   int a = -1, b = -1, result = -1;
   bool final_stage = false;
   bool tc = false;          // tensor-core split path (else FP32 on CUDA cores)
+  bool outer = false;       // last step over K <= 16 terms: the FP32 outer-product kernel (outer.cu)
   PlanOperand opa, opb;
   int64_t M = 0, N = 0, K = 0, Kp = 0;
   uint64_t mask_m = 0, mask_n = 0;
@@ -142,6 +143,15 @@ int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precisio
 int run_plan(const ContractionPlan& plan, const float* const* inputs, const int64_t* in_bstride, int batch,
              float* out, int64_t out_bstride, double* sum, float alpha, int precision, int64_t row_begin,
              int64_t row_end, uint8_t* ws, cudaStream_t st);
+
+// Last step over few cut terms: P[m][n] = alpha * sum_k A[m][k] B[n][k] in
+// FP32 on CUDA cores, row-major in n (mask_n the low bits), K in {1, 4, 16},
+// M a multiple of 32, N of 128, at least 2^22 outputs; sum (nullable) gets the float64 total and
+// cmax (nullable) the 32 x 64 block maxima laid out as for the paired GEMM.
+bool outer_small_k_supported(int64_t K, int64_t M, int64_t N, uint64_t mask_m, uint64_t mask_n);
+int launch_outer_small_k(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M, int64_t N, int64_t K,
+                         float alpha, uint64_t mask_m, uint64_t mask_n, float* out, double* sum, float* cmax,
+                         cudaStream_t st);
 
 // Tensor-core GEMM (tcgen05, FP16 hi/lo split, three products) with the same
 // epilogue; operands from launch_prep_rows in half mode with Kp % 64 == 0:

@@ -264,7 +264,7 @@ int dd_step_ws(int n_sub, const cutqc_subcircuit* s, const int32_t* active_bits,
   ContractionPlan plan;
   if ((rc = plan_contraction_batched(in, precision, n_jobs, &plan, true, min_tc_outputs))) return rc;
   *bytes = align_up(plan.ws_bytes, 256) + topk_scratch((int64_t)1 << tot, n_jobs) +
-           (precision != CUTQC_PREC_FP32_SIMT ? block_max_scratch((int64_t)1 << tot, n_jobs) : 0);
+           block_max_scratch((int64_t)1 << tot, n_jobs);
   return CUTQC_OK;
 }
 
@@ -466,7 +466,7 @@ static int dd_step_impl(int n_sub, const cutqc_subcircuit* s, const int32_t* act
   if ((rc = plan_contraction_batched(in, precision, n_jobs, &plan, false, min_tc_outputs))) return rc;
   const size_t plan_ws = align_up(plan.ws_bytes, 256);
   const size_t topk_ws = topk_scratch(nb, n_jobs);
-  const size_t bmax_ws = precision != CUTQC_PREC_FP32_SIMT && topk > 0 ? block_max_scratch(nb, n_jobs) : 0;
+  const size_t bmax_ws = topk > 0 ? block_max_scratch(nb, n_jobs) : 0;
   const size_t need = plan_ws + topk_ws + bmax_ws;
   if (ws_bytes < need || (need && !ws_dev)) return set_error(CUTQC_ENOMEM, "DD workspace needs %zu bytes", need);
   cudaStream_t st = (cudaStream_t)stream;

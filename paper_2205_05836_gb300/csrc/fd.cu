@@ -269,7 +269,12 @@ int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precisio
       R.pos = lo_t.pos;
       R.pos.insert(R.pos.end(), hi_t.pos.begin(), hi_t.pos.end());
     }
-    st.tc = precision != CUTQC_PREC_FP32_SIMT && (double)st.M * (double)st.N * batch >= (double)min_tc_outputs;
+    // the last step over a handful of cut terms is store-bound: FP32 outer
+    // products at HBM speed (FMAs, no split) beat the tensor-core GEMM,
+    // which pads the terms to 64 and drains every tile through its epilogue
+    st.outer = final_stage && outer_small_k_supported(st.K, st.M, st.N, st.mask_m, st.mask_n);
+    st.tc = !st.outer && precision != CUTQC_PREC_FP32_SIMT &&
+            (double)st.M * (double)st.N * batch >= (double)min_tc_outputs;
     if (st.tc) {
       st.Kp = (int64_t)align_up((size_t)st.K, 64);
       for (PlanOperand* op : {&st.opa, &st.opb}) {
@@ -453,6 +458,55 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
                             sum_ptr ? sum_ptr + b : nullptr, streaming, st, prune ? meta + 1 : nullptr, cmax, amax);
         if (rc) return rc;
         if (stg.final_stage && g_gemm_start && b == batch - 1) {
+          CUTQC_CUDA_TRY(cudaEventRecord(g_gemm_stop, st));
+          g_gemm_start = g_gemm_stop = nullptr;
+        }
+      }
+      return CUTQC_OK;
+    }
+    if (stg.outer && !partial) {
+      // FP32 outer products per item; operands gathered as for the FP32
+      // GEMM (Kp = K)
+      for (int b = 0; b < batch; ++b) {
+        OperandView va = stg.opa.view, vb = stg.opb.view;
+        va.src += b * sa_b;
+        vb.src += b * sb_b;
+        const float* A = va.src;
+        const float* B = vb.src;
+        int64_t lda = stg.K, ldb = stg.K;
+        if (!stg.opa.trivial) {
+          float* a32 = (float*)(ws + stg.opa.off32) + (size_t)b * M * stg.Kp;
+          rc = launch_prep_rows(va, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), 0, M, stg.Kp, a32, nullptr,
+                                nullptr, nullptr, st);
+          if (rc) return rc;
+          A = a32;
+          lda = stg.Kp;
+        }
+        if (!stg.opb.trivial) {
+          float* b32 = (float*)(ws + stg.opb.off32) + (size_t)b * stg.N * stg.Kp;
+          rc = launch_prep_rows(vb, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp, b32,
+                                nullptr, nullptr, nullptr, st);
+          if (rc) return rc;
+          B = b32;
+          ldb = stg.Kp;
+        }
+        float* cmax = nullptr;
+        if (g_bmax && g_bmax->cmax && ((M + 31) / 32) * ((stg.N + 63) / 64) == g_bmax->per_item) {
+          cmax = g_bmax->cmax + (size_t)b * g_bmax->per_item;
+          if (b == batch - 1) {
+            g_bmax->written = true;
+            g_bmax->M = M;
+            g_bmax->N = stg.N;
+            g_bmax->mask_m = stg.mask_m;
+            g_bmax->mask_n = stg.mask_n;
+          }
+        }
+        const bool timed = g_gemm_start && b == 0;
+        if (timed) CUTQC_CUDA_TRY(cudaEventRecord(g_gemm_start, st));
+        rc = launch_outer_small_k(A, lda, B, ldb, M, stg.N, stg.K, alpha, stg.mask_m, stg.mask_n, dst + b * dst_b,
+                                  sum_ptr ? sum_ptr + b : nullptr, cmax, st);
+        if (rc) return rc;
+        if (g_gemm_start && b == batch - 1) {
           CUTQC_CUDA_TRY(cudaEventRecord(g_gemm_stop, st));
           g_gemm_start = g_gemm_stop = nullptr;
         }

@@ -173,6 +173,45 @@ def _wide_range(rng, rows, cols, decades):
     return a.astype(np.float32).astype(np.float64)
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["simt", "tc", "tc_prune"])
+@pytest.mark.parametrize("k,order", [(0, 0), (1, 0), (2, 0), (1, 1), (2, 1)])
+def test_fd_last_step_over_few_terms(cq, k, order, precision):
+    """A last step over 4^k <= 16 cut terms whose output is row-major in the
+    column index runs FP32 outer products (outer.cu) under every precision:
+    two synthetic subcircuits (2^9 x 2^13 outputs, k cuts, values spread over
+    three decades with both signs), every output against the FP64 oracle to
+    2^-20 of the sum of |terms|, in Kronecker order and in a permuted
+    original qubit order (the row operand's bits reordered), and the float64
+    total against the outputs' own sum."""
+    import torch
+    from types import SimpleNamespace
+    from oracle import fd
+    oA, oB = 9, 13
+    rng = np.random.default_rng(300 + 10 * k + order)
+    e = list(range(k))
+    qa = [int(q) for q in oB + rng.permutation(oA)] if order else list(range(oB, oB + oA))
+    sA = SimpleNamespace(w=oA + k, in_local=[], in_edge=[], out_local=list(range(oA, oA + k)), out_edge=e,
+                         out_qubit=qa, edges=e, o=oA)
+    sB = SimpleNamespace(w=oB, in_local=list(range(k)), in_edge=e, out_local=[], out_edge=[],
+                         out_qubit=list(range(oB)), edges=e, o=oB)
+    A = [(rng.standard_normal((1 << s.o, 4 ** k)) * 10.0 ** rng.uniform(-3, 0, size=(1 << s.o, 1)))
+         .astype(np.float32).astype(np.float64) for s in (sA, sB)]
+    ref = fd.reconstruct_kron(A, [e, e], k)
+    bound = fd.reconstruct_kron([np.abs(a) for a in A], [e, e], k)
+    if order:
+        ref = fd.kron_to_original(ref, [sA.out_qubit, sB.out_qubit])
+        bound = fd.kron_to_original(bound, [sA.out_qubit, sB.out_qubit])
+    att = [torch.from_numpy(a.astype(np.float32)).cuda() for a in A]
+    total = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out, _ = cq.cutqc_reconstruct_fd([sA, sB], att, order, precision, sum_out=total)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    err = np.abs(got - ref)
+    assert (err <= 2.0 ** -20 * bound + 1e-30).all(), (err / (bound + 1e-300)).max()
+    assert abs(total.item() - got.sum()) <= 2.0 ** -20 * np.abs(got).sum()
+    assert cq.cutqc_device_status() == 0
+
+
 @pytest.mark.parametrize("decades", [8, 10])
 def test_fd_wide_dynamic_range(cq, decades):
     """Split-precision robustness: two subcircuits joined by 4 cuts (one
