@@ -296,7 +296,7 @@ int cutqc_dd_run(int n_sub, const cutqc_subcircuit* s, const float* const* attri
  *                 the FD tensor-core path; levels whose jobs have fewer than
  *                 4 bins, or whose bins do not start 16-byte aligned, run
  *                 in FP32, and so does every contraction step with fewer
- *                 than 2^20 outputs over the level's jobs (FP32 on CUDA
+ *                 than 2^22 outputs over the level's jobs (FP32 on CUDA
  *                 cores is the faster and no less accurate choice there;
  *                 tc_min_outputs moves that floor).
  *                 Bin totals are float64 either way.
@@ -314,7 +314,7 @@ typedef struct cutqc_dd_options {
   int32_t merge_ctas;
   int32_t topk_threads;
   int32_t precision;
-  int32_t tc_min_outputs;   /* 0: steps below 2^20 outputs run in FP32; b > 0: the
+  int32_t tc_min_outputs;   /* 0: steps below 2^22 outputs run in FP32; b > 0: the
                                floor is 2^(b-1) outputs (1: every step on the
                                split path) */
 } cutqc_dd_options;

@@ -126,8 +126,9 @@ __global__ void dd_block_gather(const float* __restrict__ bins, int64_t nb, cons
 // outputs (all jobs together) run in FP32 on CUDA cores: at DD's usual
 // 2^16-bin jobs the split's per-job operand preps and launches cost more
 // than its GEMMs save (three 16-active-qubit circuits: 1.5 ms against
-// 0.39 ms), and FP32 is at least as accurate.
-constexpr int64_t kDdMinTcOutputs = (int64_t)1 << 20;
+// 0.39 ms; the dense recursion's 2^20-output middle step also ran faster
+// in FP32), and FP32 is at least as accurate.
+constexpr int64_t kDdMinTcOutputs = (int64_t)1 << 22;
 constexpr int64_t kTopkChunkMin = (int64_t)1 << 16;   // bins per chunk at least
 constexpr int64_t kTopkChunksMax = 2048;
 inline int64_t topk_chunks(int64_t nb, int64_t min_chunk = kTopkChunkMin) {

@@ -263,7 +263,7 @@ def test_dd_split_precision_matches_oracle(cq, kind, M, T, precision):
 @pytest.mark.parametrize("kind,M,T", [("brickwall", 10, 2), ("aqft", 6, 1)])
 def test_dd_split_precision_small_steps_take_fp32(cq, kind, M, T):
     """Under the tensor-core precision with the default floor, a level whose
-    contraction steps have fewer than 2^20 outputs runs them in FP32 on CUDA
+    contraction steps have fewer than 2^22 outputs runs them in FP32 on CUDA
     cores: the records and bins equal the FP32 run's bit for bit (the
     float64 totals to rounding)."""
     cut = _cut(kind)
@@ -426,7 +426,7 @@ def test_dd_dense_topk_candidates_with_ties(cq, T):
     att = [torch.from_numpy(rng.integers(0, 3, size=(1 << s.o, 4)).astype(np.float32)).cuda() for s in (s0, s1)]
     n = o0 + o1
     jobs, n_jobs, bins = cq.cutqc_dd_run_async([s0, s1], att, n, n, 1, T, max_jobs=2,
-                                               options={"precision": 1})
+                                               options={"precision": 1, "tc_min_outputs": 1})
     js = cq.dd_jobs_from_device(jobs, n_jobs)
     assert len(js) == 1 and js[0].n_active == n
     b = bins[:1 << n].cpu().numpy().astype(np.float64)
