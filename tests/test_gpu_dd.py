@@ -283,6 +283,20 @@ def test_dd_split_precision_small_steps_take_fp32(cq, kind, M, T):
     assert cq.cutqc_device_status() == 0
 
 
+def test_dd_options_out_of_range(cq):
+    """Options are checked before anything is enqueued: a size floor beyond
+    2^61 or negative, an unknown precision and an oversized merge split are
+    rejected with CUTQC_EINVAL."""
+    cut = _cut("brickwall")
+    subs, A, At = _setup(cut)
+    n = cut.circuit.n
+    for opt in ({"tc_min_outputs": 63}, {"tc_min_outputs": -1}, {"precision": 7}, {"merge_ctas": 5000}):
+        with pytest.raises(cq.CutqcError) as e:
+            cq.cutqc_dd_run_async(subs, At, n, 4, 2, 2, options=opt)
+        assert e.value.code == cq.EINVAL, opt
+    assert cq.cutqc_device_status() == 0
+
+
 @pytest.mark.parametrize("T", [1, 4, 17])
 def test_dd_topk_large_job_with_ties(cq, T):
     """Selection on jobs of more than 2^16 bins (chunked first pass, then the
