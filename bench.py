@@ -305,6 +305,26 @@ def _threads():
         return os.cpu_count()
 
 
+def chain_config(w, ws=1, r0=0, r1=None):
+    """The bench line's `config` for the 32-qubit chain, the same dict in
+    both arms: the workload and its shape (the last contraction: rows of the
+    first subcircuit pair, columns of the second, cut terms between them),
+    how L2 is handled between steps, and the parallelism."""
+    subs = w.subcircuits
+    half = len(subs) // 2
+    edges_lo = {e for s in subs[:half] for e in s.edges}
+    edges_hi = {e for s in subs[half:] for e in s.edges}
+    rows = 1 << sum(s.o for s in subs[:half])
+    cols = 1 << sum(s.o for s in subs[half:])
+    r1 = rows if r1 is None else r1
+    return {"workload": WORKLOAD, "n_qubits": w.n, "cuts": w.K,
+            "subcircuit_widths": [s.w for s in subs], "subcircuit_outputs": [s.o for s in subs],
+            "last_contraction": [rows, cols, 4 ** len(edges_lo & edges_hi)],
+            "l2": "output 16 GiB > L2 each step; no flush",
+            "parallelism": f"{ws} rank(s), each writing rows [{r0}, {r1}) of the last contraction"
+                           if ws > 1 else "one GPU"}
+
+
 def run_reference(args):
     """The reference arm: the FP64 oracle on the host cores, same workload and
     metric; each step a bounded sample of Eq. 1 at contiguous outputs (the
@@ -329,7 +349,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": v, "unit": "probs/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": statistics.median(step_s) * 1e3, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference", "config": {"workload": WORKLOAD, "n_qubits": w.n, "cuts": w.K},
+            "impl": "reference", "config": chain_config(w),
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "probs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "full_job_s_at_this_rate": 2 ** w.n / v,
@@ -585,13 +605,7 @@ def run(args):
             "vs_baseline": None,
             "dtype": "f32 (FP16x3 split tensor-core products, FP32 accumulate)" if prec else "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_qubits": w.n, "cuts": w.K,
-                       "subcircuit_widths": [s.w for s in subs], "subcircuit_outputs": [s.o for s in subs],
-                       "last_contraction": [rows, cols, k_last], "precision": args.precision,
-                       "tuned": tuned,
-                       "l2": "output 16 GiB > L2 each step; no flush",
-                       "parallelism": f"{ws} rank(s), each writing rows [{r0}, {r1}) of the last contraction"
-                                      if ws > 1 else "one GPU"},
+            "config": chain_config(w, ws, r0, r1), "precision": args.precision, "tuned": tuned,
             "sum_p_error": sum_err, "tv": tv, "device_status": status,
             "roofline": roofline, "clocks": clk.summary(),
             "e2e": {"value": (n_all if ws > 1 else n_out) / (e2e_ms * 1e-3), "unit": "probs/s",
