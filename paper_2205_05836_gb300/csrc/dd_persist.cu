@@ -214,7 +214,7 @@ __device__ bool grid_barrier(GridBar* g, int* status) {
           res = 0;
           break;
         }
-        __nanosleep(32);
+        __nanosleep(8);
       }
     }
     ok = res && !*vabort;
