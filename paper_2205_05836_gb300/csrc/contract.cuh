@@ -181,10 +181,11 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int64_t Kp, float alp
 
 // Block maxima of the final step's output (DD's top-T selection).  Set on
 // the calling thread around run_plan: when the final step runs on the paired
-// tensor-core GEMM over the full row range with M >= 32, N >= 64 and
-// ceil(M/32) * ceil(N/64) == per_item, it writes item b's block maxima at
-// cmax + b * per_item (layout as for launch_tc_pair_gemm) and records the
-// output geometry; otherwise `written` stays false.
+// tensor-core GEMM (M >= 32, N >= 64) or as outer products
+// (launch_outer_small_k), over the full row range, with ceil(M/32) *
+// ceil(N/64) == per_item, it writes item b's block maxima at cmax + b *
+// per_item (layout as for launch_tc_pair_gemm) and records the output
+// geometry; otherwise `written` stays false.
 struct BlockMaxSink {
   float* cmax = nullptr;
   int64_t per_item = 0;
