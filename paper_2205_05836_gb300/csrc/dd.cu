@@ -51,8 +51,9 @@ dd_topk_kernel(const float* __restrict__ vals, const int32_t* __restrict__ cidx,
                                    gridDim.y);
 }
 
-// Top-T from block maxima.  The output of the final GEMM is cut into blocks
-// (32 rows x 64 columns), and the GEMM wrote each block's largest value.  Let
+// Top-T from block maxima.  The output of the last contraction step is cut
+// into blocks (32 rows x 64 columns), and that step (the paired GEMM or the
+// outer-product kernel) wrote each block's largest value.  Let
 // v* be the T-th largest of the block maxima: T distinct bins are >= v*, so
 // every bin among the T largest is >= v*, and so is the maximum of its block.
 // The blocks whose maximum is >= v* therefore hold all of the T largest bins
