@@ -212,6 +212,36 @@ def test_fd_last_step_over_few_terms(cq, k, order, precision):
     assert cq.cutqc_device_status() == 0
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["simt", "tc"])
+def test_fd_last_step_over_few_terms_row_range(cq, precision):
+    """The few-term last step over a row range (the outer-product kernel
+    covers whole outputs only; a range takes the FP32 GEMM): rows [64, 320)
+    of a 2^22-output, 4-term step against the FP64 oracle's rows."""
+    import torch
+    from types import SimpleNamespace
+    from oracle import fd
+    oA, oB, k = 9, 13, 1
+    rng = np.random.default_rng(401)
+    e = list(range(k))
+    sA = SimpleNamespace(w=oA + k, in_local=[], in_edge=[], out_local=list(range(oA, oA + k)), out_edge=e,
+                         out_qubit=list(range(oB, oB + oA)), edges=e, o=oA)
+    sB = SimpleNamespace(w=oB, in_local=list(range(k)), in_edge=e, out_local=[], out_edge=[],
+                         out_qubit=list(range(oB)), edges=e, o=oB)
+    A = [rng.standard_normal((1 << s.o, 4 ** k)).astype(np.float32).astype(np.float64) for s in (sA, sB)]
+    rows, cols = cq.cutqc_fd_shape([sA, sB])
+    r0, r1 = 64, 320
+    assert rows >= r1 and rows * cols == 1 << (oA + oB)
+    ref = fd.reconstruct_kron(A, [e, e], k)[r0 * cols:r1 * cols]
+    bound = fd.reconstruct_kron([np.abs(a) for a in A], [e, e], k)[r0 * cols:r1 * cols]
+    att = [torch.from_numpy(a.astype(np.float32)).cuda() for a in A]
+    out, _ = cq.cutqc_reconstruct_fd([sA, sB], att, 0, precision, row_begin=r0, row_end=r1)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    assert got.shape == ref.shape
+    assert (np.abs(got - ref) <= 2.0 ** -20 * bound + 1e-30).all()
+    assert cq.cutqc_device_status() == 0
+
+
 @pytest.mark.parametrize("decades", [8, 10])
 def test_fd_wide_dynamic_range(cq, decades):
     """Split-precision robustness: two subcircuits joined by 4 cuts (one
