@@ -16,7 +16,9 @@
 // axis by axis.  Measured side (attr_meas_run): a CTA owns one measurement
 // run and 128 output rows, each thread takes the Walsh-Hadamard transform of
 // its row's 2^k_out outcomes in registers and writes the basis strings that
-// run serves.  Subcircuits with both kinds of cut take two passes through a
+// run serves; with measured cuts only (attr_meas_grp) a CTA takes the 9 runs
+// that fill whole blocks of 16 columns and stores them as 16-byte vectors.
+// Subcircuits with both kinds of cut take two passes through a
 // float32 workspace: the measured side first, on the variants as given
 // (3^k_out runs x 2^k_out outcomes -> 4^k_out bases per output row), then the
 // initialised side along the columns of the smaller result
@@ -492,16 +494,17 @@ attr_meas_run(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, 
           v[t][i | h] = a - c;
         }
     if (xr[t] >= p.n_rows) continue;
-    // every subset z of the computational digits: Z there (mask bit set), I elsewhere
-    for (int z = comp;; z = (z - 1) & comp) {
+    // transform entries fixed | z, z any subset of the computational digits
+    // (Z there, I elsewhere), walked by entry so that v stays in registers
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      if ((i & fixed) != fixed) continue;
+      const int z = i & comp;
       int g = gx;
 #pragma unroll
       for (int j = 0; j < KOUT; ++j)
         if ((z >> j) & 1) g |= 3 << (2 * j);
-      float out = 0.f;
-#pragma unroll
-      for (int i = 0; i < NB; ++i)
-        if (i == (fixed | z)) out = v[t][i];
+      const float out = v[t][i];
       if (staged) {
         dst[((int64_t)s * G + g) * p.n_rows + xr[t]] = out;
       } else {     // no init cut: the attributed layout, row x, the measured digits' columns
@@ -510,9 +513,147 @@ attr_meas_run(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, 
         for (int j = 0; j < KOUT; ++j) col |= ((g >> (2 * j)) & 3) << p.col_shift_out[j];
         dst[xr[t] * (int64_t)G + col] = out;
       }
-      if (z == 0) break;
     }
   }
+}
+
+// Measured side of a subcircuit with measured cuts only, written straight
+// into the attributed layout [x][col].  There one run's basis strings are
+// scattered over the row (a digit's four bases come from three runs), so a
+// CTA takes a group of runs instead: the 3^NG runs over the bases of the NG
+// cuts whose digits are the lowest of the column index (NG = 2, or 1 for a
+// single cut), with the other cuts' measurement bases fixed.  Those runs
+// cover, for each choice of I or Z at the other computational cuts, a block
+// of 4^NG consecutive columns.  Warp r of the CTA takes run r of the group
+// for kGrpRows consecutive rows (lane = row: the same loads and transform
+// as attr_meas_run), parks its values in shared memory, and the CTA then
+// stores each row's blocks as whole 16-byte vectors.  dst 16-byte aligned.
+constexpr int kGrpRows = 32;
+
+template <typename T, int KOUT>
+__global__ void __launch_bounds__(32 * (KOUT >= 2 ? 9 : 3))
+attr_meas_grp(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, int ja, int jb, int64_t n_xb) {
+  constexpr int NB = 1 << KOUT;
+  constexpr int NG = KOUT >= 2 ? 2 : 1;
+  constexpr int GC = 1 << (2 * NG);           // columns of a block
+  constexpr int G = 1 << (2 * KOUT);
+  constexpr int SO = 1 << (KOUT - NG);        // most blocks a group writes
+  __shared__ float tile[SO][kGrpRows][GC + 1];
+  const int64_t W = (int64_t)1 << p.w;
+  const int64_t xb = blockIdx.x % n_xb;
+  const int key = (int)(blockIdx.x / n_xb);   // base-3 digits of the other cuts, in cut order
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // measurement basis per cut (0 computational, 1 X, 2 Y; two bits per cut
+  // in dig): the grouped cuts' from the warp index, the others' from the key
+  int dig = 0, m = 0, fixed = 0, comp = 0;
+  {
+    int kk = key, p3 = 1;
+#pragma unroll
+    for (int j = 0; j < KOUT; ++j) {
+      int d;
+      if (j == ja) d = warp % 3;
+      else if (NG == 2 && j == jb) d = warp / 3;
+      else { d = kk % 3; kk /= 3; }
+      dig |= d << (2 * j);
+      m += d * p3;
+      p3 *= 3;
+      if (d) fixed |= 1 << j; else comp |= 1 << j;
+    }
+  }
+  const int64_t x = xb * kGrpRows + lane;
+  const bool ok = x < p.n_rows;
+  const int64_t rb = ok ? (int64_t)pdep64((uint64_t)x, p.out_mask) : 0;
+  const T* base = src + (int64_t)m * W;
+  float v[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    uint64_t bp = 0;
+#pragma unroll
+    for (int j = 0; j < KOUT; ++j)
+      if ((b >> j) & 1) bp |= p.meas_mask[j];
+    v[b] = ok ? load_val(base + (rb | (int64_t)bp)) : 0.f;
+  }
+  // Walsh-Hadamard transform over the outcome bits, as in attr_meas_run
+#pragma unroll
+  for (int h = 1; h < NB; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+      if ((i & h) == 0) {
+        const float a = v[i], c = v[i | h];
+        v[i] = a + c;
+        v[i | h] = a - c;
+      }
+  // transform entries fixed | z, z any subset of the computational digits
+  // (Z there, I elsewhere), walked by entry so that v stays in registers:
+  // column within the block from the grouped cuts' digits, block index from
+  // z's bits at the other computational cuts (in cut order)
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    if ((i & fixed) != fixed) continue;
+    const int z = i & comp;
+    int cl = 0, sb = 0, nb = 0;
+#pragma unroll
+    for (int j = 0; j < KOUT; ++j) {
+      const int dj = (dig >> (2 * j)) & 3;
+      const int d = ((z >> j) & 1) ? 3 : dj;
+      if (j == ja) cl |= d;
+      else if (NG == 2 && j == jb) cl |= d << 2;
+      else if (dj == 0) { sb |= ((z >> j) & 1) << nb; ++nb; }
+    }
+    tile[sb][lane][cl] = v[i];
+  }
+  __syncthreads();
+  // blocks of this group: 2^(computational cuts among the others)
+  int n_oc = 0;
+#pragma unroll
+  for (int j = 0; j < KOUT; ++j)
+    if (j != ja && !(NG == 2 && j == jb) && ((dig >> (2 * j)) & 3) == 0) ++n_oc;
+  constexpr int Q = GC / 4;                   // 16-byte vectors per block row
+  const int items = (1 << n_oc) * kGrpRows * Q;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int q = it % Q, row = (it / Q) % kGrpRows, sb = it / Q / kGrpRows;
+    const int64_t xr = xb * kGrpRows + row;
+    if (xr >= p.n_rows) continue;
+    int col = 0, nb = 0;
+#pragma unroll
+    for (int j = 0; j < KOUT; ++j) {
+      if (j == ja || (NG == 2 && j == jb)) continue;
+      int d = (dig >> (2 * j)) & 3;
+      if (d == 0) { d = ((sb >> nb) & 1) ? 3 : 0; ++nb; }
+      col |= d << p.col_shift_out[j];
+    }
+    const float* t = tile[sb][row] + 4 * q;
+    *reinterpret_cast<float4*>(dst + xr * (int64_t)G + col + 4 * q) = make_float4(t[0], t[1], t[2], t[3]);
+  }
+}
+
+template <typename T, int KOUT>
+int run_meas_grp(const T* src, float* out, const AttrParams& p, cudaStream_t st) {
+  int ja = -1, jb = -1;
+  for (int j = 0; j < KOUT; ++j) {
+    if (p.col_shift_out[j] == 0) ja = j;
+    if (p.col_shift_out[j] == 2) jb = j;
+  }
+  if (ja < 0 || (KOUT >= 2 && jb < 0)) return set_error(CUTQC_EINVAL, "internal: measured cuts' columns");
+  constexpr int NG = KOUT >= 2 ? 2 : 1;
+  const int64_t xb = (p.n_rows + kGrpRows - 1) / kGrpRows;
+  const int64_t ntask = xb * pow3(KOUT - NG);
+  if (ntask > 0x7fffffffLL) return set_error(CUTQC_EUNSUPPORTED, "attribution tensor too large");
+  attr_meas_grp<T, KOUT><<<(unsigned)ntask, 32 * pow3(NG), 0, st>>>(src, out, p, ja, jb, xb);
+  CUTQC_LAUNCH_CHECK("attr_meas_grp");
+  return CUTQC_OK;
+}
+
+template <typename T>
+int dispatch_meas_grp(const T* src, float* out, const AttrParams& p, cudaStream_t st) {
+  switch (p.k_out) {
+    case 1: return run_meas_grp<T, 1>(src, out, p, st);
+    case 2: return run_meas_grp<T, 2>(src, out, p, st);
+    case 3: return run_meas_grp<T, 3>(src, out, p, st);
+    case 4: return run_meas_grp<T, 4>(src, out, p, st);
+    case 5: return run_meas_grp<T, 5>(src, out, p, st);
+  }
+  return set_error(CUTQC_EUNSUPPORTED, "k_out = %d", p.k_out);
 }
 
 template <typename T, int KOUT>
@@ -567,6 +708,7 @@ int launch_attr(const cutqc_subcircuit* s, const T* src, float* dst, float* tmp,
     return dispatch_init<T>(src, dst, p, 1, st);
   }
   p.n_rows = (int64_t)1 << o;
+  if (((uintptr_t)dst & 15) == 0) return dispatch_meas_grp<T>(src, dst, p, st);
   return dispatch_meas_run<T>(src, dst, p, 0, st);
 }
 

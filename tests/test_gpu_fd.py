@@ -69,6 +69,43 @@ def test_attribution_matches_oracle(cq, name, cut):
             assert np.abs(g - r).max() <= 4e-7 * scale, name
 
 
+@pytest.mark.parametrize("kout,w,aligned", [(1, 3, True), (2, 4, True), (3, 9, True), (4, 12, True),
+                                             (5, 11, True), (5, 5, True), (4, 6, True), (2, 9, False),
+                                             (4, 12, False)])
+def test_attribution_measured_cuts_only(cq, kout, w, aligned):
+    """Subcircuits with measured cuts only write the attributed layout
+    directly: a CTA takes the group of runs that fills whole blocks of
+    columns (the run-at-a-time kernel when the output is not 16-byte
+    aligned).  Random variants, measured qubits anywhere, edge ids in any
+    order, 2^o rows from 1 (fewer than one CTA's 32) to several CTAs;
+    every entry written (NaN-filled output) and within the float32
+    rounding of a k_out-level Walsh-Hadamard transform of the oracle."""
+    import torch
+    from types import SimpleNamespace
+    from oracle import attribution
+    rng = np.random.default_rng(1000 * kout + w)
+    out_local = sorted(rng.choice(w, size=kout, replace=False).tolist())
+    out_edge = rng.permutation(np.arange(3, 3 + 2 * kout, 2)).tolist()
+    sub = SimpleNamespace(w=w, in_local=[], out_local=out_local, in_edge=[], out_edge=out_edge,
+                          out_qubit=list(range(w - kout)))
+    var = rng.uniform(0.0, 1.0, size=(1, 3 ** kout, 2 ** w))
+    ref = attribution.attribute(var, w, [], out_local, [], out_edge)
+    n = ref.size
+    # inputs rounded once, then k_out add/subtract levels over 2^k_out values <= 1
+    tol = (kout + 2) * 2.0 ** (kout - 24)
+    for dtype in (torch.float64, torch.float32):
+        buf = torch.full((n + 4,), float("nan"), dtype=torch.float32, device="cuda")
+        out = buf[0 if aligned else 1:][:n].view(ref.shape)
+        assert (out.data_ptr() % 16 == 0) == aligned
+        cq.cutqc_attribute(sub, torch.from_numpy(var).cuda().to(dtype), out=out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.float64)
+        assert np.isfinite(got).all()
+        assert np.abs(got - ref).max() <= tol, (kout, w, dtype)
+        lo = 0 if aligned else 1
+        assert torch.isnan(buf[:lo]).all() and torch.isnan(buf[lo + n:]).all()     # nothing outside
+
+
 @pytest.mark.parametrize("precision", [0, 1, 2], ids=["simt", "tc", "tc_prune"])
 @pytest.mark.parametrize("order", [0, 1], ids=["kron", "original"])
 @pytest.mark.parametrize("name,cut", CASES, ids=[c[0] for c in CASES])
