@@ -427,20 +427,56 @@ int dispatch_init_cols(const float* src, float* out, const AttrParams& p, cudaSt
 }
 
 
+// Shared by the two measured-side kernels: the outcome values of output row
+// x of one run and their Walsh-Hadamard transform over the outcome bits
+// (entry `mask` = sum_b (-1)^popcount(b & mask) V[b]).  The row's offset
+// within the run is x with a zero bit inserted at each measured qubit (the
+// cut qubits are in ascending order); outcome b adds the bits of its
+// measured qubits.  Offsets fit 32 bits (w <= 30).
+template <typename T, int KOUT>
+__device__ __forceinline__ void load_run_row(const T* run, const AttrParams& p, int x, bool ok,
+                                             float (&v)[1 << KOUT]) {
+  constexpr int NB = 1 << KOUT;
+  int rb = x;
+#pragma unroll
+  for (int j = 0; j < KOUT; ++j) {
+    const int lowm = (int)p.meas_mask[j] - 1;
+    rb = ((rb & ~lowm) << 1) | (rb & lowm);
+  }
+  const T* row = run + rb;
+  int bp[NB];
+  bp[0] = 0;
+#pragma unroll
+  for (int j = 0; j < KOUT; ++j) {
+    const int mj = (int)p.meas_mask[j];
+#pragma unroll
+    for (int b = 0; b < (1 << j); ++b) bp[b | (1 << j)] = bp[b] | mj;
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) v[b] = ok ? load_val(row + bp[b]) : 0.f;
+#pragma unroll
+  for (int h = 1; h < NB; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+      if ((i & h) == 0) {
+        const float a = v[i], c = v[i | h];
+        v[i] = a + c;
+        v[i | h] = a - c;
+      }
+}
+
 // Measured side of a subcircuit with both kinds of cut, one measurement run
 // at a time.  CTA (x block, run m, init state s): each thread loads the
 // 2^KOUT outcome values of one output row x of run m (a warp's loads are
 // runs of consecutive values when the output qubits are the low local bits),
-// takes their
-// Walsh-Hadamard transform over the outcomes in registers (entry `mask` =
-// sum_b (-1)^popcount(b & mask) V[b]), and writes the basis strings g whose
-// run is m -- a measured cut's digit is X or Y where the run measured in that
-// basis, I or Z where it measured in the computational basis -- to
-// W[s][g][x], x fastest (coalesced).
+// takes their Walsh-Hadamard transform in registers, and writes the basis
+// strings g whose run is m -- a measured cut's digit is X or Y where the run
+// measured in that basis, I or Z where it measured in the computational
+// basis -- to W[s][g][x], x fastest (coalesced).  The transform entry of
+// each basis string is fixed | z, z the subset of the computational digits
+// read as Z; lane i works out where entry i goes (the same for the whole
+// CTA) and the warp reads it by shuffle.
 constexpr int kRunRows = 128;     // threads per CTA
-// rows per thread: 2 measured slower, also as adjacent rows read by one
-// vector load (33 against 29 us on the 30-qubit workload's 2^13-row subcircuit)
-constexpr int kRunRpt = 1;
 
 template <typename T, int KOUT>
 __global__ void __launch_bounds__(kRunRows)
@@ -449,30 +485,17 @@ attr_meas_run(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, 
   constexpr int NM = pow3(KOUT);
   constexpr int G = 1 << (2 * KOUT);
   const int64_t W = (int64_t)1 << p.w;
-  // task: x block (kRunRows * kRunRpt rows) fastest, then the run, then the
-  // init state (consecutive CTAs read neighbouring blocks of the variants)
+  // task: x block fastest, then the run, then the init state (consecutive
+  // CTAs read neighbouring blocks of the variants)
   const int64_t task = blockIdx.x;
   const int64_t xb = task % n_xb;
   const int m = (int)((task / n_xb) % NM);
   const int s = (int)(task / n_xb / NM);
-  const T* base = src + ((int64_t)s * NM + m) * W;
-  // every thread loads all outcomes of its kRunRpt rows before any arithmetic
-  float v[kRunRpt][NB];
-  int64_t xr[kRunRpt];
-#pragma unroll
-  for (int t = 0; t < kRunRpt; ++t) {
-    xr[t] = xb * (kRunRows * kRunRpt) + t * kRunRows + threadIdx.x;
-    const bool ok = xr[t] < p.n_rows;
-    const int64_t rb = ok ? (int64_t)pdep64((uint64_t)xr[t], p.out_mask) : 0;
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      uint64_t bp = 0;
-#pragma unroll
-      for (int j = 0; j < KOUT; ++j)
-        if ((b >> j) & 1) bp |= p.meas_mask[j];
-      v[t][b] = ok ? load_val(base + (rb | (int64_t)bp)) : 0.f;
-    }
-  }
+  const int lane = threadIdx.x & 31;
+  const int x = (int)(xb * kRunRows) + threadIdx.x;
+  const bool ok = x < p.n_rows;
+  float v[NB];
+  load_run_row<T, KOUT>(src + ((int64_t)s * NM + m) * W, p, x, ok, v);
   // run m's digits (base 3): 0 computational, 1 X, 2 Y
   int fixed = 0, comp = 0, gx = 0;
 #pragma unroll
@@ -480,40 +503,30 @@ attr_meas_run(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, 
     const int md = mm % 3;
     if (md) { fixed |= 1 << j; gx |= md << (2 * j); } else comp |= 1 << j;
   }
+  // lane i: the column of entry i in the output (basis string g when staged,
+  // the attributed layout's column otherwise), -1 if the run has no entry i
+  int my_col = -1;
+  if (lane < NB && (lane & fixed) == fixed) {
+    const int z = lane & comp;
+    int g = gx;
 #pragma unroll
-  for (int t = 0; t < kRunRpt; ++t) {
-    // Walsh-Hadamard transform over the outcome bits: v[mask] = sum_b
-    // (-1)^popcount(b & mask) V[b]
+    for (int j = 0; j < KOUT; ++j)
+      if ((z >> j) & 1) g |= 3 << (2 * j);
+    if (staged) {
+      my_col = g;
+    } else {
+      int col = 0;
 #pragma unroll
-    for (int h = 1; h < NB; h <<= 1)
-#pragma unroll
-      for (int i = 0; i < NB; ++i)
-        if ((i & h) == 0) {
-          const float a = v[t][i], c = v[t][i | h];
-          v[t][i] = a + c;
-          v[t][i | h] = a - c;
-        }
-    if (xr[t] >= p.n_rows) continue;
-    // transform entries fixed | z, z any subset of the computational digits
-    // (Z there, I elsewhere), walked by entry so that v stays in registers
-#pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      if ((i & fixed) != fixed) continue;
-      const int z = i & comp;
-      int g = gx;
-#pragma unroll
-      for (int j = 0; j < KOUT; ++j)
-        if ((z >> j) & 1) g |= 3 << (2 * j);
-      const float out = v[t][i];
-      if (staged) {
-        dst[((int64_t)s * G + g) * p.n_rows + xr[t]] = out;
-      } else {     // no init cut: the attributed layout, row x, the measured digits' columns
-        int col = 0;
-#pragma unroll
-        for (int j = 0; j < KOUT; ++j) col |= ((g >> (2 * j)) & 3) << p.col_shift_out[j];
-        dst[xr[t] * (int64_t)G + col] = out;
-      }
+      for (int j = 0; j < KOUT; ++j) col |= ((g >> (2 * j)) & 3) << p.col_shift_out[j];
+      my_col = col;
     }
+  }
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int col = __shfl_sync(0xffffffffu, my_col, i);
+    if (col < 0 || !ok) continue;
+    if (staged) dst[((int64_t)s * G + col) * p.n_rows + x] = v[i];
+    else dst[(int64_t)x * G + col] = v[i];      // no init cut: row x of the attributed layout
   }
 }
 
@@ -525,8 +538,8 @@ attr_meas_run(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, 
 // single cut), with the other cuts' measurement bases fixed.  Those runs
 // cover, for each choice of I or Z at the other computational cuts, a block
 // of 4^NG consecutive columns.  Warp r of the CTA takes run r of the group
-// for kGrpRows consecutive rows (lane = row: the same loads and transform
-// as attr_meas_run), parks its values in shared memory, and the CTA then
+// for kGrpRows consecutive rows (lane = row: the loads and transform of
+// attr_meas_run), parks its values in shared memory, and the CTA then
 // stores each row's blocks as whole 16-byte vectors.  dst 16-byte aligned.
 constexpr int kGrpRows = 32;
 
@@ -536,9 +549,10 @@ attr_meas_grp(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, 
   constexpr int NB = 1 << KOUT;
   constexpr int NG = KOUT >= 2 ? 2 : 1;
   constexpr int GC = 1 << (2 * NG);           // columns of a block
+  constexpr int RS = GC + 1;                  // padded tile row
   constexpr int G = 1 << (2 * KOUT);
   constexpr int SO = 1 << (KOUT - NG);        // most blocks a group writes
-  __shared__ float tile[SO][kGrpRows][GC + 1];
+  __shared__ float tile[SO * kGrpRows * RS];  // [block][row][column]
   const int64_t W = (int64_t)1 << p.w;
   const int64_t xb = blockIdx.x % n_xb;
   const int key = (int)(blockIdx.x / n_xb);   // base-3 digits of the other cuts, in cut order
@@ -560,37 +574,17 @@ attr_meas_grp(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, 
       if (d) fixed |= 1 << j; else comp |= 1 << j;
     }
   }
-  const int64_t x = xb * kGrpRows + lane;
+  const int x = (int)(xb * kGrpRows) + lane;
   const bool ok = x < p.n_rows;
-  const int64_t rb = ok ? (int64_t)pdep64((uint64_t)x, p.out_mask) : 0;
-  const T* base = src + (int64_t)m * W;
   float v[NB];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    uint64_t bp = 0;
-#pragma unroll
-    for (int j = 0; j < KOUT; ++j)
-      if ((b >> j) & 1) bp |= p.meas_mask[j];
-    v[b] = ok ? load_val(base + (rb | (int64_t)bp)) : 0.f;
-  }
-  // Walsh-Hadamard transform over the outcome bits, as in attr_meas_run
-#pragma unroll
-  for (int h = 1; h < NB; h <<= 1)
-#pragma unroll
-    for (int i = 0; i < NB; ++i)
-      if ((i & h) == 0) {
-        const float a = v[i], c = v[i | h];
-        v[i] = a + c;
-        v[i | h] = a - c;
-      }
-  // transform entries fixed | z, z any subset of the computational digits
-  // (Z there, I elsewhere), walked by entry so that v stays in registers:
-  // column within the block from the grouped cuts' digits, block index from
-  // z's bits at the other computational cuts (in cut order)
-#pragma unroll
-  for (int i = 0; i < NB; ++i) {
-    if ((i & fixed) != fixed) continue;
-    const int z = i & comp;
+  load_run_row<T, KOUT>(src + (int64_t)m * W, p, x, ok, v);
+  // lane i: where entry i = fixed | z goes in the tile (z: Z at those
+  // computational cuts, I at the others), -1 if the run has no entry i.  The
+  // column within the block comes from the grouped cuts' digits, the block
+  // from z's bits at the other computational cuts (in cut order).
+  int my_off = -1;
+  if (lane < NB && (lane & fixed) == fixed) {
+    const int z = lane & comp;
     int cl = 0, sb = 0, nb = 0;
 #pragma unroll
     for (int j = 0; j < KOUT; ++j) {
@@ -600,7 +594,13 @@ attr_meas_grp(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, 
       else if (NG == 2 && j == jb) cl |= d << 2;
       else if (dj == 0) { sb |= ((z >> j) & 1) << nb; ++nb; }
     }
-    tile[sb][lane][cl] = v[i];
+    my_off = sb * (kGrpRows * RS) + cl;
+  }
+  float* trow = tile + lane * RS;
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int off = __shfl_sync(0xffffffffu, my_off, i);
+    if (off >= 0) trow[off] = v[i];
   }
   __syncthreads();
   // blocks of this group: 2^(computational cuts among the others)
@@ -622,7 +622,7 @@ attr_meas_grp(const T* __restrict__ src, float* __restrict__ dst, AttrParams p, 
       if (d == 0) { d = ((sb >> nb) & 1) ? 3 : 0; ++nb; }
       col |= d << p.col_shift_out[j];
     }
-    const float* t = tile[sb][row] + 4 * q;
+    const float* t = tile + (sb * kGrpRows + row) * RS + 4 * q;
     *reinterpret_cast<float4*>(dst + xr * (int64_t)G + col + 4 * q) = make_float4(t[0], t[1], t[2], t[3]);
   }
 }
@@ -658,7 +658,7 @@ int dispatch_meas_grp(const T* src, float* out, const AttrParams& p, cudaStream_
 
 template <typename T, int KOUT>
 int run_meas_run(const T* src, float* out, const AttrParams& p, int staged, cudaStream_t st) {
-  const int64_t xb = (p.n_rows + kRunRows * kRunRpt - 1) / (kRunRows * kRunRpt);
+  const int64_t xb = (p.n_rows + kRunRows - 1) / kRunRows;
   const int64_t ntask = xb * pow3(KOUT) << (2 * p.k_in);
   // one task per CTA (a grid of resident CTAs walking the tasks measured
   // slower: 86 against 76 us on the 32-qubit chain's middle subcircuits)

@@ -225,6 +225,79 @@ __global__ void __launch_bounds__(256) absmax_kernel(const float* __restrict__ x
   }
 }
 
+// Rows of K = Kp = 256 values, the shared digits the lowest of the source
+// columns (the usual operand of a 4-cut contraction): one warp per row as in
+// prep_kernel's vector path (two float4 per lane), but kPrepRows rows per
+// step with all their loads issued before the splits, so that a warp keeps
+// 4 KiB in flight instead of 1.  Modes 0 and 1 of prep_kernel, same results.
+constexpr int kPrepRows = 4;
+
+__global__ void __launch_bounds__(256)
+prep_rows256_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows, __half* __restrict__ hi,
+                    __half* __restrict__ lo, float* __restrict__ scale, int64_t src_bstride, int64_t dst_bstride,
+                    int mode, const unsigned int* __restrict__ gmax) {
+  constexpr int K4 = 64;
+  v.src += (int64_t)blockIdx.y * src_bstride;
+  hi += (int64_t)blockIdx.y * dst_bstride * 256;
+  lo += (int64_t)blockIdx.y * dst_bstride * 256;
+  scale += (int64_t)blockIdx.y * dst_bstride;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int64_t C = (int64_t)1 << (2 * v.k);
+  const float gsc = mode == 1 ? pow2_scale(__uint_as_float(*gmax)) : 1.f;
+  for (int64_t base = (int64_t)warp * kPrepRows; base < rows; base += (int64_t)nwarps * kPrepRows) {
+    float4 val[kPrepRows][2];
+#pragma unroll
+    for (int g = 0; g < kPrepRows; ++g) {
+      const int64_t r = base + g;
+      val[g][0] = val[g][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < rows) {
+        const int64_t m = r + row0;
+        const uint64_t xp = (uint64_t)m >> (2 * v.n_open);
+        uint64_t x = xp;
+        if (rm.permute) {
+          x = 0;
+          for (int j = 0; j < rm.n; ++j) x |= ((xp >> j) & 1) << rm.bit[j];
+        }
+        const uint64_t open = (uint64_t)m & (((uint64_t)1 << (2 * v.n_open)) - 1);
+        const float4* row4 = reinterpret_cast<const float4*>(v.src + (int64_t)x * C + pdep64(open, v.open_dmask));
+        val[g][0] = __ldg(row4 + lane);
+        val[g][1] = __ldg(row4 + lane + 32);
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < kPrepRows; ++g) {
+      const int64_t r = base + g;
+      if (r >= rows) break;
+      float sc = gsc;
+      if (mode == 0) {
+        float mx = 0.f;
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+          mx = fmaxf(mx, fmaxf(fmaxf(fabsf(val[g][i].x), fabsf(val[g][i].y)),
+                               fmaxf(fabsf(val[g][i].z), fabsf(val[g][i].w))));
+        for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        sc = pow2_scale(mx);
+      }
+      const float inv = 1.f / sc;   // exact: power of two
+      if (lane == 0 && (mode == 0 || r == 0)) scale[mode == 0 ? r : 0] = sc;
+      uint2* h4 = reinterpret_cast<uint2*>(hi + r * 256);
+      uint2* l4 = reinterpret_cast<uint2*>(lo + r * 256);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float y0 = val[g][i].x * inv, y1 = val[g][i].y * inv, y2 = val[g][i].z * inv, y3 = val[g][i].w * inv;
+        const __half a0 = __float2half_rn(y0), a1 = __float2half_rn(y1), a2 = __float2half_rn(y2),
+                     a3 = __float2half_rn(y3);
+        h4[lane + 32 * i] = pack4(a0, a1, a2, a3);
+        l4[lane + 32 * i] = pack4(__float2half_rn(y0 - __half2float(a0)), __float2half_rn(y1 - __half2float(a1)),
+                                  __float2half_rn(y2 - __half2float(a2)), __float2half_rn(y3 - __half2float(a3)));
+      }
+    }
+  }
+  static_assert(K4 == 2 * 32, "two float4 per lane per row");
+}
+
 // Short rows (Kp = 8 G half columns, K <= Kp values, K % 4 == 0, the
 // shared digits the lowest of the source columns): G lanes per row, each
 // lane loading its 8 columns (two float4, zeros past K) and writing them as
@@ -679,6 +752,25 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
       launch(0);
     }
     CUTQC_LAUNCH_CHECK("prep_small_kernel");
+    return CUTQC_OK;
+  }
+  if (!cols && !out32 && hi && low_shared && K == 256 && Kp == 256 && ((uintptr_t)v.src & 15) == 0 &&
+      src_bstride % 4 == 0) {
+    const int rblocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>((rows + 8 * kPrepRows - 1) / (8 * kPrepRows), (int64_t)sm_count() * 8));
+    if (gmax) {
+      if (batch != 1) return set_error(CUTQC_EINVAL, "internal: operand-wide scale needs batch 1");
+      int rc = max_pass([&]() -> int {
+        prep_kernel<<<dim3(blocks, 1), 256, 0, st>>>(v, rm, row0, rows, K, Kp, out32, hi, lo, scale, src_bstride,
+                                                     rows, 2, gmax, cols, meta);
+        CUTQC_LAUNCH_CHECK("prep_kernel (max)");
+        return CUTQC_OK;
+      });
+      if (rc) return rc;
+    }
+    prep_rows256_kernel<<<dim3(rblocks, gmax ? 1 : batch), 256, 0, st>>>(v, rm, row0, rows, hi, lo, scale,
+                                                                         src_bstride, rows, gmax ? 1 : 0, gmax);
+    CUTQC_LAUNCH_CHECK("prep_rows256_kernel");
     return CUTQC_OK;
   }
   if (gmax) {
