@@ -52,8 +52,16 @@ struct AttrParams {
   int k;                    // k_in + k_out
 };
 
-__device__ __forceinline__ float load_val(const double* p) { return (float)__ldg(p); }
+__device__ __forceinline__ float load_val(const double* p) { return f64_to_f32_rn(__ldg(p)); }
 __device__ __forceinline__ float load_val(const float* p) { return __ldg(p); }
+// The conversion alone, for loops that issue all their loads first (a
+// conversion between two loads would hold the second back).  Value i of
+// such a loop (i known at compile time) converts on the FP64 pipe when even
+// and on the integer pipes (f64_to_f32_rn) when odd: on GB300 either alone,
+// given every value, bounds these kernels (FP64 pipe 90% busy, or ALU 74%);
+// both round to nearest even, so the results are the same.
+__device__ __forceinline__ float to_f32(double x, int i) { return (i & 1) ? f64_to_f32_rn(x) : __double2float_rn(x); }
+__device__ __forceinline__ float to_f32(float x, int) { return x; }
 
 // 4x4 map of the initialised side: bases I, X, Y, Z from the runs
 // |0>, |1>, |+>, |+i> (in registers).
@@ -109,17 +117,17 @@ attr_init_pass(const T* __restrict__ src, float* __restrict__ dst, AttrParams p,
   const int64_t fstride = (int64_t)nm * W;
   // loads in batches of kBatch per thread (all issued before any store)
   for (int i0 = 0; i0 < F * R; i0 += kThreads * kBatch) {
-    float v[kBatch];
+    T raw[kBatch];
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
       const int i = i0 + u * kThreads + threadIdx.x;
       const int f = i / R, r = i % R;
-      v[u] = (i < F * R && r < rows) ? load_val(base + f * fstride + r) : 0.f;
+      raw[u] = (i < F * R && r < rows) ? __ldg(base + f * fstride + r) : T(0);
     }
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
       const int i = i0 + u * kThreads + threadIdx.x;
-      if (i < F * R) buf[(i / R) * RS + i % R] = v[u];
+      if (i < F * R) buf[(i / R) * RS + i % R] = to_f32(raw[u], u);
     }
   }
   __syncthreads();
@@ -444,6 +452,7 @@ __device__ __forceinline__ void load_run_row(const T* run, const AttrParams& p, 
     rb = ((rb & ~lowm) << 1) | (rb & lowm);
   }
   const T* row = run + rb;
+  T raw[NB];
   int bp[NB];
   bp[0] = 0;
 #pragma unroll
@@ -453,7 +462,9 @@ __device__ __forceinline__ void load_run_row(const T* run, const AttrParams& p, 
     for (int b = 0; b < (1 << j); ++b) bp[b | (1 << j)] = bp[b] | mj;
   }
 #pragma unroll
-  for (int b = 0; b < NB; ++b) v[b] = ok ? load_val(row + bp[b]) : 0.f;
+  for (int b = 0; b < NB; ++b) raw[b] = ok ? __ldg(row + bp[b]) : T(0);
+#pragma unroll
+  for (int b = 0; b < NB; ++b) v[b] = to_f32(raw[b], b);
 #pragma unroll
   for (int h = 1; h < NB; h <<= 1)
 #pragma unroll

@@ -383,7 +383,10 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
         max_into[dep] = (int)c;
     }
   }
-  auto run_stage = [&](const PlanStage& stg0, cudaStream_t st, size_t si) -> int {
+  // wait_b: an event the column operand's producer records on another
+  // stream; the tensor-core path waits for it after preparing the row
+  // operand (which then runs beside that producer), the other paths first
+  auto run_stage = [&](const PlanStage& stg0, cudaStream_t st, size_t si, cudaEvent_t wait_b) -> int {
     PlanStage stg = stg0;
     int64_t sa_b = 0, sb_b = 0;
     stg.opa.view.src = src_of(stg.a, &sa_b);
@@ -398,8 +401,11 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
     const float alpha = stg.final_stage ? alpha_final : 1.0f;
     double* sum_ptr = stg.final_stage ? sum : nullptr;
     const int streaming = stg.final_stage ? 1 : 0;
+    if (!stg.tc && wait_b) CUTQC_CUDA_TRY(cudaStreamWaitEvent(st, wait_b, 0));
     if (stg.tc) {
       const bool prune = precision == CUTQC_PREC_FP16X3_TC_PRUNE && stg.final_stage && stg.K <= kPruneMaxK;
+      // the term selection reads both operands
+      if (prune && wait_b) CUTQC_CUDA_TRY(cudaStreamWaitEvent(st, wait_b, 0));
       const size_t prune_bytes = prune_scratch_bytes(stg.K);
       for (int b = 0; b < batch; ++b) {
         OperandView va = stg.opa.view, vb = stg.opb.view;
@@ -427,6 +433,7 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
         rc = launch_prep_rows(va, stg.opa.row_bits.data(), (int)stg.opa.row_bits.size(), r0, M, stg.Kp, nullptr, ah,
                               al, as, st, 1, 0, nullptr, cols, meta);
         if (rc) return rc;
+        if (!prune && wait_b && b == 0) CUTQC_CUDA_TRY(cudaStreamWaitEvent(st, wait_b, 0));
         const int bdep = plan.stage_of[stg.b];
         const bool max_ready = bdep >= 0 && max_into[bdep] == (int)si;
         rc = launch_prep_rows(vb, stg.opb.row_bits.data(), (int)stg.opb.row_bits.size(), 0, stg.N, stg.Kp, nullptr,
@@ -583,6 +590,7 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
   for (size_t si = 0; si < ns; ++si) {
     const PlanStage& stg = plan.stages[si];
     cudaStream_t st = caller;
+    cudaEvent_t wait_b = nullptr;
     if (par) {
       if (side[si]) {
         st = ss->s[nside % kSideStreams];
@@ -590,12 +598,11 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
         on_side[si] = 1;
         CUTQC_CUDA_TRY(cudaStreamWaitEvent(st, ss->fork, 0));
       }
-      for (int t : {stg.a, stg.b}) {
-        const int dep = plan.stage_of[t];
-        if (dep >= 0 && (on_side[dep] || side[si])) CUTQC_CUDA_TRY(cudaStreamWaitEvent(st, ss->done[dep], 0));
-      }
+      const int da = plan.stage_of[stg.a], db = plan.stage_of[stg.b];
+      if (da >= 0 && (on_side[da] || side[si])) CUTQC_CUDA_TRY(cudaStreamWaitEvent(st, ss->done[da], 0));
+      if (db >= 0 && db != da && (on_side[db] || side[si])) wait_b = ss->done[db];
     }
-    if ((rc = run_stage(stg, st, si))) return rc;
+    if ((rc = run_stage(stg, st, si, wait_b))) return rc;
     if (par) CUTQC_CUDA_TRY(cudaEventRecord(ss->done[si], st));
   }
   nside = std::min(nside, kSideStreams);

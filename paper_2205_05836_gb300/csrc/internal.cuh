@@ -52,6 +52,54 @@ __device__ __forceinline__ void record_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
+// IEEE 754 binary64 -> binary32, round to nearest, ties to even, on the
+// integer pipes.  GB300's FP64 pipe converts only a few values per SM per
+// clock, which is what bounded the FP64 attribution loads; this follows the
+// two formats' definitions instead.  Binary64 fields: sign, 11-bit exponent
+// e (bias 1023), 52-bit fraction; binary32: 8-bit exponent (bias 127), 23-bit
+// fraction, subnormals in units of 2^-149.  NaN stays a (quiet) NaN.
+// The rare cases: binary32 subnormals and underflow, overflow, infinities,
+// NaN (e in 1..896 or 1151..2047).
+__device__ __forceinline__ float f64_to_f32_rare(unsigned hi, unsigned lo) {
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const unsigned fh = hi & 0xfffffu;                        // fraction bits 51..32
+  if (e == 0x7ff) return __uint_as_float(sign | ((fh | lo) ? 0x7fc00000u : 0x7f800000u));
+  if (e >= 1151) return __uint_as_float(sign | 0x7f800000u);  // |d| >= 2^128
+  // binary32 subnormal or zero: d = sig * 2^(e - 1075) with sig = 2^52 +
+  // fraction, i.e. sig * 2^(e - 926) units of 2^-149
+  const int s = 926 - e;                                     // >= 30 here
+  if (e == 0 || s >= 54) return __uint_as_float(sign);
+  const unsigned long long sig = (1ull << 52) | ((unsigned long long)fh << 32) | lo;
+  unsigned long long q = sig >> s;
+  const unsigned long long rem = sig & ((1ull << s) - 1), half = 1ull << (s - 1);
+  q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+  return __uint_as_float(sign | (unsigned)q);
+}
+
+// The common case in a handful of instructions: a binary32 normal result
+// (biased exponent e - 896 in 1..254: rebias the exponent, keep fraction bits
+// 51..29, round on bits 28..0, the low bit of r deciding a tie; a carry out
+// of the fraction bumps the exponent, to infinity above the largest float),
+// or zero for e = 0 (zero or a binary64 subnormal).  The rare cases run only
+// in warps that hold one, behind a vote, so that the common path keeps its
+// registers and needs no branch per value.
+__device__ __forceinline__ float f64_to_f32_rn(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned mag = hi & 0x7fffffffu;
+  const unsigned e = mag >> 20;
+  unsigned r = ((mag - (896u << 20)) << 3) | (lo >> 29);
+  r += ((lo & 0x1fffffffu) + (r & 1u)) > 0x10000000u ? 1u : 0u;
+  r = e == 0 ? 0u : r;
+  float f = __uint_as_float((hi & 0x80000000u) | r);
+  const bool rare = e != 0 && e - 897u >= 254u;
+  if (__any_sync(__activemask(), rare)) {
+    if (rare) f = f64_to_f32_rare(hi, lo);
+  }
+  return f;
+}
+
 // Software bit deposit: scatter the low bits of v to the set bits of mask.
 __host__ __device__ __forceinline__ uint64_t pdep64(uint64_t v, uint64_t mask) {
   uint64_t r = 0;

@@ -106,6 +106,43 @@ def test_attribution_measured_cuts_only(cq, kout, w, aligned):
         assert torch.isnan(buf[:lo]).all() and torch.isnan(buf[lo + n:]).all()     # nothing outside
 
 
+def test_float64_loads_round_to_nearest_even(cq):
+    """The attribution's FP64 loads convert to float32 on the integer pipes
+    (binary64 -> binary32 round to nearest, ties to even, written out from
+    the two formats).  A subcircuit without cuts is that conversion alone:
+    bit-identical to the device's own conversion (torch float64 -> float32)
+    on random bit patterns of every exponent, ties and near-ties, the float32
+    subnormal and overflow edges, zeros and infinities; NaN stays NaN."""
+    import torch
+    from types import SimpleNamespace
+    rng = np.random.default_rng(7)
+    n = 1 << 20
+    u = rng.integers(0, 1 << 62, size=n, dtype=np.uint64) * np.uint64(4) + rng.integers(0, 4, size=n, dtype=np.uint64)
+    # a quarter of the patterns at exponents around the float32 range edges
+    # (binary64 biased exponents 860..930 and 1140..1160, 0, 2047), their
+    # dropped 29 bits a tie, just below one, or just above one
+    m = n // 4
+    exps = rng.choice(np.r_[np.arange(860, 931), np.arange(1140, 1161), [0, 1, 1023, 2046, 2047]], size=m)
+    frac = rng.integers(0, 1 << 52, size=m, dtype=np.uint64)
+    kind = rng.integers(0, 4, size=m)
+    low29 = np.uint64((1 << 29) - 1)
+    frac = np.where(kind == 0, (frac & ~low29) | np.uint64(1 << 28), frac)
+    frac = np.where(kind == 1, (frac & ~low29) | np.uint64((1 << 28) - 1), frac)
+    frac = np.where(kind == 2, (frac & ~low29) | np.uint64((1 << 28) + 1), frac)
+    sgn = rng.integers(0, 2, size=m, dtype=np.uint64) << np.uint64(63)
+    u[:m] = sgn | (exps.astype(np.uint64) << np.uint64(52)) | frac
+    d = u.view(np.float64)
+    sub = SimpleNamespace(w=20, in_local=[], out_local=[], in_edge=[], out_edge=[], out_qubit=list(range(20)))
+    t = torch.from_numpy(d).cuda()
+    got = cq.cutqc_attribute(sub, t).view(-1)
+    ref = t.to(torch.float32)
+    torch.cuda.synchronize()
+    nan = torch.isnan(ref)
+    assert torch.equal(torch.isnan(got), nan)
+    assert torch.equal(got.view(torch.int32)[~nan], ref.view(torch.int32)[~nan])
+    assert int(nan.sum()) > 0 and int(torch.isinf(ref).sum()) > 0 and int((ref == 0).sum()) > 0
+
+
 @pytest.mark.parametrize("precision", [0, 1, 2], ids=["simt", "tc", "tc_prune"])
 @pytest.mark.parametrize("order", [0, 1], ids=["kron", "original"])
 @pytest.mark.parametrize("name,cut", CASES, ids=[c[0] for c in CASES])
