@@ -435,15 +435,41 @@ def run(args):
         for ev in joins:
             cur.wait_event(ev)
 
-    def reconstruct(dst=out, tot=total):
+    def reconstruct(dst=out, tot=total, events=None):
         tot.zero_()
         if n_out > 0:
             cq.cutqc_reconstruct_fd(subs, att, cq.ORDER_KRON, prec, row_begin=r0, row_end=r1, out=dst,
-                                    sum_out=tot, ws=fd_ws)
+                                    sum_out=tot, ws=fd_ws, input_events=events)
+
+    def attribute_and_reconstruct(dst=out, tot=total):
+        # the contraction of the second pair (C2 x C3, then the split of its
+        # 256 MB result) is the longer path to the last step: its inputs are
+        # attributed first, on one side stream; C1 and C0 follow on the
+        # other once C2's tensor is written, beside that contraction; the
+        # reconstruction, issued at once, starts each contraction when its
+        # own inputs are written (cutqc_fd_input_events)
+        cur = torch.cuda.current_stream(dev)
+        fork = torch.cuda.Event()
+        fork.record(cur)
+        sa, sb = att_side
+        sa.wait_event(fork)
+        sb.wait_event(fork)
+        ev = [torch.cuda.Event() for _ in subs]
+        with torch.cuda.stream(sa):
+            for i in (2, 3):
+                cq.cutqc_attribute(subs[i], var[i], out=att[i], ws=att_ws[i])
+                ev[i].record(sa)
+        sb.wait_event(ev[2])
+        with torch.cuda.stream(sb):
+            for i in (1, 0):
+                cq.cutqc_attribute(subs[i], var[i], out=att[i], ws=att_ws[i])
+                ev[i].record(sb)
+        reconstruct(dst, tot, events=ev)
+        cur.wait_stream(sa)
+        cur.wait_stream(sb)
 
     def step():
-        attribute_all()
-        reconstruct()
+        attribute_and_reconstruct()
 
     # the contraction's work-item size, autotuned on this data (outputs must
     # be bit-identical across the candidates); set before the graphs capture
@@ -575,8 +601,7 @@ def run(args):
             stream.wait_event(copied[b])           # the previous download of this buffer is done
         for hv, v in zip(host_var, var):
             v.copy_(hv, non_blocking=True)
-        attribute_all()
-        reconstruct(dev_out[b], dev_total[b])
+        attribute_and_reconstruct(dev_out[b], dev_total[b])
         done = torch.cuda.Event()
         done.record(stream)
         copy_stream.wait_event(done)

@@ -184,6 +184,18 @@ int cutqc_fd_shape(int n_sub, const cutqc_subcircuit* s, int64_t* rows, int64_t*
  * by the caller; null, null cancels.  Errors: CUTQC_EINVAL if only one event
  * is given.                                                                 */
 int cutqc_fd_timing_events(void* start_event, void* stop_event);
+/* Input readiness (no paper counterpart): the next cutqc_reconstruct_fd made
+ * by the calling thread does not need its attributed tensors written when it
+ * is issued.  Instead, every contraction step that reads subcircuit i's
+ * tensor first makes its stream wait for events[i] (a cudaEvent_t the caller
+ * records after the work that writes that tensor, on any stream of the same
+ * device), so that steps over early inputs run while later ones are still
+ * being attributed.  A null entry means that input is ready when the call is
+ * issued.  n must equal that call's n_sub (else that call fails with
+ * CUTQC_EINVAL).  The events are the caller's; the setting applies to one
+ * call and is then cleared, and n = 0 clears it.  Errors: CUTQC_EINVAL for
+ * n outside 0..4096 or a null array with n > 0.                            */
+int cutqc_fd_input_events(int n, const void* const* events);
 /* Launch shape of the tensor-core contraction on SM pairs (process-wide; no
  * paper counterpart): each pair takes work items of one 256-row block of the
  * row operand and up to this many consecutive 128-column tiles (0, the

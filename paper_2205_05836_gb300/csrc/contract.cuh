@@ -139,10 +139,12 @@ int plan_contraction_batched(const std::vector<TensorDesc>& inputs, int precisio
 
 // Runs the plan for `batch` independent items: input i of item b at
 // inputs[i] + b * in_bstride[i]; output of item b at out + b * out_bstride;
-// sum + b (if sum).  Workspace: plan.ws_bytes * batch.
+// sum + b (if sum).  Workspace: plan.ws_bytes * batch.  in_ready (nullable):
+// one event per input (null entries allowed) that the steps reading that
+// input wait for on their stream.
 int run_plan(const ContractionPlan& plan, const float* const* inputs, const int64_t* in_bstride, int batch,
              float* out, int64_t out_bstride, double* sum, float alpha, int precision, int64_t row_begin,
-             int64_t row_end, uint8_t* ws, cudaStream_t st);
+             int64_t row_end, uint8_t* ws, cudaStream_t st, const cudaEvent_t* in_ready = nullptr);
 
 // Last step over few cut terms: P[m][n] = alpha * sum_k A[m][k] B[n][k] in
 // FP32 on CUDA cores, row-major in n (mask_n the low bits), K in {1, 4, 16},

@@ -34,6 +34,10 @@ static thread_local std::string g_last_error;
 // contraction's GEMM launch (then clears): see cutqc_fd_timing_events.
 static thread_local cudaEvent_t g_gemm_start = nullptr, g_gemm_stop = nullptr;
 
+// Readiness events of the next reconstruction's inputs on this thread (one
+// per subcircuit, null = ready at the call): see cutqc_fd_input_events.
+static thread_local std::vector<cudaEvent_t> g_input_events;
+
 // Block maxima requested for the next final step on this thread.
 static thread_local BlockMaxSink* g_bmax = nullptr;
 void set_block_max_sink(BlockMaxSink* sink) { g_bmax = sink; }
@@ -339,9 +343,10 @@ __global__ void single_copy(const float* __restrict__ T, int64_t rows, uint64_t 
 
 int run_plan(const ContractionPlan& plan, const float* const* inputs, const int64_t* in_bstride, int batch,
              float* out, int64_t out_bstride, double* sum, float alpha_final, int precision, int64_t row_begin,
-             int64_t row_end, uint8_t* ws, cudaStream_t caller) {
+             int64_t row_end, uint8_t* ws, cudaStream_t caller, const cudaEvent_t* in_ready) {
   const size_t n_in = plan.stage_of.size() - plan.stages.size();
   if (plan.stages.empty()) {
+    if (in_ready && in_ready[0]) CUTQC_CUDA_TRY(cudaStreamWaitEvent(caller, in_ready[0], 0));
     const TensorDesc& T = plan.tensors[0];
     uint64_t mask = 0;
     for (int b = 0; b < T.o; ++b) mask |= (uint64_t)1 << T.pos[b];
@@ -602,6 +607,9 @@ int run_plan(const ContractionPlan& plan, const float* const* inputs, const int6
       if (da >= 0 && (on_side[da] || side[si])) CUTQC_CUDA_TRY(cudaStreamWaitEvent(st, ss->done[da], 0));
       if (db >= 0 && db != da && (on_side[db] || side[si])) wait_b = ss->done[db];
     }
+    // inputs written by work the caller issued elsewhere
+    for (int t : {stg.a, stg.b})
+      if (in_ready && t < (int)n_in && in_ready[t]) CUTQC_CUDA_TRY(cudaStreamWaitEvent(st, in_ready[t], 0));
     if ((rc = run_stage(stg, st, si, wait_b))) return rc;
     if (par) CUTQC_CUDA_TRY(cudaEventRecord(ss->done[si], st));
   }
@@ -688,6 +696,14 @@ extern "C" int cutqc_kernel_launches(int64_t* count) {
   return CUTQC_OK;
 }
 
+extern "C" int cutqc_fd_input_events(int n, const void* const* events) {
+  if (n < 0 || n > 4096) return set_error(CUTQC_EINVAL, "n = %d outside 0..4096", n);
+  if (n > 0 && !events) return set_error(CUTQC_EINVAL, "null event array");
+  g_input_events.assign(n, nullptr);
+  for (int i = 0; i < n; ++i) g_input_events[i] = (cudaEvent_t)events[i];
+  return CUTQC_OK;
+}
+
 extern "C" int cutqc_fd_timing_events(void* start_event, void* stop_event) {
   if ((start_event == nullptr) != (stop_event == nullptr))
     return set_error(CUTQC_EINVAL, "give both events or neither");
@@ -732,6 +748,11 @@ extern "C" int cutqc_reconstruct_fd_workspace_size(int n_sub, const cutqc_subcir
 extern "C" int cutqc_reconstruct_fd(int n_sub, const cutqc_subcircuit* s, const float* const* attributed,
                                     int out_order, int precision, int64_t row_begin, int64_t row_end,
                                     float* out, double* sum, void* ws_dev, size_t ws_bytes, void* stream) {
+  // this call's input events (if any were set), cleared whatever happens
+  std::vector<cudaEvent_t> ready;
+  ready.swap(g_input_events);
+  if (!ready.empty() && (int)ready.size() != n_sub)
+    return set_error(CUTQC_EINVAL, "%d input events set for %d subcircuits", (int)ready.size(), n_sub);
   std::vector<TensorDesc> in;
   int rc = fd_inputs(n_sub, s, out_order, &in);
   if (rc) return rc;
@@ -757,5 +778,5 @@ extern "C" int cutqc_reconstruct_fd(int n_sub, const cutqc_subcircuit* s, const 
   }
   std::vector<int64_t> bstride(n_sub, 0);
   return run_plan(plan, attributed, bstride.data(), 1, out, 0, sum, std::ldexp(1.0f, -plan.K), precision, row_begin,
-                  row_end, (uint8_t*)ws_dev, (cudaStream_t)stream);
+                  row_end, (uint8_t*)ws_dev, (cudaStream_t)stream, ready.empty() ? nullptr : ready.data());
 }

@@ -201,6 +201,19 @@ def cutqc_fd_timing_events(start=None, stop=None):
     _check(lib().cutqc_fd_timing_events(c_void_p(start.cuda_event), c_void_p(stop.cuda_event)))
 
 
+def cutqc_fd_input_events(events=None):
+    """The next cutqc_reconstruct_fd on this thread waits, in each step that
+    reads subcircuit i's tensor, for events[i] (a recorded torch.cuda.Event,
+    or None: ready at the call) instead of needing every input written when
+    it is issued; None or [] clears."""
+    events = list(events or [])
+    for e in events:
+        if e is not None and not e.cuda_event:
+            raise ValueError("record each input event before passing it")
+    arr = (c_void_p * max(1, len(events)))(*[None if e is None else e.cuda_event for e in events])
+    _check(lib().cutqc_fd_input_events(c_int(len(events)), arr if events else None))
+
+
 def cutqc_fd_set_tiles_per_item(tiles_per_item=0):
     """Work-item size of the tensor-core contraction (0: automatic)."""
     _check(lib().cutqc_fd_set_tiles_per_item(c_int(int(tiles_per_item))))
@@ -214,8 +227,10 @@ def cutqc_reconstruct_fd_workspace_size(subs, precision):
 
 
 def cutqc_reconstruct_fd(subs, attributed, out_order=ORDER_KRON, precision=PREC_FP16X3_TC, row_begin=0,
-                         row_end=-1, out=None, sum_out=None, ws=None, stream=None):
-    """Eq. 1 over the subcircuits.  Returns (out, sum_out)."""
+                         row_end=-1, out=None, sum_out=None, ws=None, stream=None, input_events=None):
+    """Eq. 1 over the subcircuits.  Returns (out, sum_out).  input_events:
+    optional recorded torch.cuda.Event per subcircuit (None = ready), see
+    cutqc_fd_input_events."""
     import torch
     arr, keep = _subs(subs)
     dev = attributed[0].device
@@ -231,6 +246,8 @@ def cutqc_reconstruct_fd(subs, attributed, out_order=ORDER_KRON, precision=PREC_
     if ws is None and need:
         ws = torch.empty(need, dtype=torch.uint8, device=dev)
     ptrs = (c_void_p * len(attributed))(*[t.data_ptr() for t in attributed])
+    if input_events is not None:
+        cutqc_fd_input_events(input_events)
     _check(lib().cutqc_reconstruct_fd(c_int(len(subs)), arr, ptrs, c_int(out_order), c_int(precision),
                                       c_int64(row_begin), c_int64(row_end), _ptr(out), _ptr(sum_out), _ptr(ws),
                                       c_size_t(0 if ws is None else ws.numel()), _stream(stream)))

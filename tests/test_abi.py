@@ -217,3 +217,46 @@ def test_dd_batch_many_runs_shape(built):
     assert many["phases"] == one["phases"] == 12
     assert many["ops"] == 90 * one["ops"] and many["tasks"] == 90 * one["tasks"]
     assert cq.cutqc_dd_batch_workspace_size([run] * 90) > 90 * cq.cutqc_dd_batch_workspace_size([run]) // 2
+
+
+def test_fd_input_events_host_checks(built):
+    """cutqc_fd_input_events: argument checks, and a count that does not
+    match the next reconstruction's subcircuits fails that call (then the
+    setting is gone).  Every call here fails on the host: null tensors and an
+    invalid output order, so nothing can reach a kernel launch."""
+    cutqc = built
+    L = cutqc.lib()
+    assert L.cutqc_fd_input_events(ctypes.c_int(-1), None) == cutqc.EINVAL
+    assert L.cutqc_fd_input_events(ctypes.c_int(4097), None) == cutqc.EINVAL
+    assert L.cutqc_fd_input_events(ctypes.c_int(2), None) == cutqc.EINVAL
+    assert L.cutqc_fd_input_events(ctypes.c_int(0), None) == cutqc.OK
+
+    class U:
+        w = 3
+        in_local = []
+        out_local = [2]
+        in_edge = []
+        out_edge = [0]
+        out_qubit = [0, 1]
+
+    class V:
+        w = 3
+        in_local = [0]
+        out_local = []
+        in_edge = [0]
+        out_edge = []
+        out_qubit = [2, 3, 4]
+    arr, keep = cutqc._subs([U, V])
+    ptrs = (ctypes.c_void_p * 2)(None, None)
+    none3 = (ctypes.c_void_p * 3)(None, None, None)
+    assert L.cutqc_fd_input_events(ctypes.c_int(3), none3) == cutqc.OK
+
+    def call():
+        return L.cutqc_reconstruct_fd(ctypes.c_int(2), arr, ptrs, ctypes.c_int(7),
+                                      ctypes.c_int(cutqc.PREC_FP32_SIMT), ctypes.c_int64(0), ctypes.c_int64(-1),
+                                      None, None, None, ctypes.c_size_t(0), None)
+    assert call() == cutqc.EINVAL
+    assert "input events" in cutqc.cutqc_last_error()
+    # cleared by that call: the next one fails on the output order instead
+    assert call() == cutqc.EINVAL
+    assert "out_order" in cutqc.cutqc_last_error()

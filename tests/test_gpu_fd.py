@@ -734,3 +734,69 @@ def test_bounded_wait_expires_with_status(cq):
     out, _ = cq.cutqc_reconstruct_fd(subs, _gpu_att(cq, subs, var), 0, 1)
     assert metrics.tv(out.cpu().numpy().astype(np.float64), ref) <= TV_GATE
     assert cq.cutqc_device_status() == 0
+
+
+@pytest.mark.parametrize("graph", [False, True], ids=["eager", "graph"])
+@pytest.mark.parametrize("precision", [0, 1], ids=["simt", "tc"])
+def test_fd_waits_for_input_events(cq, precision, graph):
+    """Issued before its inputs are written: the subcircuits are attributed
+    on two other streams (one held back ~1 ms by a sleep kernel) into
+    NaN-filled tensors, each followed by an event; the reconstruction, on a
+    stream that never waited for them, gets those events
+    (cutqc_fd_input_events) and must give the bits of the reconstruction of
+    the same tensors written beforehand, eagerly and as a replayed graph."""
+    import torch
+    from workloads import circuits as C
+    from workloads.cutting import search_cut
+    from workloads.simulate import simulate_variants
+    cut = search_cut(C.brickwall(12, 3, 2), 5, 4, restarts=6)
+    subs = cut.subcircuits
+    assert len(subs) >= 3
+    var = [torch.from_numpy(simulate_variants(s)).cuda() for s in subs]
+    ref_att = [cq.cutqc_attribute(s, v) for s, v in zip(subs, var)]
+    ref, _ = cq.cutqc_reconstruct_fd(subs, ref_att, 0, precision)
+    torch.cuda.synchronize()
+    att = [torch.full_like(a, float("nan")) for a in ref_att]
+    out = torch.full_like(ref, float("nan"))
+    ws = torch.empty(max(1, cq.cutqc_reconstruct_fd_workspace_size(subs, precision)), dtype=torch.uint8,
+                     device="cuda")
+    att_ws = [torch.empty(max(1, cq.cutqc_attribute_workspace_size(s)), dtype=torch.uint8, device="cuda")
+              for s in subs]
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def step():
+        cur = torch.cuda.current_stream()
+        fork = torch.cuda.Event()
+        fork.record(cur)
+        sa.wait_event(fork)
+        sb.wait_event(fork)
+        ev = [torch.cuda.Event() for _ in subs]
+        for i, s in enumerate(subs):
+            st = sa if i % 2 == 0 else sb
+            with torch.cuda.stream(st):
+                if i == 0:
+                    torch.cuda._sleep(2_000_000)
+                cq.cutqc_attribute(s, var[i], out=att[i], ws=att_ws[i])
+            ev[i].record(st)
+        cq.cutqc_reconstruct_fd(subs, att, 0, precision, out=out, ws=ws, input_events=ev)
+        cur.wait_stream(sa)
+        cur.wait_stream(sb)
+
+    if not graph:
+        step()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    else:
+        stream = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            step()
+        for _ in range(2):
+            for a in att:
+                a.fill_(float("nan"))
+            out.fill_(float("nan"))
+            torch.cuda.synchronize()
+            g.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(out, ref)
+    assert cq.cutqc_device_status() == 0
