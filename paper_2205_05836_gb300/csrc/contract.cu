@@ -298,6 +298,96 @@ prep_rows256_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows, __half
   static_assert(K4 == 2 * 32, "two float4 per lane per row");
 }
 
+// Rows of 256 source values with a column list (cut-term pruning): each
+// row read whole as in prep_rows256_kernel (two float4 per lane, kPrepRows
+// rows per warp in flight) into the warp's part of shared memory, then the
+// kept columns gathered from there.  A few dozen scattered columns of a 1 KB
+// row touch nearly all of its sectors anyway, and whole-row vector loads
+// take far fewer instructions than one load per kept column.  Output column
+// s < meta[0] is source column cols[s], columns [meta[0], meta[2]) are zero,
+// the rest of the row (stride 256) is not written.  Modes 0 and 1 of
+// prep_kernel, same results.
+__global__ void __launch_bounds__(256)
+prep_rows256_cols_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows, __half* __restrict__ hi,
+                         __half* __restrict__ lo, float* __restrict__ scale, int mode,
+                         const unsigned int* __restrict__ gmax, const int* __restrict__ cols,
+                         const int* __restrict__ meta) {
+  __shared__ __align__(16) float srow[8][kPrepRows][256];
+  __shared__ int scols[256];
+  const int K = __ldg(meta), Kw = __ldg(meta + 2);
+  for (int c = threadIdx.x; c < K; c += blockDim.x) scols[c] = __ldg(cols + c);
+  __syncthreads();
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int64_t C = (int64_t)1 << (2 * v.k);
+  const float gsc = mode == 1 ? pow2_scale(__uint_as_float(*gmax)) : 1.f;
+  float (*sw)[256] = srow[threadIdx.x >> 5];
+  for (int64_t base = (int64_t)warp * kPrepRows; base < rows; base += (int64_t)nwarps * kPrepRows) {
+    float4 val[kPrepRows][2];
+#pragma unroll
+    for (int g = 0; g < kPrepRows; ++g) {
+      const int64_t r = base + g;
+      val[g][0] = val[g][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < rows) {
+        const int64_t m = r + row0;
+        const uint64_t xp = (uint64_t)m >> (2 * v.n_open);
+        uint64_t x = xp;
+        if (rm.permute) {
+          x = 0;
+          for (int j = 0; j < rm.n; ++j) x |= ((xp >> j) & 1) << rm.bit[j];
+        }
+        const uint64_t open = (uint64_t)m & (((uint64_t)1 << (2 * v.n_open)) - 1);
+        const float4* row4 = reinterpret_cast<const float4*>(v.src + (int64_t)x * C + pdep64(open, v.open_dmask));
+        val[g][0] = __ldg(row4 + lane);
+        val[g][1] = __ldg(row4 + lane + 32);
+      }
+    }
+    __syncwarp();        // the previous step's gathers from sw are done
+#pragma unroll
+    for (int g = 0; g < kPrepRows; ++g) {
+      reinterpret_cast<float4*>(sw[g])[lane] = val[g][0];
+      reinterpret_cast<float4*>(sw[g])[lane + 32] = val[g][1];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int g = 0; g < kPrepRows; ++g) {
+      const int64_t r = base + g;
+      if (r >= rows) break;
+      float y[2][4];
+      float mx = 0.f;
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int c = 4 * (lane + 32 * j) + e;
+          y[j][e] = c < K ? sw[g][scols[c]] : 0.f;
+          mx = fmaxf(mx, fabsf(y[j][e]));
+        }
+      float sc = gsc;
+      if (mode == 0) {
+        for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        sc = pow2_scale(mx);
+      }
+      const float inv = 1.f / sc;   // exact: power of two
+      if (lane == 0 && (mode == 0 || r == 0)) scale[mode == 0 ? r : 0] = sc;
+      uint2* h4 = reinterpret_cast<uint2*>(hi + r * 256);
+      uint2* l4 = reinterpret_cast<uint2*>(lo + r * 256);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int q = lane + 32 * j;
+        if (4 * q >= Kw) continue;
+        const float y0 = y[j][0] * inv, y1 = y[j][1] * inv, y2 = y[j][2] * inv, y3 = y[j][3] * inv;
+        const __half a0 = __float2half_rn(y0), a1 = __float2half_rn(y1), a2 = __float2half_rn(y2),
+                     a3 = __float2half_rn(y3);
+        h4[q] = pack4(a0, a1, a2, a3);
+        l4[q] = pack4(__float2half_rn(y0 - __half2float(a0)), __float2half_rn(y1 - __half2float(a1)),
+                      __float2half_rn(y2 - __half2float(a2)), __float2half_rn(y3 - __half2float(a3)));
+      }
+    }
+  }
+}
+
 // Short rows (Kp = 8 G half columns, K <= Kp values, K % 4 == 0, the
 // shared digits the lowest of the source columns): G lanes per row, each
 // lane loading its 8 columns (two float4, zeros past K) and writing them as
@@ -771,6 +861,15 @@ int launch_prep_rows(const OperandView& v, const int* row_bits, int n_bits, int6
     prep_rows256_kernel<<<dim3(rblocks, gmax ? 1 : batch), 256, 0, st>>>(v, rm, row0, rows, hi, lo, scale,
                                                                          src_bstride, rows, gmax ? 1 : 0, gmax);
     CUTQC_LAUNCH_CHECK("prep_rows256_kernel");
+    return CUTQC_OK;
+  }
+  if (cols && !out32 && hi && low_shared && K == 256 && Kp == 256 && batch == 1 && ((uintptr_t)v.src & 15) == 0) {
+    // (with a column list the max over the kept columns is already in *gmax)
+    const int rblocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>((rows + 8 * kPrepRows - 1) / (8 * kPrepRows), (int64_t)sm_count() * 4));
+    prep_rows256_cols_kernel<<<rblocks, 256, 0, st>>>(v, rm, row0, rows, hi, lo, scale, gmax ? 1 : 0, gmax, cols,
+                                                      meta);
+    CUTQC_LAUNCH_CHECK("prep_rows256_cols_kernel");
     return CUTQC_OK;
   }
   if (gmax) {
