@@ -592,7 +592,42 @@ colw_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows, int64_t K, flo
   float acc[NPL], mx[NPL];
 #pragma unroll
   for (int i = 0; i < NPL; ++i) acc[i] = mx[i] = 0.f;
-  for (int64_t r = warp; r < rows; r += nwarps) {
+  // rows of exactly 256 contiguous values: kPrepRows rows per warp step, all
+  // their loads issued first (one row at a time kept 1 KB in flight per warp)
+  const bool vec4 = vec && NPL == 8 && K == 256;
+  for (int64_t base = (int64_t)warp * kPrepRows; vec4 && base < rows; base += (int64_t)nwarps * kPrepRows) {
+    float4 q[kPrepRows][2];
+#pragma unroll
+    for (int g = 0; g < kPrepRows; ++g) {
+      const int64_t r = base + g;
+      q[g][0] = q[g][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < rows) {
+        const int64_t m = r + row0;
+        const uint64_t xp = (uint64_t)m >> (2 * v.n_open);
+        uint64_t x = xp;
+        if (rm.permute) {
+          x = 0;
+          for (int j = 0; j < rm.n; ++j) x |= ((xp >> j) & 1) << rm.bit[j];
+        }
+        const uint64_t open = (uint64_t)m & (((uint64_t)1 << (2 * v.n_open)) - 1);
+        const float4* row4 = reinterpret_cast<const float4*>(v.src + (int64_t)x * C + pdep64(open, v.open_dmask));
+        q[g][0] = __ldg(row4 + lane);
+        q[g][1] = __ldg(row4 + lane + 32);
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < kPrepRows; ++g)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const float e[4] = {fabsf(q[g][j].x), fabsf(q[g][j].y), fabsf(q[g][j].z), fabsf(q[g][j].w)};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          acc[4 * j + t] += e[t];
+          mx[4 * j + t] = fmaxf(mx[4 * j + t], e[t]);
+        }
+      }
+  }
+  for (int64_t r = warp; !vec4 && r < rows; r += nwarps) {
     const int64_t m = r + row0;
     const uint64_t xp = (uint64_t)m >> (2 * v.n_open);
     uint64_t x = xp;
@@ -723,8 +758,14 @@ int launch_prune_select(const OperandView& va, const int* a_bits, int a_nbits, i
       rm.bit[j] = (int8_t)bits[j];
       if (bits[j] != j) rm.permute = 1;
     }
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows * 32 + 255) / 256, (int64_t)sm_count() * 8));
+    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows * 32 + 255) / 256, (int64_t)sm_count() * 8));
     const size_t smem = 2 * (size_t)K * sizeof(float);
+    if (K <= 256) {
+      // one wave of grid-stride CTAs (a partial second wave would idle SMs)
+      int resident = 0;
+      CUTQC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, colw_kernel<8>, 256, smem));
+      blocks = std::min(blocks, sm_count() * std::max(1, resident));
+    }
     if (K <= 256) colw_kernel<8><<<blocks, 256, smem, st>>>(v, rm, row0, rows, K, out, omax);
     else colw_kernel<32><<<blocks, 256, smem, st>>>(v, rm, row0, rows, K, out, omax);
     CUTQC_LAUNCH_CHECK("colw_kernel");
