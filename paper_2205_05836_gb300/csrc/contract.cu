@@ -476,6 +476,8 @@ prep_small_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows, int64_t 
 // a submask increment), stage it in shared memory ([K][33], conflict-free
 // both ways), then write the rows K-major exactly as prep_kernel does.
 // Requires row0 % 32 == 0 so that a tile never straddles two source rows.
+constexpr int kTrBatch = 8;
+
 __global__ void prep_tr_kernel(OperandView v, RowMap rm, int64_t row0, int64_t rows, int64_t K, int64_t Kp,
                                float* __restrict__ out32, __half* __restrict__ hi, __half* __restrict__ lo,
                                float* __restrict__ scale, int64_t src_bstride, int64_t dst_bstride, int mode,
@@ -511,12 +513,20 @@ __global__ void prep_tr_kernel(OperandView v, RowMap rm, int64_t row0, int64_t r
     const bool rvalid = r0 + lane < rows;
     const float* base = v.src + (int64_t)x * C + (int64_t)open0 + lane;
     uint64_t col = col_lo;
-#pragma unroll 8
-    for (int64_t s = s_lo; s < s_hi; ++s) {
-      const float val = rvalid ? __ldg(base + col) : 0.f;
-      if (mode == 2) wmax = fmaxf(wmax, fabsf(val));
-      else tile[s * 33 + lane] = val;
-      col = ((col | ~smask) + 1) & smask;     // next submask of smask in increasing order
+    for (int64_t s0 = s_lo; s0 < s_hi; s0 += kTrBatch) {
+      // kTrBatch loads in flight per lane before any store to shared memory
+      float val[kTrBatch];
+#pragma unroll
+      for (int u = 0; u < kTrBatch; ++u) {
+        val[u] = (rvalid && s0 + u < s_hi) ? __ldg(base + col) : 0.f;
+        col = ((col | ~smask) + 1) & smask;     // next submask of smask in increasing order
+      }
+#pragma unroll
+      for (int u = 0; u < kTrBatch; ++u) {
+        if (s0 + u >= s_hi) break;
+        if (mode == 2) wmax = fmaxf(wmax, fabsf(val[u]));
+        else tile[(s0 + u) * 33 + lane] = val[u];
+      }
     }
     if (mode == 2) continue;
     __syncthreads();
