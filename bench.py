@@ -442,12 +442,10 @@ def run(args):
                                     sum_out=tot, ws=fd_ws, input_events=events)
 
     def attribute_and_reconstruct(dst=out, tot=total):
-        # the contraction of the second pair (C2 x C3, then the split of its
-        # 256 MB result) is the longer path to the last step: its inputs are
-        # attributed first, on one side stream; C1 and C0 follow on the
-        # other once C2's tensor is written, beside that contraction; the
-        # reconstruction, issued at once, starts each contraction when its
-        # own inputs are written (cutqc_fd_input_events)
+        # each pair's subcircuits attributed on a side stream of its own (C2
+        # and C3, then C1 and C0); the reconstruction, issued at once, starts
+        # each contraction when its own inputs are written
+        # (cutqc_fd_input_events) instead of after all four
         cur = torch.cuda.current_stream(dev)
         fork = torch.cuda.Event()
         fork.record(cur)
@@ -459,7 +457,6 @@ def run(args):
             for i in (2, 3):
                 cq.cutqc_attribute(subs[i], var[i], out=att[i], ws=att_ws[i])
                 ev[i].record(sa)
-        sb.wait_event(ev[2])
         with torch.cuda.stream(sb):
             for i in (1, 0):
                 cq.cutqc_attribute(subs[i], var[i], out=att[i], ws=att_ws[i])
